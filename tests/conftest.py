@@ -1,0 +1,22 @@
+"""Shared pytest configuration: the `gpu` marker and common fixtures."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
+    config.addinivalue_line("markers", "slow: oracle work taking more than a few seconds")
+
+
+@pytest.fixture(scope="session")
+def oracle():
+    """The FP64 CPU oracle (built on first use with gcc)."""
+    from oracle import oracle as orc
+    orc.build()
+    return orc
