@@ -1,0 +1,365 @@
+"""Throughput of the deformed hash-grid radiance field hot path on one B300 (or N replicas).
+
+One step = one training step over one batch of key-frame rays: ray sampling with
+occupancy skipping, nearest-node dual-quaternion warp, hash encoding, MLPs, compositing,
+Huber loss, the adjoint chain (compositing, MLPs, hash-table scatter) and Adam.  The
+workload is the training step of the paper-shaped synthetic capture: 2^18 rays drawn
+from four 512x512 ring cameras, 128 samples per ray, the human field (L=16, T=2^19, F=2)
+warped by a 2048-node graph (K=4) with 128^3 occupancy skipping.  The render throughput
+of the two-field 512x512 view (human + object, 128 samples) is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|bf16] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (the path has
+no exchange step at one GPU per key-frame set); value = all ranks' samples / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train samples/s (fwd+bwd) & render Mrays/s, mixed-prec vs FP32 at fixed error"
+UNIT = "samples/s"
+# kernels launched per TIMED record of the library (scan = 3 kernels, composite_train = 2)
+KERNELS_PER_RECORD = {"scan": 3, "composite_train": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rays", type=int, default=1 << 18)
+    ap.add_argument("--no-render", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device, self.rows, self.proc = device, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.05)
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ workloads
+def build_train(invr, ctx, tw, prec):
+    import torch
+    fields = {id(fp): invr.Field.from_synth(ctx, fp, prec) for fp in tw.fields}
+    keep, batches = [], []
+    for b in tw.batches:
+        g = None
+        if b.view.graph is not None:
+            sg = b.view.graph
+            g = invr.Graph(ctx, sg.x_canon.shape[1], sg.K, sg.radius, 1, torch.from_numpy(sg.x_canon).cuda())
+            g.set_pose(0, torch.from_numpy(sg.dq).cuda(), torch.from_numpy(sg.x_live).cuda())
+        occ = torch.from_numpy(b.view.occupancy).cuda() if b.view.occupancy is not None else None
+        view = invr.View(fields[id(b.view.field)], g, 0, b.view.rigid_dq, occ)
+        o = torch.from_numpy(b.rays.o).cuda()
+        d = torch.from_numpy(b.rays.d).cuda()
+        t = torch.from_numpy(b.target).cuda()
+        keep.append((g, occ, view))
+        batches.append((o, d, view, t))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    return tb, fields, keep
+
+
+def occupied_samples(invr, ctx, tb):
+    """Occupied samples per batch (the samples the path evaluates), via the sampling step."""
+    total = 0
+    for (o, d, view, _t) in tb.batches:
+        count, _, _ = invr.ray_samples(ctx, o, d, tb.args.batches[0].n_samples, view.occupancy)
+        total += int(count.sum().item())
+    return total
+
+
+# algorithmic work per kernel of one training step ("Roofline")
+def kernel_work(name, R, S_occ, n_samples, L, n_params, n_w):
+    mlp_f = 2 * n_w                       # multiply-adds x 2 per sample, forward
+    if name == "mlp_fwd":
+        return "alu", S_occ * mlp_f
+    if name == "mlp_bwd":
+        return "alu", S_occ * 3 * mlp_f   # recompute forward + input grads + weight grads
+    if name == "adam":
+        return "hbm", n_params * 32       # read p,g,m,v; write p,g(=0),m,v
+    if name == "encode":
+        return "hbm", S_occ * (12 + L * (8 * 8 + 8))    # vc in, 8 corner gathers + 2 features out per level
+    if name == "encode_bwd":
+        return "hbm", S_occ * (12 + L * (8 + 8 * 8))    # vc, dfeat in, 8 corner atomics per level
+    if name == "march_count":
+        return "hbm", R * 28
+    return None, None
+
+
+def fp32_alu_peak(sm_mhz):
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2304_03184_b300 import build, synth
+    build.build()
+    import paper_2304_03184_b300 as invr
+    prec = invr.INVR_FP32 if args.prec == "fp32" else invr.INVR_MLP_BF16
+    ctx = invr.Context(local)
+    tw = synth.train_step_workload(n_rays=args.rays)
+    tb, fields, keep = build_train(invr, ctx, tw, prec)
+    R = sum(b[0].shape[1] for b in tb.batches)
+    S_nom = R * tw.n_samples
+    S_occ = occupied_samples(invr, ctx, tb)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 126 MB L2
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        invr.train_step(ctx, tb)
+    ctx.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.enable_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        flush.fill_(1)                    # L2 flush between steps (outside the timed events)
+        a.record(stream)
+        invr.train_step(ctx, tb)
+        b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ktime = ctx.timing()
+    ctx.enable_timing(False)
+    ctx.sync()
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * S_nom / (ms * 1e-3)
+    launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktime.items())
+
+    # roofline of the dominant kernel
+    fp = tw.fields[0]
+    n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()
+    dom = max(ktime.items(), key=lambda kv: kv[1][0])
+    name, (kms, kn) = dom
+    bound, work = kernel_work(name, R, S_occ, tw.n_samples, fp.desc.L, n_params, fp.desc.n_weight_params())
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    roof = None
+    if bound == "alu":
+        peak = fp32_alu_peak(peaks.get("sm_max_mhz", 2032.0))
+        ach = work / (kms / kn * 1e-3) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x max SM clock"}
+    elif bound == "hbm":
+        peak = peaks.get("hbm_gbs", 6400.0)
+        ach = work / (kms / kn * 1e-3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    # end to end through the public API with host buffers: copy rays + targets in, loss out
+    e2e = None
+    if True:
+        host_in = [(b[0].cpu().pin_memory(), b[1].cpu().pin_memory(), b[3].cpu().pin_memory()) for b in tb.batches]
+        loss_h = torch.empty(1, pin_memory=True)
+        h2d = sum(x.numel() * 4 for trip in host_in for x in trip)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            for (ho, hd, ht), (o, d, _v, t) in zip(host_in, tb.batches):
+                o.copy_(ho, non_blocking=True)
+                d.copy_(hd, non_blocking=True)
+            # targets live back to back ([3][R_b] per batch) inside TrainBatches
+            off = 0
+            for (ho, hd, ht) in host_in:
+                n = ht.numel()
+                tb.targets[off:off + n].copy_(ht.reshape(-1), non_blocking=True)
+                off += n
+            loss = invr.train_step(ctx, tb)
+            loss_h.copy_(loss, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / args.steps
+        e2e = {"value": world * S_nom / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+
+    # render throughput of the two-field 512x512 view
+    render = None
+    if not args.no_render:
+        render = bench_render(invr, ctx, prec, args, flush)
+    clk = clocks.stop()          # sampled over the train, end-to-end and render regions
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16-mlp/f32",
+           "data": "synthetic",
+           "config": {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples,
+                      "occupied_samples": S_occ, "fields": len(tw.fields), "parallelism": f"replicas{world}",
+                      "l2": "flushed between timed steps (256 MiB write)", "prec": args.prec},
+           "roofline": roof, "e2e": e2e, "render": render, "clocks": clk, "gpu_launches": launches,
+           "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(ktime.items())}}
+    return out, tw
+
+
+def bench_render(invr, ctx, prec, args, flush):
+    import torch
+    from paper_2304_03184_b300 import synth
+    w = synth.two_field_render()
+    keep, views = [], []
+    for sv in w.views:
+        f = invr.Field.from_synth(ctx, sv.field, prec)
+        g = None
+        if sv.graph is not None:
+            gg = sv.graph
+            g = invr.Graph(ctx, gg.x_canon.shape[1], gg.K, gg.radius, 1, torch.from_numpy(gg.x_canon).cuda())
+            g.set_pose(0, torch.from_numpy(gg.dq).cuda(), torch.from_numpy(gg.x_live).cuda())
+        occ = torch.from_numpy(sv.occupancy).cuda()
+        keep.append((f, g, occ))
+        views.append(invr.View(f, g, 0, sv.rigid_dq, occ))
+    o, d = torch.from_numpy(w.rays.o).cuda(), torch.from_numpy(w.rays.d).cuda()
+    for _ in range(max(args.warmup, 3)):
+        invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, views)
+    ctx.sync()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        flush.fill_(1)
+        a.record(stream)
+        invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, views)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    return {"value": round(w.rays.n / (ms * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_frame": round(ms, 3),
+            "workload": w.name}
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+def oracle_train_sample(tw, n_rays):
+    """The oracle's train step (loss, gradient, Adam) on the first n_rays rays of the batch."""
+    from oracle import oracle
+    b = tw.batches[0]
+    sub = slice(0, n_rays)
+    f = oracle.Field.from_params(b.view.field)
+    v = oracle.View.from_synth(b.view, field=f)
+    ob = oracle.TrainBatch(b.rays.o[:, sub], b.rays.d[:, sub], v, b.target[:, sub])
+    t0 = time.perf_counter()
+    _, grads = oracle.train_loss_grad([ob], tw.n_samples, tw.t_eps, tw.huber_delta)
+    gt, gw = grads[id(f)]
+    p = np.concatenate([f.tables, f.weights])
+    m, vv = np.zeros_like(p), np.zeros_like(p)
+    oracle.adam(p, np.concatenate([gt, gw]), m, vv, 1, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(tw, n_rays=32768):
+    from oracle import oracle
+    oracle.build()
+    dt = oracle_train_sample(tw, n_rays)
+    return {"value": round(n_rays * tw.n_samples / dt, 1), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {n_rays} rays of the workload, one train step (loss+grad+Adam), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    from paper_2304_03184_b300 import synth
+    tw = synth.train_step_workload(n_rays=args.rays)
+    n = 1024
+    times = []
+    for _ in range(args.warmup):
+        oracle_train_sample(tw, n)
+    for _ in range(args.steps):
+        times.append(oracle_train_sample(tw, n))
+    ms = float(np.mean(times)) * 1e3
+    value = n * tw.n_samples / (ms * 1e-3)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": tw.name, "rays": n, "samples_per_ray": tw.n_samples,
+                       "note": "FP64 CPU oracle on a 1024-ray sample of the workload per step"},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n} rays x {tw.n_samples} samples per step"},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out, tw = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(tw)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

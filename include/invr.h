@@ -1,0 +1,234 @@
+/*
+ * invr.h -- C ABI of the B300 (sm_103a) hot path of Instant-NVR: per-ray-sample
+ * evaluation of the deformed hash-grid radiance field (warp -> hash encoding -> MLPs ->
+ * volume rendering), forward and training backward.
+ *
+ * The calls follow the paper's statement of the back-end's problem (Sec. 3 "Neural
+ * Rendering Back-end" and Sec. 4.2): per frame the back-end receives the tracked human
+ * motion {dq_i^t} on the deformation-graph nodes x_i and the object pose T^t; it keeps a
+ * canonical hash-grid radiance field per branch (H^h, E^h_g, E^h_c for the human,
+ * H^o, E^o_g, E^o_c for the object), trains them on key-frame rays and renders novel
+ * views, combining the two branches by depth (Sec. 4.3).
+ *
+ * General rules
+ *   - Every pointer named *_dev is device memory on the context's device, owned by the
+ *     caller; the library never frees it.  Host pointers are named without the suffix.
+ *   - Streams are passed as `invr_stream` (a cudaStream_t; NULL = the legacy default
+ *     stream).  Calls enqueue work and return; argument errors are reported
+ *     synchronously by the return code, device-side conditions (non-finite values) by a
+ *     device status word that invr_ctx_sync() reads.
+ *   - Handles are not thread-safe; use one handle from one host thread at a time.
+ *   - Layouts are structure-of-arrays: rays [3][R], node positions [3][N], node dual
+ *     quaternions [8][N] as (real w,x,y,z ; dual w,x,y,z), hash tables [L][T][F], MLP
+ *     weights W1..W5 row-major [out][in] concatenated.
+ *   - No exception crosses this boundary.  On error the last error text is kept in the
+ *     context (invr_last_error_detail).
+ */
+#ifndef INVR_H
+#define INVR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct invr_ctx_s* invr_ctx;     /* device, workspace, status word              */
+typedef struct invr_field_s* invr_field; /* hash tables + MLP weights + grads + Adam    */
+typedef struct invr_graph_s* invr_graph; /* deformation-graph nodes and per-frame poses */
+typedef void* invr_stream;               /* cudaStream_t                                */
+
+typedef enum {
+    INVR_OK = 0,
+    INVR_E_ARG = -1,        /* invalid argument (size, pointer, unsupported shape)   */
+    INVR_E_OOM = -2,        /* device allocation failed                               */
+    INVR_E_CUDA = -3,       /* a CUDA runtime call failed (text in last_error_detail) */
+    INVR_E_TIMEOUT = -4,    /* a bounded device-side wait gave up                     */
+    INVR_E_NONFINITE = -5,  /* a kernel produced a NaN/Inf output                      */
+    INVR_E_STATE = -6       /* call out of order (e.g. backward without forward)       */
+} invr_status;
+
+typedef enum {
+    INVR_FP32 = 0,      /* every step in FP32                                        */
+    INVR_MLP_FP16 = 1,  /* MLP GEMMs on tensor cores, FP16 operands, FP32 accumulate   */
+    INVR_MLP_BF16 = 2   /* MLP GEMMs on tensor cores, BF16 operands, FP32 accumulate   */
+} invr_precision;
+
+/* ------------------------------------------------------------------ context */
+/* Create a context on CUDA device `device`.  Owns the sample workspace (grown on demand,
+ * or sized once by invr_ctx_reserve) and a device status word. */
+invr_status invr_ctx_create(invr_ctx* out, int device);
+invr_status invr_ctx_destroy(invr_ctx ctx);
+
+/* Size the workspace for calls of up to max_rays rays in total (summed over views and
+ * batches) and max_samples samples per ray, so that later calls allocate nothing (needed
+ * before capturing calls into a CUDA graph). */
+invr_status invr_ctx_reserve(invr_ctx ctx, int64_t max_rays, int max_samples);
+
+/* Wait for `stream`, then read and clear the device status word: INVR_E_NONFINITE if a
+ * kernel flagged a non-finite output since the last sync, INVR_E_TIMEOUT if a bounded
+ * wait gave up, else INVR_OK. */
+invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around every kernel
+ * launch of the library (off by default).  enable != 0 starts a new record (clearing the
+ * old one).  invr_ctx_timing synchronises the device, then fills up to max entries:
+ * names[i] (static strings), total milliseconds ms[i] and launch counts launches[i], one
+ * entry per kernel name; it returns the number of entries (or a negative invr_status). */
+invr_status invr_ctx_enable_timing(invr_ctx ctx, int enable);
+int invr_ctx_timing(invr_ctx ctx, const char** names, double* ms, int64_t* launches, int max);
+
+const char* invr_status_string(invr_status s);
+/* Copy the text of the context's last error (NUL-terminated, truncated to n bytes). */
+invr_status invr_last_error_detail(invr_ctx ctx, char* buf, size_t n);
+
+/* ------------------------------------------------------------------ fields */
+/* One canonical radiance field (Sec. 4.2, "Separated instant neural representation"):
+ * a multiresolution hash encoding H (L levels of T = 2^log2_T entries of F features,
+ * level resolution floor(N_min growth^l)) feeding the geometry MLP E_g
+ * (mlp_in -> mlp_hidden -> mlp_hidden -> geo_out, ReLU, density exp(o_0)) and the colour
+ * MLP E_c (o_1..o_{geo_out-1} -> col_hidden -> 3, ReLU then sigmoid), no biases.
+ * Supported: L*F = mlp_in in {16, 32}, F = 2, L <= 16, mlp_hidden = col_hidden = 64,
+ * geo_out = 16, 10 <= log2_T <= 24.  Other shapes return INVR_E_ARG. */
+typedef struct {
+    int L, log2_T, F, N_min;
+    double growth;
+    int mlp_in, mlp_hidden, geo_out, col_hidden;
+    invr_precision prec;
+} invr_field_desc;
+
+/* Allocates parameters (tables + weights), gradients and Adam moments (zeroed, step 0).
+ * Parameters are undefined until invr_field_set_params. */
+invr_status invr_field_create(invr_ctx ctx, const invr_field_desc* desc, invr_field* out);
+invr_status invr_field_destroy(invr_field field);
+
+/* Copy parameters in: tables_dev [L][T][F] and weights_dev (W1..W5) FP32. */
+invr_status invr_field_set_params(invr_field field, const float* tables_dev, const float* weights_dev,
+                                  invr_stream stream);
+/* Copy parameters and optimiser state out; any pointer may be NULL.  Adam moments are laid
+ * out as tables then weights (L*T*F + n_weights floats).  *step (host) receives the number
+ * of Adam steps taken (read after the stream's prior work completes). */
+invr_status invr_field_get_params(invr_field field, float* tables_dev, float* weights_dev, float* adam_m_dev,
+                                  float* adam_v_dev, int64_t* step, invr_stream stream);
+/* Copy the accumulated gradients out (same layouts as the parameters); either may be NULL. */
+invr_status invr_field_get_grads(invr_field field, float* grad_tables_dev, float* grad_weights_dev,
+                                 invr_stream stream);
+invr_status invr_field_zero_grads(invr_field field, invr_stream stream);
+/* Number of weights of W1..W5 for a description (host-side helper). */
+int64_t invr_field_weight_count(const invr_field_desc* desc);
+
+/* ------------------------------------------------------------------ deformation graph */
+/* Embedded-deformation graph W = {dq_i, x_i} (Sec. 4.1, Eq. 2): n_nodes canonical nodes,
+ * K nearest deformed nodes blended per sample with weights exp(-|v - x_i^t|^2 / radius^2)
+ * (radius 0.1 in the paper), poses for n_frames frames.  Requires 1 <= K <= 8,
+ * K <= n_nodes <= 65535. */
+typedef struct {
+    int n_nodes, K;
+    float radius;
+    int n_frames;
+} invr_graph_desc;
+
+invr_status invr_graph_create(invr_ctx ctx, const invr_graph_desc* desc, const float* x_canon_dev,
+                              invr_graph* out);
+/* Set frame `frame`'s motion (Sec. 4.2, Eq. 4): node dual quaternions dq_dev [8][N]
+ * (canonical -> live) and deformed node positions x_live_dev [3][N] (x_i^t = dq_i^t x_i,
+ * the tracker's output).  The library copies both and builds, on `stream`, its
+ * per-frame nearest-node candidate grid over the live nodes. */
+invr_status invr_graph_set_pose(invr_graph graph, int frame, const float* dq_dev, const float* x_live_dev,
+                                invr_stream stream);
+invr_status invr_graph_destroy(invr_graph graph);
+
+/* ------------------------------------------------------------------ rendering */
+/* One field seen in one frame: the human field through `graph` at `frame` (inverse
+ * dual-quaternion-blend warp, Eq. 4), or, when graph == NULL, the object field through
+ * the rigid pose rigid_dq (host pointer to 8 floats: unit dual quaternion canonical ->
+ * live, Sec. 4.1 "Object Rigid Tracking"; its values are copied at call time).
+ * occupancy_dev: live-space 128^3 bitfield over [-1,1]^3 (bit x + 128(y + 128 z) set =
+ * occupied; samples in empty cells have zero density and are not evaluated) or NULL. */
+typedef struct {
+    invr_field field;
+    invr_graph graph;
+    int frame;
+    const float* rigid_dq;
+    const uint32_t* occupancy_dev;
+} invr_field_view;
+
+/* Volume rendering of n_rays rays (Sec. 3, "share volumetric rendering"): each ray is
+ * clipped to [-1,1]^3 and sampled at n_samples uniform midpoints; per view the samples
+ * are composited front to back, stopping after the first sample whose transmittance
+ * falls below t_eps.  With two views (view 0 = human, view 1 = object) the nearer field
+ * by expected depth is laid over the farther (Sec. 4.3).  Outputs: rgba_dev [4][R]
+ * (colour on a black background and opacity) and depth_dev [R] (opacity-weighted depth
+ * sum; divide by opacity for the expected depth).  1 <= n_samples <= 1024. */
+typedef struct {
+    int64_t n_rays;
+    const float* o_dev;  /* [3][R] */
+    const float* d_dev;  /* [3][R] */
+    int n_samples;
+    float t_eps;
+    int n_views;         /* 1 or 2 */
+    const invr_field_view* views;
+    float* rgba_dev;     /* [4][R] */
+    float* depth_dev;    /* [R]    */
+} invr_render_args;
+
+invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* args, invr_stream stream);
+
+/* ------------------------------------------------------------------ training */
+/* One training step over key-frame ray batches (Sec. 4.2 "On-the-fly Radiance Fields",
+ * key frames of Sec. 4.2): each batch is one field seen in one frame (n_views = 1; its
+ * rgba_dev/depth_dev may be NULL or receive the rendered values).  Loss: Huber penalty
+ * (threshold huber_delta) of rendered colour minus target, averaged over all rays of all
+ * batches and the 3 channels; targets_dev holds each batch's [3][R_b] block back to
+ * back.  The backward pass recomputes per-sample MLP activations, scatter-adds hash-table
+ * gradients, and Adam (lr, beta1, beta2, adam_eps, bias-corrected) then updates every
+ * parameter of every field used.  loss_dev (device, 1 float) receives the loss.  At most
+ * 16 batches. */
+typedef struct {
+    int n_batches;
+    const invr_render_args* batches;
+    const float* targets_dev;
+    float huber_delta;
+    float lr, beta1, beta2, adam_eps;
+    float* loss_dev;
+} invr_train_args;
+
+invr_status invr_train_step(invr_ctx ctx, const invr_train_args* args, invr_stream stream);
+
+/* The forward and backward halves of invr_train_step, for autograd front ends:
+ * forward_train renders every batch, writes loss_dev and keeps the per-sample state in the
+ * context's workspace; backward adds dLoss/dparams (scaled by grad_scale) into each
+ * field's gradient buffers; invr_field_adam applies one Adam step from the gradient
+ * buffer and zeroes it. */
+invr_status invr_field_forward_train(invr_ctx ctx, const invr_train_args* args, invr_stream stream);
+invr_status invr_field_backward(invr_ctx ctx, const invr_train_args* args, float grad_scale, invr_stream stream);
+invr_status invr_field_adam(invr_field field, float lr, float beta1, float beta2, float eps, invr_stream stream);
+
+/* ------------------------------------------------------------------ single steps */
+/* Samples of n_rays rays as the renderer takes them: count_dev [R] occupied samples per
+ * ray, t_dev [R][n_samples] and p_dev [3][R][n_samples] hold each ray's occupied samples
+ * in its first count slots (remaining slots untouched).  occupancy_dev may be NULL. */
+invr_status invr_ray_samples(invr_ctx ctx, int64_t n_rays, const float* o_dev, const float* d_dev, int n_samples,
+                             const uint32_t* occupancy_dev, int32_t* count_dev, float* t_dev, float* p_dev,
+                             invr_stream stream);
+/* Warp n live points p_dev [3][n] to canonical vc_dev [3][n] through `view` (Eq. 4 or
+ * the rigid pose).  knn_ids_dev [K][n] (may be NULL) receives the selected node ids,
+ * nearest first (human view only). */
+invr_status invr_warp_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p_dev,
+                             float* vc_dev, int32_t* knn_ids_dev, invr_stream stream);
+/* Hash-encode n canonical points x_dev [3][n]: feat_dev [L*F][n]; idx_dev [L*8][n] (may be
+ * NULL) receives the table slot of each level's 8 cell corners (bit 0 = +x, 1 = +y, 2 = +z). */
+invr_status invr_encode_points(invr_ctx ctx, invr_field field, int64_t n, const float* x_dev, float* feat_dev,
+                               uint32_t* idx_dev, invr_stream stream);
+/* Evaluate the MLPs on n feature vectors feat_dev [mlp_in][n]: out_dev [4][n] = (sigma,r,g,b). */
+invr_status invr_mlp_points(invr_ctx ctx, invr_field field, int64_t n, const float* feat_dev, float* out_dev,
+                            invr_stream stream);
+/* Warp + encode + MLPs at n live points p_dev [3][n]: out_dev [4][n] = (sigma,r,g,b). */
+invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p_dev,
+                              float* out_dev, invr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INVR_H */

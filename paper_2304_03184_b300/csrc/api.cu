@@ -1,0 +1,790 @@
+// C ABI of the hot path: handles, argument checks, workspace, and the launch sequences of
+// render_rays / train_step.  See include/invr.h for the contract of each call.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "invr.h"
+#include "invr_internal.cuh"
+
+using namespace invr;
+
+struct invr_ctx_s {
+  int device = 0;
+  int num_sms = 148;
+  Workspace ws{};
+  int64_t cap_R = 0, cap_S = 0;
+  bool cap_train = false;
+  unsigned* status = nullptr;
+  std::string err;
+  // per-kernel event timing (invr_ctx_enable_timing)
+  bool timing = false;
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  // state kept between invr_field_forward_train and invr_field_backward
+  bool fwd_valid = false;
+  Plan fwd_plan{};
+  std::vector<int64_t> fwd_sig;
+};
+
+struct invr_field_s {
+  invr_ctx ctx = nullptr;
+  invr_field_desc desc{};
+  int64_t n_tab = 0, n_w = 0;
+  float* params = nullptr;  // tables then weights
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  int64_t* step = nullptr;  // device step counter
+  int res[kMaxL] = {};
+  uint32_t dense_mask = 0;
+};
+
+struct invr_graph_s {
+  invr_ctx ctx = nullptr;
+  invr_graph_desc desc{};
+  float* x_canon = nullptr;
+  struct Frame {
+    float4* x_live = nullptr;
+    float4* dq = nullptr;
+    uint16_t* cand = nullptr;
+    uint16_t* cand_n = nullptr;
+    bool set = false;
+  };
+  std::vector<Frame> frames;
+  int cap = 0;  // 0: no candidate grid (scan all nodes)
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Brackets one launch with events on its stream when timing is enabled.
+struct Timed {
+  invr_ctx ctx;
+  cudaStream_t s;
+  invr_ctx_s::Rec rec{};
+  Timed(invr_ctx c, const char* name, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx->timing) return;
+    rec.name = name;
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    cudaEventRecord(rec.a, s);
+  }
+  ~Timed() {
+    if (!ctx->timing) return;
+    cudaEventRecord(rec.b, s);
+    ctx->recs.push_back(rec);
+  }
+};
+
+#define TIMED(ctx, name, s, call) \
+  [&]() -> cudaError_t {          \
+    Timed t_(ctx, name, s);       \
+    return (call);                \
+  }()
+
+void clear_timing(invr_ctx ctx) {
+  for (auto& r : ctx->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  ctx->recs.clear();
+}
+
+invr_status fail(invr_ctx ctx, invr_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+#define INVR_CUDA(ctx, call)                                                                     \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? INVR_E_OOM : INVR_E_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+template <class T>
+cudaError_t dmalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+int level_resolution(int N_min, double growth, int l) {
+  return (int)std::floor((double)N_min * std::pow(growth, (double)l));
+}
+
+int64_t weight_count(int in, int hidden, int geo, int col) {
+  return (int64_t)hidden * in + (int64_t)hidden * hidden + (int64_t)geo * hidden + (int64_t)col * (geo - 1) +
+         3LL * col;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &st);
+  return st != cudaStreamCaptureStatusNone;
+}
+
+void free_workspace(Workspace& w) {
+  void* ptrs[] = {w.ray_count, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray, w.s_t,
+                  w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part};
+  for (void* p : ptrs) dfree(p);
+  w = Workspace{};
+}
+
+// Grow the workspace to hold R rays and S sample slots (and the training buffers).
+invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cudaStream_t stream) {
+  if (R <= ctx->cap_R && S <= ctx->cap_S && (!train || ctx->cap_train)) return INVR_OK;
+  if (capturing(stream))
+    return fail(ctx, INVR_E_STATE, "workspace too small during stream capture: call invr_ctx_reserve first");
+  R = std::max(R, ctx->cap_R);
+  S = std::max(S, ctx->cap_S);
+  train = train || ctx->cap_train;
+  INVR_CUDA(ctx, cudaDeviceSynchronize());
+  free_workspace(ctx->ws);
+  ctx->cap_R = ctx->cap_S = 0;
+  ctx->cap_train = false;
+  Workspace& w = ctx->ws;
+  const int64_t blocks = R / 1024 + kMaxViews + 1;
+  INVR_CUDA(ctx, dmalloc(&w.ray_count, R));
+  INVR_CUDA(ctx, dmalloc(&w.ray_first, R));
+  INVR_CUDA(ctx, dmalloc(&w.ray_used, R));
+  INVR_CUDA(ctx, dmalloc(&w.ray_out, 5 * R));
+  INVR_CUDA(ctx, dmalloc(&w.block_sums, blocks));
+  INVR_CUDA(ctx, dmalloc(&w.view_base, 2 * (kMaxViews + 1)));
+  w.view_count = w.view_base + kMaxViews + 1;
+  INVR_CUDA(ctx, dmalloc(&w.s_ray, S));
+  INVR_CUDA(ctx, dmalloc(&w.s_t, S));
+  INVR_CUDA(ctx, dmalloc(&w.s_pos, 3 * S));
+  INVR_CUDA(ctx, dmalloc(&w.s_vc, 3 * S));
+  float* feat = nullptr;
+  INVR_CUDA(ctx, dmalloc(&feat, (size_t)kMaxIn * S));
+  w.feat = feat;
+  INVR_CUDA(ctx, dmalloc(&w.out, 4 * S));
+  INVR_CUDA(ctx, dmalloc(&w.loss_part, R / 256 + 1));
+  if (train) {
+    INVR_CUDA(ctx, dmalloc(&w.dout, 4 * S));
+    INVR_CUDA(ctx, dmalloc(&w.dfeat, (size_t)kMaxIn * S));
+  }
+  w.S_cap = S;
+  w.R_cap = R;
+  ctx->cap_R = R;
+  ctx->cap_S = S;
+  ctx->cap_train = train;
+  ctx->fwd_valid = false;
+  return INVR_OK;
+}
+
+FieldDev field_dev(invr_field f) {
+  FieldDev F{};
+  F.tables = f->params;
+  F.weights = f->params + f->n_tab;
+  F.weights_lp = nullptr;
+  F.grad_tables = f->grads;
+  F.grad_weights = f->grads + f->n_tab;
+  F.L = f->desc.L;
+  F.log2T = f->desc.log2_T;
+  F.mlp_in = f->desc.mlp_in;
+  F.mlp_kind = (int)f->desc.prec;
+  for (int l = 0; l < kMaxL; ++l) F.res[l] = f->res[l];
+  F.dense_mask = f->dense_mask;
+  return F;
+}
+
+// Rotation and translation of a (renormalised) unit dual quaternion, in double.
+void dq_rigid(const float* dq, float R[9], float t[3]) {
+  double b[8];
+  for (int i = 0; i < 8; ++i) b[i] = dq[i];
+  const double n = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3]);
+  double r[4], d[4], dot = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    r[i] = b[i] / n;
+    d[i] = b[4 + i] / n;
+  }
+  for (int i = 0; i < 4; ++i) dot += r[i] * d[i];
+  for (int i = 0; i < 4; ++i) d[i] -= dot * r[i];
+  const double w = r[0], x = r[1], y = r[2], z = r[3];
+  const double M[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                       2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                       2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+  for (int i = 0; i < 9; ++i) R[i] = (float)M[i];
+  // t = 2 vec(d r^*)
+  t[0] = (float)(2.0 * (-d[0] * x + d[1] * w - d[2] * z + d[3] * y));
+  t[1] = (float)(2.0 * (-d[0] * y + d[1] * z + d[2] * w - d[3] * x));
+  t[2] = (float)(2.0 * (-d[0] * z - d[1] * y + d[2] * x + d[3] * w));
+}
+
+invr_status warp_dev(invr_ctx ctx, const invr_field_view& v, WarpDev& W) {
+  W = WarpDev{};
+  if (!v.graph) {
+    if (!v.rigid_dq) return fail(ctx, INVR_E_ARG, "view without graph needs rigid_dq (8 host floats)");
+    W.mode = 0;
+    dq_rigid(v.rigid_dq, W.R, W.t);
+    return INVR_OK;
+  }
+  invr_graph g = v.graph;
+  if (g->ctx != ctx) return fail(ctx, INVR_E_ARG, "graph belongs to another context");
+  if (v.frame < 0 || v.frame >= (int)g->frames.size()) return fail(ctx, INVR_E_ARG, "frame out of range");
+  const auto& fr = g->frames[v.frame];
+  if (!fr.set) return fail(ctx, INVR_E_STATE, "frame pose not set (invr_graph_set_pose)");
+  W.mode = 1;
+  W.x_live = fr.x_live;
+  W.dq = fr.dq;
+  W.cand = fr.cand;
+  W.cand_n = fr.cand_n;
+  W.n_nodes = g->desc.n_nodes;
+  W.K = g->desc.K;
+  W.cap = g->cap;
+  W.inv_r2 = 1.0f / (g->desc.radius * g->desc.radius);
+  return INVR_OK;
+}
+
+invr_status check_field(invr_ctx ctx, invr_field f) {
+  if (!f) return fail(ctx, INVR_E_ARG, "null field");
+  if (f->ctx != ctx) return fail(ctx, INVR_E_ARG, "field belongs to another context");
+  return INVR_OK;
+}
+
+// Build the plan of a call: one entry per view (render) or per batch (training).
+invr_status build_plan(invr_ctx ctx, const std::vector<const invr_render_args*>& rays,
+                       const std::vector<const invr_field_view*>& views, int n_samples, float t_eps, Plan& P) {
+  P = Plan{};
+  const int nv = (int)views.size();
+  if (nv < 1 || nv > kMaxViews) return fail(ctx, INVR_E_ARG, "1..16 views/batches per call");
+  if (n_samples < 1 || n_samples > 1024) return fail(ctx, INVR_E_ARG, "n_samples must be in [1, 1024]");
+  P.n_views = nv;
+  P.n_samples = n_samples;
+  P.t_eps = t_eps;
+  P.agg_res = 256;
+  P.grad_scale = 1.0f;
+  int64_t ray_begin = 0;
+  int blocks = 0;
+  for (int i = 0; i < nv; ++i) {
+    const invr_render_args* a = rays[i];
+    const invr_field_view& v = *views[i];
+    if (a->n_rays < 0) return fail(ctx, INVR_E_ARG, "n_rays < 0");
+    if (a->n_rays > 0 && (!a->o_dev || !a->d_dev)) return fail(ctx, INVR_E_ARG, "null ray pointer");
+    invr_status st = check_field(ctx, v.field);
+    if (st != INVR_OK) return st;
+    ViewDev& V = P.v[i];
+    V.o = a->o_dev;
+    V.d = a->d_dev;
+    V.occ = v.occupancy_dev;
+    V.n_rays = a->n_rays;
+    V.ray_begin = ray_begin;
+    V.scan_block_begin = blocks;
+    V.field = field_dev(v.field);
+    st = warp_dev(ctx, v, V.warp);
+    if (st != INVR_OK) return st;
+    ray_begin += a->n_rays;
+    blocks += (int)((a->n_rays + 1023) / 1024);
+  }
+  P.total_rays = ray_begin;
+  P.n_scan_blocks = blocks;
+  P.status = ctx->status;
+  return INVR_OK;
+}
+
+cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = TIMED(ctx, "march_count", s, launch_march_count(P, s))) != cudaSuccess) return e;
+  if ((e = TIMED(ctx, "scan", s, launch_scan(P, s))) != cudaSuccess) return e;
+  if ((e = TIMED(ctx, "march_emit", s, launch_march_emit(P, s))) != cudaSuccess) return e;
+  if ((e = TIMED(ctx, "warp", s, launch_warp(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  if ((e = TIMED(ctx, "encode", s, launch_encode(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  return TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s));
+}
+
+invr_status check_desc(invr_ctx ctx, const invr_field_desc* d) {
+  if (!d) return fail(ctx, INVR_E_ARG, "null field desc");
+  if (d->F != kF) return fail(ctx, INVR_E_ARG, "F must be 2");
+  if (d->L < 1 || d->L > kMaxL) return fail(ctx, INVR_E_ARG, "L must be in [1, 16]");
+  if (d->mlp_in != d->L * d->F || (d->mlp_in != 16 && d->mlp_in != 32))
+    return fail(ctx, INVR_E_ARG, "mlp_in must equal L*F and be 16 or 32");
+  if (d->mlp_hidden != kHidden || d->col_hidden != kColHidden || d->geo_out != kGeoOut)
+    return fail(ctx, INVR_E_ARG, "mlp_hidden = col_hidden = 64 and geo_out = 16 are supported");
+  if (d->log2_T < 10 || d->log2_T > 24) return fail(ctx, INVR_E_ARG, "log2_T must be in [10, 24]");
+  if (d->N_min < 1 || !(d->growth >= 1.0)) return fail(ctx, INVR_E_ARG, "N_min >= 1 and growth >= 1 required");
+  if (d->prec != INVR_FP32 && d->prec != INVR_MLP_FP16 && d->prec != INVR_MLP_BF16)
+    return fail(ctx, INVR_E_ARG, "unknown precision");
+  if (level_resolution(d->N_min, d->growth, d->L - 1) > (1 << 20))
+    return fail(ctx, INVR_E_ARG, "finest level resolution above 2^20");
+  return INVR_OK;
+}
+
+std::vector<int64_t> signature(const invr_train_args* a) {
+  std::vector<int64_t> s{a->n_batches};
+  for (int b = 0; b < a->n_batches; ++b) {
+    s.push_back(a->batches[b].n_rays);
+    s.push_back((int64_t)(uintptr_t)a->batches[b].views[0].field);
+  }
+  return s;
+}
+
+invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s) {
+  if (!a || a->n_batches < 1 || a->n_batches > kMaxViews || !a->batches)
+    return fail(ctx, INVR_E_ARG, "1..16 batches per training call");
+  if (!a->targets_dev || !a->loss_dev) return fail(ctx, INVR_E_ARG, "null targets_dev or loss_dev");
+  std::vector<const invr_render_args*> rays;
+  std::vector<const invr_field_view*> views;
+  const int ns = a->batches[0].n_samples;
+  const float te = a->batches[0].t_eps;
+  for (int b = 0; b < a->n_batches; ++b) {
+    const invr_render_args& r = a->batches[b];
+    if (r.n_views != 1 || !r.views) return fail(ctx, INVR_E_ARG, "each training batch has exactly one view");
+    if (r.n_samples != ns || r.t_eps != te) return fail(ctx, INVR_E_ARG, "batches must share n_samples and t_eps");
+    rays.push_back(&r);
+    views.push_back(&r.views[0]);
+  }
+  Plan P;
+  invr_status st = build_plan(ctx, rays, views, ns, te, P);
+  if (st != INVR_OK) return st;
+  if (P.total_rays == 0) return fail(ctx, INVR_E_ARG, "training call without rays");
+  int64_t off = 0;
+  for (int b = 0; b < a->n_batches; ++b) {
+    P.v[b].target = a->targets_dev + 3 * off;
+    P.v[b].rgba_out = a->batches[b].rgba_dev;
+    P.v[b].depth_out = a->batches[b].depth_dev;
+    off += a->batches[b].n_rays;
+  }
+  P.loss_norm = (float)(1.0 / (3.0 * (double)P.total_rays));
+  P.huber_delta = a->huber_delta;
+  st = ensure_workspace(ctx, P.total_rays, P.total_rays * ns + (int64_t)P.n_views * kTile, true, s);
+  if (st != INVR_OK) return st;
+  P.ws = ctx->ws;
+  INVR_CUDA(ctx, run_forward(ctx, P, s));
+  INVR_CUDA(ctx, TIMED(ctx, "composite_train", s, launch_composite_train(P, a->loss_dev, s)));
+  ctx->fwd_plan = P;
+  ctx->fwd_sig = signature(a);
+  ctx->fwd_valid = true;
+  return INVR_OK;
+}
+
+invr_status train_backward(invr_ctx ctx, const invr_train_args* a, float scale, cudaStream_t s) {
+  if (!a || !ctx->fwd_valid || signature(a) != ctx->fwd_sig)
+    return fail(ctx, INVR_E_STATE, "invr_field_backward needs the matching invr_field_forward_train first");
+  Plan P = ctx->fwd_plan;
+  P.grad_scale = scale;
+  INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd", s, launch_mlp_bwd_f32(P, ctx->num_sms, s)));
+  P.grad_scale = 1.0f;  // dL/dfeat already carries the scale
+  INVR_CUDA(ctx, TIMED(ctx, "encode_bwd", s, launch_encode_bwd(P, ctx->num_sms, s)));
+  return INVR_OK;
+}
+
+invr_status adam_step(invr_field f, float lr, float b1, float b2, float eps, cudaStream_t s) {
+  invr_ctx ctx = f->ctx;
+  INVR_CUDA(ctx, TIMED(ctx, "step_increment", s, launch_step_increment(f->step, s)));
+  INVR_CUDA(ctx, TIMED(ctx, "adam", s,
+                       launch_adam(f->params, f->grads, f->grads, f->m, f->v, f->n_tab + f->n_w, f->step, lr, b1,
+                                   b2, eps, s)));
+  return INVR_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* invr_status_string(invr_status s) {
+  switch (s) {
+    case INVR_OK: return "ok";
+    case INVR_E_ARG: return "invalid argument";
+    case INVR_E_OOM: return "out of device memory";
+    case INVR_E_CUDA: return "CUDA error";
+    case INVR_E_TIMEOUT: return "device wait timed out";
+    case INVR_E_NONFINITE: return "non-finite value produced";
+    case INVR_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+invr_status invr_ctx_create(invr_ctx* out, int device) {
+  if (!out) return INVR_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return INVR_E_ARG;
+  DeviceGuard guard(device);
+  invr_ctx ctx = new invr_ctx_s();
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess || cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
+    delete ctx;
+    return INVR_E_OOM;
+  }
+  *out = ctx;
+  return INVR_OK;
+}
+
+invr_status invr_ctx_destroy(invr_ctx ctx) {
+  if (!ctx) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  clear_timing(ctx);
+  free_workspace(ctx->ws);
+  dfree(ctx->status);
+  delete ctx;
+  return INVR_OK;
+}
+
+invr_status invr_ctx_reserve(invr_ctx ctx, int64_t max_rays, int max_samples) {
+  if (!ctx || max_rays < 0 || max_samples < 1 || max_samples > 1024) return fail(ctx, INVR_E_ARG, "bad reserve sizes");
+  DeviceGuard guard(ctx->device);
+  return ensure_workspace(ctx, max_rays, max_rays * max_samples + (int64_t)kMaxViews * kTile, true, nullptr);
+}
+
+invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream) {
+  if (!ctx) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  INVR_CUDA(ctx, cudaStreamSynchronize(s));
+  unsigned st = 0;
+  INVR_CUDA(ctx, cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  INVR_CUDA(ctx, cudaMemset(ctx->status, 0, sizeof(unsigned)));
+  if (st & kStatusNonFinite) return fail(ctx, INVR_E_NONFINITE, "a kernel produced a non-finite output");
+  if (st & kStatusTimeout) return fail(ctx, INVR_E_TIMEOUT, "a bounded device wait gave up");
+  if (st & kStatusOverflow) return fail(ctx, INVR_E_STATE, "sample workspace overflow");
+  return INVR_OK;
+}
+
+invr_status invr_ctx_enable_timing(invr_ctx ctx, int enable) {
+  if (!ctx) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  clear_timing(ctx);
+  ctx->timing = enable != 0;
+  return INVR_OK;
+}
+
+int invr_ctx_timing(invr_ctx ctx, const char** names, double* ms, int64_t* launches, int max) {
+  if (!ctx || max < 0) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(ctx, INVR_E_CUDA, "synchronize failed");
+  int n = 0;
+  for (const auto& r : ctx->recs) {
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    int i = 0;
+    while (i < n && std::strcmp(names[i], r.name) != 0) ++i;
+    if (i == n) {
+      if (n == max) continue;
+      names[n] = r.name;
+      ms[n] = 0.0;
+      launches[n] = 0;
+      ++n;
+    }
+    ms[i] += t;
+    launches[i] += 1;
+  }
+  return n;
+}
+
+invr_status invr_last_error_detail(invr_ctx ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return INVR_E_ARG;
+  std::snprintf(buf, n, "%s", ctx->err.c_str());
+  return INVR_OK;
+}
+
+int64_t invr_field_weight_count(const invr_field_desc* d) {
+  if (!d) return -1;
+  return weight_count(d->mlp_in, d->mlp_hidden, d->geo_out, d->col_hidden);
+}
+
+invr_status invr_field_create(invr_ctx ctx, const invr_field_desc* desc, invr_field* out) {
+  if (!ctx || !out) return INVR_E_ARG;
+  *out = nullptr;
+  invr_status st = check_desc(ctx, desc);
+  if (st != INVR_OK) return st;
+  DeviceGuard guard(ctx->device);
+  invr_field f = new invr_field_s();
+  f->ctx = ctx;
+  f->desc = *desc;
+  f->n_tab = (int64_t)desc->L * ((int64_t)1 << desc->log2_T) * desc->F;
+  f->n_w = weight_count(desc->mlp_in, desc->mlp_hidden, desc->geo_out, desc->col_hidden);
+  for (int l = 0; l < desc->L; ++l) {
+    f->res[l] = level_resolution(desc->N_min, desc->growth, l);
+    const int64_t v = (int64_t)f->res[l] + 1;
+    if (v * v * v <= ((int64_t)1 << desc->log2_T)) f->dense_mask |= 1u << l;
+  }
+  const int64_t n = f->n_tab + f->n_w;
+  if (dmalloc(&f->params, n) != cudaSuccess || dmalloc(&f->grads, n) != cudaSuccess ||
+      dmalloc(&f->m, n) != cudaSuccess || dmalloc(&f->v, n) != cudaSuccess || dmalloc(&f->step, 1) != cudaSuccess) {
+    dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step);
+    delete f;
+    return fail(ctx, INVR_E_OOM, "field allocation failed");
+  }
+  cudaMemset(f->grads, 0, n * sizeof(float));
+  cudaMemset(f->m, 0, n * sizeof(float));
+  cudaMemset(f->v, 0, n * sizeof(float));
+  cudaMemset(f->step, 0, sizeof(int64_t));
+  INVR_CUDA(ctx, cudaDeviceSynchronize());
+  *out = f;
+  return INVR_OK;
+}
+
+invr_status invr_field_destroy(invr_field f) {
+  if (!f) return INVR_E_ARG;
+  DeviceGuard guard(f->ctx->device);
+  cudaDeviceSynchronize();
+  dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step);
+  delete f;
+  return INVR_OK;
+}
+
+invr_status invr_field_set_params(invr_field f, const float* tables_dev, const float* weights_dev, invr_stream stream) {
+  if (!f) return INVR_E_ARG;
+  invr_ctx ctx = f->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (tables_dev) INVR_CUDA(ctx, cudaMemcpyAsync(f->params, tables_dev, f->n_tab * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (weights_dev)
+    INVR_CUDA(ctx, cudaMemcpyAsync(f->params + f->n_tab, weights_dev, f->n_w * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return INVR_OK;
+}
+
+invr_status invr_field_get_params(invr_field f, float* tables_dev, float* weights_dev, float* m_dev, float* v_dev,
+                                  int64_t* step, invr_stream stream) {
+  if (!f) return INVR_E_ARG;
+  invr_ctx ctx = f->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = f->n_tab + f->n_w;
+  if (tables_dev) INVR_CUDA(ctx, cudaMemcpyAsync(tables_dev, f->params, f->n_tab * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (weights_dev)
+    INVR_CUDA(ctx, cudaMemcpyAsync(weights_dev, f->params + f->n_tab, f->n_w * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (m_dev) INVR_CUDA(ctx, cudaMemcpyAsync(m_dev, f->m, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (v_dev) INVR_CUDA(ctx, cudaMemcpyAsync(v_dev, f->v, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (step) {
+    INVR_CUDA(ctx, cudaStreamSynchronize(s));
+    INVR_CUDA(ctx, cudaMemcpy(step, f->step, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  }
+  return INVR_OK;
+}
+
+invr_status invr_field_get_grads(invr_field f, float* gt_dev, float* gw_dev, invr_stream stream) {
+  if (!f) return INVR_E_ARG;
+  invr_ctx ctx = f->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (gt_dev) INVR_CUDA(ctx, cudaMemcpyAsync(gt_dev, f->grads, f->n_tab * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (gw_dev)
+    INVR_CUDA(ctx, cudaMemcpyAsync(gw_dev, f->grads + f->n_tab, f->n_w * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return INVR_OK;
+}
+
+invr_status invr_field_zero_grads(invr_field f, invr_stream stream) {
+  if (!f) return INVR_E_ARG;
+  invr_ctx ctx = f->ctx;
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, cudaMemsetAsync(f->grads, 0, (f->n_tab + f->n_w) * sizeof(float), static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_graph_create(invr_ctx ctx, const invr_graph_desc* desc, const float* x_canon_dev, invr_graph* out) {
+  if (!ctx || !out || !desc) return INVR_E_ARG;
+  *out = nullptr;
+  if (desc->K < 1 || desc->K > 8 || desc->n_nodes < desc->K || desc->n_nodes > 65535)
+    return fail(ctx, INVR_E_ARG, "need 1 <= K <= 8 and K <= n_nodes <= 65535");
+  if (desc->n_frames < 1 || !(desc->radius > 0.0f)) return fail(ctx, INVR_E_ARG, "need n_frames >= 1 and radius > 0");
+  DeviceGuard guard(ctx->device);
+  invr_graph g = new invr_graph_s();
+  g->ctx = ctx;
+  g->desc = *desc;
+  g->frames.resize(desc->n_frames);
+  g->cap = desc->n_nodes <= 64 ? 0 : (desc->K <= 4 ? 64 : 128);
+  if (dmalloc(&g->x_canon, 3 * (size_t)desc->n_nodes) != cudaSuccess) {
+    delete g;
+    return fail(ctx, INVR_E_OOM, "graph allocation failed");
+  }
+  if (x_canon_dev)
+    INVR_CUDA(ctx, cudaMemcpy(g->x_canon, x_canon_dev, 3 * (size_t)desc->n_nodes * sizeof(float), cudaMemcpyDeviceToDevice));
+  *out = g;
+  return INVR_OK;
+}
+
+invr_status invr_graph_set_pose(invr_graph g, int frame, const float* dq_dev, const float* x_live_dev, invr_stream stream) {
+  if (!g) return INVR_E_ARG;
+  invr_ctx ctx = g->ctx;
+  if (frame < 0 || frame >= (int)g->frames.size()) return fail(ctx, INVR_E_ARG, "frame out of range");
+  if (!dq_dev || !x_live_dev) return fail(ctx, INVR_E_ARG, "null pose pointer");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto& fr = g->frames[frame];
+  const int N = g->desc.n_nodes;
+  if (!fr.x_live) {
+    if (capturing(s)) return fail(ctx, INVR_E_STATE, "first pose of a frame cannot be set during capture");
+    INVR_CUDA(ctx, dmalloc(&fr.x_live, N));
+    INVR_CUDA(ctx, dmalloc(&fr.dq, 2 * (size_t)N));
+    if (g->cap > 0) {
+      const size_t cells = (size_t)kKnnG * kKnnG * kKnnG;
+      INVR_CUDA(ctx, dmalloc(&fr.cand, cells * g->cap));
+      INVR_CUDA(ctx, dmalloc(&fr.cand_n, cells));
+    }
+  }
+  INVR_CUDA(ctx, TIMED(ctx, "graph_pack", s, launch_graph_pack(dq_dev, x_live_dev, N, fr.dq, fr.x_live, s)));
+  if (g->cap > 0)
+    INVR_CUDA(ctx, TIMED(ctx, "knn_grid_build", s,
+                         launch_knn_grid_build(fr.x_live, N, g->desc.K, g->cap, fr.cand, fr.cand_n, ctx->num_sms, s)));
+  fr.set = true;
+  return INVR_OK;
+}
+
+invr_status invr_graph_destroy(invr_graph g) {
+  if (!g) return INVR_E_ARG;
+  DeviceGuard guard(g->ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& fr : g->frames) {
+    dfree(fr.x_live); dfree(fr.dq); dfree(fr.cand); dfree(fr.cand_n);
+  }
+  dfree(g->x_canon);
+  delete g;
+  return INVR_OK;
+}
+
+invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* a, invr_stream stream) {
+  if (!ctx || !a) return INVR_E_ARG;
+  if (a->n_views < 1 || a->n_views > 2 || !a->views) return fail(ctx, INVR_E_ARG, "render takes 1 or 2 views");
+  if (a->n_rays > 0 && (!a->rgba_dev || !a->depth_dev)) return fail(ctx, INVR_E_ARG, "null output pointer");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (a->n_rays == 0) return INVR_OK;
+  std::vector<const invr_render_args*> rays(a->n_views, a);
+  std::vector<const invr_field_view*> views;
+  for (int v = 0; v < a->n_views; ++v) views.push_back(&a->views[v]);
+  Plan P;
+  invr_status st = build_plan(ctx, rays, views, a->n_samples, a->t_eps, P);
+  if (st != INVR_OK) return st;
+  st = ensure_workspace(ctx, P.total_rays, P.total_rays * a->n_samples + (int64_t)P.n_views * kTile, false, s);
+  if (st != INVR_OK) return st;
+  P.ws = ctx->ws;
+  ctx->fwd_valid = false;
+  INVR_CUDA(ctx, run_forward(ctx, P, s));
+  INVR_CUDA(ctx, TIMED(ctx, "composite_render", s, launch_composite_render(P, a->n_rays, a->rgba_dev, a->depth_dev, s)));
+  return INVR_OK;
+}
+
+invr_status invr_field_forward_train(invr_ctx ctx, const invr_train_args* a, invr_stream stream) {
+  if (!ctx) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  return train_forward(ctx, a, static_cast<cudaStream_t>(stream));
+}
+
+invr_status invr_field_backward(invr_ctx ctx, const invr_train_args* a, float grad_scale, invr_stream stream) {
+  if (!ctx) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  return train_backward(ctx, a, grad_scale, static_cast<cudaStream_t>(stream));
+}
+
+invr_status invr_field_adam(invr_field f, float lr, float b1, float b2, float eps, invr_stream stream) {
+  if (!f) return INVR_E_ARG;
+  DeviceGuard guard(f->ctx->device);
+  return adam_step(f, lr, b1, b2, eps, static_cast<cudaStream_t>(stream));
+}
+
+invr_status invr_train_step(invr_ctx ctx, const invr_train_args* a, invr_stream stream) {
+  if (!ctx) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  invr_status st = train_forward(ctx, a, s);
+  if (st != INVR_OK) return st;
+  st = train_backward(ctx, a, 1.0f, s);
+  if (st != INVR_OK) return st;
+  std::vector<invr_field> done;
+  for (int b = 0; b < a->n_batches; ++b) {
+    invr_field f = a->batches[b].views[0].field;
+    if (std::find(done.begin(), done.end(), f) != done.end()) continue;
+    done.push_back(f);
+    st = adam_step(f, a->lr, a->beta1, a->beta2, a->adam_eps, s);
+    if (st != INVR_OK) return st;
+  }
+  return INVR_OK;
+}
+
+invr_status invr_ray_samples(invr_ctx ctx, int64_t n_rays, const float* o, const float* d, int n_samples,
+                             const uint32_t* occ, int32_t* count, float* t, float* p, invr_stream stream) {
+  if (!ctx || n_rays < 0 || n_samples < 1 || n_samples > 1024) return fail(ctx, INVR_E_ARG, "bad ray_samples sizes");
+  if (n_rays > 0 && (!o || !d || !count || !t || !p)) return fail(ctx, INVR_E_ARG, "null pointer");
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, launch_ray_samples(n_rays, o, d, n_samples, occ, count, t, p, static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_warp_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p, float* vc,
+                             int32_t* ids, invr_stream stream) {
+  if (!ctx || !view || n < 0) return fail(ctx, INVR_E_ARG, "bad warp_points arguments");
+  if (n > 0 && (!p || !vc)) return fail(ctx, INVR_E_ARG, "null pointer");
+  DeviceGuard guard(ctx->device);
+  WarpDev W;
+  invr_status st = warp_dev(ctx, *view, W);
+  if (st != INVR_OK) return st;
+  INVR_CUDA(ctx, launch_warp_points(W, n, p, vc, W.mode == 1 ? ids : nullptr, static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_encode_points(invr_ctx ctx, invr_field f, int64_t n, const float* x, float* feat, uint32_t* idx,
+                               invr_stream stream) {
+  if (!ctx || n < 0) return fail(ctx, INVR_E_ARG, "bad encode_points arguments");
+  invr_status st = check_field(ctx, f);
+  if (st != INVR_OK) return st;
+  if (n > 0 && (!x || !feat)) return fail(ctx, INVR_E_ARG, "null pointer");
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, launch_encode_points(field_dev(f), n, x, feat, idx, static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_mlp_points(invr_ctx ctx, invr_field f, int64_t n, const float* feat, float* out, invr_stream stream) {
+  if (!ctx || n < 0) return fail(ctx, INVR_E_ARG, "bad mlp_points arguments");
+  invr_status st = check_field(ctx, f);
+  if (st != INVR_OK) return st;
+  if (n > 0 && (!feat || !out)) return fail(ctx, INVR_E_ARG, "null pointer");
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, launch_mlp_points_f32(field_dev(f), n, feat, out, ctx->num_sms, static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p, float* out,
+                              invr_stream stream) {
+  if (!ctx || !view || n < 0) return fail(ctx, INVR_E_ARG, "bad query_points arguments");
+  invr_status st = check_field(ctx, view->field);
+  if (st != INVR_OK) return st;
+  if (n == 0) return INVR_OK;
+  if (!p || !out) return fail(ctx, INVR_E_ARG, "null pointer");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WarpDev W;
+  st = warp_dev(ctx, *view, W);
+  if (st != INVR_OK) return st;
+  float *vc = nullptr, *feat = nullptr;
+  INVR_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void**>(&vc), 3 * n * sizeof(float), s));
+  INVR_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void**>(&feat), (size_t)view->field->desc.mlp_in * n * sizeof(float), s));
+  const FieldDev F = field_dev(view->field);
+  cudaError_t e = launch_warp_points(W, n, p, vc, nullptr, s);
+  if (e == cudaSuccess) e = launch_encode_points(F, n, vc, feat, nullptr, s);
+  if (e == cudaSuccess) e = launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s);
+  cudaFreeAsync(vc, s);
+  cudaFreeAsync(feat, s);
+  INVR_CUDA(ctx, e);
+  return INVR_OK;
+}
+
+}  // extern "C"

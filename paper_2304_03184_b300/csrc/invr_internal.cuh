@@ -1,0 +1,234 @@
+// Internal structures and device helpers of the sm_103a hot path.
+//
+// Every launch receives a `Plan` by value (__grid_constant__): the view table (one entry
+// per field-in-a-frame), the sample-workspace pointers and the sizes.  Nothing is copied
+// host->device per call, so a whole render or train step can be captured in a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace invr {
+
+constexpr int kMaxViews = 16;   // batches per call (8 key frames x 2 fields)
+constexpr int kMaxL = 16;       // hash levels
+constexpr int kF = 2;           // features per level
+constexpr int kMaxIn = kMaxL * kF;
+constexpr int kHidden = 64;
+constexpr int kGeoOut = 16;
+constexpr int kColHidden = 64;
+constexpr int kOccRes = 128;    // occupancy grid resolution over [-1,1]^3
+constexpr int kTile = 128;      // sample tile: every view's sample range is padded to it
+constexpr int kKnnG = 64;       // nearest-node candidate grid resolution over [-1,1]^3
+constexpr uint16_t kKnnOverflow = 0xFFFF;
+
+// Device status word bits (read and cleared by invr_ctx_sync).
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+constexpr unsigned kStatusOverflow = 4u;
+
+enum MlpKind : int { kMlpF32 = 0, kMlpF16 = 1, kMlpBF16 = 2 };
+
+struct FieldDev {
+  const float* tables;      // [L][T][F]
+  const float* weights;     // W1..W5 FP32, row-major [out][in]
+  const void* weights_lp;   // packed 16-bit weights for the tensor-core MLP (or null)
+  float* grad_tables;       // [L][T][F]
+  float* grad_weights;      // W1..W5
+  int L, log2T, mlp_in, mlp_kind;
+  int res[kMaxL];           // level resolutions N_l
+  uint32_t dense_mask;      // bit l: level l stored densely
+};
+
+struct WarpDev {
+  int mode;                 // 0 = rigid pose, 1 = dual-quaternion blend of K nodes
+  float R[9];               // rigid: rotation (row-major) and translation of the pose
+  float t[3];
+  const float4* x_live;     // [N] (x, y, z, 0)
+  const float4* dq;         // [N][2] (real, dual)
+  const uint16_t* cand;     // [G^3][cap] candidate node ids per grid cell
+  const uint16_t* cand_n;   // [G^3] candidate count, kKnnOverflow = use all nodes
+  int n_nodes, K, cap;
+  float inv_r2;             // 1 / radius^2
+};
+
+struct ViewDev {
+  const float* o;           // [3][n_rays]
+  const float* d;           // [3][n_rays]
+  const uint32_t* occ;      // 128^3 bits or null
+  const float* target;      // [3][n_rays] (training) or null
+  float* rgba_out;          // [4][n_rays] per-view output (training) or null
+  float* depth_out;         // [n_rays] or null
+  int64_t n_rays;
+  int64_t ray_begin;        // first global ray index of this view
+  int scan_block_begin;     // first scan block of this view
+  FieldDev field;
+  WarpDev warp;
+};
+
+struct Workspace {
+  int32_t* ray_count;       // [R] occupied samples per ray
+  int32_t* ray_first;       // [R] first sample slot of the ray
+  int32_t* ray_used;        // [R] samples composited (early termination)
+  float* ray_out;           // [5][R] C, A, D per global ray
+  int32_t* block_sums;      // [n_scan_blocks]
+  int32_t* view_base;       // [kMaxViews + 1] padded sample base per view; [n_views] = total
+  int32_t* view_count;      // [kMaxViews] occupied samples per view (before padding)
+  int32_t* s_ray;           // [S] global ray id of each sample, -1 = padding
+  float* s_t;               // [S] sample depth t_j
+  float* s_pos;             // [3][S] live position
+  float* s_vc;              // [3][S] canonical position
+  void* feat;               // [mlp_in][S] FP32, or [S][mlp_in] 16-bit for the tensor-core MLP
+  float* out;               // [4][S] sigma, r, g, b
+  float* dout;              // [4][S] dL/d o_0, dL/d z_rgb
+  float* dfeat;             // [mlp_in][S]
+  float* loss_part;         // [n loss blocks]
+  int64_t S_cap;            // sample slots
+  int64_t R_cap;            // ray slots
+};
+
+struct Plan {
+  int n_views;
+  int n_samples;
+  float t_eps;
+  int n_scan_blocks;
+  int64_t total_rays;
+  float loss_norm;          // 1 / (3 * total_rays)
+  float huber_delta;
+  float grad_scale;
+  int agg_res;              // levels with N_l <= agg_res aggregate gradient runs per warp
+  Workspace ws;
+  unsigned* status;         // device status word
+  ViewDev v[kMaxViews];
+};
+
+// ------------------------------------------------------------------ FP32 recipes
+// The discrete decisions (sample positions, occupancy cell, hash cell, nearest-node key)
+// use explicitly rounded single-precision operations (no contraction into FMA), so that
+// they are reproducible by any implementation performing the same rounded operations.
+
+__device__ __forceinline__ bool ray_box(float3 o, float3 d, int n_samples, float& tn, float& dt) {
+  float tnear = -INFINITY, tfar = INFINITY;
+  const float oo[3] = {o.x, o.y, o.z};
+  const float dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (dd[a] == 0.0f) {
+      if (oo[a] < -1.0f || oo[a] > 1.0f) return false;
+      continue;
+    }
+    float t0 = __fdiv_rn(__fsub_rn(-1.0f, oo[a]), dd[a]);
+    float t1 = __fdiv_rn(__fsub_rn(1.0f, oo[a]), dd[a]);
+    float lo = t0 < t1 ? t0 : t1;
+    float hi = t0 < t1 ? t1 : t0;
+    if (lo > tnear) tnear = lo;
+    if (hi < tfar) tfar = hi;
+  }
+  tn = tnear > 0.0f ? tnear : 0.0f;
+  if (!(tfar > tn)) return false;
+  dt = __fdiv_rn(__fsub_rn(tfar, tn), (float)n_samples);
+  return true;
+}
+
+__device__ __forceinline__ float sample_t(float tn, float dt, int j) {
+  return __fadd_rn(tn, __fmul_rn(__fadd_rn((float)j, 0.5f), dt));
+}
+
+__device__ __forceinline__ float3 sample_p(float3 o, float3 d, float t) {
+  return make_float3(__fadd_rn(o.x, __fmul_rn(t, d.x)), __fadd_rn(o.y, __fmul_rn(t, d.y)),
+                     __fadd_rn(o.z, __fmul_rn(t, d.z)));
+}
+
+__device__ __forceinline__ int grid_cell(float x, int res) {
+  float q = __fmul_rn(__fmul_rn(__fadd_rn(x, 1.0f), 0.5f), (float)res);
+  int i = (int)floorf(q);
+  return i < 0 ? 0 : (i > res - 1 ? res - 1 : i);
+}
+
+__device__ __forceinline__ bool occupied(const uint32_t* bits, float3 p) {
+  uint32_t idx = (uint32_t)grid_cell(p.x, kOccRes) +
+                 kOccRes * ((uint32_t)grid_cell(p.y, kOccRes) + kOccRes * (uint32_t)grid_cell(p.z, kOccRes));
+  return (__ldg(bits + (idx >> 5)) >> (idx & 31u)) & 1u;
+}
+
+// Hash-level cell of one coordinate: u = clamp((x+1)/2, 0, 1), q = u N, c = min(floor q, N-1)
+// (the FP32 decision).  The fraction q - c is evaluated as x N/2 + (N/2 - c) with a single
+// rounding (N/2 - c is exact), so it is accurate to ~1e-7 even where q ~ 2000 has an FP32
+// spacing of 1.2e-4; it may fall a rounding step outside [0,1] next to a cell boundary,
+// where the trilinear blend is continuous.
+__device__ __forceinline__ int level_cell(float x, int res, float& frac) {
+  float u = __fmul_rn(__fadd_rn(x, 1.0f), 0.5f);
+  u = fminf(fmaxf(u, 0.0f), 1.0f);
+  float q = __fmul_rn(u, (float)res);
+  int c = (int)floorf(q);
+  c = c > res - 1 ? res - 1 : c;
+  const float half = 0.5f * (float)res;
+  const float xc = fminf(fmaxf(x, -1.0f), 1.0f);
+  frac = __fmaf_rn(xc, half, half - (float)c);
+  return c;
+}
+
+__device__ __forceinline__ uint32_t vertex_index(uint32_t x, uint32_t y, uint32_t z, int res, bool dense,
+                                                 uint32_t tmask) {
+  if (dense) {
+    uint32_t n = (uint32_t)res + 1u;
+    return x + y * n + z * n * n;
+  }
+  return ((x * 1u) ^ (y * 2654435761u) ^ (z * 805459861u)) & tmask;
+}
+
+__device__ __forceinline__ float knn_key(float3 p, float4 x) {
+  float dx = __fsub_rn(p.x, x.x), dy = __fsub_rn(p.y, x.y), dz = __fsub_rn(p.z, x.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// View of a global ray / of a padded sample slot (linear search over <= 16 views).
+__device__ __forceinline__ int view_of_ray(const Plan& P, int64_t g) {
+  int v = 0;
+  while (v + 1 < P.n_views && g >= P.v[v + 1].ray_begin) ++v;
+  return v;
+}
+
+__device__ __forceinline__ int view_of_slot(const int32_t* view_base, int n_views, int64_t s) {
+  int v = 0;
+  while (v + 1 < n_views && s >= view_base[v + 1]) ++v;
+  return v;
+}
+
+__device__ __forceinline__ void flag_status(unsigned* status, unsigned bit) { atomicOr(status, bit); }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ launchers
+// Each returns cudaGetLastError() of its launches.
+cudaError_t launch_march_count(const Plan& P, cudaStream_t s);
+cudaError_t launch_scan(const Plan& P, cudaStream_t s);
+cudaError_t launch_march_emit(const Plan& P, cudaStream_t s);
+cudaError_t launch_warp(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s);
+cudaError_t launch_composite_train(const Plan& P, float* loss, cudaStream_t s);
+cudaError_t launch_adam(float* params, const float* grads_in, float* grads_zero, float* m, float* v, int64_t n,
+                        const int64_t* step_dev, float lr, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t launch_step_increment(int64_t* step_dev, cudaStream_t s);
+
+// graph preprocessing
+cudaError_t launch_graph_pack(const float* dq_soa, const float* x_soa, int n, float4* dq_out, float4* x_out,
+                              cudaStream_t s);
+cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* cand, uint16_t* cand_n,
+                                  int num_sms, cudaStream_t s);
+
+// single-step entry points
+cudaError_t launch_ray_samples(int64_t n_rays, const float* o, const float* d, int n_samples, const uint32_t* occ,
+                               int32_t* count, float* t, float* p, cudaStream_t s);
+cudaError_t launch_warp_points(const WarpDev& w, int64_t n, const float* p, float* vc, int32_t* ids,
+                               cudaStream_t s);
+cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, float* feat, uint32_t* idx,
+                                 cudaStream_t s);
+cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
+                                  cudaStream_t s);
+
+}  // namespace invr

@@ -1,0 +1,198 @@
+// Front-to-back volume rendering of every ray through every view (Sec. 3 "share
+// volumetric rendering"; Sec. 4.3 depth-occlusion composition), and, for training, the
+// Huber colour loss and the adjoint of the compositing.
+//
+//   alpha_j = 1 - exp(-sigma_j dt),  T_{j+1} = T_j (1 - alpha_j),
+//   C = sum T_j alpha_j c_j,  A = sum T_j alpha_j,  D = sum T_j alpha_j t_j,
+// over the occupied samples in order, stopping after the first with T_{j+1} < t_eps.
+// Two views (human, object): the nearer by expected depth (D_h A_o <= D_o A_h, ties to
+// the human) is laid over the farther: X = X_n + (1 - A_n) X_f for X in {C, A, D}.
+//
+// Training adjoint per ray (k <= stop):
+//   dC/dc_j = T_j alpha_j,   dC/dsigma_j = dt (T_{j+1} c_j - (C - sum_{k<=j} T_k alpha_k c_k))
+// folded with sigma = exp(o_0) and c = sigmoid(z) into dL/do_0 and dL/dz per sample.
+//
+// One thread per ray; bound by the per-sample reads (16 B/sample).
+#include "invr_internal.cuh"
+
+namespace invr {
+
+__device__ __forceinline__ bool ray_dt(const ViewDev& V, int64_t r, int n_samples, float& dt) {
+  const int64_t n = V.n_rays;
+  const float3 o = make_float3(__ldg(V.o + r), __ldg(V.o + n + r), __ldg(V.o + 2 * n + r));
+  const float3 d = make_float3(__ldg(V.d + r), __ldg(V.d + n + r), __ldg(V.d + 2 * n + r));
+  float tn;
+  return ray_box(o, d, n_samples, tn, dt);
+}
+
+// Composite one ray of one view; res = (C.rgb, A, D); returns samples used.
+__device__ __forceinline__ int composite(const Plan& P, int64_t g, float dt, float res[5]) {
+  const int64_t S_cap = P.ws.S_cap;
+  const int64_t first = P.ws.ray_first[g];
+  const int cnt = P.ws.ray_count[g];
+  float T = 1.0f;
+  for (int c = 0; c < 5; ++c) res[c] = 0.0f;
+  int used = cnt;
+  for (int k = 0; k < cnt; ++k) {
+    const int64_t s = first + k;
+    const float sigma = P.ws.out[s];
+    const float x = sigma * dt;
+    const float alpha = -expm1f(-x);
+    const float w = T * alpha;
+    res[0] = fmaf(w, P.ws.out[S_cap + s], res[0]);
+    res[1] = fmaf(w, P.ws.out[2 * S_cap + s], res[1]);
+    res[2] = fmaf(w, P.ws.out[3 * S_cap + s], res[2]);
+    res[3] += w;
+    res[4] = fmaf(w, P.ws.s_t[s], res[4]);
+    T *= expf(-x);
+    if (T < P.t_eps) {
+      used = k + 1;
+      break;
+    }
+  }
+  return used;
+}
+
+__global__ void __launch_bounds__(256) k_composite_render(const __grid_constant__ Plan P, int64_t n_rays,
+                                                          float* rgba, float* depth) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  if (P.ws.view_base[P.n_views] > P.ws.S_cap) return;
+  float res[2][5];
+  for (int v = 0; v < P.n_views; ++v) {
+    const int64_t g = P.v[v].ray_begin + r;
+    float dt = 0.0f;
+    if (ray_dt(P.v[v], r, P.n_samples, dt)) {
+      P.ws.ray_used[g] = composite(P, g, dt, res[v]);
+    } else {
+      for (int c = 0; c < 5; ++c) res[v][c] = 0.0f;
+      P.ws.ray_used[g] = 0;
+    }
+  }
+  float out[5];
+  if (P.n_views == 1) {
+    for (int c = 0; c < 5; ++c) out[c] = res[0][c];
+  } else {
+    const bool human_near = res[0][4] * res[1][3] <= res[1][4] * res[0][3];
+    const float* n = res[human_near ? 0 : 1];
+    const float* f = res[human_near ? 1 : 0];
+    for (int c = 0; c < 5; ++c) out[c] = n[c] + (1.0f - n[3]) * f[c];
+  }
+  bool finite = true;
+  for (int c = 0; c < 4; ++c) {
+    rgba[c * n_rays + r] = out[c];
+    finite &= isfinite(out[c]);
+  }
+  depth[r] = out[4];
+  if (!(finite && isfinite(out[4]))) flag_status(P.status, kStatusNonFinite);
+}
+
+cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s) {
+  if (n_rays > 0) k_composite_render<<<ceil_div(n_rays, 256), 256, 0, s>>>(P, n_rays, rgba, depth);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ training
+__device__ __forceinline__ float huber(float x, float delta) {
+  const float ax = fabsf(x);
+  return ax <= delta ? 0.5f * x * x : delta * (ax - 0.5f * delta);
+}
+
+__device__ __forceinline__ float huber_grad(float x, float delta) {
+  return fabsf(x) <= delta ? x : copysignf(delta, x);
+}
+
+__global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__ Plan P, float* loss_part) {
+  __shared__ float red[8];
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t S_cap = P.ws.S_cap;
+  float loss = 0.0f;
+  if (g < P.total_rays && P.ws.view_base[P.n_views] <= S_cap) {
+    const ViewDev& V = P.v[view_of_ray(P, g)];
+    const int64_t r = g - V.ray_begin;
+    float dt = 0.0f;
+    float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    int used = 0;
+    if (ray_dt(V, r, P.n_samples, dt)) used = composite(P, g, dt, res);
+    P.ws.ray_used[g] = used;
+    float dC[3];
+    bool finite = true;
+    for (int c = 0; c < 3; ++c) {
+      const float e = res[c] - __ldg(V.target + c * V.n_rays + r);
+      loss += huber(e, P.huber_delta);
+      dC[c] = huber_grad(e, P.huber_delta) * P.loss_norm;
+      finite &= isfinite(res[c]);
+    }
+    if (!finite) flag_status(P.status, kStatusNonFinite);
+    if (V.rgba_out) {
+      for (int c = 0; c < 4; ++c) V.rgba_out[c * V.n_rays + r] = res[c];
+    }
+    if (V.depth_out) V.depth_out[r] = res[4];
+    // adjoint walk
+    const int64_t first = P.ws.ray_first[g];
+    const int cnt = P.ws.ray_count[g];
+    float T = 1.0f, pre[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < cnt; ++k) {
+      const int64_t s = first + k;
+      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+      if (k < used) {
+        const float sigma = P.ws.out[s];
+        const float col[3] = {P.ws.out[S_cap + s], P.ws.out[2 * S_cap + s], P.ws.out[3 * S_cap + s]};
+        const float x = sigma * dt;
+        const float alpha = -expm1f(-x);
+        const float w = T * alpha;
+        const float Tn = T * expf(-x);
+        float dsig = 0.0f;
+        float dz[3];
+        for (int c = 0; c < 3; ++c) {
+          pre[c] = fmaf(w, col[c], pre[c]);
+          dsig = fmaf(dC[c], Tn * col[c] - (res[c] - pre[c]), dsig);
+          dz[c] = dC[c] * w * col[c] * (1.0f - col[c]);
+        }
+        d0 = dsig * dt * sigma;
+        d1 = dz[0];
+        d2 = dz[1];
+        d3 = dz[2];
+        T = Tn;
+      }
+      P.ws.dout[s] = d0;
+      P.ws.dout[S_cap + s] = d1;
+      P.ws.dout[2 * S_cap + s] = d2;
+      P.ws.dout[3 * S_cap + s] = d3;
+    }
+  }
+  // deterministic block sum of the per-ray Huber terms
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    loss_part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_loss_finalize(const float* part, int n, float norm, float* loss) {
+  __shared__ float red[32];
+  float t = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int w = 0; w < 32; ++w) s += red[w];
+    *loss = s * norm;
+  }
+}
+
+cudaError_t launch_composite_train(const Plan& P, float* loss, cudaStream_t s) {
+  const int blocks = ceil_div(P.total_rays, 256);
+  k_composite_train<<<blocks, 256, 0, s>>>(P, P.ws.loss_part);
+  k_loss_finalize<<<1, 1024, 0, s>>>(P.ws.loss_part, blocks, P.loss_norm, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace invr

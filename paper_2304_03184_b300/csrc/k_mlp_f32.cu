@@ -1,0 +1,433 @@
+// Geometry + colour MLPs in FP32 (the plain-precision path; Sec. 4.2 "geometry MLP E_g
+// and color MLP E_c").  Shapes: in (16|32) -> 64 -> 64 -> 16 (ReLU hidden, no biases),
+// sigma = exp(o_0); o_1..o_15 -> 64 (ReLU) -> 3, sigmoid.
+//
+// Persistent CTAs of 256 threads walk 64-sample tiles.  A tile's activations live in
+// shared memory as [units][64 samples] (row stride 65 floats, conflict-free columns);
+// each layer is a small SIMT GEMM in which a thread owns (rows/16) x 4 outputs.  The
+// colour layers are padded to 16-wide (W4 gets a zero column for o_0, W5 gets 13 zero
+// rows) so every dimension is a multiple of 16.
+//
+// Backward (per tile): the forward activations are recomputed from the stored encoding
+// features, then deltas flow back layer by layer (in place over the activations), and the
+// weight gradients dW = sum_s delta_s a_s^T are accumulated in registers across all tiles
+// a CTA visits, flushed once per field with atomics.
+//
+// Bound: FP32 FMA pipe (9216 padded multiply-adds per sample forward, ~3x backward).
+#include "invr_internal.cuh"
+
+namespace invr {
+
+namespace {
+
+constexpr int kTS = 64;    // samples per tile
+constexpr int kLD = 65;    // activation row stride
+constexpr int kThreads = 256;
+
+struct MlpArgs {
+  const float* feat;        // [IN][ld]
+  float* out;               // [4][ld]
+  const float* dout;        // [4][ld]: dL/do_0, dL/dz_rgb
+  float* dfeat;             // [IN][ld]
+  const int32_t* s_ray;     // padding marker (< 0) or null
+  const int32_t* view_base; // per-view tile-aligned sample ranges (device) or null
+  int64_t ld;
+  int64_t n;                // samples when view_base is null
+  int n_views;
+  float grad_scale;
+  FieldDev f[kMaxViews];
+};
+
+// Shared-memory plan (floats).
+constexpr int kW1 = 0;                   // [IN][64]  (transposed)
+constexpr int kW2 = kW1 + 32 * 64;       // [64][64]
+constexpr int kW3 = kW2 + 64 * 64;       // [64][16]
+constexpr int kW4 = kW3 + 64 * 16;       // [16][64]
+constexpr int kW5 = kW4 + 16 * 64;       // [64][16]
+constexpr int kWSize = kW5 + 64 * 16;    // 9216
+
+struct WeightOffsets {
+  int w1, w2, w3, w4, w5;
+  __device__ WeightOffsets(int in) {
+    w1 = 0;
+    w2 = w1 + kHidden * in;
+    w3 = w2 + kHidden * kHidden;
+    w4 = w3 + kGeoOut * kHidden;
+    w5 = w4 + kColHidden * (kGeoOut - 1);
+  }
+};
+
+// Padded weight element [o][k] of layer `layer` (1-based) from the flat W1..W5 array.
+__device__ __forceinline__ float padded_w(const float* W, const WeightOffsets& off, int in, int layer, int o, int k) {
+  switch (layer) {
+    case 1: return W[off.w1 + o * in + k];
+    case 2: return W[off.w2 + o * kHidden + k];
+    case 3: return W[off.w3 + o * kHidden + k];
+    case 4: return k == 0 ? 0.0f : W[off.w4 + o * (kGeoOut - 1) + (k - 1)];
+    default: return o < 3 ? W[off.w5 + o * kColHidden + k] : 0.0f;
+  }
+}
+
+// Load the five (padded) layers: transposed copies [k][o] into Wt; if Wn is non-null also
+// the [o][k] copies.
+__device__ void load_weights(const float* __restrict__ W, int in, float* Wt, float* Wn) {
+  const WeightOffsets off(in);
+  const int outs[5] = {64, 64, 16, 64, 16};
+  const int ins[5] = {in, 64, 64, 16, 64};
+  const int base[5] = {kW1, kW2, kW3, kW4, kW5};
+  for (int layer = 0; layer < 5; ++layer) {
+    const int O = outs[layer], I = ins[layer];
+    for (int e = threadIdx.x; e < O * I; e += blockDim.x) {
+      const int o = e / I, k = e % I;
+      const float w = padded_w(W, off, in, layer + 1, o, k);
+      Wt[base[layer] + k * O + o] = w;
+      if (Wn) Wn[base[layer] + o * I + k] = w;
+    }
+  }
+}
+
+// Y[o][s] = act(sum_k Wt[k][o] X[k][s]); thread owns rows og*R..og*R+R-1, samples sg+16c.
+template <int OUT, int IN, bool RELU>
+__device__ __forceinline__ void layer_fwd(const float* __restrict__ Wt, const float* __restrict__ X, float* Y) {
+  constexpr int R = OUT / 16;
+  const int og = threadIdx.x >> 4, sg = threadIdx.x & 15;
+  float acc[R][4];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < IN; ++k) {
+    float x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = X[k * kLD + sg + 16 * c];
+    float w[R];
+    if constexpr (R == 4) {
+      const float4 w4 = *reinterpret_cast<const float4*>(Wt + k * OUT + og * 4);
+      w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
+    } else {
+#pragma unroll
+      for (int a = 0; a < R; ++a) w[a] = Wt[k * OUT + og * R + a];
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(w[a], x[c], acc[a][c]);
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Y[(og * R + a) * kLD + sg + 16 * c] = RELU ? fmaxf(acc[a][c], 0.0f) : acc[a][c];
+}
+
+// dX[k][s] = (sum_o W[o][k] dY[o][s]) masked by (M[k][s] > 0); W in [OUT][IN] layout.
+// Output to shared memory (stride kLD) or, if G != null, to global G[k*ld + s].
+template <int OUT, int IN, bool MASK>
+__device__ __forceinline__ void layer_bwd_in(const float* __restrict__ Wn, const float* __restrict__ dY, float* dX,
+                                             const float* M, float* G, int64_t ld, int valid) {
+  constexpr int R = IN / 16;
+  const int kg = threadIdx.x >> 4, sg = threadIdx.x & 15;
+  float acc[R][4];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+#pragma unroll 4
+  for (int o = 0; o < OUT; ++o) {
+    float y[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] = dY[o * kLD + sg + 16 * c];
+    float w[R];
+    if constexpr (R == 4) {
+      const float4 w4 = *reinterpret_cast<const float4*>(Wn + o * IN + kg * 4);
+      w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
+    } else {
+#pragma unroll
+      for (int a = 0; a < R; ++a) w[a] = Wn[o * IN + kg * R + a];
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(w[a], y[c], acc[a][c]);
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = kg * R + a, s = sg + 16 * c;
+      float v = acc[a][c];
+      if (MASK && !(M[k * kLD + s] > 0.0f)) v = 0.0f;
+      if (G) {
+        if (s < valid) G[(int64_t)k * ld + s] = v;
+      } else {
+        dX[k * kLD + s] = v;
+      }
+    }
+}
+
+// acc[i][j] += sum_s dY[i][s] X[j][s]; thread owns rows ig*RI+a, columns jg+16c.
+template <int OUT, int IN>
+__device__ __forceinline__ void acc_dw(const float* __restrict__ dY, const float* __restrict__ X, float* acc) {
+  constexpr int RI = OUT / 16, CJ = IN / 16;
+  const int ig = threadIdx.x >> 4, jg = threadIdx.x & 15;
+#pragma unroll 2
+  for (int s = 0; s < kTS; ++s) {
+    float y[RI], x[CJ];
+#pragma unroll
+    for (int a = 0; a < RI; ++a) y[a] = dY[(ig * RI + a) * kLD + s];
+#pragma unroll
+    for (int c = 0; c < CJ; ++c) x[c] = X[(jg + 16 * c) * kLD + s];
+#pragma unroll
+    for (int a = 0; a < RI; ++a)
+#pragma unroll
+      for (int c = 0; c < CJ; ++c) acc[a * CJ + c] = fmaf(y[a], x[c], acc[a * CJ + c]);
+  }
+}
+
+template <int OUT, int IN>
+__device__ __forceinline__ void flush_dw(float* acc, float* G, const WeightOffsets& off, int in, int layer) {
+  constexpr int RI = OUT / 16, CJ = IN / 16;
+  const int ig = threadIdx.x >> 4, jg = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < RI; ++a)
+#pragma unroll
+    for (int c = 0; c < CJ; ++c) {
+      const int i = ig * RI + a, j = jg + 16 * c;
+      const float v = acc[a * CJ + c];
+      acc[a * CJ + c] = 0.0f;
+      int idx = -1;
+      switch (layer) {
+        case 1: idx = off.w1 + i * in + j; break;
+        case 2: idx = off.w2 + i * kHidden + j; break;
+        case 3: idx = off.w3 + i * kHidden + j; break;
+        case 4: idx = j == 0 ? -1 : off.w4 + i * (kGeoOut - 1) + (j - 1); break;
+        default: idx = i < 3 ? off.w5 + i * kColHidden + j : -1; break;
+      }
+      if (idx >= 0 && v != 0.0f) atomicAdd(G + idx, v);
+    }
+}
+
+__device__ __forceinline__ void tile_range(const MlpArgs& A, int64_t& n_tiles) {
+  const int64_t S = A.view_base ? (int64_t)A.view_base[A.n_views] : A.n;
+  n_tiles = (S + kTS - 1) / kTS;
+}
+
+__device__ __forceinline__ int tile_view(const MlpArgs& A, int64_t s0) {
+  return A.view_base ? view_of_slot(A.view_base, A.n_views, s0) : 0;
+}
+
+__device__ __forceinline__ int tile_valid(const MlpArgs& A, int64_t s0) {
+  const int64_t S = A.view_base ? (int64_t)A.view_base[A.n_views] : A.n;
+  const int64_t rem = S - s0;
+  return rem < kTS ? (int)rem : kTS;
+}
+
+template <int IN>
+__device__ void load_x(const MlpArgs& A, int64_t s0, int valid, float* X) {
+  for (int e = threadIdx.x; e < IN * kTS; e += blockDim.x) {
+    const int k = e / kTS, s = e % kTS;
+    X[k * kLD + s] = s < valid ? A.feat[(int64_t)k * A.ld + s0 + s] : 0.0f;
+  }
+}
+
+template <int IN>
+__device__ __forceinline__ void tile_forward(const MlpArgs& A, int64_t s0, int valid, const float* Wt, float* X, float* H1, float* H2,
+                             float* O, float* Z) {
+  load_x<IN>(A, s0, valid, X);
+  __syncthreads();
+  layer_fwd<64, IN, true>(Wt + kW1, X, H1);
+  __syncthreads();
+  layer_fwd<64, 64, true>(Wt + kW2, H1, H2);
+  __syncthreads();
+  layer_fwd<16, 64, false>(Wt + kW3, H2, O);
+  __syncthreads();
+  layer_fwd<64, 16, true>(Wt + kW4, O, H1);  // H4 reuses H1
+  __syncthreads();
+  layer_fwd<16, 64, false>(Wt + kW5, H1, Z);
+  __syncthreads();
+  if (threadIdx.x < kTS && (int)threadIdx.x < valid) {
+    const int s = threadIdx.x;
+    const int64_t gs = s0 + s;
+    A.out[gs] = expf(O[s]);
+    for (int c = 0; c < 3; ++c) A.out[(int64_t)(1 + c) * A.ld + gs] = 1.0f / (1.0f + expf(-Z[c * kLD + s]));
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_fwd_f32(const __grid_constant__ MlpArgs A) {
+  extern __shared__ float sm[];
+  float* Wt = sm;
+  float* X = Wt + kWSize;
+  float* H1 = X + 32 * kLD;
+  float* H2 = H1 + 64 * kLD;
+  float* O = H2 + 64 * kLD;
+  float* Z = O + 16 * kLD;
+  int64_t n_tiles;
+  tile_range(A, n_tiles);
+  const float* loaded = nullptr;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t s0 = t * kTS;
+    const FieldDev& F = A.f[tile_view(A, s0)];
+    if (F.weights != loaded) {
+      __syncthreads();
+      load_weights(F.weights, F.mlp_in, Wt, nullptr);
+      loaded = F.weights;
+      __syncthreads();
+    }
+    const int valid = tile_valid(A, s0);
+    if (F.mlp_in == 16)
+      tile_forward<16>(A, s0, valid, Wt, X, H1, H2, O, Z);
+    else
+      tile_forward<32>(A, s0, valid, Wt, X, H1, H2, O, Z);
+  }
+}
+
+template <int IN>
+__device__ __forceinline__ void tile_backward(const MlpArgs& A, int64_t s0, int valid, const float* Wt, const float* Wn, float* X,
+                              float* H1, float* H2, float* H4, float* O, float* D, float* acc1, float* acc2,
+                              float* acc3, float* acc4, float* acc5) {
+  load_x<IN>(A, s0, valid, X);
+  __syncthreads();
+  layer_fwd<64, IN, true>(Wt + kW1, X, H1);
+  __syncthreads();
+  layer_fwd<64, 64, true>(Wt + kW2, H1, H2);
+  __syncthreads();
+  layer_fwd<16, 64, false>(Wt + kW3, H2, O);
+  __syncthreads();
+  layer_fwd<64, 16, true>(Wt + kW4, O, H4);
+  // dZ (rows 0..2 from dL/dz_rgb, rows 3..15 zero) into D
+  for (int e = threadIdx.x; e < 16 * kTS; e += blockDim.x) {
+    const int i = e / kTS, s = e % kTS;
+    float v = 0.0f;
+    if (i < 3 && s < valid && (!A.s_ray || A.s_ray[s0 + s] >= 0)) v = A.dout[(int64_t)(1 + i) * A.ld + s0 + s] * A.grad_scale;
+    D[i * kLD + s] = v;
+  }
+  __syncthreads();
+  acc_dw<16, 64>(D, H4, acc5);
+  __syncthreads();
+  layer_bwd_in<16, 64, true>(Wn + kW5, D, H4, H4, nullptr, 0, kTS);  // dH4 in place
+  __syncthreads();
+  acc_dw<64, 16>(H4, O, acc4);
+  __syncthreads();
+  layer_bwd_in<64, 16, false>(Wn + kW4, H4, D, nullptr, nullptr, 0, kTS);  // dO into D
+  __syncthreads();
+  for (int s = threadIdx.x; s < kTS; s += blockDim.x) {
+    float v = 0.0f;
+    if (s < valid && (!A.s_ray || A.s_ray[s0 + s] >= 0)) v = A.dout[s0 + s] * A.grad_scale;
+    D[s] = v;  // row 0: dL/do_0 (the colour MLP does not read o_0)
+  }
+  __syncthreads();
+  acc_dw<16, 64>(D, H2, acc3);
+  __syncthreads();
+  layer_bwd_in<16, 64, true>(Wn + kW3, D, H2, H2, nullptr, 0, kTS);  // dH2 in place
+  __syncthreads();
+  acc_dw<64, 64>(H2, H1, acc2);
+  __syncthreads();
+  layer_bwd_in<64, 64, true>(Wn + kW2, H2, H1, H1, nullptr, 0, kTS);  // dH1 in place
+  __syncthreads();
+  acc_dw<64, IN>(H1, X, acc1);
+  layer_bwd_in<64, IN, false>(Wn + kW1, H1, nullptr, nullptr, A.dfeat + s0, A.ld, valid);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void flush_all(float* acc1, float* acc2, float* acc3, float* acc4, float* acc5, const FieldDev& F) {
+  const WeightOffsets off(F.mlp_in);
+  if (F.mlp_in == 16)
+    flush_dw<64, 16>(acc1, F.grad_weights, off, 16, 1);
+  else
+    flush_dw<64, 32>(acc1, F.grad_weights, off, 32, 1);
+  flush_dw<64, 64>(acc2, F.grad_weights, off, F.mlp_in, 2);
+  flush_dw<16, 64>(acc3, F.grad_weights, off, F.mlp_in, 3);
+  flush_dw<64, 16>(acc4, F.grad_weights, off, F.mlp_in, 4);
+  flush_dw<16, 64>(acc5, F.grad_weights, off, F.mlp_in, 5);
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_bwd_f32(const __grid_constant__ MlpArgs A) {
+  extern __shared__ float sm[];
+  float* Wt = sm;
+  float* Wn = Wt + kWSize;
+  float* X = Wn + kWSize;
+  float* H1 = X + 32 * kLD;
+  float* H2 = H1 + 64 * kLD;
+  float* H4 = H2 + 64 * kLD;
+  float* O = H4 + 64 * kLD;
+  float* D = O + 16 * kLD;
+  float acc1[8], acc2[16], acc3[4], acc4[4], acc5[4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc1[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc2[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc3[i] = acc4[i] = acc5[i] = 0.0f;
+  int64_t n_tiles;
+  tile_range(A, n_tiles);
+  int cur = -1;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t s0 = t * kTS;
+    const int v = tile_view(A, s0);
+    const FieldDev& F = A.f[v];
+    if (cur < 0 || F.weights != A.f[cur].weights) {
+      if (cur >= 0) flush_all(acc1, acc2, acc3, acc4, acc5, A.f[cur]);
+      __syncthreads();
+      load_weights(F.weights, F.mlp_in, Wt, Wn);
+      cur = v;
+      __syncthreads();
+    }
+    const int valid = tile_valid(A, s0);
+    if (F.mlp_in == 16)
+      tile_backward<16>(A, s0, valid, Wt, Wn, X, H1, H2, H4, O, D, acc1, acc2, acc3, acc4, acc5);
+    else
+      tile_backward<32>(A, s0, valid, Wt, Wn, X, H1, H2, H4, O, D, acc1, acc2, acc3, acc4, acc5);
+  }
+  if (cur >= 0) flush_all(acc1, acc2, acc3, acc4, acc5, A.f[cur]);
+}
+
+constexpr size_t kFwdSmem = (size_t)(kWSize + 32 * kLD + 64 * kLD * 2 + 16 * kLD * 2) * sizeof(float);
+constexpr size_t kBwdSmem = (size_t)(2 * kWSize + 32 * kLD + 64 * kLD * 3 + 16 * kLD * 2) * sizeof(float);
+
+MlpArgs plan_args(const Plan& P) {
+  MlpArgs A{};
+  A.feat = static_cast<const float*>(P.ws.feat);
+  A.out = P.ws.out;
+  A.dout = P.ws.dout;
+  A.dfeat = P.ws.dfeat;
+  A.s_ray = P.ws.s_ray;
+  A.view_base = P.ws.view_base;
+  A.ld = P.ws.S_cap;
+  A.n = 0;
+  A.n_views = P.n_views;
+  A.grad_scale = P.grad_scale;
+  for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
+  return A;
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s) {
+  cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(plan_args(P));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s) {
+  cudaFuncSetAttribute(k_mlp_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+  k_mlp_bwd_f32<<<num_sms, kThreads, kBwdSmem, s>>>(plan_args(P));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
+                                  cudaStream_t s) {
+  MlpArgs A{};
+  A.feat = feat;
+  A.out = out;
+  A.ld = n;
+  A.n = n;
+  A.n_views = 1;
+  A.grad_scale = 1.0f;
+  A.f[0] = f;
+  cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  if (n > 0) k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace invr

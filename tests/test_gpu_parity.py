@@ -1,0 +1,377 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
+inputs.  Discrete results (sample positions, occupancy, hash slots, nearest-node ids) must
+match bit for bit on identical FP32 inputs; FP32 colour and opacity within 1e-5 absolute;
+gradients within 1e-3 relative (spec tolerances of the FP32 path)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2304_03184_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+COLOUR_TOL = 1e-5     # colour / opacity, FP32 path vs FP64 oracle
+GRAD_RTOL = 1e-3      # gradients, FP32 path vs FP64 oracle
+
+
+@pytest.fixture(scope="module")
+def env(oracle):
+    import torch
+    from paper_2304_03184_b300 import build
+    build.build()
+    import paper_2304_03184_b300 as invr
+    assert torch.cuda.is_available()
+    ctx = invr.Context(0)
+    yield invr, ctx, oracle
+    torch.cuda.synchronize()
+
+
+def cu(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+class Side:
+    """The same synthetic view on both sides: GPU handles and oracle wrappers."""
+
+    def __init__(self, invr, ctx, oracle, sv: synth.View, prec=0, field=None, ofield=None):
+        self.field = field or invr.Field.from_synth(ctx, sv.field, prec)
+        self.graph = None
+        if sv.graph is not None:
+            g = sv.graph
+            self.graph = invr.Graph(ctx, g.x_canon.shape[1], g.K, g.radius, 1, cu(g.x_canon))
+            self.graph.set_pose(0, cu(g.dq), cu(g.x_live))
+        self.occ = cu(sv.occupancy) if sv.occupancy is not None else None
+        self.view = invr.View(self.field, self.graph, 0, sv.rigid_dq, self.occ)
+        self.oview = oracle.View.from_synth(sv, field=ofield)
+
+
+# ------------------------------------------------------------------ sampling
+def _oracle_compacted(oracle, rays, n_samples, occupancy):
+    hit, tn, dt, t, p = oracle.ray_samples(rays.o, rays.d, n_samples)
+    R = rays.n
+    keep = np.ones((R, n_samples), bool) & hit[:, None].astype(bool)
+    if occupancy is not None:
+        occ = oracle.occupied_points(occupancy, p.reshape(3, -1)).reshape(R, n_samples).astype(bool)
+        keep &= occ
+    return keep, t, p
+
+
+@pytest.mark.parametrize("which", ["plain", "occupancy", "oblique"])
+def test_ray_samples_bit_exact(env, which):
+    invr, ctx, oracle = env
+    occ = None
+    if which == "plain":
+        rays, S = synth.plain_forward().rays, 64
+    elif which == "occupancy":
+        w = synth.two_field_render(width=96, height=80)
+        rays, S, occ = w.rays, 128, w.views[0].occupancy
+    else:
+        rays, S = synth.pinhole_rays(37, 29, 70.0, (0.7, 1.9, 1.4)), 33
+    count, t, p = invr.ray_samples(ctx, cu(rays.o), cu(rays.d), S, cu(occ) if occ is not None else None)
+    count, t, p = host(count), host(t), host(p)
+    keep, ot, op = _oracle_compacted(oracle, rays, S, occ)
+    np.testing.assert_array_equal(count, keep.sum(axis=1))
+    for r in range(rays.n):
+        k = count[r]
+        np.testing.assert_array_equal(t[r, :k].view(np.uint32), ot[r, keep[r]].view(np.uint32))
+        np.testing.assert_array_equal(p[:, r, :k].view(np.uint32), op[:, r, keep[r]].view(np.uint32))
+
+
+# ------------------------------------------------------------------ hash encoding
+@pytest.mark.parametrize("desc", [synth.CFG1_FIELD, synth.CFG2_FIELD, synth.CFG5_FIELD])
+def test_encode_indices_bit_exact(env, desc):
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(30)
+    fp = synth.make_field(rng, desc)
+    f = invr.Field.from_synth(ctx, fp)
+    x = rng.uniform(-1.1, 1.1, size=(3, 3001)).astype(np.float32)
+    x[:, :64] = (-1.0 + rng.integers(0, 17, size=(3, 64)) / 8.0).astype(np.float32)  # exact vertices
+    feat, idx = invr.encode_points(ctx, f, cu(x), with_index=True)
+    ofeat, oidx, _ = oracle.encode_points(oracle.Field.from_params(fp), x.astype(np.float64), with_index=True)
+    np.testing.assert_array_equal(host(idx).view(np.uint32), oidx)
+    np.testing.assert_allclose(host(feat), ofeat, rtol=0, atol=1e-6)
+
+
+# ------------------------------------------------------------------ warp
+def _probe_points(rng, g, n_near=3000):
+    near = g.x_live[:, rng.integers(0, g.x_live.shape[1], n_near)] + rng.normal(scale=0.06, size=(3, n_near))
+    far = rng.uniform(-1.0, 1.0, size=(3, 500))
+    out = rng.uniform(-1.6, 1.6, size=(3, 100))      # partly outside the box: full scan
+    return np.concatenate([near, far, out], axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("n_nodes,K", [(64, 4), (2048, 4), (2048, 1), (4096, 8)])
+def test_nearest_nodes_bit_exact(env, n_nodes, K):
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(31)
+    g = synth.make_graph(rng, n_nodes, K=K)
+    sv = synth.View(synth.make_field(rng, synth.CFG1_FIELD), graph=g)
+    side = Side(invr, ctx, oracle, sv)
+    p = _probe_points(rng, g)
+    vc, ids = invr.warp_points(ctx, side.view, cu(p), with_ids=True)
+    oids, _ = oracle.knn_points(side.oview.graph, p)
+    np.testing.assert_array_equal(host(ids), oids)
+    ovc = oracle.warp_points(side.oview, p)
+    np.testing.assert_allclose(host(vc), ovc, rtol=0, atol=2e-6)
+
+
+def test_rigid_warp(env):
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(32)
+    dq, R, t = synth.make_object_pose(rng)
+    sv = synth.View(synth.make_field(rng, synth.CFG1_FIELD), rigid_dq=dq)
+    side = Side(invr, ctx, oracle, sv)
+    p = rng.uniform(-1.2, 1.2, size=(3, 1000)).astype(np.float32)
+    vc = invr.warp_points(ctx, side.view, cu(p))
+    np.testing.assert_allclose(host(vc), oracle.warp_points(side.oview, p), rtol=0, atol=1e-6)
+
+
+# ------------------------------------------------------------------ MLP
+@pytest.mark.parametrize("desc", [synth.CFG1_FIELD, synth.CFG2_FIELD])
+def test_mlp_matches_oracle(env, desc):
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(33)
+    fp = synth.make_field(rng, desc)
+    f = invr.Field.from_synth(ctx, fp)
+    feat = rng.uniform(-0.5, 0.5, size=(desc.mlp_in, 1000)).astype(np.float32)   # ragged tail
+    out = host(invr.mlp_points(ctx, f, cu(feat)))
+    want = oracle.mlp_points(oracle.Field.from_params(fp), feat)
+    np.testing.assert_allclose(out, want, rtol=1e-5, atol=1e-6)
+    # zero weights: sigma = 1, colour 1/2 exactly
+    fp.weights[:] = 0
+    f.set_params(None, cu(fp.weights))
+    out = host(invr.mlp_points(ctx, f, cu(feat)))
+    np.testing.assert_array_equal(out[0], 1.0)
+    np.testing.assert_array_equal(out[1:], 0.5)
+
+
+# ------------------------------------------------------------------ rendering
+def _render_both(env, w, views_synth, prec=0, sel=None):
+    invr, ctx, oracle = env
+    sides = [Side(invr, ctx, oracle, v, prec) for v in views_synth]
+    rgba, depth = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [s.view for s in sides])
+    ctx.sync()
+    rgba, depth = host(rgba), host(depth)
+    rays = w.rays if sel is None else synth.subset_rays(w.rays, sel)
+    ref = oracle.render(rays.o, rays.d, w.n_samples, w.t_eps, [s.oview for s in sides])
+    if sel is not None:
+        rgba, depth = rgba[:, sel], depth[sel]
+    return rgba, depth, ref
+
+
+def test_render_plain_forward_fp32(env):
+    w = synth.plain_forward()
+    rgba, depth, ref = _render_both(env, w, w.views)
+    assert ref.rgba[3].max() > 0.5                      # the field is visible
+    np.testing.assert_allclose(rgba, ref.rgba, rtol=0, atol=COLOUR_TOL)
+    np.testing.assert_allclose(depth, ref.depth, rtol=COLOUR_TOL, atol=COLOUR_TOL)
+
+
+def _near_tie(ref, scale=1e-4):
+    """Rays where both fields are visible at nearly the same expected depth: the depth
+    ordering is a discrete decision taken in FP32 on the GPU and in FP64 by the oracle."""
+    a = ref.depth_v[0] * ref.rgba_v[1][3]
+    b = ref.depth_v[1] * ref.rgba_v[0][3]
+    both = (ref.rgba_v[0][3] > 0) & (ref.rgba_v[1][3] > 0)
+    return both & (np.abs(a - b) <= scale * (np.abs(a) + np.abs(b)))
+
+
+def test_render_two_fields_fp32_small(env):
+    w = synth.two_field_render(width=80, height=72)
+    rgba, depth, ref = _render_both(env, w, w.views)
+    assert ref.n_used[0].sum() > 0 and ref.n_used[1].sum() > 0
+    ok = ~_near_tie(ref)
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=COLOUR_TOL)
+    np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
+
+
+def test_render_two_fields_full_size_sampled(env):
+    w = synth.two_field_render()                          # 512 x 512, 128 samples
+    rng = np.random.default_rng(34)
+    sel = np.sort(rng.choice(w.rays.n, 1500, replace=False))
+    rgba, depth, ref = _render_both(env, w, w.views, sel=sel)
+    ok = ~_near_tie(ref)
+    np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=COLOUR_TOL)
+    np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
+
+
+def test_early_termination(env):
+    invr, ctx, oracle = env
+    w = synth.plain_forward(res=48)
+    v = w.views[0]
+    d = v.field.desc
+    off = d.hidden * d.mlp_in + d.hidden * d.hidden
+    v.field.weights[off:off + d.hidden] *= 25.0           # dense field: rays terminate
+    rgba, depth, ref = _render_both(env, w, [v])
+    assert np.mean(ref.n_used[0] < w.n_samples) > 0.2
+    err = np.max(np.abs(rgba - ref.rgba), axis=0)
+    # a stop decision taken on the other side of t_eps moves a ray by at most t_eps
+    assert np.mean(err <= COLOUR_TOL) > 0.995
+    assert err.max() <= w.t_eps + COLOUR_TOL
+
+
+# ------------------------------------------------------------------ edge cases
+def test_edge_cases(env):
+    invr, ctx, oracle = env
+    import torch
+    w = synth.plain_forward(res=16, n_samples=1)
+    side = Side(invr, ctx, oracle, w.views[0])
+    # one sample per ray
+    rgba, depth = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), 1, 1e-4, [side.view])
+    ref = oracle.render(w.rays.o, w.rays.d, 1, 1e-4, [side.oview])
+    np.testing.assert_allclose(host(rgba), ref.rgba, atol=COLOUR_TOL)
+    # no rays
+    e = torch.zeros((3, 0), device="cuda")
+    rgba, depth = invr.render_rays(ctx, e, e, 8, 1e-4, [side.view])
+    assert rgba.shape == (4, 0)
+    # rays that all miss the box
+    miss = synth.pinhole_rays(8, 8, 20.0, (0.0, 3.0, 2.5), target=(0.0, 6.0, 0.0))
+    rgba, depth = invr.render_rays(ctx, cu(miss.o), cu(miss.d), 16, 1e-4, [side.view])
+    assert np.all(host(rgba) == 0) and np.all(host(depth) == 0)
+    # an empty occupancy grid renders nothing
+    empty = cu(np.zeros(128 ** 3 // 32, np.uint32))
+    v = invr.View(side.field, side.graph, 0, None, empty)
+    rgba, _ = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), 16, 1e-4, [v])
+    assert np.all(host(rgba) == 0)
+    ctx.sync()
+
+
+def test_invalid_arguments_raise(env):
+    invr, ctx, oracle = env
+    w = synth.plain_forward(res=8)
+    side = Side(invr, ctx, oracle, w.views[0])
+    with pytest.raises(invr.InvrError):
+        invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), 0, 1e-4, [side.view])
+    with pytest.raises(invr.InvrError):
+        invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), 2000, 1e-4, [side.view])
+    with pytest.raises(invr.InvrError):
+        invr.Graph(ctx, 3, 4)                            # K > n_nodes
+    with pytest.raises(invr.InvrError):
+        invr.Field(ctx, invr.field_desc(8, 14, F=4))      # F != 2
+    with pytest.raises(invr.InvrError):                  # frame never posed
+        invr.warp_points(ctx, invr.View(side.field, side.graph, 5), cu(np.zeros((3, 4), np.float32)))
+
+
+# ------------------------------------------------------------------ training
+def _train_both(env, tw: synth.TrainWorkload, prec=0):
+    invr, ctx, oracle = env
+    ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
+    gfields = {id(fp): invr.Field.from_synth(ctx, fp, prec) for fp in tw.fields}
+    batches, obatches, keep = [], [], []
+    for b in tw.batches:
+        side = Side(invr, ctx, oracle, b.view, prec, field=gfields[id(b.view.field)],
+                    ofield=ofields[id(b.view.field)])
+        keep.append(side)
+        batches.append((cu(b.rays.o), cu(b.rays.d), side.view, cu(b.target)))
+        obatches.append(oracle.TrainBatch(b.rays.o, b.rays.d, side.oview, b.target))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    return tb, gfields, ofields, obatches, keep
+
+
+def _assert_grads_close(g, want, what):
+    """Per tensor: relative L2 error <= GRAD_RTOL; per entry: within GRAD_RTOL of the entry
+    plus GRAD_RTOL of the tensor's RMS over touched entries (entries that are sums of many
+    cancelling per-sample terms carry the absolute FP32 error of those terms)."""
+    touched = want != 0
+    assert touched.any(), what
+    rms = np.sqrt(np.mean(want[touched] ** 2))
+    err = np.abs(g - want)
+    rel = np.linalg.norm(g - want) / np.linalg.norm(want)
+    assert rel <= GRAD_RTOL, (what, rel)
+    bad = err > GRAD_RTOL * np.abs(want) + GRAD_RTOL * rms
+    assert not bad.any(), (what, int(bad.sum()), float(err.max()), float(rms))
+
+
+def test_train_gradients_match_oracle(env):
+    invr, ctx, oracle = env
+    tw = synth.train_step_workload(n_rays=1536)
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
+    fp = tw.fields[0]
+    gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+    ogt, ogw = ograds[id(ofields[id(fp)])]
+    d = fp.desc
+    per_level = d.T * d.F
+    for l in range(d.L):
+        _assert_grads_close(gt[l * per_level:(l + 1) * per_level], ogt[l * per_level:(l + 1) * per_level],
+                            f"table level {l}")
+    off = 0
+    for i, (r, c) in enumerate(d.weight_shapes()):
+        _assert_grads_close(gw[off:off + r * c], ogw[off:off + r * c], f"W{i + 1}")
+        off += r * c
+
+
+def test_train_step_adam_matches_oracle(env):
+    invr, ctx, oracle = env
+    tw = synth.train_step_workload(seed=5, n_rays=1024)
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw)
+    invr.train_step(ctx, tb)
+    ctx.sync()
+    fp = tw.fields[0]
+    of = ofields[id(fp)]
+    _, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    ogt, ogw = ograds[id(of)]
+    g = np.concatenate([ogt, ogw])
+    p = np.concatenate([of.tables, of.weights]).copy()
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    oracle.adam(p, g, m, v, 1, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    t, w_, gm, gv, step = gfields[id(fp)].get_params()
+    assert step == 1
+    gp = np.concatenate([host(t), host(w_)])
+    # with eps = 1e-15 the first step moves every touched parameter by lr * sign(g); compare
+    # where the gradient sign is unambiguous at FP32 accuracy
+    sure = np.abs(g) > 1e-3 * np.abs(g).max()
+    np.testing.assert_allclose(gp[sure], p[sure], rtol=0, atol=1e-6)
+    # moments are (1-b1) g and (1-b2) g^2: gradient parity in disguise
+    assert np.linalg.norm(host(gm) - m) <= GRAD_RTOL * np.linalg.norm(m)
+    assert np.linalg.norm(host(gv) - v) <= 2 * GRAD_RTOL * np.linalg.norm(v)
+    # every parameter that moved took a full step of lr (Adam with eps = 1e-15); entries the
+    # oracle never touches move only where a sample sits on a cell boundary in FP32
+    p0 = np.concatenate([fp.tables.ravel(), fp.weights]).astype(np.float64)
+    moved = np.abs(gp - p0) > 1e-7
+    assert np.all(np.abs(np.abs(gp - p0)[moved] - tw.lr) < 1e-5)
+    untouched = g == 0
+    assert (moved & untouched).sum() <= 1e-3 * (~untouched).sum()
+
+
+def test_keyframe_batches_two_fields(env):
+    invr, ctx, oracle = env
+    tw = synth.keyframe_batch_workload(n_frames=3, log2_rays=(7.0, 9.0))
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
+    for fp in tw.fields:
+        gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+        ogt, ogw = ograds[id(ofields[id(fp)])]
+        assert np.linalg.norm(gt - ogt) <= GRAD_RTOL * np.linalg.norm(ogt)
+        assert np.linalg.norm(gw - ogw) <= GRAD_RTOL * np.linalg.norm(ogw)
+
+
+def test_autograd_function(env):
+    invr, ctx, oracle = env
+    import torch
+    tw = synth.train_step_workload(seed=6, n_rays=512)
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw)
+    fp = tw.fields[0]
+    tables = cu(fp.tables.ravel()).requires_grad_(True)
+    weights = cu(fp.weights).requires_grad_(True)
+    loss = invr.field_render_loss(tables, weights, ctx, gfields[id(fp)], tb)
+    (2.0 * loss).sum().backward()
+    _, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    ogt, ogw = ograds[id(ofields[id(fp)])]
+    assert np.linalg.norm(host(weights.grad) - 2 * ogw) <= GRAD_RTOL * np.linalg.norm(2 * ogw)
+    assert np.linalg.norm(host(tables.grad) - 2 * ogt) <= GRAD_RTOL * np.linalg.norm(2 * ogt)
