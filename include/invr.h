@@ -228,6 +228,23 @@ invr_status invr_mlp_points(invr_ctx ctx, invr_field field, int64_t n, const flo
 invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p_dev,
                               float* out_dev, invr_stream stream);
 
+/* ------------------------------------------------------------------ no allocation */
+/* Not part of the paper's method (the paper has no counterpart): a variant of
+ * invr_query_points for callers that cannot call cudaMalloc -- for example code that runs
+ * inside a host framework which owns all device memory through its own pool, or a
+ * real-time loop where an allocation (and the synchronisation it can imply) is not
+ * allowed.  Inputs, outputs and results are those of invr_query_points.  Its scratch
+ * (canonical positions and encoding features, (3 + mlp_in) floats per point) lives in one
+ * fixed device array of 35 x INVR_NOALLOC_MAX_POINTS floats (9.2 MB) compiled into the
+ * library; every device that loads the library holds it until the process exits.  The call
+ * allocates nothing.  The first call on a device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the one array and each call
+ * overwrites it: calls that overlap on the GPU (other streams, other host threads) race, so
+ * the caller must serialise them.  n > INVR_NOALLOC_MAX_POINTS returns INVR_E_ARG. */
+#define INVR_NOALLOC_MAX_POINTS 65536
+invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p_dev,
+                                      float* out_dev, invr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

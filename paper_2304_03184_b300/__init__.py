@@ -81,6 +81,7 @@ _SIGNATURES = {
     "invr_query_points": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
     "invr_ctx_enable_timing": [_VP, _I],
     "invr_ctx_timing": [_VP, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64), _I],
+    "invr_query_points_noalloc": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
 }
 
 _lib_handle = None
@@ -372,6 +373,22 @@ def query_points(ctx: Context, view: View, p):
     out = torch.empty((4, n), device=p.device)
     cv = view.c()
     _check(lib().invr_query_points(ctx.h, C.byref(cv), n, _ptr(p), _ptr(out), _stream()), ctx.h)
+    return out
+
+
+NOALLOC_MAX_POINTS = 65536
+
+
+def query_points_noalloc(ctx: Context, view: View, p, out=None):
+    """invr_query_points_noalloc: query without any device allocation inside the library
+    (scratch in a fixed 9.2 MB device array, at most NOALLOC_MAX_POINTS points per call; calls
+    share that array, so calls that overlap on the GPU must be serialised by the caller)."""
+    torch = _torch()
+    n = p.shape[1]
+    if out is None:
+        out = torch.empty((4, n), device=p.device)
+    cv = view.c()
+    _check(lib().invr_query_points_noalloc(ctx.h, C.byref(cv), n, _ptr(p), _ptr(out), _stream()), ctx.h)
     return out
 
 

@@ -788,3 +788,23 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
 }
 
 }  // extern "C"
+
+// Helpers for entry points defined in other files (the no-allocation query).
+namespace invr {
+
+invr_status resolve_point_query(invr_ctx ctx, const invr_field_view* view, WarpDev& W, FieldDev& F, int& device,
+                                int& num_sms) {
+  if (!ctx || !view) return INVR_E_ARG;
+  invr_status st = check_field(ctx, view->field);
+  if (st != INVR_OK) return st;
+  st = warp_dev(ctx, *view, W);
+  if (st != INVR_OK) return st;
+  F = field_dev(view->field);
+  device = ctx->device;
+  num_sms = ctx->num_sms;
+  return INVR_OK;
+}
+
+invr_status record_error(invr_ctx ctx, invr_status st, const char* msg) { return fail(ctx, st, msg); }
+
+}  // namespace invr
