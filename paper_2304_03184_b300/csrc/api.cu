@@ -313,7 +313,11 @@ cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
   if ((e = TIMED(ctx, "march_emit", s, launch_march_emit(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "warp", s, launch_warp(P, ctx->num_sms, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "encode", s, launch_encode(P, ctx->num_sms, s))) != cudaSuccess) return e;
-  return TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s));
+  if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
+    return e;
+  if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
+    e = TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_tc(P, ctx->num_sms, s));
+  return e;
 }
 
 invr_status check_desc(invr_ctx ctx, const invr_field_desc* d) {
@@ -758,7 +762,12 @@ invr_status invr_mlp_points(invr_ctx ctx, invr_field f, int64_t n, const float* 
   if (st != INVR_OK) return st;
   if (n > 0 && (!feat || !out)) return fail(ctx, INVR_E_ARG, "null pointer");
   DeviceGuard guard(ctx->device);
-  INVR_CUDA(ctx, launch_mlp_points_f32(field_dev(f), n, feat, out, ctx->num_sms, static_cast<cudaStream_t>(stream)));
+  const FieldDev F = field_dev(f);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (F.mlp_kind == kMlpF32)
+    INVR_CUDA(ctx, launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s));
+  else
+    INVR_CUDA(ctx, launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->num_sms, s));
   return INVR_OK;
 }
 
@@ -780,7 +789,9 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
   const FieldDev F = field_dev(view->field);
   cudaError_t e = launch_warp_points(W, n, p, vc, nullptr, s);
   if (e == cudaSuccess) e = launch_encode_points(F, n, vc, feat, nullptr, s);
-  if (e == cudaSuccess) e = launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s);
+  if (e == cudaSuccess)
+    e = F.mlp_kind == kMlpF32 ? launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s)
+                              : launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->num_sms, s);
   cudaFreeAsync(vc, s);
   cudaFreeAsync(feat, s);
   INVR_CUDA(ctx, e);

@@ -209,6 +209,10 @@ cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s);
+bool plan_has_kind(const Plan& P, int kind);
+cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
+                                 int num_sms, cudaStream_t s);
 cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s);
 cudaError_t launch_composite_train(const Plan& P, float* loss, cudaStream_t s);
 cudaError_t launch_adam(float* params, const float* grads_in, float* grads_zero, float* m, float* v, int64_t n,

@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_fwd_f32(const __grid_constant_
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t s0 = t * kTS;
     const FieldDev& F = A.f[tile_view(A, s0)];
+    if (F.mlp_kind != kMlpF32) continue;  // mixed-precision fields run on the tensor cores
     if (F.weights != loaded) {
       __syncthreads();
       load_weights(F.weights, F.mlp_in, Wt, nullptr);

@@ -155,6 +155,31 @@ def test_mlp_matches_oracle(env, desc):
     np.testing.assert_array_equal(out[1:], 0.5)
 
 
+# 16-bit unit roundoff (relative): BF16 keeps 8 significant bits, FP16 11.
+U16 = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -11}
+MIXED_RGB_TOL = 2e-3   # rendered colour / opacity, mixed-precision MLP vs FP64 oracle
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("desc", [synth.CFG1_FIELD, synth.CFG2_FIELD])
+def test_mlp_tensor_cores_match_oracle(env, desc, prec):
+    """tcgen05 MLP (16-bit operands, FP32 accumulate): sigma = exp(o_0) within 8 units of
+    roundoff relative (o_0 collects a few roundings of operands and activations), colour
+    within 2 units absolute (sigmoid' <= 1/4)."""
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(35)
+    fp = synth.make_field(rng, desc)
+    code = invr.INVR_MLP_BF16 if prec == "bf16" else invr.INVR_MLP_FP16
+    f = invr.Field.from_synth(ctx, fp, code)
+    feat = rng.uniform(-0.5, 0.5, size=(desc.mlp_in, 1000)).astype(np.float32)   # 7 tiles + ragged tail
+    out = host(invr.mlp_points(ctx, f, cu(feat)))
+    ctx.sync()
+    want = oracle.mlp_points(oracle.Field.from_params(fp), feat)
+    u = U16[prec]
+    assert np.all(np.abs(out[0] - want[0]) <= 8 * u * want[0])
+    assert np.all(np.abs(out[1:] - want[1:]) <= 2 * u)
+
+
 # ------------------------------------------------------------------ rendering
 def _render_both(env, w, views_synth, prec=0, sel=None):
     invr, ctx, oracle = env
@@ -175,6 +200,19 @@ def test_render_plain_forward_fp32(env):
     assert ref.rgba[3].max() > 0.5                      # the field is visible
     np.testing.assert_allclose(rgba, ref.rgba, rtol=0, atol=COLOUR_TOL)
     np.testing.assert_allclose(depth, ref.depth, rtol=COLOUR_TOL, atol=COLOUR_TOL)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_render_mixed_precision(env, prec):
+    invr, ctx, oracle = env
+    code = invr.INVR_MLP_BF16 if prec == "bf16" else invr.INVR_MLP_FP16
+    w = synth.plain_forward()
+    rgba, depth, ref = _render_both(env, w, w.views, prec=code)
+    np.testing.assert_allclose(rgba, ref.rgba, rtol=0, atol=MIXED_RGB_TOL)
+    w2 = synth.two_field_render(width=64, height=64)
+    rgba, depth, ref = _render_both(env, w2, w2.views, prec=code)
+    ok = ~_near_tie(ref, 1e-2)
+    np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=MIXED_RGB_TOL)
 
 
 def _near_tie(ref, scale=1e-4):
