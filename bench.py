@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--prec", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--prec", choices=["fp32", "fp16", "bf16"], default="bf16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=1 << 18)
     ap.add_argument("--no-render", action="store_true")
@@ -130,11 +130,17 @@ def occupied_samples(invr, ctx, tb):
 
 # algorithmic work per kernel of one training step ("Roofline")
 def kernel_work(name, R, S_occ, n_samples, L, n_params, n_w):
-    mlp_f = 2 * n_w                       # multiply-adds x 2 per sample, forward
+    """(bound, algorithmic work per launch) of one kernel of the training step: FLOPs for the
+    MLPs (2 per multiply-add of the unpadded layers), bytes for the streaming/gather ones."""
+    mlp_f = 2 * n_w                       # FLOPs per sample, forward
     if name == "mlp_fwd":
         return "alu", S_occ * mlp_f
     if name == "mlp_bwd":
         return "alu", S_occ * 3 * mlp_f   # recompute forward + input grads + weight grads
+    if name == "mlp_fwd_tc":
+        return "tensor", S_occ * mlp_f
+    if name == "mlp_bwd_tc":
+        return "tensor", S_occ * 3 * mlp_f
     if name == "adam":
         return "hbm", n_params * 32       # read p,g,m,v; write p,g(=0),m,v
     if name == "encode":
@@ -150,31 +156,21 @@ def fp32_alu_peak(sm_mhz):
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes
 
 
-def run_ours(args, rank, world, local):
+PRECS = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+
+def time_train(invr, ctx, tb, steps, warmup, flush, world):
+    """Per-step CUDA-event times (L2 flushed between steps) and the per-kernel breakdown."""
     import torch
-    torch.cuda.set_device(local)
-    from paper_2304_03184_b300 import build, synth
-    build.build()
-    import paper_2304_03184_b300 as invr
-    prec = invr.INVR_FP32 if args.prec == "fp32" else invr.INVR_MLP_BF16
-    ctx = invr.Context(local)
-    tw = synth.train_step_workload(n_rays=args.rays)
-    tb, fields, keep = build_train(invr, ctx, tw, prec)
-    R = sum(b[0].shape[1] for b in tb.batches)
-    S_nom = R * tw.n_samples
-    S_occ = occupied_samples(invr, ctx, tb)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 126 MB L2
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         invr.train_step(ctx, tb)
     ctx.sync()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     ctx.enable_timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, b in ev:
         flush.fill_(1)                    # L2 flush between steps (outside the timed events)
         a.record(stream)
@@ -183,81 +179,117 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     ktime = ctx.timing()
     ctx.enable_timing(False)
     ctx.sync()
-    ms = float(np.mean(step_ms))
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * S_nom / (ms * 1e-3)
-    launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktime.items())
+    return ms, ktime
 
-    # roofline of the dominant kernel
+
+def roofline(ktime, tw, R, S_occ, peaks):
     fp = tw.fields[0]
     n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()
-    dom = max(ktime.items(), key=lambda kv: kv[1][0])
-    name, (kms, kn) = dom
+    name, (kms, kn) = max(ktime.items(), key=lambda kv: kv[1][0])
     bound, work = kernel_work(name, R, S_occ, tw.n_samples, fp.desc.L, n_params, fp.desc.n_weight_params())
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    roof = None
+    dur = kms / kn * 1e-3
     if bound == "alu":
         peak = fp32_alu_peak(peaks.get("sm_max_mhz", 2032.0))
-        ach = work / (kms / kn * 1e-3) / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
+        ach = work / dur / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
                 "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x max SM clock"}
-    elif bound == "hbm":
+    if bound == "tensor":
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        ach = work / dur / 1e12
+        return {"kernel": name, "bound": "tensor", "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": "measured (sustained dense bf16)" if "bf16_tflops_sustained" in peaks else "fallback"}
+    if bound == "hbm":
         peak = peaks.get("hbm_gbs", 6400.0)
-        ach = work / (kms / kn * 1e-3) / 1e9
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+        ach = work / dur / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2304_03184_b300 import build, synth
+    build.build()
+    import paper_2304_03184_b300 as invr
+    ctx = invr.Context(local)
+    tw = synth.train_step_workload(n_rays=args.rays)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 126 MB L2
+    clocks = ClockSampler(local)
+    clocks.start()
+
+    # the requested precision, then the other two for the mixed-vs-FP32 comparison
+    order = [args.prec] + [p for p in ("fp32", "fp16", "bf16") if p != args.prec]
+    variants, main = {}, None
+    for p in order:
+        tb, fields, keep = build_train(invr, ctx, tw, PRECS[p])
+        if main is None:
+            R = sum(b[0].shape[1] for b in tb.batches)
+            S_nom = R * tw.n_samples
+            S_occ = occupied_samples(invr, ctx, tb)
+        steps = args.steps if p == args.prec else max(5, args.steps // 4)
+        ms, ktime = time_train(invr, ctx, tb, steps, args.warmup, flush, world)
+        variants[p] = {"value": round(world * S_nom / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
+                       "kernels_ms_per_step": {k: round(v[0] / steps, 4) for k, v in sorted(ktime.items())}}
+        if main is None:
+            main = (tb, fields, keep, ms, ktime)
+    tb, fields, keep, ms, ktime = main
+    value = world * S_nom / (ms * 1e-3)
+    launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktime.items())
+    roof = roofline(ktime, tw, R, S_occ, peaks)
 
     # end to end through the public API with host buffers: copy rays + targets in, loss out
-    e2e = None
-    if True:
-        host_in = [(b[0].cpu().pin_memory(), b[1].cpu().pin_memory(), b[3].cpu().pin_memory()) for b in tb.batches]
-        loss_h = torch.empty(1, pin_memory=True)
-        h2d = sum(x.numel() * 4 for trip in host_in for x in trip)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(args.steps):
-            for (ho, hd, ht), (o, d, _v, t) in zip(host_in, tb.batches):
-                o.copy_(ho, non_blocking=True)
-                d.copy_(hd, non_blocking=True)
-            # targets live back to back ([3][R_b] per batch) inside TrainBatches
-            off = 0
-            for (ho, hd, ht) in host_in:
-                n = ht.numel()
-                tb.targets[off:off + n].copy_(ht.reshape(-1), non_blocking=True)
-                off += n
-            loss = invr.train_step(ctx, tb)
-            loss_h.copy_(loss, non_blocking=True)
-        b.record(stream)
-        torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b) / args.steps
-        e2e = {"value": world * S_nom / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+    host_in = [(b[0].cpu().pin_memory(), b[1].cpu().pin_memory(), b[3].cpu().pin_memory()) for b in tb.batches]
+    loss_h = torch.empty(1, pin_memory=True)
+    h2d = sum(x.numel() * 4 for trip in host_in for x in trip)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        for (ho, hd, ht), (o, d, _v, t) in zip(host_in, tb.batches):
+            o.copy_(ho, non_blocking=True)
+            d.copy_(hd, non_blocking=True)
+        off = 0
+        for (ho, hd, ht) in host_in:      # targets live back to back ([3][R_b] per batch)
+            n = ht.numel()
+            tb.targets[off:off + n].copy_(ht.reshape(-1), non_blocking=True)
+            off += n
+        loss = invr.train_step(ctx, tb)
+        loss_h.copy_(loss, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e_ms = a.elapsed_time(b) / args.steps
+    e2e = {"value": round(world * S_nom / (e_ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
 
-    # render throughput of the two-field 512x512 view
     render = None
     if not args.no_render:
-        render = bench_render(invr, ctx, prec, args, flush)
+        render = {p: bench_render(invr, ctx, PRECS[p], args, flush) for p in order}
     clk = clocks.stop()          # sampled over the train, end-to-end and render regions
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16-mlp/f32",
+           "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else f"{args.prec}-mlp/f32",
            "data": "synthetic",
            "config": {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples,
                       "occupied_samples": S_occ, "fields": len(tw.fields), "parallelism": f"replicas{world}",
                       "l2": "flushed between timed steps (256 MiB write)", "prec": args.prec},
-           "roofline": roof, "e2e": e2e, "render": render, "clocks": clk, "gpu_launches": launches,
+           "roofline": roof, "e2e": e2e, "render": render, "variants": variants, "clocks": clk,
+           "gpu_launches": launches,
            "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(ktime.items())}}
     return out, tw
 

@@ -390,7 +390,9 @@ invr_status train_backward(invr_ctx ctx, const invr_train_args* a, float scale, 
     return fail(ctx, INVR_E_STATE, "invr_field_backward needs the matching invr_field_forward_train first");
   Plan P = ctx->fwd_plan;
   P.grad_scale = scale;
-  INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd", s, launch_mlp_bwd_f32(P, ctx->num_sms, s)));
+  if (plan_has_kind(P, kMlpF32)) INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd", s, launch_mlp_bwd_f32(P, ctx->num_sms, s)));
+  if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
+    INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd_tc", s, launch_mlp_bwd_tc(P, ctx->num_sms, s)));
   P.grad_scale = 1.0f;  // dL/dfeat already carries the scale
   INVR_CUDA(ctx, TIMED(ctx, "encode_bwd", s, launch_encode_bwd(P, ctx->num_sms, s)));
   return INVR_OK;

@@ -211,6 +211,7 @@ cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 bool plan_has_kind(const Plan& P, int kind);
 cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
                                  int num_sms, cudaStream_t s);
 cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s);

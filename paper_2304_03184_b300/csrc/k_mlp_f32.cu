@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_f32(const __grid_constant_
     const int64_t s0 = t * kTS;
     const int v = tile_view(A, s0);
     const FieldDev& F = A.f[v];
+    if (F.mlp_kind != kMlpF32) continue;  // mixed-precision fields train on the tensor cores
     if (cur < 0 || F.weights != A.f[cur].weights) {
       if (cur >= 0) flush_all(acc1, acc2, acc3, acc4, acc5, A.f[cur]);
       __syncthreads();

@@ -1,0 +1,363 @@
+// Backward of the geometry + colour MLPs on the tcgen05 tensor cores, 16-bit operands (the
+// field's FP16 or BF16) with FP32 accumulation (mixed-precision fields).  The incoming
+// dL/d(outputs) are multiplied by in_scale (the inverse of the loss's mean normalisation,
+// so per-sample gradients are O(1) and do not underflow FP16) and the FP32 results (dX,
+// dW) by out_scale on the way out.
+//
+// One CTA = one warpgroup of 128 threads; per 128-sample tile (thread t = sample t):
+//   recompute  X -> H1 -> H2 -> O -> H4          (4 chained MMAs, M = 128, ReLU epilogues)
+//   adjoint    dZ -> dH4 -> dO -> dH2 -> dH1 -> dX (5 chained MMAs against transposed weights,
+//              ReLU masks read back from the stored activations)
+//   weights    dW5^T += H4^T dZ, dW4 += dH4^T O, dW3^T += H2^T dO, dW2 += dH2^T H1,
+//              dW1 += dH1^T X: M = 64 MMAs with K = the 128 samples, issued next to the
+//              chain and accumulated in tensor memory over every tile the CTA visits.
+// The weight-gradient MMAs read the [sample][unit] activation buffers as MN-major operands
+// (each 8 x 16-byte core matrix holds 8 units of 8 samples), so no transposed copies exist.
+// The accumulated dW are read out once per field (M = 64 accumulator: row r in TMEM lane
+// 32 (r / 16) + r % 16) and added to the gradient buffer with one atomic per weight per CTA.
+// dL/dX (the encoding features' gradient) is written FP32 feature-major for the hash
+// scatter.  All waits are bounded; a timeout sets the status word and the CTA frees its
+// tensor memory and returns.
+#include "mlp_tc_common.cuh"
+
+namespace invr {
+
+namespace {
+
+using namespace mlp_tc;
+
+constexpr int kThreadsB = 128;
+constexpr uint32_t kTmemColsB = 256;
+// tensor-memory columns
+constexpr uint32_t C_CHAIN = 0;     // 64: the chain's current layer
+constexpr uint32_t C_DW2 = 64;      // 64
+constexpr uint32_t C_DW1 = 128;     // 32
+constexpr uint32_t C_DW4 = 160;     // 16
+constexpr uint32_t C_DW3T = 176;    // 16
+constexpr uint32_t C_DW5T = 192;    // 16
+
+// shared-memory plan (bytes); [n][k] = K-major operand with n rows and k columns
+constexpr uint32_t B_W1 = 0;                  // [64][32]  forward weights
+constexpr uint32_t B_W2 = B_W1 + 64 * 32 * 2; // [64][64]
+constexpr uint32_t B_W3 = B_W2 + 64 * 64 * 2; // [16][64]
+constexpr uint32_t B_W4 = B_W3 + 16 * 64 * 2; // [64][16]
+constexpr uint32_t B_W5T = B_W4 + 64 * 16 * 2;  // [64][16] transposed weights
+constexpr uint32_t B_W4T = B_W5T + 64 * 16 * 2; // [16][64]
+constexpr uint32_t B_W3T = B_W4T + 16 * 64 * 2; // [64][16]
+constexpr uint32_t B_W2T = B_W3T + 64 * 16 * 2; // [64][64]
+constexpr uint32_t B_W1T = B_W2T + 64 * 64 * 2; // [32][64]
+constexpr uint32_t B_X = B_W1T + 32 * 64 * 2;   // [128][32] activations and deltas
+constexpr uint32_t B_H1 = B_X + kTM * 32 * 2;   // [128][64]
+constexpr uint32_t B_H2 = B_H1 + kTM * 64 * 2;
+constexpr uint32_t B_O = B_H2 + kTM * 64 * 2;   // [128][16]
+constexpr uint32_t B_H4 = B_O + kTM * 16 * 2;   // [128][64]
+constexpr uint32_t B_DZ = B_H4 + kTM * 64 * 2;  // [128][16]
+constexpr uint32_t B_DH4 = B_DZ + kTM * 16 * 2; // [128][64]
+constexpr uint32_t B_DO = B_DH4 + kTM * 64 * 2; // [128][16]
+constexpr uint32_t B_DH2 = B_DO + kTM * 16 * 2; // [128][64]
+constexpr uint32_t B_DH1 = B_DH2 + kTM * 64 * 2;
+constexpr uint32_t B_MISC = B_DH1 + kTM * 64 * 2;
+constexpr uint32_t kSmemB = B_MISC + 64 + 8192;  // + guard band
+
+struct TcBwdArgs {
+  const float* feat;        // [in][ld] FP32 encoding features
+  const float* dout;        // [4][ld]: dL/do_0, dL/dz_rgb
+  float* dfeat;             // [in][ld]
+  const int32_t* s_ray;     // padding marker (< 0) or null
+  const int32_t* view_base;
+  int64_t ld;
+  int n_views;
+  float in_scale;           // applied to dL/d(outputs) before rounding to 16 bit
+  float out_scale;          // applied to dX and dW (FP32) on the way out
+  unsigned* status;
+  FieldDev f[kMaxViews];
+};
+
+// One thread: weight-gradient MMA, D (M = 64 rows x N) += A^T B over the tile's 128 samples.
+// A (rows = M units) and B (rows = N units) are [sample][units] K-major activation buffers
+// read MN-major: unit groups 128 B apart, sample groups units*16 B apart.
+__device__ __forceinline__ void issue_dw(uint32_t d_tmem, uint32_t a_saddr, int a_units, uint32_t b_saddr,
+                                         int b_units, int N, bool accumulate, bool bf16) {
+  const uint32_t idesc = tc::idesc_f16(64, N, bf16) | (1u << 15) | (1u << 16);
+  for (int kk = 0; kk < kTM / 16; ++kk) {
+    const uint64_t ad = tc::smem_desc(a_saddr + kk * 32 * a_units, a_units * 16, 128);
+    const uint64_t bd = tc::smem_desc(b_saddr + kk * 32 * b_units, b_units * 16, 128);
+    tc::mma_f16(d_tmem, ad, bd, idesc, (accumulate || kk > 0) ? 1u : 0u);
+  }
+}
+
+template <bool BF16>
+__device__ void stage_bwd_weights(uint8_t* sm, const FieldDev& F) {
+  const WOff off(F.mlp_in);
+  const int in = F.mlp_in;
+  if (in == 16) {
+    stage<BF16, false, 64, 16>(sm + B_W1, F.weights, off, in, 1);
+    stage<BF16, true, 16, 64>(sm + B_W1T, F.weights, off, in, 1);
+  } else {
+    stage<BF16, false, 64, 32>(sm + B_W1, F.weights, off, in, 1);
+    stage<BF16, true, 32, 64>(sm + B_W1T, F.weights, off, in, 1);
+  }
+  stage<BF16, false, 64, 64>(sm + B_W2, F.weights, off, in, 2);
+  stage<BF16, false, 16, 64>(sm + B_W3, F.weights, off, in, 3);
+  stage<BF16, false, 64, 16>(sm + B_W4, F.weights, off, in, 4);
+  stage<BF16, true, 64, 16>(sm + B_W5T, F.weights, off, in, 5);
+  stage<BF16, true, 16, 64>(sm + B_W4T, F.weights, off, in, 4);
+  stage<BF16, true, 64, 16>(sm + B_W3T, F.weights, off, in, 3);
+  stage<BF16, true, 64, 64>(sm + B_W2T, F.weights, off, in, 2);
+}
+
+// Read the M = 64 weight-gradient accumulators and add them to the field's gradient buffer.
+__device__ void flush_dw(uint32_t tmem, const FieldDev& F, float scale) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  const int row = warp * 16 + lane;  // valid for lane < 16
+  const WOff off(F.mlp_in);
+  const int in = F.mlp_in;
+  float* G = F.grad_weights;
+  float v[16];
+  // dW2 [64 out][64 in]
+  for (int c = 0; c < 4; ++c) {
+    tc::tmem_ld16(taddr + C_DW2 + 16 * c, v);
+    if (lane < 16)
+      for (int j = 0; j < 16; ++j) atomicAdd(G + off.w2 + row * kHidden + 16 * c + j, v[j] * scale);
+  }
+  // dW1 [64 out][in]
+  for (int c = 0; c < in / 16; ++c) {
+    tc::tmem_ld16(taddr + C_DW1 + 16 * c, v);
+    if (lane < 16)
+      for (int j = 0; j < 16; ++j) atomicAdd(G + off.w1 + row * in + 16 * c + j, v[j] * scale);
+  }
+  // dW4p [64 out][16 in], column 0 is padding
+  tc::tmem_ld16(taddr + C_DW4, v);
+  if (lane < 16)
+    for (int j = 1; j < 16; ++j) atomicAdd(G + off.w4 + row * (kGeoOut - 1) + j - 1, v[j] * scale);
+  // dW3^T [64 in][16 out]
+  tc::tmem_ld16(taddr + C_DW3T, v);
+  if (lane < 16)
+    for (int j = 0; j < 16; ++j) atomicAdd(G + off.w3 + j * kHidden + row, v[j] * scale);
+  // dW5p^T [64 in][16 out], outputs 3..15 are padding
+  tc::tmem_ld16(taddr + C_DW5T, v);
+  if (lane < 16)
+    for (int j = 0; j < 3; ++j) atomicAdd(G + off.w5 + j * kColHidden + row, v[j] * scale);
+}
+
+__device__ __forceinline__ bool chain_wait(uint32_t mbar, uint32_t& phase) {
+  bool ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+  phase ^= 1u;
+  ok = __syncthreads_and(ok);
+  tc::fence_after_sync();
+  return ok;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_constant__ TcBwdArgs A) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int t = threadIdx.x, warp = t >> 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + B_MISC + 8);
+  const uint32_t mbar = tc::smem_u32(sm + B_MISC);
+  const uint32_t sb = tc::smem_u32(sm);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemColsB);
+  if (t == 0) tc::mbar_init(mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t row_t = tmem + ((uint32_t)(warp * 32) << 16);
+
+  const int64_t S = (int64_t)A.view_base[A.n_views];
+  const int64_t n_tiles = (S + kTM - 1) / kTM;
+  int cur = -1;            // view whose field's weights are staged
+  bool dw_live = false;    // weight-gradient accumulators hold data
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const int64_t s0 = tile * kTM;
+    const int v = view_of_slot(A.view_base, A.n_views, s0);
+    const FieldDev& F = A.f[v];
+    if (F.mlp_kind != (BF16 ? kMlpBF16 : kMlpF16)) continue;  // uniform over the CTA
+    if (cur < 0 || F.weights != A.f[cur].weights) {
+      if (dw_live) {
+        if (t == 0) tc::commit_to(mbar);
+        if (!(ok = chain_wait(mbar, phase))) break;
+        flush_dw(tmem, A.f[cur], A.out_scale);
+        tc::fence_before_sync();
+        __syncthreads();
+        dw_live = false;
+      }
+      stage_bwd_weights<BF16>(sm, F);
+      cur = v;
+    }
+    const int in = F.mlp_in;
+    const int valid = (int)(S - s0 < kTM ? S - s0 : kTM);
+    const bool live = t < valid && (!A.s_ray || A.s_ray[s0 + t] >= 0);
+    // ---- X row, dZ row (dL/dz for rgb; zero for the padded outputs), dL/do_0
+    for (int j = 0; j < in / 8; ++j) {
+      float x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = t < valid ? A.feat[(int64_t)(8 * j + i) * A.ld + s0 + t] : 0.0f;
+      uint4 q;
+      q.x = tc::pack2<BF16>(x[0], x[1]);
+      q.y = tc::pack2<BF16>(x[2], x[3]);
+      q.z = tc::pack2<BF16>(x[4], x[5]);
+      q.w = tc::pack2<BF16>(x[6], x[7]);
+      *reinterpret_cast<uint4*>(sm + B_X + tc::kmajor_offset(t, 8 * j, in)) = q;
+    }
+    float dz[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dz[i] = 0.0f;
+    float do0 = 0.0f;
+    if (live) {
+      for (int i = 0; i < 3; ++i) dz[i] = A.dout[(int64_t)(1 + i) * A.ld + s0 + t] * A.in_scale;
+      do0 = A.dout[s0 + t] * A.in_scale;
+    }
+    row16_out<BF16>(dz, sm + B_DZ, t);
+    operands_ready();
+    // ---- recompute: H1
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_X, sb + B_W1, in, 64, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H1, nullptr, t);
+    operands_ready();
+    // ---- H2
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_H1, sb + B_W2, 64, 64, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H2, nullptr, t);
+    operands_ready();
+    // ---- O = (0, o_1..o_15)
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_H2, sb + B_W3, 64, 16, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    {
+      float o[16];
+      tc::tmem_ld16(row_t + C_CHAIN, o);
+      o[0] = 0.0f;
+      row16_out<BF16>(o, sm + B_O, t);
+    }
+    operands_ready();
+    // ---- H4
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_O, sb + B_W4, 16, 64, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H4, nullptr, t);
+    operands_ready();
+    // ---- dH4 = (dZ W5p) * [H4 > 0];  dW5p^T += H4^T dZ
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_DZ, sb + B_W5T, 16, 64, BF16);
+      issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH4, sm + B_H4, t);
+    operands_ready();
+    // ---- dO = dH4 W4p (o_0 slot carries dL/do_0);  dW4p += dH4^T O
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_DH4, sb + B_W4T, 64, 16, BF16);
+      issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    {
+      float d[16];
+      tc::tmem_ld16(row_t + C_CHAIN, d);
+      d[0] = do0;
+      row16_out<BF16>(d, sm + B_DO, t);
+    }
+    operands_ready();
+    // ---- dH2 = (dO W3) * [H2 > 0];  dW3^T += H2^T dO
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_DO, sb + B_W3T, 16, 64, BF16);
+      issue_dw(tmem + C_DW3T, sb + B_H2, 64, sb + B_DO, 16, 16, dw_live, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH2, sm + B_H2, t);
+    operands_ready();
+    // ---- dH1 = (dH2 W2) * [H1 > 0];  dW2 += dH2^T H1
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_DH2, sb + B_W2T, 64, 64, BF16);
+      issue_dw(tmem + C_DW2, sb + B_DH2, 64, sb + B_H1, 64, 64, dw_live, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH1, sm + B_H1, t);
+    operands_ready();
+    // ---- dX = dH1 W1;  dW1 += dH1^T X
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_chain(tmem + C_CHAIN, sb + B_DH1, sb + B_W1T, 64, in, BF16);
+      issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + B_X, in, in, dw_live, BF16);
+      tc::commit_to(mbar);
+    }
+    if (!(ok = chain_wait(mbar, phase))) break;
+    dw_live = true;
+    for (int c = 0; c < in / 16; ++c) {
+      float d[16];
+      tc::tmem_ld16(row_t + C_CHAIN + 16 * c, d);
+      if (t < valid)
+        for (int j = 0; j < 16; ++j) A.dfeat[(int64_t)(16 * c + j) * A.ld + s0 + t] = d[j] * A.out_scale;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (ok && dw_live) {
+    tc::fence_after_sync();
+    flush_dw(tmem, A.f[cur], A.out_scale);  // every MMA completed at the last chain wait
+  }
+  if (!ok && t == 0) atomicOr(A.status, kStatusTimeout);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemColsB);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  TcBwdArgs A{};
+  A.feat = static_cast<const float*>(P.ws.feat);
+  A.dout = P.ws.dout;
+  A.dfeat = P.ws.dfeat;
+  A.s_ray = P.ws.s_ray;
+  A.view_base = P.ws.view_base;
+  A.ld = P.ws.S_cap;
+  A.n_views = P.n_views;
+  // dL/dout carries the loss's 1 / (3 R); take it out of the 16-bit operands
+  A.in_scale = P.grad_scale / P.loss_norm;
+  A.out_scale = P.loss_norm;
+  A.status = P.status;
+  for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
+  cudaError_t e = cudaSuccess;
+  if (plan_has_kind(P, kMlpBF16)) {
+    cudaFuncSetAttribute(k_mlp_bwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB);
+    k_mlp_bwd_tc<true><<<num_sms, kThreadsB, kSmemB, s>>>(A);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) {
+    cudaFuncSetAttribute(k_mlp_bwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB);
+    k_mlp_bwd_tc<false><<<num_sms, kThreadsB, kSmemB, s>>>(A);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace invr
