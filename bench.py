@@ -2,13 +2,16 @@
 
 One step = one training step over one batch of key-frame rays: ray sampling with
 occupancy skipping, nearest-node dual-quaternion warp, hash encoding, MLPs, compositing,
-Huber loss, the adjoint chain (compositing, MLPs, hash-table scatter) and Adam.  The
-workload is the training step of the paper-shaped synthetic capture: 2^18 rays drawn
-from four 512x512 ring cameras, 128 samples per ray, the human field (L=16, T=2^19, F=2)
-warped by a 2048-node graph (K=4) with 128^3 occupancy skipping.  The render throughput
-of the two-field 512x512 view (human + object, 128 samples) is reported beside it.
+Huber loss, the adjoint chain (compositing, MLPs, hash-table scatter) and Adam.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|bf16] [--impl ours|reference]
+Headline workload (value, e2e, roofline): the batched key-frame step -- 8 key frames, each
+with its own 2048-node graph pose and object pose, rays drawn log-uniformly between 2^14 and
+2^18 per frame and field (human and object fields, L=16, T=2^19), 128 samples per ray --
+in BF16 MLP with FP32 accumulation, launch shapes autotuned, the whole step captured in one
+CUDA graph.  Beside it: the same frames as 8 sequential FP32 calls, the single-batch
+training step (2^18 rays) in BF16 / FP16 / FP32, and the two-field 512x512 render.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp16|bf16] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (the path has
 no exchange step at one GPU per key-frame set); value = all ranks' samples / max time.
@@ -44,6 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=1 << 18)
     ap.add_argument("--no-render", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-interleave", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -279,8 +284,10 @@ def run_ours(args, rank, world, local):
     render = None
     if not args.no_render:
         render = {p: bench_render(invr, ctx, PRECS[p], args, flush) for p in order}
-    clk = clocks.stop()          # sampled over the train, end-to-end and render regions
 
+    single = {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples, "occupied_samples": S_occ,
+              "value": round(value, 1), "ms_per_step": round(ms, 3), "e2e": e2e, "roofline": roof,
+              "variants": variants}
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else f"{args.prec}-mlp/f32",
@@ -288,10 +295,204 @@ def run_ours(args, rank, world, local):
            "config": {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples,
                       "occupied_samples": S_occ, "fields": len(tw.fields), "parallelism": f"replicas{world}",
                       "l2": "flushed between timed steps (256 MiB write)", "prec": args.prec},
-           "roofline": roof, "e2e": e2e, "render": render, "variants": variants, "clocks": clk,
+           "roofline": roof, "e2e": e2e, "render": render, "variants": variants, "clocks": None,
            "gpu_launches": launches,
            "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(ktime.items())}}
+    if not args.no_batched:
+        bt = bench_batched(invr, args, flush, world, args.prec)
+        bvalue = world * bt["S_nom"] / (bt["ms"] * 1e-3)
+        btw = bt["tw"]
+        out["value"] = round(bvalue, 1)
+        out["ms_per_step"] = round(bt["ms"], 3)
+        out["config"] = {"workload": bt["workload"], "rays": bt["rays"], "samples_per_ray": bt["samples_per_ray"],
+                         "occupied_samples": bt["occupied_samples"], "batches": bt["batches"],
+                         "fields": len(btw.fields), "parallelism": f"replicas{world}",
+                         "l2": "flushed between timed steps (256 MiB write)", "prec": args.prec,
+                         "launch": "one CUDA graph per step (all batches per stage launch)", "tune": bt["tune"]}
+        out["e2e"] = bt["e2e"]
+        bR, bS = bt["rays"], bt["occupied_samples"]
+        out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks)
+        nsteps = max(5, args.steps // 4)
+        out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
+        out["gpu_launches"] = int(round(sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in bt["ktime"].items())
+                                        / nsteps * args.steps))
+        out["variants"] = {args.prec + "_graph": {"value": round(bvalue, 1), "ms_per_step": round(bt["ms"], 3)},
+                           args.prec + "_eager": {"value": round(world * bt["S_nom"] / (bt["eager_ms"] * 1e-3), 1),
+                                                  "ms_per_step": round(bt["eager_ms"], 3)},
+                           "fp32_sequential": bt["fp32_sequential"]}
+        out["single_batch_train"] = single
+        tw = btw
+    if not args.no_interleave:
+        out["interleave"] = bench_interleave(invr, args, args.prec)
+    out["clocks"] = clocks.stop()      # sampled over every timed region above
     return out, tw
+
+
+def frames_of(tw):
+    """Split the key-frame workload's batches (frame-major: human, object) per frame."""
+    from paper_2304_03184_b300 import synth
+    out = []
+    for i in range(0, len(tw.batches), 2):
+        out.append(synth.TrainWorkload(tw.name, tw.batches[i:i + 2], tw.fields, tw.n_samples, tw.t_eps,
+                                       tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps))
+    return out
+
+
+def bench_batched(invr, args, flush, world, prec_name):
+    """Headline: batched key-frame step, mixed precision, autotuned, one CUDA graph per step."""
+    import torch
+    from paper_2304_03184_b300 import synth
+    tw = synth.keyframe_batch_workload()
+    R = sum(b.rays.n for b in tw.batches)
+    S_nom = R * tw.n_samples
+    stream = torch.cuda.current_stream()
+
+    ctx = invr.Context(torch.cuda.current_device())
+    tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
+    S_occ = occupied_samples(invr, ctx, tb)
+    ctx.reserve(R, max(32, 2 * (S_occ // R + 1)))       # fixed workspace: capture allocates nothing
+    tune = ctx.autotune(tb)
+    # eager timed steps: per-kernel breakdown (same kernels as the graph)
+    eager_ms, ktime = time_train(invr, ctx, tb, max(5, args.steps // 4), args.warmup, flush, world)
+    graph = invr.TrainGraph(ctx, tb, warmup=2)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        flush.fill_(1)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ctx.sync()
+
+    # end to end: copy every batch's rays and targets from pinned host memory, replay, read the loss
+    host_in = [(b[0].cpu().pin_memory(), b[1].cpu().pin_memory(), b[3].cpu().pin_memory()) for b in tb.batches]
+    loss_h = torch.empty(1, pin_memory=True)
+    h2d = sum(x.numel() * 4 for trip in host_in for x in trip)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        off = 0
+        for (ho, hd, ht), (o, d, _v, _t) in zip(host_in, tb.batches):
+            o.copy_(ho, non_blocking=True)
+            d.copy_(hd, non_blocking=True)
+            n = ht.numel()
+            tb.targets[off:off + n].copy_(ht.reshape(-1), non_blocking=True)
+            off += n
+        loss_h.copy_(graph.replay(), non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e_ms = a.elapsed_time(b) / args.steps
+    e2e = {"value": round(world * S_nom / (e_ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+    # plain path: the same frames as 8 sequential FP32 calls (2 batches each), no graph
+    ctx32 = invr.Context(torch.cuda.current_device())
+    per_frame = [build_train(invr, ctx32, fw, PRECS["fp32"]) for fw in frames_of(tw)]
+    for _ in range(2):
+        for fb in per_frame:
+            invr.train_step(ctx32, fb[0])
+    ctx32.sync()
+    steps32 = max(3, args.steps // 8)
+    ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps32)]
+    for a, b in ev32:
+        flush.fill_(1)
+        a.record(stream)
+        for fb in per_frame:
+            invr.train_step(ctx32, fb[0])
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms32 = float(np.mean([a.elapsed_time(b) for a, b in ev32]))
+    ctx32.sync()
+    return {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples, "occupied_samples": S_occ,
+            "batches": len(tw.batches), "S_nom": S_nom, "ms": ms, "eager_ms": eager_ms, "ktime": ktime,
+            "tune": tune, "e2e": e2e, "tw": tw,
+            "fp32_sequential": {"value": round(world * S_nom / (ms32 * 1e-3), 1), "ms_per_step": round(ms32, 3),
+                                "launches": "8 sequential train_step calls (2 batches each), FP32, no graph"}}
+
+
+def build_views(invr, ctx, w, prec):
+    import torch
+    keep, views = [], []
+    for sv in w.views:
+        f = invr.Field.from_synth(ctx, sv.field, prec)
+        g = None
+        if sv.graph is not None:
+            gg = sv.graph
+            g = invr.Graph(ctx, gg.x_canon.shape[1], gg.K, gg.radius, 1, torch.from_numpy(gg.x_canon).cuda())
+            g.set_pose(0, torch.from_numpy(gg.dq).cuda(), torch.from_numpy(gg.x_live).cuda())
+        occ = torch.from_numpy(sv.occupancy).cuda()
+        keep.append((f, g, occ))
+        views.append(invr.View(f, g, 0, sv.rigid_dq, occ))
+    return views, keep
+
+
+def bench_interleave(invr, args, prec_name):
+    """1280x720 two-field renders (T=2^21, L=16, up to 192 samples, 4096 nodes, K=8) on one
+    stream, alternating with 2^18-ray training steps of the human field on a second stream;
+    the renderer reads a parameter snapshot taken after each training step.  Beside it the
+    plain path: the same render and step in FP32, one after the other on one stream."""
+    import torch
+    from paper_2304_03184_b300 import synth
+    rw = synth.two_field_render(seed=5, width=1280, height=720, n_samples=192, field_desc=synth.CFG5_FIELD,
+                                n_nodes=4096, K=8)
+    tw = synth.train_step_workload(seed=5, n_rays=1 << 18, field_desc=synth.CFG5_FIELD, n_nodes=4096, K=8)
+    dev = torch.cuda.current_device()
+    o, d = torch.from_numpy(rw.rays.o).cuda(), torch.from_numpy(rw.rays.d).cuda()
+    n_iter = max(5, args.steps // 2)
+
+    def run(prec, overlap):
+        ctx_r, ctx_t = invr.Context(dev), invr.Context(dev)
+        views, keep_r = build_views(invr, ctx_r, rw, prec)
+        tb, fields, keep_t = build_train(invr, ctx_t, tw, prec)
+        trained = list(fields.values())[0]
+        snap = views[0].field                       # the renderer's copy of the human field
+        ctx_r.reserve(2 * rw.rays.n, 48)
+        ctx_t.reserve(sum(b[0].shape[1] for b in tb.batches), 48)
+        s_r = torch.cuda.Stream() if overlap else torch.cuda.current_stream()
+        s_t = torch.cuda.Stream() if overlap else torch.cuda.current_stream()
+        stepped, copied = torch.cuda.Event(), torch.cuda.Event()
+        for it in range(n_iter + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(torch.cuda.current_stream())
+                s_r.wait_stream(torch.cuda.current_stream())
+                s_t.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s_t):
+                s_t.wait_event(copied)              # the snapshot of the previous step is taken
+                invr.train_step(ctx_t, tb)
+                stepped.record(s_t)
+            with torch.cuda.stream(s_r):
+                s_r.wait_event(stepped)             # snapshot after this step's update
+                snap.copy_params_from(trained)
+                copied.record(s_r)
+                invr.render_rays(ctx_r, o, d, rw.n_samples, rw.t_eps, views)
+        torch.cuda.current_stream().wait_stream(s_r)
+        torch.cuda.current_stream().wait_stream(s_t)
+        t1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ctx_r.sync()
+        ctx_t.sync()
+        ms = t0.elapsed_time(t1) / n_iter
+        R = sum(b[0].shape[1] for b in tb.batches)
+        return {"frames_per_s": round(1e3 / ms, 2), "train_samples_per_s": round(R * tw.n_samples / (ms * 1e-3), 1),
+                "ms_per_iteration": round(ms, 3)}
+
+    return {"render_workload": rw.name, "train_workload": tw.name, "iterations": n_iter,
+            prec_name + "_two_streams": run(PRECS[prec_name], True), "fp32_one_stream": run(PRECS["fp32"], False)}
 
 
 def bench_render(invr, ctx, prec, args, flush):
@@ -327,49 +528,55 @@ def bench_render(invr, ctx, prec, args, flush):
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm
-def oracle_train_sample(tw, n_rays):
-    """The oracle's train step (loss, gradient, Adam) on the first n_rays rays of the batch."""
+def oracle_train_sample(tw, rays_per_batch):
+    """The oracle's training step (loss, gradient, Adam on every field) on the first
+    rays_per_batch rays of every batch of the workload; returns seconds."""
     from oracle import oracle
-    b = tw.batches[0]
-    sub = slice(0, n_rays)
-    f = oracle.Field.from_params(b.view.field)
-    v = oracle.View.from_synth(b.view, field=f)
-    ob = oracle.TrainBatch(b.rays.o[:, sub], b.rays.d[:, sub], v, b.target[:, sub])
+    ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
+    obs = []
+    for b in tw.batches:
+        n = min(rays_per_batch, b.rays.n)
+        v = oracle.View.from_synth(b.view, field=ofields[id(b.view.field)])
+        obs.append(oracle.TrainBatch(b.rays.o[:, :n], b.rays.d[:, :n], v, b.target[:, :n]))
     t0 = time.perf_counter()
-    _, grads = oracle.train_loss_grad([ob], tw.n_samples, tw.t_eps, tw.huber_delta)
-    gt, gw = grads[id(f)]
-    p = np.concatenate([f.tables, f.weights])
-    m, vv = np.zeros_like(p), np.zeros_like(p)
-    oracle.adam(p, np.concatenate([gt, gw]), m, vv, 1, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
-    return time.perf_counter() - t0
+    _, grads = oracle.train_loss_grad(obs, tw.n_samples, tw.t_eps, tw.huber_delta)
+    for f in ofields.values():
+        gt, gw = grads[id(f)]
+        p = np.concatenate([f.tables, f.weights])
+        m, vv = np.zeros_like(p), np.zeros_like(p)
+        oracle.adam(p, np.concatenate([gt, gw]), m, vv, 1, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    return time.perf_counter() - t0, sum(min(rays_per_batch, b.rays.n) for b in tw.batches)
 
 
-def cpu_baseline(tw, n_rays=32768):
+def cpu_baseline(tw, rays_per_batch=2048):
     from oracle import oracle
     oracle.build()
-    dt = oracle_train_sample(tw, n_rays)
-    return {"value": round(n_rays * tw.n_samples / dt, 1), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"first {n_rays} rays of the workload, one train step (loss+grad+Adam), {dt:.1f} s"}
+    dt, n = oracle_train_sample(tw, rays_per_batch)
+    return {"value": round(n * tw.n_samples / dt, 1), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {rays_per_batch} rays of each of the {len(tw.batches)} batches ({n} rays), "
+                      f"one training step (loss + gradient + Adam), {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
     from paper_2304_03184_b300 import synth
-    tw = synth.train_step_workload(n_rays=args.rays)
-    n = 1024
+    tw = synth.keyframe_batch_workload()
+    per_batch = 64
     times = []
     for _ in range(args.warmup):
-        oracle_train_sample(tw, n)
+        oracle_train_sample(tw, per_batch)
+    n = 0
     for _ in range(args.steps):
-        times.append(oracle_train_sample(tw, n))
+        dt, n = oracle_train_sample(tw, per_batch)
+        times.append(dt)
     ms = float(np.mean(times)) * 1e3
     value = n * tw.n_samples / (ms * 1e-3)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": tw.name, "rays": n, "samples_per_ray": tw.n_samples,
-                       "note": "FP64 CPU oracle on a 1024-ray sample of the workload per step"},
+            "config": {"workload": tw.name, "rays": n, "samples_per_ray": tw.n_samples, "batches": len(tw.batches),
+                       "note": f"FP64 CPU oracle on the first {per_batch} rays of every batch per step"},
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{n} rays x {tw.n_samples} samples per step"},
+                             "sample": f"{per_batch} rays x {len(tw.batches)} batches x {tw.n_samples} samples per step"},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

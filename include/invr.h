@@ -61,9 +61,12 @@ typedef enum {
 invr_status invr_ctx_create(invr_ctx* out, int device);
 invr_status invr_ctx_destroy(invr_ctx ctx);
 
-/* Size the workspace for calls of up to max_rays rays in total (summed over views and
- * batches) and max_samples samples per ray, so that later calls allocate nothing (needed
- * before capturing calls into a CUDA graph). */
+/* Size the workspace once for calls of up to max_rays rays in total (summed over views and
+ * batches) and max_samples occupied samples per ray on average; afterwards the workspace
+ * never grows, so later calls allocate nothing (needed before capturing calls into a CUDA
+ * graph).  A call with more rays returns INVR_E_ARG; a call whose occupied samples exceed
+ * the reserved slots is detected on the device, skips its sample work and makes the next
+ * invr_ctx_sync return INVR_E_STATE. */
 invr_status invr_ctx_reserve(invr_ctx ctx, int64_t max_rays, int max_samples);
 
 /* Wait for `stream`, then read and clear the device status word: INVR_E_NONFINITE if a
@@ -111,6 +114,10 @@ invr_status invr_field_set_params(invr_field field, const float* tables_dev, con
  * of Adam steps taken (read after the stream's prior work completes). */
 invr_status invr_field_get_params(invr_field field, float* tables_dev, float* weights_dev, float* adam_m_dev,
                                   float* adam_v_dev, int64_t* step, invr_stream stream);
+/* Copy src's parameters (tables and weights, not gradients or Adam state) into dst, on
+ * `stream`; both fields must have the same description apart from precision.  Used to give a
+ * renderer a snapshot of a field that another stream keeps training. */
+invr_status invr_field_copy_params(invr_field dst, invr_field src, invr_stream stream);
 /* Copy the accumulated gradients out (same layouts as the parameters); either may be NULL. */
 invr_status invr_field_get_grads(invr_field field, float* grad_tables_dev, float* grad_weights_dev,
                                  invr_stream stream);
@@ -204,6 +211,17 @@ invr_status invr_train_step(invr_ctx ctx, const invr_train_args* args, invr_stre
 invr_status invr_field_forward_train(invr_ctx ctx, const invr_train_args* args, invr_stream stream);
 invr_status invr_field_backward(invr_ctx ctx, const invr_train_args* args, float grad_scale, invr_stream stream);
 invr_status invr_field_adam(invr_field field, float lr, float beta1, float beta2, float eps, invr_stream stream);
+
+/* Autotuner of the launch shapes (CTAs per SM of the warp, encoding and gradient-scatter
+ * kernels, and the level resolution up to which gradient runs are summed per warp before
+ * the atomics): coordinate descent, each candidate timed with CUDA events on `stream` over
+ * forward_train + backward of `args` (best of 2 after a warm-up run).  Parameters are not
+ * changed (no Adam step); the gradients it accumulates are cleared.  The chosen shapes are
+ * kept in the context for all later calls.  Synchronises `stream`; not during capture. */
+invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* args, invr_stream stream);
+/* The context's launch shapes: out4 = {warp CTAs/SM, encode CTAs/SM, scatter CTAs/SM,
+ * aggregation resolution}. */
+invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4);
 
 /* ------------------------------------------------------------------ single steps */
 /* Samples of n_rays rays as the renderer takes them: count_dev [R] occupied samples per

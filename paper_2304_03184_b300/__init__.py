@@ -82,6 +82,9 @@ _SIGNATURES = {
     "invr_ctx_enable_timing": [_VP, _I],
     "invr_ctx_timing": [_VP, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64), _I],
     "invr_query_points_noalloc": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
+    "invr_ctx_autotune": [_VP, C.POINTER(invr_train_args), _VP],
+    "invr_ctx_get_tune": [_VP, C.POINTER(C.c_int)],
+    "invr_field_copy_params": [_VP, _VP, _VP],
 }
 
 _lib_handle = None
@@ -154,6 +157,17 @@ class Context:
     def sync(self):
         _check(lib().invr_ctx_sync(self.h, _stream()), self.h)
 
+    def autotune(self, tb: "TrainBatches"):
+        """Pick the launch shapes for this workload (times forward + backward candidates)."""
+        _check(lib().invr_ctx_autotune(self.h, C.byref(tb.args), _stream()), self.h)
+        return self.tune()
+
+    def tune(self):
+        out = (C.c_int * 4)()
+        _check(lib().invr_ctx_get_tune(self.h, out), self.h)
+        return {"warp_ctas_per_sm": out[0], "encode_ctas_per_sm": out[1], "encode_bwd_ctas_per_sm": out[2],
+                "agg_res": out[3]}
+
     def enable_timing(self, on: bool = True):
         _check(lib().invr_ctx_enable_timing(self.h, 1 if on else 0), self.h)
 
@@ -222,6 +236,10 @@ class Field:
         gw = torch.empty(self.n_weights, device="cuda")
         _check(lib().invr_field_get_grads(self.h, _ptr(gt), _ptr(gw), _stream()), self.ctx.h)
         return gt, gw
+
+    def copy_params_from(self, src: "Field"):
+        """Snapshot src's tables and weights into this field (enqueued on the current stream)."""
+        _check(lib().invr_field_copy_params(self.h, src.h, _stream()), self.ctx.h)
 
     def zero_grads(self):
         _check(lib().invr_field_zero_grads(self.h, _stream()), self.ctx.h)
@@ -310,6 +328,30 @@ class TrainBatches:
         self.args = invr_train_args(len(rargs), self._rargs, _ptr(self.targets), huber_delta, lr, beta1, beta2,
                                     adam_eps, _ptr(self.loss))
         self.ctx = None
+
+
+class TrainGraph:
+    """A training step captured once into a CUDA graph and replayed: every batch of the step
+    (key frames x fields) goes through one launch per stage, and the whole step is one graph
+    launch.  The context must have been sized with Context.reserve first."""
+
+    def __init__(self, ctx: Context, tb: TrainBatches, warmup: int = 2):
+        torch = _torch()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                train_step(ctx, tb)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            train_step(ctx, tb)
+        self.ctx, self.tb = ctx, tb
+
+    def replay(self):
+        self.graph.replay()
+        return self.tb.loss
 
 
 def train_step(ctx: Context, tb: TrainBatches):

@@ -18,6 +18,8 @@ struct invr_ctx_s {
   Workspace ws{};
   int64_t cap_R = 0, cap_S = 0;
   bool cap_train = false;
+  bool cap_fixed = false;   // set by invr_ctx_reserve: never grow, overflow is flagged on device
+  Tune tune;
   unsigned* status = nullptr;
   std::string err;
   // per-kernel event timing (invr_ctx_enable_timing)
@@ -156,6 +158,13 @@ void free_workspace(Workspace& w) {
 // Grow the workspace to hold R rays and S sample slots (and the training buffers).
 invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cudaStream_t stream) {
   if (R <= ctx->cap_R && S <= ctx->cap_S && (!train || ctx->cap_train)) return INVR_OK;
+  if (ctx->cap_fixed) {
+    // a reserved workspace never grows: more rays is an argument error, more samples than
+    // reserved is detected on the device (status word, reported by invr_ctx_sync)
+    if (R > ctx->cap_R) return fail(ctx, INVR_E_ARG, "more rays than reserved with invr_ctx_reserve");
+    if (train && !ctx->cap_train) return fail(ctx, INVR_E_STATE, "reserved workspace has no training buffers");
+    return INVR_OK;
+  }
   if (capturing(stream))
     return fail(ctx, INVR_E_STATE, "workspace too small during stream capture: call invr_ctx_reserve first");
   R = std::max(R, ctx->cap_R);
@@ -276,7 +285,8 @@ invr_status build_plan(invr_ctx ctx, const std::vector<const invr_render_args*>&
   P.n_views = nv;
   P.n_samples = n_samples;
   P.t_eps = t_eps;
-  P.agg_res = 256;
+  P.tune = ctx->tune;
+  P.agg_res = ctx->tune.agg_res;
   P.grad_scale = 1.0f;
   int64_t ray_begin = 0;
   int blocks = 0;
@@ -456,7 +466,86 @@ invr_status invr_ctx_destroy(invr_ctx ctx) {
 invr_status invr_ctx_reserve(invr_ctx ctx, int64_t max_rays, int max_samples) {
   if (!ctx || max_rays < 0 || max_samples < 1 || max_samples > 1024) return fail(ctx, INVR_E_ARG, "bad reserve sizes");
   DeviceGuard guard(ctx->device);
-  return ensure_workspace(ctx, max_rays, max_rays * max_samples + (int64_t)kMaxViews * kTile, true, nullptr);
+  ctx->cap_fixed = false;
+  ctx->cap_R = ctx->cap_S = 0;  // force a fresh allocation of exactly the reserved size
+  ctx->cap_train = false;
+  invr_status st = ensure_workspace(ctx, max_rays, max_rays * max_samples + (int64_t)kMaxViews * kTile, true, nullptr);
+  if (st == INVR_OK) ctx->cap_fixed = true;
+  return st;
+}
+
+invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_stream stream) {
+  if (!ctx || !a) return INVR_E_ARG;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (capturing(s)) return fail(ctx, INVR_E_STATE, "autotune cannot run during stream capture");
+  const bool timing_was = ctx->timing;
+  // time forward + backward (no optimiser step, parameters unchanged) per candidate
+  auto measure = [&](float& ms) -> invr_status {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ctx->timing = false;
+    invr_status st = INVR_OK;
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && st == INVR_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      st = train_forward(ctx, a, s);
+      if (st == INVR_OK) st = train_backward(ctx, a, 1.0f, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) best = std::min(best, t);  // first repetition warms caches
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ms = best;
+    return st;
+  };
+  Tune best = ctx->tune;
+  float best_ms = 0.0f;
+  invr_status st = measure(best_ms);
+  // coordinate descent over the launch shapes
+  const int warp_c[] = {4, 8, 16}, enc_c[] = {1, 2, 4, 8}, agg_c[] = {0, 64, 256, 1024};
+  for (int dim = 0; dim < 4 && st == INVR_OK; ++dim) {
+    const int* cands = dim == 0 ? warp_c : (dim == 3 ? agg_c : enc_c);
+    const int n = dim == 0 ? 3 : 4;
+    for (int i = 0; i < n && st == INVR_OK; ++i) {
+      Tune t = best;
+      int* slot = dim == 0 ? &t.warp_ctas_per_sm
+                           : dim == 1 ? &t.encode_ctas_per_sm : dim == 2 ? &t.encode_bwd_ctas_per_sm : &t.agg_res;
+      if (*slot == cands[i]) continue;
+      *slot = cands[i];
+      ctx->tune = t;
+      float ms = 0.0f;
+      st = measure(ms);
+      if (st == INVR_OK && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  }
+  ctx->tune = best;
+  ctx->timing = timing_was;
+  ctx->fwd_valid = false;
+  if (st != INVR_OK) return st;
+  // the timed backward passes accumulated gradients: clear them
+  for (int b = 0; b < a->n_batches; ++b) {
+    invr_field f = a->batches[b].views[0].field;
+    INVR_CUDA(ctx, cudaMemsetAsync(f->grads, 0, (f->n_tab + f->n_w) * sizeof(float), s));
+  }
+  INVR_CUDA(ctx, cudaStreamSynchronize(s));
+  return INVR_OK;
+}
+
+invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4) {
+  if (!ctx || !out4) return INVR_E_ARG;
+  out4[0] = ctx->tune.warp_ctas_per_sm;
+  out4[1] = ctx->tune.encode_ctas_per_sm;
+  out4[2] = ctx->tune.encode_bwd_ctas_per_sm;
+  out4[3] = ctx->tune.agg_res;
+  return INVR_OK;
 }
 
 invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream) {
@@ -584,6 +673,19 @@ invr_status invr_field_get_params(invr_field f, float* tables_dev, float* weight
     INVR_CUDA(ctx, cudaStreamSynchronize(s));
     INVR_CUDA(ctx, cudaMemcpy(step, f->step, sizeof(int64_t), cudaMemcpyDeviceToHost));
   }
+  return INVR_OK;
+}
+
+invr_status invr_field_copy_params(invr_field dst, invr_field src, invr_stream stream) {
+  if (!dst || !src) return INVR_E_ARG;
+  invr_ctx ctx = dst->ctx;
+  if (src->ctx->device != ctx->device) return fail(ctx, INVR_E_ARG, "fields on different devices");
+  if (dst->n_tab != src->n_tab || dst->n_w != src->n_w || dst->desc.L != src->desc.L ||
+      dst->desc.N_min != src->desc.N_min || dst->desc.growth != src->desc.growth)
+    return fail(ctx, INVR_E_ARG, "field descriptions differ");
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, cudaMemcpyAsync(dst->params, src->params, (src->n_tab + src->n_w) * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
   return INVR_OK;
 }
 

@@ -87,6 +87,14 @@ struct Workspace {
   int64_t R_cap;            // ray slots
 };
 
+// Launch shapes the autotuner chooses: CTAs per SM of the grid-stride kernels.
+struct Tune {
+  int warp_ctas_per_sm = 8;
+  int encode_ctas_per_sm = 2;
+  int encode_bwd_ctas_per_sm = 2;
+  int agg_res = 256;
+};
+
 struct Plan {
   int n_views;
   int n_samples;
@@ -97,6 +105,7 @@ struct Plan {
   float huber_delta;
   float grad_scale;
   int agg_res;              // levels with N_l <= agg_res aggregate gradient runs per warp
+  Tune tune;                // launch shapes (autotuned per context)
   Workspace ws;
   unsigned* status;         // device status word
   ViewDev v[kMaxViews];

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan
 cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s) {
   int L = 0;
   for (int v = 0; v < P.n_views; ++v) L = P.v[v].field.L > L ? P.v[v].field.L : L;
-  dim3 grid(num_sms * 2, L);
+  dim3 grid(num_sms * P.tune.encode_ctas_per_sm, L);
   k_encode<<<grid, 256, 0, s>>>(P);
   return cudaGetLastError();
 }
@@ -152,7 +152,7 @@ cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s) {
 cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s) {
   int L = 0;
   for (int v = 0; v < P.n_views; ++v) L = P.v[v].field.L > L ? P.v[v].field.L : L;
-  dim3 grid(num_sms * 2, L);
+  dim3 grid(num_sms * P.tune.encode_bwd_ctas_per_sm, L);
   k_encode_bwd<<<grid, 256, 0, s>>>(P);
   return cudaGetLastError();
 }

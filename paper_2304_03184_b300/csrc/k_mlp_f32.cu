@@ -209,7 +209,8 @@ __device__ __forceinline__ void flush_dw(float* acc, float* G, const WeightOffse
 
 __device__ __forceinline__ void tile_range(const MlpArgs& A, int64_t& n_tiles) {
   const int64_t S = A.view_base ? (int64_t)A.view_base[A.n_views] : A.n;
-  n_tiles = (S + kTS - 1) / kTS;
+  // a sample list longer than the workspace (flagged by the scan) is not processed
+  n_tiles = (A.view_base && S > A.ld) ? 0 : (S + kTS - 1) / kTS;
 }
 
 __device__ __forceinline__ int tile_view(const MlpArgs& A, int64_t s0) {

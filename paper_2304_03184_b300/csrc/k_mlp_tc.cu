@@ -144,6 +144,7 @@ __device__ __forceinline__ void operands_ready() {
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_constant__ TcArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
+  if (A.view_base && (int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 8);
   const uint32_t mbar = tc::smem_u32(sm + OFF_MISC);

@@ -6,8 +6,8 @@
 //
 // One CTA = one warpgroup of 128 threads; per 128-sample tile (thread t = sample t):
 //   recompute  X -> H1 -> H2 -> O -> H4          (4 chained MMAs, M = 128, ReLU epilogues)
-//   adjoint    dZ -> dH4 -> dO -> dH2 -> dH1 -> dX (5 chained MMAs against transposed weights,
-//              ReLU masks read back from the stored activations)
+//   adjoint    dZ -> dH4 -> dO -> dH2 -> dH1 -> dX (5 chained MMAs; each reads the forward
+//              weight as an MN-major operand; ReLU masks read back from the stored activations)
 //   weights    dW5^T += H4^T dZ, dW4 += dH4^T O, dW3^T += H2^T dO, dW2 += dH2^T H1,
 //              dW1 += dH1^T X: M = 64 MMAs with K = the 128 samples, issued next to the
 //              chain and accumulated in tensor memory over every tile the CTA visits.
@@ -36,28 +36,27 @@ constexpr uint32_t C_DW4 = 160;     // 16
 constexpr uint32_t C_DW3T = 176;    // 16
 constexpr uint32_t C_DW5T = 192;    // 16
 
-// shared-memory plan (bytes); [n][k] = K-major operand with n rows and k columns
-constexpr uint32_t B_W1 = 0;                  // [64][32]  forward weights
-constexpr uint32_t B_W2 = B_W1 + 64 * 32 * 2; // [64][64]
-constexpr uint32_t B_W3 = B_W2 + 64 * 64 * 2; // [16][64]
-constexpr uint32_t B_W4 = B_W3 + 16 * 64 * 2; // [64][16]
-constexpr uint32_t B_W5T = B_W4 + 64 * 16 * 2;  // [64][16] transposed weights
-constexpr uint32_t B_W4T = B_W5T + 64 * 16 * 2; // [16][64]
-constexpr uint32_t B_W3T = B_W4T + 16 * 64 * 2; // [64][16]
-constexpr uint32_t B_W2T = B_W3T + 64 * 16 * 2; // [64][64]
-constexpr uint32_t B_W1T = B_W2T + 64 * 64 * 2; // [32][64]
-constexpr uint32_t B_X = B_W1T + 32 * 64 * 2;   // [128][32] activations and deltas
-constexpr uint32_t B_H1 = B_X + kTM * 32 * 2;   // [128][64]
+// shared-memory plan (bytes); [n][k] = K-major operand with n rows and k columns.  The
+// transposed products of the adjoint chain read the forward weights as MN-major operands,
+// and three buffers are reused once their last reader (an MMA that completed at an earlier
+// commit wait, or an epilogue) is done: H4 -> dH2, dZ -> dO, dH4 -> dH1.
+constexpr uint32_t B_W1 = 0;                   // [64][32] forward weights (W4p, W5p padded)
+constexpr uint32_t B_W2 = B_W1 + 64 * 32 * 2;  // [64][64]
+constexpr uint32_t B_W3 = B_W2 + 64 * 64 * 2;  // [16][64]
+constexpr uint32_t B_W4 = B_W3 + 16 * 64 * 2;  // [64][16]
+constexpr uint32_t B_W5 = B_W4 + 64 * 16 * 2;  // [16][64]
+constexpr uint32_t B_X = B_W5 + 16 * 64 * 2;   // [128][32] activations and deltas
+constexpr uint32_t B_H1 = B_X + kTM * 32 * 2;  // [128][64]
 constexpr uint32_t B_H2 = B_H1 + kTM * 64 * 2;
-constexpr uint32_t B_O = B_H2 + kTM * 64 * 2;   // [128][16]
-constexpr uint32_t B_H4 = B_O + kTM * 16 * 2;   // [128][64]
-constexpr uint32_t B_DZ = B_H4 + kTM * 64 * 2;  // [128][16]
-constexpr uint32_t B_DH4 = B_DZ + kTM * 16 * 2; // [128][64]
-constexpr uint32_t B_DO = B_DH4 + kTM * 64 * 2; // [128][16]
-constexpr uint32_t B_DH2 = B_DO + kTM * 16 * 2; // [128][64]
-constexpr uint32_t B_DH1 = B_DH2 + kTM * 64 * 2;
-constexpr uint32_t B_MISC = B_DH1 + kTM * 64 * 2;
-constexpr uint32_t kSmemB = B_MISC + 64 + 8192;  // + guard band
+constexpr uint32_t B_O = B_H2 + kTM * 64 * 2;    // [128][16]
+constexpr uint32_t B_H4 = B_O + kTM * 16 * 2;    // [128][64], later dH2
+constexpr uint32_t B_DZ = B_H4 + kTM * 64 * 2;   // [128][16], later dO
+constexpr uint32_t B_DH4 = B_DZ + kTM * 16 * 2;  // [128][64], later dH1
+constexpr uint32_t B_MISC = B_DH4 + kTM * 64 * 2;
+constexpr uint32_t B_DH2 = B_H4;
+constexpr uint32_t B_DO = B_DZ;
+constexpr uint32_t B_DH1 = B_DH4;
+constexpr uint32_t kSmemB = B_MISC + 64;         // 98 KB: two CTAs per SM
 
 struct TcBwdArgs {
   const float* feat;        // [in][ld] FP32 encoding features
@@ -90,20 +89,27 @@ template <bool BF16>
 __device__ void stage_bwd_weights(uint8_t* sm, const FieldDev& F) {
   const WOff off(F.mlp_in);
   const int in = F.mlp_in;
-  if (in == 16) {
+  if (in == 16)
     stage<BF16, false, 64, 16>(sm + B_W1, F.weights, off, in, 1);
-    stage<BF16, true, 16, 64>(sm + B_W1T, F.weights, off, in, 1);
-  } else {
+  else
     stage<BF16, false, 64, 32>(sm + B_W1, F.weights, off, in, 1);
-    stage<BF16, true, 32, 64>(sm + B_W1T, F.weights, off, in, 1);
-  }
   stage<BF16, false, 64, 64>(sm + B_W2, F.weights, off, in, 2);
   stage<BF16, false, 16, 64>(sm + B_W3, F.weights, off, in, 3);
   stage<BF16, false, 64, 16>(sm + B_W4, F.weights, off, in, 4);
-  stage<BF16, true, 64, 16>(sm + B_W5T, F.weights, off, in, 5);
-  stage<BF16, true, 16, 64>(sm + B_W4T, F.weights, off, in, 4);
-  stage<BF16, true, 64, 16>(sm + B_W3T, F.weights, off, in, 3);
-  stage<BF16, true, 64, 64>(sm + B_W2T, F.weights, off, in, 2);
+  stage<BF16, false, 16, 64>(sm + B_W5, F.weights, off, in, 5);
+}
+
+// One thread: adjoint-chain MMA D (128 x N) = dY (smem, 128 x K, K-major) * W, with W the
+// forward weight [K rows][N columns] (K-major in its own layout) read as an MN-major
+// operand: column groups 128 B apart, row groups N*16 B apart.
+__device__ __forceinline__ void issue_adjoint(uint32_t d_tmem, uint32_t a_saddr, uint32_t w_saddr, int K, int N,
+                                              bool bf16) {
+  const uint32_t idesc = tc::idesc_f16(kTM, N, bf16) | (1u << 16);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t ad = tc::smem_desc(a_saddr + kk * 256, 128, K * 16);
+    const uint64_t bd = tc::smem_desc(w_saddr + kk * 32 * N, N * 16, 128);
+    tc::mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+  }
 }
 
 // Read the M = 64 weight-gradient accumulators and add them to the field's gradient buffer.
@@ -150,8 +156,9 @@ __device__ __forceinline__ bool chain_wait(uint32_t mbar, uint32_t& phase) {
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_constant__ TcBwdArgs A) {
+__global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_constant__ TcBwdArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
+  if ((int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + B_MISC + 8);
   const uint32_t mbar = tc::smem_u32(sm + B_MISC);
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_consta
     // ---- dH4 = (dZ W5p) * [H4 > 0];  dW5p^T += H4^T dZ
     if (t == 0) {
       tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_DZ, sb + B_W5T, 16, 64, BF16);
+      issue_adjoint(tmem + C_CHAIN, sb + B_DZ, sb + B_W5, 16, 64, BF16);
       issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
       tc::commit_to(mbar);
     }
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_consta
     // ---- dO = dH4 W4p (o_0 slot carries dL/do_0);  dW4p += dH4^T O
     if (t == 0) {
       tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_DH4, sb + B_W4T, 64, 16, BF16);
+      issue_adjoint(tmem + C_CHAIN, sb + B_DH4, sb + B_W4, 64, 16, BF16);
       issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
       tc::commit_to(mbar);
     }
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_consta
     // ---- dH2 = (dO W3) * [H2 > 0];  dW3^T += H2^T dO
     if (t == 0) {
       tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_DO, sb + B_W3T, 16, 64, BF16);
+      issue_adjoint(tmem + C_CHAIN, sb + B_DO, sb + B_W3, 16, 64, BF16);
       issue_dw(tmem + C_DW3T, sb + B_H2, 64, sb + B_DO, 16, 16, dw_live, BF16);
       tc::commit_to(mbar);
     }
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_consta
     // ---- dH1 = (dH2 W2) * [H1 > 0];  dW2 += dH2^T H1
     if (t == 0) {
       tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_DH2, sb + B_W2T, 64, 64, BF16);
+      issue_adjoint(tmem + C_CHAIN, sb + B_DH2, sb + B_W2, 64, 64, BF16);
       issue_dw(tmem + C_DW2, sb + B_DH2, 64, sb + B_H1, 64, 64, dw_live, BF16);
       tc::commit_to(mbar);
     }
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_mlp_bwd_tc(const __grid_consta
     // ---- dX = dH1 W1;  dW1 += dH1^T X
     if (t == 0) {
       tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_DH1, sb + B_W1T, 64, in, BF16);
+      issue_adjoint(tmem + C_CHAIN, sb + B_DH1, sb + B_W1, 64, in, BF16);
       issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + B_X, in, in, dw_live, BF16);
       tc::commit_to(mbar);
     }
@@ -349,12 +356,12 @@ cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (plan_has_kind(P, kMlpBF16)) {
     cudaFuncSetAttribute(k_mlp_bwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB);
-    k_mlp_bwd_tc<true><<<num_sms, kThreadsB, kSmemB, s>>>(A);
+    k_mlp_bwd_tc<true><<<num_sms * 2, kThreadsB, kSmemB, s>>>(A);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) {
     cudaFuncSetAttribute(k_mlp_bwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB);
-    k_mlp_bwd_tc<false><<<num_sms, kThreadsB, kSmemB, s>>>(A);
+    k_mlp_bwd_tc<false><<<num_sms * 2, kThreadsB, kSmemB, s>>>(A);
     e = cudaGetLastError();
   }
   return e;

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_warp(const __grid_constant__ Plan P) {
 }
 
 cudaError_t launch_warp(const Plan& P, int num_sms, cudaStream_t s) {
-  k_warp<<<num_sms * 8, 256, 0, s>>>(P);
+  k_warp<<<num_sms * P.tune.warp_ctas_per_sm, 256, 0, s>>>(P);
   return cudaGetLastError();
 }
 

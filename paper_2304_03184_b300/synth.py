@@ -330,11 +330,11 @@ def two_field_render(seed: int = 2, width: int = 512, height: int = 512, n_sampl
 
 def train_step_workload(seed: int = 3, n_rays: int = 1 << 18, n_samples: int = 128,
                         image: int = 512, field_desc: FieldDesc = CFG2_FIELD,
-                        n_nodes: int = 2048) -> TrainWorkload:
+                        n_nodes: int = 2048, K: int = 4) -> TrainWorkload:
     """Human field of the two-field render, n_rays drawn from 4 ring cameras, Huber loss."""
     rng = np.random.default_rng(seed)
     field = make_field(rng, field_desc)
-    graph = make_graph(rng, n_nodes, K=4)
+    graph = make_graph(rng, n_nodes, K=K)
     all_rays = ring_rays(4, image, image, 50.0, 2.5)
     idx = np.sort(rng.choice(all_rays.n, size=n_rays, replace=False))
     idx = rng.permutation(idx)

@@ -1,0 +1,113 @@
+"""Batched key-frame training (several frames x both fields in one call), the CUDA-graph
+captured step, the launch-shape autotuner and the fixed-size workspace, on the GPU."""
+import numpy as np
+import pytest
+
+from paper_2304_03184_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(oracle):
+    import torch
+    from paper_2304_03184_b300 import build
+    build.build()
+    import paper_2304_03184_b300 as invr
+    assert torch.cuda.is_available()
+    return invr, oracle
+
+
+def cu(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make_batches(invr, ctx, tw, prec):
+    fields = {id(fp): invr.Field.from_synth(ctx, fp, prec) for fp in tw.fields}
+    keep, batches = [], []
+    for b in tw.batches:
+        g = None
+        if b.view.graph is not None:
+            sg = b.view.graph
+            g = invr.Graph(ctx, sg.x_canon.shape[1], sg.K, sg.radius, 1, cu(sg.x_canon))
+            g.set_pose(0, cu(sg.dq), cu(sg.x_live))
+        occ = cu(b.view.occupancy) if b.view.occupancy is not None else None
+        view = invr.View(fields[id(b.view.field)], g, 0, b.view.rigid_dq, occ)
+        keep.append((g, occ))
+        batches.append((cu(b.rays.o), cu(b.rays.d), view, cu(b.target)))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    return tb, fields, keep
+
+
+def test_graph_replay_matches_eager_steps(env):
+    """The captured step replays the same sequence: losses of successive replays equal
+    those of successive eager steps on an identical copy of the fields."""
+    invr, _ = env
+    tw = synth.keyframe_batch_workload(n_frames=3, log2_rays=(9.0, 11.0))
+    total = sum(b.rays.n for b in tw.batches)
+    ctx_e, ctx_g = invr.Context(0), invr.Context(0)
+    tb_e, f_e, k_e = make_batches(invr, ctx_e, tw, invr.INVR_MLP_BF16)
+    tb_g, f_g, k_g = make_batches(invr, ctx_g, tw, invr.INVR_MLP_BF16)
+    ctx_g.reserve(total, tw.n_samples)
+    eager = []
+    for _ in range(4):
+        eager.append(float(invr.train_step(ctx_e, tb_e).item()))
+    graph = invr.TrainGraph(ctx_g, tb_g, warmup=2)          # warm-up = two eager steps
+    replay = [float(graph.replay().item()) for _ in range(2)]
+    ctx_g.sync()
+    np.testing.assert_allclose(replay, eager[2:], rtol=1e-4)
+    assert eager[3] < eager[0]                              # training makes progress
+
+
+def test_autotune_keeps_parameters(env):
+    invr, _ = env
+    import torch
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    ctx = invr.Context(0)
+    tb, fields, keep = make_batches(invr, ctx, tw, invr.INVR_MLP_BF16)
+    before = [f.get_params()[:2] for f in fields.values()]
+    tune = ctx.autotune(tb)
+    assert tune["warp_ctas_per_sm"] in (4, 8, 16) and tune["encode_ctas_per_sm"] in (1, 2, 4, 8)
+    assert tune["encode_bwd_ctas_per_sm"] in (1, 2, 4, 8) and tune["agg_res"] in (0, 64, 256, 1024)
+    for f, (t0, w0) in zip(fields.values(), before):
+        t1, w1, _, _, step = f.get_params()
+        assert step == 0 and torch.equal(t0, t1) and torch.equal(w0, w1)
+        gt, gw = f.get_grads()
+        assert float(gt.abs().max()) == 0.0 and float(gw.abs().max()) == 0.0
+    ctx.sync()
+
+
+def test_reserved_workspace_overflow_is_reported(env):
+    """A workspace reserved for fewer occupied samples than a call produces: the scan flags
+    it, every sample kernel skips its work, and invr_ctx_sync reports INVR_E_STATE."""
+    invr, _ = env
+    w = synth.plain_forward(res=32, n_samples=64)          # no occupancy: ~64 samples per ray
+    ctx = invr.Context(0)
+    ctx.reserve(w.rays.n, 1)
+    sv = w.views[0]
+    f = invr.Field.from_synth(ctx, sv.field)
+    g = invr.Graph(ctx, sv.graph.x_canon.shape[1], sv.graph.K, sv.graph.radius, 1, cu(sv.graph.x_canon))
+    g.set_pose(0, cu(sv.graph.dq), cu(sv.graph.x_live))
+    invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [invr.View(f, g)])
+    with pytest.raises(invr.InvrError, match="overflow"):
+        ctx.sync()
+    # more rays than reserved is an argument error
+    big = synth.plain_forward(res=40, n_samples=4)
+    with pytest.raises(invr.InvrError):
+        invr.render_rays(ctx, cu(big.rays.o), cu(big.rays.d), 4, 1e-4, [invr.View(f, g)])
+    ctx.sync()
+
+
+def test_keyframe_batch_matches_oracle_loss(env):
+    """The batched call (frames x fields, uneven ray counts) gives the oracle's loss."""
+    invr, oracle = env
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(7.0, 9.0))
+    ctx = invr.Context(0)
+    tb, fields, keep = make_batches(invr, ctx, tw, invr.INVR_FP32)
+    loss = float(invr.forward_train(ctx, tb).item())
+    ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
+    ob = [oracle.TrainBatch(b.rays.o, b.rays.d, oracle.View.from_synth(b.view, field=ofields[id(b.view.field)]),
+                            b.target) for b in tw.batches]
+    oloss, _ = oracle.train_loss_grad(ob, tw.n_samples, tw.t_eps, tw.huber_delta, grads=False)
+    assert abs(loss - oloss) <= 1e-5 * oloss
