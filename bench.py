@@ -164,6 +164,20 @@ def fp32_alu_peak(sm_mhz):
 PRECS = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
+def aggregate_replicas(ms_local: float, samples_local: float, world: int):
+    """Whole-job throughput of independent replicas: every rank's samples over the slowest
+    rank's time (max over ranks of the per-step milliseconds).  Returns (value, max_ms)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * samples_local / (ms * 1e-3), ms
+
+
 def time_train(invr, ctx, tb, steps, warmup, flush, world):
     """Per-step CUDA-event times (L2 flushed between steps) and the per-kernel breakdown."""
     import torch
@@ -188,10 +202,7 @@ def time_train(invr, ctx, tb, steps, warmup, flush, world):
     ctx.enable_timing(False)
     ctx.sync()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    _, ms = aggregate_replicas(ms, 1.0, world)
     return ms, ktime
 
 
@@ -314,7 +325,8 @@ def run_ours(args, rank, world, local):
         out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks)
         nsteps = max(5, args.steps // 4)
         out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
-        out["gpu_launches"] = int(round(sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in bt["ktime"].items())
+        per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
+        out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
                                         / nsteps * args.steps))
         out["variants"] = {args.prec + "_graph": {"value": round(bvalue, 1), "ms_per_step": round(bt["ms"], 3)},
                            args.prec + "_eager": {"value": round(world * bt["S_nom"] / (bt["eager_ms"] * 1e-3), 1),
@@ -370,10 +382,7 @@ def bench_batched(invr, args, flush, world, prec_name):
     if world > 1:
         torch.distributed.barrier()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    _, ms = aggregate_replicas(ms, 1.0, world)
     ctx.sync()
 
     # end to end: copy every batch's rays and targets from pinned host memory, replay, read the loss

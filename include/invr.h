@@ -69,9 +69,10 @@ invr_status invr_ctx_destroy(invr_ctx ctx);
  * invr_ctx_sync return INVR_E_STATE. */
 invr_status invr_ctx_reserve(invr_ctx ctx, int64_t max_rays, int max_samples);
 
-/* Wait for `stream`, then read and clear the device status word: INVR_E_NONFINITE if a
- * kernel flagged a non-finite output since the last sync, INVR_E_TIMEOUT if a bounded
- * wait gave up, else INVR_OK. */
+/* Wait for `stream`, then read and clear the device status word, reporting the first of:
+ * INVR_E_TIMEOUT if a bounded device wait gave up, INVR_E_STATE if a call's occupied samples
+ * overflowed a reserved workspace, INVR_E_NONFINITE if a kernel flagged a non-finite output
+ * since the last sync; else INVR_OK. */
 invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around every kernel
@@ -222,6 +223,11 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* args, invr_st
 /* The context's launch shapes: out4 = {warp CTAs/SM, encode CTAs/SM, scatter CTAs/SM,
  * aggregation resolution}. */
 invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4);
+/* Polls of each bounded device-side wait (the tensor-core kernels' mbarrier waits) before
+ * the kernel gives up, records INVR_E_TIMEOUT in the status word, lets its in-flight work
+ * finish, frees its tensor memory and returns.  Default 2^22 (a few seconds).  0 makes every
+ * such wait give up at once, which exercises the failure path without a fault. */
+invr_status invr_ctx_set_wait_limit(invr_ctx ctx, uint32_t polls);
 
 /* ------------------------------------------------------------------ single steps */
 /* Samples of n_rays rays as the renderer takes them: count_dev [R] occupied samples per

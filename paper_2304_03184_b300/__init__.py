@@ -85,6 +85,7 @@ _SIGNATURES = {
     "invr_ctx_autotune": [_VP, C.POINTER(invr_train_args), _VP],
     "invr_ctx_get_tune": [_VP, C.POINTER(C.c_int)],
     "invr_field_copy_params": [_VP, _VP, _VP],
+    "invr_ctx_set_wait_limit": [_VP, C.c_uint32],
 }
 
 _lib_handle = None
@@ -161,6 +162,10 @@ class Context:
         """Pick the launch shapes for this workload (times forward + backward candidates)."""
         _check(lib().invr_ctx_autotune(self.h, C.byref(tb.args), _stream()), self.h)
         return self.tune()
+
+    def set_wait_limit(self, polls: int):
+        """Polls per bounded device wait (0: every wait gives up at once; default 2^22)."""
+        _check(lib().invr_ctx_set_wait_limit(self.h, polls), self.h)
 
     def tune(self):
         out = (C.c_int * 4)()

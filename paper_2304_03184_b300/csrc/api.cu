@@ -20,6 +20,7 @@ struct invr_ctx_s {
   bool cap_train = false;
   bool cap_fixed = false;   // set by invr_ctx_reserve: never grow, overflow is flagged on device
   Tune tune;
+  uint32_t wait_limit = kDefaultWaitLimit;
   unsigned* status = nullptr;
   std::string err;
   // per-kernel event timing (invr_ctx_enable_timing)
@@ -283,6 +284,9 @@ invr_status build_plan(invr_ctx ctx, const std::vector<const invr_render_args*>&
   if (nv < 1 || nv > kMaxViews) return fail(ctx, INVR_E_ARG, "1..16 views/batches per call");
   if (n_samples < 1 || n_samples > 1024) return fail(ctx, INVR_E_ARG, "n_samples must be in [1, 1024]");
   P.n_views = nv;
+  P.view_lo = 0;
+  P.view_hi = nv;
+  P.wait_limit = ctx->wait_limit;
   P.n_samples = n_samples;
   P.t_eps = t_eps;
   P.tune = ctx->tune;
@@ -322,7 +326,7 @@ cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
   if ((e = TIMED(ctx, "scan", s, launch_scan(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "march_emit", s, launch_march_emit(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "warp", s, launch_warp(P, ctx->num_sms, s))) != cudaSuccess) return e;
-  if ((e = TIMED(ctx, "encode", s, launch_encode(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  if ((e = TIMED(ctx, "encode", s, launch_encode_by_field(P, ctx->num_sms, s))) != cudaSuccess) return e;
   if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
     return e;
   if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
@@ -368,19 +372,34 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
     const invr_render_args& r = a->batches[b];
     if (r.n_views != 1 || !r.views) return fail(ctx, INVR_E_ARG, "each training batch has exactly one view");
     if (r.n_samples != ns || r.t_eps != te) return fail(ctx, INVR_E_ARG, "batches must share n_samples and t_eps");
-    rays.push_back(&r);
-    views.push_back(&r.views[0]);
+  }
+  // Batches of the same field are laid out next to each other (stable order), so that the
+  // per-field launches of the encoding and the gradient scatter each keep one field's
+  // tables and gradients in L2.
+  std::vector<int> order;
+  std::vector<invr_field> seen;
+  for (int b = 0; b < a->n_batches; ++b) {
+    invr_field f = a->batches[b].views[0].field;
+    if (std::find(seen.begin(), seen.end(), f) == seen.end()) seen.push_back(f);
+  }
+  for (invr_field f : seen)
+    for (int b = 0; b < a->n_batches; ++b)
+      if (a->batches[b].views[0].field == f) order.push_back(b);
+  std::vector<int64_t> target_off(a->n_batches, 0);
+  for (int b = 1; b < a->n_batches; ++b) target_off[b] = target_off[b - 1] + a->batches[b - 1].n_rays;
+  for (int b : order) {
+    rays.push_back(&a->batches[b]);
+    views.push_back(&a->batches[b].views[0]);
   }
   Plan P;
   invr_status st = build_plan(ctx, rays, views, ns, te, P);
   if (st != INVR_OK) return st;
   if (P.total_rays == 0) return fail(ctx, INVR_E_ARG, "training call without rays");
-  int64_t off = 0;
-  for (int b = 0; b < a->n_batches; ++b) {
-    P.v[b].target = a->targets_dev + 3 * off;
-    P.v[b].rgba_out = a->batches[b].rgba_dev;
-    P.v[b].depth_out = a->batches[b].depth_dev;
-    off += a->batches[b].n_rays;
+  for (int i = 0; i < a->n_batches; ++i) {
+    const int b = order[i];
+    P.v[i].target = a->targets_dev + 3 * target_off[b];
+    P.v[i].rgba_out = a->batches[b].rgba_dev;
+    P.v[i].depth_out = a->batches[b].depth_dev;
   }
   P.loss_norm = (float)(1.0 / (3.0 * (double)P.total_rays));
   P.huber_delta = a->huber_delta;
@@ -404,7 +423,7 @@ invr_status train_backward(invr_ctx ctx, const invr_train_args* a, float scale, 
   if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
     INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd_tc", s, launch_mlp_bwd_tc(P, ctx->num_sms, s)));
   P.grad_scale = 1.0f;  // dL/dfeat already carries the scale
-  INVR_CUDA(ctx, TIMED(ctx, "encode_bwd", s, launch_encode_bwd(P, ctx->num_sms, s)));
+  INVR_CUDA(ctx, TIMED(ctx, "encode_bwd", s, launch_encode_bwd_by_field(P, ctx->num_sms, s)));
   return INVR_OK;
 }
 
@@ -539,6 +558,12 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
   return INVR_OK;
 }
 
+invr_status invr_ctx_set_wait_limit(invr_ctx ctx, uint32_t polls) {
+  if (!ctx) return INVR_E_ARG;
+  ctx->wait_limit = polls;
+  return INVR_OK;
+}
+
 invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4) {
   if (!ctx || !out4) return INVR_E_ARG;
   out4[0] = ctx->tune.warp_ctas_per_sm;
@@ -556,9 +581,10 @@ invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream) {
   unsigned st = 0;
   INVR_CUDA(ctx, cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
   INVR_CUDA(ctx, cudaMemset(ctx->status, 0, sizeof(unsigned)));
-  if (st & kStatusNonFinite) return fail(ctx, INVR_E_NONFINITE, "a kernel produced a non-finite output");
+  // root causes first: a timed-out or skipped stage leaves later stages reading stale values
   if (st & kStatusTimeout) return fail(ctx, INVR_E_TIMEOUT, "a bounded device wait gave up");
   if (st & kStatusOverflow) return fail(ctx, INVR_E_STATE, "sample workspace overflow");
+  if (st & kStatusNonFinite) return fail(ctx, INVR_E_NONFINITE, "a kernel produced a non-finite output");
   return INVR_OK;
 }
 
@@ -871,7 +897,7 @@ invr_status invr_mlp_points(invr_ctx ctx, invr_field f, int64_t n, const float* 
   if (F.mlp_kind == kMlpF32)
     INVR_CUDA(ctx, launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s));
   else
-    INVR_CUDA(ctx, launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->num_sms, s));
+    INVR_CUDA(ctx, launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->wait_limit, ctx->num_sms, s));
   return INVR_OK;
 }
 
@@ -895,7 +921,7 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
   if (e == cudaSuccess) e = launch_encode_points(F, n, vc, feat, nullptr, s);
   if (e == cudaSuccess)
     e = F.mlp_kind == kMlpF32 ? launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s)
-                              : launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->num_sms, s);
+                              : launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->wait_limit, ctx->num_sms, s);
   cudaFreeAsync(vc, s);
   cudaFreeAsync(feat, s);
   INVR_CUDA(ctx, e);
@@ -908,7 +934,7 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
 namespace invr {
 
 invr_status resolve_point_query(invr_ctx ctx, const invr_field_view* view, WarpDev& W, FieldDev& F, int& device,
-                                int& num_sms) {
+                                int& num_sms, unsigned*& status, uint32_t& wait_limit) {
   if (!ctx || !view) return INVR_E_ARG;
   invr_status st = check_field(ctx, view->field);
   if (st != INVR_OK) return st;
@@ -917,6 +943,8 @@ invr_status resolve_point_query(invr_ctx ctx, const invr_field_view* view, WarpD
   F = field_dev(view->field);
   device = ctx->device;
   num_sms = ctx->num_sms;
+  status = ctx->status;
+  wait_limit = ctx->wait_limit;
   return INVR_OK;
 }
 

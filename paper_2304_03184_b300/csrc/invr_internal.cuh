@@ -105,6 +105,8 @@ struct Plan {
   float huber_delta;
   float grad_scale;
   int agg_res;              // levels with N_l <= agg_res aggregate gradient runs per warp
+  int view_lo, view_hi;     // views processed by the per-field launches ([0, n_views) by default)
+  uint32_t wait_limit;      // polls per bounded device wait
   Tune tune;                // launch shapes (autotuned per context)
   Workspace ws;
   unsigned* status;         // device status word
@@ -216,13 +218,16 @@ cudaError_t launch_march_emit(const Plan& P, cudaStream_t s);
 cudaError_t launch_warp(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_encode_by_field(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_encode_bwd_by_field(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 bool plan_has_kind(const Plan& P, int kind);
 cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
-                                 int num_sms, cudaStream_t s);
+                                 uint32_t wait_limit, int num_sms, cudaStream_t s);
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // polls of try_wait: a few seconds
 cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s);
 cudaError_t launch_composite_train(const Plan& P, float* loss, cudaStream_t s);
 cudaError_t launch_adam(float* params, const float* grads_in, float* grads_zero, float* m, float* v, int64_t n,

@@ -41,8 +41,20 @@ __device__ __forceinline__ void level_corners(const FieldDev& F, int l, float3 x
 __device__ __forceinline__ float2 level_feature(const FieldDev& F, int l, const Corners& c) {
   const float2* tab = reinterpret_cast<const float2*>(F.tables) + ((size_t)l << F.log2T);
   float2 e[8];
+  // the two corners that differ in x share one 16-byte load when their slots are an
+  // aligned adjacent pair
 #pragma unroll
-  for (int k = 0; k < 8; ++k) e[k] = __ldg(tab + c.idx[k]);
+  for (int k = 0; k < 8; k += 2) {
+    const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
+    if (i1 == i0 + 1u && !(i0 & 1u)) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(tab + i0));
+      e[k] = make_float2(q.x, q.y);
+      e[k + 1] = make_float2(q.z, q.w);
+    } else {
+      e[k] = __ldg(tab + i0);
+      e[k + 1] = __ldg(tab + i1);
+    }
+  }
   float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -55,12 +67,12 @@ __device__ __forceinline__ float2 level_feature(const FieldDev& F, int l, const 
 __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) {
   const int l = blockIdx.y;
   const int64_t S_cap = P.ws.S_cap;
-  const int64_t S = P.ws.view_base[P.n_views];
-  if (S > S_cap) return;
+  if (P.ws.view_base[P.n_views] > S_cap) return;
+  const int64_t S0 = P.ws.view_base[P.view_lo], S = P.ws.view_base[P.view_hi];
   float* feat = static_cast<float*>(P.ws.feat);
-  int v = 0;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    while (v + 1 < P.n_views && s >= P.ws.view_base[v + 1]) ++v;
+  int v = P.view_lo;
+  for (int64_t s = S0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    while (v + 1 < P.view_hi && s >= P.ws.view_base[v + 1]) ++v;
     const FieldDev& F = P.v[v].field;
     if (l >= F.L) continue;
     float2 f = make_float2(0.0f, 0.0f);
@@ -77,39 +89,59 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) 
 // Warp-aggregated scatter: lanes hold consecutive samples, mostly of one ray, so lanes
 // hitting the same slot form contiguous runs on coarse levels.  A segmented inclusive
 // scan sums each run; the run's last lane issues one atomic for the whole run.  Lanes
-// with nothing to add carry a key no neighbour can share.
+// with nothing to add are run heads that issue nothing.  When no lane continues a run the
+// scan is skipped.
 __device__ __forceinline__ void scatter_runs(float2* table, uint32_t key, bool live, float2 val) {
   const int lane = threadIdx.x & 31;
   const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
   const bool head = !live || lane == 0 || prev != key;
   const unsigned heads = __ballot_sync(0xffffffffu, head);
-  const unsigned livem = __ballot_sync(0xffffffffu, live);
-  const int run_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  if (heads != 0xffffffffu) {
+    const int run_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float x = __shfl_up_sync(0xffffffffu, val.x, o);
-    const float y = __shfl_up_sync(0xffffffffu, val.y, o);
-    if (lane - o >= run_start) {
-      val.x += x;
-      val.y += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const float x = __shfl_up_sync(0xffffffffu, val.x, o);
+      const float y = __shfl_up_sync(0xffffffffu, val.y, o);
+      if (lane - o >= run_start) {
+        val.x += x;
+        val.y += y;
+      }
     }
   }
-  const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) || !((livem >> (lane + 1)) & 1u);
+  const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
   if (live && tail) atomicAdd(table + key, val);
+}
+
+// Scatter of one sample-level without run summation: the two corners of a cell that differ
+// in x go out as one 16-byte atomic when their slots are an aligned adjacent pair (dense
+// rows, or a hashed slot with x even), else as two 8-byte atomics.
+__device__ __forceinline__ void scatter_pairs(float2* table, const Corners& c, float2 g) {
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) {
+    const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
+    const float2 v0 = make_float2(c.w[k] * g.x, c.w[k] * g.y);
+    const float2 v1 = make_float2(c.w[k + 1] * g.x, c.w[k + 1] * g.y);
+    if (i1 == i0 + 1u && !(i0 & 1u)) {
+      atomicAdd(reinterpret_cast<float4*>(table + i0), make_float4(v0.x, v0.y, v1.x, v1.y));
+    } else {
+      atomicAdd(table + i0, v0);
+      atomicAdd(table + i1, v1);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan P) {
   const int l = blockIdx.y;
   const int64_t S_cap = P.ws.S_cap;
-  const int64_t S = P.ws.view_base[P.n_views];
-  if (S > S_cap) return;
+  if (P.ws.view_base[P.n_views] > S_cap) return;
+  const int64_t S0 = P.ws.view_base[P.view_lo], S = P.ws.view_base[P.view_hi];
   const float scale = P.grad_scale;
-  int v = 0;
-  // warps never straddle two views: view ranges are kTile-aligned and blockDim divides kTile * 2
-  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x; s0 < S; s0 += (int64_t)gridDim.x * blockDim.x) {
+  int v = P.view_lo;
+  // warps never straddle two views: view ranges are kTile-aligned (S0 too) and a warp is 32
+  for (int64_t s0 = S0 + (int64_t)blockIdx.x * blockDim.x; s0 < S; s0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = s0 + threadIdx.x;
     const int64_t sw = s0 + (threadIdx.x & ~31);
-    while (v + 1 < P.n_views && sw >= P.ws.view_base[v + 1]) ++v;
+    while (v + 1 < P.view_hi && sw >= P.ws.view_base[v + 1]) ++v;
     const FieldDev& F = P.v[v].field;
     if (l >= F.L || sw >= S) continue;  // warp-uniform
     bool live = s < S && P.ws.s_ray[s] >= 0;
@@ -135,8 +167,7 @@ __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan
       for (int k = 0; k < 8; ++k)
         scatter_runs(gt, c.idx[k], live, make_float2(c.w[k] * g.x, c.w[k] * g.y));
     } else if (live) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) atomicAdd(gt + c.idx[k], make_float2(c.w[k] * g.x, c.w[k] * g.y));
+      scatter_pairs(gt, c, g);
     }
   }
 }
@@ -155,6 +186,31 @@ cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s) {
   dim3 grid(num_sms * P.tune.encode_bwd_ctas_per_sm, L);
   k_encode_bwd<<<grid, 256, 0, s>>>(P);
   return cudaGetLastError();
+}
+
+// One launch per group of consecutive views that share a field.
+template <class Launch>
+cudaError_t per_field(const Plan& P, Launch launch) {
+  Plan Q = P;
+  int lo = 0;
+  while (lo < P.n_views) {
+    int hi = lo + 1;
+    while (hi < P.n_views && P.v[hi].field.tables == P.v[lo].field.tables) ++hi;
+    Q.view_lo = lo;
+    Q.view_hi = hi;
+    const cudaError_t e = launch(Q);
+    if (e != cudaSuccess) return e;
+    lo = hi;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_encode_by_field(const Plan& P, int num_sms, cudaStream_t s) {
+  return per_field(P, [&](const Plan& Q) { return launch_encode(Q, num_sms, s); });
+}
+
+cudaError_t launch_encode_bwd_by_field(const Plan& P, int num_sms, cudaStream_t s) {
+  return per_field(P, [&](const Plan& Q) { return launch_encode_bwd(Q, num_sms, s); });
 }
 
 // ------------------------------------------------------------------ single step

@@ -49,6 +49,7 @@ struct TcArgs {
   int64_t ld;
   int64_t n;                // samples when view_base is null
   int n_views;
+  uint32_t wait_limit;      // polls per bounded wait (0: give up at once)
   unsigned* status;
   FieldDev f[kMaxViews];
 };
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
       issue_layer(tmem + 0, sbase + OFF_X, sbase + OFF_W1, in, 64, BF16);
       tc::commit_to(mbar);
     }
-    ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(mbar, phase, A.wait_limit);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
       issue_layer(tmem + 64, sbase + OFF_H1, sbase + OFF_W2, 64, 64, BF16);
       tc::commit_to(mbar);
     }
-    ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(mbar, phase, A.wait_limit);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
       issue_layer(tmem + 0, sbase + OFF_H2, sbase + OFF_W3, 64, 16, BF16);
       tc::commit_to(mbar);
     }
-    ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(mbar, phase, A.wait_limit);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
       issue_layer(tmem + 64, sbase + OFF_O, sbase + OFF_W4, 16, 64, BF16);
       tc::commit_to(mbar);
     }
-    ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(mbar, phase, A.wait_limit);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
       issue_layer(tmem + 16, sbase + OFF_H1, sbase + OFF_W5, 64, 16, BF16);
       tc::commit_to(mbar);
     }
-    ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(mbar, phase, A.wait_limit);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
@@ -273,7 +274,12 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
     tc::fence_before_sync();
     __syncthreads();  // every thread is done with this tile's TMEM and operands
   }
-  if (!ok && t == 0) atomicOr(A.status, kStatusTimeout);
+  if (!ok) {
+    // a wait gave up: record it, then let the pending MMAs finish (bounded) before the
+    // tensor memory they write is freed
+    if (t == 0) atomicOr(A.status, kStatusTimeout);
+    tc::mbar_wait(mbar, phase ^ 1u, kWaitLimit);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -304,6 +310,7 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   A.view_base = P.ws.view_base;
   A.ld = P.ws.S_cap;
   A.n_views = P.n_views;
+  A.wait_limit = P.wait_limit;
   A.status = P.status;
   for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
   cudaError_t e = cudaSuccess;
@@ -313,8 +320,9 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
 }
 
 cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
-                                 int num_sms, cudaStream_t s) {
+                                 uint32_t wait_limit, int num_sms, cudaStream_t s) {
   TcArgs A{};
+  A.wait_limit = wait_limit;
   A.feat = feat;
   A.out = out;
   A.ld = n;

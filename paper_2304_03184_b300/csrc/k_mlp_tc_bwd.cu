@@ -68,6 +68,7 @@ struct TcBwdArgs {
   int n_views;
   float in_scale;           // applied to dL/d(outputs) before rounding to 16 bit
   float out_scale;          // applied to dX and dW (FP32) on the way out
+  uint32_t wait_limit;      // polls per bounded wait (0: give up at once)
   unsigned* status;
   FieldDev f[kMaxViews];
 };
@@ -147,8 +148,8 @@ __device__ void flush_dw(uint32_t tmem, const FieldDev& F, float scale) {
     for (int j = 0; j < 3; ++j) atomicAdd(G + off.w5 + j * kColHidden + row, v[j] * scale);
 }
 
-__device__ __forceinline__ bool chain_wait(uint32_t mbar, uint32_t& phase) {
-  bool ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+__device__ __forceinline__ bool chain_wait(uint32_t mbar, uint32_t& phase, uint32_t limit) {
+  bool ok = tc::mbar_wait(mbar, phase, limit);
   phase ^= 1u;
   ok = __syncthreads_and(ok);
   tc::fence_after_sync();
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     if (cur < 0 || F.weights != A.f[cur].weights) {
       if (dw_live) {
         if (t == 0) tc::commit_to(mbar);
-        if (!(ok = chain_wait(mbar, phase))) break;
+        if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
         flush_dw(tmem, A.f[cur], A.out_scale);
         tc::fence_before_sync();
         __syncthreads();
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_chain(tmem + C_CHAIN, sb + B_X, sb + B_W1, in, 64, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H1, nullptr, t);
     operands_ready();
     // ---- H2
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_chain(tmem + C_CHAIN, sb + B_H1, sb + B_W2, 64, 64, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H2, nullptr, t);
     operands_ready();
     // ---- O = (0, o_1..o_15)
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_chain(tmem + C_CHAIN, sb + B_H2, sb + B_W3, 64, 16, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     {
       float o[16];
       tc::tmem_ld16(row_t + C_CHAIN, o);
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_chain(tmem + C_CHAIN, sb + B_O, sb + B_W4, 16, 64, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H4, nullptr, t);
     operands_ready();
     // ---- dH4 = (dZ W5p) * [H4 > 0];  dW5p^T += H4^T dZ
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH4, sm + B_H4, t);
     operands_ready();
     // ---- dO = dH4 W4p (o_0 slot carries dL/do_0);  dW4p += dH4^T O
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     {
       float d[16];
       tc::tmem_ld16(row_t + C_CHAIN, d);
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_dw(tmem + C_DW3T, sb + B_H2, 64, sb + B_DO, 16, 16, dw_live, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH2, sm + B_H2, t);
     operands_ready();
     // ---- dH1 = (dH2 W2) * [H1 > 0];  dW2 += dH2^T H1
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_dw(tmem + C_DW2, sb + B_DH2, 64, sb + B_H1, 64, 64, dw_live, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH1, sm + B_H1, t);
     operands_ready();
     // ---- dX = dH1 W1;  dW1 += dH1^T X
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + B_X, in, in, dw_live, BF16);
       tc::commit_to(mbar);
     }
-    if (!(ok = chain_wait(mbar, phase))) break;
+    if (!(ok = chain_wait(mbar, phase, A.wait_limit))) break;
     dw_live = true;
     for (int c = 0; c < in / 16; ++c) {
       float d[16];
@@ -328,7 +329,12 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     tc::fence_after_sync();
     flush_dw(tmem, A.f[cur], A.out_scale);  // every MMA completed at the last chain wait
   }
-  if (!ok && t == 0) atomicOr(A.status, kStatusTimeout);
+  if (!ok) {
+    // a wait gave up: record it, then let the pending MMAs finish (bounded) before the
+    // tensor memory they write is freed
+    if (t == 0) atomicOr(A.status, kStatusTimeout);
+    tc::mbar_wait(mbar, phase ^ 1u, kWaitLimit);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -351,6 +357,7 @@ cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   // dL/dout carries the loss's 1 / (3 R); take it out of the 16-bit operands
   A.in_scale = P.grad_scale / P.loss_norm;
   A.out_scale = P.loss_norm;
+  A.wait_limit = P.wait_limit;
   A.status = P.status;
   for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
   cudaError_t e = cudaSuccess;

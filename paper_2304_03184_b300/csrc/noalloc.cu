@@ -9,7 +9,7 @@
 
 namespace invr {
 invr_status resolve_point_query(invr_ctx ctx, const invr_field_view* view, WarpDev& W, FieldDev& F, int& device,
-                                int& num_sms);
+                                int& num_sms, unsigned*& status, uint32_t& wait_limit);
 invr_status record_error(invr_ctx ctx, invr_status st, const char* msg);
 }  // namespace invr
 
@@ -53,7 +53,9 @@ extern "C" invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_
   WarpDev W;
   FieldDev F;
   int dev = 0, sms = 0;
-  invr_status st = resolve_point_query(ctx, view, W, F, dev, sms);
+  unsigned* status = nullptr;
+  uint32_t wait_limit = 0;
+  invr_status st = resolve_point_query(ctx, view, W, F, dev, sms, status, wait_limit);
   if (st != INVR_OK) return st;
   if (n == 0) return INVR_OK;
   if (!p || !out) return record_error(ctx, INVR_E_ARG, "null pointer");
@@ -68,7 +70,9 @@ extern "C" invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_
     float* feat = scratch + 3 * n;    // [mlp_in][n]
     e = launch_warp_points(W, n, p, vc, nullptr, s);
     if (e == cudaSuccess) e = launch_encode_points(F, n, vc, feat, nullptr, s);
-    if (e == cudaSuccess) e = launch_mlp_points_f32(F, n, feat, out, sms, s);
+    if (e == cudaSuccess)
+      e = F.mlp_kind == kMlpF32 ? launch_mlp_points_f32(F, n, feat, out, sms, s)
+                                : launch_mlp_points_tc(F, n, feat, out, status, wait_limit, sms, s);
   }
   if (prev >= 0 && prev != dev) cudaSetDevice(prev);
   if (e != cudaSuccess) return record_error(ctx, INVR_E_CUDA, cudaGetErrorString(e));

@@ -111,3 +111,35 @@ def test_keyframe_batch_matches_oracle_loss(env):
                             b.target) for b in tw.batches]
     oloss, _ = oracle.train_loss_grad(ob, tw.n_samples, tw.t_eps, tw.huber_delta, grads=False)
     assert abs(loss - oloss) <= 1e-5 * oloss
+
+
+def test_device_wait_timeout_reported_and_recovered(env):
+    """Bounded waits giving up (wait limit 0) are reported as INVR_E_TIMEOUT by the next
+    sync, with no fault; afterwards the same context renders and trains correctly."""
+    invr, oracle = env
+    ctx = invr.Context(0)
+    w = synth.plain_forward(res=16, n_samples=32)
+    sv = w.views[0]
+    f = invr.Field.from_synth(ctx, sv.field, invr.INVR_MLP_BF16)
+    g = invr.Graph(ctx, sv.graph.x_canon.shape[1], sv.graph.K, sv.graph.radius, 1, cu(sv.graph.x_canon))
+    g.set_pose(0, cu(sv.graph.dq), cu(sv.graph.x_live))
+    view = invr.View(f, g)
+    o, d = cu(w.rays.o), cu(w.rays.d)
+    tgt = cu(synth.target_colours(np.random.default_rng(0), w.rays))
+    tb = invr.TrainBatches([(o, d, view, tgt)], w.n_samples, w.t_eps)
+    ctx.set_wait_limit(0)
+    invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, [view])          # forward tensor-core kernel
+    with pytest.raises(invr.InvrError, match="TIMEOUT"):
+        ctx.sync()
+    invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)                                               # backward tensor-core kernel
+    with pytest.raises(invr.InvrError, match="TIMEOUT"):
+        ctx.sync()
+    ctx.set_wait_limit(1 << 22)
+    f.zero_grads()
+    rgba, _ = invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, [view])
+    ctx.sync()
+    ref = oracle.render(w.rays.o, w.rays.d, w.n_samples, w.t_eps, [oracle.View.from_synth(sv)])
+    np.testing.assert_allclose(rgba.cpu().numpy(), ref.rgba, atol=2e-3)
+    invr.train_step(ctx, tb)
+    ctx.sync()

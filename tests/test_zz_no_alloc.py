@@ -54,6 +54,22 @@ def test_noalloc_query_matches_allocating_query(ctx_env):
         np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=0, atol=COLOUR_TOL)
 
 
+def test_noalloc_query_mixed_precision_field(ctx_env):
+    """A field with a 16-bit MLP goes through the tensor-core MLP in both entry points."""
+    invr, ctx = ctx_env
+    rng = np.random.default_rng(42)
+    fp = synth.make_field(rng, synth.CFG1_FIELD)
+    f = invr.Field.from_synth(ctx, fp, invr.INVR_MLP_BF16)
+    dq, _, _ = synth.make_object_pose(rng)
+    view = invr.View(f, rigid_dq=dq)
+    p = _cu(rng.uniform(-1, 1, size=(3, 3000)).astype(np.float32))
+    want = invr.query_points(ctx, view, p)
+    got = invr.query_points_noalloc(ctx, view, p)
+    ctx.sync()
+    assert np.isfinite(want.cpu().numpy()).all()
+    np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=0, atol=COLOUR_TOL)
+
+
 def test_noalloc_query_rejects_oversize(ctx_env):
     invr, ctx = ctx_env
     rng = np.random.default_rng(41)
