@@ -14,55 +14,9 @@
 //
 // Bound: L2 (tables up to 64 MiB per field stay L2-resident) -- 8 x 8 B gathers per
 // sample-level forward, 8 x 8 B atomics backward.
-#include "invr_internal.cuh"
+#include "hash_grid.cuh"
 
 namespace invr {
-
-struct Corners {
-  uint32_t idx[8];
-  float w[8];
-};
-
-__device__ __forceinline__ void level_corners(const FieldDev& F, int l, float3 x, Corners& c) {
-  const int res = F.res[l];
-  const bool dense = (F.dense_mask >> l) & 1u;
-  const uint32_t tmask = (1u << F.log2T) - 1u;
-  float fx, fy, fz;
-  const int cx = level_cell(x.x, res, fx), cy = level_cell(x.y, res, fy), cz = level_cell(x.z, res, fz);
-  const float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int bx = k & 1, by = (k >> 1) & 1, bz = (k >> 2) & 1;
-    c.idx[k] = vertex_index((uint32_t)(cx + bx), (uint32_t)(cy + by), (uint32_t)(cz + bz), res, dense, tmask);
-    c.w[k] = (wx[bx] * wy[by]) * wz[bz];
-  }
-}
-
-__device__ __forceinline__ float2 level_feature(const FieldDev& F, int l, const Corners& c) {
-  const float2* tab = reinterpret_cast<const float2*>(F.tables) + ((size_t)l << F.log2T);
-  float2 e[8];
-  // the two corners that differ in x share one 16-byte load when their slots are an
-  // aligned adjacent pair
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) {
-    const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
-    if (i1 == i0 + 1u && !(i0 & 1u)) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(tab + i0));
-      e[k] = make_float2(q.x, q.y);
-      e[k + 1] = make_float2(q.z, q.w);
-    } else {
-      e[k] = __ldg(tab + i0);
-      e[k + 1] = __ldg(tab + i1);
-    }
-  }
-  float f0 = 0.0f, f1 = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    f0 = fmaf(c.w[k], e[k].x, f0);
-    f1 = fmaf(c.w[k], e[k].y, f1);
-  }
-  return make_float2(f0, f1);
-}
 
 __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) {
   const int l = blockIdx.y;
@@ -83,50 +37,6 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) 
     }
     feat[(int64_t)(2 * l) * S_cap + s] = f.x;
     feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
-  }
-}
-
-// Warp-aggregated scatter: lanes hold consecutive samples, mostly of one ray, so lanes
-// hitting the same slot form contiguous runs on coarse levels.  A segmented inclusive
-// scan sums each run; the run's last lane issues one atomic for the whole run.  Lanes
-// with nothing to add are run heads that issue nothing.  When no lane continues a run the
-// scan is skipped.
-__device__ __forceinline__ void scatter_runs(float2* table, uint32_t key, bool live, float2 val) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const bool head = !live || lane == 0 || prev != key;
-  const unsigned heads = __ballot_sync(0xffffffffu, head);
-  if (heads != 0xffffffffu) {
-    const int run_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float x = __shfl_up_sync(0xffffffffu, val.x, o);
-      const float y = __shfl_up_sync(0xffffffffu, val.y, o);
-      if (lane - o >= run_start) {
-        val.x += x;
-        val.y += y;
-      }
-    }
-  }
-  const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (live && tail) atomicAdd(table + key, val);
-}
-
-// Scatter of one sample-level without run summation: the two corners of a cell that differ
-// in x go out as one 16-byte atomic when their slots are an aligned adjacent pair (dense
-// rows, or a hashed slot with x even), else as two 8-byte atomics.
-__device__ __forceinline__ void scatter_pairs(float2* table, const Corners& c, float2 g) {
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) {
-    const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
-    const float2 v0 = make_float2(c.w[k] * g.x, c.w[k] * g.y);
-    const float2 v1 = make_float2(c.w[k + 1] * g.x, c.w[k + 1] * g.y);
-    if (i1 == i0 + 1u && !(i0 & 1u)) {
-      atomicAdd(reinterpret_cast<float4*>(table + i0), make_float4(v0.x, v0.y, v1.x, v1.y));
-    } else {
-      atomicAdd(table + i0, v0);
-      atomicAdd(table + i1, v1);
-    }
   }
 }
 
