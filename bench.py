@@ -206,7 +206,50 @@ def time_train(invr, ctx, tb, steps, warmup, flush, world):
     return ms, ktime
 
 
-def roofline(ktime, tw, R, S_occ, peaks):
+def measure_l2(invr, ctx):
+    """L2 ceilings measured on this device by the library's probe kernels: a read stream over
+    a 64 MiB resident buffer (the size of one field's tables) and random float4 / float2
+    atomic adds into it (the forms the hash-gradient scatter issues).  Best of 5, CUDA events."""
+    import torch
+    buf = torch.ones(1 << 24, dtype=torch.float32, device="cuda")        # 64 MiB < 126 MB L2
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def best(fn, nbytes):
+        fn()                                                             # warm: buffer into L2
+        out = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+        return max(out)
+    passes, n_ops = 40, 1 << 27
+    res = {"read_gbs": best(lambda: invr.probe_l2_read(ctx, buf, passes, sink), passes * buf.numel() * 4),
+           "atomic_v4_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 4, n_ops), n_ops * 16),
+           "atomic_v2_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 2, n_ops), n_ops * 8)}
+    ctx.sync()
+    return {k: round(v, 1) for k, v in res.items()}
+
+
+def l2_roofline(name, kms_per_launch, S_occ, L, l2):
+    """The L2 view of a gather/scatter kernel: table payload per launch (8 corners x F=2
+    floats per level and sample) over its duration, against the probe's ceiling for that
+    access form."""
+    if l2 is None or name not in ("encode", "encode_bwd"):
+        return None
+    payload = S_occ * L * 8 * 2 * 4
+    ach = payload / (kms_per_launch * 1e-3) / 1e9
+    peak = l2["read_gbs"] if name == "encode" else l2["atomic_v4_gbs"]
+    return {"achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "payload_bytes": payload,
+            "peak_source": "measured by probe: " + ("L2-resident read stream" if name == "encode"
+                                                    else "random float4 atomic adds into a 64 MiB table")}
+
+
+def roofline(ktime, tw, R, S_occ, peaks, l2=None):
     fp = tw.fields[0]
     n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()
     name, (kms, kn) = max(ktime.items(), key=lambda kv: kv[1][0])
@@ -229,7 +272,8 @@ def roofline(ktime, tw, R, S_occ, peaks):
         ach = work / dur / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "l2": l2_roofline(name, kms / kn, S_occ, fp.desc.L, l2)}
     return None
 
 
@@ -322,7 +366,9 @@ def run_ours(args, rank, world, local):
                          "launch": "one CUDA graph per step (all batches per stage launch)", "tune": bt["tune"]}
         out["e2e"] = bt["e2e"]
         bR, bS = bt["rays"], bt["occupied_samples"]
-        out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks)
+        l2 = measure_l2(invr, ctx)
+        out["l2_probe"] = l2
+        out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks, l2)
         nsteps = max(5, args.steps // 4)
         out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
         per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))

@@ -269,6 +269,23 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
 invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p_dev,
                                       float* out_dev, invr_stream stream);
 
+/* ---- L2 ceiling probes (measurement helpers; the paper has no counterpart) -------------
+ * The hash tables of a field with T = 2^19 (64 MiB) stay resident in L2, so the encoding's
+ * gathers and the backward's scatter-add are bound by L2 rather than HBM.  These calls
+ * launch one kernel each, asynchronously on `stream`, that the caller times with events:
+ *  - invr_probe_l2_read: `passes` coalesced 16-byte reads of every element of buf_dev
+ *    (n_floats floats, a multiple of 4, 16-byte aligned; choose n_floats * 4 bytes below
+ *    the L2 size and warm it first).  Bytes read = passes * n_floats * 4.  sink_dev: one
+ *    float the kernel may write (never, for finite contents of buf_dev).
+ *  - invr_probe_l2_atomic: n_ops vector float atomic adds of +1.0 per component, width
+ *    4 (16-byte float4) or 2 (8-byte float2), at pseudo-random entries of table_dev
+ *    (n_floats floats, a multiple of 4, 16-byte aligned).  Payload = n_ops * width * 4 B.
+ * Bad sizes or null pointers return INVR_E_ARG. */
+invr_status invr_probe_l2_read(invr_ctx ctx, const float* buf_dev, int64_t n_floats, int passes, float* sink_dev,
+                               invr_stream stream);
+invr_status invr_probe_l2_atomic(invr_ctx ctx, float* table_dev, int64_t n_floats, int width, int64_t n_ops,
+                                 invr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

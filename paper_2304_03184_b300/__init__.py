@@ -82,6 +82,8 @@ _SIGNATURES = {
     "invr_ctx_enable_timing": [_VP, _I],
     "invr_ctx_timing": [_VP, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64), _I],
     "invr_query_points_noalloc": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
+    "invr_probe_l2_read": [_VP, _VP, _I64, C.c_int, _VP, _VP],
+    "invr_probe_l2_atomic": [_VP, _VP, _I64, C.c_int, _I64, _VP],
     "invr_ctx_autotune": [_VP, C.POINTER(invr_train_args), _VP],
     "invr_ctx_get_tune": [_VP, C.POINTER(C.c_int)],
     "invr_field_copy_params": [_VP, _VP, _VP],
@@ -470,3 +472,15 @@ def _autograd():
 def field_render_loss(tables, weights, ctx: Context, field: Field, tb: TrainBatches):
     """Differentiable Huber render loss (torch.autograd) of one field's training batches."""
     return _autograd().apply(tables, weights, ctx, field, tb)
+
+
+def probe_l2_read(ctx: Context, buf, passes: int, sink):
+    """invr_probe_l2_read: `passes` 16-byte coalesced reads of every float of `buf` (a CUDA
+    float32 tensor meant to stay resident in L2); the caller times it with events."""
+    _check(lib().invr_probe_l2_read(ctx.h, _ptr(buf), buf.numel(), passes, _ptr(sink), _stream()), ctx.h)
+
+
+def probe_l2_atomic(ctx: Context, table, width: int, n_ops: int):
+    """invr_probe_l2_atomic: n_ops float4 (width 4) or float2 (width 2) atomic adds at
+    pseudo-random entries of `table` (a CUDA float32 tensor)."""
+    _check(lib().invr_probe_l2_atomic(ctx.h, _ptr(table), table.numel(), width, n_ops, _stream()), ctx.h)

@@ -150,8 +150,8 @@ bool capturing(cudaStream_t s) {
 }
 
 void free_workspace(Workspace& w) {
-  void* ptrs[] = {w.ray_count, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray, w.s_t,
-                  w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part};
+  void* ptrs[] = {w.ray_count, w.ray_bits, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray,
+                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part};
   for (void* p : ptrs) dfree(p);
   w = Workspace{};
 }
@@ -178,6 +178,7 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
   Workspace& w = ctx->ws;
   const int64_t blocks = R / 1024 + kMaxViews + 1;
   INVR_CUDA(ctx, dmalloc(&w.ray_count, R));
+  INVR_CUDA(ctx, dmalloc(&w.ray_bits, (size_t)R * kRayBitWords));
   INVR_CUDA(ctx, dmalloc(&w.ray_first, R));
   INVR_CUDA(ctx, dmalloc(&w.ray_used, R));
   INVR_CUDA(ctx, dmalloc(&w.ray_out, 5 * R));
@@ -860,6 +861,25 @@ invr_status invr_ray_samples(invr_ctx ctx, int64_t n_rays, const float* o, const
   if (n_rays > 0 && (!o || !d || !count || !t || !p)) return fail(ctx, INVR_E_ARG, "null pointer");
   DeviceGuard guard(ctx->device);
   INVR_CUDA(ctx, launch_ray_samples(n_rays, o, d, n_samples, occ, count, t, p, static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_probe_l2_read(invr_ctx ctx, const float* buf, int64_t n_floats, int passes, float* sink,
+                               invr_stream stream) {
+  if (!ctx || !buf || !sink || n_floats < 4 || n_floats % 4 || passes < 1 || (uintptr_t)buf % 16)
+    return fail(ctx, INVR_E_ARG, "bad probe_l2_read arguments");
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, launch_probe_l2_read(buf, n_floats, passes, sink, ctx->num_sms, static_cast<cudaStream_t>(stream)));
+  return INVR_OK;
+}
+
+invr_status invr_probe_l2_atomic(invr_ctx ctx, float* table, int64_t n_floats, int width, int64_t n_ops,
+                                 invr_stream stream) {
+  if (!ctx || !table || n_floats < 4 || n_floats % 4 || n_floats / 2 > 0xFFFFFFFFll || (width != 2 && width != 4) ||
+      n_ops < 0 || (uintptr_t)table % 16)
+    return fail(ctx, INVR_E_ARG, "bad probe_l2_atomic arguments");
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, launch_probe_l2_atomic(table, n_floats, width, n_ops, ctx->num_sms, static_cast<cudaStream_t>(stream)));
   return INVR_OK;
 }
 

@@ -21,6 +21,7 @@ constexpr int kOccRes = 128;    // occupancy grid resolution over [-1,1]^3
 constexpr int kTile = 128;      // sample tile: every view's sample range is padded to it
 constexpr int kKnnG = 64;       // nearest-node candidate grid resolution over [-1,1]^3
 constexpr uint16_t kKnnOverflow = 0xFFFF;
+constexpr int kRayBitWords = 32;   // 1024 samples per ray at most
 
 // Device status word bits (read and cleared by invr_ctx_sync).
 constexpr unsigned kStatusNonFinite = 1u;
@@ -68,6 +69,7 @@ struct ViewDev {
 
 struct Workspace {
   int32_t* ray_count;       // [R] occupied samples per ray
+  uint32_t* ray_bits;       // [kRayBitWords][R_cap] occupancy bit of every sample of the ray
   int32_t* ray_first;       // [R] first sample slot of the ray
   int32_t* ray_used;        // [R] samples composited (early termination)
   float* ray_out;           // [5][R] C, A, D per global ray
@@ -249,5 +251,11 @@ cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, f
                                  cudaStream_t s);
 cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
                                   cudaStream_t s);
+
+// L2 ceiling probes (measurement only)
+cudaError_t launch_probe_l2_read(const float* buf, int64_t n_floats, int passes, float* sink, int num_sms,
+                                 cudaStream_t s);
+cudaError_t launch_probe_l2_atomic(float* table, int64_t n_floats, int width, int64_t n_ops, int num_sms,
+                                   cudaStream_t s);
 
 }  // namespace invr

@@ -7,8 +7,11 @@
 // in order; every view's range starts on a kTile boundary so that an MLP tile never
 // mixes two fields.  Padding slots carry s_ray = -1.
 //
+// The count pass records each ray's occupancy bits (word-major, coalesced), so the emit
+// pass visits only the occupied samples instead of re-marching the ray.
+//
 // Bound: HBM reads of the rays (24 B/ray) and bitfield lookups that hit L1/L2 (256 KiB
-// per view); writes 24 B per occupied sample.
+// per view); writes 4 B per 32 samples of each ray and 24 B per occupied sample.
 #include "invr_internal.cuh"
 
 namespace invr {
@@ -29,12 +32,21 @@ __global__ void __launch_bounds__(256) k_march_count(const __grid_constant__ Pla
   load_ray(V, g - V.ray_begin, o, d);
   float tn, dt;
   int cnt = 0;
-  if (ray_box(o, d, P.n_samples, tn, dt)) {
-    if (!V.occ) {
-      cnt = P.n_samples;
-    } else {
-      for (int j = 0; j < P.n_samples; ++j) cnt += occupied(V.occ, sample_p(o, d, sample_t(tn, dt, j)));
+  uint32_t* bits = P.ws.ray_bits + g;
+  const int64_t R_cap = P.ws.R_cap;
+  const int words = (P.n_samples + 31) / 32;
+  const bool hit = ray_box(o, d, P.n_samples, tn, dt);
+  for (int w = 0; w < words; ++w) {
+    uint32_t m = 0;
+    if (hit) {
+      const int j1 = min(32, P.n_samples - 32 * w);
+      for (int i = 0; i < j1; ++i) {
+        const int j = 32 * w + i;
+        if (!V.occ || occupied(V.occ, sample_p(o, d, sample_t(tn, dt, j)))) m |= 1u << i;
+      }
     }
+    bits[w * R_cap] = m;
+    cnt += __popc(m);
   }
   P.ws.ray_count[g] = cnt;
 }
@@ -154,16 +166,21 @@ __global__ void __launch_bounds__(256) k_march_emit(const __grid_constant__ Plan
   float tn, dt;
   ray_box(o, d, P.n_samples, tn, dt);
   int64_t s = P.ws.ray_first[g];
-  for (int j = 0; j < P.n_samples; ++j) {
-    const float t = sample_t(tn, dt, j);
-    const float3 p = sample_p(o, d, t);
-    if (V.occ && !occupied(V.occ, p)) continue;
-    P.ws.s_ray[s] = (int32_t)g;
-    P.ws.s_t[s] = t;
-    P.ws.s_pos[s] = p.x;
-    P.ws.s_pos[S_cap + s] = p.y;
-    P.ws.s_pos[2 * S_cap + s] = p.z;
-    ++s;
+  const uint32_t* bits = P.ws.ray_bits + g;
+  const int words = (P.n_samples + 31) / 32;
+  for (int w = 0; w < words; ++w) {
+    // the occupied samples recorded by the count pass, in order
+    for (uint32_t m = bits[w * P.ws.R_cap]; m; m &= m - 1) {
+      const int j = 32 * w + __ffs(m) - 1;
+      const float t = sample_t(tn, dt, j);
+      const float3 p = sample_p(o, d, t);
+      P.ws.s_ray[s] = (int32_t)g;
+      P.ws.s_t[s] = t;
+      P.ws.s_pos[s] = p.x;
+      P.ws.s_pos[S_cap + s] = p.y;
+      P.ws.s_pos[2 * S_cap + s] = p.z;
+      ++s;
+    }
   }
 }
 

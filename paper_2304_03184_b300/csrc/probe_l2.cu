@@ -1,0 +1,66 @@
+// Measurement helpers: the L2 ceilings of the gather/scatter kernels.
+//
+// The hash tables of a 2^19-entry field (64 MiB) stay resident in the 126 MB L2, so the
+// encoding's gathers and the backward's atomic scatter are bound by L2, not HBM.  These
+// two kernels measure that ceiling on the device: a read stream over an L2-resident
+// buffer, and vector atomic adds (the float4 / float2 forms the scatter issues) at
+// pseudo-random entries of an L2-resident table.  Neither is part of the method.
+#include "invr_internal.cuh"
+
+namespace invr {
+
+__global__ void __launch_bounds__(256) k_probe_l2_read(const float4* __restrict__ buf, int64_t n4, int passes,
+                                                       float* sink) {
+  float acc = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int p = 0; p < passes; ++p) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const float4 v = __ldcg(buf + i);
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  }
+  if (acc == 1.2345f) sink[0] = acc;  // keeps the loads; the buffer is filled so this never holds
+}
+
+__device__ __forceinline__ uint32_t probe_hash(uint64_t i) {
+  uint64_t z = i * 0x9E3779B97F4A7C15ull;
+  z ^= z >> 31;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 29;
+  return (uint32_t)z;
+}
+
+// width 4: atomicAdd(float4*) at random 16-byte-aligned entries; width 2: float2.
+template <int W>
+__global__ void __launch_bounds__(256) k_probe_l2_atomic(float* table, uint32_t n_vec, int64_t n_ops) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_ops; i += stride) {
+    const uint32_t e = probe_hash((uint64_t)i) % n_vec;
+    if (W == 4) {
+      atomicAdd(reinterpret_cast<float4*>(table) + e, make_float4(1.0f, 1.0f, 1.0f, 1.0f));
+    } else {
+      atomicAdd(reinterpret_cast<float2*>(table) + e, make_float2(1.0f, 1.0f));
+    }
+  }
+}
+
+cudaError_t launch_probe_l2_read(const float* buf, int64_t n_floats, int passes, float* sink, int num_sms,
+                                 cudaStream_t s) {
+  const int64_t n4 = n_floats / 4;
+  const int blocks = num_sms * 8;
+  k_probe_l2_read<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(buf), n4, passes, sink);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_l2_atomic(float* table, int64_t n_floats, int width, int64_t n_ops, int num_sms,
+                                   cudaStream_t s) {
+  const int blocks = num_sms * 8;
+  if (width == 4) {
+    k_probe_l2_atomic<4><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 4), n_ops);
+  } else {
+    k_probe_l2_atomic<2><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 2), n_ops);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace invr

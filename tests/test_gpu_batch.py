@@ -143,3 +143,23 @@ def test_device_wait_timeout_reported_and_recovered(env):
     np.testing.assert_allclose(rgba.cpu().numpy(), ref.rgba, atol=2e-3)
     invr.train_step(ctx, tb)
     ctx.sync()
+
+
+def test_l2_probes_do_the_counted_work(env):
+    """The L2 ceiling probes do exactly the work their byte counts assume: the atomic probe
+    adds +1 per component n_ops times (sum = n_ops x width), the read probe writes nothing."""
+    invr, _ = env
+    import torch
+    ctx = invr.Context(0)
+    for width in (4, 2):
+        table = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
+        invr.probe_l2_atomic(ctx, table, width, 3 << 18)
+        assert float(table.double().sum()) == float((3 << 18) * width)
+        assert float(table.max()) >= 1.0
+    buf = torch.ones(1 << 20, dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    invr.probe_l2_read(ctx, buf, 3, sink)
+    ctx.sync()
+    assert float(sink.item()) == 0.0
+    with pytest.raises(invr.InvrError):
+        invr.probe_l2_atomic(ctx, buf, 3, 10)
