@@ -64,6 +64,8 @@ typedef struct {
     const float* target;        /* [3][R] */
     double* grad_tables;        /* accumulates dLoss/dtables of view->field */
     double* grad_weights;       /* accumulates dLoss/dweights of view->field */
+    const float* mask;          /* [R] M(r) of the paper's losses, NULL = 1 */
+    const float* depth;         /* [R] sensor depth D(r) of the paper's depth loss */
 } orc_batch;
 
 /* ---------------------------------------------------------------- hash-grid geometry */
@@ -543,12 +545,43 @@ static void add_atomic(double* p, double v)
  *   dC/dsigma_j = dt (T_{j+1} c_j - (C - sum_{k<=j} T_k alpha_k c_k)),
  * then sigma = exp(o_0), c = sigmoid(z), the MLP chain rule, and the trilinear weights
  * scatter dL/dfeat into the 8 corner entries of every level. */
+/* Per-ray loss and its derivatives dl/dC (3) and dl/dD of the rendered colour C and depth D.
+ * Huber (kind 0): sum over the 3 channels of the Huber penalty of C - target, scaled by
+ * `norm`.  The paper's losses (kind 1, Sec. 4.4 Implementation Details): the colour term
+ * ||M (C_hat - C)||_2, the Euclidean norm of the masked colour error (its gradient is taken
+ * as 0 where the error is exactly 0), plus depth_weight times the depth term
+ * |M (D_hat - D)|, the L1 norm of the masked depth error (sign(0) = 0); summed over rays. */
+static double orc_ray_loss(int kind, const orc_batch* B, int64_t r, const double out[5], double huber_delta,
+                           double norm, double depth_weight, double dC[3], double* dD)
+{
+    int64_t R = B->n_rays;
+    double e[3];
+    for (int c = 0; c < 3; ++c) e[c] = out[c] - (double)B->target[(int64_t)c * R + r];
+    *dD = 0.0;
+    if (kind == 0) {
+        double l = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            l += orc_huber(e[c], huber_delta);
+            dC[c] = orc_huber_grad(e[c], huber_delta) * norm;
+        }
+        return l;
+    }
+    double M = B->mask ? (double)B->mask[r] : 1.0;
+    double n = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    for (int c = 0; c < 3; ++c) dC[c] = n > 0.0 ? M * e[c] / n : 0.0;
+    double ed = out[4] - (double)B->depth[r];
+    double sgn = ed > 0.0 ? 1.0 : (ed < 0.0 ? -1.0 : 0.0);
+    *dD = depth_weight * M * sgn;
+    return M * n + depth_weight * M * fabs(ed);
+}
+
 double orc_train_loss_grad(int n_batches, const orc_batch* batches, int n_samples, double t_eps,
-                           double huber_delta, int grads)
+                           double huber_delta, int grads, int loss_kind, double depth_weight)
 {
     int64_t total = 0;
     for (int b = 0; b < n_batches; ++b) total += batches[b].n_rays;
-    double norm = 1.0 / (3.0 * (double)total);
+    /* Huber: mean over rays and channels; the paper's losses: sum over rays */
+    double norm = loss_kind == 0 ? 1.0 / (3.0 * (double)total) : 1.0;
     double loss = 0.0;
     for (int b = 0; b < n_batches; ++b) {
         const orc_batch* B = &batches[b];
@@ -569,16 +602,12 @@ double orc_train_loss_grad(int n_batches, const orc_batch* batches, int n_sample
                 float rd[3] = {B->d[r], B->d[R + r], B->d[2 * R + r]};
                 double out[5];
                 int n = orc_composite_ray(v, ro, rd, n_samples, t_eps, out, rec, NULL);
-                double dC[3];
-                for (int c = 0; c < 3; ++c) {
-                    double e = out[c] - (double)B->target[(int64_t)c * R + r];
-                    bl += orc_huber(e, huber_delta);
-                    dC[c] = orc_huber_grad(e, huber_delta) * norm;
-                }
+                double dC[3], dD;
+                bl += orc_ray_loss(loss_kind, B, r, out, huber_delta, norm, depth_weight, dC, &dD);
                 if (!grads) continue;
                 float tn, dt;
                 if (!orc_ray_setup(ro, rd, n_samples, &tn, &dt)) continue;
-                double prefix[3] = {0.0, 0.0, 0.0};
+                double prefix[3] = {0.0, 0.0, 0.0}, prefix_d = 0.0;
                 for (int k = 0; k < n; ++k) {
                     const orc_rec* s = &rec[k];
                     double w = s->T * s->alpha;
@@ -590,6 +619,9 @@ double orc_train_loss_grad(int n_batches, const orc_batch* batches, int n_sample
                         dsigma += dC[c] * (double)dt * (T_next * s->rgb[c] - rest);
                         drgb[c] = dC[c] * w;
                     }
+                    /* depth D = sum T_j alpha_j t_j: the same adjoint with c_j -> t_j */
+                    prefix_d += w * (double)s->t;
+                    dsigma += dD * (double)dt * (T_next * (double)s->t - (out[4] - prefix_d));
                     orc_act a;
                     uint32_t idx[ORC_MAX_L * 8];
                     double cw[ORC_MAX_L * 8], dfeat[ORC_MAX_L * ORC_MAX_F];

@@ -26,6 +26,9 @@ What pins each oracle function (tests/test_oracle_pins.py, run with -m "not gpu"
                         field at p; depth ordering cases of the two-field composition
   loss / gradient       Huber closed form; central finite differences in FP64 of the
                         loss on 64 parameters
+  paper's losses        constant-density closed form of the masked colour L2 norm plus
+                        the masked depth L1 term (Sec. 4.4); central differences; a binary
+                        mask equals cutting the batch down to the masked-in rays
   Adam                  first and second steps in closed form
 """
 from __future__ import annotations
@@ -84,7 +87,8 @@ class CView(C.Structure):
 class CBatch(C.Structure):
     _fields_ = [("n_rays", C.c_int64), ("o", C.POINTER(C.c_float)), ("d", C.POINTER(C.c_float)),
                 ("view", C.POINTER(CView)), ("target", C.POINTER(C.c_float)),
-                ("grad_tables", C.POINTER(C.c_double)), ("grad_weights", C.POINTER(C.c_double))]
+                ("grad_tables", C.POINTER(C.c_double)), ("grad_weights", C.POINTER(C.c_double)),
+                ("mask", C.POINTER(C.c_float)), ("depth", C.POINTER(C.c_float))]
 
 
 def _declare(L):
@@ -99,7 +103,8 @@ def _declare(L):
     L.orc_huber.restype = C.c_double
     L.orc_render.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, C.c_int, P, P, P, P, P, P, P]
     L.orc_render.restype = None
-    L.orc_train_loss_grad.argtypes = [C.c_int, P, C.c_int, C.c_double, C.c_double, C.c_int]
+    L.orc_train_loss_grad.argtypes = [C.c_int, P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                      C.c_double]
     L.orc_train_loss_grad.restype = C.c_double
     L.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
                            C.c_double]
@@ -286,14 +291,27 @@ def render(o, d, n_samples: int, t_eps: float, views: Sequence[View]) -> RenderR
 
 
 class TrainBatch:
-    def __init__(self, o, d, view: View, target):
+    """One key-frame batch: rays o, d [3][R], the field view, target colour [3][R] and, for
+    the paper's losses, the mask M(r) [R] (None = 1) and sensor depth D(r) [R]."""
+
+    def __init__(self, o, d, view: View, target, mask=None, depth=None):
         self.o, self.d, self.target = _f32(o), _f32(d), _f32(target)
+        self.mask = None if mask is None else _f32(mask)
+        self.depth = None if depth is None else _f32(depth)
         self.view = view
 
 
+LOSS_KINDS = {"huber": 0, "paper": 1}
+
+
 def train_loss_grad(batches: List[TrainBatch], n_samples: int, t_eps: float, huber_delta: float,
-                    grads: bool = True):
-    """Returns (loss, {id(field): (grad_tables, grad_weights)})."""
+                    grads: bool = True, loss: str = "huber", depth_weight: float = 1.0):
+    """Returns (loss, {id(field): (grad_tables, grad_weights)}).  loss = "huber" (mean
+    Huber penalty over rays x channels) or "paper" (Sec. 4.4: sum over rays of the masked
+    colour L2 norm plus depth_weight x the masked depth L1 norm)."""
+    kind = LOSS_KINDS[loss]
+    if kind == 1 and any(b.depth is None for b in batches):
+        raise ValueError("the paper's depth loss needs every batch's sensor depth")
     out = {}
     cb = []
     for b in batches:
@@ -304,11 +322,13 @@ def train_loss_grad(batches: List[TrainBatch], n_samples: int, t_eps: float, hub
         cb.append(CBatch(b.o.shape[1], b.o.ctypes.data_as(C.POINTER(C.c_float)),
                          b.d.ctypes.data_as(C.POINTER(C.c_float)), C.pointer(b.view._c),
                          b.target.ctypes.data_as(C.POINTER(C.c_float)),
-                         gt.ctypes.data_as(C.POINTER(C.c_double)), gw.ctypes.data_as(C.POINTER(C.c_double))))
+                         gt.ctypes.data_as(C.POINTER(C.c_double)), gw.ctypes.data_as(C.POINTER(C.c_double)),
+                         None if b.mask is None else b.mask.ctypes.data_as(C.POINTER(C.c_float)),
+                         None if b.depth is None else b.depth.ctypes.data_as(C.POINTER(C.c_float))))
     arr = (CBatch * len(cb))(*cb)
-    loss = lib().orc_train_loss_grad(len(cb), C.cast(arr, C.c_void_p), n_samples, t_eps, huber_delta,
-                                     1 if grads else 0)
-    return loss, out
+    value = lib().orc_train_loss_grad(len(cb), C.cast(arr, C.c_void_p), n_samples, t_eps, huber_delta,
+                                      1 if grads else 0, kind, depth_weight)
+    return value, out
 
 
 def adam(p, g, m, v, step: int, lr: float, b1: float, b2: float, eps: float):

@@ -24,18 +24,23 @@ Recipes (all seeded with numpy's PCG64):
   * hash tables U(-0.5, 0.5); MLP weights Xavier-uniform U(+-sqrt(6/(fan_in+fan_out))).
   * target colours: 0.5 + 0.45 sin(a_k . d + b_k) per channel k, smooth in the ray
     direction d (a stand-in for the paper's RGB captures, which are not available).
+  * sensor depth and mask per training ray (stand-ins for the RGBD depth and the
+    segmentation masks): first hit of the canonical body ellipsoid (human batches) or of
+    the posed object sphere (object batches); mask 1 on a hit, else depth 0 and mask 0.
+    Computed from the rays alone, so they draw no random numbers.
 """
 from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
 OCC_RES = 128
 ELLIPSOID = (0.4, 0.8, 0.3)
 OBJECT_CENTRE = (0.55, 0.0, 0.0)
+OBJECT_RADIUS = 0.25
 
 
 # --------------------------------------------------------------------------- containers
@@ -240,7 +245,7 @@ def occupancy_near_nodes(x_live: np.ndarray, dist: float = 0.12) -> np.ndarray:
     return pack_bits(d <= dist)
 
 
-def occupancy_sphere(centre, radius: float = 0.25) -> np.ndarray:
+def occupancy_sphere(centre, radius: float = OBJECT_RADIUS) -> np.ndarray:
     c = _cell_centres()
     return pack_bits(np.sum((c - np.asarray(centre)[None]) ** 2, axis=1) <= radius * radius)
 
@@ -257,6 +262,24 @@ def xavier_weights(rng: np.random.Generator, desc: FieldDesc) -> np.ndarray:
 def make_field(rng: np.random.Generator, desc: FieldDesc) -> FieldParams:
     tables = rng.uniform(-0.5, 0.5, size=(desc.L, desc.T, desc.F)).astype(np.float32)
     return FieldParams(desc, tables, xavier_weights(rng, desc))
+
+
+def sensor_depth_mask(rays: Rays, centre, axes) -> Tuple[np.ndarray, np.ndarray]:
+    """Stand-in for the RGBD sensor and the segmentation mask of one actor: the distance
+    along each (unit-direction) ray to its first hit of an ellipsoid (centre, semi-axes),
+    and a mask that is 1 where the ray hits it; depth 0 and mask 0 elsewhere."""
+    c = np.asarray(centre, np.float64)[:, None]
+    a = np.asarray(axes, np.float64)[:, None]
+    o = (rays.o.astype(np.float64) - c) / a
+    d = rays.d.astype(np.float64) / a
+    qa = np.sum(d * d, axis=0)
+    qb = 2.0 * np.sum(o * d, axis=0)
+    qc = np.sum(o * o, axis=0) - 1.0
+    disc = qb * qb - 4.0 * qa * qc
+    hit = disc >= 0.0
+    t = np.where(hit, (-qb - np.sqrt(np.where(hit, disc, 0.0))) / (2.0 * qa), 0.0)
+    hit &= t > 0.0
+    return np.where(hit, 1.0, 0.0).astype(np.float32), np.where(hit, t, 0.0).astype(np.float32)
 
 
 def target_colours(rng: np.random.Generator, rays: Rays) -> np.ndarray:
@@ -286,6 +309,8 @@ class TrainBatch:
     rays: Rays
     view: View
     target: np.ndarray  # float32 [3][R]
+    mask: Optional[np.ndarray] = None    # float32 [R], 1 where the ray sees the field's actor
+    depth: Optional[np.ndarray] = None   # float32 [R], sensor depth along the ray (0 = none)
 
 
 @dataclasses.dataclass
@@ -340,7 +365,7 @@ def train_step_workload(seed: int = 3, n_rays: int = 1 << 18, n_samples: int = 1
     idx = rng.permutation(idx)
     rays = subset_rays(all_rays, idx)
     view = View(field, graph=graph, occupancy=occupancy_near_nodes(graph.x_live))
-    batch = TrainBatch(rays, view, target_colours(rng, rays))
+    batch = TrainBatch(rays, view, target_colours(rng, rays), *sensor_depth_mask(rays, (0, 0, 0), ELLIPSOID))
     return TrainWorkload(f"train_step_{n_rays}rays_s{n_samples}_L{field_desc.L}_T2^{field_desc.log2_T}"
                          f"_N{n_nodes}", [batch], [field], n_samples)
 
@@ -362,10 +387,10 @@ def keyframe_batch_workload(seed: int = 4, n_frames: int = 8, n_samples: int = 1
         centre = oR @ np.asarray(OBJECT_CENTRE) + ot
         hv = View(human, graph=g, occupancy=occupancy_near_nodes(g.x_live))
         ov = View(obj, rigid_dq=odq, occupancy=occupancy_sphere(centre))
-        for v in (hv, ov):
+        for v, (c, ax) in ((hv, ((0, 0, 0), ELLIPSOID)), (ov, (centre, (OBJECT_RADIUS,) * 3))):
             n = int(math.floor(2.0 ** rng.uniform(*log2_rays)))
             idx = rng.choice(all_rays.n, size=n, replace=False)
             rays = subset_rays(all_rays, idx)
-            batches.append(TrainBatch(rays, v, target_colours(rng, rays)))
+            batches.append(TrainBatch(rays, v, target_colours(rng, rays), *sensor_depth_mask(rays, c, ax)))
     return TrainWorkload(f"keyframe_batch_{n_frames}frames_x2fields_s{n_samples}", batches,
                          [human, obj], n_samples)

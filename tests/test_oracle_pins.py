@@ -470,7 +470,11 @@ def _small_train(oracle, rng, n_rays=48, n_samples=24):
 def test_gradients_match_central_differences(oracle):
     rng = np.random.default_rng(19)
     f, batches, S = _small_train(oracle, rng)
-    loss, grads = oracle.train_loss_grad(batches, S, 0.0, 0.1)
+    _check_central_differences(oracle, rng, f, batches, S)
+
+
+def _check_central_differences(oracle, rng, f, batches, S, **kw):
+    loss, grads = oracle.train_loss_grad(batches, S, 0.0, 0.1, **kw)
     gt, gw = grads[id(f)]
     assert loss > 0
     hit = np.flatnonzero(np.abs(gt) > 1e-3 * np.abs(gt).max())
@@ -479,9 +483,9 @@ def test_gradients_match_central_differences(oracle):
     def fd(arr, i, h):
         old = arr[i]
         arr[i] = old + h
-        lp, _ = oracle.train_loss_grad(batches, S, 0.0, 0.1, grads=False)
+        lp, _ = oracle.train_loss_grad(batches, S, 0.0, 0.1, grads=False, **kw)
         arr[i] = old - h
-        lm, _ = oracle.train_loss_grad(batches, S, 0.0, 0.1, grads=False)
+        lm, _ = oracle.train_loss_grad(batches, S, 0.0, 0.1, grads=False, **kw)
         arr[i] = old
         return (lp - lm) / (2 * h)
 
@@ -498,6 +502,72 @@ def test_gradients_match_central_differences(oracle):
                 continue
             assert abs(f2 - g[i]) <= 1e-5 * abs(g[i]) + 50 * eps * loss / 1e-6, (i, f2, g[i])
     assert skipped <= 4
+
+
+# ------------------------------------------------------- the paper's losses (Sec. 4.4)
+def _with_sensor(oracle, batches, rng, p_mask=0.7):
+    """Copies of the batches with a random binary mask and sensor depths in the box's range."""
+    out = []
+    for b in batches:
+        R = b.o.shape[1]
+        mask = (rng.uniform(size=R) < p_mask).astype(np.float32)
+        depth = rng.uniform(1.5, 3.5, size=R).astype(np.float32)
+        out.append(oracle.TrainBatch(b.o, b.d, b.view, b.target, mask, depth))
+    return out
+
+
+def test_paper_loss_constant_density_closed_form(oracle):
+    """sigma = 1, c = 1/2 everywhere: C_hat = A/2 per channel with A = 1 - exp(-(t_f - t_n)),
+    D_hat the arithmetico-geometric series of the constant-density pin, so the loss is
+    sum_r M_r (||A_r/2 - C_r||_2 + w |D_hat_r - D_r|) in closed form."""
+    rng = np.random.default_rng(41)
+    fp = tiny_field(rng, zero=True)
+    g = synth.make_graph(rng, 16, K=4)
+    v = oracle.View(oracle.Field.from_params(fp), graph=oracle.Graph.from_synth(g))
+    rays = synth.pinhole_rays(10, 10, 50.0, (0.0, 0.0, 2.5))
+    N, R = 40, rays.n
+    hit, tn, dt, _, _ = oracle.ray_samples(rays.o, rays.d, N)
+    h = hit.astype(bool)
+    D = dt.astype(np.float64)
+    A = np.where(h, 1.0 - np.exp(-N * D), 0.0)
+    q = np.exp(-D)
+    s0 = (1 - q ** N) / (1 - np.where(h, q, 0.5))
+    s1 = q * (1 - N * q ** (N - 1) + (N - 1) * q ** N) / (1 - np.where(h, q, 0.5)) ** 2
+    Dh = np.where(h, (1 - q) * ((tn + 0.5 * D) * s0 + D * s1), 0.0)
+    target = np.stack([np.full(R, 0.1), np.full(R, 0.25), np.full(R, 0.6)]).astype(np.float32)
+    mask = (rng.uniform(size=R) < 0.6).astype(np.float32)
+    depth = rng.uniform(1.5, 3.5, size=R).astype(np.float32)
+    w = 0.7
+    b = oracle.TrainBatch(rays.o, rays.d, v, target, mask, depth)
+    loss, _ = oracle.train_loss_grad([b], N, 0.0, 0.1, grads=False, loss="paper", depth_weight=w)
+    e = 0.5 * A[None, :] - target.astype(np.float64)
+    want = np.sum(mask * (np.sqrt(np.sum(e * e, axis=0)) + w * np.abs(Dh - depth)))
+    assert abs(loss - want) <= 1e-9 * want
+
+
+def test_paper_loss_gradients_match_central_differences(oracle):
+    rng = np.random.default_rng(43)
+    f, batches, S = _small_train(oracle, rng)
+    batches = _with_sensor(oracle, batches, rng)
+    _check_central_differences(oracle, rng, f, batches, S, loss="paper", depth_weight=0.5)
+
+
+def test_paper_loss_mask_selects_rays(oracle):
+    """M(r) in {0,1} selects rays: the masked loss and gradients equal those of the batch
+    cut down to the rays with M = 1 (unmasked); an all-zero mask gives zero everything."""
+    rng = np.random.default_rng(47)
+    f, batches, S = _small_train(oracle, rng)
+    (b,) = _with_sensor(oracle, batches, rng, p_mask=0.5)
+    keep = b.mask > 0
+    sub = oracle.TrainBatch(b.o[:, keep], b.d[:, keep], b.view, b.target[:, keep], None, b.depth[keep])
+    l1, g1 = oracle.train_loss_grad([b], S, 0.0, 0.1, loss="paper", depth_weight=0.3)
+    l2, g2 = oracle.train_loss_grad([sub], S, 0.0, 0.1, loss="paper", depth_weight=0.3)
+    assert abs(l1 - l2) <= 1e-12 * l2
+    for x, y in zip(g1[id(f)], g2[id(f)]):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-12 * np.abs(y).max())
+    zero = oracle.TrainBatch(b.o, b.d, b.view, b.target, np.zeros_like(b.mask), b.depth)
+    l0, g0 = oracle.train_loss_grad([zero], S, 0.0, 0.1, loss="paper")
+    assert l0 == 0.0 and all(np.all(x == 0.0) for x in g0[id(f)])
 
 
 # -------------------------------------------------------------------------- Adam
