@@ -103,7 +103,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workloads
-def build_train(invr, ctx, tw, prec):
+def build_train(invr, ctx, tw, prec, loss="huber"):
     import torch
     fields = {id(fp): invr.Field.from_synth(ctx, fp, prec) for fp in tw.fields}
     keep, batches = [], []
@@ -119,15 +119,19 @@ def build_train(invr, ctx, tw, prec):
         d = torch.from_numpy(b.rays.d).cuda()
         t = torch.from_numpy(b.target).cuda()
         keep.append((g, occ, view))
-        batches.append((o, d, view, t))
-    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+        if loss == "paper":      # the paper's masked colour L2 + depth L1 losses
+            batches.append((o, d, view, t, torch.from_numpy(b.mask).cuda(), torch.from_numpy(b.depth).cuda()))
+        else:
+            batches.append((o, d, view, t))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps,
+                           loss=loss)
     return tb, fields, keep
 
 
 def occupied_samples(invr, ctx, tb):
     """Occupied samples per batch (the samples the path evaluates), via the sampling step."""
     total = 0
-    for (o, d, view, _t) in tb.batches:
+    for (o, d, view, *_) in tb.batches:
         count, _, _ = invr.ray_samples(ctx, o, d, tb.args.batches[0].n_samples, view.occupancy)
         total += int(count.sum().item())
     return total
@@ -306,6 +310,14 @@ def run_ours(args, rank, world, local):
                        "kernels_ms_per_step": {k: round(v[0] / steps, 4) for k, v in sorted(ktime.items())}}
         if main is None:
             main = (tb, fields, keep, ms, ktime)
+    # the paper's losses (masked colour L2 + depth L1) in place of the Huber penalty
+    tbp, fields_p, keep_p = build_train(invr, ctx, tw, PRECS[args.prec], loss="paper")
+    steps_p = max(5, args.steps // 4)
+    ms_p, ktime_p = time_train(invr, ctx, tbp, steps_p, args.warmup, flush, world)
+    variants[args.prec + "_paper_loss"] = {
+        "value": round(world * S_nom / (ms_p * 1e-3), 1), "ms_per_step": round(ms_p, 3),
+        "kernels_ms_per_step": {k: round(v[0] / steps_p, 4) for k, v in sorted(ktime_p.items())}}
+    del tbp, fields_p, keep_p
     tb, fields, keep, ms, ktime = main
     value = world * S_nom / (ms * 1e-3)
     launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktime.items())
@@ -320,7 +332,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     a.record(stream)
     for _ in range(args.steps):
-        for (ho, hd, ht), (o, d, _v, t) in zip(host_in, tb.batches):
+        for (ho, hd, ht), (o, d, _v, t, *_) in zip(host_in, tb.batches):
             o.copy_(ho, non_blocking=True)
             d.copy_(hd, non_blocking=True)
         off = 0
@@ -440,7 +452,7 @@ def bench_batched(invr, args, flush, world, prec_name):
     a.record(stream)
     for _ in range(args.steps):
         off = 0
-        for (ho, hd, ht), (o, d, _v, _t) in zip(host_in, tb.batches):
+        for (ho, hd, ht), (o, d, _v, _t, *_) in zip(host_in, tb.batches):
             o.copy_(ho, non_blocking=True)
             d.copy_(hd, non_blocking=True)
             n = ht.numel()

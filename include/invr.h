@@ -184,15 +184,27 @@ typedef struct {
 invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* args, invr_stream stream);
 
 /* ------------------------------------------------------------------ training */
+/* Training losses.
+ *  INVR_LOSS_HUBER: Huber penalty (threshold huber_delta) of rendered colour minus target,
+ *    averaged over all rays of all batches and the 3 channels.
+ *  INVR_LOSS_PAPER: the paper's photometric and depth losses (Sec. 4.4, Implementation
+ *    Details), summed over all rays of all batches:
+ *      sum_r ||M(r) (C_hat(r) - C(r))||_2 + depth_weight * sum_r |M(r) (D_hat(r) - D(r))|
+ *    with C_hat the rendered colour, D_hat = sum_j T_j alpha_j t_j the rendered depth,
+ *    C(r) the target colour, D(r) the sensor depth and M(r) >= 0 the mask of the field's
+ *    actor (human or object, so each field is supervised by its own mask).  Where the
+ *    colour error is exactly 0 its gradient is taken as 0; sign(0) = 0 for the depth. */
+typedef enum { INVR_LOSS_HUBER = 0, INVR_LOSS_PAPER = 1 } invr_loss;
+
 /* One training step over key-frame ray batches (Sec. 4.2 "On-the-fly Radiance Fields",
  * key frames of Sec. 4.2): each batch is one field seen in one frame (n_views = 1; its
- * rgba_dev/depth_dev may be NULL or receive the rendered values).  Loss: Huber penalty
- * (threshold huber_delta) of rendered colour minus target, averaged over all rays of all
- * batches and the 3 channels; targets_dev holds each batch's [3][R_b] block back to
- * back.  The backward pass recomputes per-sample MLP activations, scatter-adds hash-table
+ * rgba_dev/depth_dev may be NULL or receive the rendered values).  targets_dev holds each
+ * batch's [3][R_b] target colours back to back; for INVR_LOSS_PAPER, masks_dev (or NULL
+ * for M = 1) and depths_dev hold each batch's [R_b] masks and sensor depths back to back.
+ * The backward pass recomputes per-sample MLP activations, scatter-adds hash-table
  * gradients, and Adam (lr, beta1, beta2, adam_eps, bias-corrected) then updates every
  * parameter of every field used.  loss_dev (device, 1 float) receives the loss.  At most
- * 16 batches. */
+ * 16 batches.  An unknown loss, or INVR_LOSS_PAPER without depths_dev, is INVR_E_ARG. */
 typedef struct {
     int n_batches;
     const invr_render_args* batches;
@@ -200,6 +212,10 @@ typedef struct {
     float huber_delta;
     float lr, beta1, beta2, adam_eps;
     float* loss_dev;
+    int loss;                   /* invr_loss */
+    const float* masks_dev;     /* per batch [R_b], back to back; NULL = 1 */
+    const float* depths_dev;    /* per batch [R_b], back to back */
+    float depth_weight;
 } invr_train_args;
 
 invr_status invr_train_step(invr_ctx ctx, const invr_train_args* args, invr_stream stream);

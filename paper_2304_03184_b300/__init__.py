@@ -50,7 +50,8 @@ class invr_train_args(C.Structure):
     _fields_ = [("n_batches", C.c_int), ("batches", C.POINTER(invr_render_args)),
                 ("targets_dev", C.c_void_p), ("huber_delta", C.c_float), ("lr", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("adam_eps", C.c_float),
-                ("loss_dev", C.c_void_p)]
+                ("loss_dev", C.c_void_p), ("loss", C.c_int), ("masks_dev", C.c_void_p),
+                ("depths_dev", C.c_void_p), ("depth_weight", C.c_float)]
 
 
 _VP, _I64, _I, _F = C.c_void_p, C.c_int64, C.c_int, C.c_float
@@ -312,20 +313,36 @@ def render_rays(ctx: Context, o, d, n_samples: int, t_eps: float, views: Sequenc
     return rgba, depth
 
 
+INVR_LOSS_HUBER, INVR_LOSS_PAPER = 0, 1
+LOSSES = {"huber": INVR_LOSS_HUBER, "paper": INVR_LOSS_PAPER}
+
+
 class TrainBatches:
-    """Key-frame ray batches of one training call: each batch = (o, d, view, target)."""
+    """Key-frame ray batches of one training call: each batch = (o, d, view, target) or,
+    for the paper's losses, (o, d, view, target, mask, depth) with mask [R] (or None for
+    M = 1) and sensor depth [R].  loss = "huber" or "paper" (see invr_loss)."""
 
     def __init__(self, batches, n_samples: int, t_eps: float = 1e-4, huber_delta: float = 0.1, lr: float = 1e-2,
-                 beta1: float = 0.9, beta2: float = 0.99, adam_eps: float = 1e-15, keep_outputs: bool = False):
+                 beta1: float = 0.9, beta2: float = 0.99, adam_eps: float = 1e-15, keep_outputs: bool = False,
+                 loss: str = "huber", depth_weight: float = 1.0):
         torch = _torch()
-        self.batches = list(batches)
+        self.batches = [tuple(b) for b in batches]
         # each batch's [3][R_b] target block, back to back
         self.targets = torch.cat([b[3].reshape(-1) for b in self.batches]).contiguous()
         self.loss = torch.zeros(1, device=self.targets.device)
+        self.masks = self.depths = None
+        kind = LOSSES[loss]
+        if kind == INVR_LOSS_PAPER:
+            if any(len(b) < 6 or b[5] is None for b in self.batches):
+                raise ValueError("the paper's depth loss needs every batch's sensor depth")
+            self.depths = torch.cat([b[5].reshape(-1) for b in self.batches]).contiguous()
+            if any(b[4] is not None for b in self.batches):
+                self.masks = torch.cat([b[4].reshape(-1) if b[4] is not None else
+                                        torch.ones(b[0].shape[1], device=b[0].device) for b in self.batches])
         self._views = [_views_array([b[2]]) for b in self.batches]
         self.outputs = []
         rargs = []
-        for (o, d, view, tgt), va in zip(self.batches, self._views):
+        for (o, d, view, *_), va in zip(self.batches, self._views):
             R = o.shape[1]
             rgba = torch.empty((4, R), device=o.device) if keep_outputs else None
             depth = torch.empty(R, device=o.device) if keep_outputs else None
@@ -333,7 +350,8 @@ class TrainBatches:
             rargs.append(invr_render_args(R, _ptr(o), _ptr(d), n_samples, t_eps, 1, va, _ptr(rgba), _ptr(depth)))
         self._rargs = (invr_render_args * len(rargs))(*rargs)
         self.args = invr_train_args(len(rargs), self._rargs, _ptr(self.targets), huber_delta, lr, beta1, beta2,
-                                    adam_eps, _ptr(self.loss))
+                                    adam_eps, _ptr(self.loss), kind, _ptr(self.masks), _ptr(self.depths),
+                                    depth_weight)
         self.ctx = None
 
 

@@ -352,8 +352,10 @@ invr_status check_desc(invr_ctx ctx, const invr_field_desc* d) {
   return INVR_OK;
 }
 
+static_assert(kLossHuber == INVR_LOSS_HUBER && kLossPaper == INVR_LOSS_PAPER, "loss codes");
+
 std::vector<int64_t> signature(const invr_train_args* a) {
-  std::vector<int64_t> s{a->n_batches};
+  std::vector<int64_t> s{a->n_batches, a->loss};
   for (int b = 0; b < a->n_batches; ++b) {
     s.push_back(a->batches[b].n_rays);
     s.push_back((int64_t)(uintptr_t)a->batches[b].views[0].field);
@@ -365,6 +367,9 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
   if (!a || a->n_batches < 1 || a->n_batches > kMaxViews || !a->batches)
     return fail(ctx, INVR_E_ARG, "1..16 batches per training call");
   if (!a->targets_dev || !a->loss_dev) return fail(ctx, INVR_E_ARG, "null targets_dev or loss_dev");
+  if (a->loss != INVR_LOSS_HUBER && a->loss != INVR_LOSS_PAPER) return fail(ctx, INVR_E_ARG, "unknown loss");
+  if (a->loss == INVR_LOSS_PAPER && !a->depths_dev)
+    return fail(ctx, INVR_E_ARG, "the paper's depth loss needs depths_dev");
   std::vector<const invr_render_args*> rays;
   std::vector<const invr_field_view*> views;
   const int ns = a->batches[0].n_samples;
@@ -399,11 +404,15 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
   for (int i = 0; i < a->n_batches; ++i) {
     const int b = order[i];
     P.v[i].target = a->targets_dev + 3 * target_off[b];
+    P.v[i].mask = a->loss == INVR_LOSS_PAPER && a->masks_dev ? a->masks_dev + target_off[b] : nullptr;
+    P.v[i].depth_target = a->loss == INVR_LOSS_PAPER ? a->depths_dev + target_off[b] : nullptr;
     P.v[i].rgba_out = a->batches[b].rgba_dev;
     P.v[i].depth_out = a->batches[b].depth_dev;
   }
-  P.loss_norm = (float)(1.0 / (3.0 * (double)P.total_rays));
+  P.loss_kind = a->loss;
+  P.loss_norm = a->loss == INVR_LOSS_HUBER ? (float)(1.0 / (3.0 * (double)P.total_rays)) : 1.0f;
   P.huber_delta = a->huber_delta;
+  P.depth_weight = a->depth_weight;
   st = ensure_workspace(ctx, P.total_rays, P.total_rays * ns + (int64_t)P.n_views * kTile, true, s);
   if (st != INVR_OK) return st;
   P.ws = ctx->ws;

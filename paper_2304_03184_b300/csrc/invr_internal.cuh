@@ -22,6 +22,8 @@ constexpr int kTile = 128;      // sample tile: every view's sample range is pad
 constexpr int kKnnG = 64;       // nearest-node candidate grid resolution over [-1,1]^3
 constexpr uint16_t kKnnOverflow = 0xFFFF;
 constexpr int kRayBitWords = 32;   // 1024 samples per ray at most
+constexpr int kLossHuber = 0;      // values of invr_loss
+constexpr int kLossPaper = 1;
 
 // Device status word bits (read and cleared by invr_ctx_sync).
 constexpr unsigned kStatusNonFinite = 1u;
@@ -58,6 +60,8 @@ struct ViewDev {
   const float* d;           // [3][n_rays]
   const uint32_t* occ;      // 128^3 bits or null
   const float* target;      // [3][n_rays] (training) or null
+  const float* mask;        // [n_rays] M(r) of the paper's losses, or null (= 1)
+  const float* depth_target;  // [n_rays] sensor depth of the paper's depth loss
   float* rgba_out;          // [4][n_rays] per-view output (training) or null
   float* depth_out;         // [n_rays] or null
   int64_t n_rays;
@@ -103,8 +107,10 @@ struct Plan {
   float t_eps;
   int n_scan_blocks;
   int64_t total_rays;
-  float loss_norm;          // 1 / (3 * total_rays)
+  float loss_norm;          // Huber: 1 / (3 * total_rays); the paper's losses: 1
   float huber_delta;
+  int loss_kind;            // INVR_LOSS_HUBER or INVR_LOSS_PAPER
+  float depth_weight;
   float grad_scale;
   int agg_res;              // levels with N_l <= agg_res aggregate gradient runs per warp
   int view_lo, view_hi;     // views processed by the per-field launches ([0, n_views) by default)

@@ -115,13 +115,28 @@ __global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__
     int used = 0;
     if (ray_dt(V, r, P.n_samples, dt)) used = composite(P, g, dt, res);
     P.ws.ray_used[g] = used;
-    float dC[3];
+    float dC[3], dD = 0.0f;
     bool finite = true;
+    float e[3];
     for (int c = 0; c < 3; ++c) {
-      const float e = res[c] - __ldg(V.target + c * V.n_rays + r);
-      loss += huber(e, P.huber_delta);
-      dC[c] = huber_grad(e, P.huber_delta) * P.loss_norm;
+      e[c] = res[c] - __ldg(V.target + c * V.n_rays + r);
       finite &= isfinite(res[c]);
+    }
+    if (P.loss_kind == kLossHuber) {
+      for (int c = 0; c < 3; ++c) {
+        loss += huber(e[c], P.huber_delta);
+        dC[c] = huber_grad(e[c], P.huber_delta) * P.loss_norm;
+      }
+    } else {
+      // the paper's losses: M ||e||_2 + w M |D_hat - D| (sum over rays, loss_norm = 1)
+      const float M = V.mask ? __ldg(V.mask + r) : 1.0f;
+      const float n = sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      const float inv = n > 0.0f ? M / n : 0.0f;
+      for (int c = 0; c < 3; ++c) dC[c] = e[c] * inv;
+      const float ed = res[4] - __ldg(V.depth_target + r);
+      dD = P.depth_weight * M * (ed > 0.0f ? 1.0f : (ed < 0.0f ? -1.0f : 0.0f));
+      loss += M * n + P.depth_weight * M * fabsf(ed);
+      finite &= isfinite(res[4]);
     }
     if (!finite) flag_status(P.status, kStatusNonFinite);
     if (V.rgba_out) {
@@ -131,7 +146,7 @@ __global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__
     // adjoint walk
     const int64_t first = P.ws.ray_first[g];
     const int cnt = P.ws.ray_count[g];
-    float T = 1.0f, pre[3] = {0.f, 0.f, 0.f};
+    float T = 1.0f, pre[3] = {0.f, 0.f, 0.f}, pre_d = 0.0f;
     for (int k = 0; k < cnt; ++k) {
       const int64_t s = first + k;
       float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
@@ -148,6 +163,12 @@ __global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__
           pre[c] = fmaf(w, col[c], pre[c]);
           dsig = fmaf(dC[c], Tn * col[c] - (res[c] - pre[c]), dsig);
           dz[c] = dC[c] * w * col[c] * (1.0f - col[c]);
+        }
+        if (dD != 0.0f) {
+          // depth D = sum T_j alpha_j t_j: the colour adjoint with c_j -> t_j
+          const float tj = P.ws.s_t[s];
+          pre_d = fmaf(w, tj, pre_d);
+          dsig = fmaf(dD, Tn * tj - (res[4] - pre_d), dsig);
         }
         d0 = dsig * dt * sigma;
         d1 = dz[0];

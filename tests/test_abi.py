@@ -59,6 +59,8 @@ int main(void) {
   F(invr_render_args, n_samples) F(invr_render_args, t_eps) F(invr_render_args, views) F(invr_render_args, depth_dev)
   printf("invr_train_args %zu\n", sizeof(invr_train_args));
   F(invr_train_args, targets_dev) F(invr_train_args, huber_delta) F(invr_train_args, loss_dev)
+  F(invr_train_args, loss) F(invr_train_args, masks_dev) F(invr_train_args, depths_dev)
+  F(invr_train_args, depth_weight)
   return 0;
 }
 """

@@ -302,7 +302,7 @@ def test_invalid_arguments_raise(env):
 
 
 # ------------------------------------------------------------------ training
-def _train_both(env, tw: synth.TrainWorkload, prec=0):
+def _train_both(env, tw: synth.TrainWorkload, prec=0, loss="huber", depth_weight=1.0):
     invr, ctx, oracle = env
     ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
     gfields = {id(fp): invr.Field.from_synth(ctx, fp, prec) for fp in tw.fields}
@@ -311,9 +311,14 @@ def _train_both(env, tw: synth.TrainWorkload, prec=0):
         side = Side(invr, ctx, oracle, b.view, prec, field=gfields[id(b.view.field)],
                     ofield=ofields[id(b.view.field)])
         keep.append(side)
-        batches.append((cu(b.rays.o), cu(b.rays.d), side.view, cu(b.target)))
-        obatches.append(oracle.TrainBatch(b.rays.o, b.rays.d, side.oview, b.target))
-    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+        if loss == "paper":
+            batches.append((cu(b.rays.o), cu(b.rays.d), side.view, cu(b.target), cu(b.mask), cu(b.depth)))
+            obatches.append(oracle.TrainBatch(b.rays.o, b.rays.d, side.oview, b.target, b.mask, b.depth))
+        else:
+            batches.append((cu(b.rays.o), cu(b.rays.d), side.view, cu(b.target)))
+            obatches.append(oracle.TrainBatch(b.rays.o, b.rays.d, side.oview, b.target))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps,
+                           loss=loss, depth_weight=depth_weight)
     return tb, gfields, ofields, obatches, keep
 
 
@@ -403,6 +408,68 @@ def test_train_gradients_mixed_precision(env, prec):
     for i, (r, c) in enumerate(d.weight_shapes()):
         _assert_grads_close(gw[off:off + r * c], ogw[off:off + r * c], f"W{i + 1}", MIXED_W_RTOL)
         off += r * c
+
+
+# ------------------------------------------------ the paper's losses (Sec. 4.4)
+def _paper_workload(seed, n_rays, identity=False):
+    """The train-step workload with the rays restricted to those the body ellipsoid's mask
+    keeps for half of them (so masked-out rays are present), identity motion if asked."""
+    tw = synth.train_step_workload(seed=seed, n_rays=n_rays)
+    b = tw.batches[0]
+    if identity:
+        g = b.view.graph
+        g.dq[:] = np.array([1, 0, 0, 0, 0, 0, 0, 0], np.float32)[:, None]
+        g.x_live[:] = g.x_canon
+    # half of the masked-out rays get mask 1 with a far sensor depth: the depth term then
+    # acts on rays through empty space too
+    rng = np.random.default_rng(seed)
+    out = np.flatnonzero(b.mask == 0)
+    flip = rng.choice(out, len(out) // 2, replace=False)
+    b.mask[flip] = 1.0
+    b.depth[flip] = 3.0
+    return tw
+
+
+def test_paper_loss_gradients_identity_motion(env):
+    """FP32 path with the paper's masked colour L2 + depth L1 losses: loss and every
+    gradient tensor against the oracle (identity motion isolates the adjoint chain)."""
+    invr, ctx, oracle = env
+    tw = _paper_workload(11, 1536, identity=True)
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw, loss="paper", depth_weight=0.5)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta, loss="paper",
+                                           depth_weight=0.5)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
+    fp = tw.fields[0]
+    gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+    ogt, ogw = ograds[id(ofields[id(fp)])]
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_paper_loss_keyframe_two_fields(env, prec):
+    """Batched key frames (human and object batches, each with its own actor mask and
+    sensor depth) under the paper's losses: loss and gradients of both fields."""
+    invr, ctx, oracle = env
+    code = invr.INVR_MLP_BF16 if prec == "bf16" else invr.INVR_FP32
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw, code, loss="paper")
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta, loss="paper")
+    assert abs(float(host(loss)[0]) - oloss) <= (1e-5 if prec == "fp32" else 2e-3) * oloss
+    w_rtol = GRAD_RTOL_WARP if prec == "fp32" else MIXED_W_RTOL
+    for fp in tw.fields:
+        gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+        ogt, ogw = ograds[id(ofields[id(fp)])]
+        _assert_grads_close(gw, ogw, "weights", w_rtol)
+        if prec == "fp32":
+            _assert_grads_close(gt, ogt, "tables", GRAD_RTOL_WARP)
+        else:
+            _assert_grads_close(gt, ogt, "tables", MIXED_TABLE_RTOL["bf16"])
 
 
 def test_train_step_adam_matches_oracle(env):
