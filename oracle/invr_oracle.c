@@ -47,7 +47,14 @@ typedef struct {
     double radius;          /* influence radius r of Eq. 2 (0.1 in the paper) */
     const float* x_live;    /* deformed node positions x_i^t = dq_i^t x_i, [3][N] */
     const float* dq;        /* node motions dq_i^t, [8][N] */
+    /* look-up-table neighbour search (Sec. 4.2, "On-the-fly Radiance Fields"); unused
+     * when lut_live is NULL */
+    int lut_res;                /* G: G^3 voxels over [-1,1]^3 in both spaces */
+    const uint16_t* lut_canon;  /* [G^3][K] canonical KNN field */
+    const uint32_t* lut_live;   /* [G^3] live voxel -> canonical voxel, ORC_LUT_EMPTY = none */
 } orc_graph;
+
+#define ORC_LUT_EMPTY 0xFFFFFFFFu
 
 typedef struct {
     const orc_field* field;
@@ -241,6 +248,188 @@ void orc_knn(const orc_graph* g, const float p[3], int* ids, float* keys)
     }
 }
 
+/* ---------------------------------------- look-up-table neighbour search (Sec. 4.2) */
+/* The paper replaces the O(N) neighbour query by tables: a canonical KNN field of G^3
+ * voxels (G = 512 there) holding each voxel's K nearest canonical nodes, built once; per
+ * frame every canonical voxel centre is carried to live space by the forward warp of
+ * Eq. 2 (its own K nodes blended) and its index is stored in the live voxel it lands in;
+ * a sample then reads its live voxel, the canonical voxel stored there, and that voxel's
+ * K nodes, and blends them as in Eq. 4.
+ *
+ * Readings where the paper is silent: several canonical voxels landing in one live voxel
+ * leave the smallest canonical index; canonical voxels carried outside [-1,1]^3 are
+ * dropped; a sample whose live voxel received none (a hole) uses the exact K nearest
+ * deformed nodes.  The integer results (voxel of a point, KNN ids, live voxel of a warped
+ * centre) are decided in single precision by the recipes below, so that any
+ * implementation performing the same rounded operations builds identical tables; the
+ * exponential of the blend weights is computed by Cody-Waite range reduction
+ * (x = n ln2 + r, ln2 split in a short high part and a low part, |r| <= ln2/2) and the
+ * degree-6 Taylor polynomial of e^r by Horner's rule, scaled by 2^n, for x <= 0; it is 0
+ * where n < -125 (x below about -86.6), a weight negligible next to the nearest node's 1. */
+static float orc_lut_exp(float x)
+{
+    float n = rintf(x * 1.44269504f);
+    if (n < -125.0f) return 0.0f;
+    float r = (x - n * 0.693145752f) - n * 1.42860682e-06f;
+    float p = 1.38888889e-03f;    /* 1/6! ... 1/3!: decimal literals, no constant folding */
+    p = p * r + 8.33333333e-03f;
+    p = p * r + 4.16666667e-02f;
+    p = p * r + 1.66666667e-01f;
+    p = p * r + 0.5f;
+    p = p * r + 1.0f;
+    p = p * r + 1.0f;
+    union { uint32_t u; float f; } scale;
+    scale.u = (uint32_t)((int)n + 127) << 23;
+    return p * scale.f;
+}
+
+/* Centre of voxel i of G along one axis: (i + 1/2) (2/G) - 1 (exact for G a power of 2). */
+static float orc_lut_centre(int i, int G)
+{
+    return ((float)i + 0.5f) * (2.0f / (float)G) - 1.0f;
+}
+
+/* Voxel of one coordinate: floor(((x + 1) * 0.5) * G); -1 when outside [0, G). */
+static int orc_lut_cell(float x, int G)
+{
+    float q = ((x + 1.0f) * 0.5f) * (float)G;
+    float f = floorf(q);
+    return (f < 0.0f || f >= (float)G) ? -1 : (int)f;
+}
+
+/* Canonical KNN field: for every voxel centre the K nearest canonical nodes x_i, same key
+ * and tie rule as orc_knn, ids ascending by (key, id).  out [G^3][K], voxel x + G(y + G z). */
+void orc_lut_canon_knn(int n_nodes, int K, const float* x_canon, int G, uint16_t* out)
+{
+    orc_graph cg = {n_nodes, K, 0.0, x_canon, NULL, 0, NULL, NULL};
+    int64_t n = (int64_t)G * G * G;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; ++v) {
+        float c[3] = {orc_lut_centre((int)(v % G), G), orc_lut_centre((int)((v / G) % G), G),
+                      orc_lut_centre((int)(v / ((int64_t)G * G)), G)};
+        int ids[ORC_MAX_K];
+        float keys[ORC_MAX_K];
+        orc_knn(&cg, c, ids, keys);
+        for (int k = 0; k < K; ++k) out[v * K + k] = (uint16_t)ids[k];
+    }
+}
+
+/* Forward warp (Eq. 2) of canonical point c by the blend of its K canonical neighbours
+ * ids (ascending by canonical key), single-precision recipe: weights
+ * exp((key_0 - key_k) / r^2) with key_k = |c - x_k|^2 (the shift by the nearest key cancels
+ * in the normalisation), sign alignment to the nearest node, blend, normalisation
+ * q_r = b_r/|b_r|, q_d = b_d/|b_r| - (q_r.b_d/|b_r|) q_r, then R(q_r) c + t with
+ * t = 2 vec(q_d q_r^*). */
+static void orc_lut_forward(int N, int K, float radius, const float* x_canon, const float* dq, const int* ids,
+                            const float c[3], float out[3])
+{
+    float keys[ORC_MAX_K];
+    for (int k = 0; k < K; ++k) {
+        float dx = c[0] - x_canon[0 * N + ids[k]];
+        float dy = c[1] - x_canon[1 * N + ids[k]];
+        float dz = c[2] - x_canon[2 * N + ids[k]];
+        keys[k] = ((dx * dx) + (dy * dy)) + (dz * dz);
+    }
+    float inv_r2 = 1.0f / (radius * radius);
+    float ref[4];
+    for (int a = 0; a < 4; ++a) ref[a] = dq[a * N + ids[0]];
+    float b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+        const int i = ids[k];
+        float w = orc_lut_exp((keys[0] - keys[k]) * inv_r2);
+        float dot = (((dq[0 * N + i] * ref[0]) + (dq[1 * N + i] * ref[1])) + (dq[2 * N + i] * ref[2])) +
+                    (dq[3 * N + i] * ref[3]);
+        if (dot < 0.0f) w = -w;
+        for (int a = 0; a < 8; ++a) b[a] = b[a] + w * dq[a * N + i];
+    }
+    float nr = sqrtf((((b[0] * b[0]) + (b[1] * b[1])) + (b[2] * b[2])) + (b[3] * b[3]));
+    float qr[4], dn[4];
+    for (int a = 0; a < 4; ++a) {
+        qr[a] = b[a] / nr;
+        dn[a] = b[4 + a] / nr;
+    }
+    float dot = (((qr[0] * dn[0]) + (qr[1] * dn[1])) + (qr[2] * dn[2])) + (qr[3] * dn[3]);
+    float qd[4];
+    for (int a = 0; a < 4; ++a) qd[a] = dn[a] - dot * qr[a];
+    /* q_r = (w, u), q_d = (s, v): vec(q_d q_r^*) = w v - s u - v x u */
+    float w = qr[0], u[3] = {qr[1], qr[2], qr[3]}, sd = qd[0], v[3] = {qd[1], qd[2], qd[3]};
+    float vxu[3] = {(v[1] * u[2]) - (v[2] * u[1]), (v[2] * u[0]) - (v[0] * u[2]), (v[0] * u[1]) - (v[1] * u[0])};
+    float t[3];
+    for (int a = 0; a < 3; ++a) t[a] = 2.0f * (((w * v[a]) - (sd * u[a])) - vxu[a]);
+    /* R(q_r) c = c + w tt + u x tt with tt = 2 (u x c) */
+    float tt[3] = {2.0f * ((u[1] * c[2]) - (u[2] * c[1])), 2.0f * ((u[2] * c[0]) - (u[0] * c[2])),
+                   2.0f * ((u[0] * c[1]) - (u[1] * c[0]))};
+    float uxt[3] = {(u[1] * tt[2]) - (u[2] * tt[1]), (u[2] * tt[0]) - (u[0] * tt[2]),
+                    (u[0] * tt[1]) - (u[1] * tt[0])};
+    for (int a = 0; a < 3; ++a) out[a] = ((c[a] + (w * tt[a])) + uxt[a]) + t[a];
+}
+
+/* Live index field of one frame: every canonical voxel k, in increasing order, forward
+ * warped (orc_lut_forward with its K canonical neighbours and the frame's motions dq) and
+ * stored in the live voxel it lands in unless that voxel already holds a smaller index
+ * (so each live voxel keeps the smallest k).  live [G^3]. */
+void orc_lut_live_index(int n_nodes, int K, float radius, const float* x_canon, const float* dq, int G,
+                        const uint16_t* canon, uint32_t* live)
+{
+    int64_t n = (int64_t)G * G * G;
+    for (int64_t v = 0; v < n; ++v) live[v] = ORC_LUT_EMPTY;
+    for (int64_t k = 0; k < n; ++k) {
+        float c[3] = {orc_lut_centre((int)(k % G), G), orc_lut_centre((int)((k / G) % G), G),
+                      orc_lut_centre((int)(k / ((int64_t)G * G)), G)};
+        int ids[ORC_MAX_K];
+        for (int j = 0; j < K; ++j) ids[j] = canon[k * K + j];
+        float q[3];
+        orc_lut_forward(n_nodes, K, radius, x_canon, dq, ids, c, q);
+        int cx = orc_lut_cell(q[0], G), cy = orc_lut_cell(q[1], G), cz = orc_lut_cell(q[2], G);
+        if (cx < 0 || cy < 0 || cz < 0) continue;
+        int64_t f = cx + (int64_t)G * (cy + (int64_t)G * cz);
+        if (live[f] == ORC_LUT_EMPTY) live[f] = (uint32_t)k;
+    }
+}
+
+/* Neighbour set of a live point: with tables, the K nodes of the canonical voxel stored
+ * in p's live voxel (p's voxel clamped into the grid), ordered by the same live key and
+ * tie rule as orc_knn; without tables or in a hole, the exact K nearest (orc_knn).
+ * Returns 1 when the tables supplied the set. */
+int orc_neighbours(const orc_graph* g, const float p[3], int* ids, float* keys)
+{
+    if (!g->lut_live) {
+        orc_knn(g, p, ids, keys);
+        return 0;
+    }
+    int G = g->lut_res, N = g->n_nodes, K = g->K;
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        int i = (int)floorf(((p[a] + 1.0f) * 0.5f) * (float)G);
+        c[a] = i < 0 ? 0 : (i > G - 1 ? G - 1 : i);
+    }
+    uint32_t k = g->lut_live[c[0] + (int64_t)G * (c[1] + (int64_t)G * c[2])];
+    if (k == ORC_LUT_EMPTY) {
+        orc_knn(g, p, ids, keys);
+        return 0;
+    }
+    for (int j = 0; j < K; ++j) {
+        keys[j] = INFINITY;
+        ids[j] = -1;
+    }
+    for (int j = 0; j < K; ++j) {
+        int i = g->lut_canon[(int64_t)k * K + j];
+        float dx = p[0] - g->x_live[0 * N + i];
+        float dy = p[1] - g->x_live[1 * N + i];
+        float dz = p[2] - g->x_live[2 * N + i];
+        float key = ((dx * dx) + (dy * dy)) + (dz * dz);
+        int pos = K - 1;
+        while (pos > 0 && (keys[pos - 1] > key || (keys[pos - 1] == key && ids[pos - 1] > i))) {
+            keys[pos] = keys[pos - 1];
+            ids[pos] = ids[pos - 1];
+            --pos;
+        }
+        keys[pos] = key;
+        ids[pos] = i;
+    }
+    return 1;
+}
+
 /* Dual-quaternion blend of the K nearest deformed nodes (Eq. 2 blending, applied with
  * the deformed nodes as in Eq. 4).  Weights w_i = exp(-|p - x_i^t|^2 / r^2), evaluated
  * shifted by the nearest node's squared distance (the common factor cancels in the
@@ -251,7 +440,7 @@ void orc_blend(const orc_graph* g, const float p[3], double qr[4], double qd[4],
     int ids[ORC_MAX_K];
     float keys[ORC_MAX_K];
     int N = g->n_nodes, K = g->K;
-    orc_knn(g, p, ids, keys);
+    orc_neighbours(g, p, ids, keys);
     double d2[ORC_MAX_K];
     for (int k = 0; k < K; ++k) {
         double s = 0.0;
@@ -703,6 +892,38 @@ void orc_knn_points(const orc_graph* g, int64_t n, const float* p, int* ids, flo
             ids[(int64_t)k * n + i] = id[k];
             keys[(int64_t)k * n + i] = ky[k];
         }
+    }
+}
+
+/* Neighbour sets of n points p[3][n] (orc_neighbours): ids [K][n]; from_lut[n] = 1 where the
+ * tables supplied the set, 0 where the exact search did. */
+void orc_neighbour_points(const orc_graph* g, int64_t n, const float* p, int* ids, int* from_lut)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        float q[3] = {p[i], p[n + i], p[2 * n + i]};
+        int id[ORC_MAX_K];
+        float ky[ORC_MAX_K];
+        from_lut[i] = orc_neighbours(g, q, id, ky);
+        for (int k = 0; k < g->K; ++k) ids[(int64_t)k * n + i] = id[k];
+    }
+}
+
+/* The table exponential of n arguments (for its error-bound pin). */
+void orc_lut_exp_points(int64_t n, const float* x, float* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_lut_exp(x[i]);
+}
+
+/* Forward warp (single-precision recipe) of n canonical points c[3][n] with neighbour ids
+ * [n][K] (ascending by canonical key): out[3][n]. */
+void orc_lut_forward_points(int n_nodes, int K, float radius, const float* x_canon, const float* dq, int64_t n,
+                            const float* c, const int* ids, float* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float q[3] = {c[i], c[n + i], c[2 * n + i]}, r[3];
+        orc_lut_forward(n_nodes, K, radius, x_canon, dq, ids + i * K, q, r);
+        for (int a = 0; a < 3; ++a) out[a * n + i] = r[a];
     }
 }
 

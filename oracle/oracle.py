@@ -20,6 +20,14 @@ What pins each oracle function (tests/test_oracle_pins.py, run with -m "not gpu"
                         identity motion gives v_c = p; sign flips of node quaternions do
                         not change the result; x_live = R x + t of the input generator
   rigid warp            R orthonormal, round trip T^-1 T p = p
+  look-up-table search  table exponential within 4e-7 of exp; canonical KNN field = numpy
+                        lexsort per voxel; identity motion maps every voxel to itself; a
+                        one-voxel translation shifts the live index by one; the FP32
+                        forward-warp recipe within 2e-6 of an FP64 blend computed in the
+                        test; live index = brute-force smallest canonical voxel per cell
+                        (FP64, cell-face cases exempt); table neighbour sets give the
+                        exact warp wherever they equal the exact K nearest, holes use
+                        the exact set
   MLPs                  zero weights give sigma = 1, c = 1/2; numpy matmul chain
   compositing           constant density closed forms for A, C, D; single sample;
                         early-termination bound; identity deformation equals the rigid
@@ -76,7 +84,9 @@ class CField(C.Structure):
 
 class CGraph(C.Structure):
     _fields_ = [("n_nodes", C.c_int), ("K", C.c_int), ("radius", C.c_double),
-                ("x_live", C.POINTER(C.c_float)), ("dq", C.POINTER(C.c_float))]
+                ("x_live", C.POINTER(C.c_float)), ("dq", C.POINTER(C.c_float)),
+                ("lut_res", C.c_int), ("lut_canon", C.POINTER(C.c_uint16)),
+                ("lut_live", C.POINTER(C.c_uint32))]
 
 
 class CView(C.Structure):
@@ -103,6 +113,11 @@ def _declare(L):
     L.orc_huber.restype = C.c_double
     L.orc_render.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, C.c_int, P, P, P, P, P, P, P]
     L.orc_render.restype = None
+    L.orc_lut_canon_knn.argtypes = [C.c_int, C.c_int, P, C.c_int, P]
+    L.orc_lut_live_index.argtypes = [C.c_int, C.c_int, C.c_float, P, P, C.c_int, P, P]
+    L.orc_lut_exp_points.argtypes = [C.c_int64, P, P]
+    L.orc_lut_forward_points.argtypes = [C.c_int, C.c_int, C.c_float, P, P, C.c_int64, P, P, P]
+    L.orc_neighbour_points.argtypes = [P, C.c_int64, P, P, P]
     L.orc_train_loss_grad.argtypes = [C.c_int, P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                       C.c_double]
     L.orc_train_loss_grad.restype = C.c_double
@@ -149,16 +164,73 @@ class Field:
 
 
 class Graph:
-    def __init__(self, x_live, dq, K: int, radius: float):
+    """Deformed nodes x_live [3][N] and motions dq [8][N] of one frame.  With lut=(G, canon,
+    live) the neighbour sets come from the look-up tables (lut_canon_knn, lut_live_index)
+    instead of the exact search."""
+
+    def __init__(self, x_live, dq, K: int, radius: float, lut=None):
         self.x_live = _f32(x_live)
         self.dq = _f32(dq)
         self._c = CGraph(self.x_live.shape[1], K, float(radius),
                          self.x_live.ctypes.data_as(C.POINTER(C.c_float)),
-                         self.dq.ctypes.data_as(C.POINTER(C.c_float)))
+                         self.dq.ctypes.data_as(C.POINTER(C.c_float)), 0, None, None)
+        self.lut = None
+        if lut is not None:
+            G, canon, live = lut
+            self.lut = (int(G), np.ascontiguousarray(canon, np.uint16), np.ascontiguousarray(live, np.uint32))
+            self._c.lut_res = self.lut[0]
+            self._c.lut_canon = self.lut[1].ctypes.data_as(C.POINTER(C.c_uint16))
+            self._c.lut_live = self.lut[2].ctypes.data_as(C.POINTER(C.c_uint32))
 
     @classmethod
-    def from_synth(cls, g):
-        return cls(g.x_live, g.dq, g.K, g.radius)
+    def from_synth(cls, g, lut=None):
+        return cls(g.x_live, g.dq, g.K, g.radius, lut)
+
+
+LUT_EMPTY = 0xFFFFFFFF
+
+
+def lut_canon_knn(x_canon, K: int, G: int) -> np.ndarray:
+    """Canonical KNN field [G^3][K] (uint16 node ids, ascending by key)."""
+    x = _f32(x_canon)
+    out = np.zeros((G ** 3, K), np.uint16)
+    lib().orc_lut_canon_knn(x.shape[1], K, _p(x), G, _p(out))
+    return out
+
+
+def lut_live_index(x_canon, dq, K: int, radius: float, G: int, canon) -> np.ndarray:
+    """Live index field [G^3] (uint32 canonical voxel per live voxel, LUT_EMPTY = none)."""
+    x, q = _f32(x_canon), _f32(dq)
+    canon = np.ascontiguousarray(canon, np.uint16)
+    live = np.zeros(G ** 3, np.uint32)
+    lib().orc_lut_live_index(x.shape[1], K, float(radius), _p(x), _p(q), G, _p(canon), _p(live))
+    return live
+
+
+def lut_exp(x) -> np.ndarray:
+    x = _f32(x)
+    out = np.zeros_like(x)
+    lib().orc_lut_exp_points(x.size, _p(x), _p(out))
+    return out
+
+
+def lut_forward_points(x_canon, dq, K: int, radius: float, c, ids) -> np.ndarray:
+    """Single-precision forward warp of canonical points c [3][n] by neighbours ids [n][K]."""
+    x, q, c = _f32(x_canon), _f32(dq), _f32(c)
+    ids = np.ascontiguousarray(ids, np.int32)
+    out = np.zeros_like(c)
+    lib().orc_lut_forward_points(x.shape[1], K, float(radius), _p(x), _p(q), c.shape[1], _p(c), _p(ids), _p(out))
+    return out
+
+
+def neighbour_points(graph: Graph, p):
+    """Neighbour ids [K][n] of live points and whether the tables supplied each set."""
+    p = _f32(p)
+    n = p.shape[1]
+    ids = np.zeros((graph._c.K, n), np.int32)
+    from_lut = np.zeros(n, np.int32)
+    lib().orc_neighbour_points(C.byref(graph._c), n, _p(p), _p(ids), _p(from_lut))
+    return ids, from_lut.astype(bool)
 
 
 class View:

@@ -586,3 +586,157 @@ def test_adam_constant_gradient_steps_by_lr_sign(oracle):
     q, m0, v0 = p0.copy(), np.zeros(100), np.zeros(100)
     oracle.adam(q, np.zeros(100), m0, v0, 1, 1e-2, 0.9, 0.99, 1e-15)
     np.testing.assert_array_equal(q, p0)
+
+
+# ------------------------------------- look-up-table neighbour search (Sec. 4.2)
+def test_lut_exp_error_bound(oracle):
+    """The tables' exponential (Cody-Waite reduction + degree-6 Taylor) stays within
+    4e-7 relative of exp on [-86, 0], is exact at 0, and is 0 below -86.6 (2^-125)."""
+    x = np.linspace(-86.0, 0.0, 200001).astype(np.float32)
+    got = oracle.lut_exp(x).astype(np.float64)
+    want = np.exp(x.astype(np.float64))
+    assert np.max(np.abs(got - want) / want) <= 4e-7
+    assert oracle.lut_exp(np.zeros(1, np.float32))[0] == 1.0
+    assert np.all(oracle.lut_exp(np.array([-87.0, -200.0, -1e30], np.float32)) == 0.0)
+
+
+def _centres(G):
+    c = ((np.arange(G, dtype=np.float32) + np.float32(0.5)) * np.float32(2.0 / G) - np.float32(1.0)).astype(np.float32)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()])       # voxel x + G (y + G z)
+
+
+def test_lut_canonical_field_matches_lexsort(oracle):
+    rng = np.random.default_rng(51)
+    G, K = 8, 4
+    x = rng.uniform(-0.9, 0.9, size=(3, 40)).astype(np.float32)
+    canon = oracle.lut_canon_knn(x, K, G)
+    c = _centres(G)
+    for v in range(G ** 3):
+        d = (c[:, v:v + 1] - x).astype(np.float32)
+        key = ((d[0] * d[0]) + (d[1] * d[1])) + (d[2] * d[2])
+        order = np.lexsort((np.arange(x.shape[1]), key))[:K]
+        assert list(canon[v]) == list(order), v
+
+
+def _identity_graph(g):
+    g.dq[:] = np.array([1, 0, 0, 0, 0, 0, 0, 0], np.float32)[:, None]
+    g.x_live[:] = g.x_canon
+    return g
+
+
+def test_lut_identity_motion_maps_each_voxel_to_itself(oracle):
+    rng = np.random.default_rng(52)
+    G = 16
+    g = _identity_graph(synth.make_graph(rng, 48, K=4))
+    canon = oracle.lut_canon_knn(g.x_canon, 4, G)
+    live = oracle.lut_live_index(g.x_canon, g.dq, 4, g.radius, G, canon)
+    assert np.array_equal(live, np.arange(G ** 3, dtype=np.uint32))
+
+
+def test_lut_one_voxel_translation_shifts_the_index(oracle):
+    """Every node translated by one voxel along +x: canonical voxel (x, y, z) lands in live
+    voxel (x+1, y, z), so live[f] = f - 1 and the x = 0 plane stays empty."""
+    rng = np.random.default_rng(53)
+    G = 16
+    g = synth.make_graph(rng, 48, K=4)
+    g.dq[:] = np.array([1, 0, 0, 0, 0, 1.0 / G, 0, 0], np.float32)[:, None]   # q_d = 1/2 (0, t) q_r
+    canon = oracle.lut_canon_knn(g.x_canon, 4, G)
+    live = oracle.lut_live_index(g.x_canon, g.dq, 4, g.radius, G, canon).reshape(G, G, G)   # [z][y][x]
+    f = np.arange(G ** 3, dtype=np.int64).reshape(G, G, G)
+    assert np.all(live[:, :, 0] == oracle.LUT_EMPTY)
+    assert np.array_equal(live[:, :, 1:].astype(np.int64), f[:, :, 1:] - 1)
+
+
+def _fp64_forward(oracle, g, ids, c):
+    """FP64 forward warp of Eq. 2 from scratch: weights exp(-|c - x_i|^2 / r^2) over the
+    given canonical neighbours, sign alignment, blend, then the oracle's pinned SE3 apply
+    (which normalises)."""
+    x = g.x_canon.astype(np.float64)
+    q = g.dq.astype(np.float64)
+    n = c.shape[1]
+    b = np.zeros((8, n))
+    d2 = np.stack([np.sum((c.astype(np.float64) - x[:, ids[:, k]]) ** 2, axis=0) for k in range(ids.shape[1])])
+    ref = q[:4, ids[:, 0]]
+    for k in range(ids.shape[1]):
+        w = np.exp(-(d2[k] - d2[0]) / g.radius ** 2)
+        s = np.where(np.sum(q[:4, ids[:, k]] * ref, axis=0) < 0, -1.0, 1.0)
+        b += s * w * q[:, ids[:, k]]
+    c64 = c.astype(np.float64)
+    return np.concatenate([oracle.dq_apply_points(b[:, i], c64[:, i:i + 1]) for i in range(n)], axis=1)
+
+
+def test_lut_forward_warp_matches_fp64(oracle):
+    rng = np.random.default_rng(54)
+    G = 16
+    g = synth.make_graph(rng, 64, K=4)
+    canon = oracle.lut_canon_knn(g.x_canon, 4, G)
+    c = _centres(G)
+    got = oracle.lut_forward_points(g.x_canon, g.dq, 4, g.radius, c, canon.astype(np.int32))
+    want = _fp64_forward(oracle, g, canon.astype(np.int64), c)
+    assert np.max(np.abs(got - want)) <= 2e-6
+
+
+def test_lut_live_index_brute_force(oracle):
+    """Each live voxel holds the smallest canonical voxel whose FP64 forward warp lands in
+    it, and empty voxels receive none; voxels warped to within 1e-5 of a cell face (where
+    single and double precision may pick different cells) are exempt."""
+    rng = np.random.default_rng(55)
+    G = 12
+    g = synth.make_graph(rng, 48, K=4)
+    canon = oracle.lut_canon_knn(g.x_canon, 4, G)
+    live = oracle.lut_live_index(g.x_canon, g.dq, 4, g.radius, G, canon).astype(np.int64)
+    pos = _fp64_forward(oracle, g, canon.astype(np.int64), _centres(G))
+    q = (pos + 1.0) * 0.5 * G
+    fl = np.floor(q)
+    ambiguous = np.any(np.minimum(q - fl, fl + 1 - q) < 1e-5 * G, axis=0)
+    inside = np.all((fl >= 0) & (fl < G), axis=0)
+    cell = (fl[0] + G * (fl[1] + G * fl[2])).astype(np.int64)
+    assert ambiguous.sum() < 0.01 * G ** 3
+    want = np.full(G ** 3, -1, np.int64)
+    for k in np.flatnonzero(inside & ~ambiguous)[::-1]:     # descending: the smallest k wins
+        want[cell[k]] = k
+    empty = live == oracle.LUT_EMPTY
+    for f in range(G ** 3):
+        if want[f] >= 0:
+            assert not empty[f] and (live[f] == want[f] or (live[f] < want[f] and ambiguous[live[f]])), f
+        elif not empty[f]:
+            assert ambiguous[live[f]], f
+    assert empty.sum() > 0 and (~empty).sum() > 0.5 * G ** 3
+
+
+def test_lut_neighbours_and_warp(oracle):
+    """Neighbour sets from the tables: under identity motion they are the canonical field's
+    entry of the point's voxel; under motion, where a set equals the exact K nearest the
+    warp is identical to the exact warp, and points in empty live voxels use the exact set."""
+    rng = np.random.default_rng(56)
+    G = 32
+    gi = _identity_graph(synth.make_graph(rng, 64, K=4))
+    canon_i = oracle.lut_canon_knn(gi.x_canon, 4, G)
+    live_i = oracle.lut_live_index(gi.x_canon, gi.dq, 4, gi.radius, G, canon_i)
+    p = rng.uniform(-0.95, 0.95, size=(3, 3000)).astype(np.float32)
+    ids, from_lut = oracle.neighbour_points(oracle.Graph.from_synth(gi, (G, canon_i, live_i)), p)
+    assert from_lut.all()
+    vox = np.floor(((p + np.float32(1)) * np.float32(0.5)) * np.float32(G)).astype(np.int64)
+    v = vox[0] + G * (vox[1] + G * vox[2])
+    assert np.array_equal(np.sort(ids, axis=0), np.sort(canon_i[v].T.astype(np.int32), axis=0))
+
+    g = synth.make_graph(rng, 64, K=4)
+    canon = oracle.lut_canon_knn(g.x_canon, 4, G)
+    live = oracle.lut_live_index(g.x_canon, g.dq, 4, g.radius, G, canon)
+    lut_graph = oracle.Graph.from_synth(g, (G, canon, live))
+    exact_graph = oracle.Graph.from_synth(g)
+    near = g.x_live[:, rng.integers(0, 64, 3000)] + rng.normal(scale=0.05, size=(3, 3000)).astype(np.float32)
+    ids_l, from_lut = oracle.neighbour_points(lut_graph, near)
+    ids_e, _ = oracle.knn_points(exact_graph, near)
+    f = oracle.Field.from_params(tiny_field(rng))
+    vc_l = oracle.warp_points(oracle.View(f, graph=lut_graph), near)
+    vc_e = oracle.warp_points(oracle.View(f, graph=exact_graph), near)
+    same = np.all(ids_l == ids_e, axis=0)
+    assert 0.3 < same.mean() < 1.0                 # an approximation that is mostly right
+    assert np.array_equal(vc_l[:, same], vc_e[:, same])
+    assert np.array_equal(ids_l[:, ~from_lut], ids_e[:, ~from_lut])
+    holes = live == oracle.LUT_EMPTY
+    vox = np.floor(((np.clip(near, -1, 1) + np.float32(1)) * np.float32(0.5)) * np.float32(G)).astype(np.int64)
+    vox = np.clip(vox, 0, G - 1)
+    assert np.array_equal(~from_lut, holes[vox[0] + G * (vox[1] + G * vox[2])])
