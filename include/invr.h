@@ -147,6 +147,29 @@ invr_status invr_graph_set_pose(invr_graph graph, int frame, const float* dq_dev
                                 invr_stream stream);
 invr_status invr_graph_destroy(invr_graph graph);
 
+/* Look-up-table neighbour search (Sec. 4.2, "On-the-fly Radiance Fields"), the paper's
+ * approximate O(1) replacement of the K-nearest-node query of the human warp.
+ * invr_graph_enable_lut builds, asynchronously on `stream`, a canonical KNN field of
+ * resolution^3 voxels over [-1,1]^3 (each voxel's K nearest canonical nodes; 512 in the
+ * paper) and, for every frame already posed, a live index field: each canonical voxel
+ * centre is carried to live space by the forward warp of Eq. 2 and its index stored in the
+ * live voxel it lands in (several: the smallest index; outside the box: dropped).  Every
+ * later invr_graph_set_pose rebuilds its frame's live field.  While a graph has tables,
+ * warps of views on it take each sample's K nodes from the canonical voxel stored in its
+ * live voxel (ordered by live distance, ties to the lower index); samples in a live voxel
+ * that received no canonical voxel use the exact search.  Device memory: resolution^3 x K x
+ * 2 bytes once plus resolution^3 x 4 bytes per posed frame (1 GiB + 512 MiB per frame at
+ * 512 and K = 4).  resolution: a power of two in [4, 1024], else INVR_E_ARG; not during
+ * stream capture (INVR_E_STATE).  Calling it again rebuilds at the new resolution.
+ * invr_graph_disable_lut frees the tables (after a device synchronisation); warps return
+ * to the exact search.  invr_graph_get_lut copies the canonical field ([G^3][K] uint16,
+ * voxel x + G (y + G z)) and/or one frame's live field ([G^3] uint32, 0xFFFFFFFF = none)
+ * into caller device buffers (either may be NULL); INVR_E_STATE without tables. */
+invr_status invr_graph_enable_lut(invr_graph graph, int resolution, invr_stream stream);
+invr_status invr_graph_disable_lut(invr_graph graph);
+invr_status invr_graph_get_lut(invr_graph graph, int frame, uint16_t* canon_dev, uint32_t* live_dev,
+                               invr_stream stream);
+
 /* ------------------------------------------------------------------ rendering */
 /* One field seen in one frame: the human field through `graph` at `frame` (inverse
  * dual-quaternion-blend warp, Eq. 4), or, when graph == NULL, the object field through

@@ -294,7 +294,7 @@ static int orc_lut_cell(float x, int G)
 {
     float q = ((x + 1.0f) * 0.5f) * (float)G;
     float f = floorf(q);
-    return (f < 0.0f || f >= (float)G) ? -1 : (int)f;
+    return (f >= 0.0f && f < (float)G) ? (int)f : -1;
 }
 
 /* Canonical KNN field: for every voxel centre the K nearest canonical nodes x_i, same key

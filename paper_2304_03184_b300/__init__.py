@@ -83,6 +83,9 @@ _SIGNATURES = {
     "invr_ctx_enable_timing": [_VP, _I],
     "invr_ctx_timing": [_VP, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64), _I],
     "invr_query_points_noalloc": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
+    "invr_graph_enable_lut": [_VP, C.c_int, _VP],
+    "invr_graph_disable_lut": [_VP],
+    "invr_graph_get_lut": [_VP, C.c_int, _VP, _VP, _VP],
     "invr_probe_l2_read": [_VP, _VP, _I64, C.c_int, _VP, _VP],
     "invr_probe_l2_atomic": [_VP, _VP, _I64, C.c_int, _I64, _VP],
     "invr_ctx_autotune": [_VP, C.POINTER(invr_train_args), _VP],
@@ -272,6 +275,25 @@ class Graph:
 
     def set_pose(self, frame: int, dq, x_live):
         _check(lib().invr_graph_set_pose(self.h, frame, _ptr(dq), _ptr(x_live), _stream()), self.ctx.h)
+
+    def enable_lut(self, resolution: int = 512):
+        """Look-up-table neighbour search (invr_graph_enable_lut)."""
+        _check(lib().invr_graph_enable_lut(self.h, resolution, _stream()), self.ctx.h)
+        self.lut_res = resolution
+
+    def disable_lut(self):
+        _check(lib().invr_graph_disable_lut(self.h), self.ctx.h)
+        self.lut_res = 0
+
+    def get_lut(self, frame: int = 0):
+        """Device copies of the canonical KNN field ([G^3][K] node ids, int16 holding uint16)
+        and of the frame's live index field ([G^3], int32 holding uint32; -1 = none)."""
+        torch = _torch()
+        G = self.lut_res
+        canon = torch.empty((G ** 3, self.desc.K), dtype=torch.int16, device="cuda")
+        live = torch.empty(G ** 3, dtype=torch.int32, device="cuda")
+        _check(lib().invr_graph_get_lut(self.h, frame, _ptr(canon), _ptr(live), _stream()), self.ctx.h)
+        return canon, live
 
     def close(self):
         if self.h:

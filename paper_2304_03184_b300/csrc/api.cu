@@ -58,10 +58,17 @@ struct invr_graph_s {
     float4* dq = nullptr;
     uint16_t* cand = nullptr;
     uint16_t* cand_n = nullptr;
+    uint32_t* lut_live = nullptr;   // [G^3] live index field of this frame
     bool set = false;
   };
   std::vector<Frame> frames;
   int cap = 0;  // 0: no candidate grid (scan all nodes)
+  // look-up-table neighbour search (Sec. 4.2); lut_res == 0: exact search
+  int lut_res = 0;
+  uint16_t* lut_canon = nullptr;   // [G^3][K] canonical KNN field
+  float4* x_canon4 = nullptr;      // canonical nodes, packed
+  uint16_t* canon_cand = nullptr;  // candidate grid over the canonical nodes
+  uint16_t* canon_cand_n = nullptr;
 };
 
 namespace {
@@ -268,6 +275,11 @@ invr_status warp_dev(invr_ctx ctx, const invr_field_view& v, WarpDev& W) {
   W.K = g->desc.K;
   W.cap = g->cap;
   W.inv_r2 = 1.0f / (g->desc.radius * g->desc.radius);
+  if (g->lut_res > 0) {
+    W.lut_res = g->lut_res;
+    W.lut_canon = g->lut_canon;
+    W.lut_live = fr.lut_live;
+  }
   return INVR_OK;
 }
 
@@ -789,7 +801,100 @@ invr_status invr_graph_set_pose(invr_graph g, int frame, const float* dq_dev, co
   if (g->cap > 0)
     INVR_CUDA(ctx, TIMED(ctx, "knn_grid_build", s,
                          launch_knn_grid_build(fr.x_live, N, g->desc.K, g->cap, fr.cand, fr.cand_n, ctx->num_sms, s)));
+  if (g->lut_res > 0) {
+    const size_t G3 = (size_t)g->lut_res * g->lut_res * g->lut_res;
+    if (!fr.lut_live) {
+      if (capturing(s)) return fail(ctx, INVR_E_STATE, "first pose of a frame cannot be set during capture");
+      INVR_CUDA(ctx, dmalloc(&fr.lut_live, G3));
+    }
+    INVR_CUDA(ctx, TIMED(ctx, "lut_live", s,
+                         launch_lut_live(g->x_canon4, fr.dq, N, g->desc.K, 1.0f / (g->desc.radius * g->desc.radius),
+                                         g->lut_res, g->lut_canon, fr.lut_live, ctx->num_sms, s)));
+  }
   fr.set = true;
+  return INVR_OK;
+}
+
+static void free_lut(invr_graph g) {
+  for (auto& fr : g->frames) {
+    dfree(fr.lut_live);
+    fr.lut_live = nullptr;
+  }
+  dfree(g->lut_canon); dfree(g->x_canon4); dfree(g->canon_cand); dfree(g->canon_cand_n);
+  g->lut_canon = nullptr; g->x_canon4 = nullptr; g->canon_cand = nullptr; g->canon_cand_n = nullptr;
+  g->lut_res = 0;
+}
+
+invr_status invr_graph_enable_lut(invr_graph g, int resolution, invr_stream stream) {
+  if (!g) return INVR_E_ARG;
+  invr_ctx ctx = g->ctx;
+  if (resolution < 4 || resolution > 1024 || (resolution & (resolution - 1)))
+    return fail(ctx, INVR_E_ARG, "table resolution must be a power of two in [4, 1024]");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (capturing(s)) return fail(ctx, INVR_E_STATE, "tables cannot be built during capture");
+  if (g->lut_res > 0) {
+    cudaDeviceSynchronize();
+    free_lut(g);
+  }
+  const int N = g->desc.n_nodes, K = g->desc.K;
+  const size_t G3 = (size_t)resolution * resolution * resolution;
+  if (dmalloc(&g->lut_canon, G3 * K) != cudaSuccess || dmalloc(&g->x_canon4, (size_t)N) != cudaSuccess) {
+    free_lut(g);
+    return fail(ctx, INVR_E_OOM, "table allocation failed");
+  }
+  if (g->cap > 0) {
+    const size_t cells = (size_t)kKnnG * kKnnG * kKnnG;
+    if (dmalloc(&g->canon_cand, cells * g->cap) != cudaSuccess || dmalloc(&g->canon_cand_n, cells) != cudaSuccess) {
+      free_lut(g);
+      return fail(ctx, INVR_E_OOM, "table allocation failed");
+    }
+  }
+  for (auto& fr : g->frames) {
+    if (fr.set && dmalloc(&fr.lut_live, G3) != cudaSuccess) {
+      free_lut(g);
+      return fail(ctx, INVR_E_OOM, "table allocation failed");
+    }
+  }
+  g->lut_res = resolution;
+  INVR_CUDA(ctx, launch_pack_points(g->x_canon, N, g->x_canon4, s));
+  if (g->cap > 0)
+    INVR_CUDA(ctx, launch_knn_grid_build(g->x_canon4, N, K, g->cap, g->canon_cand, g->canon_cand_n, ctx->num_sms, s));
+  INVR_CUDA(ctx, TIMED(ctx, "lut_canon", s,
+                       launch_lut_canon(g->x_canon4, N, K, g->canon_cand, g->canon_cand_n, g->cap, resolution,
+                                        g->lut_canon, ctx->num_sms, s)));
+  for (auto& fr : g->frames) {
+    if (!fr.set) continue;
+    INVR_CUDA(ctx, TIMED(ctx, "lut_live", s,
+                         launch_lut_live(g->x_canon4, fr.dq, N, K, 1.0f / (g->desc.radius * g->desc.radius),
+                                         resolution, g->lut_canon, fr.lut_live, ctx->num_sms, s)));
+  }
+  return INVR_OK;
+}
+
+invr_status invr_graph_disable_lut(invr_graph g) {
+  if (!g) return INVR_E_ARG;
+  DeviceGuard guard(g->ctx->device);
+  cudaDeviceSynchronize();
+  free_lut(g);
+  return INVR_OK;
+}
+
+invr_status invr_graph_get_lut(invr_graph g, int frame, uint16_t* canon_dev, uint32_t* live_dev, invr_stream stream) {
+  if (!g) return INVR_E_ARG;
+  invr_ctx ctx = g->ctx;
+  if (g->lut_res == 0) return fail(ctx, INVR_E_STATE, "graph has no tables (invr_graph_enable_lut)");
+  if (frame < 0 || frame >= (int)g->frames.size()) return fail(ctx, INVR_E_ARG, "frame out of range");
+  if (live_dev && !g->frames[frame].lut_live) return fail(ctx, INVR_E_STATE, "frame pose not set");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t G3 = (size_t)g->lut_res * g->lut_res * g->lut_res;
+  if (canon_dev)
+    INVR_CUDA(ctx, cudaMemcpyAsync(canon_dev, g->lut_canon, G3 * g->desc.K * sizeof(uint16_t),
+                                   cudaMemcpyDeviceToDevice, s));
+  if (live_dev)
+    INVR_CUDA(ctx, cudaMemcpyAsync(live_dev, g->frames[frame].lut_live, G3 * sizeof(uint32_t),
+                                   cudaMemcpyDeviceToDevice, s));
   return INVR_OK;
 }
 
@@ -797,6 +902,7 @@ invr_status invr_graph_destroy(invr_graph g) {
   if (!g) return INVR_E_ARG;
   DeviceGuard guard(g->ctx->device);
   cudaDeviceSynchronize();
+  free_lut(g);
   for (auto& fr : g->frames) {
     dfree(fr.x_live); dfree(fr.dq); dfree(fr.cand); dfree(fr.cand_n);
   }

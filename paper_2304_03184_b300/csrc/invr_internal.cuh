@@ -22,6 +22,7 @@ constexpr int kTile = 128;      // sample tile: every view's sample range is pad
 constexpr int kKnnG = 64;       // nearest-node candidate grid resolution over [-1,1]^3
 constexpr uint16_t kKnnOverflow = 0xFFFF;
 constexpr int kRayBitWords = 32;   // 1024 samples per ray at most
+constexpr uint32_t kLutEmpty = 0xFFFFFFFFu;
 constexpr int kLossHuber = 0;      // values of invr_loss
 constexpr int kLossPaper = 1;
 
@@ -53,6 +54,10 @@ struct WarpDev {
   const uint16_t* cand_n;   // [G^3] candidate count, kKnnOverflow = use all nodes
   int n_nodes, K, cap;
   float inv_r2;             // 1 / radius^2
+  // look-up-table neighbour search (Sec. 4.2); lut_live == null: exact search
+  int lut_res;              // G
+  const uint16_t* lut_canon;  // [G^3][K] canonical KNN field
+  const uint32_t* lut_live;   // [G^3] live voxel -> canonical voxel, kLutEmpty = none
 };
 
 struct ViewDev {
@@ -257,6 +262,13 @@ cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, f
                                  cudaStream_t s);
 cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
                                   cudaStream_t s);
+
+// look-up-table neighbour search (Sec. 4.2)
+cudaError_t launch_pack_points(const float* x_soa, int n, float4* out, cudaStream_t s);
+cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint16_t* cand, const uint16_t* cand_n,
+                             int cap, int G, uint16_t* canon, int num_sms, cudaStream_t s);
+cudaError_t launch_lut_live(const float4* x_canon, const float4* dq, int n, int K, float inv_r2, int G,
+                            const uint16_t* canon, uint32_t* live, int num_sms, cudaStream_t s);
 
 // L2 ceiling probes (measurement only)
 cudaError_t launch_probe_l2_read(const float* buf, int64_t n_floats, int passes, float* sink, int num_sms,

@@ -14,56 +14,14 @@
 // single-precision rounding of the keys and of the cell assignment) in index order, so
 // scanning the list with the same keys and tie rule as a scan of all nodes selects the
 // same K nodes.  Cells whose list exceeds the capacity, and points outside the box, fall
-// back to scanning all nodes.  This replaces the approximate 512^3 look-up table of
-// Sec. 4.2 ("On-the-fly Radiance Fields") by an exact one.
+// back to scanning all nodes.  This is the default; the approximate look-up tables of
+// Sec. 4.2 ("On-the-fly Radiance Fields", built in k_lut.cu) replace the search when a
+// graph has them.
 //
 // Bound: FP32 ALU (about 10 operations per candidate key) plus L1-resident node reads.
-#include "invr_internal.cuh"
+#include "knn.cuh"
 
 namespace invr {
-
-constexpr float kKnnH = 2.0f / kKnnG;
-constexpr float kKnnRho = 0.8660254037844386f * kKnnH;  // half-diagonal sqrt(3)/2 h
-
-// Insert (key, id) into the ascending list; equal keys keep the earlier (lower) id first.
-template <int K>
-__device__ __forceinline__ void knn_insert(float key, int id, float (&keys)[K], int (&ids)[K]) {
-  if (!(key < keys[K - 1])) return;
-#pragma unroll
-  for (int m = 0; m < K; ++m) {
-    const bool lt = key < keys[m];
-    const float tk = lt ? keys[m] : key;
-    const int ti = lt ? ids[m] : id;
-    keys[m] = lt ? key : keys[m];
-    ids[m] = lt ? id : ids[m];
-    key = tk;
-    id = ti;
-  }
-}
-
-template <int K>
-__device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&keys)[K], int (&ids)[K]) {
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    keys[k] = INFINITY;
-    ids[k] = -1;
-  }
-  uint32_t n = kKnnOverflow;
-  int64_t cell = 0;
-  if (W.cand_n && fabsf(p.x) <= 1.001f && fabsf(p.y) <= 1.001f && fabsf(p.z) <= 1.001f) {
-    cell = grid_cell(p.x, kKnnG) + kKnnG * (grid_cell(p.y, kKnnG) + kKnnG * grid_cell(p.z, kKnnG));
-    n = __ldg(W.cand_n + cell);
-  }
-  if (n == kKnnOverflow) {
-    for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
-  } else {
-    const uint16_t* list = W.cand + cell * W.cap;
-    for (uint32_t c = 0; c < n; ++c) {
-      const int i = __ldg(list + c);
-      knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
-    }
-  }
-}
 
 __device__ __forceinline__ float3 rigid_inverse(const WarpDev& W, float3 p) {
   const float qx = p.x - W.t[0], qy = p.y - W.t[1], qz = p.z - W.t[2];
@@ -93,12 +51,57 @@ __device__ __forceinline__ float3 dq_inverse_apply(float4 br, float4 bd, float3 
   return make_float3(R00 * qx + R10 * qy + R20 * qz, R01 * qx + R11 * qy + R21 * qz, R02 * qx + R12 * qy + R22 * qz);
 }
 
+// (key, id) ascending insertion with the tie rule written out: the table's ids arrive in
+// canonical-key order, not in index order.
+template <int K>
+__device__ __forceinline__ void lut_insert(float key, int id, float (&keys)[K], int (&ids)[K]) {
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const bool lt = key < keys[m] || (key == keys[m] && id < ids[m]);
+    const float tk = lt ? keys[m] : key;
+    const int ti = lt ? ids[m] : id;
+    keys[m] = lt ? key : keys[m];
+    ids[m] = lt ? id : ids[m];
+    key = tk;
+    id = ti;
+  }
+}
+
+// Neighbour set from the tables (Sec. 4.2): the sample's live voxel (clamped into the
+// grid) -> the canonical voxel stored there -> its K nodes, ordered by the live key; a
+// hole (no canonical voxel landed there) falls back to the exact search.
+template <int K>
+__device__ __forceinline__ void lut_select(const WarpDev& W, float3 p, float (&keys)[K], int (&ids)[K]) {
+  const int G = W.lut_res;
+  const int64_t v = grid_cell(p.x, G) + (int64_t)G * (grid_cell(p.y, G) + (int64_t)G * grid_cell(p.z, G));
+  const uint32_t k = __ldg(W.lut_live + v);
+  if (k == kLutEmpty) {
+    knn_select<K>(W, p, keys, ids);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    keys[j] = INFINITY;
+    ids[j] = 0x7FFFFFFF;
+  }
+  const uint16_t* row = W.lut_canon + (int64_t)k * K;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int id = __ldg(row + j);
+    lut_insert<K>(knn_key(p, __ldg(W.x_live + id)), id, keys, ids);
+  }
+}
+
 template <int K>
 __device__ __forceinline__ float3 dqb_warp(const WarpDev& W, float3 p, int32_t* ids_out, int64_t ids_ld,
                                            int64_t i) {
   float keys[K];
   int ids[K];
-  knn_select<K>(W, p, keys, ids);
+  if (W.lut_live) {
+    lut_select<K>(W, p, keys, ids);
+  } else {
+    knn_select<K>(W, p, keys, ids);
+  }
   if (ids[0] < 0) return p;  // unreachable for finite p (every list holds >= K nodes)
   const float4 ref = __ldg(W.dq + 2 * ids[0]);
   float4 br = make_float4(0.f, 0.f, 0.f, 0.f), bd = br;

@@ -1,0 +1,55 @@
+// Exact K-nearest-node selection shared by the warp and the look-up-table builder: the
+// FP32 key ((dx*dx)+(dy*dy))+(dz*dz), ties to the lower node index, candidates from the
+// per-frame 64^3 candidate grid (or all nodes where a cell overflowed).
+#pragma once
+#include "invr_internal.cuh"
+
+namespace invr {
+
+constexpr float kKnnH = 2.0f / kKnnG;
+constexpr float kKnnRho = 0.8660254037844386f * kKnnH;  // half-diagonal sqrt(3)/2 h
+
+// Insert (key, id) into the ascending list; equal keys keep the earlier (lower) id first.
+// From the first slot whose key is larger, every later entry shifts down by one (an
+// entry carried down is never compared again, so entries with equal keys keep their order).
+template <int K>
+__device__ __forceinline__ void knn_insert(float key, int id, float (&keys)[K], int (&ids)[K]) {
+  if (!(key < keys[K - 1])) return;
+  bool shift = false;
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    shift = shift || key < keys[m];
+    const float tk = shift ? keys[m] : key;
+    const int ti = shift ? ids[m] : id;
+    keys[m] = shift ? key : keys[m];
+    ids[m] = shift ? id : ids[m];
+    key = tk;
+    id = ti;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&keys)[K], int (&ids)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    keys[k] = INFINITY;
+    ids[k] = -1;
+  }
+  uint32_t n = kKnnOverflow;
+  int64_t cell = 0;
+  if (W.cand_n && fabsf(p.x) <= 1.001f && fabsf(p.y) <= 1.001f && fabsf(p.z) <= 1.001f) {
+    cell = grid_cell(p.x, kKnnG) + kKnnG * (grid_cell(p.y, kKnnG) + kKnnG * grid_cell(p.z, kKnnG));
+    n = __ldg(W.cand_n + cell);
+  }
+  if (n == kKnnOverflow) {
+    for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
+  } else {
+    const uint16_t* list = W.cand + cell * W.cap;
+    for (uint32_t c = 0; c < n; ++c) {
+      const int i = __ldg(list + c);
+      knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
+    }
+  }
+}
+
+}  // namespace invr

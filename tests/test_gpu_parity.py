@@ -125,6 +125,23 @@ def test_nearest_nodes_bit_exact(env, n_nodes, K):
     np.testing.assert_allclose(host(vc), ovc, rtol=0, atol=2e-6)
 
 
+def test_nearest_nodes_exact_ties(env):
+    """Nodes at identical positions give equal keys: the lower index goes first, also when
+    a nearer node is inserted after the tied ones (the list shifts, it does not re-sort)."""
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(33)
+    g = synth.make_graph(rng, 256, K=4)
+    for a, b in ((3, 10), (3, 40), (100, 7), (200, 150), (201, 150)):
+        g.x_live[:, b] = g.x_live[:, a]
+    sv = synth.View(synth.make_field(rng, synth.CFG1_FIELD), graph=g)
+    side = Side(invr, ctx, oracle, sv)
+    p = np.concatenate([_probe_points(rng, g, 2000), g.x_live[:, [3, 100, 150]] + np.float32(1e-3)], axis=1)
+    p = p.astype(np.float32)
+    _, ids = invr.warp_points(ctx, side.view, cu(p), with_ids=True)
+    oids, _ = oracle.knn_points(side.oview.graph, p)
+    np.testing.assert_array_equal(host(ids), oids)
+
+
 def test_rigid_warp(env):
     invr, ctx, oracle = env
     rng = np.random.default_rng(32)
