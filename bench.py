@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-render", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-interleave", action="store_true")
+    ap.add_argument("--no-lut", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -392,6 +393,8 @@ def run_ours(args, rank, world, local):
                            "fp32_sequential": bt["fp32_sequential"]}
         out["single_batch_train"] = single
         tw = btw
+    if not args.no_lut:
+        out["lut_search"] = bench_lut(invr, args, flush, world, args.prec)
     if not args.no_interleave:
         out["interleave"] = bench_interleave(invr, args, args.prec)
     out["clocks"] = clocks.stop()      # sampled over every timed region above
@@ -503,6 +506,71 @@ def build_views(invr, ctx, w, prec):
         keep.append((f, g, occ))
         views.append(invr.View(f, g, 0, sv.rigid_dq, occ))
     return views, keep
+
+
+def bench_lut(invr, args, flush, world, prec_name, G=512):
+    """The look-up-table neighbour search (Sec. 4.2) against the exact search on the
+    single-batch train step, for two motions of the 2048-node graph: the workload's own
+    (every node rotated independently about the origin) and a spatially coherent
+    articulated pose.  Per motion: table build times, the warp kernel and the whole step,
+    and on the occupied samples of 2^15 rays the fraction in table holes, the fraction whose
+    table neighbour set equals the exact K nearest, and the canonical-position difference
+    of the two warps (median, 99th percentile)."""
+    import torch
+    from paper_2304_03184_b300 import synth
+    base = synth.train_step_workload(n_rays=args.rays)
+    b0 = base.batches[0]
+    g_art = synth.articulated_pose(np.random.default_rng(9), b0.view.graph)
+    out = {"workload": base.name, "resolution": G, "prec": prec_name}
+    for motion, g in (("independent_nodes", b0.view.graph), ("articulated", g_art)):
+        occ = b0.view.occupancy if g is b0.view.graph else synth.occupancy_near_nodes(g.x_live)
+        view_s = synth.View(b0.view.field, graph=g, occupancy=occ)
+        tw = synth.TrainWorkload(base.name, [synth.TrainBatch(b0.rays, view_s, b0.target)], base.fields,
+                                 base.n_samples)
+        ctx = invr.Context(torch.cuda.current_device())
+        tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
+        graph, view = keep[0][0], keep[0][2]
+        steps = max(5, args.steps // 4)
+        ms_exact, kt_exact = time_train(invr, ctx, tb, steps, args.warmup, flush, world)
+        stream = torch.cuda.current_stream()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        dq, xl = torch.from_numpy(g.dq).cuda(), torch.from_numpy(g.x_live).cuda()
+        torch.cuda.synchronize()
+        a.record(stream)
+        graph.enable_lut(G)                      # canonical field + this frame's live field
+        b.record(stream)
+        graph.set_pose(0, dq, xl)                # per frame: pack, candidate grid, live field
+        c.record(stream)
+        torch.cuda.synchronize()
+        enable_ms, pose_ms = a.elapsed_time(b), b.elapsed_time(c)
+        ms_lut, kt_lut = time_train(invr, ctx, tb, steps, args.warmup, flush, world)
+
+        o, d = tb.batches[0][0][:, :1 << 15].contiguous(), tb.batches[0][1][:, :1 << 15].contiguous()
+        count, _, pos = invr.ray_samples(ctx, o, d, tw.n_samples, view.occupancy)
+        keep_s = torch.arange(tw.n_samples, device="cuda")[None, :] < count[:, None].long()
+        p = pos[:, keep_s].contiguous()
+        vc_lut, ids_lut = invr.warp_points(ctx, view, p, with_ids=True)
+        _, live = graph.get_lut(0)
+        vox = torch.clamp(torch.floor(((p + 1.0) * 0.5) * G).long(), 0, G - 1)
+        hole = live[vox[0] + G * (vox[1] + G * vox[2])] == -1
+        del live
+        graph.disable_lut()
+        vc_exact, ids_exact = invr.warp_points(ctx, view, p, with_ids=True)
+        same = torch.all(torch.sort(ids_lut, dim=0)[0] == torch.sort(ids_exact, dim=0)[0], dim=0)
+        err = torch.linalg.vector_norm(vc_lut - vc_exact, dim=0)
+        ctx.sync()
+        S_nom = tb.batches[0][0].shape[1] * tw.n_samples
+        out[motion] = {
+            "enable_ms": round(enable_ms, 3), "set_pose_ms": round(pose_ms, 3),
+            "exact": {"value": round(world * S_nom / (ms_exact * 1e-3), 1), "ms_per_step": round(ms_exact, 3),
+                      "warp_ms": round(kt_exact["warp"][0] / steps, 4)},
+            "lut": {"value": round(world * S_nom / (ms_lut * 1e-3), 1), "ms_per_step": round(ms_lut, 3),
+                    "warp_ms": round(kt_lut["warp"][0] / steps, 4)},
+            "samples_checked": int(p.shape[1]), "hole_fraction": round(float(hole.float().mean()), 4),
+            "neighbour_set_agreement": round(float(same.float().mean()), 4),
+            "canonical_position_diff": {"median": float(err.median()), "p99": float(torch.quantile(err, 0.99))}}
+        del tb, fields, keep, graph, view, ctx
+    return out
 
 
 def bench_interleave(invr, args, prec_name):

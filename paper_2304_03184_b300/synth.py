@@ -216,6 +216,38 @@ def repose_graph(rng: np.random.Generator, g: Graph, max_deg: float = 15.0, max_
     return Graph(g.x_canon, dq.astype(np.float32), xl.astype(np.float32), g.K, g.radius)
 
 
+def _hamilton(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    return np.array([a[0] * b[0] - np.dot(a[1:], b[1:]), *(a[0] * b[1:] + b[0] * a[1:] + np.cross(a[1:], b[1:]))])
+
+
+def articulated_pose(rng: np.random.Generator, g: Graph, max_deg: float = 15.0, max_t: float = 0.05,
+                     max_twist: float = 30.0) -> Graph:
+    """A spatially coherent per-frame pose of the canonical graph: a twist about the
+    vertical axis through the origin whose angle grows linearly with height (beta y/0.8,
+    clamped, beta ~ U(-max_twist, max_twist) deg), followed by one global motion (random axis,
+    U(0, max_deg) deg about the origin, translation uniform in the max_t ball).  Nearby
+    nodes get nearby motions, as the tracker's regularised motion field does (unlike
+    repose_graph, which moves every node independently)."""
+    n = g.x_canon.shape[1]
+    axis = random_axes(rng, 1)[0]
+    ang = math.radians(rng.uniform(0.0, max_deg))
+    t = random_in_ball(rng, 1, max_t)[0]
+    beta = math.radians(rng.uniform(-max_twist, max_twist))
+    qg = np.array([math.cos(0.5 * ang), *(math.sin(0.5 * ang) * axis)])
+    Rg = rodrigues(axis, ang)
+    dq = np.zeros((8, n))
+    xl = np.zeros((3, n))
+    ey = np.array([0.0, 1.0, 0.0])
+    for i in range(n):
+        x = g.x_canon[:, i].astype(np.float64)
+        a = beta * min(1.0, max(-1.0, x[1] / 0.8))
+        qr = _hamilton(qg, np.array([math.cos(0.5 * a), 0.0, math.sin(0.5 * a), 0.0]))
+        qd = 0.5 * _hamilton(np.array([0.0, *t]), qr)
+        dq[:, i] = np.concatenate([qr, qd])
+        xl[:, i] = Rg @ (rodrigues(ey, a) @ x) + t
+    return Graph(g.x_canon, dq.astype(np.float32), xl.astype(np.float32), g.K, g.radius)
+
+
 def make_object_pose(rng: np.random.Generator, angle_deg: float = 30.0, t_len: float = 0.2):
     """(dual quaternion float32[8], R, t) of the object's canonical -> live motion."""
     axis = random_axes(rng, 1)[0]
