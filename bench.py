@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-interleave", action="store_true")
     ap.add_argument("--no-lut", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the batched key-frame step (no single-batch, FP32, render, LUT sections)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -282,6 +284,33 @@ def roofline(ktime, tw, R, S_occ, peaks, l2=None):
     return None
 
 
+def apply_batched(out, bt, invr, ctx, args, world, peaks):
+    """Fill the bench line from the batched key-frame run (the headline workload)."""
+    bvalue = world * bt["S_nom"] / (bt["ms"] * 1e-3)
+    btw = bt["tw"]
+    out["value"] = round(bvalue, 1)
+    out["ms_per_step"] = round(bt["ms"], 3)
+    out["config"] = {"workload": bt["workload"], "rays": bt["rays"], "samples_per_ray": bt["samples_per_ray"],
+                     "occupied_samples": bt["occupied_samples"], "batches": bt["batches"],
+                     "fields": len(btw.fields), "parallelism": f"replicas{world}",
+                     "l2": "flushed between timed steps (256 MiB write)", "prec": args.prec,
+                     "launch": "one CUDA graph per step (all batches per stage launch)", "tune": bt["tune"]}
+    out["e2e"] = bt["e2e"]
+    bR, bS = bt["rays"], bt["occupied_samples"]
+    l2 = measure_l2(invr, ctx)
+    out["l2_probe"] = l2
+    out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks, l2)
+    nsteps = max(5, args.steps // 4)
+    out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
+    per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
+    out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
+                                    / nsteps * args.steps))
+    out["variants"] = {args.prec + "_graph": {"value": round(bvalue, 1), "ms_per_step": round(bt["ms"], 3)},
+                       args.prec + "_eager": {"value": round(world * bt["S_nom"] / (bt["eager_ms"] * 1e-3), 1),
+                                              "ms_per_step": round(bt["eager_ms"], 3)},
+                       "fp32_sequential": bt["fp32_sequential"]}
+
+
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
@@ -295,6 +324,15 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 126 MB L2
     clocks = ClockSampler(local)
     clocks.start()
+    if args.headline_only:        # the batched key-frame step alone (clean launch lists)
+        out = {"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else f"{args.prec}-mlp/f32",
+               "data": "synthetic", "clocks": None}
+        bt = bench_batched(invr, args, flush, world, args.prec, with_fp32=False)
+        apply_batched(out, bt, invr, ctx, args, world, peaks)
+        out["clocks"] = clocks.stop()
+        return out, bt["tw"]
 
     # the requested precision, then the other two for the mixed-vs-FP32 comparison
     order = [args.prec] + [p for p in ("fp32", "fp16", "bf16") if p != args.prec]
@@ -368,31 +406,9 @@ def run_ours(args, rank, world, local):
            "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(ktime.items())}}
     if not args.no_batched:
         bt = bench_batched(invr, args, flush, world, args.prec)
-        bvalue = world * bt["S_nom"] / (bt["ms"] * 1e-3)
-        btw = bt["tw"]
-        out["value"] = round(bvalue, 1)
-        out["ms_per_step"] = round(bt["ms"], 3)
-        out["config"] = {"workload": bt["workload"], "rays": bt["rays"], "samples_per_ray": bt["samples_per_ray"],
-                         "occupied_samples": bt["occupied_samples"], "batches": bt["batches"],
-                         "fields": len(btw.fields), "parallelism": f"replicas{world}",
-                         "l2": "flushed between timed steps (256 MiB write)", "prec": args.prec,
-                         "launch": "one CUDA graph per step (all batches per stage launch)", "tune": bt["tune"]}
-        out["e2e"] = bt["e2e"]
-        bR, bS = bt["rays"], bt["occupied_samples"]
-        l2 = measure_l2(invr, ctx)
-        out["l2_probe"] = l2
-        out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks, l2)
-        nsteps = max(5, args.steps // 4)
-        out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
-        per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
-        out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
-                                        / nsteps * args.steps))
-        out["variants"] = {args.prec + "_graph": {"value": round(bvalue, 1), "ms_per_step": round(bt["ms"], 3)},
-                           args.prec + "_eager": {"value": round(world * bt["S_nom"] / (bt["eager_ms"] * 1e-3), 1),
-                                                  "ms_per_step": round(bt["eager_ms"], 3)},
-                           "fp32_sequential": bt["fp32_sequential"]}
+        apply_batched(out, bt, invr, ctx, args, world, peaks)
         out["single_batch_train"] = single
-        tw = btw
+        tw = bt["tw"]
     if not args.no_lut:
         out["lut_search"] = bench_lut(invr, args, flush, world, args.prec)
     if not args.no_interleave:
@@ -411,8 +427,9 @@ def frames_of(tw):
     return out
 
 
-def bench_batched(invr, args, flush, world, prec_name):
-    """Headline: batched key-frame step, mixed precision, autotuned, one CUDA graph per step."""
+def bench_batched(invr, args, flush, world, prec_name, with_fp32=True):
+    """Headline: batched key-frame step, mixed precision, autotuned, one CUDA graph per step;
+    with_fp32 adds the plain comparison (the same frames as sequential FP32 calls)."""
     import torch
     from paper_2304_03184_b300 import synth
     tw = synth.keyframe_batch_workload()
@@ -467,6 +484,11 @@ def bench_batched(invr, args, flush, world, prec_name):
     e_ms = a.elapsed_time(b) / args.steps
     e2e = {"value": round(world * S_nom / (e_ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(e_ms, 3),
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+    out = {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples, "occupied_samples": S_occ,
+           "batches": len(tw.batches), "S_nom": S_nom, "ms": ms, "eager_ms": eager_ms, "ktime": ktime,
+           "tune": tune, "e2e": e2e, "tw": tw, "fp32_sequential": None}
+    if not with_fp32:
+        return out
     # plain path: the same frames as 8 sequential FP32 calls (2 batches each), no graph
     ctx32 = invr.Context(torch.cuda.current_device())
     per_frame = [build_train(invr, ctx32, fw, PRECS["fp32"]) for fw in frames_of(tw)]
@@ -485,11 +507,9 @@ def bench_batched(invr, args, flush, world, prec_name):
     torch.cuda.synchronize()
     ms32 = float(np.mean([a.elapsed_time(b) for a, b in ev32]))
     ctx32.sync()
-    return {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples, "occupied_samples": S_occ,
-            "batches": len(tw.batches), "S_nom": S_nom, "ms": ms, "eager_ms": eager_ms, "ktime": ktime,
-            "tune": tune, "e2e": e2e, "tw": tw,
-            "fp32_sequential": {"value": round(world * S_nom / (ms32 * 1e-3), 1), "ms_per_step": round(ms32, 3),
-                                "launches": "8 sequential train_step calls (2 batches each), FP32, no graph"}}
+    out["fp32_sequential"] = {"value": round(world * S_nom / (ms32 * 1e-3), 1), "ms_per_step": round(ms32, 3),
+                              "launches": "8 sequential train_step calls (2 batches each), FP32, no graph"}
+    return out
 
 
 def build_views(invr, ctx, w, prec):
