@@ -705,6 +705,88 @@ void orc_render(int64_t n_rays, const float* o, const float* d, int n_samples, d
     }
 }
 
+/* Joint per-sample compositing of the human field (view 0) and the object field (view 1)
+ * along each ray, the alternative to laying one field's image over the other's: both
+ * fields are sampled at the same t_j (same ray, same sample count), so at every sample the
+ * densities add and the colours mix in proportion to density,
+ *   sigma = sigma_h + sigma_o,  c = (sigma_h c_h + sigma_o c_o) / sigma,
+ * a field whose occupancy bit is clear contributing sigma = 0 there, and the mixture is
+ * composited front to back with early termination (T < t_eps) as for one field.
+ * rgba[4][R], depth[R]; n_used[R] samples composited (samples where either field is occupied). */
+void orc_render_joint(int64_t n_rays, const float* o, const float* d, int n_samples, double t_eps,
+                      const orc_view* views, double* rgba, double* depth, int* n_used)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < n_rays; ++r) {
+        float ro[3] = {o[r], o[n_rays + r], o[2 * n_rays + r]};
+        float rd[3] = {d[r], d[n_rays + r], d[2 * n_rays + r]};
+        double out[5] = {0, 0, 0, 0, 0};
+        int n = 0;
+        float tn, dt;
+        if (orc_ray_setup(ro, rd, n_samples, &tn, &dt)) {
+            double T = 1.0;
+            for (int j = 0; j < n_samples; ++j) {
+                float t, p[3];
+                orc_sample(ro, rd, tn, dt, j, &t, p);
+                double sig[2] = {0.0, 0.0}, col[2][3] = {{0, 0, 0}, {0, 0, 0}};
+                int any = 0;
+                for (int v = 0; v < 2; ++v) {
+                    if (views[v].occupancy && !orc_occupied(views[v].occupancy, p)) continue;
+                    orc_act a;
+                    orc_eval_sample(&views[v], p, &a, NULL, NULL);
+                    sig[v] = a.sigma;
+                    for (int c = 0; c < 3; ++c) col[v][c] = a.rgb[c];
+                    any = 1;
+                }
+                if (!any) continue;
+                double sigma = sig[0] + sig[1];
+                double alpha = 1.0 - exp(-sigma * (double)dt);
+                double w = T * alpha;
+                for (int c = 0; c < 3; ++c) {
+                    double mix = sigma > 0.0 ? (sig[0] * col[0][c] + sig[1] * col[1][c]) / sigma : 0.0;
+                    out[c] += w * mix;
+                }
+                out[3] += w;
+                out[4] += w * (double)t;
+                ++n;
+                T = T * (1.0 - alpha);
+                if (T < t_eps) break;
+            }
+        }
+        for (int c = 0; c < 4; ++c) rgba[(int64_t)c * n_rays + r] = out[c];
+        depth[r] = out[4];
+        n_used[r] = n;
+    }
+}
+
+/* ---------------------------------------------------------------- occupancy grid */
+/* Density-driven maintenance of a view's 128^3 live-space occupancy bitfield (the given
+ * bitfield of the hot path, kept up to date per frame): the density at every cell centre
+ * ((i + 1/2) 2/128 - 1 per axis, FP32 recipe) is evaluated through the view's warp, encoding
+ * and MLPs; density[c] = max(decay * density[c], sigma); the bit of cell c (index
+ * x + 128 (y + 128 z), bit c & 31 of word c >> 5) is set iff density[c] > threshold. */
+void orc_occupancy_update(const orc_view* v, double decay, double threshold, double* density, uint32_t* bits)
+{
+    const int G = ORC_OCC_RES;
+    const int64_t n = (int64_t)G * G * G;
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+        float p[3];
+        int64_t ijk[3] = {c % G, (c / G) % G, c / ((int64_t)G * G)};
+        for (int a = 0; a < 3; ++a) p[a] = ((float)ijk[a] + 0.5f) * (2.0f / (float)G) - 1.0f;
+        orc_act act;
+        orc_eval_sample(v, p, &act, NULL, NULL);
+        double dn = decay * density[c];
+        density[c] = dn > act.sigma ? dn : act.sigma;
+    }
+    for (int64_t w = 0; w < n / 32; ++w) {
+        uint32_t m = 0;
+        for (int b = 0; b < 32; ++b)
+            if (density[w * 32 + b] > threshold) m |= 1u << b;
+        bits[w] = m;
+    }
+}
+
 /* ------------------------------------------------------------------ loss + gradient */
 /* Huber penalty with threshold delta and its derivative. */
 double orc_huber(double x, double delta)

@@ -38,6 +38,11 @@ What pins each oracle function (tests/test_oracle_pins.py, run with -m "not gpu"
                         the masked depth L1 term (Sec. 4.4); central differences; a binary
                         mask equals cutting the batch down to the masked-in rays
   Adam                  first and second steps in closed form
+  joint compositing     an empty second field reproduces the single-field render; two
+                        constant fields (sigma = 1 each, c = 1/2) give A = 1 - exp(-2 L)
+  occupancy update      a field built so that sigma = exp(max(a.x + b, 0)) exactly (affine
+                        dense level, identity-like first layers) gives that density at
+                        every cell centre; decay keeps max(decay d, sigma); bits = d > thr
 """
 from __future__ import annotations
 
@@ -113,6 +118,8 @@ def _declare(L):
     L.orc_huber.restype = C.c_double
     L.orc_render.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, C.c_int, P, P, P, P, P, P, P]
     L.orc_render.restype = None
+    L.orc_render_joint.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, P, P, P, P]
+    L.orc_occupancy_update.argtypes = [P, C.c_double, C.c_double, P, P]
     L.orc_lut_canon_knn.argtypes = [C.c_int, C.c_int, P, C.c_int, P]
     L.orc_lut_live_index.argtypes = [C.c_int, C.c_int, C.c_float, P, P, C.c_int, P, P]
     L.orc_lut_exp_points.argtypes = [C.c_int64, P, P]
@@ -360,6 +367,33 @@ def render(o, d, n_samples: int, t_eps: float, views: Sequence[View]) -> RenderR
     lib().orc_render(R, _p(o), _p(d), n_samples, t_eps, V, C.cast(arr, C.c_void_p), _p(rgba_v),
                      _p(depth_v), _p(n_used), _p(T_end), _p(rgba), _p(depth))
     return RenderResult(rgba, depth, rgba_v, depth_v, n_used, T_end)
+
+
+def render_joint(o, d, n_samples: int, t_eps: float, human: View, obj: View):
+    """Joint per-sample compositing of the two fields: (rgba [4][R], depth [R], n_used [R])."""
+    o, d = _f32(o), _f32(d)
+    R = o.shape[1]
+    arr = (CView * 2)(human._c, obj._c)
+    rgba = np.zeros((4, R))
+    depth = np.zeros(R)
+    n_used = np.zeros(R, np.int32)
+    lib().orc_render_joint(R, _p(o), _p(d), n_samples, t_eps, C.cast(arr, C.c_void_p), _p(rgba), _p(depth),
+                           _p(n_used))
+    return rgba, depth, n_used
+
+
+def occupancy_update(view: View, decay: float, threshold: float, density=None):
+    """One density-driven update of the 128^3 live-space occupancy: (density [128^3] FP64,
+    bits [65536] uint32).  `density` (updated in place if given) starts at zero otherwise."""
+    n = OCC_RES ** 3
+    density = np.zeros(n) if density is None else density
+    assert density.dtype == np.float64 and density.shape == (n,)
+    bits = np.zeros(n // 32, np.uint32)
+    lib().orc_occupancy_update(C.byref(view._c), decay, threshold, _p(density), _p(bits))
+    return density, bits
+
+
+OCC_RES = 128
 
 
 class TrainBatch:

@@ -740,3 +740,87 @@ def test_lut_neighbours_and_warp(oracle):
     vox = np.floor(((np.clip(near, -1, 1) + np.float32(1)) * np.float32(0.5)) * np.float32(G)).astype(np.int64)
     vox = np.clip(vox, 0, G - 1)
     assert np.array_equal(~from_lut, holes[vox[0] + G * (vox[1] + G * vox[2])])
+
+
+# ----------------------------------- joint compositing and occupancy maintenance
+def test_joint_compositing_with_an_empty_field_is_the_single_render(oracle):
+    rng = np.random.default_rng(71)
+    w = synth.two_field_render(width=24, height=24, n_samples=48, n_nodes=256)
+    hv = oracle.View.from_synth(w.views[0])
+    ov = oracle.View.from_synth(w.views[1])
+    empty = oracle.View(ov.field, rigid_dq=w.views[1].rigid_dq, occupancy=np.zeros(128 ** 3 // 32, np.uint32))
+    rgba, depth, n_used = oracle.render_joint(w.rays.o, w.rays.d, w.n_samples, w.t_eps, hv, empty)
+    ref = oracle.render(w.rays.o, w.rays.d, w.n_samples, w.t_eps, [hv])
+    assert ref.rgba[3].max() > 0.2
+    np.testing.assert_allclose(rgba, ref.rgba, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(depth, ref.depth, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(n_used, ref.n_used[0])
+
+
+def test_joint_compositing_two_constant_fields_closed_form(oracle):
+    """sigma = 1 and c = 1/2 in both fields, no occupancy: the mixture has sigma = 2 and
+    c = 1/2, so A = 1 - exp(-2 (t_f - t_n)) and C = A/2 per channel."""
+    rng = np.random.default_rng(72)
+    f1 = oracle.Field.from_params(tiny_field(rng, zero=True))
+    f2 = oracle.Field.from_params(tiny_field(rng, zero=True))
+    g = synth.make_graph(rng, 16, K=4)
+    dq, _, _ = synth.make_object_pose(rng)
+    hv = oracle.View(f1, graph=oracle.Graph.from_synth(g))
+    ov = oracle.View(f2, rigid_dq=dq)
+    rays = synth.pinhole_rays(10, 10, 50.0, (0.0, 0.0, 2.5))
+    N = 40
+    rgba, depth, n_used = oracle.render_joint(rays.o, rays.d, N, 0.0, hv, ov)
+    hit, tn, dt, _, _ = oracle.ray_samples(rays.o, rays.d, N)
+    h = hit.astype(bool)
+    A = np.where(h, 1.0 - np.exp(-2.0 * N * dt.astype(np.float64)), 0.0)
+    np.testing.assert_allclose(rgba[3], A, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(rgba[:3], np.broadcast_to(0.5 * A, (3, rays.n)), rtol=0, atol=1e-13)
+    assert np.all(n_used[h] == N) and np.all(n_used[~h] == 0)
+
+
+def _affine_density_field(oracle, a0, a):
+    """A field with sigma(x) = exp(max(a0 + a . q, 0)) exactly, q = clamp((x+1)/2, 0, 1) N_0:
+    level 0 (dense) holds the affine function of the vertex coordinates in feature 0, and
+    the first layers pass feature 0 through (W1[0][0] = W2[0][0] = W3[0][0] = 1, all other
+    weights 0, so c = 1/2)."""
+    rng = np.random.default_rng(0)
+    fp = tiny_field(rng, zero=True)
+    d = fp.desc
+    tables = np.zeros((d.L, d.T, d.F))
+    res = oracle.level_res(d.N_min, d.growth, 0)
+    assert oracle.level_dense(res, d.log2_T)
+    for z in range(res + 1):
+        for y in range(res + 1):
+            for x in range(res + 1):
+                tables[0, oracle.vertex_index(res, d.log2_T, x, y, z), 0] = a0 + np.dot(a, [x, y, z])
+    weights = np.zeros(d.n_weight_params())
+    shapes = d.weight_shapes()
+    off = 0
+    for k, (r, c) in enumerate(shapes):
+        if k < 3:
+            weights[off] = 1.0                            # W_k[0][0]
+        off += r * c
+    return oracle.Field(d, tables, weights), res
+
+
+def test_occupancy_update_affine_density(oracle):
+    a0, a = -1.0, np.array([0.5, 0.2, -0.3])
+    f, res = _affine_density_field(oracle, a0, a)
+    ident = np.array([1, 0, 0, 0, 0, 0, 0, 0], np.float32)
+    v = oracle.View(f, rigid_dq=ident)
+    G = oracle.OCC_RES
+    c = (np.arange(G, dtype=np.float32) + np.float32(0.5)) * np.float32(2.0 / G) - np.float32(1.0)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    q = np.stack([x.ravel(), y.ravel(), z.ravel()]).astype(np.float64)
+    q = np.clip((q + 1.0) * 0.5, 0.0, 1.0) * res
+    want = np.exp(np.maximum(a0 + a @ q, 0.0))
+    thr = 1.2
+    dens, bits = oracle.occupancy_update(v, 0.9, thr)
+    np.testing.assert_allclose(dens, want, rtol=1e-12)
+    np.testing.assert_array_equal(bits, synth.pack_bits(want > thr))
+    assert 0 < (want > thr).mean() < 1
+    # a second update with a constant-density field (sigma = 1) and decay 1/2
+    zero = oracle.View(oracle.Field.from_params(tiny_field(np.random.default_rng(1), zero=True)), rigid_dq=ident)
+    dens2, bits2 = oracle.occupancy_update(zero, 0.5, thr, dens.copy())
+    np.testing.assert_allclose(dens2, np.maximum(0.5 * want, 1.0), rtol=1e-12)
+    np.testing.assert_array_equal(bits2, synth.pack_bits(np.maximum(0.5 * want, 1.0) > thr))
