@@ -206,6 +206,28 @@ typedef struct {
 
 invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* args, invr_stream stream);
 
+/* Joint per-sample compositing of the two views of `args` (n_views = 2: the human field,
+ * then the object field), the alternative to laying one field's image over the other's
+ * (Sec. 4.3 composes the two images by depth; this mixes them inside the volume): both
+ * fields are sampled at the same t_j, densities add and colours mix in proportion to
+ * density, sigma = sigma_h + sigma_o, c = (sigma_h c_h + sigma_o c_o) / sigma (a field whose
+ * occupancy bit is clear contributes sigma = 0), and the mixture is composited front to
+ * back with early termination.  Outputs as invr_render_rays; n_views != 2 is INVR_E_ARG. */
+invr_status invr_render_rays_joint(invr_ctx ctx, const invr_render_args* args, invr_stream stream);
+
+/* Density-driven maintenance of a view's 128^3 live-space occupancy bitfield (the layout of
+ * invr_field_view.occupancy_dev).  The density at every cell centre ((i + 1/2) 2/128 - 1 per
+ * axis) is evaluated through the view's warp (its frame's pose), encoding and MLPs; then per
+ * cell density_dev[c] = max(decay * density_dev[c], sigma) and the bit of cell c
+ * (x + 128 (y + 128 z); bit c & 31 of word c >> 5) is set iff density_dev[c] > threshold.
+ * The view's own occupancy_dev is not read.  density_dev: [128^3] floats, caller-owned,
+ * updated in place (start from zeros); bits_dev: [65536] words, written.  The paper takes
+ * the occupied space as given; this keeps it current as the fields train and the poses
+ * change.  Asynchronous on `stream`; scratch of ~350 MB is taken from the stream-ordered
+ * allocator.  decay outside [0, 1] or null pointers: INVR_E_ARG. */
+invr_status invr_occupancy_update(invr_ctx ctx, const invr_field_view* view, float decay, float threshold,
+                                  float* density_dev, uint32_t* bits_dev, invr_stream stream);
+
 /* ------------------------------------------------------------------ training */
 /* Training losses.
  *  INVR_LOSS_HUBER: Huber penalty (threshold huber_delta) of rendered colour minus target,

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "invr_ctx_enable_timing": [_VP, _I],
     "invr_ctx_timing": [_VP, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64), _I],
     "invr_query_points_noalloc": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
+    "invr_render_rays_joint": [_VP, C.POINTER(invr_render_args), _VP],
+    "invr_occupancy_update": [_VP, C.POINTER(invr_field_view), C.c_float, C.c_float, _VP, _VP, _VP],
     "invr_graph_enable_lut": [_VP, C.c_int, _VP],
     "invr_graph_disable_lut": [_VP],
     "invr_graph_get_lut": [_VP, C.c_int, _VP, _VP, _VP],
@@ -323,16 +325,31 @@ def _views_array(views: Sequence[View]):
 
 
 # ----------------------------------------------------------------------- calls
-def render_rays(ctx: Context, o, d, n_samples: int, t_eps: float, views: Sequence[View]):
-    """Render R rays (o, d: [3][R] CUDA float32) through 1 or 2 views -> (rgba [4][R], depth [R])."""
+def render_rays(ctx: Context, o, d, n_samples: int, t_eps: float, views: Sequence[View], joint: bool = False):
+    """Render R rays (o, d: [3][R] CUDA float32) through 1 or 2 views -> (rgba [4][R], depth [R]).
+    Two views are composed by depth (the nearer image over the farther) or, with joint=True,
+    composited together per sample (invr_render_rays_joint)."""
     torch = _torch()
     R = o.shape[1]
     rgba = torch.empty((4, R), device=o.device)
     depth = torch.empty(R, device=o.device)
     arr = _views_array(views)
     args = invr_render_args(R, _ptr(o), _ptr(d), n_samples, t_eps, len(views), arr, _ptr(rgba), _ptr(depth))
-    _check(lib().invr_render_rays(ctx.h, C.byref(args), _stream()), ctx.h)
+    fn = lib().invr_render_rays_joint if joint else lib().invr_render_rays
+    _check(fn(ctx.h, C.byref(args), _stream()), ctx.h)
     return rgba, depth
+
+
+OCC_RES = 128
+
+
+def occupancy_update(ctx: Context, view: View, density, bits, decay: float = 0.95, threshold: float = 0.01):
+    """invr_occupancy_update: density [128^3] float32 (updated in place) and bits [65536]
+    int32 / uint32 words (written) on the device."""
+    cv = view.c()
+    _check(lib().invr_occupancy_update(ctx.h, C.byref(cv), decay, threshold, _ptr(density), _ptr(bits), _stream()),
+           ctx.h)
+    return density, bits
 
 
 INVR_LOSS_HUBER, INVR_LOSS_PAPER = 0, 1

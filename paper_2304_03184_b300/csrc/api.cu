@@ -911,9 +911,10 @@ invr_status invr_graph_destroy(invr_graph g) {
   return INVR_OK;
 }
 
-invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* a, invr_stream stream) {
+static invr_status render(invr_ctx ctx, const invr_render_args* a, bool joint, invr_stream stream) {
   if (!ctx || !a) return INVR_E_ARG;
   if (a->n_views < 1 || a->n_views > 2 || !a->views) return fail(ctx, INVR_E_ARG, "render takes 1 or 2 views");
+  if (joint && a->n_views != 2) return fail(ctx, INVR_E_ARG, "joint compositing takes 2 views");
   if (a->n_rays > 0 && (!a->rgba_dev || !a->depth_dev)) return fail(ctx, INVR_E_ARG, "null output pointer");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -929,8 +930,21 @@ invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* a, invr_strea
   P.ws = ctx->ws;
   ctx->fwd_valid = false;
   INVR_CUDA(ctx, run_forward(ctx, P, s));
-  INVR_CUDA(ctx, TIMED(ctx, "composite_render", s, launch_composite_render(P, a->n_rays, a->rgba_dev, a->depth_dev, s)));
+  if (joint) {
+    INVR_CUDA(ctx, TIMED(ctx, "composite_joint", s, launch_composite_joint(P, a->n_rays, a->rgba_dev, a->depth_dev, s)));
+  } else {
+    INVR_CUDA(ctx, TIMED(ctx, "composite_render", s,
+                         launch_composite_render(P, a->n_rays, a->rgba_dev, a->depth_dev, s)));
+  }
   return INVR_OK;
+}
+
+invr_status invr_render_rays(invr_ctx ctx, const invr_render_args* a, invr_stream stream) {
+  return render(ctx, a, false, stream);
+}
+
+invr_status invr_render_rays_joint(invr_ctx ctx, const invr_render_args* a, invr_stream stream) {
+  return render(ctx, a, true, stream);
 }
 
 invr_status invr_field_forward_train(invr_ctx ctx, const invr_train_args* a, invr_stream stream) {
@@ -1059,6 +1073,42 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
                               : launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->wait_limit, ctx->num_sms, s);
   cudaFreeAsync(vc, s);
   cudaFreeAsync(feat, s);
+  INVR_CUDA(ctx, e);
+  return INVR_OK;
+}
+
+invr_status invr_occupancy_update(invr_ctx ctx, const invr_field_view* view, float decay, float threshold,
+                                  float* density, uint32_t* bits, invr_stream stream) {
+  if (!ctx || !view) return INVR_E_ARG;
+  if (!density || !bits) return fail(ctx, INVR_E_ARG, "null density or bits");
+  if (!(decay >= 0.0f && decay <= 1.0f)) return fail(ctx, INVR_E_ARG, "decay must lie in [0, 1]");
+  invr_status st = check_field(ctx, view->field);
+  if (st != INVR_OK) return st;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WarpDev W;
+  st = warp_dev(ctx, *view, W);
+  if (st != INVR_OK) return st;
+  const int64_t n = (int64_t)kOccRes * kOccRes * kOccRes;
+  const FieldDev F = field_dev(view->field);
+  float *p = nullptr, *vc = nullptr, *feat = nullptr, *out = nullptr;
+  INVR_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void**>(&p), 3 * n * sizeof(float), s));
+  INVR_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void**>(&vc), 3 * n * sizeof(float), s));
+  INVR_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void**>(&feat), (size_t)view->field->desc.mlp_in * n * sizeof(float), s));
+  INVR_CUDA(ctx, cudaMallocAsync(reinterpret_cast<void**>(&out), 4 * n * sizeof(float), s));
+  cudaError_t e = TIMED(ctx, "occ_centres", s, launch_occ_centres(p, n, s));
+  if (e == cudaSuccess) e = TIMED(ctx, "warp_points", s, launch_warp_points(W, n, p, vc, nullptr, s));
+  if (e == cudaSuccess) e = TIMED(ctx, "encode_points", s, launch_encode_points(F, n, vc, feat, nullptr, s));
+  if (e == cudaSuccess)
+    e = TIMED(ctx, "mlp_points", s,
+              F.mlp_kind == kMlpF32 ? launch_mlp_points_f32(F, n, feat, out, ctx->num_sms, s)
+                                    : launch_mlp_points_tc(F, n, feat, out, ctx->status, ctx->wait_limit,
+                                                           ctx->num_sms, s));
+  if (e == cudaSuccess) e = TIMED(ctx, "occ_update", s, launch_occ_update(out, n, decay, threshold, density, bits, s));
+  cudaFreeAsync(p, s);
+  cudaFreeAsync(vc, s);
+  cudaFreeAsync(feat, s);
+  cudaFreeAsync(out, s);
   INVR_CUDA(ctx, e);
   return INVR_OK;
 }

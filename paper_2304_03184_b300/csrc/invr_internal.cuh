@@ -54,7 +54,12 @@ struct WarpDev {
   const uint16_t* cand_n;   // [G^3] candidate count, kKnnOverflow = use all nodes
   int n_nodes, K, cap;
   float inv_r2;             // 1 / radius^2
-  // look-up-table neighbour search (Sec. 4.2); lut_live == null: exact search
+  // occupancy maintenance
+cudaError_t launch_occ_centres(float* p, int64_t n, cudaStream_t s);
+cudaError_t launch_occ_update(const float* sigma, int64_t n, float decay, float threshold, float* density,
+                              uint32_t* bits, cudaStream_t s);
+
+// look-up-table neighbour search (Sec. 4.2); lut_live == null: exact search
   int lut_res;              // G
   const uint16_t* lut_canon;  // [G^3][K] canonical KNN field
   const uint32_t* lut_live;   // [G^3] live voxel -> canonical voxel, kLutEmpty = none
@@ -241,6 +246,7 @@ cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
                                  uint32_t wait_limit, int num_sms, cudaStream_t s);
 constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // polls of try_wait: a few seconds
+cudaError_t launch_composite_joint(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s);
 cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s);
 cudaError_t launch_composite_train(const Plan& P, float* loss, cudaStream_t s);
 cudaError_t launch_adam(float* params, const float* grads_in, float* grads_zero, float* m, float* v, int64_t n,
@@ -262,6 +268,11 @@ cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, f
                                  cudaStream_t s);
 cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
                                   cudaStream_t s);
+
+// occupancy maintenance
+cudaError_t launch_occ_centres(float* p, int64_t n, cudaStream_t s);
+cudaError_t launch_occ_update(const float* sigma, int64_t n, float decay, float threshold, float* density,
+                              uint32_t* bits, cudaStream_t s);
 
 // look-up-table neighbour search (Sec. 4.2)
 cudaError_t launch_pack_points(const float* x_soa, int n, float4* out, cudaStream_t s);

@@ -6,7 +6,8 @@
 //   C = sum T_j alpha_j c_j,  A = sum T_j alpha_j,  D = sum T_j alpha_j t_j,
 // over the occupied samples in order, stopping after the first with T_{j+1} < t_eps.
 // Two views (human, object): the nearer by expected depth (D_h A_o <= D_o A_h, ties to
-// the human) is laid over the farther: X = X_n + (1 - A_n) X_f for X in {C, A, D}.
+// the human) is laid over the farther: X = X_n + (1 - A_n) X_f for X in {C, A, D}; or,
+// jointly per sample (k_composite_joint), densities added and colours mixed by density.
 //
 // Training adjoint per ray (k <= stop):
 //   dC/dc_j = T_j alpha_j,   dC/dsigma_j = dt (T_{j+1} c_j - (C - sum_{k<=j} T_k alpha_k c_k))
@@ -89,6 +90,70 @@ __global__ void __launch_bounds__(256) k_composite_render(const __grid_constant_
 
 cudaError_t launch_composite_render(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s) {
   if (n_rays > 0) k_composite_render<<<ceil_div(n_rays, 256), 256, 0, s>>>(P, n_rays, rgba, depth);
+  return cudaGetLastError();
+}
+
+// Joint per-sample compositing of two views (human = view 0, object = view 1) of the same
+// rays: both are sampled at the same t_j, so the two compacted sample lists of a ray merge
+// by t; at a shared t_j the densities add and the colours mix in proportion to density,
+// and the mixture is composited front to back with early termination.
+__global__ void __launch_bounds__(256) k_composite_joint(const __grid_constant__ Plan P, int64_t n_rays,
+                                                         float* rgba, float* depth) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rays) return;
+  if (P.ws.view_base[P.n_views] > P.ws.S_cap) return;
+  const int64_t S_cap = P.ws.S_cap;
+  float out[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float dt = 0.0f;
+  if (ray_dt(P.v[0], r, P.n_samples, dt)) {
+    const int64_t g0 = P.v[0].ray_begin + r, g1 = P.v[1].ray_begin + r;
+    int64_t i = P.ws.ray_first[g0], k = P.ws.ray_first[g1];
+    const int64_t i_end = i + P.ws.ray_count[g0], k_end = k + P.ws.ray_count[g1];
+    float T = 1.0f;
+    while (i < i_end || k < k_end) {
+      const float ti = i < i_end ? P.ws.s_t[i] : INFINITY;
+      const float tk = k < k_end ? P.ws.s_t[k] : INFINITY;
+      const float t = fminf(ti, tk);
+      float sig = 0.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+      if (ti == t) {
+        const float si = P.ws.out[i];
+        sig += si;
+        cr = fmaf(si, P.ws.out[S_cap + i], cr);
+        cg = fmaf(si, P.ws.out[2 * S_cap + i], cg);
+        cb = fmaf(si, P.ws.out[3 * S_cap + i], cb);
+        ++i;
+      }
+      if (tk == t) {
+        const float sk = P.ws.out[k];
+        sig += sk;
+        cr = fmaf(sk, P.ws.out[S_cap + k], cr);
+        cg = fmaf(sk, P.ws.out[2 * S_cap + k], cg);
+        cb = fmaf(sk, P.ws.out[3 * S_cap + k], cb);
+        ++k;
+      }
+      const float inv = sig > 0.0f ? 1.0f / sig : 0.0f;
+      const float x = sig * dt;
+      const float w = T * -expm1f(-x);
+      out[0] = fmaf(w, cr * inv, out[0]);
+      out[1] = fmaf(w, cg * inv, out[1]);
+      out[2] = fmaf(w, cb * inv, out[2]);
+      out[3] += w;
+      out[4] = fmaf(w, t, out[4]);
+      T *= expf(-x);
+      if (T < P.t_eps) break;
+    }
+  }
+  bool finite = true;
+  for (int c = 0; c < 4; ++c) {
+    rgba[c * n_rays + r] = out[c];
+    finite &= isfinite(out[c]);
+  }
+  depth[r] = out[4];
+  if (!(finite && isfinite(out[4]))) flag_status(P.status, kStatusNonFinite);
+}
+
+cudaError_t launch_composite_joint(const Plan& P, int64_t n_rays, float* rgba, float* depth, cudaStream_t s) {
+  if (n_rays > 0) k_composite_joint<<<ceil_div(n_rays, 256), 256, 0, s>>>(P, n_rays, rgba, depth);
   return cudaGetLastError();
 }
 
