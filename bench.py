@@ -666,20 +666,35 @@ def bench_render(invr, ctx, prec, args, flush):
         keep.append((f, g, occ))
         views.append(invr.View(f, g, 0, sv.rigid_dq, occ))
     o, d = torch.from_numpy(w.rays.o).cuda(), torch.from_numpy(w.rays.d).cuda()
-    for _ in range(max(args.warmup, 3)):
-        invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, views)
-    ctx.sync()
     stream = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for a, b in ev:
-        flush.fill_(1)
-        a.record(stream)
-        invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, views)
-        b.record(stream)
-    torch.cuda.synchronize()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        ctx.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(1)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    ms = timed(lambda: invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, views), args.steps)
+    ms_joint = timed(lambda: invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, views, joint=True),
+                     max(5, args.steps // 4))
+    # occupancy maintenance of the human field (2 M cell queries through warp, encoding, MLPs)
+    n = invr.OCC_RES ** 3
+    dens = torch.zeros(n, device="cuda")
+    bits = torch.empty(n // 32, dtype=torch.int32, device="cuda")
+    ms_occ = timed(lambda: invr.occupancy_update(ctx, views[0], dens, bits, 0.95, 0.01), max(5, args.steps // 4))
     return {"value": round(w.rays.n / (ms * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_frame": round(ms, 3),
-            "workload": w.name}
+            "workload": w.name,
+            "joint": {"value": round(w.rays.n / (ms_joint * 1e-3) / 1e6, 3), "unit": "Mrays/s",
+                      "ms_per_frame": round(ms_joint, 3)},
+            "occupancy_update": {"ms": round(ms_occ, 3), "cells_per_s": round(n / (ms_occ * 1e-3), 1),
+                                 "cells": n}}
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm
