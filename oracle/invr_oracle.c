@@ -56,11 +56,25 @@ typedef struct {
 
 #define ORC_LUT_EMPTY 0xFFFFFFFFu
 
+/* Pose-conditioned deformation net (Sec. 4.2 Eq. 4 and the text after it; sizes from
+ * Sec. 4.4): its own hash encoding of the warped point (L levels x F features, 32 in the
+ * paper) concatenated with the pose (72), n_hidden ReLU layers of width `hidden` (4 x 128),
+ * a linear output of the residual displacement (3); no biases. */
+typedef struct orc_deform_s {
+    int L, log2_T, F, N_min;
+    double growth;
+    int pose_dim, hidden, n_hidden;
+    const double* tables;   /* [L][T][F] */
+    const double* weights;  /* W_1 [hidden][L*F + pose_dim], W_2..W_n [hidden][hidden], W_out [3][hidden] */
+} orc_deform;
+
 typedef struct {
     const orc_field* field;
     const orc_graph* graph;     /* NULL: rigid (object) field */
     const float* rigid_dq;      /* [8] canonical -> live pose T^t, used when graph == NULL */
     const uint32_t* occupancy;  /* live-space 128^3 bitfield, or NULL for none */
+    const struct orc_deform_s* deform;  /* pose-conditioned deformation net, or NULL */
+    const float* pose;          /* [pose_dim] pose theta^t of this view's frame */
 } orc_view;
 
 typedef struct {
@@ -73,6 +87,8 @@ typedef struct {
     double* grad_weights;       /* accumulates dLoss/dweights of view->field */
     const float* mask;          /* [R] M(r) of the paper's losses, NULL = 1 */
     const float* depth;         /* [R] sensor depth D(r) of the paper's depth loss */
+    double* grad_deform_tables;   /* accumulates dLoss/d(deformation-net tables), if any */
+    double* grad_deform_weights;  /* accumulates dLoss/d(deformation-net weights), if any */
 } orc_batch;
 
 /* ---------------------------------------------------------------- hash-grid geometry */
@@ -466,9 +482,9 @@ void orc_blend(const orc_graph* g, const float p[3], double qr[4], double qd[4],
         for (int k = 0; k < K; ++k) ids_out[k] = ids[k];
 }
 
-/* Live -> canonical warp of one sample: Eq. 4 for the human field, the inverse of the
- * tracked rigid pose for the object field. */
-void orc_warp(const orc_view* v, const float p[3], double vc[3])
+/* Live -> canonical warp of one sample before the deformation net: Eq. 4 for the human
+ * field (v^h_t), the inverse of the tracked rigid pose for the object field. */
+static void orc_warp_vt(const orc_view* v, const float p[3], double vc[3])
 {
     double qr[4], qd[4];
     if (v->graph) {
@@ -512,6 +528,141 @@ void orc_encode(const orc_field* fd, const double x[3], double* feat, uint32_t* 
             if (idx_out) idx_out[l * 8 + corner] = idx;
             if (w_out) w_out[l * 8 + corner] = w;
         }
+    }
+}
+
+/* Derivative of the encoding with respect to the point: dx[a] = sum_l sum_f dfeat[l F + f]
+ * d feat[l F + f] / d x_a.  Per level, d/dx_a of the trilinear weight of a corner is the
+ * product of the other two axes' weights times +-1 (corner bit set / clear) times N_l / 2
+ * (q = (x + 1)/2 N_l); an axis whose u = (x + 1)/2 lies outside [0, 1] is clamped and
+ * contributes 0.  Parity pinned against the affine-table closed form and central
+ * differences of orc_encode. */
+void orc_encode_dx(const orc_field* fd, const double x[3], const double* dfeat, double dx[3])
+{
+    int L = fd->L, F = fd->F;
+    int64_t T = (int64_t)1 << fd->log2_T;
+    dx[0] = dx[1] = dx[2] = 0.0;
+    for (int l = 0; l < L; ++l) {
+        int res = orc_level_res(fd->N_min, fd->growth, l);
+        int c[3];
+        double fr[3], scale[3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = orc_level_cell(x[a], res);
+            double u = (x[a] + 1.0) * 0.5;
+            scale[a] = (u < 0.0 || u > 1.0) ? 0.0 : 0.5 * (double)res;
+            u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+            fr[a] = u * (double)res - (double)c[a];
+        }
+        for (int corner = 0; corner < 8; ++corner) {
+            int b[3] = {corner & 1, (corner >> 1) & 1, (corner >> 2) & 1};
+            double w1[3];
+            for (int a = 0; a < 3; ++a) w1[a] = b[a] ? fr[a] : 1.0 - fr[a];
+            uint32_t idx = orc_vertex_index(res, fd->log2_T, (uint32_t)(c[0] + b[0]), (uint32_t)(c[1] + b[1]),
+                                            (uint32_t)(c[2] + b[2]));
+            const double* e = fd->tables + ((int64_t)l * T + idx) * F;
+            double g = 0.0;
+            for (int f = 0; f < F; ++f) g += dfeat[l * F + f] * e[f];
+            for (int a = 0; a < 3; ++a) {
+                double dw = (b[a] ? 1.0 : -1.0) * scale[a];
+                for (int o = 0; o < 3; ++o)
+                    if (o != a) dw *= w1[o];
+                dx[a] += dw * g;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------ deformation net */
+static void dense(const double* W, const double* x, int out, int in, double* y, int relu);
+
+#define ORC_MAX_DIN 256
+#define ORC_MAX_DW 256
+#define ORC_MAX_DH 8
+
+typedef struct {
+    double vt[3];                  /* the point v^h_t the net reads */
+    double x[ORC_MAX_DIN];         /* [hash features of v^h_t, pose] */
+    double h[ORC_MAX_DH][ORC_MAX_DW];
+    double dv[3];                  /* delta v^h */
+} orc_dact;
+
+static void orc_deform_field(const orc_deform* d, orc_field* fd)
+{
+    memset(fd, 0, sizeof(*fd));
+    fd->L = d->L; fd->log2_T = d->log2_T; fd->F = d->F; fd->N_min = d->N_min; fd->growth = d->growth;
+    fd->tables = d->tables;
+}
+
+/* delta v^h of the point vt under pose theta: encode vt with the net's own tables,
+ * append the pose, ReLU layers, linear output. */
+void orc_deform_forward(const orc_deform* d, const float* pose, const double vt[3], orc_dact* a)
+{
+    orc_field fd;
+    orc_deform_field(d, &fd);
+    int LF = d->L * d->F, in = LF + d->pose_dim, H = d->hidden;
+    for (int k = 0; k < 3; ++k) a->vt[k] = vt[k];
+    orc_encode(&fd, vt, a->x, NULL, NULL);
+    for (int k = 0; k < d->pose_dim; ++k) a->x[LF + k] = pose[k];
+    const double* W = d->weights;
+    dense(W, a->x, H, in, a->h[0], 1);
+    W += (int64_t)H * in;
+    for (int k = 1; k < d->n_hidden; ++k) {
+        dense(W, a->h[k - 1], H, H, a->h[k], 1);
+        W += (int64_t)H * H;
+    }
+    dense(W, a->h[d->n_hidden - 1], 3, H, a->dv, 0);
+}
+
+/* Backward of the net for dL/d(delta v) = ddv: weight gradients added to dW (same layout
+ * as the weights), dL/d(hash features) written to dfeat [L*F]. */
+static void orc_deform_backward(const orc_deform* d, const orc_dact* a, const double ddv[3], double* dW,
+                                double* dfeat)
+{
+    int LF = d->L * d->F, in = LF + d->pose_dim, H = d->hidden, n = d->n_hidden;
+    int64_t off[ORC_MAX_DH + 1];
+    off[0] = 0;
+    off[1] = (int64_t)H * in;
+    for (int k = 2; k <= n; ++k) off[k] = off[k - 1] + (int64_t)H * H;
+    const double* W = d->weights;
+    double g[ORC_MAX_DW], gp[ORC_MAX_DW];
+    /* output layer */
+    for (int o = 0; o < 3; ++o)
+        for (int k = 0; k < H; ++k) dW[off[n] + o * H + k] += ddv[o] * a->h[n - 1][k];
+    for (int k = 0; k < H; ++k) {
+        double s = 0.0;
+        for (int o = 0; o < 3; ++o) s += W[off[n] + o * H + k] * ddv[o];
+        g[k] = a->h[n - 1][k] > 0.0 ? s : 0.0;
+    }
+    /* hidden layers n-1 .. 1: g = dL/d(pre-activation of layer k) */
+    for (int k = n - 1; k >= 1; --k) {
+        for (int o = 0; o < H; ++o)
+            for (int i = 0; i < H; ++i) dW[off[k] + o * H + i] += g[o] * a->h[k - 1][i];
+        for (int i = 0; i < H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < H; ++o) s += W[off[k] + o * H + i] * g[o];
+            gp[i] = a->h[k - 1][i] > 0.0 ? s : 0.0;
+        }
+        for (int i = 0; i < H; ++i) g[i] = gp[i];
+    }
+    /* first layer */
+    for (int o = 0; o < H; ++o)
+        for (int i = 0; i < in; ++i) dW[o * in + i] += g[o] * a->x[i];
+    for (int i = 0; i < LF; ++i) {
+        double s = 0.0;
+        for (int o = 0; o < H; ++o) s += W[o * in + i] * g[o];
+        dfeat[i] = s;
+    }
+}
+
+/* Live -> canonical warp of one sample: v^h_t by Eq. 4, then, with a deformation net,
+ * v^h_c = v^h_t + delta v^h (Sec. 4.2); the object field's rigid inverse pose. */
+void orc_warp(const orc_view* v, const float p[3], double vc[3])
+{
+    orc_warp_vt(v, p, vc);
+    if (v->graph && v->deform) {
+        orc_dact a;
+        orc_deform_forward(v->deform, v->pose, vc, &a);
+        for (int k = 0; k < 3; ++k) vc[k] += a.dv[k];
     }
 }
 
@@ -862,11 +1013,22 @@ double orc_train_loss_grad(int n_batches, const orc_batch* batches, int n_sample
         int64_t T = (int64_t)1 << fd->log2_T;
         int nw = fd->hidden * fd->mlp_in + fd->hidden * fd->hidden + fd->geo_out * fd->hidden +
                  fd->col_hidden * (fd->geo_out - 1) + 3 * fd->col_hidden;
+        const orc_deform* def = v->graph ? v->deform : NULL;
+        int nwd = 0;
+        orc_field dfd;
+        int64_t Td = 0;
+        if (def) {
+            nwd = def->hidden * (def->L * def->F + def->pose_dim) + (def->n_hidden - 1) * def->hidden * def->hidden +
+                  3 * def->hidden;
+            orc_deform_field(def, &dfd);
+            Td = (int64_t)1 << def->log2_T;
+        }
         double bl = 0.0;
 #pragma omp parallel reduction(+ : bl)
         {
             orc_rec* rec = (orc_rec*)malloc(sizeof(orc_rec) * (size_t)n_samples);
             double* dW = grads ? (double*)calloc((size_t)nw, sizeof(double)) : NULL;
+            double* dWd = (grads && def) ? (double*)calloc((size_t)nwd, sizeof(double)) : NULL;
 #pragma omp for schedule(dynamic, 16)
             for (int64_t r = 0; r < R; ++r) {
                 float ro[3] = {B->o[r], B->o[R + r], B->o[2 * R + r]};
@@ -904,10 +1066,34 @@ double orc_train_loss_grad(int n_batches, const orc_batch* batches, int n_sample
                             double* gp = B->grad_tables + ((int64_t)l * T + idx[l * 8 + corner]) * fd->F;
                             for (int f = 0; f < fd->F; ++f) add_atomic(&gp[f], wc * dfeat[l * fd->F + f]);
                         }
+                    if (def) {
+                        /* v_c = v_t + delta v: dL/d(delta v) = dL/dv_c, the encoding's
+                         * derivative in the point; then back through the net and into
+                         * its tables at v_t */
+                        double vt[3], vcn[3], dx[3], dfd_feat[ORC_MAX_DIN];
+                        orc_dact da;
+                        orc_warp_vt(v, s->p, vt);
+                        orc_deform_forward(def, v->pose, vt, &da);
+                        for (int k = 0; k < 3; ++k) vcn[k] = vt[k] + da.dv[k];
+                        orc_encode_dx(fd, vcn, dfeat, dx);
+                        orc_deform_backward(def, &da, dx, dWd, dfd_feat);
+                        uint32_t didx[ORC_MAX_L * 8];
+                        double dcw[ORC_MAX_L * 8], dfe[ORC_MAX_L * ORC_MAX_F];
+                        orc_encode(&dfd, vt, dfe, didx, dcw);
+                        for (int l = 0; l < def->L; ++l)
+                            for (int corner = 0; corner < 8; ++corner) {
+                                double wc = dcw[l * 8 + corner];
+                                double* gp = B->grad_deform_tables + ((int64_t)l * Td + didx[l * 8 + corner]) * def->F;
+                                for (int f = 0; f < def->F; ++f) add_atomic(&gp[f], wc * dfd_feat[l * def->F + f]);
+                            }
+                    }
                 }
             }
             if (grads)
                 for (int i = 0; i < nw; ++i) add_atomic(&B->grad_weights[i], dW[i]);
+            if (dWd)
+                for (int i = 0; i < nwd; ++i) add_atomic(&B->grad_deform_weights[i], dWd[i]);
+            free(dWd);
             free(dW);
             free(rec);
         }
@@ -988,6 +1174,30 @@ void orc_neighbour_points(const orc_graph* g, int64_t n, const float* p, int* id
         float ky[ORC_MAX_K];
         from_lut[i] = orc_neighbours(g, q, id, ky);
         for (int k = 0; k < g->K; ++k) ids[(int64_t)k * n + i] = id[k];
+    }
+}
+
+/* delta v of n points vt[3][n] under pose: dv[3][n] (deformation net forward). */
+void orc_deform_points(const orc_deform* d, const float* pose, int64_t n, const double* vt, double* dv)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double q[3] = {vt[i], vt[n + i], vt[2 * n + i]};
+        orc_dact a;
+        orc_deform_forward(d, pose, q, &a);
+        for (int k = 0; k < 3; ++k) dv[k * n + i] = a.dv[k];
+    }
+}
+
+/* Encoding derivative of n points x[3][n] for dfeat [L*F][n]: dx[3][n]. */
+void orc_encode_dx_points(const orc_field* fd, int64_t n, const double* x, const double* dfeat, double* dx)
+{
+    int LF = fd->L * fd->F;
+    for (int64_t i = 0; i < n; ++i) {
+        double q[3] = {x[i], x[n + i], x[2 * n + i]}, g[ORC_MAX_L * ORC_MAX_F], r[3];
+        for (int k = 0; k < LF; ++k) g[k] = dfeat[(int64_t)k * n + i];
+        orc_encode_dx(fd, q, g, r);
+        for (int a = 0; a < 3; ++a) dx[a * n + i] = r[a];
     }
 }
 

@@ -40,6 +40,11 @@ What pins each oracle function (tests/test_oracle_pins.py, run with -m "not gpu"
   Adam                  first and second steps in closed form
   joint compositing     an empty second field reproduces the single-field render; two
                         constant fields (sigma = 1 each, c = 1/2) give A = 1 - exp(-2 L)
+  deformation net       forward = numpy matmul chain on the hash features and pose; a
+                        zero output layer leaves the warp unchanged; the encoding's point
+                        derivative = the affine-table closed form and central differences;
+                        training gradients of the net's tables and weights and of the
+                        field through v_c = v_t + delta v by central differences
   occupancy update      a field built so that sigma = exp(max(a.x + b, 0)) exactly (affine
                         dense level, identity-like first layers) gives that density at
                         every cell centre; decay keeps max(decay d, sigma); bits = d > thr
@@ -94,16 +99,24 @@ class CGraph(C.Structure):
                 ("lut_live", C.POINTER(C.c_uint32))]
 
 
+class CDeform(C.Structure):
+    _fields_ = [("L", C.c_int), ("log2_T", C.c_int), ("F", C.c_int), ("N_min", C.c_int),
+                ("growth", C.c_double), ("pose_dim", C.c_int), ("hidden", C.c_int), ("n_hidden", C.c_int),
+                ("tables", C.POINTER(C.c_double)), ("weights", C.POINTER(C.c_double))]
+
+
 class CView(C.Structure):
     _fields_ = [("field", C.POINTER(CField)), ("graph", C.POINTER(CGraph)),
-                ("rigid_dq", C.POINTER(C.c_float)), ("occupancy", C.POINTER(C.c_uint32))]
+                ("rigid_dq", C.POINTER(C.c_float)), ("occupancy", C.POINTER(C.c_uint32)),
+                ("deform", C.POINTER(CDeform)), ("pose", C.POINTER(C.c_float))]
 
 
 class CBatch(C.Structure):
     _fields_ = [("n_rays", C.c_int64), ("o", C.POINTER(C.c_float)), ("d", C.POINTER(C.c_float)),
                 ("view", C.POINTER(CView)), ("target", C.POINTER(C.c_float)),
                 ("grad_tables", C.POINTER(C.c_double)), ("grad_weights", C.POINTER(C.c_double)),
-                ("mask", C.POINTER(C.c_float)), ("depth", C.POINTER(C.c_float))]
+                ("mask", C.POINTER(C.c_float)), ("depth", C.POINTER(C.c_float)),
+                ("grad_deform_tables", C.POINTER(C.c_double)), ("grad_deform_weights", C.POINTER(C.c_double))]
 
 
 def _declare(L):
@@ -118,6 +131,8 @@ def _declare(L):
     L.orc_huber.restype = C.c_double
     L.orc_render.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, C.c_int, P, P, P, P, P, P, P]
     L.orc_render.restype = None
+    L.orc_deform_points.argtypes = [P, P, C.c_int64, P, P]
+    L.orc_encode_dx_points.argtypes = [P, C.c_int64, P, P, P]
     L.orc_render_joint.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, P, P, P, P]
     L.orc_occupancy_update.argtypes = [P, C.c_double, C.c_double, P, P]
     L.orc_lut_canon_knn.argtypes = [C.c_int, C.c_int, P, C.c_int, P]
@@ -197,6 +212,23 @@ class Graph:
 LUT_EMPTY = 0xFFFFFFFF
 
 
+def deform_points(deform: Deform, pose, vt) -> np.ndarray:
+    """delta v [3][n] of points vt [3][n] under pose (deformation net forward)."""
+    vt = _f64(vt)
+    pose = _f32(pose)
+    dv = np.zeros_like(vt)
+    lib().orc_deform_points(C.byref(deform._c), _p(pose), vt.shape[1], _p(vt), _p(dv))
+    return dv
+
+
+def encode_dx_points(field: Field, x, dfeat) -> np.ndarray:
+    """Encoding derivative: dx [3][n] = sum over features dfeat [L*F][n] x d feat / d x."""
+    x, dfeat = _f64(x), _f64(dfeat)
+    dx = np.zeros_like(x)
+    lib().orc_encode_dx_points(C.byref(field._c), x.shape[1], _p(x), _p(dfeat), _p(dx))
+    return dx
+
+
 def lut_canon_knn(x_canon, K: int, G: int) -> np.ndarray:
     """Canonical KNN field [G^3][K] (uint16 node ids, ascending by key)."""
     x = _f32(x_canon)
@@ -240,20 +272,41 @@ def neighbour_points(graph: Graph, p):
     return ids, from_lut.astype(bool)
 
 
-class View:
-    def __init__(self, field: Field, graph: Optional[Graph] = None, rigid_dq=None, occupancy=None):
-        self.field, self.graph = field, graph
-        self.rigid_dq = None if rigid_dq is None else _f32(rigid_dq)
-        self.occupancy = None if occupancy is None else np.ascontiguousarray(occupancy, np.uint32)
-        self._c = CView(C.pointer(field._c), C.pointer(graph._c) if graph is not None else None,
-                        self.rigid_dq.ctypes.data_as(C.POINTER(C.c_float)) if self.rigid_dq is not None else None,
-                        self.occupancy.ctypes.data_as(C.POINTER(C.c_uint32)) if self.occupancy is not None else None)
+class Deform:
+    """FP64 copy of a pose-conditioned deformation net (tables [L][T][F], weights W_1..W_out)."""
+
+    def __init__(self, desc, tables, weights):
+        self.desc = desc
+        self.tables = _f64(tables).reshape(-1)
+        self.weights = _f64(weights).reshape(-1)
+        self._c = CDeform(desc.L, desc.log2_T, desc.F, desc.N_min, float(desc.growth), desc.pose_dim, desc.hidden,
+                          desc.n_hidden, self.tables.ctypes.data_as(C.POINTER(C.c_double)),
+                          self.weights.ctypes.data_as(C.POINTER(C.c_double)))
 
     @classmethod
-    def from_synth(cls, v, field: Optional[Field] = None):
+    def from_params(cls, dp):
+        return cls(dp.desc, dp.tables, dp.weights)
+
+
+class View:
+    def __init__(self, field: Field, graph: Optional[Graph] = None, rigid_dq=None, occupancy=None,
+                 deform: Optional[Deform] = None, pose=None):
+        self.field, self.graph, self.deform = field, graph, deform
+        self.rigid_dq = None if rigid_dq is None else _f32(rigid_dq)
+        self.occupancy = None if occupancy is None else np.ascontiguousarray(occupancy, np.uint32)
+        self.pose = None if pose is None else _f32(pose)
+        self._c = CView(C.pointer(field._c), C.pointer(graph._c) if graph is not None else None,
+                        self.rigid_dq.ctypes.data_as(C.POINTER(C.c_float)) if self.rigid_dq is not None else None,
+                        self.occupancy.ctypes.data_as(C.POINTER(C.c_uint32)) if self.occupancy is not None else None,
+                        C.pointer(deform._c) if deform is not None else None,
+                        self.pose.ctypes.data_as(C.POINTER(C.c_float)) if self.pose is not None else None)
+
+    @classmethod
+    def from_synth(cls, v, field: Optional[Field] = None, deform: Optional[Deform] = None):
         f = field if field is not None else Field.from_params(v.field)
         g = Graph.from_synth(v.graph) if v.graph is not None else None
-        return cls(f, g, v.rigid_dq, v.occupancy)
+        d = deform if deform is not None else (Deform.from_params(v.deform) if v.deform is not None else None)
+        return cls(f, g, v.rigid_dq, v.occupancy, d, v.pose)
 
 
 # ------------------------------------------------------------------------- calls
@@ -425,12 +478,20 @@ def train_loss_grad(batches: List[TrainBatch], n_samples: int, t_eps: float, hub
         if id(f) not in out:
             out[id(f)] = (np.zeros_like(f.tables), np.zeros_like(f.weights))
         gt, gw = out[id(f)]
+        dgt = dgw = None
+        dn = b.view.deform
+        if dn is not None:
+            if id(dn) not in out:
+                out[id(dn)] = (np.zeros_like(dn.tables), np.zeros_like(dn.weights))
+            dgt, dgw = out[id(dn)]
         cb.append(CBatch(b.o.shape[1], b.o.ctypes.data_as(C.POINTER(C.c_float)),
                          b.d.ctypes.data_as(C.POINTER(C.c_float)), C.pointer(b.view._c),
                          b.target.ctypes.data_as(C.POINTER(C.c_float)),
                          gt.ctypes.data_as(C.POINTER(C.c_double)), gw.ctypes.data_as(C.POINTER(C.c_double)),
                          None if b.mask is None else b.mask.ctypes.data_as(C.POINTER(C.c_float)),
-                         None if b.depth is None else b.depth.ctypes.data_as(C.POINTER(C.c_float))))
+                         None if b.depth is None else b.depth.ctypes.data_as(C.POINTER(C.c_float)),
+                         None if dgt is None else dgt.ctypes.data_as(C.POINTER(C.c_double)),
+                         None if dgw is None else dgw.ctypes.data_as(C.POINTER(C.c_double))))
     arr = (CBatch * len(cb))(*cb)
     value = lib().orc_train_loss_grad(len(cb), C.cast(arr, C.c_void_p), n_samples, t_eps, huber_delta,
                                       1 if grads else 0, kind, depth_weight)

@@ -24,6 +24,9 @@ Recipes (all seeded with numpy's PCG64):
   * hash tables U(-0.5, 0.5); MLP weights Xavier-uniform U(+-sqrt(6/(fan_in+fan_out))).
   * target colours: 0.5 + 0.45 sin(a_k . d + b_k) per channel k, smooth in the ray
     direction d (a stand-in for the paper's RGB captures, which are not available).
+  * deformation net (Sec. 4.2, sizes of Sec. 4.4): tables U(-0.5, 0.5), Xavier weights with
+    the output layer scaled by 0.05 (|delta v| ~ 1e-2); pose: 24 axis-angle joints with
+    components U(-0.3, 0.3) rad.
   * sensor depth and mask per training ray (stand-ins for the RGBD depth and the
     segmentation masks): first hit of the canonical body ellipsoid (human batches) or of
     the posed object sphere (object batches); mask 1 on a hit, else depth 0 and mask 0.
@@ -93,12 +96,51 @@ class Graph:
 
 
 @dataclasses.dataclass
+class DeformDesc:
+    """Pose-conditioned deformation net: its own hash encoding (L x F features) of the
+    warped point, concatenated with the pose (pose_dim), n_hidden ReLU layers of width
+    hidden, a linear 3-vector output."""
+    L: int = 16
+    log2_T: int = 19
+    F: int = 2
+    N_min: int = 16
+    growth: float = 1.38
+    pose_dim: int = 72
+    hidden: int = 128
+    n_hidden: int = 4
+
+    @property
+    def T(self) -> int:
+        return 1 << self.log2_T
+
+    @property
+    def n_in(self) -> int:
+        return self.L * self.F + self.pose_dim
+
+    def weight_shapes(self):
+        return ([(self.hidden, self.n_in)] + [(self.hidden, self.hidden)] * (self.n_hidden - 1)
+                + [(3, self.hidden)])
+
+    def n_weight_params(self) -> int:
+        return sum(r * c for r, c in self.weight_shapes())
+
+
+@dataclasses.dataclass
+class DeformParams:
+    desc: DeformDesc
+    tables: np.ndarray   # float32 [L][T][F]
+    weights: np.ndarray  # float32 flat, W_1..W_n, W_out row-major
+
+
+@dataclasses.dataclass
 class View:
     """One field seen through one frame's motion: graph is None for the rigid field."""
     field: FieldParams
     graph: Optional[Graph] = None
     rigid_dq: Optional[np.ndarray] = None   # float32 [8], canonical -> live
     occupancy: Optional[np.ndarray] = None  # uint32 [128^3 / 32]
+    deform: Optional[DeformParams] = None   # human field only
+    pose: Optional[np.ndarray] = None       # float32 [pose_dim], the frame's pose
 
 
 @dataclasses.dataclass
@@ -294,6 +336,28 @@ def xavier_weights(rng: np.random.Generator, desc: FieldDesc) -> np.ndarray:
 def make_field(rng: np.random.Generator, desc: FieldDesc) -> FieldParams:
     tables = rng.uniform(-0.5, 0.5, size=(desc.L, desc.T, desc.F)).astype(np.float32)
     return FieldParams(desc, tables, xavier_weights(rng, desc))
+
+
+def make_deform(rng: np.random.Generator, desc: DeformDesc = DeformDesc(), out_scale: float = 0.05) -> DeformParams:
+    """Deformation net: tables U(-0.5, 0.5), Xavier-uniform weights, the output layer
+    scaled by out_scale so that the residual displacement is a small correction of the
+    warp (|delta v| of order 1e-2)."""
+    tables = rng.uniform(-0.5, 0.5, size=(desc.L, desc.T, desc.F)).astype(np.float32)
+    parts = []
+    shapes = desc.weight_shapes()
+    for k, (o, i) in enumerate(shapes):
+        a = math.sqrt(6.0 / (i + o))
+        w = rng.uniform(-a, a, size=(o, i))
+        if k == len(shapes) - 1:
+            w *= out_scale
+        parts.append(w.ravel())
+    return DeformParams(desc, tables, np.concatenate(parts).astype(np.float32))
+
+
+def make_pose(rng: np.random.Generator, pose_dim: int = 72, max_angle: float = 0.3) -> np.ndarray:
+    """A body pose theta: pose_dim / 3 joints as axis-angle vectors with components
+    U(-max_angle, max_angle) rad (the shape of an SMPL pose; the SMPL model is not used)."""
+    return rng.uniform(-max_angle, max_angle, size=pose_dim).astype(np.float32)
 
 
 def sensor_depth_mask(rays: Rays, centre, axes) -> Tuple[np.ndarray, np.ndarray]:

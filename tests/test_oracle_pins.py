@@ -824,3 +824,144 @@ def test_occupancy_update_affine_density(oracle):
     dens2, bits2 = oracle.occupancy_update(zero, 0.5, thr, dens.copy())
     np.testing.assert_allclose(dens2, np.maximum(0.5 * want, 1.0), rtol=1e-12)
     np.testing.assert_array_equal(bits2, synth.pack_bits(np.maximum(0.5 * want, 1.0) > thr))
+
+
+# ------------------------------------------- pose-conditioned deformation net (Sec. 4.2)
+TINY_DEFORM = synth.DeformDesc(L=2, log2_T=10, F=2, N_min=2, growth=1.5, pose_dim=6, hidden=16, n_hidden=3)
+
+
+def test_deform_forward_matches_numpy_chain(oracle):
+    rng = np.random.default_rng(91)
+    dp = synth.make_deform(rng, TINY_DEFORM, out_scale=1.0)
+    d = dp.desc
+    pose = synth.make_pose(rng, d.pose_dim)
+    vt = rng.uniform(-0.9, 0.9, size=(3, 50))
+    got = oracle.deform_points(oracle.Deform.from_params(dp), pose, vt)
+    enc = oracle.Field(synth.FieldDesc(L=d.L, log2_T=d.log2_T, F=d.F, N_min=d.N_min, growth=d.growth),
+                       dp.tables, np.zeros(1))
+    feat = oracle.encode_points(enc, vt)
+    x = np.concatenate([feat, np.repeat(pose.astype(np.float64)[:, None], vt.shape[1], axis=1)])
+    W, off = [], 0
+    for r, c in d.weight_shapes():
+        W.append(dp.weights[off:off + r * c].astype(np.float64).reshape(r, c))
+        off += r * c
+    h = x
+    for k in range(d.n_hidden):
+        h = np.maximum(W[k] @ h, 0.0)
+    np.testing.assert_allclose(got, W[-1] @ h, rtol=1e-12, atol=1e-14)
+    assert np.abs(got).max() > 1e-3
+
+
+def test_deform_zero_output_layer_leaves_the_warp(oracle):
+    rng = np.random.default_rng(92)
+    dp = synth.make_deform(rng, TINY_DEFORM, out_scale=0.0)
+    g = synth.make_graph(rng, 32, K=4)
+    f = oracle.Field.from_params(tiny_field(rng))
+    p = rng.uniform(-0.9, 0.9, size=(3, 300)).astype(np.float32)
+    with_net = oracle.View(f, graph=oracle.Graph.from_synth(g), deform=oracle.Deform.from_params(dp),
+                           pose=synth.make_pose(rng, TINY_DEFORM.pose_dim))
+    plain = oracle.View(f, graph=oracle.Graph.from_synth(g))
+    np.testing.assert_array_equal(oracle.warp_points(with_net, p), oracle.warp_points(plain, p))
+
+
+def test_encode_point_derivative_affine_closed_form(oracle):
+    """Dense levels holding an affine function of the vertex coordinates: d feat / d x_a =
+    coef_a N_l / 2 inside the box and 0 along an axis clamped outside it."""
+    rng = np.random.default_rng(93)
+    fp = tiny_field(rng, L=2, log2_T=10, F=2, N_min=2, growth=1.5)
+    d = fp.desc
+    tables = np.zeros((d.L, d.T, d.F))
+    coef = rng.normal(size=(d.L, d.F, 4))
+    for l in range(d.L):
+        res = oracle.level_res(d.N_min, d.growth, l)
+        for z in range(res + 1):
+            for y in range(res + 1):
+                for x in range(res + 1):
+                    tables[l, oracle.vertex_index(res, d.log2_T, x, y, z)] = coef[l, :, 0] + coef[l, :, 1:] @ [x, y, z]
+    f = oracle.Field(d, tables, fp.weights)
+    pts = rng.uniform(-0.95, 0.95, size=(3, 100))
+    pts[1, :10] = 1.3                                   # y clamped for the first ten points
+    dfeat = rng.normal(size=(d.L * d.F, 100))
+    dx = oracle.encode_dx_points(f, pts, dfeat)
+    want = np.zeros((3, 100))
+    for l in range(d.L):
+        res = oracle.level_res(d.N_min, d.growth, l)
+        for fi in range(d.F):
+            want += np.outer(coef[l, fi, 1:], dfeat[l * d.F + fi]) * 0.5 * res
+    want[1, :10] = 0.0
+    np.testing.assert_allclose(dx, want, rtol=1e-11, atol=1e-11)
+
+
+def test_encode_point_derivative_central_differences(oracle):
+    rng = np.random.default_rng(94)
+    fp = synth.make_field(rng, synth.FieldDesc(L=4, log2_T=10, F=2, N_min=4, growth=1.6))
+    f = oracle.Field.from_params(fp)
+    pts = rng.uniform(-0.9, 0.9, size=(3, 60))
+    dfeat = rng.normal(size=(8, 60))
+    dx = oracle.encode_dx_points(f, pts, dfeat)
+    h = 1e-7
+    checked = 0
+    for a in range(3):
+        e = np.zeros((3, 1))
+        e[a] = h
+        fp_ = np.sum(dfeat * oracle.encode_points(f, pts + e), axis=0)
+        fm_ = np.sum(dfeat * oracle.encode_points(f, pts - e), axis=0)
+        fd = (fp_ - fm_) / (2 * h)
+        # a cell face within h of a point makes the encoding's derivative jump; skip those
+        ok = np.ones(60, bool)
+        for l in range(4):
+            res = oracle.level_res(4, 1.6, l)
+            q = (pts[a] + 1.0) * 0.5 * res
+            ok &= np.abs(q - np.round(q)) > 1e-4
+        np.testing.assert_allclose(dx[a, ok], fd[ok], rtol=1e-6, atol=1e-6)
+        checked += ok.sum()
+    assert checked > 120
+
+
+def test_deform_gradients_match_central_differences(oracle):
+    """Training through v_c = v_t + delta v: the analytic gradients of the net's tables and of
+    every weight layer, and of the field's own parameters, against central differences."""
+    rng = np.random.default_rng(95)
+    fp = synth.make_field(rng, synth.FieldDesc(L=4, log2_T=10, F=2, N_min=4, growth=1.6))
+    dp = synth.make_deform(rng, TINY_DEFORM, out_scale=0.5)
+    g = synth.make_graph(rng, 32, K=4)
+    rays = synth.subset_rays(synth.ring_rays(4, 16, 16, 50.0, 2.5), rng.choice(4 * 256, 48, replace=False))
+    f = oracle.Field.from_params(fp)
+    dn = oracle.Deform.from_params(dp)
+    v = oracle.View(f, graph=oracle.Graph.from_synth(g), deform=dn, pose=synth.make_pose(rng, TINY_DEFORM.pose_dim))
+    batches = [oracle.TrainBatch(rays.o, rays.d, v, synth.target_colours(rng, rays))]
+    S = 24
+    loss, grads = oracle.train_loss_grad(batches, S, 0.0, 0.1)
+    dgt, dgw = grads[id(dn)]
+    gt, gw = grads[id(f)]
+    assert np.abs(dgt).max() > 0 and np.abs(dgw).max() > 0
+
+    def fd(arr, i, h):
+        old = arr[i]
+        arr[i] = old + h
+        lp, _ = oracle.train_loss_grad(batches, S, 0.0, 0.1, grads=False)
+        arr[i] = old - h
+        lm, _ = oracle.train_loss_grad(batches, S, 0.0, 0.1, grads=False)
+        arr[i] = old
+        return (lp - lm) / (2 * h)
+
+    eps = np.finfo(np.float64).eps
+    offs = np.cumsum([0] + [r * c for r, c in TINY_DEFORM.weight_shapes()])
+    picks = [(dn.tables, i, dgt) for i in rng.choice(np.flatnonzero(np.abs(dgt) > 1e-3 * np.abs(dgt).max()), 16,
+                                                      replace=False)]
+    for k in range(len(offs) - 1):                       # every layer of the net
+        seg = np.arange(offs[k], offs[k + 1])
+        seg = seg[np.abs(dgw[seg]) > 1e-3 * np.abs(dgw[seg]).max()]
+        picks += [(dn.weights, i, dgw) for i in rng.choice(seg, 6, replace=False)]
+    picks += [(f.tables, i, gt) for i in rng.choice(np.flatnonzero(np.abs(gt) > 1e-3 * np.abs(gt).max()), 8,
+                                                     replace=False)]
+    picks += [(f.weights, i, gw) for i in rng.choice(np.flatnonzero(np.abs(gw) > 1e-3 * np.abs(gw).max()), 8,
+                                                      replace=False)]
+    skipped = 0
+    for arr, i, g_ in picks:
+        f1, f2 = fd(arr, i, 1e-5), fd(arr, i, 1e-6)
+        if abs(f1 - f2) > 1e-4 * abs(f2) + 100 * eps * loss / 1e-6:
+            skipped += 1
+            continue
+        assert abs(f2 - g_[i]) <= 1e-5 * abs(g_[i]) + 50 * eps * loss / 1e-6, (i, f2, g_[i])
+    assert skipped <= 5, skipped
