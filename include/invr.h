@@ -37,6 +37,7 @@ extern "C" {
 typedef struct invr_ctx_s* invr_ctx;     /* device, workspace, status word              */
 typedef struct invr_field_s* invr_field; /* hash tables + MLP weights + grads + Adam    */
 typedef struct invr_graph_s* invr_graph; /* deformation-graph nodes and per-frame poses */
+typedef struct invr_deform_s* invr_deform; /* pose-conditioned deformation net + its optimiser state */
 typedef void* invr_stream;               /* cudaStream_t                                */
 
 typedef enum {
@@ -171,6 +172,36 @@ invr_status invr_graph_get_lut(invr_graph graph, int frame, uint16_t* canon_dev,
                                invr_stream stream);
 
 /* ------------------------------------------------------------------ rendering */
+/* ---------------------------------------------------------- deformation net */
+/* Pose-conditioned deformation net (Sec. 4.2, after Eq. 4; sizes of Sec. 4.4): the warped
+ * human point v_t = DQB^{-1}(v) v is hash-encoded with the net's own tables (L levels x
+ * F = 2 features, 32 in the paper), concatenated with the frame's pose theta (pose_dim,
+ * 72), passed through n_hidden ReLU layers of width `hidden` (4 x 128) and a linear layer
+ * giving the residual displacement delta v (3); the human field is then evaluated at
+ * v_c = v_t + delta v.  No biases.  Weights, row-major [out][in], concatenated:
+ * W_1 [hidden][L*F + pose_dim], W_2..W_n [hidden][hidden], W_out [3][hidden].  Training
+ * (invr_train_step and its halves) back-propagates through v_c into the net's tables and
+ * weights and updates them with the same Adam step as the fields.  Supported: F = 2,
+ * L*F <= 32, hidden a multiple of 16 up to 128, 1 <= n_hidden <= 4, pose_dim <= 128, prec
+ * INVR_FP32 (the net runs in FP32 whatever the field's precision); else INVR_E_ARG. */
+typedef struct {
+    int L, log2_T, F, N_min;
+    double growth;
+    int pose_dim, hidden, n_hidden;
+    invr_precision prec;
+} invr_deform_desc;
+
+invr_status invr_deform_create(invr_ctx ctx, const invr_deform_desc* desc, invr_deform* out);
+invr_status invr_deform_destroy(invr_deform deform);
+/* tables [L][2^log2_T][F] and weights (layout above), device, copied in / out. */
+invr_status invr_deform_set_params(invr_deform deform, const float* tables_dev, const float* weights_dev,
+                                   invr_stream stream);
+invr_status invr_deform_get_params(invr_deform deform, float* tables_dev, float* weights_dev, invr_stream stream);
+/* Accumulated gradients (cleared by the Adam step, or by invr_deform_zero_grads). */
+invr_status invr_deform_get_grads(invr_deform deform, float* grad_tables_dev, float* grad_weights_dev,
+                                  invr_stream stream);
+invr_status invr_deform_zero_grads(invr_deform deform, invr_stream stream);
+
 /* One field seen in one frame: the human field through `graph` at `frame` (inverse
  * dual-quaternion-blend warp, Eq. 4), or, when graph == NULL, the object field through
  * the rigid pose rigid_dq (host pointer to 8 floats: unit dual quaternion canonical ->
@@ -183,6 +214,13 @@ typedef struct {
     int frame;
     const float* rigid_dq;
     const uint32_t* occupancy_dev;
+    /* pose-conditioned deformation net (human field only; NULL: none) and the pose theta^t
+     * of this view's frame (device, deform's pose_dim floats): v_c = v_t + delta v.  The
+     * render and training calls run it; the per-point calls (invr_warp_points,
+     * invr_query_points, invr_query_points_noalloc, invr_occupancy_update) reject a view
+     * that has one with INVR_E_ARG. */
+    invr_deform deform;
+    const float* pose_dev;
 } invr_field_view;
 
 /* Volume rendering of n_rays rays (Sec. 3, "share volumetric rendering"): each ray is

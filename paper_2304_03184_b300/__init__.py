@@ -37,7 +37,13 @@ class invr_graph_desc(C.Structure):
 
 class invr_field_view(C.Structure):
     _fields_ = [("field", C.c_void_p), ("graph", C.c_void_p), ("frame", C.c_int),
-                ("rigid_dq", C.POINTER(C.c_float)), ("occupancy_dev", C.c_void_p)]
+                ("rigid_dq", C.POINTER(C.c_float)), ("occupancy_dev", C.c_void_p),
+                ("deform", C.c_void_p), ("pose_dev", C.c_void_p)]
+
+
+class invr_deform_desc(C.Structure):
+    _fields_ = [("L", C.c_int), ("log2_T", C.c_int), ("F", C.c_int), ("N_min", C.c_int), ("growth", C.c_double),
+                ("pose_dim", C.c_int), ("hidden", C.c_int), ("n_hidden", C.c_int), ("prec", C.c_int)]
 
 
 class invr_render_args(C.Structure):
@@ -84,6 +90,12 @@ _SIGNATURES = {
     "invr_ctx_timing": [_VP, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64), _I],
     "invr_query_points_noalloc": [_VP, C.POINTER(invr_field_view), _I64, _VP, _VP, _VP],
     "invr_render_rays_joint": [_VP, C.POINTER(invr_render_args), _VP],
+    "invr_deform_create": [_VP, C.POINTER(invr_deform_desc), C.POINTER(C.c_void_p)],
+    "invr_deform_destroy": [_VP],
+    "invr_deform_set_params": [_VP, _VP, _VP, _VP],
+    "invr_deform_get_params": [_VP, _VP, _VP, _VP],
+    "invr_deform_get_grads": [_VP, _VP, _VP, _VP],
+    "invr_deform_zero_grads": [_VP, _VP],
     "invr_occupancy_update": [_VP, C.POINTER(invr_field_view), C.c_float, C.c_float, _VP, _VP, _VP],
     "invr_graph_enable_lut": [_VP, C.c_int, _VP],
     "invr_graph_disable_lut": [_VP],
@@ -303,11 +315,61 @@ class Graph:
             self.h = None
 
 
-class View:
-    """A field seen in one frame: through `graph` at `frame`, or through rigid_dq."""
+class Deform:
+    """A pose-conditioned deformation net (invr_deform): its hash tables, weights, gradients
+    and Adam state on the device."""
 
-    def __init__(self, field: Field, graph: Optional[Graph] = None, frame: int = 0, rigid_dq=None, occupancy=None):
+    def __init__(self, ctx: Context, L=16, log2_T=19, F=2, N_min=16, growth=1.38, pose_dim=72, hidden=128,
+                 n_hidden=4):
+        h = C.c_void_p()
+        desc = invr_deform_desc(L, log2_T, F, N_min, growth, pose_dim, hidden, n_hidden, INVR_FP32)
+        _check(lib().invr_deform_create(ctx.h, C.byref(desc), C.byref(h)), ctx.h)
+        self.ctx, self.desc, self.h = ctx, desc, h
+        self.n_tab = L * (1 << log2_T) * F
+        self.n_w = hidden * (L * F + pose_dim) + (n_hidden - 1) * hidden * hidden + 3 * hidden
+
+    @classmethod
+    def from_synth(cls, ctx: Context, dp):
+        torch = _torch()
+        d = dp.desc
+        net = cls(ctx, d.L, d.log2_T, d.F, d.N_min, d.growth, d.pose_dim, d.hidden, d.n_hidden)
+        net.set_params(torch.from_numpy(dp.tables.reshape(-1)).cuda(), torch.from_numpy(dp.weights).cuda())
+        return net
+
+    def set_params(self, tables, weights):
+        _check(lib().invr_deform_set_params(self.h, _ptr(tables), _ptr(weights), _stream()), self.ctx.h)
+
+    def get_params(self):
+        torch = _torch()
+        t = torch.empty(self.n_tab, device="cuda")
+        w = torch.empty(self.n_w, device="cuda")
+        _check(lib().invr_deform_get_params(self.h, _ptr(t), _ptr(w), _stream()), self.ctx.h)
+        return t, w
+
+    def get_grads(self):
+        torch = _torch()
+        t = torch.empty(self.n_tab, device="cuda")
+        w = torch.empty(self.n_w, device="cuda")
+        _check(lib().invr_deform_get_grads(self.h, _ptr(t), _ptr(w), _stream()), self.ctx.h)
+        return t, w
+
+    def zero_grads(self):
+        _check(lib().invr_deform_zero_grads(self.h, _stream()), self.ctx.h)
+
+    def close(self):
+        if self.h:
+            lib().invr_deform_destroy(self.h)
+            self.h = None
+
+
+class View:
+    """A field seen in one frame: through `graph` at `frame`, or through rigid_dq; the human
+    view may carry a deformation net and the frame's pose (a CUDA float32 tensor)."""
+
+    def __init__(self, field: Field, graph: Optional[Graph] = None, frame: int = 0, rigid_dq=None, occupancy=None,
+                 deform: Optional[Deform] = None, pose=None):
         self.field, self.graph, self.frame, self.occupancy = field, graph, frame, occupancy
+        self.deform, self.pose = deform, pose
         self._dq = None
         if rigid_dq is not None:
             import numpy as np
@@ -316,7 +378,7 @@ class View:
     def c(self) -> invr_field_view:
         return invr_field_view(self.field.h, self.graph.h if self.graph else None, self.frame,
                                C.cast(self._dq, C.POINTER(C.c_float)) if self._dq is not None else None,
-                               _ptr(self.occupancy))
+                               _ptr(self.occupancy), self.deform.h if self.deform else None, _ptr(self.pose))
 
 
 def _views_array(views: Sequence[View]):

@@ -22,6 +22,8 @@ struct invr_ctx_s {
   Tune tune;
   uint32_t wait_limit = kDefaultWaitLimit;
   unsigned* status = nullptr;
+  float* pose_bias = nullptr;  // [kMaxViews][kDeformMaxHidden] per-view first-layer pose terms
+  int64_t cap_deform = 0;      // sample slots of the deformation-net buffers
   std::string err;
   // per-kernel event timing (invr_ctx_enable_timing)
   bool timing = false;
@@ -45,6 +47,20 @@ struct invr_field_s {
   float* m = nullptr;
   float* v = nullptr;
   int64_t* step = nullptr;  // device step counter
+  int res[kMaxL] = {};
+  uint32_t dense_mask = 0;
+};
+
+struct invr_deform_s {
+  invr_ctx ctx = nullptr;
+  invr_deform_desc desc{};
+  int64_t n_tab = 0, n_w = 0;
+  float* params = nullptr;  // tables then weights
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  int64_t* step = nullptr;
+  float* scratch = nullptr; // [num_sms][n_w] weight-gradient partials of the backward
   int res[kMaxL] = {};
   uint32_t dense_mask = 0;
 };
@@ -158,7 +174,8 @@ bool capturing(cudaStream_t s) {
 
 void free_workspace(Workspace& w) {
   void* ptrs[] = {w.ray_count, w.ray_bits, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray,
-                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part};
+                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part,
+                  w.s_vt, w.feat_d, w.dvc, w.dfeat_d};
   for (void* p : ptrs) dfree(p);
   w = Workspace{};
 }
@@ -210,8 +227,54 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
   ctx->cap_R = R;
   ctx->cap_S = S;
   ctx->cap_train = train;
+  ctx->cap_deform = 0;
   ctx->fwd_valid = false;
   return INVR_OK;
+}
+
+// The deformation-net buffers (v_t, the net's features, dL/dv_c, dL/d features), sized like
+// the sample slots; allocated the first time a call has a net.
+invr_status ensure_deform_workspace(invr_ctx ctx, cudaStream_t stream) {
+  Workspace& w = ctx->ws;
+  if (ctx->cap_deform >= w.S_cap && w.s_vt) return INVR_OK;
+  if (capturing(stream))
+    return fail(ctx, INVR_E_STATE, "deformation-net buffers missing during stream capture: run one call first");
+  INVR_CUDA(ctx, cudaDeviceSynchronize());
+  dfree(w.s_vt); dfree(w.feat_d); dfree(w.dvc); dfree(w.dfeat_d);
+  const int64_t S = w.S_cap;
+  INVR_CUDA(ctx, dmalloc(&w.s_vt, 3 * S));
+  INVR_CUDA(ctx, dmalloc(&w.feat_d, (size_t)kDeformMaxFeat * S));
+  INVR_CUDA(ctx, dmalloc(&w.dvc, 3 * S));
+  INVR_CUDA(ctx, dmalloc(&w.dfeat_d, (size_t)kDeformMaxFeat * S));
+  ctx->cap_deform = S;
+  return INVR_OK;
+}
+
+DeformDev deform_dev(invr_ctx ctx, invr_deform d, const float* pose, int view) {
+  DeformDev D{};
+  const invr_deform_desc& q = d->desc;
+  D.weights = d->params + d->n_tab;
+  D.grad_weights = d->grads + d->n_tab;
+  D.dw_scratch = d->scratch;
+  D.pose = pose;
+  D.pose_bias = ctx->pose_bias + (int64_t)view * kDeformMaxHidden;
+  D.enc.tables = d->params;
+  D.enc.weights = nullptr;
+  D.enc.weights_lp = nullptr;
+  D.enc.grad_tables = d->grads;
+  D.enc.grad_weights = nullptr;
+  D.enc.L = q.L;
+  D.enc.log2T = q.log2_T;
+  D.enc.mlp_in = q.L * q.F;
+  D.enc.mlp_kind = kMlpF32;
+  for (int l = 0; l < kMaxL; ++l) D.enc.res[l] = d->res[l];
+  D.enc.dense_mask = d->dense_mask;
+  D.n_feat = q.L * q.F;
+  D.pose_dim = q.pose_dim;
+  D.hidden = q.hidden;
+  D.n_hidden = q.n_hidden;
+  D.n_w = (int)d->n_w;
+  return D;
 }
 
 FieldDev field_dev(invr_field f) {
@@ -324,6 +387,14 @@ invr_status build_plan(invr_ctx ctx, const std::vector<const invr_render_args*>&
     V.field = field_dev(v.field);
     st = warp_dev(ctx, v, V.warp);
     if (st != INVR_OK) return st;
+    if (v.deform) {
+      if (v.deform->ctx != ctx) return fail(ctx, INVR_E_ARG, "deformation net belongs to another context");
+      if (!v.graph) return fail(ctx, INVR_E_ARG, "a deformation net needs the human view (graph != NULL)");
+      if (!v.pose_dev) return fail(ctx, INVR_E_ARG, "a deformation net needs pose_dev");
+      V.has_deform = 1;
+      V.deform = deform_dev(ctx, v.deform, v.pose_dev, i);
+      P.has_deform = 1;
+    }
     ray_begin += a->n_rays;
     blocks += (int)((a->n_rays + 1023) / 1024);
   }
@@ -333,12 +404,50 @@ invr_status build_plan(invr_ctx ctx, const std::vector<const invr_render_args*>&
   return INVR_OK;
 }
 
+// Run `launch` on plan copies that see the deformation net's encoding as each view's
+// field, v_t as the positions and the net's feature buffers, once per run of consecutive
+// views with a net (views without one are outside the runs).
+template <class Launch>
+cudaError_t deform_runs(const Plan& P, bool backward, Launch launch) {
+  for (int lo = 0; lo < P.n_views;) {
+    if (!P.v[lo].has_deform) {
+      ++lo;
+      continue;
+    }
+    int hi = lo + 1;
+    while (hi < P.n_views && P.v[hi].has_deform) ++hi;
+    Plan Q = P;
+    Q.view_lo = lo;
+    Q.view_hi = hi;
+    for (int v = lo; v < hi; ++v) Q.v[v].field = P.v[v].deform.enc;
+    Q.ws.s_vc = P.ws.s_vt;
+    Q.ws.feat = P.ws.feat_d;
+    Q.ws.dfeat = P.ws.dfeat_d;
+    if (backward) Q.grad_scale = 1.0f;  // dL/df of the net already carries the scale
+    cudaError_t e = launch(Q);
+    if (e != cudaSuccess) return e;
+    lo = hi;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
   cudaError_t e;
   if ((e = TIMED(ctx, "march_count", s, launch_march_count(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "scan", s, launch_scan(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "march_emit", s, launch_march_emit(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "warp", s, launch_warp(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  if (P.has_deform) {
+    // v_t = the warp; the net's features of v_t; v_c = v_t + delta v (written over s_vc)
+    if ((e = cudaMemcpyAsync(P.ws.s_vt, P.ws.s_vc, 3 * P.ws.S_cap * sizeof(float), cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+      return e;
+    if ((e = TIMED(ctx, "deform_encode", s, deform_runs(P, false, [&](const Plan& Q) {
+                     return launch_encode(Q, ctx->num_sms, s);
+                   }))) != cudaSuccess)
+      return e;
+    if ((e = TIMED(ctx, "deform_fwd", s, launch_deform_forward(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  }
   if ((e = TIMED(ctx, "encode", s, launch_encode_by_field(P, ctx->num_sms, s))) != cudaSuccess) return e;
   if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
     return e;
@@ -427,6 +536,7 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
   P.depth_weight = a->depth_weight;
   st = ensure_workspace(ctx, P.total_rays, P.total_rays * ns + (int64_t)P.n_views * kTile, true, s);
   if (st != INVR_OK) return st;
+  if (P.has_deform && (st = ensure_deform_workspace(ctx, s)) != INVR_OK) return st;
   P.ws = ctx->ws;
   INVR_CUDA(ctx, run_forward(ctx, P, s));
   INVR_CUDA(ctx, TIMED(ctx, "composite_train", s, launch_composite_train(P, a->loss_dev, s)));
@@ -445,6 +555,25 @@ invr_status train_backward(invr_ctx ctx, const invr_train_args* a, float scale, 
   if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
     INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd_tc", s, launch_mlp_bwd_tc(P, ctx->num_sms, s)));
   P.grad_scale = 1.0f;  // dL/dfeat already carries the scale
+  if (P.has_deform) {
+    // dL/dv_c through the field's encoding, then back through the net into its weights
+    // (per-CTA partials, summed per net) and its tables
+    INVR_CUDA(ctx, TIMED(ctx, "encode_dx", s, launch_encode_dx(P, ctx->num_sms, s)));
+    std::vector<const DeformDev*> nets;
+    for (int v = 0; v < P.n_views; ++v) {
+      if (!P.v[v].has_deform) continue;
+      bool seen = false;
+      for (const DeformDev* q : nets) seen = seen || q->dw_scratch == P.v[v].deform.dw_scratch;
+      if (!seen) nets.push_back(&P.v[v].deform);
+    }
+    for (const DeformDev* q : nets)
+      INVR_CUDA(ctx, cudaMemsetAsync(q->dw_scratch, 0, (size_t)ctx->num_sms * q->n_w * sizeof(float), s));
+    INVR_CUDA(ctx, TIMED(ctx, "deform_bwd", s, launch_deform_backward(P, ctx->num_sms, s)));
+    for (const DeformDev* q : nets) INVR_CUDA(ctx, launch_deform_reduce(*q, ctx->num_sms, s));
+    INVR_CUDA(ctx, TIMED(ctx, "deform_encode_bwd", s, deform_runs(P, true, [&](const Plan& Q) {
+                           return launch_encode_bwd(Q, ctx->num_sms, s);
+                         })));
+  }
   INVR_CUDA(ctx, TIMED(ctx, "encode_bwd", s, launch_encode_bwd_by_field(P, ctx->num_sms, s)));
   return INVR_OK;
 }
@@ -485,7 +614,9 @@ invr_status invr_ctx_create(invr_ctx* out, int device) {
   invr_ctx ctx = new invr_ctx_s();
   ctx->device = device;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess || cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
+  if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess || cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&ctx->pose_bias, sizeof(float) * kMaxViews * kDeformMaxHidden) != cudaSuccess) {
+    dfree(ctx->status);
     delete ctx;
     return INVR_E_OOM;
   }
@@ -500,6 +631,7 @@ invr_status invr_ctx_destroy(invr_ctx ctx) {
   clear_timing(ctx);
   free_workspace(ctx->ws);
   dfree(ctx->status);
+  dfree(ctx->pose_bias);
   delete ctx;
   return INVR_OK;
 }
@@ -927,6 +1059,7 @@ static invr_status render(invr_ctx ctx, const invr_render_args* a, bool joint, i
   if (st != INVR_OK) return st;
   st = ensure_workspace(ctx, P.total_rays, P.total_rays * a->n_samples + (int64_t)P.n_views * kTile, false, s);
   if (st != INVR_OK) return st;
+  if (P.has_deform && (st = ensure_deform_workspace(ctx, s)) != INVR_OK) return st;
   P.ws = ctx->ws;
   ctx->fwd_valid = false;
   INVR_CUDA(ctx, run_forward(ctx, P, s));
@@ -974,13 +1107,112 @@ invr_status invr_train_step(invr_ctx ctx, const invr_train_args* a, invr_stream 
   st = train_backward(ctx, a, 1.0f, s);
   if (st != INVR_OK) return st;
   std::vector<invr_field> done;
+  std::vector<invr_deform> nets;
   for (int b = 0; b < a->n_batches; ++b) {
     invr_field f = a->batches[b].views[0].field;
+    invr_deform d = a->batches[b].views[0].deform;
+    if (d && std::find(nets.begin(), nets.end(), d) == nets.end()) {
+      nets.push_back(d);
+      INVR_CUDA(ctx, TIMED(ctx, "step_increment", s, launch_step_increment(d->step, s)));
+      INVR_CUDA(ctx, TIMED(ctx, "adam", s,
+                           launch_adam(d->params, d->grads, d->grads, d->m, d->v, d->n_tab + d->n_w, d->step, a->lr,
+                                       a->beta1, a->beta2, a->adam_eps, s)));
+    }
     if (std::find(done.begin(), done.end(), f) != done.end()) continue;
     done.push_back(f);
     st = adam_step(f, a->lr, a->beta1, a->beta2, a->adam_eps, s);
     if (st != INVR_OK) return st;
   }
+  return INVR_OK;
+}
+
+invr_status invr_deform_create(invr_ctx ctx, const invr_deform_desc* desc, invr_deform* out) {
+  if (!ctx || !out || !desc) return INVR_E_ARG;
+  *out = nullptr;
+  const invr_deform_desc& q = *desc;
+  if (q.F != 2 || q.L < 1 || q.L > kMaxL || q.L * q.F > kDeformMaxFeat || (q.L * q.F) % 8 || q.log2_T < 4 ||
+      q.log2_T > 24 || q.N_min < 2 || !(q.growth >= 1.0) || q.hidden < 16 || q.hidden > kDeformMaxHidden ||
+      q.hidden % 16 || q.n_hidden < 1 || q.n_hidden > kDeformMaxLayers || q.pose_dim < 0 ||
+      q.pose_dim > kDeformMaxPose || q.prec != INVR_FP32)
+    return fail(ctx, INVR_E_ARG,
+                "deformation net: F = 2, L*F a multiple of 8 up to 32, hidden a multiple of 16 up to 128, "
+                "1..4 hidden layers, pose_dim <= 128, INVR_FP32");
+  DeviceGuard guard(ctx->device);
+  invr_deform d = new invr_deform_s();
+  d->ctx = ctx;
+  d->desc = q;
+  d->n_tab = (int64_t)q.L * ((int64_t)1 << q.log2_T) * q.F;
+  d->n_w = (int64_t)q.hidden * (q.L * q.F + q.pose_dim) + (int64_t)(q.n_hidden - 1) * q.hidden * q.hidden +
+           3 * (int64_t)q.hidden;
+  for (int l = 0; l < q.L; ++l) {
+    d->res[l] = level_resolution(q.N_min, q.growth, l);
+    const int64_t v = (int64_t)d->res[l] + 1;
+    if (v * v * v <= ((int64_t)1 << q.log2_T)) d->dense_mask |= 1u << l;
+  }
+  const int64_t n = d->n_tab + d->n_w;
+  if (dmalloc(&d->params, n) != cudaSuccess || dmalloc(&d->grads, n) != cudaSuccess ||
+      dmalloc(&d->m, n) != cudaSuccess || dmalloc(&d->v, n) != cudaSuccess || dmalloc(&d->step, 1) != cudaSuccess ||
+      dmalloc(&d->scratch, (size_t)ctx->num_sms * d->n_w) != cudaSuccess) {
+    dfree(d->params); dfree(d->grads); dfree(d->m); dfree(d->v); dfree(d->step); dfree(d->scratch);
+    delete d;
+    return fail(ctx, INVR_E_OOM, "deformation net allocation failed");
+  }
+  cudaMemset(d->params, 0, n * sizeof(float));
+  cudaMemset(d->grads, 0, n * sizeof(float));
+  cudaMemset(d->m, 0, n * sizeof(float));
+  cudaMemset(d->v, 0, n * sizeof(float));
+  cudaMemset(d->step, 0, sizeof(int64_t));
+  INVR_CUDA(ctx, cudaDeviceSynchronize());
+  *out = d;
+  return INVR_OK;
+}
+
+invr_status invr_deform_destroy(invr_deform d) {
+  if (!d) return INVR_E_ARG;
+  DeviceGuard guard(d->ctx->device);
+  cudaDeviceSynchronize();
+  dfree(d->params); dfree(d->grads); dfree(d->m); dfree(d->v); dfree(d->step); dfree(d->scratch);
+  delete d;
+  return INVR_OK;
+}
+
+invr_status invr_deform_set_params(invr_deform d, const float* tables, const float* weights, invr_stream stream) {
+  if (!d) return INVR_E_ARG;
+  invr_ctx ctx = d->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (tables) INVR_CUDA(ctx, cudaMemcpyAsync(d->params, tables, d->n_tab * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (weights)
+    INVR_CUDA(ctx, cudaMemcpyAsync(d->params + d->n_tab, weights, d->n_w * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return INVR_OK;
+}
+
+invr_status invr_deform_get_params(invr_deform d, float* tables, float* weights, invr_stream stream) {
+  if (!d) return INVR_E_ARG;
+  invr_ctx ctx = d->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (tables) INVR_CUDA(ctx, cudaMemcpyAsync(tables, d->params, d->n_tab * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (weights)
+    INVR_CUDA(ctx, cudaMemcpyAsync(weights, d->params + d->n_tab, d->n_w * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return INVR_OK;
+}
+
+invr_status invr_deform_get_grads(invr_deform d, float* gt, float* gw, invr_stream stream) {
+  if (!d) return INVR_E_ARG;
+  invr_ctx ctx = d->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (gt) INVR_CUDA(ctx, cudaMemcpyAsync(gt, d->grads, d->n_tab * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (gw) INVR_CUDA(ctx, cudaMemcpyAsync(gw, d->grads + d->n_tab, d->n_w * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return INVR_OK;
+}
+
+invr_status invr_deform_zero_grads(invr_deform d, invr_stream stream) {
+  if (!d) return INVR_E_ARG;
+  invr_ctx ctx = d->ctx;
+  DeviceGuard guard(ctx->device);
+  INVR_CUDA(ctx, cudaMemsetAsync(d->grads, 0, (d->n_tab + d->n_w) * sizeof(float), static_cast<cudaStream_t>(stream)));
   return INVR_OK;
 }
 
@@ -1015,6 +1247,7 @@ invr_status invr_probe_l2_atomic(invr_ctx ctx, float* table, int64_t n_floats, i
 invr_status invr_warp_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p, float* vc,
                              int32_t* ids, invr_stream stream) {
   if (!ctx || !view || n < 0) return fail(ctx, INVR_E_ARG, "bad warp_points arguments");
+  if (view->deform) return fail(ctx, INVR_E_ARG, "per-point calls do not run the deformation net");
   if (n > 0 && (!p || !vc)) return fail(ctx, INVR_E_ARG, "null pointer");
   DeviceGuard guard(ctx->device);
   WarpDev W;
@@ -1053,6 +1286,7 @@ invr_status invr_mlp_points(invr_ctx ctx, invr_field f, int64_t n, const float* 
 invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p, float* out,
                               invr_stream stream) {
   if (!ctx || !view || n < 0) return fail(ctx, INVR_E_ARG, "bad query_points arguments");
+  if (view->deform) return fail(ctx, INVR_E_ARG, "per-point calls do not run the deformation net");
   invr_status st = check_field(ctx, view->field);
   if (st != INVR_OK) return st;
   if (n == 0) return INVR_OK;
@@ -1081,6 +1315,7 @@ invr_status invr_occupancy_update(invr_ctx ctx, const invr_field_view* view, flo
                                   float* density, uint32_t* bits, invr_stream stream) {
   if (!ctx || !view) return INVR_E_ARG;
   if (!density || !bits) return fail(ctx, INVR_E_ARG, "null density or bits");
+  if (view->deform) return fail(ctx, INVR_E_ARG, "per-point calls do not run the deformation net");
   if (!(decay >= 0.0f && decay <= 1.0f)) return fail(ctx, INVR_E_ARG, "decay must lie in [0, 1]");
   invr_status st = check_field(ctx, view->field);
   if (st != INVR_OK) return st;
@@ -1121,6 +1356,7 @@ namespace invr {
 invr_status resolve_point_query(invr_ctx ctx, const invr_field_view* view, WarpDev& W, FieldDev& F, int& device,
                                 int& num_sms, unsigned*& status, uint32_t& wait_limit) {
   if (!ctx || !view) return INVR_E_ARG;
+  if (view->deform) return fail(ctx, INVR_E_ARG, "per-point calls do not run the deformation net");
   invr_status st = check_field(ctx, view->field);
   if (st != INVR_OK) return st;
   st = warp_dev(ctx, *view, W);

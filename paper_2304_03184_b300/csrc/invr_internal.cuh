@@ -54,15 +54,22 @@ struct WarpDev {
   const uint16_t* cand_n;   // [G^3] candidate count, kKnnOverflow = use all nodes
   int n_nodes, K, cap;
   float inv_r2;             // 1 / radius^2
-  // occupancy maintenance
-cudaError_t launch_occ_centres(float* p, int64_t n, cudaStream_t s);
-cudaError_t launch_occ_update(const float* sigma, int64_t n, float decay, float threshold, float* density,
-                              uint32_t* bits, cudaStream_t s);
-
-// look-up-table neighbour search (Sec. 4.2); lut_live == null: exact search
+  // look-up-table neighbour search (Sec. 4.2); lut_live == null: exact search
   int lut_res;              // G
   const uint16_t* lut_canon;  // [G^3][K] canonical KNN field
   const uint32_t* lut_live;   // [G^3] live voxel -> canonical voxel, kLutEmpty = none
+};
+
+// Pose-conditioned deformation net of a human view (Sec. 4.2): its hash encoding, FP32
+// weights W_1 [hidden][n_feat + pose_dim], W_2..W_n [hidden][hidden], W_out [3][hidden].
+struct DeformDev {
+  const float* weights;
+  float* grad_weights;
+  float* dw_scratch;        // [num_sms][n_w]: per-CTA weight-gradient partials of the backward
+  const float* pose;        // [pose_dim] theta of the view's frame
+  float* pose_bias;         // [hidden] W_1[:, n_feat:] theta (computed per call)
+  FieldDev enc;             // the net's own hash encoding (F = 2; mlp_kind F32, mlp_in = n_feat)
+  int n_feat, pose_dim, hidden, n_hidden, n_w;
 };
 
 struct ViewDev {
@@ -79,6 +86,8 @@ struct ViewDev {
   int scan_block_begin;     // first scan block of this view
   FieldDev field;
   WarpDev warp;
+  int has_deform;
+  DeformDev deform;
 };
 
 struct Workspace {
@@ -99,6 +108,11 @@ struct Workspace {
   float* dout;              // [4][S] dL/d o_0, dL/d z_rgb
   float* dfeat;             // [mlp_in][S]
   float* loss_part;         // [n loss blocks]
+  // deformation net (allocated when a call has one)
+  float* s_vt;              // [3][S] v_t, the warp before the net
+  float* feat_d;            // [n_feat][S] the net's hash features
+  float* dvc;               // [3][S] dL/dv_c (scaled like dfeat)
+  float* dfeat_d;           // [n_feat][S] dL/d(net features)
   int64_t S_cap;            // sample slots
   int64_t R_cap;            // ray slots
 };
@@ -124,6 +138,7 @@ struct Plan {
   float grad_scale;
   int agg_res;              // levels with N_l <= agg_res aggregate gradient runs per warp
   int view_lo, view_hi;     // views processed by the per-field launches ([0, n_views) by default)
+  int has_deform;           // some view has a deformation net
   uint32_t wait_limit;      // polls per bounded device wait
   Tune tune;                // launch shapes (autotuned per context)
   Workspace ws;
@@ -268,6 +283,16 @@ cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, f
                                  cudaStream_t s);
 cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
                                   cudaStream_t s);
+
+// deformation net
+cudaError_t launch_deform_forward(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_encode_dx(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_deform_backward(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_deform_reduce(const DeformDev& D, int n_parts, cudaStream_t s);
+constexpr int kDeformMaxFeat = 32;
+constexpr int kDeformMaxHidden = 128;
+constexpr int kDeformMaxLayers = 4;
+constexpr int kDeformMaxPose = 128;
 
 // occupancy maintenance
 cudaError_t launch_occ_centres(float* p, int64_t n, cudaStream_t s);

@@ -55,6 +55,9 @@ int main(void) {
   F(invr_graph_desc, radius) F(invr_graph_desc, n_frames)
   printf("invr_field_view %zu\n", sizeof(invr_field_view));
   F(invr_field_view, frame) F(invr_field_view, rigid_dq) F(invr_field_view, occupancy_dev)
+  F(invr_field_view, deform) F(invr_field_view, pose_dev)
+  printf("invr_deform_desc %zu\n", sizeof(invr_deform_desc));
+  F(invr_deform_desc, growth) F(invr_deform_desc, pose_dim) F(invr_deform_desc, n_hidden) F(invr_deform_desc, prec)
   printf("invr_render_args %zu\n", sizeof(invr_render_args));
   F(invr_render_args, n_samples) F(invr_render_args, t_eps) F(invr_render_args, views) F(invr_render_args, depth_dev)
   printf("invr_train_args %zu\n", sizeof(invr_train_args));
@@ -75,7 +78,8 @@ def test_ctypes_struct_layouts_match_header(invr, tmp_path):
     for line in subprocess.check_output([str(exe)], text=True).splitlines():
         k, v = line.split()
         got[k] = int(v)
-    for name in ("invr_field_desc", "invr_graph_desc", "invr_field_view", "invr_render_args", "invr_train_args"):
+    for name in ("invr_field_desc", "invr_graph_desc", "invr_field_view", "invr_render_args", "invr_train_args",
+                 "invr_deform_desc"):
         cls = getattr(invr, name)
         assert C.sizeof(cls) == got[name], name
         for key, off in got.items():
