@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-interleave", action="store_true")
     ap.add_argument("--no-lut", action="store_true")
+    ap.add_argument("--no-deform", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the batched key-frame step (no single-batch, FP32, render, LUT sections)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -411,6 +412,8 @@ def run_ours(args, rank, world, local):
         tw = bt["tw"]
     if not args.no_lut:
         out["lut_search"] = bench_lut(invr, args, flush, world, args.prec)
+    if not args.no_deform:
+        out["deform_net"] = bench_deform(invr, args, flush, world, args.prec)
     if not args.no_interleave:
         out["interleave"] = bench_interleave(invr, args, args.prec)
     out["clocks"] = clocks.stop()      # sampled over every timed region above
@@ -591,6 +594,66 @@ def bench_lut(invr, args, flush, world, prec_name, G=512):
             "canonical_position_diff": {"median": float(err.median()), "p99": float(torch.quantile(err, 0.99))}}
         del tb, fields, keep, graph, view, ctx
     return out
+
+
+def bench_deform(invr, args, flush, world, prec_name):
+    """The pose-conditioned deformation net (32 hash features + 72 pose -> 4 x 128 -> 3, FP32)
+    in front of the human field: the single-batch training step and the 512x512 human render,
+    with and without the net, and the per-kernel breakdown of the training step."""
+    import torch
+    from paper_2304_03184_b300 import synth
+    rng = np.random.default_rng(11)
+    tw = synth.train_step_workload(n_rays=args.rays)
+    dp, pose = synth.make_deform(rng), synth.make_pose(rng)
+    ctx = invr.Context(torch.cuda.current_device())
+    tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
+    steps = max(5, args.steps // 4)
+    ms_plain, _ = time_train(invr, ctx, tb, steps, args.warmup, flush, world)
+    net = invr.Deform.from_synth(ctx, dp)
+    pose_d = torch.from_numpy(pose).cuda()
+    g, occ, view = keep[0]
+    dview = invr.View(view.field, g, 0, None, occ, net, pose_d)
+    b = tb.batches[0]
+    tbd = invr.TrainBatches([(b[0], b[1], dview, b[3])], tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1,
+                            tw.beta2, tw.adam_eps)
+    ms_def, kt = time_train(invr, ctx, tbd, steps, args.warmup, flush, world)
+    # the net's forward on the tensor cores (BF16 operands)
+    net_tc = invr.Deform.from_synth(ctx, dp, PRECS["bf16"])
+    tview = invr.View(view.field, g, 0, None, occ, net_tc, pose_d)
+    tbt = invr.TrainBatches([(b[0], b[1], tview, b[3])], tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1,
+                            tw.beta2, tw.adam_eps)
+    ms_tc, kt_tc = time_train(invr, ctx, tbt, steps, args.warmup, flush, world)
+    S_nom = b[0].shape[1] * tw.n_samples
+    w = synth.two_field_render()
+    o, d = torch.from_numpy(w.rays.o).cuda(), torch.from_numpy(w.rays.d).cuda()
+    stream = torch.cuda.current_stream()
+
+    def render_ms(v):
+        for _ in range(3):
+            invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, [v])
+        ctx.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, e in ev:
+            flush.fill_(1)
+            a.record(stream)
+            invr.render_rays(ctx, o, d, w.n_samples, w.t_eps, [v])
+            e.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(e) for a, e in ev]))
+    r_plain, r_def, r_tc = render_ms(view), render_ms(dview), render_ms(tview)
+    net.close()
+    net_tc.close()
+    return {"workload": tw.name, "net": "32 hash features + 72 pose -> 4 x 128 -> 3, FP32", "field_prec": prec_name,
+            "train": {"with_net": {"value": round(world * S_nom / (ms_def * 1e-3), 1), "ms_per_step": round(ms_def, 3)},
+                      "without": {"value": round(world * S_nom / (ms_plain * 1e-3), 1),
+                                  "ms_per_step": round(ms_plain, 3)},
+                      "with_net_tc_forward": {"value": round(world * S_nom / (ms_tc * 1e-3), 1),
+                                              "ms_per_step": round(ms_tc, 3)},
+                      "kernels_ms_per_step": {k: round(v[0] / steps, 4) for k, v in sorted(kt.items())},
+                      "kernels_ms_per_step_tc_forward": {k: round(v[0] / steps, 4) for k, v in sorted(kt_tc.items())}},
+            "render_human_512x512": {"with_net_ms": round(r_def, 3), "with_net_tc_ms": round(r_tc, 3),
+                                     "without_ms": round(r_plain, 3),
+                                     "with_net_tc_mrays_s": round(w.rays.n / (r_tc * 1e-3) / 1e6, 3)}}
 
 
 def bench_interleave(invr, args, prec_name):

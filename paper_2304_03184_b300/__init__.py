@@ -320,19 +320,19 @@ class Deform:
     and Adam state on the device."""
 
     def __init__(self, ctx: Context, L=16, log2_T=19, F=2, N_min=16, growth=1.38, pose_dim=72, hidden=128,
-                 n_hidden=4):
+                 n_hidden=4, prec: int = INVR_FP32):
         h = C.c_void_p()
-        desc = invr_deform_desc(L, log2_T, F, N_min, growth, pose_dim, hidden, n_hidden, INVR_FP32)
+        desc = invr_deform_desc(L, log2_T, F, N_min, growth, pose_dim, hidden, n_hidden, prec)
         _check(lib().invr_deform_create(ctx.h, C.byref(desc), C.byref(h)), ctx.h)
         self.ctx, self.desc, self.h = ctx, desc, h
         self.n_tab = L * (1 << log2_T) * F
         self.n_w = hidden * (L * F + pose_dim) + (n_hidden - 1) * hidden * hidden + 3 * hidden
 
     @classmethod
-    def from_synth(cls, ctx: Context, dp):
+    def from_synth(cls, ctx: Context, dp, prec: int = INVR_FP32):
         torch = _torch()
         d = dp.desc
-        net = cls(ctx, d.L, d.log2_T, d.F, d.N_min, d.growth, d.pose_dim, d.hidden, d.n_hidden)
+        net = cls(ctx, d.L, d.log2_T, d.F, d.N_min, d.growth, d.pose_dim, d.hidden, d.n_hidden, prec)
         net.set_params(torch.from_numpy(dp.tables.reshape(-1)).cuda(), torch.from_numpy(dp.weights).cuda())
         return net
 

@@ -70,6 +70,7 @@ struct DeformDev {
   float* pose_bias;         // [hidden] W_1[:, n_feat:] theta (computed per call)
   FieldDev enc;             // the net's own hash encoding (F = 2; mlp_kind F32, mlp_in = n_feat)
   int n_feat, pose_dim, hidden, n_hidden, n_w;
+  int tc;                   // forward on the tensor cores (BF16 operands) instead of FP32 SIMT
 };
 
 struct ViewDev {
@@ -286,6 +287,7 @@ cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* fea
 
 // deformation net
 cudaError_t launch_deform_forward(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_deform_forward_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_dx(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_deform_backward(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_deform_reduce(const DeformDev& D, int n_parts, cudaStream_t s);

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd(const __grid_constan
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t s0 = t * kFwdTS;
     const ViewDev& V = P.v[view_of_slot(P, s0)];
-    if (!V.has_deform) continue;
+    if (!V.has_deform || V.deform.tc) continue;
     const DeformDev& D = V.deform;
     const int H = D.hidden, n_in = D.n_feat + D.pose_dim;
     for (int e = threadIdx.x; e < D.n_feat * kFwdTS; e += kThreads) {
@@ -358,10 +358,20 @@ constexpr size_t kBwdSmem =
 
 cudaError_t launch_deform_forward(const Plan& P, int num_sms, cudaStream_t s) {
   k_deform_bias<<<P.n_views, kThreads, 0, s>>>(P);
-  cudaError_t e = cudaFuncSetAttribute(k_deform_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  if (e != cudaSuccess) return e;
-  k_deform_fwd<<<num_sms, kThreads, kFwdSmem, s>>>(P);
-  return cudaGetLastError();
+  bool simt = false, tc = false;
+  for (int v = 0; v < P.n_views; ++v) {
+    if (!P.v[v].has_deform) continue;
+    (P.v[v].deform.tc ? tc : simt) = true;
+  }
+  cudaError_t e = cudaSuccess;
+  if (simt) {
+    e = cudaFuncSetAttribute(k_deform_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    if (e != cudaSuccess) return e;
+    k_deform_fwd<<<num_sms, kThreads, kFwdSmem, s>>>(P);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && tc) e = launch_deform_forward_tc(P, num_sms, s);
+  return e;
 }
 
 cudaError_t launch_encode_dx(const Plan& P, int num_sms, cudaStream_t s) {

@@ -34,16 +34,20 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
+MIXED_COLOUR_TOL = 2e-3
+
+
 class Human:
     """A human view with a deformation net on both sides."""
 
-    def __init__(self, invr, ctx, oracle, sv, dp, pose, prec=0, field=None, ofield=None, net=None, onet=None):
+    def __init__(self, invr, ctx, oracle, sv, dp, pose, prec=0, field=None, ofield=None, net=None, onet=None,
+                 net_prec=0):
         self.field = field or invr.Field.from_synth(ctx, sv.field, prec)
         g = sv.graph
         self.graph = invr.Graph(ctx, g.x_canon.shape[1], g.K, g.radius, 1, cu(g.x_canon))
         self.graph.set_pose(0, cu(g.dq), cu(g.x_live))
         self.occ = cu(sv.occupancy) if sv.occupancy is not None else None
-        self.net = net or invr.Deform.from_synth(ctx, dp)
+        self.net = net or invr.Deform.from_synth(ctx, dp, net_prec)
         self.pose = cu(pose)
         self.view = invr.View(self.field, self.graph, 0, None, self.occ, self.net, self.pose)
         self.onet = onet or oracle.Deform.from_params(dp)
@@ -71,6 +75,42 @@ def test_deform_render_matches_oracle(env):
     assert np.abs(plain.rgba - ref.rgba).max() > 1e-3
 
 
+@pytest.mark.parametrize("field_prec", ["fp32", "bf16"])
+def test_deform_tensor_core_forward_matches_oracle(env, field_prec):
+    """The net's forward on the tensor cores (BF16 operands, FP32 accumulation): renders
+    within the mixed-precision colour tolerance, with an FP32 or a BF16 field."""
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(107)
+    w, dp, pose = _render_workload(rng)
+    code = invr.INVR_MLP_BF16 if field_prec == "bf16" else invr.INVR_FP32
+    hum = Human(invr, ctx, oracle, w.views[0], dp, pose, prec=code, net_prec=invr.INVR_MLP_BF16)
+    rgba, _ = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [hum.view])
+    ctx.sync()
+    ref = oracle.render(w.rays.o, w.rays.d, w.n_samples, w.t_eps, [hum.oview])
+    np.testing.assert_allclose(host(rgba), ref.rgba, rtol=0, atol=MIXED_COLOUR_TOL)
+
+
+def test_deform_tensor_core_forward_with_training(env):
+    """Training with the tensor-core forward of the net.  Its BF16 operands leave ~1e-4 of
+    error in delta v, hence in v_c, and dL/dv_c (the encoding's derivative in the point)
+    changes by the fraction of a finest-level cell that this error spans: with the 8-level
+    field (finest N_l = 273) the loss stays within 1e-3 and the net's gradients within 1e-1
+    (weights) and 2e-1 (tables) of the FP64 oracle's."""
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(108)
+    tw = synth.train_step_workload(seed=18, n_rays=1024, field_desc=synth.CFG1_FIELD)
+    dp, pose = synth.make_deform(rng), synth.make_pose(rng)
+    tb, gfields, ofields, net, onet, obatches, keep = _train(env, tw, dp, [pose], net_prec=invr.INVR_MLP_BF16)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-3 * oloss
+    gt, gw = (host(x) for x in net.get_grads())
+    ogt, ogw = ograds[id(onet)]
+    assert _rel(gw, ogw) <= 1e-1 and _rel(gt, ogt) <= 2e-1, (_rel(gw, ogw), _rel(gt, ogt))
+
+
 def test_deform_zero_output_layer_is_the_plain_warp(env):
     invr, ctx, oracle = env
     rng = np.random.default_rng(102)
@@ -84,11 +124,11 @@ def test_deform_zero_output_layer_is_the_plain_warp(env):
     np.testing.assert_array_equal(host(a), host(b))
 
 
-def _train(env, tw, dp, poses, loss="huber"):
+def _train(env, tw, dp, poses, loss="huber", net_prec=0):
     invr, ctx, oracle = env
     ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
     gfields = {id(fp): invr.Field.from_synth(ctx, fp) for fp in tw.fields}
-    net, onet = invr.Deform.from_synth(ctx, dp), oracle.Deform.from_params(dp)
+    net, onet = invr.Deform.from_synth(ctx, dp, net_prec), oracle.Deform.from_params(dp)
     batches, obatches, keep = [], [], []
     k = 0
     for b in tw.batches:
