@@ -607,6 +607,8 @@ def bench_deform(invr, args, flush, world, prec_name):
     dp, pose = synth.make_deform(rng), synth.make_pose(rng)
     ctx = invr.Context(torch.cuda.current_device())
     tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
+    R = tb.batches[0][0].shape[1]
+    ctx.reserve(R, 32)          # sample slots (and the net's operand tiles) for ~12 occupied per ray
     steps = max(5, args.steps // 4)
     ms_plain, _ = time_train(invr, ctx, tb, steps, args.warmup, flush, world)
     net = invr.Deform.from_synth(ctx, dp)
@@ -617,7 +619,7 @@ def bench_deform(invr, args, flush, world, prec_name):
     tbd = invr.TrainBatches([(b[0], b[1], dview, b[3])], tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1,
                             tw.beta2, tw.adam_eps)
     ms_def, kt = time_train(invr, ctx, tbd, steps, args.warmup, flush, world)
-    # the net's forward on the tensor cores (BF16 operands)
+    # the net on the tensor cores (BF16 operands, forward and backward)
     net_tc = invr.Deform.from_synth(ctx, dp, PRECS["bf16"])
     tview = invr.View(view.field, g, 0, None, occ, net_tc, pose_d)
     tbt = invr.TrainBatches([(b[0], b[1], tview, b[3])], tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1,
@@ -643,14 +645,15 @@ def bench_deform(invr, args, flush, world, prec_name):
     r_plain, r_def, r_tc = render_ms(view), render_ms(dview), render_ms(tview)
     net.close()
     net_tc.close()
-    return {"workload": tw.name, "net": "32 hash features + 72 pose -> 4 x 128 -> 3, FP32", "field_prec": prec_name,
+    return {"workload": tw.name, "net": "32 hash features + 72 pose -> 4 x 128 -> 3 (FP32 SIMT, or BF16 tcgen05)",
+            "field_prec": prec_name,
             "train": {"with_net": {"value": round(world * S_nom / (ms_def * 1e-3), 1), "ms_per_step": round(ms_def, 3)},
                       "without": {"value": round(world * S_nom / (ms_plain * 1e-3), 1),
                                   "ms_per_step": round(ms_plain, 3)},
-                      "with_net_tc_forward": {"value": round(world * S_nom / (ms_tc * 1e-3), 1),
+                      "with_net_tc": {"value": round(world * S_nom / (ms_tc * 1e-3), 1),
                                               "ms_per_step": round(ms_tc, 3)},
                       "kernels_ms_per_step": {k: round(v[0] / steps, 4) for k, v in sorted(kt.items())},
-                      "kernels_ms_per_step_tc_forward": {k: round(v[0] / steps, 4) for k, v in sorted(kt_tc.items())}},
+                      "kernels_ms_per_step_tc": {k: round(v[0] / steps, 4) for k, v in sorted(kt_tc.items())}},
             "render_human_512x512": {"with_net_ms": round(r_def, 3), "with_net_tc_ms": round(r_tc, 3),
                                      "without_ms": round(r_plain, 3),
                                      "with_net_tc_mrays_s": round(w.rays.n / (r_tc * 1e-3) / 1e6, 3)}}

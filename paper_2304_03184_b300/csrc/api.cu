@@ -175,7 +175,7 @@ bool capturing(cudaStream_t s) {
 void free_workspace(Workspace& w) {
   void* ptrs[] = {w.ray_count, w.ray_bits, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray,
                   w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part,
-                  w.s_vt, w.feat_d, w.dvc, w.dfeat_d};
+                  w.s_vt, w.feat_d, w.dvc, w.dfeat_d, w.def_x, w.def_h, w.def_g, w.def_gout};
   for (void* p : ptrs) dfree(p);
   w = Workspace{};
 }
@@ -241,12 +241,29 @@ invr_status ensure_deform_workspace(invr_ctx ctx, cudaStream_t stream) {
     return fail(ctx, INVR_E_STATE, "deformation-net buffers missing during stream capture: run one call first");
   INVR_CUDA(ctx, cudaDeviceSynchronize());
   dfree(w.s_vt); dfree(w.feat_d); dfree(w.dvc); dfree(w.dfeat_d);
+  dfree(w.def_x); dfree(w.def_h); dfree(w.def_g); dfree(w.def_gout);
+  w.def_x = w.def_h = w.def_g = w.def_gout = nullptr;
   const int64_t S = w.S_cap;
   INVR_CUDA(ctx, dmalloc(&w.s_vt, 3 * S));
   INVR_CUDA(ctx, dmalloc(&w.feat_d, (size_t)kDeformMaxFeat * S));
   INVR_CUDA(ctx, dmalloc(&w.dvc, 3 * S));
   INVR_CUDA(ctx, dmalloc(&w.dfeat_d, (size_t)kDeformMaxFeat * S));
   ctx->cap_deform = S;
+  return INVR_OK;
+}
+
+// Operand tiles of the tensor-core training of a net (2,144 bytes per sample slot).
+invr_status ensure_deform_tc_workspace(invr_ctx ctx, cudaStream_t stream) {
+  Workspace& w = ctx->ws;
+  if (w.def_h) return INVR_OK;
+  if (capturing(stream))
+    return fail(ctx, INVR_E_STATE, "deformation-net buffers missing during stream capture: run one call first");
+  INVR_CUDA(ctx, cudaDeviceSynchronize());
+  const size_t tiles = (size_t)(w.S_cap / kTile);
+  INVR_CUDA(ctx, dmalloc(&w.def_x, tiles * kTile * kDeformMaxFeat * 2));
+  INVR_CUDA(ctx, dmalloc(&w.def_h, (size_t)kDeformMaxLayers * tiles * kTile * kDeformMaxHidden * 2));
+  INVR_CUDA(ctx, dmalloc(&w.def_g, (size_t)kDeformMaxLayers * tiles * kTile * kDeformMaxHidden * 2));
+  INVR_CUDA(ctx, dmalloc(&w.def_gout, tiles * kTile * 16 * 2));
   return INVR_OK;
 }
 
@@ -538,6 +555,17 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
   st = ensure_workspace(ctx, P.total_rays, P.total_rays * ns + (int64_t)P.n_views * kTile, true, s);
   if (st != INVR_OK) return st;
   if (P.has_deform && (st = ensure_deform_workspace(ctx, s)) != INVR_OK) return st;
+  const DeformDev* tc_net = nullptr;
+  for (int v = 0; v < P.n_views; ++v) {
+    if (!P.v[v].has_deform || !P.v[v].deform.tc) continue;
+    if (tc_net && tc_net->weights != P.v[v].deform.weights)
+      return fail(ctx, INVR_E_ARG, "one training call takes at most one tensor-core deformation net");
+    tc_net = &P.v[v].deform;
+  }
+  if (tc_net) {
+    if ((st = ensure_deform_tc_workspace(ctx, s)) != INVR_OK) return st;
+    P.deform_store = 1;
+  }
   P.ws = ctx->ws;
   INVR_CUDA(ctx, run_forward(ctx, P, s));
   INVR_CUDA(ctx, TIMED(ctx, "composite_train", s, launch_composite_train(P, a->loss_dev, s)));
@@ -569,7 +597,11 @@ invr_status train_backward(invr_ctx ctx, const invr_train_args* a, float scale, 
     }
     for (const DeformDev* q : nets)
       INVR_CUDA(ctx, cudaMemsetAsync(q->dw_scratch, 0, (size_t)ctx->num_sms * q->n_w * sizeof(float), s));
-    INVR_CUDA(ctx, TIMED(ctx, "deform_bwd", s, launch_deform_backward(P, ctx->num_sms, s)));
+    bool simt = false, tcn = false;
+    for (int v = 0; v < P.n_views; ++v)
+      if (P.v[v].has_deform) (P.v[v].deform.tc ? tcn : simt) = true;
+    if (simt) INVR_CUDA(ctx, TIMED(ctx, "deform_bwd", s, launch_deform_backward(P, ctx->num_sms, s)));
+    if (tcn) INVR_CUDA(ctx, TIMED(ctx, "deform_bwd_tc", s, launch_deform_backward_tc(P, ctx->num_sms, s)));
     for (const DeformDev* q : nets) INVR_CUDA(ctx, launch_deform_reduce(*q, ctx->num_sms, s));
     INVR_CUDA(ctx, TIMED(ctx, "deform_encode_bwd", s, deform_runs(P, true, [&](const Plan& Q) {
                            return launch_encode_bwd(Q, ctx->num_sms, s);
@@ -1138,6 +1170,9 @@ invr_status invr_deform_create(invr_ctx ctx, const invr_deform_desc* desc, invr_
     return fail(ctx, INVR_E_ARG,
                 "deformation net: F = 2, L*F a multiple of 8 up to 32, hidden a multiple of 16 up to 128, "
                 "1..4 hidden layers, pose_dim <= 128, INVR_FP32 or INVR_MLP_BF16");
+  if (q.prec == INVR_MLP_BF16 && (q.hidden != kDeformMaxHidden || q.L * q.F != kDeformMaxFeat ||
+                                  q.pose_dim > kDeformTcMaxPose))
+    return fail(ctx, INVR_E_ARG, "a tensor-core deformation net has 32 features, hidden 128 and pose_dim <= 80");
   DeviceGuard guard(ctx->device);
   invr_deform d = new invr_deform_s();
   d->ctx = ctx;

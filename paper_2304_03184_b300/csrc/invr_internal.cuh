@@ -114,6 +114,12 @@ struct Workspace {
   float* feat_d;            // [n_feat][S] the net's hash features
   float* dvc;               // [3][S] dL/dv_c (scaled like dfeat)
   float* dfeat_d;           // [n_feat][S] dL/d(net features)
+  // tensor-core training of a net: per 128-sample tile, 16-bit operand tiles in the
+  // K-major MMA layout (32 KB per [128 x 128] tile; tile T of layer l at l * S_cap/128 + T)
+  uint8_t* def_x;           // [S/128] x [128 x 32]  the net's input features
+  uint8_t* def_h;           // [kDeformMaxLayers][S/128] x [128 x 128]  ReLU outputs h_1..h_n
+  uint8_t* def_g;           // [kDeformMaxLayers][S/128] x [128 x 128]  dL/d(pre-activation) of h_1..h_n
+  uint8_t* def_gout;        // [S/128] x [128 x 16]  dL/d(delta v), padded to 16 columns
   int64_t S_cap;            // sample slots
   int64_t R_cap;            // ray slots
 };
@@ -140,6 +146,7 @@ struct Plan {
   int agg_res;              // levels with N_l <= agg_res aggregate gradient runs per warp
   int view_lo, view_hi;     // views processed by the per-field launches ([0, n_views) by default)
   int has_deform;           // some view has a deformation net
+  int deform_store;         // training: the tensor-core forward keeps its operand tiles
   uint32_t wait_limit;      // polls per bounded device wait
   Tune tune;                // launch shapes (autotuned per context)
   Workspace ws;
@@ -288,6 +295,8 @@ cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* fea
 // deformation net
 cudaError_t launch_deform_forward(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_deform_forward_tc(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_deform_backward_tc(const Plan& P, int num_sms, cudaStream_t s);
+constexpr int kDeformTcMaxPose = 80;   // pose columns of the tensor-core weight gradient
 cudaError_t launch_encode_dx(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_deform_backward(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_deform_reduce(const DeformDev& D, int n_parts, cudaStream_t s);

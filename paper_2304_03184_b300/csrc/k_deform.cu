@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_bwd(const __grid_constan
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t s0 = t * kBwdTS;
     const ViewDev& V = P.v[view_of_slot(P, s0)];
-    if (!V.has_deform) continue;
+    if (!V.has_deform || V.deform.tc) continue;
     const DeformDev& D = V.deform;
     const int H = D.hidden, n = D.n_hidden, n_in = D.n_feat + D.pose_dim;
     float* part = D.dw_scratch + (int64_t)blockIdx.x * D.n_w;

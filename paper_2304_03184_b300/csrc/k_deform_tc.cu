@@ -25,6 +25,9 @@ constexpr int kH = kDeformMaxHidden;        // 128
 constexpr int kKf = kDeformMaxFeat;         // 32
 constexpr uint32_t kTmemCols = 512;         // per slot: D at 256 s + 0 (H cols), out at 256 s + 128 (16)
 constexpr uint32_t kDrainLimit = 1u << 22;
+constexpr int64_t kHTile = (int64_t)kTM * kH * 2;    // bytes of a stored [128 x 128] operand tile
+constexpr int64_t kXTile = (int64_t)kTM * kKf * 2;   // [128 x 32]
+constexpr int64_t kGoTile = (int64_t)kTM * 16 * 2;   // [128 x 16]
 
 // shared-memory plan (bytes)
 constexpr uint32_t OFF_W1 = 0;                                   // [H][Kf]
@@ -156,6 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
         q.z = tc::pack2<true>(x[4], x[5]);
         q.w = tc::pack2<true>(x[6], x[7]);
         *reinterpret_cast<uint4*>(X + tc::kmajor_offset(t, k, Kf)) = q;
+        if (P.deform_store)
+          *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(t, k, Kf)) = q;
       }
       float* bias = reinterpret_cast<float*>(sm + OFF_BIAS) + j * kH;
       for (int o = t; o < H; o += kThreads) bias[o] = P.v[slot[j].view].deform.pose_bias[o];
@@ -204,6 +209,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
             hi.w = tc::pack2<true>(fmaxf(v[14], 0.f), fmaxf(v[15], 0.f));
             *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c, H)) = lo;
             *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c + 8, H)) = hi;
+            if (P.deform_store) {
+              uint8_t* g = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + slot[j].s0 / kTM) * kHTile;
+              *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c, H)) = lo;
+              *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c + 8, H)) = hi;
+            }
           }
           operands_ready();
           if (t == 0) {
@@ -244,7 +254,395 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
   }
 }
 
+// ------------------------------------------------------------------ backward
+// Adjoint MMA: D (128 x N) = G (smem, 128 x K, K-major) * W with W the forward weight
+// [K rows][N columns] as staged for the forward (K-major in its own layout), read as an
+// MN-major operand: column groups 128 B apart, row groups N * 16 B apart.
+__device__ __forceinline__ void issue_adjoint(uint32_t d_tmem, uint32_t a_saddr, uint32_t w_saddr, int K, int N) {
+  const uint32_t idesc = tc::idesc_f16(kTM, N, true) | (1u << 16);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t ad = tc::smem_desc(a_saddr + kk * 256, 128, K * 16);
+    const uint64_t bd = tc::smem_desc(w_saddr + kk * 32 * N, N * 16, 128);
+    tc::mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+  }
+}
+
+// Weight-gradient MMA over the 128 samples of a tile: D (M = a_units x N = b_units) (+)=
+// A^T B, A and B [128 samples][units] K-major tiles read as MN-major operands (unit groups
+// 128 B apart, sample groups units * 16 B apart).
+__device__ __forceinline__ void issue_dw(uint32_t d_tmem, uint32_t a_saddr, int a_units, uint32_t b_saddr,
+                                         int b_units, bool accumulate) {
+  const uint32_t idesc = tc::idesc_f16(kTM, b_units, true) | (1u << 15) | (1u << 16);
+  for (int kk = 0; kk < kTM / 16; ++kk) {
+    const uint64_t ad = tc::smem_desc(a_saddr + kk * 32 * a_units, a_units * 16, 128);
+    const uint64_t bd = tc::smem_desc(b_saddr + kk * 32 * b_units, b_units * 16, 128);
+    tc::mma_f16(d_tmem, ad, bd, idesc, (accumulate || kk > 0) ? 1u : 0u);
+  }
+}
+
+// a 16-bit value is positive iff its sign bit is clear and it is not +0
+__device__ __forceinline__ float relu_mask(uint32_t w, int half) {
+  const uint32_t h = half ? (w >> 16) : (w & 0xFFFFu);
+  return (!(h & 0x8000u) && (h & 0x7FFFu)) ? 1.0f : 0.0f;
+}
+
+// The adjoint chain: per tile, dL/d(delta v) (the stored dL/dv_c, padded to 16 columns)
+// -> g_n = (g_out W_out) . [h_n > 0] -> g_{l} = (g_{l+1} W_{l+1}) . [h_l > 0] -> dL/df =
+// g_1 W_1f.  The ReLU masks come from the forward's stored h tiles; every g tile (and the
+// padded g_out tile) is stored for the weight-gradient kernel; dL/df is written FP32
+// feature-major for the scatter into the net's tables.  Two tiles in flight, as the forward.
+__global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_constant__ Plan P) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int64_t S_cap = P.ws.S_cap;
+  const int64_t S = P.ws.view_base[P.n_views];
+  if (S > S_cap) return;
+  const int t = threadIdx.x, warp = t >> 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
+  const uint32_t mbar0 = tc::smem_u32(sm + OFF_MISC);
+  const uint32_t sbase = tc::smem_u32(sm);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
+  if (t == 0) {
+    tc::mbar_init(mbar0, 1);
+    tc::mbar_init(mbar0 + 8, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const int64_t tiles_cap = S_cap / kTM;
+  const int64_t n_tiles = S / kTM;
+  const float* loaded = nullptr;
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  int64_t next = blockIdx.x;
+  auto next_tile = [&](Slot& sl) {
+    sl.s0 = -1;
+    while (next < n_tiles) {
+      const int64_t s0 = next * kTM;
+      next += gridDim.x;
+      const int v = view_of_slot(P, s0);
+      if (P.v[v].has_deform && P.v[v].deform.tc) {
+        sl.s0 = s0;
+        sl.view = v;
+        return;
+      }
+    }
+  };
+  Slot slot[2];
+  while (ok) {
+    next_tile(slot[0]);
+    next_tile(slot[1]);
+    if (slot[0].s0 < 0) break;
+    const DeformDev& D = P.v[slot[0].view].deform;
+    if (slot[1].s0 >= 0 && P.v[slot[1].view].deform.weights != D.weights) {
+      next -= gridDim.x;
+      slot[1].s0 = -1;
+    }
+    const int H = kH, n = D.n_hidden, Kf = kKf;
+    if (D.weights != loaded) {
+      __syncthreads();
+      const int n_in = D.n_feat + D.pose_dim;
+      stage(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
+      for (int l = 1; l < n; ++l) stage(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
+      stage(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      loaded = D.weights;
+    }
+    // g_out tiles: dL/dv_c (3 columns) padded to 16, in smem and stored
+    for (int j = 0; j < 2; ++j) {
+      if (slot[j].s0 < 0) continue;
+      const int64_t g = slot[j].s0 + t;
+      float v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = i < 3 ? P.ws.dvc[(int64_t)i * S_cap + g] : 0.0f;
+      uint4 lo, hi;
+      lo.x = tc::pack2<true>(v[0], v[1]);
+      lo.y = tc::pack2<true>(v[2], v[3]);
+      lo.z = tc::pack2<true>(v[4], v[5]);
+      lo.w = tc::pack2<true>(v[6], v[7]);
+      hi.x = hi.y = hi.z = hi.w = 0u;
+      uint8_t* go = sm + OFF_X + j * kXTile;
+      *reinterpret_cast<uint4*>(go + tc::kmajor_offset(t, 0, 16)) = lo;
+      *reinterpret_cast<uint4*>(go + tc::kmajor_offset(t, 8, 16)) = hi;
+      uint8_t* gg = P.ws.def_gout + (slot[j].s0 / kTM) * kGoTile;
+      *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, 0, 16)) = lo;
+      *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, 8, 16)) = hi;
+    }
+    operands_ready();
+    if (t == 0) {
+      tc::fence_after_sync();
+      for (int j = 0; j < 2; ++j) {
+        if (slot[j].s0 < 0) continue;
+        issue_adjoint(tmem + 256 * j, sbase + OFF_X + j * kXTile, sbase + OFF_WO, 16, H);
+        tc::commit_to(mbar0 + 8 * j);
+      }
+    }
+    for (int j = 0; j < 2; ++j) pending[j] = slot[j].s0 >= 0;
+    // stage e = 0..n-1: mask with h_{n-1-e}, store g, issue the next adjoint; stage n: dL/df
+    for (int e = 0; e <= n && ok; ++e) {
+      for (int j = 0; j < 2; ++j) {
+        if (slot[j].s0 < 0) continue;
+        ok = tc::mbar_wait(mbar0 + 8 * j, phase[j], P.wait_limit);
+        if (!__syncthreads_and(ok)) {
+          ok = false;
+          break;
+        }
+        phase[j] ^= 1u;
+        pending[j] = false;
+        tc::fence_after_sync();
+        const uint32_t row = tmem + 256 * j + lane_off;
+        const int64_t T = slot[j].s0 / kTM;
+        if (e < n) {
+          const int li = n - 1 - e;
+          const uint8_t* hg = P.ws.def_h + ((int64_t)li * tiles_cap + T) * kHTile;
+          uint8_t* gs = sm + OFF_HB + j * kHTile;
+          uint8_t* gg = P.ws.def_g + ((int64_t)li * tiles_cap + T) * kHTile;
+          for (int c = 0; c < H; c += 16) {
+            float v[16];
+            tc::tmem_ld16(row + c, v);
+            const uint4 m0 = *reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(t, c, H));
+            const uint4 m1 = *reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(t, c + 8, H));
+            const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              v[2 * i] *= relu_mask(mw[i], 0);
+              v[2 * i + 1] *= relu_mask(mw[i], 1);
+            }
+            uint4 lo, hi;
+            lo.x = tc::pack2<true>(v[0], v[1]);
+            lo.y = tc::pack2<true>(v[2], v[3]);
+            lo.z = tc::pack2<true>(v[4], v[5]);
+            lo.w = tc::pack2<true>(v[6], v[7]);
+            hi.x = tc::pack2<true>(v[8], v[9]);
+            hi.y = tc::pack2<true>(v[10], v[11]);
+            hi.z = tc::pack2<true>(v[12], v[13]);
+            hi.w = tc::pack2<true>(v[14], v[15]);
+            *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c, H)) = lo;
+            *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c + 8, H)) = hi;
+            *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c, H)) = lo;
+            *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c + 8, H)) = hi;
+          }
+          operands_ready();
+          if (t == 0) {
+            tc::fence_after_sync();
+            if (li > 0)
+              issue_adjoint(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_WH + (li - 1) * kH * kH * 2, H, H);
+            else
+              issue_adjoint(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_W1, H, Kf);
+            tc::commit_to(mbar0 + 8 * j);
+          }
+          pending[j] = true;
+        } else {
+          const int64_t g = slot[j].s0 + t;
+          for (int c = 0; c < Kf; c += 16) {
+            float v[16];
+            tc::tmem_ld16(row + c, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (c + i < D.n_feat) P.ws.dfeat_d[(int64_t)(c + i) * S_cap + g] = v[i];
+          }
+          tc::fence_before_sync();
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(P.status, kStatusTimeout);
+    for (int j = 0; j < 2; ++j)
+      if (pending[j]) tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Weight gradients of the net, accumulated in tensor memory over every tile the CTA visits:
+//   dW_l (l = 1..n-1) += g_l^T h_{l-1}    (128 x 128 each, columns 128 (l - 1))
+//   dW_out^T         += h_n^T g_out      (128 x 16, columns 384)
+//   dW_1f            += g_1^T x          (128 x 32, columns 400)
+//   dW_1p            += g_1^T Theta      (128 x 80, columns 432; Theta = the view's pose in
+//                                          every row, the pose columns of W_1)
+// then written as this CTA's partial (summed over CTAs by k_deform_reduce).  The stored
+// tiles are copied into shared memory, two operand pairs in flight.
+constexpr uint32_t C_DWO = 384, C_DW1F = 400, C_DW1P = 432;
+constexpr uint32_t D_BUF = 0;                              // 2 x 2 x [128 x 128] operand buffers
+constexpr uint32_t D_THETA = D_BUF + 4 * kHTile;           // [128 x 80]
+constexpr uint32_t D_MISC = D_THETA + kTM * kDeformTcMaxPose * 2;
+constexpr uint32_t kSmemDw = D_MISC + 64 + 1024;
+
+__device__ __forceinline__ void copy_tile(uint8_t* dst, const uint8_t* __restrict__ src, int64_t bytes) {
+  for (int64_t e = threadIdx.x; e < bytes / 16; e += kThreads)
+    reinterpret_cast<uint4*>(dst)[e] = __ldg(reinterpret_cast<const uint4*>(src) + e);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_constant__ Plan P) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int64_t S_cap = P.ws.S_cap;
+  const int64_t S = P.ws.view_base[P.n_views];
+  const int t = threadIdx.x, warp = t >> 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + D_MISC + 16);
+  const uint32_t mbar0 = tc::smem_u32(sm + D_MISC);
+  const uint32_t sbase = tc::smem_u32(sm);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
+  if (t == 0) {
+    tc::mbar_init(mbar0, 1);
+    tc::mbar_init(mbar0 + 8, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t tiles_cap = S_cap / kTM;
+  const int64_t n_tiles = S <= S_cap ? S / kTM : 0;
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  bool any = false;
+  int theta_view = -1;
+  const DeformDev* Dp = nullptr;
+  int pair = 0;
+  // one operand pair into buffer b (after the MMA that last read it), then its MMA
+  auto run_pair = [&](const uint8_t* a_src, int a_units, const uint8_t* b_src, int b_units, uint32_t dcol,
+                      bool b_is_theta) -> bool {
+    const int b = pair & 1;
+    ++pair;
+    if (pending[b]) {
+      const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
+      if (!__syncthreads_and(got)) return false;
+      phase[b] ^= 1u;
+      pending[b] = false;
+    }
+    uint8_t* abuf = sm + D_BUF + (2 * b) * kHTile;
+    uint8_t* bbuf = sm + D_BUF + (2 * b + 1) * kHTile;
+    copy_tile(abuf, a_src, (int64_t)kTM * a_units * 2);
+    if (!b_is_theta) copy_tile(bbuf, b_src, (int64_t)kTM * b_units * 2);
+    operands_ready();
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_dw(tmem + dcol, tc::smem_u32(abuf), a_units,
+               b_is_theta ? sbase + D_THETA : tc::smem_u32(bbuf), b_units, any);
+      tc::commit_to(mbar0 + 8 * b);
+    }
+    pending[b] = true;
+    return true;
+  };
+  for (int64_t T = blockIdx.x; T < n_tiles && ok; T += gridDim.x) {
+    const int v = view_of_slot(P, T * kTM);
+    if (!P.v[v].has_deform || !P.v[v].deform.tc) continue;
+    const DeformDev& D = P.v[v].deform;
+    Dp = &D;
+    const int n = D.n_hidden;
+    if (v != theta_view) {
+      // Theta rows = this view's pose, padded to 80 columns (after the MMA that read it)
+      for (int b = 0; b < 2 && ok; ++b) {
+        if (!pending[b]) continue;
+        const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
+        ok = __syncthreads_and(got);
+        if (ok) {
+          phase[b] ^= 1u;
+          pending[b] = false;
+        }
+      }
+      if (!ok) break;
+      for (int k = 0; k < kDeformTcMaxPose; k += 8) {
+        float x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = k + i < D.pose_dim ? D.pose[k + i] : 0.0f;
+        uint4 q;
+        q.x = tc::pack2<true>(x[0], x[1]);
+        q.y = tc::pack2<true>(x[2], x[3]);
+        q.z = tc::pack2<true>(x[4], x[5]);
+        q.w = tc::pack2<true>(x[6], x[7]);
+        *reinterpret_cast<uint4*>(sm + D_THETA + tc::kmajor_offset(t, k, kDeformTcMaxPose)) = q;
+      }
+      theta_view = v;
+    }
+    const uint8_t* hb = P.ws.def_h;
+    const uint8_t* gb = P.ws.def_g;
+    auto H_ = [&](int l) { return hb + ((int64_t)l * tiles_cap + T) * kHTile; };
+    auto G_ = [&](int l) { return gb + ((int64_t)l * tiles_cap + T) * kHTile; };
+    ok = run_pair(H_(n - 1), kH, P.ws.def_gout + T * kGoTile, 16, C_DWO, false);
+    for (int l = n - 1; l >= 1 && ok; --l) ok = run_pair(G_(l), kH, H_(l - 1), kH, 128u * (l - 1), false);
+    if (ok) ok = run_pair(G_(0), kH, P.ws.def_x + T * kXTile, kKf, C_DW1F, false);
+    if (ok) ok = run_pair(G_(0), kH, nullptr, kDeformTcMaxPose, C_DW1P, true);
+    any = true;
+  }
+  for (int b = 0; b < 2 && ok; ++b) {
+    if (!pending[b]) continue;
+    const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
+    ok = __syncthreads_and(got);
+    if (ok) {
+      phase[b] ^= 1u;
+      pending[b] = false;
+    }
+  }
+  if (ok && Dp) {
+    // write this CTA's partial: lane t is row t of every accumulator
+    tc::fence_after_sync();
+    const DeformDev& D = *Dp;
+    const int n = D.n_hidden, n_in = D.n_feat + D.pose_dim;
+    float* part = D.dw_scratch + (int64_t)blockIdx.x * D.n_w;
+    const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int l = 1; l < n; ++l) {
+      float* dst = part + (int64_t)kH * n_in + (int64_t)(l - 1) * kH * kH + (int64_t)t * kH;
+      for (int c = 0; c < kH; c += 16) {
+        float v[16];
+        tc::tmem_ld16(row + 128u * (l - 1) + c, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dst[c + i] = any ? v[i] : 0.0f;
+      }
+    }
+    {
+      float v[16];
+      tc::tmem_ld16(row + C_DWO, v);
+      float* dst = part + layer_offset(D, n);
+      for (int c = 0; c < 3; ++c) dst[c * kH + t] = any ? v[c] : 0.0f;
+    }
+    for (int c = 0; c < kKf; c += 16) {
+      float v[16];
+      tc::tmem_ld16(row + C_DW1F + c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (c + i < D.n_feat) part[(int64_t)t * n_in + c + i] = any ? v[i] : 0.0f;
+    }
+    for (int c = 0; c < kDeformTcMaxPose; c += 16) {
+      float v[16];
+      tc::tmem_ld16(row + C_DW1P + c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (c + i < D.pose_dim) part[(int64_t)t * n_in + D.n_feat + c + i] = any ? v[i] : 0.0f;
+    }
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(P.status, kStatusTimeout);
+    for (int b = 0; b < 2; ++b)
+      if (pending[b]) tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_deform_backward_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_deform_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  k_deform_chain_tc<<<num_sms, kThreads, kSmem, s>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_deform_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDw);
+  if (e != cudaSuccess) return e;
+  k_deform_dw_tc<<<num_sms, kThreads, kSmemDw, s>>>(P);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_deform_forward_tc(const Plan& P, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_deform_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
