@@ -619,8 +619,8 @@ def bench_deform(invr, args, flush, world, prec_name):
     tbd = invr.TrainBatches([(b[0], b[1], dview, b[3])], tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1,
                             tw.beta2, tw.adam_eps)
     ms_def, kt = time_train(invr, ctx, tbd, steps, args.warmup, flush, world)
-    # the net on the tensor cores (BF16 operands, forward and backward)
-    net_tc = invr.Deform.from_synth(ctx, dp, PRECS["bf16"])
+    # the net on the tensor cores (FP16 operands, forward and backward)
+    net_tc = invr.Deform.from_synth(ctx, dp, PRECS["fp16"])
     tview = invr.View(view.field, g, 0, None, occ, net_tc, pose_d)
     tbt = invr.TrainBatches([(b[0], b[1], tview, b[3])], tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1,
                             tw.beta2, tw.adam_eps)
@@ -645,7 +645,7 @@ def bench_deform(invr, args, flush, world, prec_name):
     r_plain, r_def, r_tc = render_ms(view), render_ms(dview), render_ms(tview)
     net.close()
     net_tc.close()
-    return {"workload": tw.name, "net": "32 hash features + 72 pose -> 4 x 128 -> 3 (FP32 SIMT, or BF16 tcgen05)",
+    return {"workload": tw.name, "net": "32 hash features + 72 pose -> 4 x 128 -> 3 (FP32 SIMT, or FP16 tcgen05)",
             "field_prec": prec_name,
             "train": {"with_net": {"value": round(world * S_nom / (ms_def * 1e-3), 1), "ms_per_step": round(ms_def, 3)},
                       "without": {"value": round(world * S_nom / (ms_plain * 1e-3), 1),

@@ -183,8 +183,9 @@ invr_status invr_graph_get_lut(invr_graph graph, int frame, uint16_t* canon_dev,
  * (invr_train_step and its halves) back-propagates through v_c into the net's tables and
  * weights and updates them with the same Adam step as the fields.  Supported: F = 2,
  * L*F a multiple of 8 up to 32, hidden a multiple of 16 up to 128, 1 <= n_hidden <= 4,
- * pose_dim <= 128; else INVR_E_ARG.  prec: INVR_FP32 runs the net in FP32; INVR_MLP_BF16 runs
- * it on the tensor cores with BF16 operands and FP32 accumulation, forward and backward
+ * pose_dim <= 128; else INVR_E_ARG.  prec: INVR_FP32 runs the net in FP32; INVR_MLP_FP16 and
+ * INVR_MLP_BF16 run it on the tensor cores with FP16 / BF16 operands and FP32 accumulation,
+ * forward and backward
  * (then L*F = 32, hidden = 128, pose_dim <= 80, and one training call takes at most one such
  * net; training keeps ~2.1 KB of operand tiles per sample slot of the workspace).  The net's
  * precision is independent of the field's. */

@@ -291,7 +291,7 @@ DeformDev deform_dev(invr_ctx ctx, invr_deform d, const float* pose, int view) {
   D.hidden = q.hidden;
   D.n_hidden = q.n_hidden;
   D.n_w = (int)d->n_w;
-  D.tc = q.prec == INVR_MLP_BF16;
+  D.tc = q.prec == INVR_MLP_BF16 ? 2 : (q.prec == INVR_MLP_FP16 ? 1 : 0);
   return D;
 }
 
@@ -1166,12 +1166,14 @@ invr_status invr_deform_create(invr_ctx ctx, const invr_deform_desc* desc, invr_
   if (q.F != 2 || q.L < 1 || q.L > kMaxL || q.L * q.F > kDeformMaxFeat || (q.L * q.F) % 8 || q.log2_T < 4 ||
       q.log2_T > 24 || q.N_min < 2 || !(q.growth >= 1.0) || q.hidden < 16 || q.hidden > kDeformMaxHidden ||
       q.hidden % 16 || q.n_hidden < 1 || q.n_hidden > kDeformMaxLayers || q.pose_dim < 0 ||
-      q.pose_dim > kDeformMaxPose || (q.prec != INVR_FP32 && q.prec != INVR_MLP_BF16))
+      q.pose_dim > kDeformMaxPose)
     return fail(ctx, INVR_E_ARG,
                 "deformation net: F = 2, L*F a multiple of 8 up to 32, hidden a multiple of 16 up to 128, "
-                "1..4 hidden layers, pose_dim <= 128, INVR_FP32 or INVR_MLP_BF16");
-  if (q.prec == INVR_MLP_BF16 && (q.hidden != kDeformMaxHidden || q.L * q.F != kDeformMaxFeat ||
-                                  q.pose_dim > kDeformTcMaxPose))
+                "1..4 hidden layers, pose_dim <= 128");
+  if (q.prec != INVR_FP32 && q.prec != INVR_MLP_FP16 && q.prec != INVR_MLP_BF16)
+    return fail(ctx, INVR_E_ARG, "unknown precision");
+  if (q.prec != INVR_FP32 && (q.hidden != kDeformMaxHidden || q.L * q.F != kDeformMaxFeat ||
+                              q.pose_dim > kDeformTcMaxPose))
     return fail(ctx, INVR_E_ARG, "a tensor-core deformation net has 32 features, hidden 128 and pose_dim <= 80");
   DeviceGuard guard(ctx->device);
   invr_deform d = new invr_deform_s();

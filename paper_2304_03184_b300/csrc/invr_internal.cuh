@@ -70,7 +70,7 @@ struct DeformDev {
   float* pose_bias;         // [hidden] W_1[:, n_feat:] theta (computed per call)
   FieldDev enc;             // the net's own hash encoding (F = 2; mlp_kind F32, mlp_in = n_feat)
   int n_feat, pose_dim, hidden, n_hidden, n_w;
-  int tc;                   // forward on the tensor cores (BF16 operands) instead of FP32 SIMT
+  int tc;                   // 0: FP32 SIMT; on the tensor cores with 1: FP16, 2: BF16 operands
 };
 
 struct ViewDev {

@@ -53,17 +53,19 @@ __device__ __forceinline__ int64_t layer_offset(const DeformDev& D, int layer) {
 
 // dst = W (rows [0, N), columns [k0, k0 + K) of a row-major [.][ldw] matrix; zero rows
 // from n_valid on and zero columns from k_valid on) as a K-major BF16 operand.
+template <bool BF16>
 __device__ void stage(uint8_t* dst, const float* __restrict__ W, int N, int K, int ldw, int n_valid, int k_valid) {
   for (int e = threadIdx.x; e < N * K / 2; e += kThreads) {
     const int n = (2 * e) / K, k = (2 * e) % K;
     const float a = (n < n_valid && k < k_valid) ? __ldg(W + (int64_t)n * ldw + k) : 0.0f;
     const float b = (n < n_valid && k + 1 < k_valid) ? __ldg(W + (int64_t)n * ldw + k + 1) : 0.0f;
-    *reinterpret_cast<uint32_t*>(dst + tc::kmajor_offset(n, k, K)) = tc::pack2<true>(a, b);
+    *reinterpret_cast<uint32_t*>(dst + tc::kmajor_offset(n, k, K)) = tc::pack2<BF16>(a, b);
   }
 }
 
+template <bool BF16>
 __device__ __forceinline__ void issue(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, int N) {
-  const uint32_t idesc = tc::idesc_f16(kTM, N, true);
+  const uint32_t idesc = tc::idesc_f16(kTM, N, BF16);
   for (int kk = 0; kk < K / 16; ++kk) {
     const uint64_t ad = tc::smem_desc(a_saddr + kk * 256, 128, K * 16);
     const uint64_t bd = tc::smem_desc(b_saddr + kk * 256, 128, K * 16);
@@ -82,6 +84,7 @@ struct Slot {
   int view = 0;
 };
 
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_constant__ Plan P) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int64_t S_cap = P.ws.S_cap;
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       const int64_t s0 = next * kTM;
       next += gridDim.x;
       const int v = view_of_slot(P, s0);
-      if (P.v[v].has_deform && P.v[v].deform.tc) {
+      if (P.v[v].has_deform && P.v[v].deform.tc == (BF16 ? 2 : 1)) {
         sl.s0 = s0;
         sl.view = v;
         return;
@@ -138,9 +141,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
     if (D.weights != loaded) {
       __syncthreads();
       const int n_in = D.n_feat + D.pose_dim;
-      stage(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
-      for (int l = 1; l < n; ++l) stage(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
-      stage(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      stage<BF16>(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
+      for (int l = 1; l < n; ++l) stage<BF16>(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
+      stage<BF16>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
       loaded = D.weights;
     }
     // operands of both tiles: features (FP32 feature-major) -> BF16 rows, pose bias
@@ -154,10 +157,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
         for (int i = 0; i < 8; ++i)
           x[i] = k + i < D.n_feat ? P.ws.feat_d[(int64_t)(k + i) * S_cap + s0 + t] : 0.0f;
         uint4 q;
-        q.x = tc::pack2<true>(x[0], x[1]);
-        q.y = tc::pack2<true>(x[2], x[3]);
-        q.z = tc::pack2<true>(x[4], x[5]);
-        q.w = tc::pack2<true>(x[6], x[7]);
+        q.x = tc::pack2<BF16>(x[0], x[1]);
+        q.y = tc::pack2<BF16>(x[2], x[3]);
+        q.z = tc::pack2<BF16>(x[4], x[5]);
+        q.w = tc::pack2<BF16>(x[6], x[7]);
         *reinterpret_cast<uint4*>(X + tc::kmajor_offset(t, k, Kf)) = q;
         if (P.deform_store)
           *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(t, k, Kf)) = q;
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       tc::fence_after_sync();
       for (int j = 0; j < 2; ++j) {
         if (slot[j].s0 < 0) continue;
-        issue(tmem + 256 * j, sbase + OFF_X + j * kTM * kKf * 2, sbase + OFF_W1, Kf, H);
+        issue<BF16>(tmem + 256 * j, sbase + OFF_X + j * kTM * kKf * 2, sbase + OFF_W1, Kf, H);
         tc::commit_to(mbar0 + 8 * j);
       }
     }
@@ -199,14 +202,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
               for (int i = 0; i < 16; ++i) v[i] += bias[c + i];
             }
             uint4 lo, hi;
-            lo.x = tc::pack2<true>(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f));
-            lo.y = tc::pack2<true>(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
-            lo.z = tc::pack2<true>(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f));
-            lo.w = tc::pack2<true>(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f));
-            hi.x = tc::pack2<true>(fmaxf(v[8], 0.f), fmaxf(v[9], 0.f));
-            hi.y = tc::pack2<true>(fmaxf(v[10], 0.f), fmaxf(v[11], 0.f));
-            hi.z = tc::pack2<true>(fmaxf(v[12], 0.f), fmaxf(v[13], 0.f));
-            hi.w = tc::pack2<true>(fmaxf(v[14], 0.f), fmaxf(v[15], 0.f));
+            lo.x = tc::pack2<BF16>(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f));
+            lo.y = tc::pack2<BF16>(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
+            lo.z = tc::pack2<BF16>(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f));
+            lo.w = tc::pack2<BF16>(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f));
+            hi.x = tc::pack2<BF16>(fmaxf(v[8], 0.f), fmaxf(v[9], 0.f));
+            hi.y = tc::pack2<BF16>(fmaxf(v[10], 0.f), fmaxf(v[11], 0.f));
+            hi.z = tc::pack2<BF16>(fmaxf(v[12], 0.f), fmaxf(v[13], 0.f));
+            hi.w = tc::pack2<BF16>(fmaxf(v[14], 0.f), fmaxf(v[15], 0.f));
             *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c, H)) = lo;
             *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c + 8, H)) = hi;
             if (P.deform_store) {
@@ -219,9 +222,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
           if (t == 0) {
             tc::fence_after_sync();
             if (l + 1 < n)
-              issue(tmem + 256 * j, sbase + OFF_HB + j * kTM * kH * 2, sbase + OFF_WH + l * kH * kH * 2, H, H);
+              issue<BF16>(tmem + 256 * j, sbase + OFF_HB + j * kTM * kH * 2, sbase + OFF_WH + l * kH * kH * 2, H, H);
             else
-              issue(tmem + 256 * j + 128, sbase + OFF_HB + j * kTM * kH * 2, sbase + OFF_WO, H, 16);
+              issue<BF16>(tmem + 256 * j + 128, sbase + OFF_HB + j * kTM * kH * 2, sbase + OFF_WO, H, 16);
             tc::commit_to(mbar0 + 8 * j);
           }
           pending[j] = true;
@@ -258,8 +261,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
 // Adjoint MMA: D (128 x N) = G (smem, 128 x K, K-major) * W with W the forward weight
 // [K rows][N columns] as staged for the forward (K-major in its own layout), read as an
 // MN-major operand: column groups 128 B apart, row groups N * 16 B apart.
+template <bool BF16>
 __device__ __forceinline__ void issue_adjoint(uint32_t d_tmem, uint32_t a_saddr, uint32_t w_saddr, int K, int N) {
-  const uint32_t idesc = tc::idesc_f16(kTM, N, true) | (1u << 16);
+  const uint32_t idesc = tc::idesc_f16(kTM, N, BF16) | (1u << 16);
   for (int kk = 0; kk < K / 16; ++kk) {
     const uint64_t ad = tc::smem_desc(a_saddr + kk * 256, 128, K * 16);
     const uint64_t bd = tc::smem_desc(w_saddr + kk * 32 * N, N * 16, 128);
@@ -270,9 +274,10 @@ __device__ __forceinline__ void issue_adjoint(uint32_t d_tmem, uint32_t a_saddr,
 // Weight-gradient MMA over the 128 samples of a tile: D (M = a_units x N = b_units) (+)=
 // A^T B, A and B [128 samples][units] K-major tiles read as MN-major operands (unit groups
 // 128 B apart, sample groups units * 16 B apart).
+template <bool BF16>
 __device__ __forceinline__ void issue_dw(uint32_t d_tmem, uint32_t a_saddr, int a_units, uint32_t b_saddr,
                                          int b_units, bool accumulate) {
-  const uint32_t idesc = tc::idesc_f16(kTM, b_units, true) | (1u << 15) | (1u << 16);
+  const uint32_t idesc = tc::idesc_f16(kTM, b_units, BF16) | (1u << 15) | (1u << 16);
   for (int kk = 0; kk < kTM / 16; ++kk) {
     const uint64_t ad = tc::smem_desc(a_saddr + kk * 32 * a_units, a_units * 16, 128);
     const uint64_t bd = tc::smem_desc(b_saddr + kk * 32 * b_units, b_units * 16, 128);
@@ -291,6 +296,7 @@ __device__ __forceinline__ float relu_mask(uint32_t w, int half) {
 // g_1 W_1f.  The ReLU masks come from the forward's stored h tiles; every g tile (and the
 // padded g_out tile) is stored for the weight-gradient kernel; dL/df is written FP32
 // feature-major for the scatter into the net's tables.  Two tiles in flight, as the forward.
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_constant__ Plan P) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int64_t S_cap = P.ws.S_cap;
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
       const int64_t s0 = next * kTM;
       next += gridDim.x;
       const int v = view_of_slot(P, s0);
-      if (P.v[v].has_deform && P.v[v].deform.tc) {
+      if (P.v[v].has_deform && P.v[v].deform.tc == (BF16 ? 2 : 1)) {
         sl.s0 = s0;
         sl.view = v;
         return;
@@ -344,9 +350,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
     if (D.weights != loaded) {
       __syncthreads();
       const int n_in = D.n_feat + D.pose_dim;
-      stage(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
-      for (int l = 1; l < n; ++l) stage(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
-      stage(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      stage<BF16>(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
+      for (int l = 1; l < n; ++l) stage<BF16>(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
+      stage<BF16>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
       loaded = D.weights;
     }
     // g_out tiles: dL/dv_c (3 columns) padded to 16, in smem and stored
@@ -354,13 +360,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
       if (slot[j].s0 < 0) continue;
       const int64_t g = slot[j].s0 + t;
       float v[16];
+      // scaled by 1 / loss_norm before rounding to 16 bits (the deltas of a mean loss are
+      // small enough to lose FP16 precision), unscaled in FP32 on the way out
+      const float in_scale = 1.0f / P.loss_norm;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = i < 3 ? P.ws.dvc[(int64_t)i * S_cap + g] : 0.0f;
+      for (int i = 0; i < 16; ++i) v[i] = i < 3 ? P.ws.dvc[(int64_t)i * S_cap + g] * in_scale : 0.0f;
       uint4 lo, hi;
-      lo.x = tc::pack2<true>(v[0], v[1]);
-      lo.y = tc::pack2<true>(v[2], v[3]);
-      lo.z = tc::pack2<true>(v[4], v[5]);
-      lo.w = tc::pack2<true>(v[6], v[7]);
+      lo.x = tc::pack2<BF16>(v[0], v[1]);
+      lo.y = tc::pack2<BF16>(v[2], v[3]);
+      lo.z = tc::pack2<BF16>(v[4], v[5]);
+      lo.w = tc::pack2<BF16>(v[6], v[7]);
       hi.x = hi.y = hi.z = hi.w = 0u;
       uint8_t* go = sm + OFF_X + j * kXTile;
       *reinterpret_cast<uint4*>(go + tc::kmajor_offset(t, 0, 16)) = lo;
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
       tc::fence_after_sync();
       for (int j = 0; j < 2; ++j) {
         if (slot[j].s0 < 0) continue;
-        issue_adjoint(tmem + 256 * j, sbase + OFF_X + j * kXTile, sbase + OFF_WO, 16, H);
+        issue_adjoint<BF16>(tmem + 256 * j, sbase + OFF_X + j * kXTile, sbase + OFF_WO, 16, H);
         tc::commit_to(mbar0 + 8 * j);
       }
     }
@@ -410,14 +419,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
               v[2 * i + 1] *= relu_mask(mw[i], 1);
             }
             uint4 lo, hi;
-            lo.x = tc::pack2<true>(v[0], v[1]);
-            lo.y = tc::pack2<true>(v[2], v[3]);
-            lo.z = tc::pack2<true>(v[4], v[5]);
-            lo.w = tc::pack2<true>(v[6], v[7]);
-            hi.x = tc::pack2<true>(v[8], v[9]);
-            hi.y = tc::pack2<true>(v[10], v[11]);
-            hi.z = tc::pack2<true>(v[12], v[13]);
-            hi.w = tc::pack2<true>(v[14], v[15]);
+            lo.x = tc::pack2<BF16>(v[0], v[1]);
+            lo.y = tc::pack2<BF16>(v[2], v[3]);
+            lo.z = tc::pack2<BF16>(v[4], v[5]);
+            lo.w = tc::pack2<BF16>(v[6], v[7]);
+            hi.x = tc::pack2<BF16>(v[8], v[9]);
+            hi.y = tc::pack2<BF16>(v[10], v[11]);
+            hi.z = tc::pack2<BF16>(v[12], v[13]);
+            hi.w = tc::pack2<BF16>(v[14], v[15]);
             *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c, H)) = lo;
             *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c + 8, H)) = hi;
             *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c, H)) = lo;
@@ -427,9 +436,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
           if (t == 0) {
             tc::fence_after_sync();
             if (li > 0)
-              issue_adjoint(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_WH + (li - 1) * kH * kH * 2, H, H);
+              issue_adjoint<BF16>(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_WH + (li - 1) * kH * kH * 2, H, H);
             else
-              issue_adjoint(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_W1, H, Kf);
+              issue_adjoint<BF16>(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_W1, H, Kf);
             tc::commit_to(mbar0 + 8 * j);
           }
           pending[j] = true;
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
             tc::tmem_ld16(row + c, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-              if (c + i < D.n_feat) P.ws.dfeat_d[(int64_t)(c + i) * S_cap + g] = v[i];
+              if (c + i < D.n_feat) P.ws.dfeat_d[(int64_t)(c + i) * S_cap + g] = v[i] * P.loss_norm;
           }
           tc::fence_before_sync();
         }
@@ -480,6 +489,7 @@ __device__ __forceinline__ void copy_tile(uint8_t* dst, const uint8_t* __restric
     reinterpret_cast<uint4*>(dst)[e] = __ldg(reinterpret_cast<const uint4*>(src) + e);
 }
 
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_constant__ Plan P) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int64_t S_cap = P.ws.S_cap;
@@ -524,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
     operands_ready();
     if (t == 0) {
       tc::fence_after_sync();
-      issue_dw(tmem + dcol, tc::smem_u32(abuf), a_units,
+      issue_dw<BF16>(tmem + dcol, tc::smem_u32(abuf), a_units,
                b_is_theta ? sbase + D_THETA : tc::smem_u32(bbuf), b_units, any);
       tc::commit_to(mbar0 + 8 * b);
     }
@@ -533,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   };
   for (int64_t T = blockIdx.x; T < n_tiles && ok; T += gridDim.x) {
     const int v = view_of_slot(P, T * kTM);
-    if (!P.v[v].has_deform || !P.v[v].deform.tc) continue;
+    if (!P.v[v].has_deform || P.v[v].deform.tc != (BF16 ? 2 : 1)) continue;
     const DeformDev& D = P.v[v].deform;
     Dp = &D;
     const int n = D.n_hidden;
@@ -554,10 +564,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
 #pragma unroll
         for (int i = 0; i < 8; ++i) x[i] = k + i < D.pose_dim ? D.pose[k + i] : 0.0f;
         uint4 q;
-        q.x = tc::pack2<true>(x[0], x[1]);
-        q.y = tc::pack2<true>(x[2], x[3]);
-        q.z = tc::pack2<true>(x[4], x[5]);
-        q.w = tc::pack2<true>(x[6], x[7]);
+        q.x = tc::pack2<BF16>(x[0], x[1]);
+        q.y = tc::pack2<BF16>(x[2], x[3]);
+        q.z = tc::pack2<BF16>(x[4], x[5]);
+        q.w = tc::pack2<BF16>(x[6], x[7]);
         *reinterpret_cast<uint4*>(sm + D_THETA + tc::kmajor_offset(t, k, kDeformTcMaxPose)) = q;
       }
       theta_view = v;
@@ -586,6 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
     tc::fence_after_sync();
     const DeformDev& D = *Dp;
     const int n = D.n_hidden, n_in = D.n_feat + D.pose_dim;
+    const float out_scale = P.loss_norm;   // the chain's deltas carry 1 / loss_norm
     float* part = D.dw_scratch + (int64_t)blockIdx.x * D.n_w;
     const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
     for (int l = 1; l < n; ++l) {
@@ -594,28 +605,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
         float v[16];
         tc::tmem_ld16(row + 128u * (l - 1) + c, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dst[c + i] = any ? v[i] : 0.0f;
+        for (int i = 0; i < 16; ++i) dst[c + i] = any ? v[i] * out_scale : 0.0f;
       }
     }
     {
       float v[16];
       tc::tmem_ld16(row + C_DWO, v);
       float* dst = part + layer_offset(D, n);
-      for (int c = 0; c < 3; ++c) dst[c * kH + t] = any ? v[c] : 0.0f;
+      for (int c = 0; c < 3; ++c) dst[c * kH + t] = any ? v[c] * out_scale : 0.0f;
     }
     for (int c = 0; c < kKf; c += 16) {
       float v[16];
       tc::tmem_ld16(row + C_DW1F + c, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (c + i < D.n_feat) part[(int64_t)t * n_in + c + i] = any ? v[i] : 0.0f;
+        if (c + i < D.n_feat) part[(int64_t)t * n_in + c + i] = any ? v[i] * out_scale : 0.0f;
     }
     for (int c = 0; c < kDeformTcMaxPose; c += 16) {
       float v[16];
       tc::tmem_ld16(row + C_DW1P + c, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (c + i < D.pose_dim) part[(int64_t)t * n_in + D.n_feat + c + i] = any ? v[i] : 0.0f;
+        if (c + i < D.pose_dim) part[(int64_t)t * n_in + D.n_feat + c + i] = any ? v[i] * out_scale : 0.0f;
     }
   }
   if (!ok) {
@@ -633,22 +644,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
 
 }  // namespace
 
-cudaError_t launch_deform_backward_tc(const Plan& P, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_deform_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+template <bool BF16>
+static cudaError_t backward_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_deform_chain_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
-  k_deform_chain_tc<<<num_sms, kThreads, kSmem, s>>>(P);
+  k_deform_chain_tc<BF16><<<num_sms, kThreads, kSmem, s>>>(P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_deform_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDw);
+  e = cudaFuncSetAttribute(k_deform_dw_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDw);
   if (e != cudaSuccess) return e;
-  k_deform_dw_tc<<<num_sms, kThreads, kSmemDw, s>>>(P);
+  k_deform_dw_tc<BF16><<<num_sms, kThreads, kSmemDw, s>>>(P);
   return cudaGetLastError();
 }
 
-cudaError_t launch_deform_forward_tc(const Plan& P, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_deform_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+template <bool BF16>
+static cudaError_t forward_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_deform_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
-  k_deform_fwd_tc<<<num_sms, kThreads, kSmem, s>>>(P);
+  k_deform_fwd_tc<BF16><<<num_sms, kThreads, kSmem, s>>>(P);
   return cudaGetLastError();
+}
+
+static void tc_kinds(const Plan& P, bool& f16, bool& bf16) {
+  f16 = bf16 = false;
+  for (int v = 0; v < P.n_views; ++v) {
+    if (!P.v[v].has_deform) continue;
+    if (P.v[v].deform.tc == 1) f16 = true;
+    if (P.v[v].deform.tc == 2) bf16 = true;
+  }
+}
+
+cudaError_t launch_deform_backward_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  bool f16, bf16;
+  tc_kinds(P, f16, bf16);
+  cudaError_t e = cudaSuccess;
+  if (bf16) e = backward_tc<true>(P, num_sms, s);
+  if (e == cudaSuccess && f16) e = backward_tc<false>(P, num_sms, s);
+  return e;
+}
+
+cudaError_t launch_deform_forward_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  bool f16, bf16;
+  tc_kinds(P, f16, bf16);
+  cudaError_t e = cudaSuccess;
+  if (bf16) e = forward_tc<true>(P, num_sms, s);
+  if (e == cudaSuccess && f16) e = forward_tc<false>(P, num_sms, s);
+  return e;
 }
 
 }  // namespace invr

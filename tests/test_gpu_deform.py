@@ -75,40 +75,56 @@ def test_deform_render_matches_oracle(env):
     assert np.abs(plain.rgba - ref.rgba).max() > 1e-3
 
 
-@pytest.mark.parametrize("field_prec", ["fp32", "bf16"])
-def test_deform_tensor_core_forward_matches_oracle(env, field_prec):
-    """The net's forward on the tensor cores (BF16 operands, FP32 accumulation): renders
-    within the mixed-precision colour tolerance, with an FP32 or a BF16 field."""
+@pytest.mark.parametrize("field_prec,net_prec", [("fp32", "fp16"), ("bf16", "fp16"), ("bf16", "bf16")])
+def test_deform_tensor_core_forward_matches_oracle(env, field_prec, net_prec):
+    """The net's forward on the tensor cores (FP16 or BF16 operands, FP32 accumulation):
+    renders within the mixed-precision colour tolerance, with an FP32 or a BF16 field."""
     invr, ctx, oracle = env
     rng = np.random.default_rng(107)
     w, dp, pose = _render_workload(rng)
     code = invr.INVR_MLP_BF16 if field_prec == "bf16" else invr.INVR_FP32
-    hum = Human(invr, ctx, oracle, w.views[0], dp, pose, prec=code, net_prec=invr.INVR_MLP_BF16)
+    ncode = invr.INVR_MLP_BF16 if net_prec == "bf16" else invr.INVR_MLP_FP16
+    hum = Human(invr, ctx, oracle, w.views[0], dp, pose, prec=code, net_prec=ncode)
     rgba, _ = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [hum.view])
     ctx.sync()
     ref = oracle.render(w.rays.o, w.rays.d, w.n_samples, w.t_eps, [hum.oview])
     np.testing.assert_allclose(host(rgba), ref.rgba, rtol=0, atol=MIXED_COLOUR_TOL)
 
 
-def test_deform_tensor_core_forward_with_training(env):
-    """Training with the tensor-core forward of the net.  Its BF16 operands leave ~1e-4 of
-    error in delta v, hence in v_c, and dL/dv_c (the encoding's derivative in the point)
-    changes by the fraction of a finest-level cell that this error spans: with the 8-level
-    field (finest N_l = 273) the loss stays within 1e-3 and the net's gradients within 1e-1
-    (weights) and 2e-1 (tables) of the FP64 oracle's."""
+# The net on the tensor cores, trained: its 16-bit forward moves v_c by ~1e-4 (FP16) to
+# ~4e-4 (BF16), i.e. 10-40% of a finest-level cell (N_l ~ 2000), and dL/dv_c is the derivative
+# of the rough hash-grid field at that point, so the net's gradients follow the FP64 oracle's
+# to ~0.1 (FP16; measured 0.09-0.15 per layer) and ~0.4 (BF16; 0.28-0.54); the field's own
+# gradients keep the mixed-precision levels.  Deltas are scaled by 1 / loss_norm in 16 bits.
+NET_TC_RTOL = {"fp16": (0.25, 0.2, 0.06), "bf16": (0.7, 0.45, 0.15)}   # net weights, net tables, field tables
+
+
+@pytest.mark.parametrize("net_prec", ["fp16", "bf16"])
+def test_deform_tensor_core_training(env, net_prec):
     invr, ctx, oracle = env
     rng = np.random.default_rng(108)
-    tw = synth.train_step_workload(seed=18, n_rays=1024, field_desc=synth.CFG1_FIELD)
+    tw = synth.train_step_workload(seed=18, n_rays=1024)
     dp, pose = synth.make_deform(rng), synth.make_pose(rng)
-    tb, gfields, ofields, net, onet, obatches, keep = _train(env, tw, dp, [pose], net_prec=invr.INVR_MLP_BF16)
+    ncode = invr.INVR_MLP_BF16 if net_prec == "bf16" else invr.INVR_MLP_FP16
+    tb, gfields, ofields, net, onet, obatches, keep = _train(env, tw, dp, [pose], net_prec=ncode)
     loss = invr.forward_train(ctx, tb)
     invr.backward(ctx, tb)
     ctx.sync()
     oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
     assert abs(float(host(loss)[0]) - oloss) <= 1e-3 * oloss
+    w_tol, t_tol, f_tol = NET_TC_RTOL[net_prec]
     gt, gw = (host(x) for x in net.get_grads())
     ogt, ogw = ograds[id(onet)]
-    assert _rel(gw, ogw) <= 1e-1 and _rel(gt, ogt) <= 2e-1, (_rel(gw, ogw), _rel(gt, ogt))
+    off = 0
+    for k, (r, c) in enumerate(dp.desc.weight_shapes()):
+        e = _rel(gw[off:off + r * c], ogw[off:off + r * c])
+        assert e <= w_tol, (k, e)
+        off += r * c
+    assert _rel(gt, ogt) <= t_tol
+    fp = tw.fields[0]
+    ft, fw = (host(x) for x in gfields[id(fp)].get_grads())
+    oft, ofw = ograds[id(ofields[id(fp)])]
+    assert _rel(fw, ofw) <= 1e-2 and _rel(ft, oft) <= f_tol
 
 
 def test_deform_zero_output_layer_is_the_plain_warp(env):
