@@ -141,10 +141,15 @@ __global__ void __launch_bounds__(kScanB) k_scan_final(const __grid_constant__ P
   if (g < g1) P.ws.ray_first[g] = P.ws.block_sums[blockIdx.x] + ex;
 }
 
+// One warp per 32 consecutive rays: their occupied samples fill one contiguous range of
+// slots per view, which the warp writes 32 slots at a time (coalesced).  For the slot of
+// ordinal q within the warp's samples, a binary search over the warp's inclusive prefix
+// counts (shuffles) finds its ray r, the (q - first of r)-th set bit of r's occupancy words
+// gives the sample index j, and r's ray parameters come from lane r.
 __global__ void __launch_bounds__(256) k_march_emit(const __grid_constant__ Plan P) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t S_cap = P.ws.S_cap;
-  if (P.ws.view_base[P.n_views] > S_cap) return;  // overflow flagged by the scan
+  if (P.ws.view_base[P.n_views] > S_cap) return;
   // padding slots at the end of each view's range
   if (g < (int64_t)P.n_views * kTile) {
     const int v = (int)(g / kTile);
@@ -157,30 +162,70 @@ __global__ void __launch_bounds__(256) k_march_emit(const __grid_constant__ Plan
       P.ws.s_pos[2 * S_cap + slot] = 0.0f;
     }
   }
-  if (g >= P.total_rays) return;
-  const int cnt = P.ws.ray_count[g];
-  if (cnt == 0) return;
-  const ViewDev& V = P.v[view_of_ray(P, g)];
-  float3 o, d;
-  load_ray(V, g - V.ray_begin, o, d);
-  float tn, dt;
-  ray_box(o, d, P.n_samples, tn, dt);
-  int64_t s = P.ws.ray_first[g];
-  const uint32_t* bits = P.ws.ray_bits + g;
-  const int words = (P.n_samples + 31) / 32;
-  for (int w = 0; w < words; ++w) {
-    // the occupied samples recorded by the count pass, in order
-    for (uint32_t m = bits[w * P.ws.R_cap]; m; m &= m - 1) {
-      const int j = 32 * w + __ffs(m) - 1;
-      const float t = sample_t(tn, dt, j);
-      const float3 p = sample_p(o, d, t);
-      P.ws.s_ray[s] = (int32_t)g;
-      P.ws.s_t[s] = t;
-      P.ws.s_pos[s] = p.x;
-      P.ws.s_pos[S_cap + s] = p.y;
-      P.ws.s_pos[2 * S_cap + s] = p.z;
-      ++s;
+  const int lane = threadIdx.x & 31;
+  const int64_t g0 = g - lane;                       // first ray of this warp
+  if (g0 >= P.total_rays) return;                    // warp-uniform
+  const bool mine = g < P.total_rays;
+  const int cnt = mine ? P.ws.ray_count[g] : 0;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;                            // warp-uniform
+  // this lane's ray parameters, for the lanes that emit its samples
+  float3 o = make_float3(0.f, 0.f, 0.f), d = o;
+  float tn = 0.0f, dt = 0.0f;
+  int64_t first = 0;
+  if (cnt > 0) {
+    const ViewDev& V = P.v[view_of_ray(P, g)];
+    load_ray(V, g - V.ray_begin, o, d);
+    ray_box(o, d, P.n_samples, tn, dt);
+    first = P.ws.ray_first[g];
+  }
+  const int64_t R_cap = P.ws.R_cap;
+  for (int q0 = 0; q0 < total; q0 += 32) {
+    const int q = q0 + lane;
+    const bool act = q < total;
+    // ray r of ordinal q: the first lane whose inclusive count exceeds q
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (lo + hi) >> 1;
+      const int c = __shfl_sync(0xffffffffu, incl, mid);
+      if (q < c) hi = mid; else lo = mid + 1;
     }
+    const int r = lo;
+    const int ex = __shfl_sync(0xffffffffu, incl, r) - __shfl_sync(0xffffffffu, cnt, r);
+    const float ox = __shfl_sync(0xffffffffu, o.x, r), oy = __shfl_sync(0xffffffffu, o.y, r),
+                oz = __shfl_sync(0xffffffffu, o.z, r);
+    const float dx = __shfl_sync(0xffffffffu, d.x, r), dy = __shfl_sync(0xffffffffu, d.y, r),
+                dz = __shfl_sync(0xffffffffu, d.z, r);
+    const float rtn = __shfl_sync(0xffffffffu, tn, r), rdt = __shfl_sync(0xffffffffu, dt, r);
+    const int64_t rfirst = __shfl_sync(0xffffffffu, first, r);
+    if (!act) continue;
+    // the k-th occupied sample of ray g0 + r
+    int k = q - ex, j = 0;
+    const uint32_t* bits = P.ws.ray_bits + g0 + r;
+    for (int w = 0;; ++w) {
+      const uint32_t m = bits[w * R_cap];
+      const int pc = __popc(m);
+      if (k < pc) {
+        j = 32 * w + (int)__fns(m, 0, k + 1);
+        break;
+      }
+      k -= pc;
+    }
+    const float t = sample_t(rtn, rdt, j);
+    const float3 p = sample_p(make_float3(ox, oy, oz), make_float3(dx, dy, dz), t);
+    const int64_t slot = rfirst + (q - ex);
+    P.ws.s_ray[slot] = (int32_t)(g0 + r);
+    P.ws.s_t[slot] = t;
+    P.ws.s_pos[slot] = p.x;
+    P.ws.s_pos[S_cap + slot] = p.y;
+    P.ws.s_pos[2 * S_cap + slot] = p.z;
   }
 }
 
