@@ -216,8 +216,9 @@ def time_train(invr, ctx, tb, steps, warmup, flush, world):
 
 def measure_l2(invr, ctx):
     """L2 ceilings measured on this device by the library's probe kernels: a read stream over
-    a 64 MiB resident buffer (the size of one field's tables) and random float4 / float2
-    atomic adds into it (the forms the hash-gradient scatter issues).  Best of 5, CUDA events."""
+    a 64 MiB resident buffer (the size of one field's tables), and random float4 / float2
+    loads from it and atomic adds into it (the forms the encoding's gathers and the
+    hash-gradient scatter issue).  Best of 5, CUDA events."""
     import torch
     buf = torch.ones(1 << 24, dtype=torch.float32, device="cuda")        # 64 MiB < 126 MB L2
     sink = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -237,7 +238,9 @@ def measure_l2(invr, ctx):
     passes, n_ops = 40, 1 << 27
     res = {"read_gbs": best(lambda: invr.probe_l2_read(ctx, buf, passes, sink), passes * buf.numel() * 4),
            "atomic_v4_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 4, n_ops), n_ops * 16),
-           "atomic_v2_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 2, n_ops), n_ops * 8)}
+           "atomic_v2_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 2, n_ops), n_ops * 8),
+           "gather_v4_gbs": best(lambda: invr.probe_l2_gather(ctx, buf, 4, n_ops, sink), n_ops * 16),
+           "gather_v2_gbs": best(lambda: invr.probe_l2_gather(ctx, buf, 2, n_ops, sink), n_ops * 8)}
     ctx.sync()
     return {k: round(v, 1) for k, v in res.items()}
 
@@ -250,11 +253,11 @@ def l2_roofline(name, kms_per_launch, S_occ, L, l2):
         return None
     payload = S_occ * L * 8 * 2 * 4
     ach = payload / (kms_per_launch * 1e-3) / 1e9
-    peak = l2["read_gbs"] if name == "encode" else l2["atomic_v4_gbs"]
+    peak = l2["gather_v4_gbs"] if name == "encode" else l2["atomic_v4_gbs"]
     return {"achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
             "payload_bytes": payload,
-            "peak_source": "measured by probe: " + ("L2-resident read stream" if name == "encode"
-                                                    else "random float4 atomic adds into a 64 MiB table")}
+            "peak_source": "measured by probe: random float4 " + ("loads from" if name == "encode"
+                                                                  else "atomic adds into") + " a 64 MiB table"}
 
 
 def roofline(ktime, tw, R, S_occ, peaks, l2=None):
@@ -301,6 +304,8 @@ def apply_batched(out, bt, invr, ctx, args, world, peaks):
     l2 = measure_l2(invr, ctx)
     out["l2_probe"] = l2
     out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks, l2)
+    out["l2_rooflines"] = {k: l2_roofline(k, bt["ktime"][k][0] / bt["ktime"][k][1], bS, btw.fields[0].desc.L, l2)
+                           for k in ("encode", "encode_bwd") if k in bt["ktime"]}
     nsteps = max(5, args.steps // 4)
     out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
     per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))

@@ -102,6 +102,7 @@ _SIGNATURES = {
     "invr_graph_get_lut": [_VP, C.c_int, _VP, _VP, _VP],
     "invr_probe_l2_read": [_VP, _VP, _I64, C.c_int, _VP, _VP],
     "invr_probe_l2_atomic": [_VP, _VP, _I64, C.c_int, _I64, _VP],
+    "invr_probe_l2_gather": [_VP, _VP, _I64, C.c_int, _I64, _VP, _VP],
     "invr_ctx_autotune": [_VP, C.POINTER(invr_train_args), _VP],
     "invr_ctx_get_tune": [_VP, C.POINTER(C.c_int)],
     "invr_field_copy_params": [_VP, _VP, _VP],
@@ -603,3 +604,9 @@ def probe_l2_atomic(ctx: Context, table, width: int, n_ops: int):
     """invr_probe_l2_atomic: n_ops float4 (width 4) or float2 (width 2) atomic adds at
     pseudo-random entries of `table` (a CUDA float32 tensor)."""
     _check(lib().invr_probe_l2_atomic(ctx.h, _ptr(table), table.numel(), width, n_ops, _stream()), ctx.h)
+
+
+def probe_l2_gather(ctx: Context, table, width: int, n_ops: int, sink):
+    """invr_probe_l2_gather: n_ops float4 (width 4) or float2 (width 2) loads at pseudo-random
+    entries of `table` (a CUDA float32 tensor)."""
+    _check(lib().invr_probe_l2_gather(ctx.h, _ptr(table), table.numel(), width, n_ops, _ptr(sink), _stream()), ctx.h)

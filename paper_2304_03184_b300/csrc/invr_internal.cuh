@@ -322,5 +322,7 @@ cudaError_t launch_probe_l2_read(const float* buf, int64_t n_floats, int passes,
                                  cudaStream_t s);
 cudaError_t launch_probe_l2_atomic(float* table, int64_t n_floats, int width, int64_t n_ops, int num_sms,
                                    cudaStream_t s);
+cudaError_t launch_probe_l2_gather(const float* table, int64_t n_floats, int width, int64_t n_ops, float* sink,
+                                   int num_sms, cudaStream_t s);
 
 }  // namespace invr

@@ -44,6 +44,36 @@ __global__ void __launch_bounds__(256) k_probe_l2_atomic(float* table, uint32_t 
   }
 }
 
+// width 4: float4 loads at random 16-byte-aligned entries; width 2: float2.
+template <int W>
+__global__ void __launch_bounds__(256) k_probe_l2_gather(const float* __restrict__ table, uint32_t n_vec,
+                                                         int64_t n_ops, float* sink) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float acc = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_ops; i += stride) {
+    const uint32_t e = probe_hash((uint64_t)i) % n_vec;
+    if (W == 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(table) + e);
+      acc += (v.x + v.y) + (v.z + v.w);
+    } else {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(table) + e);
+      acc += v.x + v.y;
+    }
+  }
+  if (acc == 1.2345f) sink[0] = acc;
+}
+
+cudaError_t launch_probe_l2_gather(const float* table, int64_t n_floats, int width, int64_t n_ops, float* sink,
+                                   int num_sms, cudaStream_t s) {
+  const int blocks = num_sms * 8;
+  if (width == 4) {
+    k_probe_l2_gather<4><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 4), n_ops, sink);
+  } else {
+    k_probe_l2_gather<2><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 2), n_ops, sink);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_probe_l2_read(const float* buf, int64_t n_floats, int passes, float* sink, int num_sms,
                                  cudaStream_t s) {
   const int64_t n4 = n_floats / 4;
