@@ -19,7 +19,7 @@ constexpr int kGeoOut = 16;
 constexpr int kColHidden = 64;
 constexpr int kOccRes = 128;    // occupancy grid resolution over [-1,1]^3
 constexpr int kTile = 128;      // sample tile: every view's sample range is padded to it
-constexpr int kKnnG = 64;       // nearest-node candidate grid resolution over [-1,1]^3
+constexpr int kKnnG = 128;      // nearest-node candidate grid resolution over [-1,1]^3
 constexpr uint16_t kKnnOverflow = 0xFFFF;
 constexpr int kRayBitWords = 32;   // 1024 samples per ray at most
 constexpr uint32_t kLutEmpty = 0xFFFFFFFFu;

@@ -3,7 +3,7 @@
 //
 //  * Canonical KNN field, built once per graph: for each of G^3 voxels over [-1,1]^3 the
 //    K canonical nodes x_i nearest to the voxel centre (exact, same key and tie rule as
-//    the live search, candidates from a 64^3 grid over the canonical nodes).
+//    the live search, candidates from a 128^3 grid over the canonical nodes).
 //  * Live index field, built per frame: every canonical voxel centre is carried to live
 //    space by the forward warp of Eq. 2 (the blend of its own K nodes' motions) and its
 //    index is stored in the live voxel it lands in; where several land in one voxel the

@@ -6,7 +6,7 @@
 // the nearest node's quaternion, dual-quaternion blend, normalisation, and the inverse
 // rigid motion v_c = R^T (p - t) of the blend.
 //
-// Exact K-nearest search without scanning all N nodes: once per frame a 64^3 candidate
+// Exact K-nearest search without scanning all N nodes: once per frame a 128^3 candidate
 // grid over [-1,1]^3 is built.  For a cell with centre c and half-diagonal rho, let
 // d_K(c) be the distance from c to its K-th nearest node.  Every point p of the cell has K
 // nodes within d_K(c) + rho, so each of its K nearest nodes lies within d_K(c) + 2 rho of

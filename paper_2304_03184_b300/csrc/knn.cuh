@@ -1,6 +1,6 @@
 // Exact K-nearest-node selection shared by the warp and the look-up-table builder: the
 // FP32 key ((dx*dx)+(dy*dy))+(dz*dz), ties to the lower node index, candidates from the
-// per-frame 64^3 candidate grid (or all nodes where a cell overflowed).
+// per-frame 128^3 candidate grid (or all nodes where a cell overflowed).
 #pragma once
 #include "invr_internal.cuh"
 
