@@ -613,7 +613,9 @@ def bench_deform(invr, args, flush, world, prec_name):
     ctx = invr.Context(torch.cuda.current_device())
     tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
     R = tb.batches[0][0].shape[1]
-    ctx.reserve(R, 32)          # sample slots (and the net's operand tiles) for ~12 occupied per ray
+    # sample slots (and the net's operand tiles) for ~12 occupied per ray, for the training
+    # rays and the 512x512 render below
+    ctx.reserve(max(R, 512 * 512), 32)
     steps = max(5, args.steps // 4)
     ms_plain, _ = time_train(invr, ctx, tb, steps, args.warmup, flush, world)
     net = invr.Deform.from_synth(ctx, dp)
