@@ -3,8 +3,10 @@
 // N_l, the table slots of its 8 corners (dense row-major when (N_l+1)^3 <= T, else the
 // XOR-of-primes spatial hash mod T) and the trilinear blend of their F = 2 features.
 //
-// One thread per (sample, level); blockIdx.y is the level, so a warp reads one level's
-// table for 32 consecutive samples of one ray (spatially coherent).  Tables are level-major
+// One thread per (sample, level); a block takes one level of a chunk of 256 consecutive
+// samples, so a warp reads one level's table for 32 consecutive samples of one ray
+// (spatially coherent), and the blocks of a chunk's levels run together (its positions
+// are read from DRAM once, then from L2).  Tables are level-major
 // [L][T][2] FP32: each corner is one 8-byte load, and the +x corner pair shares a 32-byte
 // sector.  Features are written feature-major [L*2][S] (coalesced).
 //
@@ -18,14 +20,20 @@
 
 namespace invr {
 
-__global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) {
-  const int l = blockIdx.y;
+// Work items: (chunk of 256 samples, level) with the level varying fastest, so the blocks
+// that handle the L levels of one chunk run together and read its positions from L2 once
+// (a level-major order streamed every sample's position from DRAM once per level).
+__global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, int L) {
   const int64_t S_cap = P.ws.S_cap;
   if (P.ws.view_base[P.n_views] > S_cap) return;
   const int64_t S0 = P.ws.view_base[P.view_lo], S = P.ws.view_base[P.view_hi];
   float* feat = static_cast<float*>(P.ws.feat);
-  int v = P.view_lo;
-  for (int64_t s = S0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t n_items = (S - S0 + 255) / 256 * L;
+  for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
+    const int l = (int)(b % L);
+    const int64_t s = S0 + (b / L) * 256 + threadIdx.x;
+    if (s >= S) continue;
+    int v = P.view_lo;
     while (v + 1 < P.view_hi && s >= P.ws.view_base[v + 1]) ++v;
     const FieldDev& F = P.v[v].field;
     if (l >= F.L) continue;
@@ -40,17 +48,20 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) 
   }
 }
 
-__global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan P) {
-  const int l = blockIdx.y;
+// Work items as in k_encode: (chunk of 256 samples, level), level fastest.
+__global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan P, int L) {
   const int64_t S_cap = P.ws.S_cap;
   if (P.ws.view_base[P.n_views] > S_cap) return;
   const int64_t S0 = P.ws.view_base[P.view_lo], S = P.ws.view_base[P.view_hi];
   const float scale = P.grad_scale;
-  int v = P.view_lo;
+  const int64_t n_items = (S - S0 + 255) / 256 * L;
   // warps never straddle two views: view ranges are kTile-aligned (S0 too) and a warp is 32
-  for (int64_t s0 = S0 + (int64_t)blockIdx.x * blockDim.x; s0 < S; s0 += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
+    const int l = (int)(b % L);
+    const int64_t s0 = S0 + (b / L) * 256;
     const int64_t s = s0 + threadIdx.x;
     const int64_t sw = s0 + (threadIdx.x & ~31);
+    int v = P.view_lo;
     while (v + 1 < P.view_hi && sw >= P.ws.view_base[v + 1]) ++v;
     const FieldDev& F = P.v[v].field;
     if (l >= F.L || sw >= S) continue;  // warp-uniform
@@ -85,16 +96,14 @@ __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan
 cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s) {
   int L = 0;
   for (int v = 0; v < P.n_views; ++v) L = P.v[v].field.L > L ? P.v[v].field.L : L;
-  dim3 grid(num_sms * P.tune.encode_ctas_per_sm, L);
-  k_encode<<<grid, 256, 0, s>>>(P);
+  k_encode<<<num_sms * P.tune.encode_ctas_per_sm * L, 256, 0, s>>>(P, L);
   return cudaGetLastError();
 }
 
 cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s) {
   int L = 0;
   for (int v = 0; v < P.n_views; ++v) L = P.v[v].field.L > L ? P.v[v].field.L : L;
-  dim3 grid(num_sms * P.tune.encode_bwd_ctas_per_sm, L);
-  k_encode_bwd<<<grid, 256, 0, s>>>(P);
+  k_encode_bwd<<<num_sms * P.tune.encode_bwd_ctas_per_sm * L, 256, 0, s>>>(P, L);
   return cudaGetLastError();
 }
 
