@@ -260,6 +260,12 @@ def l2_roofline(name, kms_per_launch, S_occ, L, l2):
                                                                   else "atomic adds into") + " a 64 MiB table"}
 
 
+# DRAM bytes per step of k_encode_bwd on the batched key-frame workload (both field launches),
+# from the ncu capture summarised in profiles/encode_bwd_keyframe_batch_dram.md; None once the
+# kernel or the workload changes
+TRAFFIC = {("encode_bwd", "keyframe_batch_8frames_x2fields_s128"): 2_516_146_000}
+
+
 def roofline(ktime, tw, R, S_occ, peaks, l2=None):
     fp = tw.fields[0]
     n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()
@@ -282,7 +288,7 @@ def roofline(ktime, tw, R, S_occ, peaks, l2=None):
         peak = peaks.get("hbm_gbs", 6400.0)
         ach = work / dur / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None,
+                "frac": round(ach / peak, 4), "traffic": TRAFFIC.get((name, tw.name)),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "l2": l2_roofline(name, kms / kn, S_occ, fp.desc.L, l2)}
     return None
