@@ -79,6 +79,8 @@ struct invr_graph_s {
   };
   std::vector<Frame> frames;
   int cap = 0;  // 0: no candidate grid (scan all nodes)
+  uint16_t* coarse = nullptr;    // scratch of the two-level candidate-grid build
+  uint16_t* coarse_n = nullptr;
   // look-up-table neighbour search (Sec. 4.2); lut_res == 0: exact search
   int lut_res = 0;
   uint16_t* lut_canon = nullptr;   // [G^3][K] canonical KNN field
@@ -963,9 +965,17 @@ invr_status invr_graph_set_pose(invr_graph g, int frame, const float* dq_dev, co
     }
   }
   INVR_CUDA(ctx, TIMED(ctx, "graph_pack", s, launch_graph_pack(dq_dev, x_live_dev, N, fr.dq, fr.x_live, s)));
-  if (g->cap > 0)
+  if (g->cap > 0) {
+    if (!g->coarse) {
+      if (capturing(s)) return fail(ctx, INVR_E_STATE, "first pose of a graph cannot be set during capture");
+      const size_t cc = (size_t)(kKnnG / 2) * (kKnnG / 2) * (kKnnG / 2);
+      INVR_CUDA(ctx, dmalloc(&g->coarse, cc * kKnnCoarseCapFactor * g->cap));
+      INVR_CUDA(ctx, dmalloc(&g->coarse_n, cc));
+    }
     INVR_CUDA(ctx, TIMED(ctx, "knn_grid_build", s,
-                         launch_knn_grid_build(fr.x_live, N, g->desc.K, g->cap, fr.cand, fr.cand_n, ctx->num_sms, s)));
+                         launch_knn_grid_build(fr.x_live, N, g->desc.K, g->cap, g->coarse, g->coarse_n, fr.cand,
+                                               fr.cand_n, ctx->num_sms, s)));
+  }
   if (g->lut_res > 0) {
     const size_t G3 = (size_t)g->lut_res * g->lut_res * g->lut_res;
     if (!fr.lut_live) {
@@ -1023,8 +1033,15 @@ invr_status invr_graph_enable_lut(invr_graph g, int resolution, invr_stream stre
   }
   g->lut_res = resolution;
   INVR_CUDA(ctx, launch_pack_points(g->x_canon, N, g->x_canon4, s));
-  if (g->cap > 0)
-    INVR_CUDA(ctx, launch_knn_grid_build(g->x_canon4, N, K, g->cap, g->canon_cand, g->canon_cand_n, ctx->num_sms, s));
+  if (g->cap > 0) {
+    if (!g->coarse) {
+      const size_t cc = (size_t)(kKnnG / 2) * (kKnnG / 2) * (kKnnG / 2);
+      INVR_CUDA(ctx, dmalloc(&g->coarse, cc * kKnnCoarseCapFactor * g->cap));
+      INVR_CUDA(ctx, dmalloc(&g->coarse_n, cc));
+    }
+    INVR_CUDA(ctx, launch_knn_grid_build(g->x_canon4, N, K, g->cap, g->coarse, g->coarse_n, g->canon_cand,
+                                         g->canon_cand_n, ctx->num_sms, s));
+  }
   INVR_CUDA(ctx, TIMED(ctx, "lut_canon", s,
                        launch_lut_canon(g->x_canon4, N, K, g->canon_cand, g->canon_cand_n, g->cap, resolution,
                                         g->lut_canon, ctx->num_sms, s)));
@@ -1071,6 +1088,7 @@ invr_status invr_graph_destroy(invr_graph g) {
   for (auto& fr : g->frames) {
     dfree(fr.x_live); dfree(fr.dq); dfree(fr.cand); dfree(fr.cand_n);
   }
+  dfree(g->coarse); dfree(g->coarse_n);
   dfree(g->x_canon);
   delete g;
   return INVR_OK;

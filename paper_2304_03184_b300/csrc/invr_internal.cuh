@@ -279,8 +279,11 @@ cudaError_t launch_step_increment(int64_t* step_dev, cudaStream_t s);
 // graph preprocessing
 cudaError_t launch_graph_pack(const float* dq_soa, const float* x_soa, int n, float4* dq_out, float4* x_out,
                               cudaStream_t s);
-cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* cand, uint16_t* cand_n,
-                                  int num_sms, cudaStream_t s);
+// candidate grid of resolution kKnnG, through a kKnnG/2 grid (coarse, coarse_n: scratch of
+// (kKnnG/2)^3 x kKnnCoarseCapFactor * cap and (kKnnG/2)^3 entries)
+constexpr int kKnnCoarseCapFactor = 4;
+cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* coarse, uint16_t* coarse_n,
+                                  uint16_t* cand, uint16_t* cand_n, int num_sms, cudaStream_t s);
 
 // single-step entry points
 cudaError_t launch_ray_samples(int64_t n_rays, const float* o, const float* d, int n_samples, const uint32_t* occ,

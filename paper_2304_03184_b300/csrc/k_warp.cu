@@ -189,22 +189,44 @@ cudaError_t launch_graph_pack(const float* dq_soa, const float* x_soa, int n, fl
   return cudaGetLastError();
 }
 
-// One warp per grid cell: K-th nearest distance from the cell centre, then every node
-// within d_K + 2 rho (with margin), in index order.
-template <int K>
-__global__ void __launch_bounds__(256) k_knn_grid_build(const float4* __restrict__ x, int n, int cap,
-                                                        uint16_t* cand, uint16_t* cand_n) {
+// One warp per grid cell of resolution G: K-th nearest distance from the cell centre, then
+// every node within d_K + 2 rho (with margin), in index order.  Built in two levels: a
+// G/2 grid scans all nodes; a G cell scans only its parent's list, which holds every node
+// it needs -- the child's K nearest are among the parent's (the child centre is a point of
+// the parent cell), and a node within d_K(c') + 2 rho' of the child centre c' lies within
+// d_K(c) + 2 rho of the parent centre c, because d_K is 1-Lipschitz, |c - c'| = rho / 2 and
+// rho' = rho / 2.  The coarse lists (build scratch only) hold 4x the fine capacity, so few
+// parents overflow; a child of an overflowed parent scans all nodes.
+template <int K, int G, bool REFINE>
+__global__ void __launch_bounds__(256) k_knn_grid_build(const float4* __restrict__ x, int n, int cap, int pcap,
+                                                        const uint16_t* __restrict__ pcand,
+                                                        const uint16_t* __restrict__ pcand_n, uint16_t* cand,
+                                                        uint16_t* cand_n) {
+  constexpr float H = 2.0f / G;
+  constexpr float Rho = 0.8660254037844386f * H;
   const int lane = threadIdx.x & 31;
-  const int64_t n_cells = (int64_t)kKnnG * kKnnG * kKnnG;
+  const int64_t n_cells = (int64_t)G * G * G;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t cell = warp0; cell < n_cells; cell += n_warps) {
-    const int ix = (int)(cell % kKnnG), iy = (int)((cell / kKnnG) % kKnnG), iz = (int)(cell / (kKnnG * kKnnG));
-    const float cx = -1.0f + (ix + 0.5f) * kKnnH, cy = -1.0f + (iy + 0.5f) * kKnnH, cz = -1.0f + (iz + 0.5f) * kKnnH;
+    const int ix = (int)(cell % G), iy = (int)((cell / G) % G), iz = (int)(cell / (G * G));
+    const float cx = -1.0f + (ix + 0.5f) * H, cy = -1.0f + (iy + 0.5f) * H, cz = -1.0f + (iz + 0.5f) * H;
+    // source of candidates: all nodes, or the parent cell's list
+    const uint16_t* src = nullptr;
+    int m = n;
+    if (REFINE) {
+      const int64_t pc = (ix >> 1) + (int64_t)(G / 2) * ((iy >> 1) + (int64_t)(G / 2) * (iz >> 1));
+      const uint16_t pn = __ldg(pcand_n + pc);
+      if (pn != kKnnOverflow) {
+        src = pcand + pc * pcap;
+        m = pn;
+      }
+    }
     float best[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) best[k] = INFINITY;
-    for (int i = lane; i < n; i += 32) {
+    for (int j = lane; j < m; j += 32) {
+      const int i = src ? (int)__ldg(src + j) : j;
       const float4 p = __ldg(x + i);
       const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
       float d2 = dx * dx + dy * dy + dz * dz;
@@ -218,51 +240,61 @@ __global__ void __launch_bounds__(256) k_knn_grid_build(const float4* __restrict
     float kth = 0.0f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      float m = best[0];
+      float mn = best[0];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      const unsigned who = __ballot_sync(0xffffffffu, best[0] == m);
+      for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      const unsigned who = __ballot_sync(0xffffffffu, best[0] == mn);
       if (lane == __ffs(who) - 1) {
 #pragma unroll
         for (int j = 0; j + 1 < K; ++j) best[j] = best[j + 1];
         best[K - 1] = INFINITY;
       }
-      kth = m;
+      kth = mn;
     }
-    const float rad = (sqrtf(kth) + 2.0f * kKnnRho) * 1.001f + 1e-4f;
+    const float rad = (sqrtf(kth) + 2.0f * Rho) * 1.001f + 1e-4f;
     const float rad2 = rad * rad;
     int count = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int i = base + lane;
+    for (int base = 0; base < m; base += 32) {
+      const int j = base + lane;
       bool in = false;
-      if (i < n) {
+      int i = 0;
+      if (j < m) {
+        i = src ? (int)__ldg(src + j) : j;
         const float4 p = __ldg(x + i);
         const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
         in = dx * dx + dy * dy + dz * dz <= rad2;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, in);
+      const unsigned mk = __ballot_sync(0xffffffffu, in);
       if (in) {
-        const int pos = count + __popc(m & ((1u << lane) - 1u));
+        const int pos = count + __popc(mk & ((1u << lane) - 1u));
         if (pos < cap) cand[cell * cap + pos] = (uint16_t)i;
       }
-      count += __popc(m);
+      count += __popc(mk);
     }
     if (lane == 0) cand_n[cell] = count <= cap ? (uint16_t)count : kKnnOverflow;
   }
 }
 
-cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* cand, uint16_t* cand_n,
-                                  int num_sms, cudaStream_t s) {
+template <int K>
+static void grid_build_k(const float4* x, int n, int cap, uint16_t* coarse, uint16_t* coarse_n, uint16_t* cand,
+                         uint16_t* cand_n, int grid, cudaStream_t s) {
+  const int pcap = kKnnCoarseCapFactor * cap;
+  k_knn_grid_build<K, kKnnG / 2, false><<<grid, 256, 0, s>>>(x, n, pcap, 0, nullptr, nullptr, coarse, coarse_n);
+  k_knn_grid_build<K, kKnnG, true><<<grid, 256, 0, s>>>(x, n, cap, pcap, coarse, coarse_n, cand, cand_n);
+}
+
+cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* coarse, uint16_t* coarse_n,
+                                  uint16_t* cand, uint16_t* cand_n, int num_sms, cudaStream_t s) {
   const int grid = num_sms * 8;
   switch (K) {
-    case 1: k_knn_grid_build<1><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    case 2: k_knn_grid_build<2><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    case 3: k_knn_grid_build<3><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    case 4: k_knn_grid_build<4><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    case 5: k_knn_grid_build<5><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    case 6: k_knn_grid_build<6><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    case 7: k_knn_grid_build<7><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
-    default: k_knn_grid_build<8><<<grid, 256, 0, s>>>(x_live, n, cap, cand, cand_n); break;
+    case 1: grid_build_k<1>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 2: grid_build_k<2>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 3: grid_build_k<3>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 4: grid_build_k<4>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 5: grid_build_k<5>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 6: grid_build_k<6>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 7: grid_build_k<7>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    default: grid_build_k<8>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
   }
   return cudaGetLastError();
 }

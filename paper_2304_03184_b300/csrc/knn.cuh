@@ -6,9 +6,6 @@
 
 namespace invr {
 
-constexpr float kKnnH = 2.0f / kKnnG;
-constexpr float kKnnRho = 0.8660254037844386f * kKnnH;  // half-diagonal sqrt(3)/2 h
-
 // Insert (key, id) into the ascending list; equal keys keep the earlier (lower) id first.
 // From the first slot whose key is larger, every later entry shifts down by one (an
 // entry carried down is never compared again, so entries with equal keys keep their order).

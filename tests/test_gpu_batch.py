@@ -163,3 +163,54 @@ def test_l2_probes_do_the_counted_work(env):
     assert float(sink.item()) == 0.0
     with pytest.raises(invr.InvrError):
         invr.probe_l2_atomic(ctx, buf, 3, 10)
+
+
+def test_graph_replay_with_deformation_net_tables_and_paper_loss(env):
+    """A captured step with the newer options on: the human field through look-up tables and
+    a tensor-core deformation net, the paper's losses.  Replays equal eager steps."""
+    invr, oracle = env
+    import torch
+    rng = np.random.default_rng(17)
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    dp = synth.make_deform(rng)
+    poses = [synth.make_pose(rng) for _ in range(2)]
+    total = sum(b.rays.n for b in tw.batches)
+
+    def build(ctx):
+        fields = {id(fp): invr.Field.from_synth(ctx, fp, invr.INVR_MLP_BF16) for fp in tw.fields}
+        net = invr.Deform.from_synth(ctx, dp, invr.INVR_MLP_FP16)
+        keep, batches, k = [], [], 0
+        for b in tw.batches:
+            sv = b.view
+            g = None
+            occ = cu(sv.occupancy)
+            if sv.graph is not None:
+                g = invr.Graph(ctx, sv.graph.x_canon.shape[1], sv.graph.K, sv.graph.radius, 1, cu(sv.graph.x_canon))
+                g.set_pose(0, cu(sv.graph.dq), cu(sv.graph.x_live))
+                g.enable_lut(64)
+                pose = cu(poses[k])
+                k += 1
+                view = invr.View(fields[id(sv.field)], g, 0, None, occ, net, pose)
+                keep.append((g, occ, pose))
+            else:
+                view = invr.View(fields[id(sv.field)], None, 0, sv.rigid_dq, occ)
+                keep.append(occ)
+            batches.append((cu(b.rays.o), cu(b.rays.d), view, cu(b.target), cu(b.mask), cu(b.depth)))
+        tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2,
+                               tw.adam_eps, loss="paper")
+        return tb, fields, net, keep
+
+    ctx_e, ctx_g = invr.Context(0), invr.Context(0)
+    tb_e, f_e, n_e, k_e = build(ctx_e)
+    tb_g, f_g, n_g, k_g = build(ctx_g)
+    ctx_g.reserve(total, tw.n_samples)
+    eager = [float(invr.train_step(ctx_e, tb_e).item()) for _ in range(4)]
+    graph = invr.TrainGraph(ctx_g, tb_g, warmup=2)
+    replay = [float(graph.replay().item()) for _ in range(2)]
+    ctx_g.sync()
+    # the float atomics of the gradient scatter sum in a different order on each run, and Adam
+    # (eps 1e-15) turns near-zero gradient differences into steps of size lr: the runs drift
+    # apart by ~1e-4 per step under the paper's summed losses
+    np.testing.assert_allclose(replay[0], eager[2], rtol=1e-4)
+    np.testing.assert_allclose(replay[1], eager[3], rtol=1e-3)
+    assert eager[3] < eager[0]
