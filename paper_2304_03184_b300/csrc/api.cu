@@ -196,6 +196,7 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
     return fail(ctx, INVR_E_STATE, "workspace too small during stream capture: call invr_ctx_reserve first");
   R = std::max(R, ctx->cap_R);
   S = std::max(S, ctx->cap_S);
+  S = (S + kTile - 1) / kTile * kTile;  // 16-byte aligned row groups of the 16-bit feature tiles
   train = train || ctx->cap_train;
   INVR_CUDA(ctx, cudaDeviceSynchronize());
   free_workspace(ctx->ws);

@@ -104,7 +104,7 @@ struct Workspace {
   float* s_t;               // [S] sample depth t_j
   float* s_pos;             // [3][S] live position
   float* s_vc;              // [3][S] canonical position
-  void* feat;               // [mlp_in][S] FP32, or [S][mlp_in] 16-bit for the tensor-core MLP
+  void* feat;               // [kMaxIn][S] FP32 feature-major, or 16-bit tiles (feat16_offset)
   float* out;               // [4][S] sigma, r, g, b
   float* dout;              // [4][S] dL/d o_0, dL/d z_rgb
   float* dfeat;             // [mlp_in][S]
@@ -248,6 +248,22 @@ __device__ __forceinline__ int view_of_slot(const int32_t* view_base, int n_view
 }
 
 __device__ __forceinline__ void flag_status(unsigned* status, unsigned bit) { atomicOr(status, bit); }
+
+// 16-bit encoding features of a tensor-core field.  Each 128-sample tile T is the first
+// MMA's A operand [128 x K] (K = mlp_in) in the K-major no-swizzle layout: 16 row groups of
+// 8 samples, K * 16 bytes each.  Row group g of tile T sits at byte g * 4 * S_cap + T * 512
+// of the feature buffer, inside the columns that the FP32 feature-major layout gives the
+// same samples, so views of different precisions in one call never overlap; with S_cap a
+// multiple of kTile every row group starts on a 16-byte boundary (one bulk copy each).
+__host__ __device__ constexpr size_t feat16_group_offset(int64_t S_cap, int64_t tile, int g) {
+  return (size_t)g * 4 * (size_t)S_cap + (size_t)tile * 512;
+}
+
+// Byte offset of feature k of sample s (k even: the pair k, k+1 is one 32-bit word).
+__host__ __device__ constexpr size_t feat16_offset(int64_t S_cap, int64_t s, int k) {
+  return feat16_group_offset(S_cap, s >> 7, (int)((s & 127) >> 3)) + (size_t)((k >> 3) * 128) +
+         (size_t)((s & 7) * 16) + (size_t)((k & 7) * 2);
+}
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -8,7 +8,8 @@
 // (spatially coherent), and the blocks of a chunk's levels run together (its positions
 // are read from DRAM once, then from L2).  Tables are level-major
 // [L][T][2] FP32: each corner is one 8-byte load, and the +x corner pair shares a 32-byte
-// sector.  Features are written feature-major [L*2][S] (coalesced).
+// sector.  Features are written feature-major [L*2][S] (coalesced) for FP32 fields, and as
+// the 16-bit MMA operand tiles of the tensor-core MLPs for FP16/BF16 fields.
 //
 // Backward: the same corners receive w_corner * dL/dfeat through float2 atomics into the
 // gradient table (same layout).  On coarse levels, lanes of a warp that hit the same slot
@@ -17,6 +18,7 @@
 // Bound: L2 (tables up to 64 MiB per field stay L2-resident) -- 8 x 8 B gathers per
 // sample-level forward, 8 x 8 B atomics backward.
 #include "hash_grid.cuh"
+#include "tc_ptx.cuh"
 
 namespace invr {
 
@@ -43,8 +45,14 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, 
       level_corners(F, l, make_float3(P.ws.s_vc[s], P.ws.s_vc[S_cap + s], P.ws.s_vc[2 * S_cap + s]), c);
       f = level_feature(F, l, c);
     }
-    feat[(int64_t)(2 * l) * S_cap + s] = f.x;
-    feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
+    if (F.mlp_kind == kMlpF32) {
+      feat[(int64_t)(2 * l) * S_cap + s] = f.x;
+      feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
+    } else {
+      // tensor-core field: the pair as 16-bit operand row s of its tile (rounded to nearest)
+      const uint32_t w = F.mlp_kind == kMlpBF16 ? tc::pack2<true>(f.x, f.y) : tc::pack2<false>(f.x, f.y);
+      *reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l)) = w;
+    }
   }
 }
 

@@ -4,19 +4,23 @@
 //
 // One CTA = 128 threads = one warpgroup; a tile is 128 samples, thread t owns sample t,
 // which is row t of every MMA (M = 128) and lane t of tensor memory.  Per tile the five
-// layers run as a chain:
-//   X [128 x in]  -> D1 = X W1^T (N 64)  -> ReLU -> H1 (smem, 16-bit)
-//   H1            -> D2 = H1 W2^T (N 64) -> ReLU -> H2
-//   H2            -> D3 = H2 W3^T (N 16) -> sigma = exp(o_0); O = (0, o_1..o_15)
-//   O             -> D4 = O W4p^T (N 64) -> ReLU -> H4 (reuses H1)
-//   H4            -> D5 = H4 W5p^T (N 16) -> rgb = sigmoid(z_0..z_2)
-// One elected thread issues each layer's MMAs (K = 16 per instruction) and commits them to
-// an mbarrier; all threads wait, read their row from tensor memory (tcgen05.ld 32x32b),
-// apply the activation in FP32, and write the next operand row in the K-major layout.
-// Weights (padded: W4p gets a zero column for o_0, W5p 13 zero rows) are converted to 16
-// bit and staged in shared memory once per field.  Several CTAs per SM overlap their
-// chains.  Every mbarrier wait is bounded; a timeout sets the status word and the CTA frees
-// its tensor memory and exits.
+// layers run as a chain through two 16 KB operand buffers P and Q:
+//   X [128 x in] (P) -> D = X W1^T (N 64)  -> ReLU -> H1 (Q)
+//   H1 (Q)           -> D = H1 W2^T (N 64) -> ReLU -> H2 (P)
+//   H2 (P)           -> D = H2 W3^T (N 16) -> sigma = exp(o_0); O = (0, o_1..o_15) (Q)
+//   O (Q)            -> D = O W4p^T (N 64) -> ReLU -> H4 (Q, over O)
+//   H4 (Q)           -> D = H4 W5p^T (N 16) -> rgb = sigmoid(z_0..z_2)
+// One elected thread issues each layer's MMAs (K = 16 per instruction) into one 64-column
+// accumulator and commits them to an mbarrier; all threads wait, read their row from tensor
+// memory (one tcgen05.ld of 64 columns), apply the activation in FP32 and write the next
+// operand row in the K-major layout.  The encoder writes the features as 16-bit operand
+// tiles, so a tile's X arrives by 16 bulk copies of one row group each; the copies of the
+// CTA's next tile are issued as soon as layer 3 has read P, and land while layers 4 and 5
+// run.  Weights (padded: W4p gets a zero column for o_0, W5p 13 zero rows) are converted
+// to 16 bit and staged in shared memory once per field.  50 KB of shared memory and 64
+// tensor-memory columns per CTA: four CTAs per SM overlap their chains.  Every mbarrier
+// wait is bounded; a timeout sets the status word, and the CTA waits (bounded) for its
+// own copies and MMAs in flight, frees its tensor memory and exits.
 #include "invr_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -26,7 +30,8 @@ namespace {
 
 constexpr int kTM = 128;             // samples per tile = MMA M
 constexpr int kThreadsTC = 128;
-constexpr uint32_t kTmemCols = 128;  // D1/D3/D5 in columns 0..63, D2/D4 in 64..127
+constexpr int kCtasPerSm = 4;
+constexpr uint32_t kTmemCols = 64;   // one accumulator, reused by every layer
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls of try_wait (bounded: a few seconds)
 
 // shared-memory plan (bytes)
@@ -35,15 +40,15 @@ constexpr uint32_t OFF_W2 = OFF_W1 + 64 * 32 * 2;    // 64 x 64
 constexpr uint32_t OFF_W3 = OFF_W2 + 64 * 64 * 2;    // 16 x 64
 constexpr uint32_t OFF_W4 = OFF_W3 + 16 * 64 * 2;    // 64 x 16
 constexpr uint32_t OFF_W5 = OFF_W4 + 64 * 16 * 2;    // 16 x 64
-constexpr uint32_t OFF_X = OFF_W5 + 16 * 64 * 2;     // 128 x 32
-constexpr uint32_t OFF_H1 = OFF_X + kTM * 32 * 2;    // 128 x 64 (H1, then H4)
-constexpr uint32_t OFF_H2 = OFF_H1 + kTM * 64 * 2;   // 128 x 64
-constexpr uint32_t OFF_O = OFF_H2 + kTM * 64 * 2;    // 128 x 16
-constexpr uint32_t OFF_MISC = OFF_O + kTM * 16 * 2;  // mbarrier (8 B) + TMEM base (4 B)
-constexpr uint32_t kSmemTC = OFF_MISC + 64 + 4096;   // + guard band
+constexpr uint32_t OFF_P = OFF_W5 + 16 * 64 * 2;     // 128 x 64: X, then H2
+constexpr uint32_t OFF_Q = OFF_P + kTM * 64 * 2;     // 128 x 64: H1, then O, then H4
+constexpr uint32_t OFF_MISC = OFF_Q + kTM * 64 * 2;  // 2 mbarriers (16 B) + TMEM base (4 B)
+constexpr uint32_t kSmemTC = OFF_MISC + 64;
+static_assert(kCtasPerSm * (kSmemTC + 1024) <= 228 * 1024, "four CTAs per SM");
+static_assert(kCtasPerSm * kTmemCols <= 512, "tensor memory of four CTAs");
 
 struct TcArgs {
-  const float* feat;        // [in][ld] FP32
+  const void* feat;         // 16-bit operand tiles (feat16_offset), or FP32 [in][ld] (points)
   float* out;               // [4][ld]
   const int32_t* view_base; // per-view tile-aligned sample ranges (device) or null
   int64_t ld;
@@ -113,25 +118,20 @@ __device__ __forceinline__ void issue_layer(uint32_t d_tmem, uint32_t a_saddr, u
   }
 }
 
-// Read 64 accumulator columns of this thread's row, apply ReLU, store as row t of a K=64
-// 16-bit operand.
+// Read the 64 accumulator columns of this thread's row, apply ReLU, store as row t of a
+// K = 64 16-bit operand.
 template <bool BF16>
 __device__ __forceinline__ void relu_row64(uint32_t taddr, uint8_t* dst, int t) {
+  float v[64];
+  tc::tmem_ld64(taddr, v);
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float v[16];
-    tc::tmem_ld16(taddr + 16 * c, v);
-    uint4 lo, hi;
-    lo.x = tc::pack2<BF16>(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f));
-    lo.y = tc::pack2<BF16>(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
-    lo.z = tc::pack2<BF16>(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f));
-    lo.w = tc::pack2<BF16>(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f));
-    hi.x = tc::pack2<BF16>(fmaxf(v[8], 0.f), fmaxf(v[9], 0.f));
-    hi.y = tc::pack2<BF16>(fmaxf(v[10], 0.f), fmaxf(v[11], 0.f));
-    hi.z = tc::pack2<BF16>(fmaxf(v[12], 0.f), fmaxf(v[13], 0.f));
-    hi.w = tc::pack2<BF16>(fmaxf(v[14], 0.f), fmaxf(v[15], 0.f));
-    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 16 * c, 64)) = lo;
-    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 16 * c + 8, 64)) = hi;
+  for (int c = 0; c < 8; ++c) {
+    uint4 q;
+    q.x = tc::pack2<BF16>(fmaxf(v[8 * c + 0], 0.f), fmaxf(v[8 * c + 1], 0.f));
+    q.y = tc::pack2<BF16>(fmaxf(v[8 * c + 2], 0.f), fmaxf(v[8 * c + 3], 0.f));
+    q.z = tc::pack2<BF16>(fmaxf(v[8 * c + 4], 0.f), fmaxf(v[8 * c + 5], 0.f));
+    q.w = tc::pack2<BF16>(fmaxf(v[8 * c + 6], 0.f), fmaxf(v[8 * c + 7], 0.f));
+    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
   }
 }
 
@@ -142,16 +142,40 @@ __device__ __forceinline__ void operands_ready() {
   __syncthreads();
 }
 
-template <bool BF16>
-__global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_constant__ TcArgs A) {
+// The CTA's tiles: from `tile` on in steps of gridDim.x, the first whose view has this
+// kernel's MLP kind (uniform over the CTA), or n_tiles.
+__device__ __forceinline__ int64_t next_tile(const TcArgs& A, int64_t tile, int64_t n_tiles, int kind) {
+  for (; tile < n_tiles; tile += gridDim.x) {
+    const FieldDev& F = A.f[A.view_base ? view_of_slot(A.view_base, A.n_views, tile * kTM) : 0];
+    if (F.mlp_kind == kind) return tile;
+  }
+  return n_tiles;
+}
+
+// One thread: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each).
+__device__ __forceinline__ void load_x(const TcArgs& A, int64_t tile, int in, uint32_t dst, uint32_t bar) {
+  const uint32_t group = (uint32_t)in * 16;
+  tc::mbar_expect_tx(bar, 16 * group);
+  const uint8_t* src = static_cast<const uint8_t*>(A.feat);
+  for (int g = 0; g < 16; ++g) tc::bulk_g2s(dst + g * group, src + feat16_group_offset(A.ld, tile, g), group, bar);
+}
+
+// TILES: the plan's 16-bit operand tiles (bulk copies, prefetched); else FP32 feature-major
+// points converted by the threads.
+template <bool BF16, bool TILES>
+__global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __grid_constant__ TcArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if (A.view_base && (int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 8);
-  const uint32_t mbar = tc::smem_u32(sm + OFF_MISC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
+  const uint32_t mbar = tc::smem_u32(sm + OFF_MISC);      // MMA completion
+  const uint32_t xbar = tc::smem_u32(sm + OFF_MISC + 8);  // X copies landed
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
-  if (t == 0) tc::mbar_init(mbar, 1);
+  if (t == 0) {
+    tc::mbar_init(mbar, 1);
+    tc::mbar_init(xbar, 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -162,13 +186,21 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
   const int64_t S = A.view_base ? (int64_t)A.view_base[A.n_views] : A.n;
   const int64_t n_tiles = (S + kTM - 1) / kTM;
   const float* loaded = nullptr;
-  uint32_t phase = 0;
+  uint32_t phase = 0, xphase = 0;
   bool ok = true;
+  bool mma_pending = false, x_pending = false;
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+  int64_t tile = next_tile(A, blockIdx.x, n_tiles, kind);
+  if (TILES && t == 0 && tile < n_tiles) {
+    const FieldDev& F0 = A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)];
+    load_x(A, tile, F0.mlp_in, sbase + OFF_P, xbar);
+  }
+  x_pending = TILES && tile < n_tiles;
+
+  while (tile < n_tiles) {
     const int64_t s0 = tile * kTM;
     const FieldDev& F = A.f[A.view_base ? view_of_slot(A.view_base, A.n_views, s0) : 0];
-    if (F.mlp_kind != kind) continue;  // uniform over the CTA
+    const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
     if (F.weights != loaded) {
       __syncthreads();
       stage_weights<BF16>(sm, F);
@@ -176,55 +208,75 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
     }
     const int in = F.mlp_in;
     const int valid = (int)(S - s0 < kTM ? S - s0 : kTM);
-    // ---- X: this thread's features (FP32, feature-major in global) -> row t
-    for (int j = 0; j < in / 8; ++j) {
-      float x[8];
+    if constexpr (!TILES) {
+      // ---- X: this thread's FP32 features (feature-major in global) -> row t
+      const float* feat = static_cast<const float*>(A.feat);
+      for (int j = 0; j < in / 8; ++j) {
+        float x[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = t < valid ? A.feat[(int64_t)(8 * j + i) * A.ld + s0 + t] : 0.0f;
-      uint4 q;
-      q.x = tc::pack2<BF16>(x[0], x[1]);
-      q.y = tc::pack2<BF16>(x[2], x[3]);
-      q.z = tc::pack2<BF16>(x[4], x[5]);
-      q.w = tc::pack2<BF16>(x[6], x[7]);
-      *reinterpret_cast<uint4*>(sm + OFF_X + tc::kmajor_offset(t, 8 * j, in)) = q;
+        for (int i = 0; i < 8; ++i) x[i] = t < valid ? feat[(int64_t)(8 * j + i) * A.ld + s0 + t] : 0.0f;
+        uint4 q;
+        q.x = tc::pack2<BF16>(x[0], x[1]);
+        q.y = tc::pack2<BF16>(x[2], x[3]);
+        q.z = tc::pack2<BF16>(x[4], x[5]);
+        q.w = tc::pack2<BF16>(x[6], x[7]);
+        *reinterpret_cast<uint4*>(sm + OFF_P + tc::kmajor_offset(t, 8 * j, in)) = q;
+      }
     }
-    operands_ready();
+    operands_ready();  // staged weights (and converted X) visible to the tensor core
+    if constexpr (TILES) {
+      ok = tc::mbar_wait(xbar, xphase, A.wait_limit);
+      if (!__syncthreads_and(ok)) { ok = false; break; }
+      xphase ^= 1u;
+      x_pending = false;
+    }
     // ---- layer 1
     if (t == 0) {
       tc::fence_after_sync();
-      issue_layer(tmem + 0, sbase + OFF_X, sbase + OFF_W1, in, 64, BF16);
+      issue_layer(tmem, sbase + OFF_P, sbase + OFF_W1, in, 64, BF16);
       tc::commit_to(mbar);
     }
+    mma_pending = true;
     ok = tc::mbar_wait(mbar, phase, A.wait_limit);
-    phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
+    phase ^= 1u;
+    mma_pending = false;
     tc::fence_after_sync();
-    relu_row64<BF16>(row_taddr + 0, sm + OFF_H1, t);
+    relu_row64<BF16>(row_taddr, sm + OFF_Q, t);
     operands_ready();
     // ---- layer 2
     if (t == 0) {
       tc::fence_after_sync();
-      issue_layer(tmem + 64, sbase + OFF_H1, sbase + OFF_W2, 64, 64, BF16);
+      issue_layer(tmem, sbase + OFF_Q, sbase + OFF_W2, 64, 64, BF16);
       tc::commit_to(mbar);
     }
+    mma_pending = true;
     ok = tc::mbar_wait(mbar, phase, A.wait_limit);
-    phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
+    phase ^= 1u;
+    mma_pending = false;
     tc::fence_after_sync();
-    relu_row64<BF16>(row_taddr + 64, sm + OFF_H2, t);
+    relu_row64<BF16>(row_taddr, sm + OFF_P, t);
     operands_ready();
     // ---- layer 3: geometry output o (16)
     if (t == 0) {
       tc::fence_after_sync();
-      issue_layer(tmem + 0, sbase + OFF_H2, sbase + OFF_W3, 64, 16, BF16);
+      issue_layer(tmem, sbase + OFF_P, sbase + OFF_W3, 64, 16, BF16);
       tc::commit_to(mbar);
     }
+    mma_pending = true;
     ok = tc::mbar_wait(mbar, phase, A.wait_limit);
-    phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
+    phase ^= 1u;
+    mma_pending = false;
     tc::fence_after_sync();
+    // P (H2) has been read: the next tile's X may land there now
+    if (TILES && nxt < n_tiles) {
+      if (t == 0) load_x(A, nxt, A.f[view_of_slot(A.view_base, A.n_views, nxt * kTM)].mlp_in, sbase + OFF_P, xbar);
+      x_pending = true;
+    }
     float o[16];
-    tc::tmem_ld16(row_taddr + 0, o);
+    tc::tmem_ld16(row_taddr, o);
     const float sigma = expf(o[0]);
     {
       uint4 lo, hi;
@@ -236,34 +288,38 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
       hi.y = tc::pack2<BF16>(o[10], o[11]);
       hi.z = tc::pack2<BF16>(o[12], o[13]);
       hi.w = tc::pack2<BF16>(o[14], o[15]);
-      *reinterpret_cast<uint4*>(sm + OFF_O + tc::kmajor_offset(t, 0, 16)) = lo;
-      *reinterpret_cast<uint4*>(sm + OFF_O + tc::kmajor_offset(t, 8, 16)) = hi;
+      *reinterpret_cast<uint4*>(sm + OFF_Q + tc::kmajor_offset(t, 0, 16)) = lo;
+      *reinterpret_cast<uint4*>(sm + OFF_Q + tc::kmajor_offset(t, 8, 16)) = hi;
     }
     operands_ready();
     // ---- layer 4: colour hidden
     if (t == 0) {
       tc::fence_after_sync();
-      issue_layer(tmem + 64, sbase + OFF_O, sbase + OFF_W4, 16, 64, BF16);
+      issue_layer(tmem, sbase + OFF_Q, sbase + OFF_W4, 16, 64, BF16);
       tc::commit_to(mbar);
     }
+    mma_pending = true;
     ok = tc::mbar_wait(mbar, phase, A.wait_limit);
-    phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
+    phase ^= 1u;
+    mma_pending = false;
     tc::fence_after_sync();
-    relu_row64<BF16>(row_taddr + 64, sm + OFF_H1, t);
+    relu_row64<BF16>(row_taddr, sm + OFF_Q, t);  // H4 over O (read by the completed layer 4)
     operands_ready();
     // ---- layer 5: colour output
     if (t == 0) {
       tc::fence_after_sync();
-      issue_layer(tmem + 16, sbase + OFF_H1, sbase + OFF_W5, 64, 16, BF16);
+      issue_layer(tmem, sbase + OFF_Q, sbase + OFF_W5, 64, 16, BF16);
       tc::commit_to(mbar);
     }
+    mma_pending = true;
     ok = tc::mbar_wait(mbar, phase, A.wait_limit);
-    phase ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
+    phase ^= 1u;
+    mma_pending = false;
     tc::fence_after_sync();
     float z[16];
-    tc::tmem_ld16(row_taddr + 16, z);
+    tc::tmem_ld16(row_taddr, z);
     if (t < valid) {
       const int64_t gs = s0 + t;
       A.out[gs] = sigma;
@@ -273,12 +329,14 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
     }
     tc::fence_before_sync();
     __syncthreads();  // every thread is done with this tile's TMEM and operands
+    tile = nxt;
   }
   if (!ok) {
-    // a wait gave up: record it, then let the pending MMAs finish (bounded) before the
-    // tensor memory they write is freed
+    // a wait gave up: record it, then let this CTA's MMAs and copies in flight finish
+    // (bounded) before the tensor memory and shared memory they write are released
     if (t == 0) atomicOr(A.status, kStatusTimeout);
-    tc::mbar_wait(mbar, phase ^ 1u, kWaitLimit);
+    if (mma_pending) tc::mbar_wait(mbar, phase, kWaitLimit);
+    if (x_pending) tc::mbar_wait(xbar, xphase, kWaitLimit);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -288,10 +346,10 @@ __global__ void __launch_bounds__(kThreadsTC, 3) k_mlp_fwd_tc(const __grid_const
   }
 }
 
-template <bool BF16>
+template <bool BF16, bool TILES>
 cudaError_t launch_tc(const TcArgs& A, int num_sms, cudaStream_t s) {
-  cudaFuncSetAttribute(k_mlp_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
-  k_mlp_fwd_tc<BF16><<<num_sms * 3, kThreadsTC, kSmemTC, s>>>(A);
+  cudaFuncSetAttribute(k_mlp_fwd_tc<BF16, TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
+  k_mlp_fwd_tc<BF16, TILES><<<num_sms * kCtasPerSm, kThreadsTC, kSmemTC, s>>>(A);
   return cudaGetLastError();
 }
 
@@ -305,7 +363,7 @@ bool plan_has_kind(const Plan& P, int kind) {
 
 cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   TcArgs A{};
-  A.feat = static_cast<const float*>(P.ws.feat);
+  A.feat = P.ws.feat;
   A.out = P.ws.out;
   A.view_base = P.ws.view_base;
   A.ld = P.ws.S_cap;
@@ -314,8 +372,8 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   A.status = P.status;
   for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
   cudaError_t e = cudaSuccess;
-  if (plan_has_kind(P, kMlpBF16)) e = launch_tc<true>(A, num_sms, s);
-  if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) e = launch_tc<false>(A, num_sms, s);
+  if (plan_has_kind(P, kMlpBF16)) e = launch_tc<true, true>(A, num_sms, s);
+  if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) e = launch_tc<false, true>(A, num_sms, s);
   return e;
 }
 
@@ -331,7 +389,7 @@ cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat
   A.status = status;
   A.f[0] = f;
   if (n <= 0) return cudaSuccess;
-  return f.mlp_kind == kMlpBF16 ? launch_tc<true>(A, num_sms, s) : launch_tc<false>(A, num_sms, s);
+  return f.mlp_kind == kMlpBF16 ? launch_tc<true, false>(A, num_sms, s) : launch_tc<false, false>(A, num_sms, s);
 }
 
 }  // namespace invr

@@ -62,39 +62,36 @@ __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint32_t a_saddr, u
   }
 }
 
-// Read 64 accumulator columns of this thread's row; write max(v, 0) (or v where the mask
-// row is positive, if MASK) as row t of a K = 64 16-bit operand.
+// Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0) (or v
+// where the mask row is positive, if MASK) as row t of a K = 64 16-bit operand.  Each
+// 16-byte chunk of the mask row is read before the same chunk of dst is written, so dst may
+// be the mask buffer itself (the delta replaces the activation it was masked by).
 template <bool BF16, bool MASK>
 __device__ __forceinline__ void row64_out(uint32_t taddr, uint8_t* dst, const uint8_t* mask, int t) {
+  float v[64];
+  tc::tmem_ld64(taddr, v);
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float v[16];
-    tc::tmem_ld16(taddr + 16 * c, v);
+  for (int c = 0; c < 8; ++c) {
+    float* x = v + 8 * c;
     if constexpr (MASK) {
-      const uint4 m0 = *reinterpret_cast<const uint4*>(mask + tc::kmajor_offset(t, 16 * c, 64));
-      const uint4 m1 = *reinterpret_cast<const uint4*>(mask + tc::kmajor_offset(t, 16 * c + 8, 64));
-      const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+      const uint4 m = *reinterpret_cast<const uint4*>(mask + tc::kmajor_offset(t, 8 * c, 64));
+      const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < 4; ++i) {
         // a 16-bit value is positive iff its sign bit is clear and it is not +0
-        if ((mw[i] & 0x8000u) || !(mw[i] & 0x7FFFu)) v[2 * i] = 0.0f;
-        if ((mw[i] & 0x80000000u) || !(mw[i] & 0x7FFF0000u)) v[2 * i + 1] = 0.0f;
+        if ((mw[i] & 0x8000u) || !(mw[i] & 0x7FFFu)) x[2 * i] = 0.0f;
+        if ((mw[i] & 0x80000000u) || !(mw[i] & 0x7FFF0000u)) x[2 * i + 1] = 0.0f;
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+      for (int i = 0; i < 8; ++i) x[i] = fmaxf(x[i], 0.0f);
     }
-    uint4 lo, hi;
-    lo.x = tc::pack2<BF16>(v[0], v[1]);
-    lo.y = tc::pack2<BF16>(v[2], v[3]);
-    lo.z = tc::pack2<BF16>(v[4], v[5]);
-    lo.w = tc::pack2<BF16>(v[6], v[7]);
-    hi.x = tc::pack2<BF16>(v[8], v[9]);
-    hi.y = tc::pack2<BF16>(v[10], v[11]);
-    hi.z = tc::pack2<BF16>(v[12], v[13]);
-    hi.w = tc::pack2<BF16>(v[14], v[15]);
-    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 16 * c, 64)) = lo;
-    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 16 * c + 8, 64)) = hi;
+    uint4 q;
+    q.x = tc::pack2<BF16>(x[0], x[1]);
+    q.y = tc::pack2<BF16>(x[2], x[3]);
+    q.z = tc::pack2<BF16>(x[4], x[5]);
+    q.w = tc::pack2<BF16>(x[6], x[7]);
+    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
   }
 }
 
