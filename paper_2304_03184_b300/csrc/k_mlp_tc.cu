@@ -152,12 +152,16 @@ __device__ __forceinline__ int64_t next_tile(const TcArgs& A, int64_t tile, int6
   return n_tiles;
 }
 
-// One thread: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each).
+// One warp: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each), one
+// per lane 0..15 after lane 0 has announced their bytes on the barrier.
 __device__ __forceinline__ void load_x(const TcArgs& A, int64_t tile, int in, uint32_t dst, uint32_t bar) {
+  const int lane = threadIdx.x & 31;
   const uint32_t group = (uint32_t)in * 16;
-  tc::mbar_expect_tx(bar, 16 * group);
-  const uint8_t* src = static_cast<const uint8_t*>(A.feat);
-  for (int g = 0; g < 16; ++g) tc::bulk_g2s(dst + g * group, src + feat16_group_offset(A.ld, tile, g), group, bar);
+  if (lane == 0) tc::mbar_expect_tx(bar, 16 * group);
+  __syncwarp();
+  if (lane < 16)
+    tc::bulk_g2s(dst + lane * group, static_cast<const uint8_t*>(A.feat) + feat16_group_offset(A.ld, tile, lane),
+                 group, bar);
 }
 
 // TILES: the plan's 16-bit operand tiles (bulk copies, prefetched); else FP32 feature-major
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
   bool mma_pending = false, x_pending = false;
 
   int64_t tile = next_tile(A, blockIdx.x, n_tiles, kind);
-  if (TILES && t == 0 && tile < n_tiles) {
+  if (TILES && warp == 0 && tile < n_tiles) {
     const FieldDev& F0 = A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)];
     load_x(A, tile, F0.mlp_in, sbase + OFF_P, xbar);
   }
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
     tc::fence_after_sync();
     // P (H2) has been read: the next tile's X may land there now
     if (TILES && nxt < n_tiles) {
-      if (t == 0) load_x(A, nxt, A.f[view_of_slot(A.view_base, A.n_views, nxt * kTM)].mlp_in, sbase + OFF_P, xbar);
+      if (warp == 0) load_x(A, nxt, A.f[view_of_slot(A.view_base, A.n_views, nxt * kTM)].mlp_in, sbase + OFF_P, xbar);
       x_pending = true;
     }
     float o[16];

@@ -4,26 +4,35 @@
 // so per-sample gradients are O(1) and do not underflow FP16) and the FP32 results (dX,
 // dW) by out_scale on the way out.
 //
-// One CTA = one warpgroup of 128 threads; per 128-sample tile (thread t = sample t):
-//   recompute  X -> H1 -> H2 -> O -> H4          (4 chained MMAs, M = 128, ReLU epilogues)
+// Per 128-sample tile (epilogue thread t = sample t, row t of every M = 128 MMA):
+//   recompute  X -> H1 -> H2 -> O -> H4          (4 chained MMAs, ReLU epilogues)
 //   adjoint    dZ -> dH4 -> dO -> dH2 -> dH1 -> dX (5 chained MMAs; each reads the forward
 //              weight as an MN-major operand; ReLU masks read back from the stored activations)
 //   weights    dW5^T += H4^T dZ, dW4 += dH4^T O, dW3^T += H2^T dO, dW2 += dH2^T H1,
-//              dW1 += dH1^T X: M = 64 MMAs with K = the 128 samples, issued next to the
-//              chain and accumulated in tensor memory over every tile the CTA visits.
+//              dW1 += dH1^T X: M = 64 MMAs with K = the 128 samples, accumulated in tensor
+//              memory over every tile the CTA visits.
 // The weight-gradient MMAs read the [sample][unit] activation buffers as MN-major operands
 // (each 8 x 16-byte core matrix holds 8 units of 8 samples), so no transposed copies exist.
-// Each masked delta is written over the activation that masks it (dH4 over H4, dH2 over H2,
-// dH1 over H1), and dO over dZ, once the MMAs that read them have completed.  X arrives as
-// the encoder's 16-bit operand tile by bulk copies into one of two buffers: the next tile's
-// copies are issued when this tile's have landed and run under its whole chain; the next
-// tile's dL/d(outputs) are loaded into registers at the same point.  90 KB of shared memory:
-// two CTAs per SM.
-// The accumulated dW are read out once per field (M = 64 accumulator: row r in TMEM lane
-// 32 (r / 16) + r % 16) and added to the gradient buffer with one atomic per weight per CTA.
-// dL/dX (the encoding features' gradient) is written FP32 feature-major for the hash
-// scatter.  All waits are bounded; a timeout sets the status word, and the CTA waits
-// (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
+//
+// Warp roles.  A tcgen05.mma instruction costs its issuing thread ~60 clocks whatever its
+// size (N <= 128), and a tile needs 65 of them, so one CTA = 4 epilogue warps + 1 issuer
+// warp.  The issuer waits for the epilogue's "operands ready" mbarrier (128 arrivals), issues
+// a stage's chain MMAs, commits them to the "accumulator ready" mbarrier, and only then
+// issues that stage's weight-gradient MMAs, which run while the epilogue works; the next
+// commit (tracking every earlier MMA) retires them.  The buffers are assigned so that an
+// epilogue never writes what the current stage's weight-gradient MMAs read: dH4 into its
+// own buffer, dO over dZ, dH2 over H4, dH1 over H2.  The issuer also moves X: the encoder's
+// 16-bit operand tile arrives by 16 bulk copies into one of two buffers, the next tile's
+// copies issued once this tile's first MMA has retired the previous tile's last
+// weight-gradient MMAs.  Epilogue threads load the next tile's dL/d(outputs) and padding
+// markers into registers under the chain (unconditionally; the padding selection is
+// applied when they are used).  106 KB of shared memory and 160 threads: two CTAs per SM.
+// The accumulated dW are read out once per field, after the issuer's "flush" commit (M = 64
+// accumulator: row r in TMEM lane 32 (r / 16) + r % 16), and added to the gradient buffer
+// with one atomic per weight per CTA.  dL/dX (the encoding features' gradient) is written
+// FP32 feature-major for the hash scatter.  All waits are bounded: a role that gives up sets
+// the status word and leaves its loop (the other role's waits then give up in turn), and the
+// issuer retires its MMAs and copies (bounded) before the tensor memory is freed.
 #include "mlp_tc_common.cuh"
 
 namespace invr {
@@ -32,7 +41,8 @@ namespace {
 
 using namespace mlp_tc;
 
-constexpr int kThreadsB = 128;
+constexpr int kEpi = 128;       // epilogue threads (warps 0..3)
+constexpr int kThreadsB = 160;  // + the issuer warp (warp 4)
 constexpr uint32_t kTmemColsB = 256;
 // tensor-memory columns
 constexpr uint32_t C_CHAIN = 0;     // 64: the chain's current layer
@@ -50,17 +60,17 @@ constexpr uint32_t B_W3 = B_W2 + 64 * 64 * 2;  // [16][64]
 constexpr uint32_t B_W4 = B_W3 + 16 * 64 * 2;  // [64][16]
 constexpr uint32_t B_W5 = B_W4 + 16 * 64 * 2;  // [16][64]
 constexpr uint32_t B_X = B_W5 + 16 * 64 * 2;   // 2 x [128][32]: this tile's X and the next
-constexpr uint32_t B_H1 = B_X + 2 * kTM * 32 * 2;  // [128][64], later dH1
-constexpr uint32_t B_H2 = B_H1 + kTM * 64 * 2;     // [128][64], later dH2
+constexpr uint32_t B_H1 = B_X + 2 * kTM * 32 * 2;  // [128][64]
+constexpr uint32_t B_H2 = B_H1 + kTM * 64 * 2;     // [128][64], later dH1
 constexpr uint32_t B_O = B_H2 + kTM * 64 * 2;      // [128][16]
-constexpr uint32_t B_H4 = B_O + kTM * 16 * 2;      // [128][64], later dH4
+constexpr uint32_t B_H4 = B_O + kTM * 16 * 2;      // [128][64], later dH2
 constexpr uint32_t B_DZ = B_H4 + kTM * 64 * 2;     // [128][16], later dO
-constexpr uint32_t B_MISC = B_DZ + kTM * 16 * 2;   // 2 mbarriers + TMEM base
-constexpr uint32_t B_DH4 = B_H4;
-constexpr uint32_t B_DH2 = B_H2;
-constexpr uint32_t B_DH1 = B_H1;
+constexpr uint32_t B_DH4 = B_DZ + kTM * 16 * 2;    // [128][64]
+constexpr uint32_t B_MISC = B_DH4 + kTM * 64 * 2;  // 5 mbarriers + TMEM base
 constexpr uint32_t B_DO = B_DZ;
-constexpr uint32_t kSmemB = B_MISC + 64;         // 90 KB: two CTAs per SM
+constexpr uint32_t B_DH2 = B_H4;
+constexpr uint32_t B_DH1 = B_H2;
+constexpr uint32_t kSmemB = B_MISC + 64;         // 106 KB: two CTAs per SM
 static_assert(2 * (kSmemB + 1024) <= 228 * 1024, "two CTAs per SM");
 
 struct TcBwdArgs {
@@ -91,18 +101,19 @@ __device__ __forceinline__ void issue_dw(uint32_t d_tmem, uint32_t a_saddr, int 
   }
 }
 
+// Epilogue threads stage the five padded weight matrices (16-bit, K-major).
 template <bool BF16>
-__device__ void stage_bwd_weights(uint8_t* sm, const FieldDev& F) {
+__device__ void stage_bwd_weights(uint8_t* sm, const FieldDev& F, int t) {
   const WOff off(F.mlp_in);
   const int in = F.mlp_in;
   if (in == 16)
-    stage<BF16, false, 64, 16>(sm + B_W1, F.weights, off, in, 1);
+    stage<BF16, false, 64, 16>(sm + B_W1, F.weights, off, in, 1, t, kEpi);
   else
-    stage<BF16, false, 64, 32>(sm + B_W1, F.weights, off, in, 1);
-  stage<BF16, false, 64, 64>(sm + B_W2, F.weights, off, in, 2);
-  stage<BF16, false, 16, 64>(sm + B_W3, F.weights, off, in, 3);
-  stage<BF16, false, 64, 16>(sm + B_W4, F.weights, off, in, 4);
-  stage<BF16, false, 16, 64>(sm + B_W5, F.weights, off, in, 5);
+    stage<BF16, false, 64, 32>(sm + B_W1, F.weights, off, in, 1, t, kEpi);
+  stage<BF16, false, 64, 64>(sm + B_W2, F.weights, off, in, 2, t, kEpi);
+  stage<BF16, false, 16, 64>(sm + B_W3, F.weights, off, in, 3, t, kEpi);
+  stage<BF16, false, 64, 16>(sm + B_W4, F.weights, off, in, 4, t, kEpi);
+  stage<BF16, false, 16, 64>(sm + B_W5, F.weights, off, in, 5, t, kEpi);
 }
 
 // One thread: adjoint-chain MMA D (128 x N) = dY (smem, 128 x K, K-major) * W, with W the
@@ -161,230 +172,268 @@ __device__ __forceinline__ int64_t next_tile(const TcBwdArgs& A, int64_t tile, i
   return n_tiles;
 }
 
-// One thread: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each).
+// One warp: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each), one
+// per lane 0..15 after lane 0 has announced their bytes on the barrier.
 __device__ __forceinline__ void load_x(const TcBwdArgs& A, int64_t tile, uint32_t dst, uint32_t bar) {
+  const int lane = threadIdx.x & 31;
   const uint32_t group = (uint32_t)A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)].mlp_in * 16;
-  tc::mbar_expect_tx(bar, 16 * group);
-  const uint8_t* src = static_cast<const uint8_t*>(A.feat);
-  for (int g = 0; g < 16; ++g) tc::bulk_g2s(dst + g * group, src + feat16_group_offset(A.ld, tile, g), group, bar);
+  if (lane == 0) tc::mbar_expect_tx(bar, 16 * group);
+  __syncwarp();
+  if (lane < 16)
+    tc::bulk_g2s(dst + lane * group, static_cast<const uint8_t*>(A.feat) + feat16_group_offset(A.ld, tile, lane),
+                 group, bar);
 }
 
-// This thread's dL/do_0 and dL/dz_rgb of tile `tile` (zero for padding), scaled by in_scale.
-__device__ __forceinline__ void load_dout(const TcBwdArgs& A, int64_t tile, int64_t S, int t, float (&d)[4]) {
+// This thread's raw dL/do_0, dL/dz_rgb and padding marker of tile `tile` (slot < S: view
+// ranges are whole tiles).  No load depends on another, so all stay in flight under the
+// chain; padding slots (marker < 0) are zeroed where the values are used.
+__device__ __forceinline__ void load_dout(const TcBwdArgs& A, int64_t tile, int t, float (&d)[4], int& ray) {
   const int64_t s = tile * kTM + t;
-  const bool live = s < S && (!A.s_ray || A.s_ray[s] >= 0);
+  ray = A.s_ray ? A.s_ray[s] : 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) d[i] = live ? A.dout[(int64_t)i * A.ld + s] * A.in_scale : 0.0f;
+  for (int i = 0; i < 4; ++i) d[i] = A.dout[(int64_t)i * A.ld + s];
+}
+
+// Epilogue thread: this thread's writes to MMA operands (shared memory) and reads of the
+// accumulator (tensor memory) are done; count it in the issuer's "operands ready" barrier.
+__device__ __forceinline__ void epi_arrive(uint32_t bar) {
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_constant__ TcBwdArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
-  const int t = threadIdx.x, warp = t >> 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + B_MISC + 16);
-  const uint32_t mbar = tc::smem_u32(sm + B_MISC);      // MMA completion
-  const uint32_t xbar = tc::smem_u32(sm + B_MISC + 8);  // X copies landed
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + B_MISC + 40);
+  const uint32_t acc_bar = tc::smem_u32(sm + B_MISC);        // chain accumulator ready (commit)
+  const uint32_t opr_bar = tc::smem_u32(sm + B_MISC + 8);    // operands ready (128 epilogue arrivals)
+  const uint32_t x_bar = tc::smem_u32(sm + B_MISC + 16);     // X copies landed
+  const uint32_t flush_bar = tc::smem_u32(sm + B_MISC + 24); // every MMA retired: dW may be read
+  const uint32_t drain_bar = tc::smem_u32(sm + B_MISC + 32); // every MMA retired (exit)
   const uint32_t sb = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemColsB);
   if (t == 0) {
-    tc::mbar_init(mbar, 1);
-    tc::mbar_init(xbar, 1);
+    tc::mbar_init(acc_bar, 1);
+    tc::mbar_init(opr_bar, kEpi);
+    tc::mbar_init(x_bar, 1);
+    tc::mbar_init(flush_bar, 1);
+    tc::mbar_init(drain_bar, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t row_t = tmem + ((uint32_t)(warp * 32) << 16);
   const int kind = BF16 ? kMlpBF16 : kMlpF16;
-
   const int64_t S = (int64_t)A.view_base[A.n_views];
   const int64_t n_tiles = (S + kTM - 1) / kTM;
-  int cur = -1;            // view whose field's weights are staged
-  bool dw_live = false;    // weight-gradient accumulators hold data
-  uint32_t phase = 0, xphase = 0, xbuf = 0;
-  bool ok = true, mma_pending = false, x_pending = false;
+  const int64_t first = next_tile(A, blockIdx.x, n_tiles, kind);
+  bool ok = true;
 
-  int64_t tile = next_tile(A, blockIdx.x, n_tiles, kind);
-  float dnext[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (tile < n_tiles) {
-    if (t == 0) load_x(A, tile, sb + B_X, xbar);
-    x_pending = true;
-    load_dout(A, tile, S, t, dnext);
-  }
-
-  // wait for the MMAs committed last; all threads, bounded
-#define INVR_CHAIN_WAIT()                                   \
-  mma_pending = true;                                       \
-  ok = tc::mbar_wait(mbar, phase, A.wait_limit);            \
-  if (!__syncthreads_and(ok)) { ok = false; break; }        \
-  phase ^= 1u;                                              \
-  mma_pending = false;                                      \
+  if (warp == 4) {
+    // ================================================================ issuer warp
+    uint32_t opr_ph = 0, acc_ph = 0, x_ph = 0, xbuf = 0;
+    bool x_pending = false, dw_live = false;
+    int cur = -1;
+    int64_t tile = first;
+    if (tile < n_tiles) {
+      load_x(A, tile, sb + B_X, x_bar);
+      x_pending = true;
+    }
+    // wait for the epilogue's next "operands ready", then order the MMAs after it
+#define INVR_OPR_WAIT()                                   \
+  if (!(ok = tc::mbar_wait(opr_bar, opr_ph, A.wait_limit))) break; \
+  opr_ph ^= 1u;                                           \
   tc::fence_after_sync();
-
-  while (tile < n_tiles) {
-    const int64_t s0 = tile * kTM;
-    const int v = view_of_slot(A.view_base, A.n_views, s0);
-    const FieldDev& F = A.f[v];
-    const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
-    if (cur < 0 || F.weights != A.f[cur].weights) {
-      if (dw_live) {
-        if (t == 0) tc::commit_to(mbar);
-        INVR_CHAIN_WAIT();
-        flush_dw(tmem, A.f[cur], A.out_scale);
-        tc::fence_before_sync();
-        __syncthreads();
+    // commit the chain MMAs issued so far to the epilogue's barrier
+#define INVR_ACC_COMMIT()                  \
+  if (lane == 0) tc::commit_to(acc_bar);   \
+  acc_ph ^= 1u;
+    while (tile < n_tiles) {
+      const int v = view_of_slot(A.view_base, A.n_views, tile * kTM);
+      const FieldDev& F = A.f[v];
+      const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
+      if (cur >= 0 && F.weights != A.f[cur].weights && dw_live) {
+        if (lane == 0) tc::commit_to(flush_bar);  // the epilogue reads the old field's dW out
         dw_live = false;
       }
-      stage_bwd_weights<BF16>(sm, F);
       cur = v;
+      const int in = F.mlp_in;
+      const uint32_t bx = B_X + xbuf * (kTM * 32 * 2);
+      // ---- S1 recompute H1 (needs: dZ rows, the previous tile's last TMEM read, weights)
+      INVR_OPR_WAIT();
+      if (!(ok = tc::mbar_wait(x_bar, x_ph, A.wait_limit))) break;
+      x_ph ^= 1u;
+      x_pending = false;
+      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + bx, sb + B_W1, in, 64, BF16);
+      INVR_ACC_COMMIT();
+      // once S1 retires, so have the previous tile's weight-gradient MMAs (they read the
+      // other X buffer): the next tile's X may land there
+      if (nxt < n_tiles) {
+        if (!(ok = tc::mbar_wait(acc_bar, acc_ph ^ 1u, A.wait_limit))) break;
+        load_x(A, nxt, sb + B_X + (xbuf ^ 1u) * (kTM * 32 * 2), x_bar);
+        x_pending = true;
+      }
+      // ---- S2 H2, S3 O, S4 H4
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + B_H1, sb + B_W2, 64, 64, BF16);
+      INVR_ACC_COMMIT();
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + B_H2, sb + B_W3, 64, 16, BF16);
+      INVR_ACC_COMMIT();
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + B_O, sb + B_W4, 16, 64, BF16);
+      INVR_ACC_COMMIT();
+      // ---- S5 dH4 = (dZ W5p) [H4 > 0];  dW5p^T += H4^T dZ
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DZ, sb + B_W5, 16, 64, BF16);
+      INVR_ACC_COMMIT();
+      if (lane == 0) issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
+      // ---- S6 dO = dH4 W4p;  dW4p += dH4^T O
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH4, sb + B_W4, 64, 16, BF16);
+      INVR_ACC_COMMIT();
+      if (lane == 0) issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
+      // ---- S7 dH2 = (dO W3) [H2 > 0];  dW3^T += H2^T dO
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DO, sb + B_W3, 16, 64, BF16);
+      INVR_ACC_COMMIT();
+      if (lane == 0) issue_dw(tmem + C_DW3T, sb + B_H2, 64, sb + B_DO, 16, 16, dw_live, BF16);
+      // ---- S8 dH1 = (dH2 W2) [H1 > 0];  dW2 += dH2^T H1
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH2, sb + B_W2, 64, 64, BF16);
+      INVR_ACC_COMMIT();
+      if (lane == 0) issue_dw(tmem + C_DW2, sb + B_DH2, 64, sb + B_H1, 64, 64, dw_live, BF16);
+      // ---- S9 dX = dH1 W1;  dW1 += dH1^T X
+      INVR_OPR_WAIT();
+      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH1, sb + B_W1, 64, in, BF16);
+      INVR_ACC_COMMIT();
+      if (lane == 0) issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + bx, in, in, dw_live, BF16);
+      dw_live = true;
+      __syncwarp();
+      xbuf ^= 1u;
+      tile = nxt;
     }
-    const int in = F.mlp_in;
-    const int valid = (int)(S - s0 < kTM ? S - s0 : kTM);
-    const uint32_t bx = B_X + xbuf * (kTM * 32 * 2);
-    // ---- dZ row (dL/dz for rgb; zero for the padded outputs) and dL/do_0 of this tile
-    const float do0 = dnext[0];
-    {
-      float dz[16];
+#undef INVR_OPR_WAIT
+#undef INVR_ACC_COMMIT
+    if (ok && dw_live && lane == 0) tc::commit_to(flush_bar);  // the last field's dW
+    if (!ok && lane == 0) atomicOr(A.status, kStatusTimeout);
+    // retire every MMA and copy of this CTA (bounded) before the tensor memory is freed
+    if (lane == 0) tc::commit_to(drain_bar);
+    tc::mbar_wait(drain_bar, 0, kWaitLimit);
+    if (x_pending) tc::mbar_wait(x_bar, x_ph, kWaitLimit);
+  } else {
+    // ================================================================ epilogue warps
+    const uint32_t row_t = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t acc_ph = 0, fl_ph = 0;
+    bool dw_live = false;
+    int cur = -1;
+    int64_t tile = first;
+    float dnext[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int ray_next = -1;
+    if (tile < n_tiles) load_dout(A, tile, t, dnext, ray_next);
+#define INVR_ACC_WAIT()                                   \
+  if (!(ok = tc::mbar_wait(acc_bar, acc_ph, A.wait_limit))) break; \
+  acc_ph ^= 1u;                                           \
+  tc::fence_after_sync();
+    while (tile < n_tiles) {
+      const int64_t s0 = tile * kTM;
+      const int v = view_of_slot(A.view_base, A.n_views, s0);
+      const FieldDev& F = A.f[v];
+      const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
+      if (cur < 0 || F.weights != A.f[cur].weights) {
+        if (dw_live) {
+          if (!(ok = tc::mbar_wait(flush_bar, fl_ph, A.wait_limit))) break;
+          fl_ph ^= 1u;
+          tc::fence_after_sync();
+          flush_dw(tmem, A.f[cur], A.out_scale);
+          dw_live = false;
+        }
+        stage_bwd_weights<BF16>(sm, F, t);  // every MMA has retired (or none was issued)
+        cur = v;
+      }
+      const int in = F.mlp_in;
+      const int valid = (int)(S - s0 < kTM ? S - s0 : kTM);
+      // ---- dZ row (dL/dz for rgb; zero for the padded outputs) and dL/do_0 of this tile
+      const bool live = t < valid && ray_next >= 0;
+      const float do0 = live ? dnext[0] * A.in_scale : 0.0f;
+      {
+        float dz[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) dz[i] = i < 3 ? dnext[1 + i] : 0.0f;
-      row16_out<BF16>(dz, sm + B_DZ, t);
-    }
-    operands_ready();
-    ok = tc::mbar_wait(xbar, xphase, A.wait_limit);
-    if (!__syncthreads_and(ok)) { ok = false; break; }
-    xphase ^= 1u;
-    x_pending = false;
-    // the next tile's X (into the other buffer) and dL/d(outputs) arrive under this chain
-    if (nxt < n_tiles) {
-      if (t == 0) load_x(A, nxt, sb + B_X + (xbuf ^ 1u) * (kTM * 32 * 2), xbar);
-      x_pending = true;
-      load_dout(A, nxt, S, t, dnext);
-    }
-    // ---- recompute: H1
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + bx, sb + B_W1, in, 64, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H1, nullptr, t);
-    operands_ready();
-    // ---- H2
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_H1, sb + B_W2, 64, 64, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H2, nullptr, t);
-    operands_ready();
-    // ---- O = (0, o_1..o_15)
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_H2, sb + B_W3, 64, 16, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    {
-      float o[16];
-      tc::tmem_ld16(row_t + C_CHAIN, o);
-      o[0] = 0.0f;
-      row16_out<BF16>(o, sm + B_O, t);
-    }
-    operands_ready();
-    // ---- H4
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_chain(tmem + C_CHAIN, sb + B_O, sb + B_W4, 16, 64, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H4, nullptr, t);
-    operands_ready();
-    // ---- dH4 = (dZ W5p) * [H4 > 0] (over H4);  dW5p^T += H4^T dZ
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_adjoint(tmem + C_CHAIN, sb + B_DZ, sb + B_W5, 16, 64, BF16);
-      issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH4, sm + B_H4, t);
-    operands_ready();
-    // ---- dO = dH4 W4p (o_0 slot carries dL/do_0; over dZ);  dW4p += dH4^T O
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_adjoint(tmem + C_CHAIN, sb + B_DH4, sb + B_W4, 64, 16, BF16);
-      issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    {
-      float d[16];
-      tc::tmem_ld16(row_t + C_CHAIN, d);
-      d[0] = do0;
-      row16_out<BF16>(d, sm + B_DO, t);
-    }
-    operands_ready();
-    // ---- dH2 = (dO W3) * [H2 > 0] (over H2);  dW3^T += H2^T dO
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_adjoint(tmem + C_CHAIN, sb + B_DO, sb + B_W3, 16, 64, BF16);
-      issue_dw(tmem + C_DW3T, sb + B_H2, 64, sb + B_DO, 16, 16, dw_live, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH2, sm + B_H2, t);
-    operands_ready();
-    // ---- dH1 = (dH2 W2) * [H1 > 0] (over H1);  dW2 += dH2^T H1
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_adjoint(tmem + C_CHAIN, sb + B_DH2, sb + B_W2, 64, 64, BF16);
-      issue_dw(tmem + C_DW2, sb + B_DH2, 64, sb + B_H1, 64, 64, dw_live, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH1, sm + B_H1, t);
-    operands_ready();
-    // ---- dX = dH1 W1;  dW1 += dH1^T X
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_adjoint(tmem + C_CHAIN, sb + B_DH1, sb + B_W1, 64, in, BF16);
-      issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + bx, in, in, dw_live, BF16);
-      tc::commit_to(mbar);
-    }
-    INVR_CHAIN_WAIT();
-    dw_live = true;
-    if (in == 32) {
-      float d[32];
-      tc::tmem_ld32(row_t + C_CHAIN, d);
-      if (t < valid)
+        for (int i = 0; i < 16; ++i) dz[i] = (i < 3 && live) ? dnext[1 + i] * A.in_scale : 0.0f;
+        row16_out<BF16>(dz, sm + B_DZ, t);
+      }
+      epi_arrive(opr_bar);
+      // ---- S1: H1
+      INVR_ACC_WAIT();
+      if (nxt < n_tiles) load_dout(A, nxt, t, dnext, ray_next);
+      row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H1, nullptr, t);
+      epi_arrive(opr_bar);
+      // ---- S2: H2
+      INVR_ACC_WAIT();
+      row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H2, nullptr, t);
+      epi_arrive(opr_bar);
+      // ---- S3: O = (0, o_1..o_15)
+      INVR_ACC_WAIT();
+      {
+        float o[16];
+        tc::tmem_ld16(row_t + C_CHAIN, o);
+        o[0] = 0.0f;
+        row16_out<BF16>(o, sm + B_O, t);
+      }
+      epi_arrive(opr_bar);
+      // ---- S4: H4
+      INVR_ACC_WAIT();
+      row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H4, nullptr, t);
+      epi_arrive(opr_bar);
+      // ---- S5: dH4
+      INVR_ACC_WAIT();
+      row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH4, sm + B_H4, t);
+      epi_arrive(opr_bar);
+      // ---- S6: dO (o_0 slot carries dL/do_0), over dZ
+      INVR_ACC_WAIT();
+      {
+        float d[16];
+        tc::tmem_ld16(row_t + C_CHAIN, d);
+        d[0] = do0;
+        row16_out<BF16>(d, sm + B_DO, t);
+      }
+      epi_arrive(opr_bar);
+      // ---- S7: dH2, over H4
+      INVR_ACC_WAIT();
+      row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH2, sm + B_H2, t);
+      epi_arrive(opr_bar);
+      // ---- S8: dH1, over H2
+      INVR_ACC_WAIT();
+      row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH1, sm + B_H1, t);
+      epi_arrive(opr_bar);
+      // ---- S9: dX -> dL/dfeat (its TMEM read is covered by the next tile's first arrival)
+      INVR_ACC_WAIT();
+      if (in == 32) {
+        float d[32];
+        tc::tmem_ld32(row_t + C_CHAIN, d);
+        if (t < valid)
 #pragma unroll
-        for (int j = 0; j < 32; ++j) A.dfeat[(int64_t)j * A.ld + s0 + t] = d[j] * A.out_scale;
-    } else {
-      float d[16];
-      tc::tmem_ld16(row_t + C_CHAIN, d);
-      if (t < valid)
+          for (int j = 0; j < 32; ++j) A.dfeat[(int64_t)j * A.ld + s0 + t] = d[j] * A.out_scale;
+      } else {
+        float d[16];
+        tc::tmem_ld16(row_t + C_CHAIN, d);
+        if (t < valid)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) A.dfeat[(int64_t)j * A.ld + s0 + t] = d[j] * A.out_scale;
+          for (int j = 0; j < 16; ++j) A.dfeat[(int64_t)j * A.ld + s0 + t] = d[j] * A.out_scale;
+      }
+      dw_live = true;
+      tile = nxt;
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    xbuf ^= 1u;
-    tile = nxt;
-  }
-#undef INVR_CHAIN_WAIT
-  if (ok && dw_live) {
-    tc::fence_after_sync();
-    flush_dw(tmem, A.f[cur], A.out_scale);  // every MMA completed at the last chain wait
-  }
-  if (!ok) {
-    // a wait gave up: record it, then let this CTA's MMAs and copies in flight finish
-    // (bounded) before the tensor memory and shared memory they write are released
-    if (t == 0) atomicOr(A.status, kStatusTimeout);
-    if (mma_pending) tc::mbar_wait(mbar, phase, kWaitLimit);
-    if (x_pending) tc::mbar_wait(xbar, xphase, kWaitLimit);
+#undef INVR_ACC_WAIT
+    if (ok && dw_live) {
+      ok = tc::mbar_wait(flush_bar, fl_ph, A.wait_limit);
+      tc::fence_after_sync();
+      if (ok) flush_dw(tmem, A.f[cur], A.out_scale);
+    }
+    if (!ok) atomicOr(A.status, kStatusTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -39,10 +39,11 @@ __device__ __forceinline__ float padded_weight(const float* __restrict__ W, cons
 
 // Stage padded layer `layer` ([OUT][IN]) as a 16-bit K-major operand with N rows and K
 // columns: the matrix itself (N = OUT, K = IN) or, if TRANS, its transpose (N = IN, K = OUT).
+// Threads tid = 0..nthr-1 share the work.
 template <bool BF16, bool TRANS, int N, int K>
 __device__ __forceinline__ void stage(uint8_t* dst, const float* __restrict__ W, const WOff& off, int in,
-                                      int layer) {
-  for (int e = threadIdx.x; e < N * K / 2; e += blockDim.x) {
+                                      int layer, int tid, int nthr) {
+  for (int e = tid; e < N * K / 2; e += nthr) {
     const int n = (2 * e) / K, k = (2 * e) % K;
     const float a = TRANS ? padded_weight(W, off, in, layer, k, n) : padded_weight(W, off, in, layer, n, k);
     const float b =
