@@ -259,6 +259,13 @@ __host__ __device__ constexpr size_t feat16_group_offset(int64_t S_cap, int64_t 
   return (size_t)g * 4 * (size_t)S_cap + (size_t)tile * 512;
 }
 
+// TMA tensor map over the 16-bit feature tiles of a buffer with S_cap slots for K = in
+// features: 3-D, innermost the in * 16 bytes of a row group (as 16-bit elements), then the
+// tile (stride 512 B), then the 16 row groups (stride 4 * S_cap B); a box {in * 8, 1, 16} at
+// (0, T, 0) is tile T in the MMA's K-major layout.  `map` points to a CUtensorMap.  Returns
+// false if the driver's encoder is unavailable or rejects the map.
+bool encode_feat16_map(void* map, const void* feat, int64_t S_cap, int in);
+
 // Byte offset of feature k of sample s (k even: the pair k, k+1 is one 32-bit word).
 __host__ __device__ constexpr size_t feat16_offset(int64_t S_cap, int64_t s, int k) {
   return feat16_group_offset(S_cap, s >> 7, (int)((s & 127) >> 3)) + (size_t)((k >> 3) * 128) +

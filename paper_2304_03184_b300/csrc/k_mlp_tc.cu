@@ -14,13 +14,15 @@
 // accumulator and commits them to an mbarrier; all threads wait, read their row from tensor
 // memory (one tcgen05.ld of 64 columns), apply the activation in FP32 and write the next
 // operand row in the K-major layout.  The encoder writes the features as 16-bit operand
-// tiles, so a tile's X arrives by 16 bulk copies of one row group each; the copies of the
-// CTA's next tile are issued as soon as layer 3 has read P, and land while layers 4 and 5
+// tiles, so a tile's X arrives by one TMA copy (a 3-D box of its 16 row groups); the copy of
+// the CTA's next tile is issued as soon as layer 3 has read P, and land while layers 4 and 5
 // run.  Weights (padded: W4p gets a zero column for o_0, W5p 13 zero rows) are converted
 // to 16 bit and staged in shared memory once per field.  50 KB of shared memory and 64
 // tensor-memory columns per CTA: four CTAs per SM overlap their chains.  Every mbarrier
 // wait is bounded; a timeout sets the status word, and the CTA waits (bounded) for its
 // own copies and MMAs in flight, frees its tensor memory and exits.
+#include <cuda.h>
+
 #include "invr_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -48,6 +50,7 @@ static_assert(kCtasPerSm * (kSmemTC + 1024) <= 228 * 1024, "four CTAs per SM");
 static_assert(kCtasPerSm * kTmemCols <= 512, "tensor memory of four CTAs");
 
 struct TcArgs {
+  CUtensorMap xmap[2];      // TMA maps of the 16-bit feature tiles for in = 16, 32 (plan path)
   const void* feat;         // 16-bit operand tiles (feat16_offset), or FP32 [in][ld] (points)
   float* out;               // [4][ld]
   const int32_t* view_base; // per-view tile-aligned sample ranges (device) or null
@@ -152,19 +155,16 @@ __device__ __forceinline__ int64_t next_tile(const TcArgs& A, int64_t tile, int6
   return n_tiles;
 }
 
-// One warp: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each), one
-// per lane 0..15 after lane 0 has announced their bytes on the barrier.
+// One warp (lane 0 works): tile `tile`'s X [128 x in] as one TMA box of its 16 row groups.
 __device__ __forceinline__ void load_x(const TcArgs& A, int64_t tile, int in, uint32_t dst, uint32_t bar) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t group = (uint32_t)in * 16;
-  if (lane == 0) tc::mbar_expect_tx(bar, 16 * group);
+  if ((threadIdx.x & 31) == 0) {
+    tc::mbar_expect_tx(bar, 16u * 16u * (uint32_t)in);
+    tc::tma_load_3d(dst, &A.xmap[in == 32 ? 1 : 0], 0, (int)tile, 0, bar);
+  }
   __syncwarp();
-  if (lane < 16)
-    tc::bulk_g2s(dst + lane * group, static_cast<const uint8_t*>(A.feat) + feat16_group_offset(A.ld, tile, lane),
-                 group, bar);
 }
 
-// TILES: the plan's 16-bit operand tiles (bulk copies, prefetched); else FP32 feature-major
+// TILES: the plan's 16-bit operand tiles (one TMA copy each, prefetched); else FP32 feature-major
 // points converted by the threads.
 template <bool BF16, bool TILES>
 __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __grid_constant__ TcArgs A) {
@@ -359,6 +359,30 @@ cudaError_t launch_tc(const TcArgs& A, int num_sms, cudaStream_t s) {
 
 }  // namespace
 
+bool encode_feat16_map(void* map, const void* feat, int64_t S_cap, int in) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  if (S_cap % kTile != 0 || (in != 16 && in != 32)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)in * 8, (cuuint64_t)(S_cap / kTile), 16};
+  const cuuint64_t strides[2] = {512, (cuuint64_t)S_cap * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)in * 8, 1, 16};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(feat), dims,
+                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool plan_has_kind(const Plan& P, int kind) {
   for (int v = 0; v < P.n_views; ++v)
     if (P.v[v].field.mlp_kind == kind) return true;
@@ -375,6 +399,9 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   A.wait_limit = P.wait_limit;
   A.status = P.status;
   for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
+  if (!encode_feat16_map(&A.xmap[0], P.ws.feat, P.ws.S_cap, 16) ||
+      !encode_feat16_map(&A.xmap[1], P.ws.feat, P.ws.S_cap, 32))
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (plan_has_kind(P, kMlpBF16)) e = launch_tc<true, true>(A, num_sms, s);
   if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) e = launch_tc<false, true>(A, num_sms, s);

@@ -22,8 +22,8 @@
 // commit (tracking every earlier MMA) retires them.  The buffers are assigned so that an
 // epilogue never writes what the current stage's weight-gradient MMAs read: dH4 into its
 // own buffer, dO over dZ, dH2 over H4, dH1 over H2.  The issuer also moves X: the encoder's
-// 16-bit operand tile arrives by 16 bulk copies into one of two buffers, the next tile's
-// copies issued once this tile's first MMA has retired the previous tile's last
+// 16-bit operand tile arrives by one TMA copy into one of two buffers, the next tile's
+// copy issued once this tile's first MMA has retired the previous tile's last
 // weight-gradient MMAs.  Epilogue threads load the next tile's dL/d(outputs) and padding
 // markers into registers under the chain (unconditionally; the padding selection is
 // applied when they are used).  106 KB of shared memory and 160 threads: two CTAs per SM.
@@ -33,6 +33,8 @@
 // FP32 feature-major for the hash scatter.  All waits are bounded: a role that gives up sets
 // the status word and leaves its loop (the other role's waits then give up in turn), and the
 // issuer retires its MMAs and copies (bounded) before the tensor memory is freed.
+#include <cuda.h>
+
 #include "mlp_tc_common.cuh"
 
 namespace invr {
@@ -74,6 +76,7 @@ constexpr uint32_t kSmemB = B_MISC + 64;         // 106 KB: two CTAs per SM
 static_assert(2 * (kSmemB + 1024) <= 228 * 1024, "two CTAs per SM");
 
 struct TcBwdArgs {
+  CUtensorMap xmap[2];      // TMA maps of the 16-bit feature tiles for in = 16, 32
   const void* feat;         // 16-bit operand tiles of the encoding features (feat16_offset)
   const float* dout;        // [4][ld]: dL/do_0, dL/dz_rgb
   float* dfeat;             // [in][ld]
@@ -172,16 +175,15 @@ __device__ __forceinline__ int64_t next_tile(const TcBwdArgs& A, int64_t tile, i
   return n_tiles;
 }
 
-// One warp: the 16 bulk copies of tile `tile`'s X (one row group of 8 samples each), one
-// per lane 0..15 after lane 0 has announced their bytes on the barrier.
+// The issuer warp (lane 0 works): tile `tile`'s X [128 x in] as one TMA box of its 16 row
+// groups.
 __device__ __forceinline__ void load_x(const TcBwdArgs& A, int64_t tile, uint32_t dst, uint32_t bar) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t group = (uint32_t)A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)].mlp_in * 16;
-  if (lane == 0) tc::mbar_expect_tx(bar, 16 * group);
+  if ((threadIdx.x & 31) == 0) {
+    const int in = A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)].mlp_in;
+    tc::mbar_expect_tx(bar, 16u * 16u * (uint32_t)in);
+    tc::tma_load_3d(dst, &A.xmap[in == 32 ? 1 : 0], 0, (int)tile, 0, bar);
+  }
   __syncwarp();
-  if (lane < 16)
-    tc::bulk_g2s(dst + lane * group, static_cast<const uint8_t*>(A.feat) + feat16_group_offset(A.ld, tile, lane),
-                 group, bar);
 }
 
 // This thread's raw dL/do_0, dL/dz_rgb and padding marker of tile `tile` (slot < S: view
@@ -460,6 +462,9 @@ cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   A.wait_limit = P.wait_limit;
   A.status = P.status;
   for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
+  if (!encode_feat16_map(&A.xmap[0], P.ws.feat, P.ws.S_cap, 16) ||
+      !encode_feat16_map(&A.xmap[1], P.ws.feat, P.ws.S_cap, 32))
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (plan_has_kind(P, kMlpBF16)) {
     cudaFuncSetAttribute(k_mlp_bwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB);

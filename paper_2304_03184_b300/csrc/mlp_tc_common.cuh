@@ -63,35 +63,43 @@ __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint32_t a_saddr, u
   }
 }
 
+// Per 16-bit half of w: 0xFFFF where that half, as FP16 or BF16, is positive (sign clear and
+// magnitude nonzero: the magnitude plus 0x7FFF carries into the half's top bit), else 0.
+__device__ __forceinline__ uint32_t positive_halves(uint32_t w) {
+  const uint32_t nonzero = ((w & 0x7FFF7FFFu) + 0x7FFF7FFFu) & 0x80008000u;
+  const uint32_t pos = nonzero & ~w;
+  return (pos >> 15) * 0xFFFFu;
+}
+
 // Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0) (or v
-// where the mask row is positive, if MASK) as row t of a K = 64 16-bit operand.  Each
-// 16-byte chunk of the mask row is read before the same chunk of dst is written, so dst may
-// be the mask buffer itself (the delta replaces the activation it was masked by).
+// where the mask row is positive, if MASK) as row t of a K = 64 16-bit operand.  A masked
+// value is rounded first and its 16 bits cleared where the mask is not positive (the same
+// bits as rounding 0).  The whole mask row is read before any chunk of dst is written, so
+// dst may also be the mask buffer itself.
 template <bool BF16, bool MASK>
 __device__ __forceinline__ void row64_out(uint32_t taddr, uint8_t* dst, const uint8_t* mask, int t) {
+  uint4 m[8];
+  if constexpr (MASK) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) m[c] = *reinterpret_cast<const uint4*>(mask + tc::kmajor_offset(t, 8 * c, 64));
+  }
   float v[64];
   tc::tmem_ld64(taddr, v);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    float* x = v + 8 * c;
-    if constexpr (MASK) {
-      const uint4 m = *reinterpret_cast<const uint4*>(mask + tc::kmajor_offset(t, 8 * c, 64));
-      const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        // a 16-bit value is positive iff its sign bit is clear and it is not +0
-        if ((mw[i] & 0x8000u) || !(mw[i] & 0x7FFFu)) x[2 * i] = 0.0f;
-        if ((mw[i] & 0x80000000u) || !(mw[i] & 0x7FFF0000u)) x[2 * i + 1] = 0.0f;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = fmaxf(x[i], 0.0f);
-    }
+    const float* x = v + 8 * c;
     uint4 q;
-    q.x = tc::pack2<BF16>(x[0], x[1]);
-    q.y = tc::pack2<BF16>(x[2], x[3]);
-    q.z = tc::pack2<BF16>(x[4], x[5]);
-    q.w = tc::pack2<BF16>(x[6], x[7]);
+    if constexpr (MASK) {
+      q.x = tc::pack2<BF16>(x[0], x[1]) & positive_halves(m[c].x);
+      q.y = tc::pack2<BF16>(x[2], x[3]) & positive_halves(m[c].y);
+      q.z = tc::pack2<BF16>(x[4], x[5]) & positive_halves(m[c].z);
+      q.w = tc::pack2<BF16>(x[6], x[7]) & positive_halves(m[c].w);
+    } else {
+      q.x = tc::pack2<BF16>(fmaxf(x[0], 0.0f), fmaxf(x[1], 0.0f));
+      q.y = tc::pack2<BF16>(fmaxf(x[2], 0.0f), fmaxf(x[3], 0.0f));
+      q.z = tc::pack2<BF16>(fmaxf(x[4], 0.0f), fmaxf(x[5], 0.0f));
+      q.w = tc::pack2<BF16>(fmaxf(x[6], 0.0f), fmaxf(x[7], 0.0f));
+    }
     *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
   }
 }

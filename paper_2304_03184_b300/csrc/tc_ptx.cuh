@@ -162,6 +162,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void* src, ui
       : "memory");
 }
 
+// Tiled TMA load of a 3-D box (coordinates in elements, innermost first) into shared
+// memory, completion counted in bytes on the mbarrier; tmap is the address of a
+// __grid_constant__ CUtensorMap.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst_saddr, const void* tmap, int c0, int c1, int c2,
+                                            uint32_t mbar_saddr) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst_saddr),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(mbar_saddr)
+      : "memory");
+}
+
 // Pack two floats into one 32-bit word of two 16-bit values (low = a).
 template <bool BF16>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
