@@ -247,6 +247,13 @@ __device__ __forceinline__ int view_of_slot(const int32_t* view_base, int n_view
   return v;
 }
 
+// View cursor for slots visited in increasing order (a CTA's tiles): advances v to the view
+// of slot s, reading the view bases from a copy in shared memory.
+__device__ __forceinline__ int advance_view(const int32_t* vb, int n_views, int64_t s, int v) {
+  while (v + 1 < n_views && s >= (int64_t)vb[v + 1]) ++v;
+  return v;
+}
+
 __device__ __forceinline__ void flag_status(unsigned* status, unsigned bit) { atomicOr(status, bit); }
 
 // 16-bit encoding features of a tensor-core field.  Each 128-sample tile T is the first

@@ -146,11 +146,12 @@ __device__ __forceinline__ void operands_ready() {
 }
 
 // The CTA's tiles: from `tile` on in steps of gridDim.x, the first whose view has this
-// kernel's MLP kind (uniform over the CTA), or n_tiles.
-__device__ __forceinline__ int64_t next_tile(const TcArgs& A, int64_t tile, int64_t n_tiles, int kind) {
+// kernel's MLP kind (uniform over the CTA), or n_tiles; v follows the view (cursor).
+__device__ __forceinline__ int64_t next_tile(const TcArgs& A, const int32_t* vb, int64_t tile, int64_t n_tiles,
+                                             int kind, int& v) {
   for (; tile < n_tiles; tile += gridDim.x) {
-    const FieldDev& F = A.f[A.view_base ? view_of_slot(A.view_base, A.n_views, tile * kTM) : 0];
-    if (F.mlp_kind == kind) return tile;
+    v = advance_view(vb, A.n_views, tile * kTM, v);
+    if (A.f[v].mlp_kind == kind) return tile;
   }
   return n_tiles;
 }
@@ -169,8 +170,10 @@ __device__ __forceinline__ void load_x(const TcArgs& A, int64_t tile, int in, ui
 template <bool BF16, bool TILES>
 __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __grid_constant__ TcArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
   if (A.view_base && (int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5;
+  if (t <= A.n_views) vb[t] = A.view_base ? A.view_base[t] : 0;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
   const uint32_t mbar = tc::smem_u32(sm + OFF_MISC);      // MMA completion
   const uint32_t xbar = tc::smem_u32(sm + OFF_MISC + 8);  // X copies landed
@@ -194,17 +197,15 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
   bool ok = true;
   bool mma_pending = false, x_pending = false;
 
-  int64_t tile = next_tile(A, blockIdx.x, n_tiles, kind);
-  if (TILES && warp == 0 && tile < n_tiles) {
-    const FieldDev& F0 = A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)];
-    load_x(A, tile, F0.mlp_in, sbase + OFF_P, xbar);
-  }
+  int vn = 0;  // view of the next tile to process
+  int64_t tile = next_tile(A, vb, blockIdx.x, n_tiles, kind, vn);
+  if (TILES && warp == 0 && tile < n_tiles) load_x(A, tile, A.f[vn].mlp_in, sbase + OFF_P, xbar);
   x_pending = TILES && tile < n_tiles;
 
   while (tile < n_tiles) {
     const int64_t s0 = tile * kTM;
-    const FieldDev& F = A.f[A.view_base ? view_of_slot(A.view_base, A.n_views, s0) : 0];
-    const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
+    const FieldDev& F = A.f[vn];
+    const int64_t nxt = next_tile(A, vb, tile + gridDim.x, n_tiles, kind, vn);
     if (F.weights != loaded) {
       __syncthreads();
       stage_weights<BF16>(sm, F);
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
     tc::fence_after_sync();
     // P (H2) has been read: the next tile's X may land there now
     if (TILES && nxt < n_tiles) {
-      if (warp == 0) load_x(A, nxt, A.f[view_of_slot(A.view_base, A.n_views, nxt * kTM)].mlp_in, sbase + OFF_P, xbar);
+      if (warp == 0) load_x(A, nxt, A.f[vn].mlp_in, sbase + OFF_P, xbar);
       x_pending = true;
     }
     float o[16];

@@ -168,18 +168,20 @@ __device__ void flush_dw(uint32_t tmem, const FieldDev& F, float scale) {
 }
 
 // The CTA's tiles: from `tile` on in steps of gridDim.x, the first whose view has this
-// kernel's MLP kind (uniform over the CTA), or n_tiles.
-__device__ __forceinline__ int64_t next_tile(const TcBwdArgs& A, int64_t tile, int64_t n_tiles, int kind) {
-  for (; tile < n_tiles; tile += gridDim.x)
-    if (A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)].mlp_kind == kind) return tile;
+// kernel's MLP kind (uniform over the CTA), or n_tiles; v follows the view (cursor).
+__device__ __forceinline__ int64_t next_tile(const TcBwdArgs& A, const int32_t* vb, int64_t tile, int64_t n_tiles,
+                                             int kind, int& v) {
+  for (; tile < n_tiles; tile += gridDim.x) {
+    v = advance_view(vb, A.n_views, tile * kTM, v);
+    if (A.f[v].mlp_kind == kind) return tile;
+  }
   return n_tiles;
 }
 
 // The issuer warp (lane 0 works): tile `tile`'s X [128 x in] as one TMA box of its 16 row
 // groups.
-__device__ __forceinline__ void load_x(const TcBwdArgs& A, int64_t tile, uint32_t dst, uint32_t bar) {
+__device__ __forceinline__ void load_x(const TcBwdArgs& A, int64_t tile, int in, uint32_t dst, uint32_t bar) {
   if ((threadIdx.x & 31) == 0) {
-    const int in = A.f[view_of_slot(A.view_base, A.n_views, tile * kTM)].mlp_in;
     tc::mbar_expect_tx(bar, 16u * 16u * (uint32_t)in);
     tc::tma_load_3d(dst, &A.xmap[in == 32 ? 1 : 0], 0, (int)tile, 0, bar);
   }
@@ -207,8 +209,10 @@ __device__ __forceinline__ void epi_arrive(uint32_t bar) {
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_constant__ TcBwdArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
   if ((int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  if (t <= A.n_views) vb[t] = A.view_base[t];
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + B_MISC + 40);
   const uint32_t acc_bar = tc::smem_u32(sm + B_MISC);        // chain accumulator ready (commit)
   const uint32_t opr_bar = tc::smem_u32(sm + B_MISC + 8);    // operands ready (128 epilogue arrivals)
@@ -231,7 +235,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
   const int kind = BF16 ? kMlpBF16 : kMlpF16;
   const int64_t S = (int64_t)A.view_base[A.n_views];
   const int64_t n_tiles = (S + kTM - 1) / kTM;
-  const int64_t first = next_tile(A, blockIdx.x, n_tiles, kind);
+  int v_first = 0;
+  const int64_t first = next_tile(A, vb, blockIdx.x, n_tiles, kind, v_first);
   bool ok = true;
 
   if (warp == 4) {
@@ -240,8 +245,9 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     bool x_pending = false, dw_live = false;
     int cur = -1;
     int64_t tile = first;
+    int vn = v_first;  // view of the next tile to process
     if (tile < n_tiles) {
-      load_x(A, tile, sb + B_X, x_bar);
+      load_x(A, tile, A.f[vn].mlp_in, sb + B_X, x_bar);
       x_pending = true;
     }
     // wait for the epilogue's next "operands ready", then order the MMAs after it
@@ -254,9 +260,9 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
   if (lane == 0) tc::commit_to(acc_bar);   \
   acc_ph ^= 1u;
     while (tile < n_tiles) {
-      const int v = view_of_slot(A.view_base, A.n_views, tile * kTM);
+      const int v = vn;
       const FieldDev& F = A.f[v];
-      const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
+      const int64_t nxt = next_tile(A, vb, tile + gridDim.x, n_tiles, kind, vn);
       if (cur >= 0 && F.weights != A.f[cur].weights && dw_live) {
         if (lane == 0) tc::commit_to(flush_bar);  // the epilogue reads the old field's dW out
         dw_live = false;
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       // other X buffer): the next tile's X may land there
       if (nxt < n_tiles) {
         if (!(ok = tc::mbar_wait(acc_bar, acc_ph ^ 1u, A.wait_limit))) break;
-        load_x(A, nxt, sb + B_X + (xbuf ^ 1u) * (kTM * 32 * 2), x_bar);
+        load_x(A, nxt, A.f[vn].mlp_in, sb + B_X + (xbuf ^ 1u) * (kTM * 32 * 2), x_bar);
         x_pending = true;
       }
       // ---- S2 H2, S3 O, S4 H4
@@ -293,11 +299,10 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DZ, sb + B_W5, 16, 64, BF16);
       INVR_ACC_COMMIT();
       if (lane == 0) issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
-      // ---- S6 dO = dH4 W4p;  dW4p += dH4^T O
+      // ---- S6 dO = dH4 W4p  (dW4p += dH4^T O is issued after S9)
       INVR_OPR_WAIT();
       if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH4, sb + B_W4, 64, 16, BF16);
       INVR_ACC_COMMIT();
-      if (lane == 0) issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
       // ---- S7 dH2 = (dO W3) [H2 > 0];  dW3^T += H2^T dO
       INVR_OPR_WAIT();
       if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DO, sb + B_W3, 16, 64, BF16);
@@ -312,7 +317,12 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       INVR_OPR_WAIT();
       if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH1, sb + B_W1, 64, in, BF16);
       INVR_ACC_COMMIT();
-      if (lane == 0) issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + bx, in, in, dw_live, BF16);
+      if (lane == 0) {
+        issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + bx, in, in, dw_live, BF16);
+        // dW4 reads dH4 and O, which stay untouched until the next tile's S3 and S5 epilogues;
+        // issued here, under the dX epilogue, instead of after S6's short one
+        issue_dw(tmem + C_DW4, sb + B_DH4, 64, sb + B_O, 16, 16, dw_live, BF16);
+      }
       dw_live = true;
       __syncwarp();
       xbuf ^= 1u;
@@ -333,6 +343,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     bool dw_live = false;
     int cur = -1;
     int64_t tile = first;
+    int vn = v_first;  // view of the next tile to process
     float dnext[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     int ray_next = -1;
     if (tile < n_tiles) load_dout(A, tile, t, dnext, ray_next);
@@ -342,9 +353,9 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
   tc::fence_after_sync();
     while (tile < n_tiles) {
       const int64_t s0 = tile * kTM;
-      const int v = view_of_slot(A.view_base, A.n_views, s0);
+      const int v = vn;
       const FieldDev& F = A.f[v];
-      const int64_t nxt = next_tile(A, tile + gridDim.x, n_tiles, kind);
+      const int64_t nxt = next_tile(A, vb, tile + gridDim.x, n_tiles, kind, vn);
       if (cur < 0 || F.weights != A.f[cur].weights) {
         if (dw_live) {
           if (!(ok = tc::mbar_wait(flush_bar, fl_ph, A.wait_limit))) break;

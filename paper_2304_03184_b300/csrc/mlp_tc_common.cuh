@@ -63,12 +63,15 @@ __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint32_t a_saddr, u
   }
 }
 
-// Per 16-bit half of w: 0xFFFF where that half, as FP16 or BF16, is positive (sign clear and
-// magnitude nonzero: the magnitude plus 0x7FFF carries into the half's top bit), else 0.
+// Per 16-bit half of a stored ReLU output w (each half +0, -0 or positive): 0xFFFF where the
+// half is positive, else 0 (one packed half-precision compare).
+template <bool BF16>
 __device__ __forceinline__ uint32_t positive_halves(uint32_t w) {
-  const uint32_t nonzero = ((w & 0x7FFF7FFFu) + 0x7FFF7FFFu) & 0x80008000u;
-  const uint32_t pos = nonzero & ~w;
-  return (pos >> 15) * 0xFFFFu;
+  if constexpr (BF16) {
+    return __hgt2_mask(*reinterpret_cast<const __nv_bfloat162*>(&w), __nv_bfloat162(__float2bfloat16(0.0f), __float2bfloat16(0.0f)));
+  } else {
+    return __hgt2_mask(*reinterpret_cast<const __half2*>(&w), __half2(__float2half(0.0f), __float2half(0.0f)));
+  }
 }
 
 // Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0) (or v
@@ -90,10 +93,10 @@ __device__ __forceinline__ void row64_out(uint32_t taddr, uint8_t* dst, const ui
     const float* x = v + 8 * c;
     uint4 q;
     if constexpr (MASK) {
-      q.x = tc::pack2<BF16>(x[0], x[1]) & positive_halves(m[c].x);
-      q.y = tc::pack2<BF16>(x[2], x[3]) & positive_halves(m[c].y);
-      q.z = tc::pack2<BF16>(x[4], x[5]) & positive_halves(m[c].z);
-      q.w = tc::pack2<BF16>(x[6], x[7]) & positive_halves(m[c].w);
+      q.x = tc::pack2<BF16>(x[0], x[1]) & positive_halves<BF16>(m[c].x);
+      q.y = tc::pack2<BF16>(x[2], x[3]) & positive_halves<BF16>(m[c].y);
+      q.z = tc::pack2<BF16>(x[4], x[5]) & positive_halves<BF16>(m[c].z);
+      q.w = tc::pack2<BF16>(x[6], x[7]) & positive_halves<BF16>(m[c].w);
     } else {
       q.x = tc::pack2<BF16>(fmaxf(x[0], 0.0f), fmaxf(x[1], 0.0f));
       q.y = tc::pack2<BF16>(fmaxf(x[2], 0.0f), fmaxf(x[3], 0.0f));
