@@ -216,9 +216,9 @@ def time_train(invr, ctx, tb, steps, warmup, flush, world):
 
 def measure_l2(invr, ctx):
     """L2 ceilings measured on this device by the library's probe kernels: a read stream over
-    a 64 MiB resident buffer (the size of one field's tables), and random float4 / float2
-    loads from it and atomic adds into it (the forms the encoding's gathers and the
-    hash-gradient scatter issue).  Best of 5, CUDA events."""
+    a 64 MiB resident buffer (the size of one field's tables), and random 32-byte / float4 /
+    float2 loads from it and float4 / float2 atomic adds into it (the forms the encoding's
+    gathers and the hash-gradient scatter issue).  Best of 5, CUDA events."""
     import torch
     buf = torch.ones(1 << 24, dtype=torch.float32, device="cuda")        # 64 MiB < 126 MB L2
     sink = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -239,6 +239,7 @@ def measure_l2(invr, ctx):
     res = {"read_gbs": best(lambda: invr.probe_l2_read(ctx, buf, passes, sink), passes * buf.numel() * 4),
            "atomic_v4_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 4, n_ops), n_ops * 16),
            "atomic_v2_gbs": best(lambda: invr.probe_l2_atomic(ctx, buf, 2, n_ops), n_ops * 8),
+           "gather_v8_gbs": best(lambda: invr.probe_l2_gather(ctx, buf, 8, n_ops, sink), n_ops * 32),
            "gather_v4_gbs": best(lambda: invr.probe_l2_gather(ctx, buf, 4, n_ops, sink), n_ops * 16),
            "gather_v2_gbs": best(lambda: invr.probe_l2_gather(ctx, buf, 2, n_ops, sink), n_ops * 8)}
     ctx.sync()

@@ -386,8 +386,9 @@ invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_view* view,
  *  - invr_probe_l2_atomic: n_ops vector float atomic adds of +1.0 per component, width
  *    4 (16-byte float4) or 2 (8-byte float2), at pseudo-random entries of table_dev
  *    (n_floats floats, a multiple of 4, 16-byte aligned).  Payload = n_ops * width * 4 B.
- *  - invr_probe_l2_gather: n_ops loads of width 4 (float4) or 2 (float2) at the same
- *    pseudo-random entries (the encoding's gather); sink_dev as for the read probe.
+ *  - invr_probe_l2_gather: n_ops loads of width 8 (32 bytes; table_dev 32-byte aligned and
+ *    n_floats a multiple of 8), 4 (float4) or 2 (float2) at the same pseudo-random entries
+ *    (the encoding's gathers); sink_dev as for the read probe.
  * Bad sizes or null pointers return INVR_E_ARG. */
 invr_status invr_probe_l2_read(invr_ctx ctx, const float* buf_dev, int64_t n_floats, int passes, float* sink_dev,
                                invr_stream stream);

@@ -607,6 +607,6 @@ def probe_l2_atomic(ctx: Context, table, width: int, n_ops: int):
 
 
 def probe_l2_gather(ctx: Context, table, width: int, n_ops: int, sink):
-    """invr_probe_l2_gather: n_ops float4 (width 4) or float2 (width 2) loads at pseudo-random
-    entries of `table` (a CUDA float32 tensor)."""
+    """invr_probe_l2_gather: n_ops 32-byte (width 8), float4 (width 4) or float2 (width 2) loads
+    at pseudo-random entries of `table` (a CUDA float32 tensor)."""
     _check(lib().invr_probe_l2_gather(ctx.h, _ptr(table), table.numel(), width, n_ops, _ptr(sink), _stream()), ctx.h)

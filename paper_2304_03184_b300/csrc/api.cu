@@ -1294,7 +1294,8 @@ invr_status invr_probe_l2_read(invr_ctx ctx, const float* buf, int64_t n_floats,
 invr_status invr_probe_l2_gather(invr_ctx ctx, const float* table, int64_t n_floats, int width, int64_t n_ops,
                                  float* sink, invr_stream stream) {
   if (!ctx || !table || !sink || n_floats < 4 || n_floats % 4 || n_floats / 2 > 0xFFFFFFFFll ||
-      (width != 2 && width != 4) || n_ops < 0 || (uintptr_t)table % 16)
+      (width != 2 && width != 4 && width != 8) || n_ops < 0 || (uintptr_t)table % 16 ||
+      (width == 8 && (n_floats % 8 || (uintptr_t)table % 32)))
     return fail(ctx, INVR_E_ARG, "bad probe_l2_gather arguments");
   DeviceGuard guard(ctx->device);
   INVR_CUDA(ctx, launch_probe_l2_gather(table, n_floats, width, n_ops, sink, ctx->num_sms,

@@ -2,9 +2,9 @@
 //
 // The hash tables of a 2^19-entry field (64 MiB) stay resident in the 126 MB L2, so the
 // encoding's gathers and the backward's atomic scatter are bound by L2, not HBM.  These
-// two kernels measure that ceiling on the device: a read stream over an L2-resident
-// buffer, and vector atomic adds (the float4 / float2 forms the scatter issues) at
-// pseudo-random entries of an L2-resident table.  Neither is part of the method.
+// kernels measure that ceiling on the device: a read stream over an L2-resident buffer,
+// and loads (32-, 16- and 8-byte) and vector atomic adds (the float4 / float2 forms the
+// scatter issues) at pseudo-random entries of an L2-resident table.  Neither is part of the method.
 #include "invr_internal.cuh"
 
 namespace invr {
@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(256) k_probe_l2_atomic(float* table, uint32_t 
   }
 }
 
-// width 4: float4 loads at random 16-byte-aligned entries; width 2: float2.
+// width 8: 32-byte loads (ld.global.nc.v8.f32) at random 32-byte-aligned entries; width 4:
+// float4 loads at random 16-byte-aligned entries; width 2: float2.
 template <int W>
 __global__ void __launch_bounds__(256) k_probe_l2_gather(const float* __restrict__ table, uint32_t n_vec,
                                                          int64_t n_ops, float* sink) {
@@ -52,7 +53,13 @@ __global__ void __launch_bounds__(256) k_probe_l2_gather(const float* __restrict
   float acc = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_ops; i += stride) {
     const uint32_t e = probe_hash((uint64_t)i) % n_vec;
-    if (W == 4) {
+    if (W == 8) {
+      float r[8];
+      asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+          : "l"(table + 8 * (size_t)e));
+      acc += ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
+    } else if (W == 4) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(table) + e);
       acc += (v.x + v.y) + (v.z + v.w);
     } else {
@@ -66,7 +73,9 @@ __global__ void __launch_bounds__(256) k_probe_l2_gather(const float* __restrict
 cudaError_t launch_probe_l2_gather(const float* table, int64_t n_floats, int width, int64_t n_ops, float* sink,
                                    int num_sms, cudaStream_t s) {
   const int blocks = num_sms * 8;
-  if (width == 4) {
+  if (width == 8) {
+    k_probe_l2_gather<8><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 8), n_ops, sink);
+  } else if (width == 4) {
     k_probe_l2_gather<4><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 4), n_ops, sink);
   } else {
     k_probe_l2_gather<2><<<blocks, 256, 0, s>>>(table, (uint32_t)(n_floats / 2), n_ops, sink);

@@ -147,7 +147,8 @@ def test_device_wait_timeout_reported_and_recovered(env):
 
 def test_l2_probes_do_the_counted_work(env):
     """The L2 ceiling probes do exactly the work their byte counts assume: the atomic probe
-    adds +1 per component n_ops times (sum = n_ops x width), the read probe writes nothing."""
+    adds +1 per component n_ops times (sum = n_ops x width), the read and gather probes write
+    nothing; a 32-byte gather needs a 32-byte-aligned table."""
     invr, _ = env
     import torch
     ctx = invr.Context(0)
@@ -159,10 +160,14 @@ def test_l2_probes_do_the_counted_work(env):
     buf = torch.ones(1 << 20, dtype=torch.float32, device="cuda")
     sink = torch.zeros(1, dtype=torch.float32, device="cuda")
     invr.probe_l2_read(ctx, buf, 3, sink)
+    for width in (8, 4, 2):
+        invr.probe_l2_gather(ctx, buf, width, 3 << 18, sink)
     ctx.sync()
     assert float(sink.item()) == 0.0
     with pytest.raises(invr.InvrError):
         invr.probe_l2_atomic(ctx, buf, 3, 10)
+    with pytest.raises(invr.InvrError):
+        invr.probe_l2_gather(ctx, buf[4:], 8, 10, sink)  # 16-byte but not 32-byte aligned
 
 
 def test_graph_replay_with_deformation_net_tables_and_paper_loss(env):
