@@ -13,7 +13,7 @@
 //   dC/dc_j = T_j alpha_j,   dC/dsigma_j = dt (T_{j+1} c_j - (C - sum_{k<=j} T_k alpha_k c_k))
 // folded with sigma = exp(o_0) and c = sigmoid(z) into dL/do_0 and dL/dz per sample.
 //
-// One thread per ray; bound by the per-sample reads (16 B/sample).
+// One thread per ray; bound by the per-sample reads (16 B/sample), issued 4 samples at a time.
 #include "invr_internal.cuh"
 
 namespace invr {
@@ -34,21 +34,33 @@ __device__ __forceinline__ int composite(const Plan& P, int64_t g, float dt, flo
   float T = 1.0f;
   for (int c = 0; c < 5; ++c) res[c] = 0.0f;
   int used = cnt;
-  for (int k = 0; k < cnt; ++k) {
-    const int64_t s = first + k;
-    const float sigma = P.ws.out[s];
-    const float x = sigma * dt;
-    const float alpha = -expm1f(-x);
-    const float w = T * alpha;
-    res[0] = fmaf(w, P.ws.out[S_cap + s], res[0]);
-    res[1] = fmaf(w, P.ws.out[2 * S_cap + s], res[1]);
-    res[2] = fmaf(w, P.ws.out[3 * S_cap + s], res[2]);
-    res[3] += w;
-    res[4] = fmaf(w, P.ws.s_t[s], res[4]);
-    T *= expf(-x);
-    if (T < P.t_eps) {
-      used = k + 1;
-      break;
+  // chunks of 4 samples: every load of a chunk is issued before its arithmetic, which runs
+  // sample by sample in order (the same operations as a one-sample loop)
+  for (int k = 0; k < cnt; k += 4) {
+    float sg[4], cr[4], cg[4], cb[4], tj[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t s = first + k + j;
+      const bool in = k + j < cnt;
+      sg[j] = in ? P.ws.out[s] : 0.0f;
+      cr[j] = in ? P.ws.out[S_cap + s] : 0.0f;
+      cg[j] = in ? P.ws.out[2 * S_cap + s] : 0.0f;
+      cb[j] = in ? P.ws.out[3 * S_cap + s] : 0.0f;
+      tj[j] = in ? P.ws.s_t[s] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (k + j >= cnt) return used;
+      const float x = sg[j] * dt;
+      const float alpha = -expm1f(-x);
+      const float w = T * alpha;
+      res[0] = fmaf(w, cr[j], res[0]);
+      res[1] = fmaf(w, cg[j], res[1]);
+      res[2] = fmaf(w, cb[j], res[2]);
+      res[3] += w;
+      res[4] = fmaf(w, tj[j], res[4]);
+      T *= expf(-x);
+      if (T < P.t_eps) return k + j + 1;
     }
   }
   return used;
@@ -212,39 +224,56 @@ __global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__
     const int64_t first = P.ws.ray_first[g];
     const int cnt = P.ws.ray_count[g];
     float T = 1.0f, pre[3] = {0.f, 0.f, 0.f}, pre_d = 0.0f;
-    for (int k = 0; k < cnt; ++k) {
-      const int64_t s = first + k;
-      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
-      if (k < used) {
-        const float sigma = P.ws.out[s];
-        const float col[3] = {P.ws.out[S_cap + s], P.ws.out[2 * S_cap + s], P.ws.out[3 * S_cap + s]};
-        const float x = sigma * dt;
-        const float alpha = -expm1f(-x);
-        const float w = T * alpha;
-        const float Tn = T * expf(-x);
-        float dsig = 0.0f;
-        float dz[3];
-        for (int c = 0; c < 3; ++c) {
-          pre[c] = fmaf(w, col[c], pre[c]);
-          dsig = fmaf(dC[c], Tn * col[c] - (res[c] - pre[c]), dsig);
-          dz[c] = dC[c] * w * col[c] * (1.0f - col[c]);
-        }
-        if (dD != 0.0f) {
-          // depth D = sum T_j alpha_j t_j: the colour adjoint with c_j -> t_j
-          const float tj = P.ws.s_t[s];
-          pre_d = fmaf(w, tj, pre_d);
-          dsig = fmaf(dD, Tn * tj - (res[4] - pre_d), dsig);
-        }
-        d0 = dsig * dt * sigma;
-        d1 = dz[0];
-        d2 = dz[1];
-        d3 = dz[2];
-        T = Tn;
+    // chunks of 4 samples as in composite(): loads first, then the in-order arithmetic
+    for (int k0 = 0; k0 < cnt; k0 += 4) {
+      float sg[4], cl[4][3], tl[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t s = first + k0 + j;
+        const bool in = k0 + j < used;
+        sg[j] = in ? P.ws.out[s] : 0.0f;
+        cl[j][0] = in ? P.ws.out[S_cap + s] : 0.0f;
+        cl[j][1] = in ? P.ws.out[2 * S_cap + s] : 0.0f;
+        cl[j][2] = in ? P.ws.out[3 * S_cap + s] : 0.0f;
+        tl[j] = in && dD != 0.0f ? P.ws.s_t[s] : 0.0f;
       }
-      P.ws.dout[s] = d0;
-      P.ws.dout[S_cap + s] = d1;
-      P.ws.dout[2 * S_cap + s] = d2;
-      P.ws.dout[3 * S_cap + s] = d3;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + j;
+        if (k >= cnt) break;
+        const int64_t s = first + k;
+        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+        if (k < used) {
+          const float sigma = sg[j];
+          const float col[3] = {cl[j][0], cl[j][1], cl[j][2]};
+          const float x = sigma * dt;
+          const float alpha = -expm1f(-x);
+          const float w = T * alpha;
+          const float Tn = T * expf(-x);
+          float dsig = 0.0f;
+          float dz[3];
+          for (int c = 0; c < 3; ++c) {
+            pre[c] = fmaf(w, col[c], pre[c]);
+            dsig = fmaf(dC[c], Tn * col[c] - (res[c] - pre[c]), dsig);
+            dz[c] = dC[c] * w * col[c] * (1.0f - col[c]);
+          }
+          if (dD != 0.0f) {
+            // depth D = sum T_j alpha_j t_j: the colour adjoint with c_j -> t_j
+            const float tj = tl[j];
+            pre_d = fmaf(w, tj, pre_d);
+            dsig = fmaf(dD, Tn * tj - (res[4] - pre_d), dsig);
+          }
+          d0 = dsig * dt * sigma;
+          d1 = dz[0];
+          d2 = dz[1];
+          d3 = dz[2];
+          T = Tn;
+        }
+        P.ws.dout[s] = d0;
+        P.ws.dout[S_cap + s] = d1;
+        P.ws.dout[2 * S_cap + s] = d2;
+        P.ws.dout[3 * S_cap + s] = d3;
+      }
     }
   }
   // deterministic block sum of the per-ray Huber terms

@@ -41,8 +41,20 @@ __device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&k
   if (n == kKnnOverflow) {
     for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
   } else {
+    // the list in chunks of 8 ids (one 16-byte load; cap is a multiple of 8), whose 8 node
+    // loads are issued together, then inserted in list order (= index order, as before)
     const uint16_t* list = W.cand + cell * W.cap;
-    for (uint32_t c = 0; c < n; ++c) {
+    uint32_t c = 0;
+    for (; c + 8 <= n; c += 8) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(list + c));
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+      float4 x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = __ldg(W.x_live + ((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) knn_insert<K>(knn_key(p, x[j]), (int)((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu), keys, ids);
+    }
+    for (; c < n; ++c) {
       const int i = __ldg(list + c);
       knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
     }
