@@ -80,16 +80,18 @@ __device__ __forceinline__ void scatter_runs(float2* table, uint32_t key, bool l
 }
 
 // Scatter of one sample-level without run summation: the two corners of a cell that differ
-// in x go out as one 16-byte atomic when their slots are an aligned adjacent pair (dense
-// rows, or a hashed slot with x even), else as two 8-byte atomics.
+// in x go out as one 16-byte atomic when their slots are the two halves of an aligned pair
+// (i, i ^ 1: dense rows with an even first slot, hashed slots whenever x is even, in either
+// order), else as two 8-byte atomics.
 __device__ __forceinline__ void scatter_pairs(float2* table, const Corners& c, float2 g) {
 #pragma unroll
   for (int k = 0; k < 8; k += 2) {
     const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
     const float2 v0 = make_float2(c.w[k] * g.x, c.w[k] * g.y);
     const float2 v1 = make_float2(c.w[k + 1] * g.x, c.w[k + 1] * g.y);
-    if (i1 == i0 + 1u && !(i0 & 1u)) {
-      atomicAdd(reinterpret_cast<float4*>(table + i0), make_float4(v0.x, v0.y, v1.x, v1.y));
+    if ((i0 ^ i1) == 1u) {
+      const float2 lo = (i0 & 1u) ? v1 : v0, hi = (i0 & 1u) ? v0 : v1;
+      atomicAdd(reinterpret_cast<float4*>(table + (i0 & ~1u)), make_float4(lo.x, lo.y, hi.x, hi.y));
     } else {
       atomicAdd(table + i0, v0);
       atomicAdd(table + i1, v1);
