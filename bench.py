@@ -162,6 +162,12 @@ def kernel_work(name, R, S_occ, n_samples, L, n_params, n_w):
         return "hbm", S_occ * (12 + L * (8 + 8 * 8))    # vc, dfeat in, 8 corner atomics per level
     if name == "march_count":
         return "hbm", R * 28
+    if name == "march_emit":
+        return "hbm", R * 32 + S_occ * 20            # o, d, first, count in; ray id, t, position out
+    if name == "composite_train":
+        return "hbm", R * 48 + S_occ * 36            # per sample sigma, rgb, t in, dL/dout out
+    if name == "warp":
+        return "hbm", S_occ * 24                     # live position in, canonical out (latency-bound)
     return None, None
 
 
@@ -295,6 +301,31 @@ def roofline(ktime, tw, R, S_occ, peaks, l2=None):
     return None
 
 
+def kernel_rooflines(ktime, tw, R, S_occ, peaks):
+    """Every timed kernel of the step against the roofline that bounds its work: algorithmic
+    work per timed record (a step stage over all batches; Adam: one field) -- FLOPs of the
+    unpadded MLP layers, or bytes -- over its CUDA-event time,
+    as a fraction of the measured peak (HBM copy bandwidth, sustained dense BF16, or the FP32
+    FMA peak derived from the SM count and the maximum SM clock)."""
+    fp = tw.fields[0]
+    n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()  # Adam is timed per field
+    res = {}
+    for name, (kms, kn) in sorted(ktime.items()):
+        bound, work = kernel_work(name, R, S_occ, tw.n_samples, fp.desc.L, n_params, fp.desc.n_weight_params())
+        if bound is None:
+            continue
+        dur = kms / kn * 1e-3
+        if bound == "hbm":
+            peak, unit, ach = peaks.get("hbm_gbs", 6400.0), "GB/s", work / dur / 1e9
+        elif bound == "tensor":
+            peak, unit, ach = peaks.get("bf16_tflops_sustained", 1400.0), "TFLOP/s", work / dur / 1e12
+        else:
+            peak, unit, ach = fp32_alu_peak(peaks.get("sm_max_mhz", 2032.0)), "TFLOP/s", work / dur / 1e12
+        res[name] = {"bound": bound, "achieved": round(ach, 1), "peak": round(peak, 1), "unit": unit,
+                     "frac": round(ach / peak, 4), "ms": round(kms / kn, 4)}
+    return res
+
+
 def apply_batched(out, bt, invr, ctx, args, world, peaks):
     """Fill the bench line from the batched key-frame run (the headline workload)."""
     bvalue = world * bt["S_nom"] / (bt["ms"] * 1e-3)
@@ -315,6 +346,7 @@ def apply_batched(out, bt, invr, ctx, args, world, peaks):
                            for k in ("encode", "encode_bwd") if k in bt["ktime"]}
     nsteps = max(5, args.steps // 4)
     out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
+    out["kernel_rooflines"] = kernel_rooflines(bt["ktime"], btw, bR, bS, peaks)
     per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
     out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
                                     / nsteps * args.steps))
