@@ -489,6 +489,46 @@ def test_paper_loss_keyframe_two_fields(env, prec):
             _assert_grads_close(gt, ogt, "tables", MIXED_TABLE_RTOL["bf16"])
 
 
+def test_fields_of_both_precisions_in_one_call(env):
+    """One render call and one training call holding an FP32 human field and a BF16 object
+    field: the FP32 features (feature-major) and the 16-bit operand tiles share the feature
+    buffer, each in its own sample slots, and each field matches the oracle at the tolerance
+    of its own precision."""
+    invr, ctx, oracle = env
+    w = synth.two_field_render(width=64, height=64)
+    sides = [Side(invr, ctx, oracle, w.views[0], invr.INVR_FP32),
+             Side(invr, ctx, oracle, w.views[1], invr.INVR_MLP_BF16)]
+    rgba, _ = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [s.view for s in sides])
+    ctx.sync()
+    ref = oracle.render(w.rays.o, w.rays.d, w.n_samples, w.t_eps, [s.oview for s in sides])
+    assert ref.rgba_v[0][3].max() > 0.2 and ref.rgba_v[1][3].max() > 0.2   # both fields visible
+    ok = ~_near_tie(ref, 1e-2)
+    np.testing.assert_allclose(host(rgba)[:, ok], ref.rgba[:, ok], rtol=0, atol=MIXED_RGB_TOL)
+
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    human, obj = tw.fields
+    precs = {id(human): invr.INVR_FP32, id(obj): invr.INVR_MLP_BF16}
+    ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
+    gfields = {id(fp): invr.Field.from_synth(ctx, fp, precs[id(fp)]) for fp in tw.fields}
+    batches, obatches, keep = [], [], []
+    for b in tw.batches:
+        side = Side(invr, ctx, oracle, b.view, field=gfields[id(b.view.field)], ofield=ofields[id(b.view.field)])
+        keep.append(side)
+        batches.append((cu(b.rays.o), cu(b.rays.d), side.view, cu(b.target)))
+        obatches.append(oracle.TrainBatch(b.rays.o, b.rays.d, side.oview, b.target))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 2e-3 * oloss
+    for fp, w_rtol, t_rtol in ((human, GRAD_RTOL_WARP, GRAD_RTOL_WARP), (obj, MIXED_W_RTOL, MIXED_TABLE_RTOL["bf16"])):
+        gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+        ogt, ogw = ograds[id(ofields[id(fp)])]
+        _assert_grads_close(gw, ogw, "weights", w_rtol)
+        _assert_grads_close(gt, ogt, "tables", t_rtol)
+
+
 def test_train_step_adam_matches_oracle(env):
     invr, ctx, oracle = env
     tw = synth.train_step_workload(seed=5, n_rays=1024)
