@@ -26,17 +26,20 @@ namespace invr {
 // that handle the L levels of one chunk run together and read its positions from L2 once
 // (a level-major order streamed every sample's position from DRAM once per level).
 __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, int L) {
+  __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
   const int64_t S_cap = P.ws.S_cap;
   if (P.ws.view_base[P.n_views] > S_cap) return;
-  const int64_t S0 = P.ws.view_base[P.view_lo], S = P.ws.view_base[P.view_hi];
+  if (threadIdx.x <= P.n_views) vb[threadIdx.x] = P.ws.view_base[threadIdx.x];
+  __syncthreads();
+  const int64_t S0 = vb[P.view_lo], S = vb[P.view_hi];
   float* feat = static_cast<float*>(P.ws.feat);
   const int64_t n_items = (S - S0 + 255) / 256 * L;
+  int v = P.view_lo;  // cursor: this thread's samples only increase over its work items
   for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
     const int l = (int)(b % L);
     const int64_t s = S0 + (b / L) * 256 + threadIdx.x;
     if (s >= S) continue;
-    int v = P.view_lo;
-    while (v + 1 < P.view_hi && s >= P.ws.view_base[v + 1]) ++v;
+    v = advance_view(vb, P.view_hi, s, v);
     const FieldDev& F = P.v[v].field;
     if (l >= F.L) continue;
     float2 f = make_float2(0.0f, 0.0f);
@@ -58,19 +61,22 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, 
 
 // Work items as in k_encode: (chunk of 256 samples, level), level fastest.
 __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan P, int L) {
+  __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
   const int64_t S_cap = P.ws.S_cap;
   if (P.ws.view_base[P.n_views] > S_cap) return;
-  const int64_t S0 = P.ws.view_base[P.view_lo], S = P.ws.view_base[P.view_hi];
+  if (threadIdx.x <= P.n_views) vb[threadIdx.x] = P.ws.view_base[threadIdx.x];
+  __syncthreads();
+  const int64_t S0 = vb[P.view_lo], S = vb[P.view_hi];
   const float scale = P.grad_scale;
   const int64_t n_items = (S - S0 + 255) / 256 * L;
+  int v = P.view_lo;  // cursor: this warp's samples only increase over its work items
   // warps never straddle two views: view ranges are kTile-aligned (S0 too) and a warp is 32
   for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
     const int l = (int)(b % L);
     const int64_t s0 = S0 + (b / L) * 256;
     const int64_t s = s0 + threadIdx.x;
     const int64_t sw = s0 + (threadIdx.x & ~31);
-    int v = P.view_lo;
-    while (v + 1 < P.view_hi && sw >= P.ws.view_base[v + 1]) ++v;
+    v = advance_view(vb, P.view_hi, sw, v);
     const FieldDev& F = P.v[v].field;
     if (l >= F.L || sw >= S) continue;  // warp-uniform
     bool live = s < S && P.ws.s_ray[s] >= 0;
