@@ -285,10 +285,16 @@ __device__ __forceinline__ void issue_dw(uint32_t d_tmem, uint32_t a_saddr, int 
   }
 }
 
-// a 16-bit value is positive iff its sign bit is clear and it is not +0
-__device__ __forceinline__ float relu_mask(uint32_t w, int half) {
-  const uint32_t h = half ? (w >> 16) : (w & 0xFFFFu);
-  return (!(h & 0x8000u) && (h & 0x7FFFu)) ? 1.0f : 0.0f;
+// Per 16-bit half of a stored ReLU output w (each half +0, -0 or positive): 0xFFFF where the
+// half is positive, else 0 (one packed half-precision compare).
+template <bool BF16>
+__device__ __forceinline__ uint32_t positive_halves(uint32_t w) {
+  if constexpr (BF16) {
+    return __hgt2_mask(*reinterpret_cast<const __nv_bfloat162*>(&w),
+                       __nv_bfloat162(__float2bfloat16(0.0f), __float2bfloat16(0.0f)));
+  } else {
+    return __hgt2_mask(*reinterpret_cast<const __half2*>(&w), __half2(__float2half(0.0f), __float2half(0.0f)));
+  }
 }
 
 // The adjoint chain: per tile, dL/d(delta v) (the stored dL/dv_c, padded to 16 columns)
@@ -388,8 +394,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
       }
     }
     for (int j = 0; j < 2; ++j) pending[j] = slot[j].s0 >= 0;
+    // the ReLU mask rows (this thread's row of the stored h tile) of the next stage of each
+    // slot, loaded one stage ahead so that they arrive under the other slot's epilogue
+    uint4 mrow[2][16];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (slot[j].s0 < 0 || n < 1) continue;
+      const uint8_t* hg = P.ws.def_h + ((int64_t)(n - 1) * tiles_cap + slot[j].s0 / kTM) * kHTile;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) mrow[j][c] = __ldg(reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(t, 8 * c, H)));
+    }
     // stage e = 0..n-1: mask with h_{n-1-e}, store g, issue the next adjoint; stage n: dL/df
     for (int e = 0; e <= n && ok; ++e) {
+#pragma unroll
       for (int j = 0; j < 2; ++j) {
         if (slot[j].s0 < 0) continue;
         ok = tc::mbar_wait(mbar0 + 8 * j, phase[j], P.wait_limit);
@@ -404,33 +421,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
         const int64_t T = slot[j].s0 / kTM;
         if (e < n) {
           const int li = n - 1 - e;
-          const uint8_t* hg = P.ws.def_h + ((int64_t)li * tiles_cap + T) * kHTile;
           uint8_t* gs = sm + OFF_HB + j * kHTile;
           uint8_t* gg = P.ws.def_g + ((int64_t)li * tiles_cap + T) * kHTile;
-          for (int c = 0; c < H; c += 16) {
-            float v[16];
-            tc::tmem_ld16(row + c, v);
-            const uint4 m0 = *reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(t, c, H));
-            const uint4 m1 = *reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(t, c + 8, H));
-            const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              v[2 * i] *= relu_mask(mw[i], 0);
-              v[2 * i + 1] *= relu_mask(mw[i], 1);
+          for (int q4 = 0; q4 < 4; ++q4) {
+            float v[32];
+            tc::tmem_ld32(row + 32 * q4, v);
+#pragma unroll
+            for (int c8 = 0; c8 < 4; ++c8) {
+              // pack, then clear the halves whose stored activation is not positive
+              const uint4 m = mrow[j][4 * q4 + c8];
+              const float* x = v + 8 * c8;
+              uint4 q;
+              q.x = tc::pack2<BF16>(x[0], x[1]) & positive_halves<BF16>(m.x);
+              q.y = tc::pack2<BF16>(x[2], x[3]) & positive_halves<BF16>(m.y);
+              q.z = tc::pack2<BF16>(x[4], x[5]) & positive_halves<BF16>(m.z);
+              q.w = tc::pack2<BF16>(x[6], x[7]) & positive_halves<BF16>(m.w);
+              const int c = 32 * q4 + 8 * c8;
+              *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c, H)) = q;
+              *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c, H)) = q;
             }
-            uint4 lo, hi;
-            lo.x = tc::pack2<BF16>(v[0], v[1]);
-            lo.y = tc::pack2<BF16>(v[2], v[3]);
-            lo.z = tc::pack2<BF16>(v[4], v[5]);
-            lo.w = tc::pack2<BF16>(v[6], v[7]);
-            hi.x = tc::pack2<BF16>(v[8], v[9]);
-            hi.y = tc::pack2<BF16>(v[10], v[11]);
-            hi.z = tc::pack2<BF16>(v[12], v[13]);
-            hi.w = tc::pack2<BF16>(v[14], v[15]);
-            *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c, H)) = lo;
-            *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c + 8, H)) = hi;
-            *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c, H)) = lo;
-            *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c + 8, H)) = hi;
+          }
+          if (li > 0) {
+            const uint8_t* hn = P.ws.def_h + ((int64_t)(li - 1) * tiles_cap + T) * kHTile;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              mrow[j][c] = __ldg(reinterpret_cast<const uint4*>(hn + tc::kmajor_offset(t, 8 * c, H)));
           }
           operands_ready();
           if (t == 0) {
