@@ -492,18 +492,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
 //   dW_1f            += g_1^T x          (128 x 32, columns 400)
 //   dW_1p            += g_1^T Theta      (128 x 80, columns 432; Theta = the view's pose in
 //                                          every row, the pose columns of W_1)
-// then written as this CTA's partial (summed over CTAs by k_deform_reduce).  The stored
-// tiles are copied into shared memory, two operand pairs in flight.
+// then written as this CTA's partial (summed over CTAs by k_deform_reduce).  The operand
+// pairs of the CTA's tiles form one sequence; pair p+1's stored tiles arrive by bulk copies
+// into the other of two buffers while pair p's MMAs run (as soon as pair p-1's MMAs have
+// released that buffer).  Theta is rewritten by the threads when the view changes, after
+// the MMAs in flight have drained.
 constexpr uint32_t C_DWO = 384, C_DW1F = 400, C_DW1P = 432;
 constexpr uint32_t D_BUF = 0;                              // 2 x 2 x [128 x 128] operand buffers
 constexpr uint32_t D_THETA = D_BUF + 4 * kHTile;           // [128 x 80]
-constexpr uint32_t D_MISC = D_THETA + kTM * kDeformTcMaxPose * 2;
+constexpr uint32_t D_MISC = D_THETA + kTM * kDeformTcMaxPose * 2;   // 4 mbarriers + TMEM base
 constexpr uint32_t kSmemDw = D_MISC + 64 + 1024;
 
-__device__ __forceinline__ void copy_tile(uint8_t* dst, const uint8_t* __restrict__ src, int64_t bytes) {
-  for (int64_t e = threadIdx.x; e < bytes / 16; e += kThreads)
-    reinterpret_cast<uint4*>(dst)[e] = __ldg(reinterpret_cast<const uint4*>(src) + e);
-}
+// One operand pair of the weight-gradient sequence.
+struct DwPair {
+  const uint8_t* a;   // [128 samples][a_units] stored tile
+  const uint8_t* b;   // [128 samples][b_units] stored tile, or null for Theta
+  int a_units, b_units;
+  uint32_t dcol;      // accumulator columns
+};
 
 template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_constant__ Plan P) {
@@ -511,13 +517,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   const int64_t S_cap = P.ws.S_cap;
   const int64_t S = P.ws.view_base[P.n_views];
   const int t = threadIdx.x, warp = t >> 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + D_MISC + 16);
-  const uint32_t mbar0 = tc::smem_u32(sm + D_MISC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + D_MISC + 32);
+  const uint32_t mbar0 = tc::smem_u32(sm + D_MISC);        // MMAs of buffer b done: mbar0 + 8 b
+  const uint32_t lbar0 = tc::smem_u32(sm + D_MISC + 16);   // copies into buffer b landed: lbar0 + 8 b
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
   if (t == 0) {
     tc::mbar_init(mbar0, 1);
     tc::mbar_init(mbar0 + 8, 1);
+    tc::mbar_init(lbar0, 1);
+    tc::mbar_init(lbar0 + 8, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -525,60 +534,76 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   const uint32_t tmem = *tmem_slot;
   const int64_t tiles_cap = S_cap / kTM;
   const int64_t n_tiles = S <= S_cap ? S / kTM : 0;
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
+  uint32_t phase[2] = {0u, 0u}, lphase[2] = {0u, 0u};
+  bool pending[2] = {false, false}, loading[2] = {false, false};
   bool ok = true;
   bool any = false;
   int theta_view = -1;
   const DeformDev* Dp = nullptr;
-  int pair = 0;
-  // one operand pair into buffer b (after the MMA that last read it), then its MMA
-  auto run_pair = [&](const uint8_t* a_src, int a_units, const uint8_t* b_src, int b_units, uint32_t dcol,
-                      bool b_is_theta) -> bool {
-    const int b = pair & 1;
-    ++pair;
-    if (pending[b]) {
-      const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
-      if (!__syncthreads_and(got)) return false;
-      phase[b] ^= 1u;
-      pending[b] = false;
+
+  // the sequence: tiles T = blockIdx.x, +gridDim.x, ... of views with this kind of net;
+  // per tile n + 2 pairs
+  auto tile_view = [&](int64_t T) -> int {
+    for (; T < n_tiles; T += gridDim.x) {
+      const int v = view_of_slot(P, T * kTM);
+      if (P.v[v].has_deform && P.v[v].deform.tc == (BF16 ? 2 : 1)) return v;
     }
-    uint8_t* abuf = sm + D_BUF + (2 * b) * kHTile;
-    uint8_t* bbuf = sm + D_BUF + (2 * b + 1) * kHTile;
-    copy_tile(abuf, a_src, (int64_t)kTM * a_units * 2);
-    if (!b_is_theta) copy_tile(bbuf, b_src, (int64_t)kTM * b_units * 2);
-    operands_ready();
+    return -1;
+  };
+  auto first_tile = [&](int64_t T) -> int64_t {
+    for (; T < n_tiles; T += gridDim.x) {
+      const int v = view_of_slot(P, T * kTM);
+      if (P.v[v].has_deform && P.v[v].deform.tc == (BF16 ? 2 : 1)) return T;
+    }
+    return n_tiles;
+  };
+  auto pair_of = [&](int64_t T, int i, int n) -> DwPair {
+    const uint8_t* hb = P.ws.def_h;
+    const uint8_t* gb = P.ws.def_g;
+    auto H_ = [&](int l) { return hb + ((int64_t)l * tiles_cap + T) * kHTile; };
+    auto G_ = [&](int l) { return gb + ((int64_t)l * tiles_cap + T) * kHTile; };
+    if (i == 0) return DwPair{H_(n - 1), P.ws.def_gout + T * kGoTile, kH, 16, C_DWO};
+    if (i < n) return DwPair{G_(n - i), H_(n - i - 1), kH, kH, 128u * (uint32_t)(n - i - 1)};
+    if (i == n) return DwPair{G_(0), P.ws.def_x + T * kXTile, kH, kKf, C_DW1F};
+    return DwPair{G_(0), nullptr, kH, kDeformTcMaxPose, C_DW1P};
+  };
+  // one thread: bulk copies of a pair's stored tiles into buffer b
+  auto load_pair = [&](const DwPair& q, int b) {
     if (t == 0) {
-      tc::fence_after_sync();
-      issue_dw<BF16>(tmem + dcol, tc::smem_u32(abuf), a_units,
-               b_is_theta ? sbase + D_THETA : tc::smem_u32(bbuf), b_units, any);
-      tc::commit_to(mbar0 + 8 * b);
+      const uint32_t abytes = (uint32_t)(kTM * q.a_units * 2), bbytes = q.b ? (uint32_t)(kTM * q.b_units * 2) : 0u;
+      tc::mbar_expect_tx(lbar0 + 8 * b, abytes + bbytes);
+      tc::bulk_g2s(sbase + D_BUF + (2 * b) * kHTile, q.a, abytes, lbar0 + 8 * b);
+      if (q.b) tc::bulk_g2s(sbase + D_BUF + (2 * b + 1) * kHTile, q.b, bbytes, lbar0 + 8 * b);
     }
-    pending[b] = true;
+    loading[b] = true;
+  };
+  // all threads: buffer b's MMAs have completed (bounded)
+  auto drain = [&](int b) -> bool {
+    if (!pending[b]) return true;
+    const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
+    if (!__syncthreads_and(got)) return false;
+    phase[b] ^= 1u;
+    pending[b] = false;
     return true;
   };
-  for (int64_t T = blockIdx.x; T < n_tiles && ok; T += gridDim.x) {
-    const int v = view_of_slot(P, T * kTM);
-    if (!P.v[v].has_deform || P.v[v].deform.tc != (BF16 ? 2 : 1)) continue;
+
+  int64_t T = first_tile(blockIdx.x);
+  int i = 0, v = T < n_tiles ? tile_view(T) : -1;
+  int p = 0;  // position in the sequence; buffer p & 1
+  if (T < n_tiles) load_pair(pair_of(T, 0, P.v[v].deform.n_hidden), 0);
+  while (T < n_tiles && ok) {
     const DeformDev& D = P.v[v].deform;
-    Dp = &D;
     const int n = D.n_hidden;
-    if (v != theta_view) {
-      // Theta rows = this view's pose, padded to 80 columns (after the MMA that read it)
-      for (int b = 0; b < 2 && ok; ++b) {
-        if (!pending[b]) continue;
-        const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
-        ok = __syncthreads_and(got);
-        if (ok) {
-          phase[b] ^= 1u;
-          pending[b] = false;
-        }
-      }
-      if (!ok) break;
+    const int b = p & 1;
+    Dp = &D;
+    if (i == 0 && v != theta_view) {
+      // Theta rows = this view's pose, padded to 80 columns, once the MMAs that read the
+      // previous Theta have completed
+      if (!(ok = drain(0) && drain(1))) break;
       for (int k = 0; k < kDeformTcMaxPose; k += 8) {
         float x[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = k + i < D.pose_dim ? D.pose[k + i] : 0.0f;
+        for (int u = 0; u < 8; ++u) x[u] = k + u < D.pose_dim ? D.pose[k + u] : 0.0f;
         uint4 q;
         q.x = tc::pack2<BF16>(x[0], x[1]);
         q.y = tc::pack2<BF16>(x[2], x[3]);
@@ -586,27 +611,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
         q.w = tc::pack2<BF16>(x[6], x[7]);
         *reinterpret_cast<uint4*>(sm + D_THETA + tc::kmajor_offset(t, k, kDeformTcMaxPose)) = q;
       }
+      tc::fence_smem_to_async();
+      tc::fence_before_sync();
+      __syncthreads();
       theta_view = v;
     }
-    const uint8_t* hb = P.ws.def_h;
-    const uint8_t* gb = P.ws.def_g;
-    auto H_ = [&](int l) { return hb + ((int64_t)l * tiles_cap + T) * kHTile; };
-    auto G_ = [&](int l) { return gb + ((int64_t)l * tiles_cap + T) * kHTile; };
-    ok = run_pair(H_(n - 1), kH, P.ws.def_gout + T * kGoTile, 16, C_DWO, false);
-    for (int l = n - 1; l >= 1 && ok; --l) ok = run_pair(G_(l), kH, H_(l - 1), kH, 128u * (l - 1), false);
-    if (ok) ok = run_pair(G_(0), kH, P.ws.def_x + T * kXTile, kKf, C_DW1F, false);
-    if (ok) ok = run_pair(G_(0), kH, nullptr, kDeformTcMaxPose, C_DW1P, true);
-    any = true;
-  }
-  for (int b = 0; b < 2 && ok; ++b) {
-    if (!pending[b]) continue;
-    const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
-    ok = __syncthreads_and(got);
-    if (ok) {
-      phase[b] ^= 1u;
-      pending[b] = false;
+    const DwPair cur = pair_of(T, i, n);
+    // the next pair of the sequence (possibly the next tile's first), loaded into the other
+    // buffer once pair p-1's MMAs have released it
+    int64_t T2 = T;
+    int i2 = i + 1, v2 = v;
+    if (i2 > n + 1) {
+      T2 = first_tile(T + gridDim.x);
+      i2 = 0;
+      v2 = T2 < n_tiles ? tile_view(T2) : -1;
     }
+    if (T2 < n_tiles) {
+      if (!(ok = drain(b ^ 1))) break;
+      load_pair(pair_of(T2, i2, P.v[v2].deform.n_hidden), b ^ 1);
+    }
+    // this pair's tiles have landed: issue its MMAs
+    ok = tc::mbar_wait(lbar0 + 8 * b, lphase[b], P.wait_limit);
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    lphase[b] ^= 1u;
+    loading[b] = false;
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_dw<BF16>(tmem + cur.dcol, sbase + D_BUF + (2 * b) * kHTile, cur.a_units,
+                     cur.b ? sbase + D_BUF + (2 * b + 1) * kHTile : sbase + D_THETA, cur.b_units, any);
+      tc::commit_to(mbar0 + 8 * b);
+    }
+    pending[b] = true;
+    ++p;
+    if (i == n + 1) any = true;  // every accumulator has been written once
+    T = T2;
+    i = i2;
+    v = v2;
   }
+  for (int b = 0; b < 2 && ok; ++b) ok = drain(b);
   if (ok && Dp) {
     // write this CTA's partial: lane t is row t of every accumulator
     tc::fence_after_sync();
@@ -618,37 +663,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
     for (int l = 1; l < n; ++l) {
       float* dst = part + (int64_t)kH * n_in + (int64_t)(l - 1) * kH * kH + (int64_t)t * kH;
       for (int c = 0; c < kH; c += 16) {
-        float v[16];
-        tc::tmem_ld16(row + 128u * (l - 1) + c, v);
+        float v16[16];
+        tc::tmem_ld16(row + 128u * (l - 1) + c, v16);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dst[c + i] = any ? v[i] * out_scale : 0.0f;
+        for (int u = 0; u < 16; ++u) dst[c + u] = any ? v16[u] * out_scale : 0.0f;
       }
     }
     {
-      float v[16];
-      tc::tmem_ld16(row + C_DWO, v);
+      float v16[16];
+      tc::tmem_ld16(row + C_DWO, v16);
       float* dst = part + layer_offset(D, n);
-      for (int c = 0; c < 3; ++c) dst[c * kH + t] = any ? v[c] * out_scale : 0.0f;
+      for (int c = 0; c < 3; ++c) dst[c * kH + t] = any ? v16[c] * out_scale : 0.0f;
     }
     for (int c = 0; c < kKf; c += 16) {
-      float v[16];
-      tc::tmem_ld16(row + C_DW1F + c, v);
+      float v16[16];
+      tc::tmem_ld16(row + C_DW1F + c, v16);
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (c + i < D.n_feat) part[(int64_t)t * n_in + c + i] = any ? v[i] * out_scale : 0.0f;
+      for (int u = 0; u < 16; ++u)
+        if (c + u < D.n_feat) part[(int64_t)t * n_in + c + u] = any ? v16[u] * out_scale : 0.0f;
     }
     for (int c = 0; c < kDeformTcMaxPose; c += 16) {
-      float v[16];
-      tc::tmem_ld16(row + C_DW1P + c, v);
+      float v16[16];
+      tc::tmem_ld16(row + C_DW1P + c, v16);
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (c + i < D.pose_dim) part[(int64_t)t * n_in + D.n_feat + c + i] = any ? v[i] * out_scale : 0.0f;
+      for (int u = 0; u < 16; ++u)
+        if (c + u < D.pose_dim) part[(int64_t)t * n_in + D.n_feat + c + u] = any ? v16[u] * out_scale : 0.0f;
     }
   }
   if (!ok) {
     if (t == 0) atomicOr(P.status, kStatusTimeout);
-    for (int b = 0; b < 2; ++b)
+    // let this CTA's MMAs and copies in flight finish (bounded) before its tensor memory and
+    // shared memory are released
+    for (int b = 0; b < 2; ++b) {
       if (pending[b]) tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit);
+      if (loading[b]) tc::mbar_wait(lbar0 + 8 * b, lphase[b], kDrainLimit);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
