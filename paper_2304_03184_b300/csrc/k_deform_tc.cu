@@ -146,16 +146,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       stage<BF16>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
       loaded = D.weights;
     }
-    // operands of both tiles: features (FP32 feature-major) -> BF16 rows, pose bias
+    // operands of both tiles: features (FP32 feature-major) -> BF16 rows, pose bias; every
+    // feature load of both tiles is issued before the first store
+    float xr[2][kKf];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+      for (int k = 0; k < kKf; ++k)
+        xr[j][k] = slot[j].s0 >= 0 && k < D.n_feat ? P.ws.feat_d[(int64_t)k * S_cap + slot[j].s0 + t] : 0.0f;
+    }
+#pragma unroll
     for (int j = 0; j < 2; ++j) {
       if (slot[j].s0 < 0) continue;
       const int64_t s0 = slot[j].s0;
       uint8_t* X = sm + OFF_X + j * kTM * kKf * 2;
-      for (int k = 0; k < Kf; k += 8) {
-        float x[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          x[i] = k + i < D.n_feat ? P.ws.feat_d[(int64_t)(k + i) * S_cap + s0 + t] : 0.0f;
+      for (int k = 0; k < kKf; k += 8) {
+        if (k >= Kf) break;
+        const float* x = xr[j] + k;
         uint4 q;
         q.x = tc::pack2<BF16>(x[0], x[1]);
         q.y = tc::pack2<BF16>(x[2], x[3]);
@@ -194,28 +202,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
         uint8_t* Hb = sm + OFF_HB + j * kTM * kH * 2;
         if (l < n) {
           const float* bias = reinterpret_cast<const float*>(sm + OFF_BIAS) + j * kH;
-          for (int c = 0; c < H; c += 16) {
-            float v[16];
-            tc::tmem_ld16(row + c, v);
+          uint8_t* g = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + slot[j].s0 / kTM) * kHTile;
+          for (int c = 0; c < H; c += 32) {
+            float v[32];
+            tc::tmem_ld32(row + c, v);
             if (l == 0) {
 #pragma unroll
-              for (int i = 0; i < 16; ++i) v[i] += bias[c + i];
+              for (int i = 0; i < 32; ++i) v[i] += bias[c + i];
             }
-            uint4 lo, hi;
-            lo.x = tc::pack2<BF16>(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f));
-            lo.y = tc::pack2<BF16>(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
-            lo.z = tc::pack2<BF16>(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f));
-            lo.w = tc::pack2<BF16>(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f));
-            hi.x = tc::pack2<BF16>(fmaxf(v[8], 0.f), fmaxf(v[9], 0.f));
-            hi.y = tc::pack2<BF16>(fmaxf(v[10], 0.f), fmaxf(v[11], 0.f));
-            hi.z = tc::pack2<BF16>(fmaxf(v[12], 0.f), fmaxf(v[13], 0.f));
-            hi.w = tc::pack2<BF16>(fmaxf(v[14], 0.f), fmaxf(v[15], 0.f));
-            *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c, H)) = lo;
-            *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c + 8, H)) = hi;
-            if (P.deform_store) {
-              uint8_t* g = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + slot[j].s0 / kTM) * kHTile;
-              *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c, H)) = lo;
-              *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c + 8, H)) = hi;
+#pragma unroll
+            for (int c8 = 0; c8 < 4; ++c8) {
+              const float* x = v + 8 * c8;
+              uint4 q;
+              q.x = tc::pack2<BF16>(fmaxf(x[0], 0.f), fmaxf(x[1], 0.f));
+              q.y = tc::pack2<BF16>(fmaxf(x[2], 0.f), fmaxf(x[3], 0.f));
+              q.z = tc::pack2<BF16>(fmaxf(x[4], 0.f), fmaxf(x[5], 0.f));
+              q.w = tc::pack2<BF16>(fmaxf(x[6], 0.f), fmaxf(x[7], 0.f));
+              *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c + 8 * c8, H)) = q;
+              if (P.deform_store) *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c + 8 * c8, H)) = q;
             }
           }
           operands_ready();
