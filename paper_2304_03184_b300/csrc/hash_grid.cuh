@@ -1,6 +1,5 @@
-// Hash-grid corner geometry, the trilinear gather, and the warp-aggregated gradient
-// scatter, shared by the encoding kernels and the tensor-core MLP backward (which scatters
-// each sample's dL/dfeat straight from its epilogue).
+// Hash-grid corner geometry, the trilinear gather, and the gradient scatter (warp-aggregated
+// runs on coarse levels, x-adjacent pairs as one float4 atomic), used by the encoding kernels.
 #pragma once
 
 #include "invr_internal.cuh"

@@ -261,7 +261,8 @@ __device__ __forceinline__ void flag_status(unsigned* status, unsigned bit) { at
 // 8 samples, K * 16 bytes each.  Row group g of tile T sits at byte g * 4 * S_cap + T * 512
 // of the feature buffer, inside the columns that the FP32 feature-major layout gives the
 // same samples, so views of different precisions in one call never overlap; with S_cap a
-// multiple of kTile every row group starts on a 16-byte boundary (one bulk copy each).
+// multiple of kTile every row group starts on a 16-byte boundary (the tile is one TMA box,
+// see encode_feat16_map).
 __host__ __device__ constexpr size_t feat16_group_offset(int64_t S_cap, int64_t tile, int g) {
   return (size_t)g * 4 * (size_t)S_cap + (size_t)tile * 512;
 }
