@@ -127,6 +127,30 @@ def test_deform_tensor_core_training(env, net_prec):
     assert _rel(fw, ofw) <= 1e-2 and _rel(ft, oft) <= f_tol
 
 
+def test_deform_tensor_core_wait_timeout_recovered(env):
+    """The net's tensor-core kernels (forward, adjoint chain, weight-gradient pipeline) with
+    every bounded wait giving up at once: INVR_E_TIMEOUT at the next sync and no fault (each
+    kernel retires its MMAs and copies in flight before freeing tensor memory); with the
+    default limit the same context then matches the oracle's loss again."""
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(121)
+    tw = synth.train_step_workload(seed=21, n_rays=512)
+    dp, pose = synth.make_deform(rng), synth.make_pose(rng)
+    tb, gfields, ofields, net, onet, obatches, keep = _train(env, tw, dp, [pose], net_prec=invr.INVR_MLP_FP16)
+    ctx.set_wait_limit(0)
+    try:
+        invr.forward_train(ctx, tb)
+        invr.backward(ctx, tb)
+        with pytest.raises(invr.InvrError, match="TIMEOUT"):
+            ctx.sync()
+    finally:
+        ctx.set_wait_limit(1 << 22)
+    loss = invr.forward_train(ctx, tb)
+    ctx.sync()
+    oloss, _ = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta, grads=False)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-3 * oloss
+
+
 def test_deform_zero_output_layer_is_the_plain_warp(env):
     invr, ctx, oracle = env
     rng = np.random.default_rng(102)
