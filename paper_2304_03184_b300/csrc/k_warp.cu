@@ -119,6 +119,32 @@ __device__ __forceinline__ float3 dqb_warp(const WarpDev& W, float3 p, int32_t* 
   return dq_inverse_apply(br, bd, p);
 }
 
+// Views whose K is at most KMAX (the plan's largest): the instantiations for larger K are not
+// compiled into the kernel, which keeps its registers (and so its occupancy) to what KMAX needs.
+template <int KMAX>
+__device__ __forceinline__ float3 warp_point_upto(const WarpDev& W, float3 p) {
+  if (W.mode == 0) return rigid_inverse(W, p);
+  if constexpr (KMAX <= 4) {
+    switch (W.K) {
+      case 1: return dqb_warp<1>(W, p, nullptr, 0, 0);
+      case 2: return dqb_warp<2>(W, p, nullptr, 0, 0);
+      case 3: return dqb_warp<3>(W, p, nullptr, 0, 0);
+      default: return dqb_warp<4>(W, p, nullptr, 0, 0);
+    }
+  } else {
+    switch (W.K) {
+      case 1: return dqb_warp<1>(W, p, nullptr, 0, 0);
+      case 2: return dqb_warp<2>(W, p, nullptr, 0, 0);
+      case 3: return dqb_warp<3>(W, p, nullptr, 0, 0);
+      case 4: return dqb_warp<4>(W, p, nullptr, 0, 0);
+      case 5: return dqb_warp<5>(W, p, nullptr, 0, 0);
+      case 6: return dqb_warp<6>(W, p, nullptr, 0, 0);
+      case 7: return dqb_warp<7>(W, p, nullptr, 0, 0);
+      default: return dqb_warp<8>(W, p, nullptr, 0, 0);
+    }
+  }
+}
+
 __device__ __forceinline__ float3 warp_point(const WarpDev& W, float3 p, int32_t* ids_out, int64_t ids_ld,
                                              int64_t i) {
   if (W.mode == 0) return rigid_inverse(W, p);
@@ -134,7 +160,8 @@ __device__ __forceinline__ float3 warp_point(const WarpDev& W, float3 p, int32_t
   }
 }
 
-__global__ void __launch_bounds__(256) k_warp(const __grid_constant__ Plan P) {
+template <int KMAX>
+__global__ void __launch_bounds__(256, KMAX <= 4 ? 4 : 1) k_warp(const __grid_constant__ Plan P) {
   const int64_t S_cap = P.ws.S_cap;
   const int64_t S = P.ws.view_base[P.n_views];
   if (S > S_cap) return;
@@ -143,7 +170,7 @@ __global__ void __launch_bounds__(256) k_warp(const __grid_constant__ Plan P) {
     float3 vc = make_float3(0.f, 0.f, 0.f);
     if (g >= 0) {
       const float3 p = make_float3(P.ws.s_pos[s], P.ws.s_pos[S_cap + s], P.ws.s_pos[2 * S_cap + s]);
-      vc = warp_point(P.v[view_of_ray(P, g)].warp, p, nullptr, 0, 0);
+      vc = warp_point_upto<KMAX>(P.v[view_of_ray(P, g)].warp, p);
     }
     P.ws.s_vc[s] = vc.x;
     P.ws.s_vc[S_cap + s] = vc.y;
@@ -152,7 +179,13 @@ __global__ void __launch_bounds__(256) k_warp(const __grid_constant__ Plan P) {
 }
 
 cudaError_t launch_warp(const Plan& P, int num_sms, cudaStream_t s) {
-  k_warp<<<num_sms * P.tune.warp_ctas_per_sm, 256, 0, s>>>(P);
+  int kmax = 0;
+  for (int v = 0; v < P.n_views; ++v)
+    if (P.v[v].warp.mode == 1 && P.v[v].warp.K > kmax) kmax = P.v[v].warp.K;
+  if (kmax <= 4)
+    k_warp<4><<<num_sms * P.tune.warp_ctas_per_sm, 256, 0, s>>>(P);
+  else
+    k_warp<8><<<num_sms * P.tune.warp_ctas_per_sm, 256, 0, s>>>(P);
   return cudaGetLastError();
 }
 
