@@ -329,6 +329,10 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* args, invr_st
 /* The context's launch shapes: out4 = {warp CTAs/SM, encode CTAs/SM, scatter CTAs/SM,
  * aggregation resolution}. */
 invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4);
+/* Set the launch shapes directly (e.g. ones an earlier autotune returned): in4 as for
+ * invr_ctx_get_tune.  CTAs per SM in [1, 32], aggregation resolution in [0, 2^20] (0: no
+ * level sums runs).  INVR_E_ARG on a value out of range; the context is then unchanged. */
+invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in4);
 /* Polls of each bounded device-side wait (the tensor-core kernels' mbarrier waits) before
  * the kernel gives up, records INVR_E_TIMEOUT in the status word, lets its in-flight work
  * finish, frees its tensor memory and returns.  Default 2^22 (a few seconds).  0 makes every

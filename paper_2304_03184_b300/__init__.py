@@ -105,6 +105,7 @@ _SIGNATURES = {
     "invr_probe_l2_gather": [_VP, _VP, _I64, C.c_int, _I64, _VP, _VP],
     "invr_ctx_autotune": [_VP, C.POINTER(invr_train_args), _VP],
     "invr_ctx_get_tune": [_VP, C.POINTER(C.c_int)],
+    "invr_ctx_set_tune": [_VP, C.POINTER(C.c_int)],
     "invr_field_copy_params": [_VP, _VP, _VP],
     "invr_ctx_set_wait_limit": [_VP, C.c_uint32],
 }
@@ -193,6 +194,12 @@ class Context:
         _check(lib().invr_ctx_get_tune(self.h, out), self.h)
         return {"warp_ctas_per_sm": out[0], "encode_ctas_per_sm": out[1], "encode_bwd_ctas_per_sm": out[2],
                 "agg_res": out[3]}
+
+    def set_tune(self, tune: dict):
+        """Set the launch shapes (a dict as returned by tune() / autotune())."""
+        keys = ("warp_ctas_per_sm", "encode_ctas_per_sm", "encode_bwd_ctas_per_sm", "agg_res")
+        arr = (C.c_int * 4)(*[int(tune[k]) for k in keys])
+        _check(lib().invr_ctx_set_tune(self.h, arr), self.h)
 
     def enable_timing(self, on: bool = True):
         _check(lib().invr_ctx_enable_timing(self.h, 1 if on else 0), self.h)

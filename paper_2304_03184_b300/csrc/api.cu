@@ -716,10 +716,10 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
   float best_ms = 0.0f;
   invr_status st = measure(best_ms);
   // coordinate descent over the launch shapes
-  const int warp_c[] = {4, 8, 16}, enc_c[] = {1, 2, 4, 8}, agg_c[] = {0, 64, 256, 1024};
+  const int warp_c[] = {4, 8, 16}, enc_c[] = {1, 2, 4, 8}, agg_c[] = {0, 64, 128, 256, 512, 1024};
   for (int dim = 0; dim < 4 && st == INVR_OK; ++dim) {
     const int* cands = dim == 0 ? warp_c : (dim == 3 ? agg_c : enc_c);
-    const int n = dim == 0 ? 3 : 4;
+    const int n = dim == 0 ? 3 : (dim == 3 ? 6 : 4);
     for (int i = 0; i < n && st == INVR_OK; ++i) {
       Tune t = best;
       int* slot = dim == 0 ? &t.warp_ctas_per_sm
@@ -745,6 +745,20 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
     INVR_CUDA(ctx, cudaMemsetAsync(f->grads, 0, (f->n_tab + f->n_w) * sizeof(float), s));
   }
   INVR_CUDA(ctx, cudaStreamSynchronize(s));
+  return INVR_OK;
+}
+
+invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in4) {
+  if (!ctx) return INVR_E_ARG;
+  if (!in4) return fail(ctx, INVR_E_ARG, "null tune array");
+  for (int i = 0; i < 3; ++i)
+    if (in4[i] < 1 || in4[i] > 32) return fail(ctx, INVR_E_ARG, "CTAs per SM must be in [1, 32]");
+  if (in4[3] < 0 || in4[3] > (1 << 20)) return fail(ctx, INVR_E_ARG, "aggregation resolution must be in [0, 2^20]");
+  ctx->tune.warp_ctas_per_sm = in4[0];
+  ctx->tune.encode_ctas_per_sm = in4[1];
+  ctx->tune.encode_bwd_ctas_per_sm = in4[2];
+  ctx->tune.agg_res = in4[3];
+  ctx->fwd_valid = false;
   return INVR_OK;
 }
 

@@ -1,5 +1,6 @@
 // Hash-grid corner geometry, the trilinear gather, and the gradient scatter (warp-aggregated
-// runs on coarse levels, x-adjacent pairs as one float4 atomic), used by the encoding kernels.
+// runs per vertex-parity slot, x-adjacent pairs as one float4 atomic), used by the encoding
+// kernels.
 #pragma once
 
 #include "invr_internal.cuh"
@@ -9,28 +10,36 @@ namespace invr {
 struct Corners {
   uint32_t idx[8];
   float w[8];
+  uint32_t par;  // parities of the cell's lower corner: slot k holds corner offset k ^ par
 };
 
+// The cell's 8 vertices (the trilinear interpolation of the hash grids, Sec. 4.2), stored by
+// coordinate parity: slot k = px + 2 py + 4 pz holds the vertex whose x, y, z coordinates have
+// parities px, py, pz.  Along each axis a cell's two vertices have opposite parity, so each
+// slot is filled once, and two cells that share a vertex hold it in the same slot.  Slots k
+// and k ^ 1 are the two x-adjacent vertices, the even-x one in the even slot.
 __device__ __forceinline__ void level_corners(const FieldDev& F, int l, float3 x, Corners& c) {
   const int res = F.res[l];
   const bool dense = (F.dense_mask >> l) & 1u;
   const uint32_t tmask = (1u << F.log2T) - 1u;
   float fx, fy, fz;
   const int cx = level_cell(x.x, res, fx), cy = level_cell(x.y, res, fy), cz = level_cell(x.z, res, fz);
-  const float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
+  c.par = (uint32_t)((cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2));
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int bx = k & 1, by = (k >> 1) & 1, bz = (k >> 2) & 1;
+    // offset of slot k's vertex from the cell's lower corner, per axis
+    const int bx = (k & 1) ^ (cx & 1), by = ((k >> 1) & 1) ^ (cy & 1), bz = ((k >> 2) & 1) ^ (cz & 1);
     c.idx[k] = vertex_index((uint32_t)(cx + bx), (uint32_t)(cy + by), (uint32_t)(cz + bz), res, dense, tmask);
-    c.w[k] = (wx[bx] * wy[by]) * wz[bz];
+    const float wx = bx ? fx : 1.0f - fx, wy = by ? fy : 1.0f - fy, wz = bz ? fz : 1.0f - fz;
+    c.w[k] = (wx * wy) * wz;
   }
 }
 
 __device__ __forceinline__ float2 level_feature(const FieldDev& F, int l, const Corners& c) {
   const float2* tab = reinterpret_cast<const float2*>(F.tables) + ((size_t)l << F.log2T);
   float2 e[8];
-  // the two corners that differ in x share one 16-byte load when their slots are an
-  // aligned adjacent pair
+  // the two x-adjacent vertices share one 16-byte load when the even-x one's table slot is
+  // even and the odd-x one's follows it
 #pragma unroll
   for (int k = 0; k < 8; k += 2) {
     const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
@@ -52,12 +61,12 @@ __device__ __forceinline__ float2 level_feature(const FieldDev& F, int l, const 
   return make_float2(f0, f1);
 }
 
-// Warp-aggregated scatter: lanes hold consecutive samples, mostly of one ray, so lanes
-// hitting the same slot form contiguous runs on coarse levels.  A segmented inclusive
-// scan sums each run; the run's last lane issues one atomic for the whole run.  Lanes
-// with nothing to add are run heads that issue nothing.  When no lane continues a run the
-// scan is skipped.
-__device__ __forceinline__ void scatter_runs(float2* table, uint32_t key, bool live, float2 val) {
+// Segmented inclusive scan of val over runs of lanes with equal key: lanes hold consecutive
+// samples, mostly of one ray, so consecutive lanes whose cells share a vertex hold it under
+// the same key (same parity slot).  Lanes with nothing to add are run heads.  When no lane
+// continues a run the scan is skipped.  Returns true on the lane that issues the run's sum
+// (its last live lane).
+__device__ __forceinline__ bool run_sum(uint32_t key, bool live, float2& val) {
   const int lane = threadIdx.x & 31;
   const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
   const bool head = !live || lane == 0 || prev != key;
@@ -75,7 +84,32 @@ __device__ __forceinline__ void scatter_runs(float2* table, uint32_t key, bool l
     }
   }
   const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (live && tail) atomicAdd(table + key, val);
+  return live && tail;
+}
+
+// Warp-aggregated scatter of one sample-level: every slot's runs summed by run_sum, then the
+// issuing lane sends slots k and k ^ 1 as one 16-byte atomic when it issues both and their
+// table slots are the two halves of an aligned pair (i, i ^ 1), else one 8-byte atomic each.
+// All lanes of the warp call it (dead lanes with live = false).
+__device__ __forceinline__ void scatter_runs(float2* table, const Corners& c, bool live, float2 g) {
+  float2 v[8];
+  bool issue[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = make_float2(c.w[k] * g.x, c.w[k] * g.y);
+    issue[k] = run_sum(c.idx[k], live, v[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) {
+    const uint32_t i0 = c.idx[k], i1 = c.idx[k + 1];
+    if (issue[k] && issue[k + 1] && (i0 ^ i1) == 1u) {
+      const float2 lo = (i0 & 1u) ? v[k + 1] : v[k], hi = (i0 & 1u) ? v[k] : v[k + 1];
+      atomicAdd(reinterpret_cast<float4*>(table + (i0 & ~1u)), make_float4(lo.x, lo.y, hi.x, hi.y));
+    } else {
+      if (issue[k]) atomicAdd(table + i0, v[k]);
+      if (issue[k + 1]) atomicAdd(table + i1, v[k + 1]);
+    }
+  }
 }
 
 // Scatter of one sample-level without run summation: the two corners of a cell that differ

@@ -98,9 +98,7 @@ __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan
     }
     float2* gt = reinterpret_cast<float2*>(F.grad_tables) + ((size_t)l << F.log2T);
     if (F.res[l] <= P.agg_res) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        scatter_runs(gt, c.idx[k], live, make_float2(c.w[k] * g.x, c.w[k] * g.y));
+      scatter_runs(gt, c, live, g);
     } else if (live) {
       scatter_pairs(gt, c, g);
     }
@@ -157,8 +155,9 @@ __global__ void __launch_bounds__(256) k_encode_points(const __grid_constant__ F
     feat[(int64_t)(2 * l) * n + i] = f.x;
     feat[(int64_t)(2 * l + 1) * n + i] = f.y;
     if (idx) {
+      // rows by corner offset bx + 2 by + 4 bz from the cell's lower corner
 #pragma unroll
-      for (int k = 0; k < 8; ++k) idx[(int64_t)(l * 8 + k) * n + i] = c.idx[k];
+      for (int k = 0; k < 8; ++k) idx[(int64_t)(l * 8 + (int)(k ^ c.par)) * n + i] = c.idx[k];
     }
   }
 }

@@ -69,13 +69,51 @@ def test_autotune_keeps_parameters(env):
     before = [f.get_params()[:2] for f in fields.values()]
     tune = ctx.autotune(tb)
     assert tune["warp_ctas_per_sm"] in (4, 8, 16) and tune["encode_ctas_per_sm"] in (1, 2, 4, 8)
-    assert tune["encode_bwd_ctas_per_sm"] in (1, 2, 4, 8) and tune["agg_res"] in (0, 64, 256, 1024)
+    assert tune["encode_bwd_ctas_per_sm"] in (1, 2, 4, 8) and tune["agg_res"] in (0, 64, 128, 256, 512, 1024)
     for f, (t0, w0) in zip(fields.values(), before):
         t1, w1, _, _, step = f.get_params()
         assert step == 0 and torch.equal(t0, t1) and torch.equal(w0, w1)
         gt, gw = f.get_grads()
         assert float(gt.abs().max()) == 0.0 and float(gw.abs().max()) == 0.0
     ctx.sync()
+
+
+def test_gradient_scatter_independent_of_aggregation(env):
+    """The hash-grid gradient scatter sums runs of lanes that share a vertex (per parity slot)
+    on levels up to the aggregation resolution and sends every corner on its own above it:
+    table gradients with runs on no level, on coarse levels and on every level agree to
+    FP32 summation-order rounding, and so do the weight gradients."""
+    invr, _ = env
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(10.0, 11.0))
+    ctx = invr.Context(0)
+    tb, fields, keep = make_batches(invr, ctx, tw, invr.INVR_FP32)
+    base = ctx.tune()
+    grads = []
+    for agg in (0, 64, 1 << 20):
+        ctx.set_tune(dict(base, agg_res=agg))
+        for f in fields.values():
+            f.zero_grads()
+        invr.forward_train(ctx, tb)
+        invr.backward(ctx, tb)
+        grads.append([tuple(x.double().cpu().numpy() for x in f.get_grads()) for f in fields.values()])
+    ctx.sync()
+    for other in grads[1:]:
+        for (gt0, gw0), (gt1, gw1) in zip(grads[0], other):
+            assert np.abs(gt0).max() > 0.0
+            np.testing.assert_allclose(gt1, gt0, rtol=1e-4, atol=1e-5 * np.abs(gt0).max())
+            np.testing.assert_allclose(gw1, gw0, rtol=1e-4, atol=1e-5 * np.abs(gw0).max())
+
+
+def test_set_tune_validates(env):
+    invr, _ = env
+    ctx = invr.Context(0)
+    t = ctx.tune()
+    for bad in (dict(t, warp_ctas_per_sm=0), dict(t, encode_ctas_per_sm=33), dict(t, agg_res=-1)):
+        with pytest.raises(invr.InvrError):
+            ctx.set_tune(bad)
+    assert ctx.tune() == t
+    ctx.set_tune(dict(t, agg_res=512))
+    assert ctx.tune()["agg_res"] == 512
 
 
 def test_reserved_workspace_overflow_is_reported(env):
