@@ -64,8 +64,8 @@ __device__ __forceinline__ float2 level_feature(const FieldDev& F, int l, const 
 // Segmented inclusive scan of val over runs of lanes with equal key: lanes hold consecutive
 // samples, mostly of one ray, so consecutive lanes whose cells share a vertex hold it under
 // the same key (same parity slot).  Lanes with nothing to add are run heads.  When no lane
-// continues a run the scan is skipped.  Returns true on the lane that issues the run's sum
-// (its last live lane).
+// continues a run the scan is skipped, and so is every step longer than the warp's longest
+// run needs.  Returns true on the lane that issues the run's sum (its last live lane).
 __device__ __forceinline__ bool run_sum(uint32_t key, bool live, float2& val) {
   const int lane = threadIdx.x & 31;
   const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
@@ -73,14 +73,19 @@ __device__ __forceinline__ bool run_sum(uint32_t key, bool live, float2& val) {
   const unsigned heads = __ballot_sync(0xffffffffu, head);
   if (heads != 0xffffffffu) {
     const int run_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    // need: bit i set when lanes i-o+1 .. i all continue their run, i.e. lane i takes the
+    // step of stride o (warp-uniform)
+    unsigned need = ~heads;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+      if (need == 0u) break;
       const float x = __shfl_up_sync(0xffffffffu, val.x, o);
       const float y = __shfl_up_sync(0xffffffffu, val.y, o);
       if (lane - o >= run_start) {
         val.x += x;
         val.y += y;
       }
+      need &= need << o;
     }
   }
   const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);

@@ -256,6 +256,24 @@ __device__ __forceinline__ int advance_view(const int32_t* vb, int n_views, int6
 
 __device__ __forceinline__ void flag_status(unsigned* status, unsigned bit) { atomicOr(status, bit); }
 
+// Grid-stride walk over the work items b = chunk * L + l (level fastest) of the encoding
+// kernels, b = blockIdx.x, blockIdx.x + gridDim.x, ..., kept as (chunk, l) so that no step
+// divides.
+struct ItemWalk {
+  int64_t chunk;
+  int l, L, dc, dl;
+  __device__ __forceinline__ explicit ItemWalk(int levels)
+      : chunk(blockIdx.x / levels), l(blockIdx.x % levels), L(levels), dc(gridDim.x / levels), dl(gridDim.x % levels) {}
+  __device__ __forceinline__ void next() {
+    chunk += dc;
+    l += dl;
+    if (l >= L) {
+      l -= L;
+      ++chunk;
+    }
+  }
+};
+
 // 16-bit encoding features of a tensor-core field.  Each 128-sample tile T is the first
 // MMA's A operand [128 x K] (K = mlp_in) in the K-major no-swizzle layout: 16 row groups of
 // 8 samples, K * 16 bytes each.  Row group g of tile T sits at byte g * 4 * S_cap + T * 512

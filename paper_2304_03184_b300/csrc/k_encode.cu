@@ -11,9 +11,10 @@
 // sector.  Features are written feature-major [L*2][S] (coalesced) for FP32 fields, and as
 // the 16-bit MMA operand tiles of the tensor-core MLPs for FP16/BF16 fields.
 //
-// Backward: the same corners receive w_corner * dL/dfeat through float2 atomics into the
-// gradient table (same layout).  On coarse levels, lanes of a warp that hit the same slot
-// are summed first (segmented run reduction) so that one atomic carries the run's sum.
+// Backward: the same corners receive w_corner * dL/dfeat through atomics into the gradient
+// table (same layout).  Corners are held by vertex parity, so consecutive lanes whose cells
+// share a vertex hold it in the same slot; on coarse levels each slot's runs are summed
+// first (segmented warp scan) and one atomic carries a run's sum.
 //
 // Bound: L2 (tables up to 64 MiB per field stay L2-resident) -- 8 x 8 B gathers per
 // sample-level forward, 8 x 8 B atomics backward.
@@ -33,11 +34,11 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, 
   __syncthreads();
   const int64_t S0 = vb[P.view_lo], S = vb[P.view_hi];
   float* feat = static_cast<float*>(P.ws.feat);
-  const int64_t n_items = (S - S0 + 255) / 256 * L;
+  const int64_t n_chunks = (S - S0 + 255) / 256;
   int v = P.view_lo;  // cursor: this thread's samples only increase over its work items
-  for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
-    const int l = (int)(b % L);
-    const int64_t s = S0 + (b / L) * 256 + threadIdx.x;
+  for (ItemWalk w(L); w.chunk < n_chunks; w.next()) {
+    const int l = w.l;
+    const int64_t s = S0 + w.chunk * 256 + threadIdx.x;
     if (s >= S) continue;
     v = advance_view(vb, P.view_hi, s, v);
     const FieldDev& F = P.v[v].field;
@@ -68,12 +69,12 @@ __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan
   __syncthreads();
   const int64_t S0 = vb[P.view_lo], S = vb[P.view_hi];
   const float scale = P.grad_scale;
-  const int64_t n_items = (S - S0 + 255) / 256 * L;
+  const int64_t n_chunks = (S - S0 + 255) / 256;
   int v = P.view_lo;  // cursor: this warp's samples only increase over its work items
   // warps never straddle two views: view ranges are kTile-aligned (S0 too) and a warp is 32
-  for (int64_t b = blockIdx.x; b < n_items; b += gridDim.x) {
-    const int l = (int)(b % L);
-    const int64_t s0 = S0 + (b / L) * 256;
+  for (ItemWalk w(L); w.chunk < n_chunks; w.next()) {
+    const int l = w.l;
+    const int64_t s0 = S0 + w.chunk * 256;
     const int64_t s = s0 + threadIdx.x;
     const int64_t sw = s0 + (threadIdx.x & ~31);
     v = advance_view(vb, P.view_hi, sw, v);
