@@ -270,7 +270,7 @@ def l2_roofline(name, kms_per_launch, S_occ, L, l2):
 # DRAM bytes per step of k_encode_bwd on the batched key-frame workload (both field launches),
 # from the ncu capture summarised in profiles/encode_bwd_keyframe_batch_dram.md; None once the
 # kernel or the workload changes
-TRAFFIC = {("encode_bwd", "keyframe_batch_8frames_x2fields_s128"): 2_496_244_000}
+TRAFFIC = {("encode_bwd", "keyframe_batch_8frames_x2fields_s128"): 2_379_938_176}
 
 
 def roofline(ktime, tw, R, S_occ, peaks, l2=None):
