@@ -261,6 +261,21 @@ def test_render_two_fields_full_size_sampled(env):
     np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
 
 
+def test_render_novel_view_full_size_sampled(env):
+    """The largest render configuration at full size (1280 x 720 rays, up to 192 samples,
+    T = 2^21, 4096 nodes, K = 8), rendered whole in FP32 in one call; sampled rays against
+    the oracle."""
+    w = synth.two_field_render(seed=5, width=1280, height=720, n_samples=192, field_desc=synth.CFG5_FIELD,
+                               n_nodes=4096, K=8)
+    rng = np.random.default_rng(35)
+    sel = np.sort(rng.choice(w.rays.n, 2000, replace=False))
+    rgba, depth, ref = _render_both(env, w, w.views, sel=sel)
+    assert (ref.rgba[3] > 0.1).mean() > 0.05                   # enough sampled rays see a field
+    ok = ~_near_tie(ref)
+    np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=COLOUR_TOL)
+    np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
+
+
 def test_early_termination(env):
     invr, ctx, oracle = env
     w = synth.plain_forward(res=48)
@@ -361,6 +376,23 @@ def _assert_field_grads(gt, gw, ogt, ogw, desc, rtol):
 def test_train_gradients_match_oracle(env):
     invr, ctx, oracle = env
     tw = synth.train_step_workload(n_rays=1536)
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
+    fp = tw.fields[0]
+    gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+    ogt, ogw = ograds[id(ofields[id(fp)])]
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL_WARP)
+
+
+def test_train_full_size_fp32(env):
+    """The training configuration at full size (2^18 rays, 128 samples, T = 2^19, 2048
+    nodes, FP32) in one call: the loss and every gradient tensor against the oracle's."""
+    invr, ctx, oracle = env
+    tw = synth.train_step_workload()
     tb, gfields, ofields, obatches, _ = _train_both(env, tw)
     loss = invr.forward_train(ctx, tb)
     invr.backward(ctx, tb)
