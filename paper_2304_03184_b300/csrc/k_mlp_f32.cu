@@ -2,11 +2,12 @@
 // and color MLP E_c").  Shapes: in (16|32) -> 64 -> 64 -> 16 (ReLU hidden, no biases),
 // sigma = exp(o_0); o_1..o_15 -> 64 (ReLU) -> 3, sigmoid.
 //
-// Persistent CTAs of 256 threads walk 64-sample tiles.  A tile's activations live in
-// shared memory as [units][64 samples] (row stride 65 floats, conflict-free columns);
-// each layer is a small SIMT GEMM in which a thread owns (rows/16) x 4 outputs.  The
-// colour layers are padded to 16-wide (W4 gets a zero column for o_0, W5 gets 13 zero
-// rows) so every dimension is a multiple of 16.
+// Persistent CTAs of 256 threads walk 128-sample tiles.  A tile's activations live in
+// shared memory as [units][128 samples] (row stride 132 floats: rows stay 16-byte aligned);
+// each layer is a small SIMT GEMM in which a thread owns (rows/16) x 8 outputs: two runs
+// of 4 samples, read as two float4 per input row, so a 64-row layer does 32 FMAs per three
+// 16-byte shared loads.  The colour layers are padded to 16-wide (W4 gets a zero
+// column for o_0, W5 gets 13 zero rows) so every dimension is a multiple of 16.
 //
 // Backward (per tile): the forward activations are recomputed from the stored encoding
 // features, then deltas flow back layer by layer (in place over the activations), and the
@@ -20,8 +21,8 @@ namespace invr {
 
 namespace {
 
-constexpr int kTS = 64;    // samples per tile
-constexpr int kLD = 65;    // activation row stride
+constexpr int kTS = 128;   // samples per tile
+constexpr int kLD = 132;   // activation row stride (floats; a multiple of 4)
 constexpr int kThreads = 256;
 
 struct MlpArgs {
@@ -86,101 +87,146 @@ __device__ void load_weights(const float* __restrict__ W, int in, float* Wt, flo
   }
 }
 
-// Y[o][s] = act(sum_k Wt[k][o] X[k][s]); thread owns rows og*R..og*R+R-1, samples sg+16c.
+// R consecutive floats of a shared-memory row (R = 1, 2 or 4; 4 R-byte aligned).
+template <int R>
+__device__ __forceinline__ void load_r(const float* p, float (&w)[R]) {
+  if constexpr (R == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+  } else if constexpr (R == 2) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    w[0] = q.x; w[1] = q.y;
+  } else {
+    w[0] = *p;
+  }
+}
+
+// A thread's 8 samples of a tile: 4 sg .. 4 sg + 3 and 64 + 4 sg .. 64 + 4 sg + 3, so that
+// the 16 sample groups of a warp read 256 contiguous bytes per float4 (no bank conflicts).
+__device__ __forceinline__ int sample_of(int sg, int c) { return (c < 4 ? 4 * sg : 64 + 4 * sg) + (c & 3); }
+
+__device__ __forceinline__ void load8(const float* row, int sg, float (&x)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(row + 4 * sg);
+  const float4 b = *reinterpret_cast<const float4*>(row + 64 + 4 * sg);
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+
+__device__ __forceinline__ void store8(float* row, int sg, const float (&v)[8]) {
+  *reinterpret_cast<float4*>(row + 4 * sg) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(row + 64 + 4 * sg) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// Y[o][s] = act(sum_k Wt[k][o] X[k][s]); thread owns rows og*R..og*R+R-1 and the 8 samples
+// sample_of(sg, 0..7).
 template <int OUT, int IN, bool RELU>
 __device__ __forceinline__ void layer_fwd(const float* __restrict__ Wt, const float* __restrict__ X, float* Y) {
   constexpr int R = OUT / 16;
   const int og = threadIdx.x >> 4, sg = threadIdx.x & 15;
-  float acc[R][4];
+  float acc[R][8];
 #pragma unroll
   for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+    for (int c = 0; c < 8; ++c) acc[a][c] = 0.0f;
 #pragma unroll 4
   for (int k = 0; k < IN; ++k) {
-    float x[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) x[c] = X[k * kLD + sg + 16 * c];
-    float w[R];
-    if constexpr (R == 4) {
-      const float4 w4 = *reinterpret_cast<const float4*>(Wt + k * OUT + og * 4);
-      w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
-    } else {
-#pragma unroll
-      for (int a = 0; a < R; ++a) w[a] = Wt[k * OUT + og * R + a];
-    }
+    float x[8], w[R];
+    load8(X + k * kLD, sg, x);
+    load_r<R>(Wt + k * OUT + og * R, w);
 #pragma unroll
     for (int a = 0; a < R; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(w[a], x[c], acc[a][c]);
+      for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(w[a], x[c], acc[a][c]);
   }
 #pragma unroll
-  for (int a = 0; a < R; ++a)
+  for (int a = 0; a < R; ++a) {
+    float v[8];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) Y[(og * R + a) * kLD + sg + 16 * c] = RELU ? fmaxf(acc[a][c], 0.0f) : acc[a][c];
+    for (int c = 0; c < 8; ++c) v[c] = RELU ? fmaxf(acc[a][c], 0.0f) : acc[a][c];
+    store8(Y + (og * R + a) * kLD, sg, v);
+  }
 }
 
 // dX[k][s] = (sum_o W[o][k] dY[o][s]) masked by (M[k][s] > 0); W in [OUT][IN] layout.
-// Output to shared memory (stride kLD) or, if G != null, to global G[k*ld + s].
+// Output to shared memory (stride kLD) or, if G != null, to global G[k*ld + s] (s < valid).
+// dX may be M itself: each element's mask is read by the thread that then writes it.
 template <int OUT, int IN, bool MASK>
 __device__ __forceinline__ void layer_bwd_in(const float* __restrict__ Wn, const float* __restrict__ dY, float* dX,
                                              const float* M, float* G, int64_t ld, int valid) {
   constexpr int R = IN / 16;
   const int kg = threadIdx.x >> 4, sg = threadIdx.x & 15;
-  float acc[R][4];
+  float acc[R][8];
 #pragma unroll
   for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+    for (int c = 0; c < 8; ++c) acc[a][c] = 0.0f;
 #pragma unroll 4
   for (int o = 0; o < OUT; ++o) {
-    float y[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) y[c] = dY[o * kLD + sg + 16 * c];
-    float w[R];
-    if constexpr (R == 4) {
-      const float4 w4 = *reinterpret_cast<const float4*>(Wn + o * IN + kg * 4);
-      w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
-    } else {
-#pragma unroll
-      for (int a = 0; a < R; ++a) w[a] = Wn[o * IN + kg * R + a];
-    }
+    float y[8], w[R];
+    load8(dY + o * kLD, sg, y);
+    load_r<R>(Wn + o * IN + kg * R, w);
 #pragma unroll
     for (int a = 0; a < R; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(w[a], y[c], acc[a][c]);
+      for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(w[a], y[c], acc[a][c]);
   }
 #pragma unroll
-  for (int a = 0; a < R; ++a)
+  for (int a = 0; a < R; ++a) {
+    const int k = kg * R + a;
+    float v[8];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int k = kg * R + a, s = sg + 16 * c;
-      float v = acc[a][c];
-      if (MASK && !(M[k * kLD + s] > 0.0f)) v = 0.0f;
-      if (G) {
-        if (s < valid) G[(int64_t)k * ld + s] = v;
-      } else {
-        dX[k * kLD + s] = v;
-      }
+    for (int c = 0; c < 8; ++c) v[c] = acc[a][c];
+    if (MASK) {
+      float m[8];
+      load8(M + k * kLD, sg, m);
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (!(m[c] > 0.0f)) v[c] = 0.0f;
     }
+    if (G) {
+      // G + k ld is 16-byte aligned: ld and the tile start are multiples of 128 samples
+      float* g = G + (int64_t)k * ld;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int s = sample_of(sg, 4 * h);
+        if (s + 4 <= valid) {
+          *reinterpret_cast<float4*>(g + s) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (s + c < valid) g[s + c] = v[4 * h + c];
+        }
+      }
+    } else {
+      store8(dX + k * kLD, sg, v);
+    }
+  }
 }
 
-// acc[i][j] += sum_s dY[i][s] X[j][s]; thread owns rows ig*RI+a, columns jg+16c.
+// acc[i][j] += sum_s dY[i][s] X[j][s]; thread owns rows ig*RI+a, columns jg+16c; the
+// samples in order, 4 per step (one float4 per row).
 template <int OUT, int IN>
 __device__ __forceinline__ void acc_dw(const float* __restrict__ dY, const float* __restrict__ X, float* acc) {
   constexpr int RI = OUT / 16, CJ = IN / 16;
   const int ig = threadIdx.x >> 4, jg = threadIdx.x & 15;
 #pragma unroll 2
-  for (int s = 0; s < kTS; ++s) {
-    float y[RI], x[CJ];
+  for (int s = 0; s < kTS; s += 4) {
+    float4 y[RI], x[CJ];
 #pragma unroll
-    for (int a = 0; a < RI; ++a) y[a] = dY[(ig * RI + a) * kLD + s];
+    for (int a = 0; a < RI; ++a) y[a] = *reinterpret_cast<const float4*>(dY + (ig * RI + a) * kLD + s);
 #pragma unroll
-    for (int c = 0; c < CJ; ++c) x[c] = X[(jg + 16 * c) * kLD + s];
+    for (int c = 0; c < CJ; ++c) x[c] = *reinterpret_cast<const float4*>(X + (jg + 16 * c) * kLD + s);
 #pragma unroll
     for (int a = 0; a < RI; ++a)
 #pragma unroll
-      for (int c = 0; c < CJ; ++c) acc[a * CJ + c] = fmaf(y[a], x[c], acc[a * CJ + c]);
+      for (int c = 0; c < CJ; ++c) {
+        float t = acc[a * CJ + c];
+        t = fmaf(y[a].x, x[c].x, t);
+        t = fmaf(y[a].y, x[c].y, t);
+        t = fmaf(y[a].z, x[c].z, t);
+        t = fmaf(y[a].w, x[c].w, t);
+        acc[a * CJ + c] = t;
+      }
   }
 }
 
@@ -223,19 +269,50 @@ __device__ __forceinline__ int tile_valid(const MlpArgs& A, int64_t s0) {
   return rem < kTS ? (int)rem : kTS;
 }
 
-template <int IN>
-__device__ void load_x(const MlpArgs& A, int64_t s0, int valid, float* X) {
-  for (int e = threadIdx.x; e < IN * kTS; e += blockDim.x) {
-    const int k = e / kTS, s = e % kTS;
-    X[k * kLD + s] = s < valid ? A.feat[(int64_t)k * A.ld + s0 + s] : 0.0f;
-  }
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid; src is then not read).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most `pending` (0 or 1) of this thread's copy groups are in flight.
+__device__ __forceinline__ void cp_async_wait(int pending) {
+  if (pending) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// The tile's inputs, staged asynchronously (one copy group per tile, issued a tile ahead):
+// X [in][kTS] (zero past `valid`) and, for the backward, dL/d(outputs) [4][kTS] and the
+// padding markers [kTS].
+__device__ void stage_inputs(const MlpArgs& A, int64_t s0, int in, float* X, float* Dp, int32_t* Rp) {
+  const int valid = tile_valid(A, s0);
+  for (int e = threadIdx.x; e < in * kTS; e += kThreads) {
+    const int k = e / kTS, s = e % kTS;
+    cp_async4(X + k * kLD + s, s < valid ? A.feat + (int64_t)k * A.ld + s0 + s : A.feat, s < valid);
+  }
+  if (Dp) {
+    for (int e = threadIdx.x; e < 4 * kTS; e += kThreads) {
+      const int i = e / kTS, s = e % kTS;
+      cp_async4(Dp + i * kTS + s, s < valid ? A.dout + (int64_t)i * A.ld + s0 + s : A.dout, s < valid);
+    }
+    if (A.s_ray)
+      for (int s = threadIdx.x; s < kTS; s += kThreads)
+        cp_async4(Rp + s, s < valid ? A.s_ray + s0 + s : A.s_ray, s < valid);
+  }
+  cp_async_commit();
+}
+
+// The next tile of this CTA from `t` on (steps of gridDim.x) whose field runs in FP32.
+__device__ __forceinline__ int64_t next_f32_tile(const MlpArgs& A, int64_t t, int64_t n_tiles) {
+  for (; t < n_tiles; t += gridDim.x)
+    if (A.f[tile_view(A, t * kTS)].mlp_kind == kMlpF32) return t;
+  return n_tiles;
+}
+
+// X staged (and visible to every thread) on entry.
 template <int IN>
 __device__ __forceinline__ void tile_forward(const MlpArgs& A, int64_t s0, int valid, const float* Wt, float* X, float* H1, float* H2,
                              float* O, float* Z) {
-  load_x<IN>(A, s0, valid, X);
-  __syncthreads();
   layer_fwd<64, IN, true>(Wt + kW1, X, H1);
   __syncthreads();
   layer_fwd<64, 64, true>(Wt + kW2, H1, H2);
@@ -258,38 +335,45 @@ __device__ __forceinline__ void tile_forward(const MlpArgs& A, int64_t s0, int v
 __global__ void __launch_bounds__(kThreads) k_mlp_fwd_f32(const __grid_constant__ MlpArgs A) {
   extern __shared__ float sm[];
   float* Wt = sm;
-  float* X = Wt + kWSize;
-  float* H1 = X + 32 * kLD;
+  float* const X0 = Wt + kWSize;  // double-buffered inputs X0, X1
+  float* const X1 = X0 + 32 * kLD;
+  float* H1 = X1 + 32 * kLD;
   float* H2 = H1 + 64 * kLD;
   float* O = H2 + 64 * kLD;
   float* Z = O + 16 * kLD;
   int64_t n_tiles;
   tile_range(A, n_tiles);
   const float* loaded = nullptr;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  int64_t t = next_f32_tile(A, blockIdx.x, n_tiles);
+  if (t < n_tiles) stage_inputs(A, t * kTS, A.f[tile_view(A, t * kTS)].mlp_in, X0, nullptr, nullptr);
+  for (int buf = 0; t < n_tiles; buf ^= 1) {
     const int64_t s0 = t * kTS;
     const FieldDev& F = A.f[tile_view(A, s0)];
-    if (F.mlp_kind != kMlpF32) continue;  // mixed-precision fields run on the tensor cores
+    const int64_t tn = next_f32_tile(A, t + gridDim.x, n_tiles);
+    float* const X = buf ? X1 : X0;
+    // the other buffer was last read by the previous tile, which ended with a barrier
+    if (tn < n_tiles) stage_inputs(A, tn * kTS, A.f[tile_view(A, tn * kTS)].mlp_in, buf ? X0 : X1, nullptr, nullptr);
     if (F.weights != loaded) {
       __syncthreads();
       load_weights(F.weights, F.mlp_in, Wt, nullptr);
       loaded = F.weights;
-      __syncthreads();
     }
+    cp_async_wait(tn < n_tiles ? 1 : 0);
+    __syncthreads();
     const int valid = tile_valid(A, s0);
     if (F.mlp_in == 16)
       tile_forward<16>(A, s0, valid, Wt, X, H1, H2, O, Z);
     else
       tile_forward<32>(A, s0, valid, Wt, X, H1, H2, O, Z);
+    t = tn;
   }
 }
 
+// X, Dp (dL/d(outputs)) and Rp (padding markers) staged and visible on entry.
 template <int IN>
 __device__ __forceinline__ void tile_backward(const MlpArgs& A, int64_t s0, int valid, const float* Wt, const float* Wn, float* X,
-                              float* H1, float* H2, float* H4, float* O, float* D, float* acc1, float* acc2,
-                              float* acc3, float* acc4, float* acc5) {
-  load_x<IN>(A, s0, valid, X);
-  __syncthreads();
+                              const float* Dp, const int32_t* Rp, float* H1, float* H2, float* H4, float* O, float* D,
+                              float* acc1, float* acc2, float* acc3, float* acc4, float* acc5) {
   layer_fwd<64, IN, true>(Wt + kW1, X, H1);
   __syncthreads();
   layer_fwd<64, 64, true>(Wt + kW2, H1, H2);
@@ -301,7 +385,7 @@ __device__ __forceinline__ void tile_backward(const MlpArgs& A, int64_t s0, int 
   for (int e = threadIdx.x; e < 16 * kTS; e += blockDim.x) {
     const int i = e / kTS, s = e % kTS;
     float v = 0.0f;
-    if (i < 3 && s < valid && (!A.s_ray || A.s_ray[s0 + s] >= 0)) v = A.dout[(int64_t)(1 + i) * A.ld + s0 + s] * A.grad_scale;
+    if (i < 3 && s < valid && (!A.s_ray || Rp[s] >= 0)) v = Dp[(1 + i) * kTS + s] * A.grad_scale;
     D[i * kLD + s] = v;
   }
   __syncthreads();
@@ -315,7 +399,7 @@ __device__ __forceinline__ void tile_backward(const MlpArgs& A, int64_t s0, int 
   __syncthreads();
   for (int s = threadIdx.x; s < kTS; s += blockDim.x) {
     float v = 0.0f;
-    if (s < valid && (!A.s_ray || A.s_ray[s0 + s] >= 0)) v = A.dout[s0 + s] * A.grad_scale;
+    if (s < valid && (!A.s_ray || Rp[s] >= 0)) v = Dp[s] * A.grad_scale;
     D[s] = v;  // row 0: dL/do_0 (the colour MLP does not read o_0)
   }
   __syncthreads();
@@ -348,12 +432,17 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_f32(const __grid_constant_
   extern __shared__ float sm[];
   float* Wt = sm;
   float* Wn = Wt + kWSize;
-  float* X = Wn + kWSize;
-  float* H1 = X + 32 * kLD;
+  float* const X0 = Wn + kWSize;  // double-buffered inputs: X, dL/d(outputs), padding markers
+  float* const X1 = X0 + 32 * kLD;
+  float* H1 = X1 + 32 * kLD;
   float* H2 = H1 + 64 * kLD;
   float* H4 = H2 + 64 * kLD;
   float* O = H4 + 64 * kLD;
   float* D = O + 16 * kLD;
+  float* const D0 = D + 16 * kLD;
+  float* const D1 = D0 + 4 * kTS;
+  int32_t* const R0 = reinterpret_cast<int32_t*>(D1 + 4 * kTS);
+  int32_t* const R1 = R0 + kTS;
   float acc1[8], acc2[16], acc3[4], acc4[4], acc5[4];
 #pragma unroll
   for (int i = 0; i < 8; ++i) acc1[i] = 0.0f;
@@ -364,29 +453,41 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_f32(const __grid_constant_
   int64_t n_tiles;
   tile_range(A, n_tiles);
   int cur = -1;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  int64_t t = next_f32_tile(A, blockIdx.x, n_tiles);
+  if (t < n_tiles) stage_inputs(A, t * kTS, A.f[tile_view(A, t * kTS)].mlp_in, X0, D0, R0);
+  for (int buf = 0; t < n_tiles; buf ^= 1) {
     const int64_t s0 = t * kTS;
     const int v = tile_view(A, s0);
     const FieldDev& F = A.f[v];
-    if (F.mlp_kind != kMlpF32) continue;  // mixed-precision fields train on the tensor cores
+    const int64_t tn = next_f32_tile(A, t + gridDim.x, n_tiles);
+    float* const X = buf ? X1 : X0;
+    const float* const Dp = buf ? D1 : D0;
+    const int32_t* const Rp = buf ? R1 : R0;
+    // the other buffers were last read by the previous tile, which ended with a barrier
+    if (tn < n_tiles)
+      stage_inputs(A, tn * kTS, A.f[tile_view(A, tn * kTS)].mlp_in, buf ? X0 : X1, buf ? D0 : D1, buf ? R0 : R1);
     if (cur < 0 || F.weights != A.f[cur].weights) {
       if (cur >= 0) flush_all(acc1, acc2, acc3, acc4, acc5, A.f[cur]);
       __syncthreads();
       load_weights(F.weights, F.mlp_in, Wt, Wn);
       cur = v;
-      __syncthreads();
     }
+    cp_async_wait(tn < n_tiles ? 1 : 0);
+    __syncthreads();
     const int valid = tile_valid(A, s0);
     if (F.mlp_in == 16)
-      tile_backward<16>(A, s0, valid, Wt, Wn, X, H1, H2, H4, O, D, acc1, acc2, acc3, acc4, acc5);
+      tile_backward<16>(A, s0, valid, Wt, Wn, X, Dp, Rp, H1, H2, H4, O, D, acc1, acc2, acc3, acc4, acc5);
     else
-      tile_backward<32>(A, s0, valid, Wt, Wn, X, H1, H2, H4, O, D, acc1, acc2, acc3, acc4, acc5);
+      tile_backward<32>(A, s0, valid, Wt, Wn, X, Dp, Rp, H1, H2, H4, O, D, acc1, acc2, acc3, acc4, acc5);
+    t = tn;
   }
   if (cur >= 0) flush_all(acc1, acc2, acc3, acc4, acc5, A.f[cur]);
 }
 
-constexpr size_t kFwdSmem = (size_t)(kWSize + 32 * kLD + 64 * kLD * 2 + 16 * kLD * 2) * sizeof(float);
-constexpr size_t kBwdSmem = (size_t)(2 * kWSize + 32 * kLD + 64 * kLD * 3 + 16 * kLD * 2) * sizeof(float);
+constexpr size_t kFwdSmem = (size_t)(kWSize + 2 * 32 * kLD + 64 * kLD * 2 + 16 * kLD * 2) * sizeof(float);
+constexpr size_t kBwdSmem =
+    (size_t)(2 * kWSize + 2 * 32 * kLD + 64 * kLD * 3 + 16 * kLD * 2 + 2 * 4 * kTS + 2 * kTS) * sizeof(float);
+static_assert(kBwdSmem <= 227 * 1024, "backward fits one CTA per SM");
 
 MlpArgs plan_args(const Plan& P) {
   MlpArgs A{};
@@ -406,9 +507,11 @@ MlpArgs plan_args(const Plan& P) {
 
 }  // namespace
 
+// One CTA per SM (135 KB of shared memory forward, 204 KB backward): persistent grids of
+// num_sms CTAs.
 cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s) {
   cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(plan_args(P));
+  k_mlp_fwd_f32<<<num_sms, kThreads, kFwdSmem, s>>>(plan_args(P));
   return cudaGetLastError();
 }
 
@@ -429,7 +532,7 @@ cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* fea
   A.grad_scale = 1.0f;
   A.f[0] = f;
   cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  if (n > 0) k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(A);
+  if (n > 0) k_mlp_fwd_f32<<<num_sms, kThreads, kFwdSmem, s>>>(A);
   return cudaGetLastError();
 }
 
