@@ -47,6 +47,7 @@ struct invr_field_s {
   float* m = nullptr;
   float* v = nullptr;
   int64_t* step = nullptr;  // device step counter
+  float* wt = nullptr;      // [kWtF32] the FP32 MLP's transposed weights (scratch of its forward)
   int res[kMaxL] = {};
   uint32_t dense_mask = 0;
 };
@@ -280,7 +281,7 @@ DeformDev deform_dev(invr_ctx ctx, invr_deform d, const float* pose, int view) {
   D.pose_bias = ctx->pose_bias + (int64_t)view * kDeformMaxHidden;
   D.enc.tables = d->params;
   D.enc.weights = nullptr;
-  D.enc.weights_lp = nullptr;
+  D.enc.wt_f32 = nullptr;
   D.enc.grad_tables = d->grads;
   D.enc.grad_weights = nullptr;
   D.enc.L = q.L;
@@ -302,7 +303,7 @@ FieldDev field_dev(invr_field f) {
   FieldDev F{};
   F.tables = f->params;
   F.weights = f->params + f->n_tab;
-  F.weights_lp = nullptr;
+  F.wt_f32 = f->wt;
   F.grad_tables = f->grads;
   F.grad_weights = f->grads + f->n_tab;
   F.L = f->desc.L;
@@ -853,8 +854,9 @@ invr_status invr_field_create(invr_ctx ctx, const invr_field_desc* desc, invr_fi
   }
   const int64_t n = f->n_tab + f->n_w;
   if (dmalloc(&f->params, n) != cudaSuccess || dmalloc(&f->grads, n) != cudaSuccess ||
-      dmalloc(&f->m, n) != cudaSuccess || dmalloc(&f->v, n) != cudaSuccess || dmalloc(&f->step, 1) != cudaSuccess) {
-    dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step);
+      dmalloc(&f->m, n) != cudaSuccess || dmalloc(&f->v, n) != cudaSuccess || dmalloc(&f->step, 1) != cudaSuccess ||
+      dmalloc(&f->wt, kWtF32) != cudaSuccess) {
+    dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step); dfree(f->wt);
     delete f;
     return fail(ctx, INVR_E_OOM, "field allocation failed");
   }
@@ -871,7 +873,7 @@ invr_status invr_field_destroy(invr_field f) {
   if (!f) return INVR_E_ARG;
   DeviceGuard guard(f->ctx->device);
   cudaDeviceSynchronize();
-  dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step);
+  dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step); dfree(f->wt);
   delete f;
   return INVR_OK;
 }

@@ -12,6 +12,7 @@ namespace invr {
 
 constexpr int kMaxViews = 16;   // batches per call (8 key frames x 2 fields)
 constexpr int kMaxL = 16;       // hash levels
+constexpr int kWtF32 = 9216;    // floats of the FP32 MLP's padded transposed weights
 constexpr int kF = 2;           // features per level
 constexpr int kMaxIn = kMaxL * kF;
 constexpr int kHidden = 64;
@@ -36,7 +37,8 @@ enum MlpKind : int { kMlpF32 = 0, kMlpF16 = 1, kMlpBF16 = 2 };
 struct FieldDev {
   const float* tables;      // [L][T][F]
   const float* weights;     // W1..W5 FP32, row-major [out][in]
-  const void* weights_lp;   // packed 16-bit weights for the tensor-core MLP (or null)
+  float* wt_f32;            // [9216]: the FP32 MLP's padded weights, transposed per layer (written
+                            // by each FP32 forward launch from `weights`), or null
   float* grad_tables;       // [L][T][F]
   float* grad_weights;      // W1..W5
   int L, log2T, mlp_in, mlp_kind;

@@ -101,6 +101,20 @@ __device__ __forceinline__ void load_r(const float* p, float (&w)[R]) {
   }
 }
 
+// R consecutive floats of a global-memory row through the read-only path (same alignment).
+template <int R>
+__device__ __forceinline__ void ldg_r(const float* p, float (&w)[R]) {
+  if constexpr (R == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+  } else if constexpr (R == 2) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+    w[0] = q.x; w[1] = q.y;
+  } else {
+    w[0] = __ldg(p);
+  }
+}
+
 // A thread's 8 samples of a tile: 4 sg .. 4 sg + 3 and 64 + 4 sg .. 64 + 4 sg + 3, so that
 // the 16 sample groups of a warp read 256 contiguous bytes per float4 (no bank conflicts).
 __device__ __forceinline__ int sample_of(int sg, int c) { return (c < 4 ? 4 * sg : 64 + 4 * sg) + (c & 3); }
@@ -119,7 +133,8 @@ __device__ __forceinline__ void store8(float* row, int sg, const float (&v)[8]) 
 
 // Y[o][s] = act(sum_k Wt[k][o] X[k][s]); thread owns rows og*R..og*R+R-1 and the 8 samples
 // sample_of(sg, 0..7).
-template <int OUT, int IN, bool RELU>
+// Wt in shared memory, or in global memory (GW; L1-resident: every warp reads the same rows).
+template <int OUT, int IN, bool RELU, bool GW = false>
 __device__ __forceinline__ void layer_fwd(const float* __restrict__ Wt, const float* __restrict__ X, float* Y) {
   constexpr int R = OUT / 16;
   const int og = threadIdx.x >> 4, sg = threadIdx.x & 15;
@@ -132,7 +147,10 @@ __device__ __forceinline__ void layer_fwd(const float* __restrict__ Wt, const fl
   for (int k = 0; k < IN; ++k) {
     float x[8], w[R];
     load8(X + k * kLD, sg, x);
-    load_r<R>(Wt + k * OUT + og * R, w);
+    if constexpr (GW)
+      ldg_r<R>(Wt + k * OUT + og * R, w);
+    else
+      load_r<R>(Wt + k * OUT + og * R, w);
 #pragma unroll
     for (int a = 0; a < R; ++a)
 #pragma unroll
@@ -309,19 +327,22 @@ __device__ __forceinline__ int64_t next_f32_tile(const MlpArgs& A, int64_t t, in
   return n_tiles;
 }
 
-// X staged (and visible to every thread) on entry.
+// X staged (and visible to every thread) on entry; Wt (global) the field's transposed
+// weights.  Once layer 1 has read X, its buffer holds O (rows 0..15) and Z (rows 16..31).
 template <int IN>
-__device__ __forceinline__ void tile_forward(const MlpArgs& A, int64_t s0, int valid, const float* Wt, float* X, float* H1, float* H2,
-                             float* O, float* Z) {
-  layer_fwd<64, IN, true>(Wt + kW1, X, H1);
+__device__ __forceinline__ void tile_forward(const MlpArgs& A, int64_t s0, int valid, const float* Wt, float* X,
+                                             float* H1, float* H2) {
+  float* O = X;
+  float* Z = X + 16 * kLD;
+  layer_fwd<64, IN, true, true>(Wt + kW1, X, H1);
   __syncthreads();
-  layer_fwd<64, 64, true>(Wt + kW2, H1, H2);
+  layer_fwd<64, 64, true, true>(Wt + kW2, H1, H2);
   __syncthreads();
-  layer_fwd<16, 64, false>(Wt + kW3, H2, O);
+  layer_fwd<16, 64, false, true>(Wt + kW3, H2, O);
   __syncthreads();
-  layer_fwd<64, 16, true>(Wt + kW4, O, H1);  // H4 reuses H1
+  layer_fwd<64, 16, true, true>(Wt + kW4, O, H1);  // H4 reuses H1
   __syncthreads();
-  layer_fwd<16, 64, false>(Wt + kW5, H1, Z);
+  layer_fwd<16, 64, false, true>(Wt + kW5, H1, Z);
   __syncthreads();
   if (threadIdx.x < kTS && (int)threadIdx.x < valid) {
     const int s = threadIdx.x;
@@ -332,18 +353,16 @@ __device__ __forceinline__ void tile_forward(const MlpArgs& A, int64_t s0, int v
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_mlp_fwd_f32(const __grid_constant__ MlpArgs A) {
+// Two CTAs per SM (99 KB of shared memory each): the weights are read from the field's
+// transposed copy in global memory (L1-resident) instead of being staged per CTA.
+__global__ void __launch_bounds__(kThreads, 2) k_mlp_fwd_f32(const __grid_constant__ MlpArgs A) {
   extern __shared__ float sm[];
-  float* Wt = sm;
-  float* const X0 = Wt + kWSize;  // double-buffered inputs X0, X1
+  float* const X0 = sm;  // double-buffered inputs X0, X1
   float* const X1 = X0 + 32 * kLD;
   float* H1 = X1 + 32 * kLD;
   float* H2 = H1 + 64 * kLD;
-  float* O = H2 + 64 * kLD;
-  float* Z = O + 16 * kLD;
   int64_t n_tiles;
   tile_range(A, n_tiles);
-  const float* loaded = nullptr;
   int64_t t = next_f32_tile(A, blockIdx.x, n_tiles);
   if (t < n_tiles) stage_inputs(A, t * kTS, A.f[tile_view(A, t * kTS)].mlp_in, X0, nullptr, nullptr);
   for (int buf = 0; t < n_tiles; buf ^= 1) {
@@ -353,21 +372,19 @@ __global__ void __launch_bounds__(kThreads) k_mlp_fwd_f32(const __grid_constant_
     float* const X = buf ? X1 : X0;
     // the other buffer was last read by the previous tile, which ended with a barrier
     if (tn < n_tiles) stage_inputs(A, tn * kTS, A.f[tile_view(A, tn * kTS)].mlp_in, buf ? X0 : X1, nullptr, nullptr);
-    if (F.weights != loaded) {
-      __syncthreads();
-      load_weights(F.weights, F.mlp_in, Wt, nullptr);
-      loaded = F.weights;
-    }
     cp_async_wait(tn < n_tiles ? 1 : 0);
     __syncthreads();
     const int valid = tile_valid(A, s0);
     if (F.mlp_in == 16)
-      tile_forward<16>(A, s0, valid, Wt, X, H1, H2, O, Z);
+      tile_forward<16>(A, s0, valid, F.wt_f32, X, H1, H2);
     else
-      tile_forward<32>(A, s0, valid, Wt, X, H1, H2, O, Z);
+      tile_forward<32>(A, s0, valid, F.wt_f32, X, H1, H2);
     t = tn;
   }
 }
+
+// One block: the padded, transposed weights of a field into its global copy Wt.
+__global__ void k_prep_wt(const float* __restrict__ W, int in, float* Wt) { load_weights(W, in, Wt, nullptr); }
 
 // X, Dp (dL/d(outputs)) and Rp (padding markers) staged and visible on entry.
 template <int IN>
@@ -484,7 +501,9 @@ __global__ void __launch_bounds__(kThreads) k_mlp_bwd_f32(const __grid_constant_
   if (cur >= 0) flush_all(acc1, acc2, acc3, acc4, acc5, A.f[cur]);
 }
 
-constexpr size_t kFwdSmem = (size_t)(kWSize + 2 * 32 * kLD + 64 * kLD * 2 + 16 * kLD * 2) * sizeof(float);
+static_assert(kWSize == kWtF32, "size of the transposed weight copy");
+constexpr size_t kFwdSmem = (size_t)(2 * 32 * kLD + 64 * kLD * 2) * sizeof(float);
+static_assert(2 * (kFwdSmem + 1024) <= 228 * 1024, "two forward CTAs per SM");
 constexpr size_t kBwdSmem =
     (size_t)(2 * kWSize + 2 * 32 * kLD + 64 * kLD * 3 + 16 * kLD * 2 + 2 * 4 * kTS + 2 * kTS) * sizeof(float);
 static_assert(kBwdSmem <= 227 * 1024, "backward fits one CTA per SM");
@@ -507,11 +526,18 @@ MlpArgs plan_args(const Plan& P) {
 
 }  // namespace
 
-// One CTA per SM (135 KB of shared memory forward, 204 KB backward): persistent grids of
-// num_sms CTAs.
+// Persistent grids: two forward CTAs per SM, one backward CTA (221 KB of shared memory).
+// Each FP32 field's transposed weight copy is rewritten before its forward (the weights
+// change with every optimiser step).
 cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s) {
+  for (int v = 0; v < P.n_views; ++v) {
+    const FieldDev& F = P.v[v].field;
+    bool seen = false;
+    for (int u = 0; u < v; ++u) seen = seen || P.v[u].field.weights == F.weights;
+    if (F.mlp_kind == kMlpF32 && !seen) k_prep_wt<<<1, kThreads, 0, s>>>(F.weights, F.mlp_in, F.wt_f32);
+  }
   cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  k_mlp_fwd_f32<<<num_sms, kThreads, kFwdSmem, s>>>(plan_args(P));
+  k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(plan_args(P));
   return cudaGetLastError();
 }
 
@@ -532,7 +558,10 @@ cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* fea
   A.grad_scale = 1.0f;
   A.f[0] = f;
   cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  if (n > 0) k_mlp_fwd_f32<<<num_sms, kThreads, kFwdSmem, s>>>(A);
+  if (n > 0) {
+    k_prep_wt<<<1, kThreads, 0, s>>>(f.weights, f.mlp_in, f.wt_f32);
+    k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(A);
+  }
   return cudaGetLastError();
 }
 
