@@ -103,8 +103,11 @@ typedef struct {
     invr_precision prec;
 } invr_field_desc;
 
-/* Allocates parameters (tables + weights), gradients and Adam moments (zeroed, step 0).
- * Parameters are undefined until invr_field_set_params. */
+/* Allocates parameters (tables + weights), gradients and Adam moments (zeroed, step 0),
+ * and a 36 KB scratch copy of the weights that every FP32 MLP forward on this field
+ * rewrites before use (so two calls that evaluate one FP32 field at the same time on
+ * different streams must not see different weights).  Parameters are undefined until
+ * invr_field_set_params. */
 invr_status invr_field_create(invr_ctx ctx, const invr_field_desc* desc, invr_field* out);
 invr_status invr_field_destroy(invr_field field);
 
