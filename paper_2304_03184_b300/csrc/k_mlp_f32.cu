@@ -133,9 +133,40 @@ __device__ __forceinline__ void store8(float* row, int sg, const float (&v)[8]) 
 
 // Y[o][s] = act(sum_k Wt[k][o] X[k][s]); thread owns rows og*R..og*R+R-1 and the 8 samples
 // sample_of(sg, 0..7).
+// 16-row layers: thread owns rows 4 og .. 4 og + 3 (og = t / 64, uniform per warp) and the
+// samples 2 sg, 2 sg + 1 (sg = t % 64): one float2 of X and one float4 of W per input row
+// for 8 FMAs, where the (rows/16) x 8 mapping would read 8 samples for one row.
+template <int IN, bool RELU, bool GW>
+__device__ __forceinline__ void layer_fwd16(const float* __restrict__ Wt, const float* __restrict__ X, float* Y) {
+  const int og = threadIdx.x >> 6, sg = threadIdx.x & 63;
+  float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+  for (int k = 0; k < IN; ++k) {
+    const float2 x = *reinterpret_cast<const float2*>(X + k * kLD + 2 * sg);
+    float w[4];
+    if constexpr (GW)
+      ldg_r<4>(Wt + k * 16 + og * 4, w);
+    else
+      load_r<4>(Wt + k * 16 + og * 4, w);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a][0] = fmaf(w[a], x.x, acc[a][0]);
+      acc[a][1] = fmaf(w[a], x.y, acc[a][1]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    *reinterpret_cast<float2*>(Y + (og * 4 + a) * kLD + 2 * sg) =
+        RELU ? make_float2(fmaxf(acc[a][0], 0.0f), fmaxf(acc[a][1], 0.0f)) : make_float2(acc[a][0], acc[a][1]);
+}
+
 // Wt in shared memory, or in global memory (GW; L1-resident: every warp reads the same rows).
 template <int OUT, int IN, bool RELU, bool GW = false>
 __device__ __forceinline__ void layer_fwd(const float* __restrict__ Wt, const float* __restrict__ X, float* Y) {
+  if constexpr (OUT == 16) {
+    layer_fwd16<IN, RELU, GW>(Wt, X, Y);
+    return;
+  }
   constexpr int R = OUT / 16;
   const int og = threadIdx.x >> 4, sg = threadIdx.x & 15;
   float acc[R][8];
@@ -168,9 +199,44 @@ __device__ __forceinline__ void layer_fwd(const float* __restrict__ Wt, const fl
 // dX[k][s] = (sum_o W[o][k] dY[o][s]) masked by (M[k][s] > 0); W in [OUT][IN] layout.
 // Output to shared memory (stride kLD) or, if G != null, to global G[k*ld + s] (s < valid).
 // dX may be M itself: each element's mask is read by the thread that then writes it.
+// 16-row outputs (IN = 16, no mask) with the mapping of layer_fwd16: rows 4 kg .. 4 kg + 3,
+// samples 2 sg, 2 sg + 1.
+template <int OUT>
+__device__ __forceinline__ void layer_bwd_in16(const float* __restrict__ Wn, const float* __restrict__ dY, float* dX,
+                                               float* G, int64_t ld, int valid) {
+  const int kg = threadIdx.x >> 6, sg = threadIdx.x & 63;
+  float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+  for (int o = 0; o < OUT; ++o) {
+    const float2 y = *reinterpret_cast<const float2*>(dY + o * kLD + 2 * sg);
+    float w[4];
+    load_r<4>(Wn + o * 16 + kg * 4, w);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a][0] = fmaf(w[a], y.x, acc[a][0]);
+      acc[a][1] = fmaf(w[a], y.y, acc[a][1]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int k = kg * 4 + a, s = 2 * sg;
+    if (G) {
+      float* g = G + (int64_t)k * ld + s;
+      if (s < valid) g[0] = acc[a][0];
+      if (s + 1 < valid) g[1] = acc[a][1];
+    } else {
+      *reinterpret_cast<float2*>(dX + k * kLD + s) = make_float2(acc[a][0], acc[a][1]);
+    }
+  }
+}
+
 template <int OUT, int IN, bool MASK>
 __device__ __forceinline__ void layer_bwd_in(const float* __restrict__ Wn, const float* __restrict__ dY, float* dX,
                                              const float* M, float* G, int64_t ld, int valid) {
+  if constexpr (IN == 16 && !MASK) {
+    layer_bwd_in16<OUT>(Wn, dY, dX, G, ld, valid);
+    return;
+  }
   constexpr int R = IN / 16;
   const int kg = threadIdx.x >> 4, sg = threadIdx.x & 15;
   float acc[R][8];
