@@ -211,8 +211,9 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
   INVR_CUDA(ctx, dmalloc(&w.ray_used, R));
   INVR_CUDA(ctx, dmalloc(&w.ray_out, 5 * R));
   INVR_CUDA(ctx, dmalloc(&w.block_sums, blocks));
-  INVR_CUDA(ctx, dmalloc(&w.view_base, 2 * (kMaxViews + 1)));
+  INVR_CUDA(ctx, dmalloc(&w.view_base, 2 * (kMaxViews + 1) + 6 * kMaxViews));
   w.view_count = w.view_base + kMaxViews + 1;
+  w.occ_box = w.view_base + 2 * (kMaxViews + 1);
   INVR_CUDA(ctx, dmalloc(&w.s_ray, S));
   INVR_CUDA(ctx, dmalloc(&w.s_t, S));
   INVR_CUDA(ctx, dmalloc(&w.s_pos, 3 * S));

@@ -8,7 +8,8 @@
 // mixes two fields.  Padding slots carry s_ray = -1.
 //
 // The count pass records each ray's occupancy bits (word-major, coalesced), so the emit
-// pass visits only the occupied samples instead of re-marching the ray.
+// pass visits only the occupied samples instead of re-marching the ray; it tests only the
+// samples inside the box of the view's occupied cells (k_occ_box, once per call).
 //
 // Bound: HBM reads of the rays (24 B/ray) and bitfield lookups that hit L1/L2 (256 KiB
 // per view); writes 4 B per 32 samples of each ray and 24 B per occupied sample.
@@ -24,10 +25,79 @@ __device__ __forceinline__ void load_ray(const ViewDev& V, int64_t r, float3& o,
   d = make_float3(__ldg(V.d + r), __ldg(V.d + n + r), __ldg(V.d + 2 * n + r));
 }
 
+// One block per view: the index bounds of the view's occupied cells (lo > hi: none; a view
+// without occupancy gets the whole grid).  Bit c of the field is cell (c % 128, c / 128 % 128,
+// c / 128^2), so a 32-bit word covers 32 consecutive x cells of one (y, z) row.
+__global__ void __launch_bounds__(256) k_occ_box(const __grid_constant__ Plan P) {
+  __shared__ int part[8][6];
+  const int v = blockIdx.x;
+  const uint32_t* occ = P.v[v].occ;
+  int b[6] = {kOccRes, kOccRes, kOccRes, -1, -1, -1};
+  if (!occ) {
+    b[0] = b[1] = b[2] = 0;
+    b[3] = b[4] = b[5] = kOccRes - 1;
+  } else {
+    constexpr int kWords = kOccRes * kOccRes * kOccRes / 32;
+    for (int w = threadIdx.x; w < kWords; w += blockDim.x) {
+      const uint32_t m = __ldg(occ + w);
+      if (!m) continue;
+      const int x0 = 32 * (w % (kOccRes / 32)), y = (w / (kOccRes / 32)) % kOccRes, z = w / (kOccRes * kOccRes / 32);
+      b[0] = min(b[0], x0 + __ffs(m) - 1);
+      b[3] = max(b[3], x0 + 31 - __clz(m));
+      b[1] = min(b[1], y);
+      b[4] = max(b[4], y);
+      b[2] = min(b[2], z);
+      b[5] = max(b[5], z);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const int r = a < 3 ? __reduce_min_sync(0xffffffffu, b[a]) : __reduce_max_sync(0xffffffffu, b[a]);
+    if (lane == 0) part[wid][a] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    int r = part[0][a];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = a < 3 ? min(r, part[w][a]) : max(r, part[w][a]);
+    P.ws.occ_box[6 * v + a] = r;
+  }
+}
+
+// The samples j0 .. j1 of a ray (tn, dt) that can lie in the box of occupied cells `b`: the
+// ray's interval inside the box widened by 1e-4 (covering every FP32 rounding of a sample
+// position and its cell) plus one sample on each side.  Outside it no sample is occupied,
+// so skipping those samples changes no result.  Returns false when the ray misses the box.
+__device__ __forceinline__ bool occupied_range(const int32_t* b, float3 o, float3 d, float tn, float dt,
+                                               int n_samples, int& j0, int& j1) {
+  if (b[0] > b[3]) return false;
+  constexpr float kCell = 2.0f / kOccRes, kMargin = 1e-4f;
+  const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  float t0 = -INFINITY, t1 = INFINITY;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float lo = -1.0f + kCell * (float)b[a] - kMargin, hi = -1.0f + kCell * (float)(b[a + 3] + 1) + kMargin;
+    if (dd[a] == 0.0f) {
+      if (oo[a] < lo || oo[a] > hi) return false;
+      continue;
+    }
+    const float ta = (lo - oo[a]) / dd[a], tb = (hi - oo[a]) / dd[a];
+    t0 = fmaxf(t0, fminf(ta, tb));
+    t1 = fminf(t1, fmaxf(ta, tb));
+  }
+  if (!(t0 <= t1)) return false;
+  const float f0 = floorf((t0 - tn) / dt - 0.5f) - 1.0f, f1 = ceilf((t1 - tn) / dt - 0.5f) + 1.0f;
+  j0 = f0 > 0.0f ? (f0 < (float)n_samples ? (int)f0 : n_samples) : 0;
+  j1 = f1 < (float)(n_samples - 1) ? (f1 > -1.0f ? (int)f1 : -1) : n_samples - 1;
+  return j0 <= j1;
+}
+
 __global__ void __launch_bounds__(256) k_march_count(const __grid_constant__ Plan P) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= P.total_rays) return;
-  const ViewDev& V = P.v[view_of_ray(P, g)];
+  const int v = view_of_ray(P, g);
+  const ViewDev& V = P.v[v];
   float3 o, d;
   load_ray(V, g - V.ray_begin, o, d);
   float tn, dt;
@@ -35,16 +105,18 @@ __global__ void __launch_bounds__(256) k_march_count(const __grid_constant__ Pla
   uint32_t* bits = P.ws.ray_bits + g;
   const int64_t R_cap = P.ws.R_cap;
   const int words = (P.n_samples + 31) / 32;
-  const bool hit = ray_box(o, d, P.n_samples, tn, dt);
+  int j0 = 0, j1 = -1;
+  if (ray_box(o, d, P.n_samples, tn, dt)) {
+    if (V.occ)
+      occupied_range(P.ws.occ_box + 6 * v, o, d, tn, dt, P.n_samples, j0, j1);
+    else
+      j1 = P.n_samples - 1;
+  }
   for (int w = 0; w < words; ++w) {
     uint32_t m = 0;
-    if (hit) {
-      const int j1 = min(32, P.n_samples - 32 * w);
-      for (int i = 0; i < j1; ++i) {
-        const int j = 32 * w + i;
-        if (!V.occ || occupied(V.occ, sample_p(o, d, sample_t(tn, dt, j)))) m |= 1u << i;
-      }
-    }
+    const int lo = max(j0, 32 * w), hi = min(j1, 32 * w + 31);
+    for (int j = lo; j <= hi; ++j)
+      if (!V.occ || occupied(V.occ, sample_p(o, d, sample_t(tn, dt, j)))) m |= 1u << (j - 32 * w);
     bits[w * R_cap] = m;
     cnt += __popc(m);
   }
@@ -230,6 +302,7 @@ __global__ void __launch_bounds__(256) k_march_emit(const __grid_constant__ Plan
 }
 
 cudaError_t launch_march_count(const Plan& P, cudaStream_t s) {
+  k_occ_box<<<P.n_views, 256, 0, s>>>(P);
   k_march_count<<<ceil_div(P.total_rays, 256), 256, 0, s>>>(P);
   return cudaGetLastError();
 }

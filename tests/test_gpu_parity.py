@@ -2,6 +2,7 @@
 inputs.  Discrete results (sample positions, occupancy, hash slots, nearest-node ids) must
 match bit for bit on identical FP32 inputs; FP32 colour and opacity within 1e-5 absolute;
 gradients within 1e-3 relative (spec tolerances of the FP32 path)."""
+import dataclasses
 import math
 
 import numpy as np
@@ -315,6 +316,47 @@ def test_edge_cases(env):
     rgba, _ = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), 16, 1e-4, [v])
     assert np.all(host(rgba) == 0)
     ctx.sync()
+
+
+def test_march_box_skips_no_occupied_sample(env):
+    """The march tests only the samples inside the box of a view's occupied cells.  Occupied
+    regions that touch the grid's faces and corners, crossed by oblique rays and by rays
+    parallel to the axes (direction components exactly 0), render as the oracle's full
+    march does."""
+    invr, ctx, oracle = env
+    w = synth.plain_forward(res=24)
+    rng = np.random.default_rng(36)
+    # rays: oblique pinhole rays, and axis-parallel rays on a grid that reaches the faces
+    o, d = [w.rays.o], [w.rays.d]
+    g = np.linspace(-0.999, 0.999, 48)
+    for a in range(3):
+        for sgn in (1.0, -1.0):
+            u, v = np.meshgrid(g, g, indexing="ij")
+            oo = np.zeros((3, u.size))
+            oo[a] = -2.0 * sgn
+            oo[(a + 1) % 3], oo[(a + 2) % 3] = u.ravel(), v.ravel()
+            dd = np.zeros_like(oo)
+            dd[a] = sgn
+            o.append(oo)
+            d.append(dd)
+    rays = synth.Rays(np.concatenate(o, 1).astype(np.float32), np.concatenate(d, 1).astype(np.float32))
+    cells = np.zeros((128, 128, 128), bool)                     # [z][y][x]
+    # a sub-box touching the x = 0 and y = 127 faces, 30% of its cells occupied
+    box = cells.copy()
+    box[10:91, 30:128, 0:41] = rng.random((81, 98, 41)) < 0.3
+    # two solid 4^3 blocks: at the (127, 127, 127) corner and on the x = 0 face
+    blocks = cells.copy()
+    blocks[124:, 124:, 124:] = True
+    blocks[60:64, 60:64, 0:4] = True
+    for mask in (box, blocks):
+        sv = dataclasses.replace(w.views[0], occupancy=synth.pack_bits(mask.ravel()))
+        side = Side(invr, ctx, oracle, sv)
+        rgba, depth = invr.render_rays(ctx, cu(rays.o), cu(rays.d), 64, 1e-4, [side.view])
+        ctx.sync()
+        ref = oracle.render(rays.o, rays.d, 64, 1e-4, [side.oview])
+        assert (ref.rgba[3] > 0.01).sum() > 20                 # rays that cross occupied cells
+        np.testing.assert_allclose(host(rgba), ref.rgba, rtol=0, atol=COLOUR_TOL)
+        np.testing.assert_allclose(host(depth), ref.depth, rtol=COLOUR_TOL, atol=COLOUR_TOL)
 
 
 def test_invalid_arguments_raise(env):
