@@ -23,9 +23,11 @@
 
 namespace invr {
 
-// Work items: (chunk of 256 samples, level) with the level varying fastest, so the blocks
-// that handle the L levels of one chunk run together and read its positions from L2 once
-// (a level-major order streamed every sample's position from DRAM once per level).
+// Work items: (chunk of 256 samples, group of 4 levels) with the group varying fastest, so
+// the blocks that handle the levels of one chunk run together and read its positions from
+// L2 once (a level-major order streamed every sample's position from DRAM once per level).
+// A thread evaluates its sample's 4 levels in turn; for a tensor-core field their 8 16-bit
+// features are one 16-byte row of an operand core matrix, written by one store.
 __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, int L) {
   __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
   const int64_t S_cap = P.ws.S_cap;
@@ -36,27 +38,37 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P, 
   float* feat = static_cast<float*>(P.ws.feat);
   const int64_t n_chunks = (S - S0 + 255) / 256;
   int v = P.view_lo;  // cursor: this thread's samples only increase over its work items
-  for (ItemWalk w(L); w.chunk < n_chunks; w.next()) {
-    const int l = w.l;
+  for (ItemWalk w((L + 3) / 4); w.chunk < n_chunks; w.next()) {
+    const int l0 = 4 * w.l;
     const int64_t s = S0 + w.chunk * 256 + threadIdx.x;
     if (s >= S) continue;
     v = advance_view(vb, P.view_hi, s, v);
     const FieldDev& F = P.v[v].field;
-    if (l >= F.L) continue;
-    float2 f = make_float2(0.0f, 0.0f);
-    if (P.ws.s_ray[s] >= 0) {
-      Corners c;
-      level_corners(F, l, make_float3(P.ws.s_vc[s], P.ws.s_vc[S_cap + s], P.ws.s_vc[2 * S_cap + s]), c);
-      f = level_feature(F, l, c);
+    if (l0 >= F.L) continue;  // F.L is a multiple of 4 (mlp_in = 2 L is 16 or 32)
+    const bool live = P.ws.s_ray[s] >= 0;
+    const float3 x = live ? make_float3(P.ws.s_vc[s], P.ws.s_vc[S_cap + s], P.ws.s_vc[2 * S_cap + s])
+                          : make_float3(0.0f, 0.0f, 0.0f);
+    uint32_t packed[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + j;
+      float2 f = make_float2(0.0f, 0.0f);
+      if (live) {
+        Corners c;
+        level_corners(F, l, x, c);
+        f = level_feature(F, l, c);
+      }
+      if (F.mlp_kind == kMlpF32) {
+        feat[(int64_t)(2 * l) * S_cap + s] = f.x;
+        feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
+      } else {
+        // tensor-core field: the pair as 16-bit operand row s of its tile (rounded to nearest)
+        packed[j] = F.mlp_kind == kMlpBF16 ? tc::pack2<true>(f.x, f.y) : tc::pack2<false>(f.x, f.y);
+      }
     }
-    if (F.mlp_kind == kMlpF32) {
-      feat[(int64_t)(2 * l) * S_cap + s] = f.x;
-      feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
-    } else {
-      // tensor-core field: the pair as 16-bit operand row s of its tile (rounded to nearest)
-      const uint32_t w = F.mlp_kind == kMlpBF16 ? tc::pack2<true>(f.x, f.y) : tc::pack2<false>(f.x, f.y);
-      *reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l)) = w;
-    }
+    if (F.mlp_kind != kMlpF32)
+      *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l0)) =
+          make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
 }
 
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(256) k_encode_bwd(const __grid_constant__ Plan
 cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s) {
   int L = 0;
   for (int v = 0; v < P.n_views; ++v) L = P.v[v].field.L > L ? P.v[v].field.L : L;
-  k_encode<<<num_sms * P.tune.encode_ctas_per_sm * L, 256, 0, s>>>(P, L);
+  k_encode<<<num_sms * P.tune.encode_ctas_per_sm * ((L + 3) / 4), 256, 0, s>>>(P, L);
   return cudaGetLastError();
 }
 
