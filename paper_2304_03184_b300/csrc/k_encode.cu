@@ -3,10 +3,11 @@
 // N_l, the table slots of its 8 corners (dense row-major when (N_l+1)^3 <= T, else the
 // XOR-of-primes spatial hash mod T) and the trilinear blend of their F = 2 features.
 //
-// One thread per (sample, level); a block takes one level of a chunk of 256 consecutive
-// samples, so a warp reads one level's table for 32 consecutive samples of one ray
-// (spatially coherent), and the blocks of a chunk's levels run together (its positions
-// are read from DRAM once, then from L2).  Tables are level-major
+// Forward: one thread per (sample, group of 4 levels); a block takes one group of a chunk of
+// 256 consecutive samples, so a warp reads a level's table for 32 consecutive samples of one
+// ray (spatially coherent), and the blocks of a chunk's groups run together (its positions
+// are read from DRAM once, then from L2).  Backward: one thread per (sample, level), the same
+// order.  Tables are level-major
 // [L][T][2] FP32: each corner is one 8-byte load, and the +x corner pair shares a 32-byte
 // sector.  Features are written feature-major [L*2][S] (coalesced) for FP32 fields, and as
 // the 16-bit MMA operand tiles of the tensor-core MLPs for FP16/BF16 fields.
