@@ -718,9 +718,10 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
   float best_ms = 0.0f;
   invr_status st = measure(best_ms);
   // coordinate descent over the launch shapes
-  const int warp_c[] = {4, 8, 16}, enc_c[] = {1, 2, 4, 8}, agg_c[] = {0, 64, 128, 256, 512, 1024};
+  const int warp_c[] = {4, 8, 16}, enc_c[] = {4, 8, 16, 32}, bwd_c[] = {1, 2, 4, 8},
+            agg_c[] = {0, 64, 128, 256, 512, 1024};
   for (int dim = 0; dim < 4 && st == INVR_OK; ++dim) {
-    const int* cands = dim == 0 ? warp_c : (dim == 3 ? agg_c : enc_c);
+    const int* cands = dim == 0 ? warp_c : dim == 1 ? enc_c : dim == 2 ? bwd_c : agg_c;
     const int n = dim == 0 ? 3 : (dim == 3 ? 6 : 4);
     for (int i = 0; i < n && st == INVR_OK; ++i) {
       Tune t = best;

@@ -130,7 +130,7 @@ struct Workspace {
 // Launch shapes the autotuner chooses: CTAs per SM of the grid-stride kernels.
 struct Tune {
   int warp_ctas_per_sm = 8;
-  int encode_ctas_per_sm = 8;
+  int encode_ctas_per_sm = 32;
   int encode_bwd_ctas_per_sm = 8;
   int agg_res = 128;
 };
