@@ -270,7 +270,7 @@ def l2_roofline(name, kms_per_launch, S_occ, L, l2):
 # DRAM bytes per step of k_encode_bwd on the batched key-frame workload (both field launches),
 # from the ncu capture summarised in profiles/encode_bwd_keyframe_batch_dram.md; None once the
 # kernel or the workload changes
-TRAFFIC = {("encode_bwd", "keyframe_batch_8frames_x2fields_s128"): 2_379_938_176}
+TRAFFIC = {("encode_bwd", "keyframe_batch_8frames_x2fields_s128"): 2_213_654_656}
 
 
 def roofline(ktime, tw, R, S_occ, peaks, l2=None):
@@ -301,18 +301,26 @@ def roofline(ktime, tw, R, S_occ, peaks, l2=None):
     return None
 
 
-def kernel_rooflines(ktime, tw, R, S_occ, peaks):
+def kernel_rooflines(ktime, tw, R, S_occ, peaks, l2=None):
     """Every timed kernel of the step against the roofline that bounds its work: algorithmic
     work per timed record (a step stage over all batches; Adam: one field) -- FLOPs of the
     unpadded MLP layers, or bytes -- over its CUDA-event time,
     as a fraction of the measured peak (HBM copy bandwidth, sustained dense BF16, or the FP32
-    FMA peak derived from the SM count and the maximum SM clock)."""
+    FMA peak derived from the SM count and the maximum SM clock).  The gather and the
+    scatter, whose tables stay in L2, are given against the L2 probe ceilings when measured
+    (table payload per second: lanes that share a vertex are served by one L2 operation, so
+    the ratio can pass 1)."""
     fp = tw.fields[0]
     n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()  # Adam is timed per field
     res = {}
     for name, (kms, kn) in sorted(ktime.items()):
         bound, work = kernel_work(name, R, S_occ, tw.n_samples, fp.desc.L, n_params, fp.desc.n_weight_params())
         if bound is None:
+            continue
+        if name in ("encode", "encode_bwd") and l2:
+            r = l2_roofline(name, kms / kn, S_occ, fp.desc.L, l2)
+            res[name] = {"bound": "l2", **{k: r[k] for k in ("achieved", "peak", "unit", "frac")},
+                         "ms": round(kms / kn, 4)}
             continue
         dur = kms / kn * 1e-3
         if bound == "hbm":
@@ -346,7 +354,7 @@ def apply_batched(out, bt, invr, ctx, args, world, peaks):
                            for k in ("encode", "encode_bwd") if k in bt["ktime"]}
     nsteps = max(5, args.steps // 4)
     out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
-    out["kernel_rooflines"] = kernel_rooflines(bt["ktime"], btw, bR, bS, peaks)
+    out["kernel_rooflines"] = kernel_rooflines(bt["ktime"], btw, bR, bS, peaks, l2)
     per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
     out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
                                     / nsteps * args.steps))
