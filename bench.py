@@ -34,8 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "train samples/s (fwd+bwd) & render Mrays/s, mixed-prec vs FP32 at fixed error"
 UNIT = "samples/s"
-# kernels launched per TIMED record of the library (scan = 3 kernels, composite_train = 2)
-KERNELS_PER_RECORD = {"scan": 3, "composite_train": 2}
+# kernels launched per TIMED record of the library (scan = 3 kernels, composite_train = 2,
+# march_count = 2: the occupied-cell bounds, then the count)
+KERNELS_PER_RECORD = {"scan": 3, "composite_train": 2, "march_count": 2}
 
 
 def parse():
