@@ -172,29 +172,30 @@ cudaError_t launch_encode_bwd_by_field(const Plan& P, int num_sms, cudaStream_t 
 }
 
 // ------------------------------------------------------------------ single step
+// One thread per point over all its levels, in step with its block (as k_encode); FP32
+// features [L*2][n].
 __global__ void __launch_bounds__(256) k_encode_points(const __grid_constant__ FieldDev F, int64_t n,
                                                        const float* __restrict__ x, float* feat, uint32_t* idx) {
-  const int l = blockIdx.y;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    Corners c;
-    level_corners(F, l, make_float3(x[i], x[n + i], x[2 * n + i]), c);
-    const float2 f = level_feature(F, l, c);
-    feat[(int64_t)(2 * l) * n + i] = f.x;
-    feat[(int64_t)(2 * l + 1) * n + i] = f.y;
-    if (idx) {
-      // rows by corner offset bx + 2 by + 4 bz from the cell's lower corner
+    const float3 p = make_float3(x[i], x[n + i], x[2 * n + i]);
+    for (int l = 0; l < F.L; ++l) {
+      Corners c;
+      level_corners(F, l, p, c);
+      const float2 f = level_feature(F, l, c);
+      feat[(int64_t)(2 * l) * n + i] = f.x;
+      feat[(int64_t)(2 * l + 1) * n + i] = f.y;
+      if (idx) {
+        // rows by corner offset bx + 2 by + 4 bz from the cell's lower corner
 #pragma unroll
-      for (int k = 0; k < 8; ++k) idx[(int64_t)(l * 8 + (int)(k ^ c.par)) * n + i] = c.idx[k];
+        for (int k = 0; k < 8; ++k) idx[(int64_t)(l * 8 + (int)(k ^ c.par)) * n + i] = c.idx[k];
+      }
     }
   }
 }
 
 cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, float* feat, uint32_t* idx,
                                  cudaStream_t s) {
-  if (n > 0) {
-    dim3 grid(min(ceil_div(n, 256), 4096), f.L);
-    k_encode_points<<<grid, 256, 0, s>>>(f, n, x, feat, idx);
-  }
+  if (n > 0) k_encode_points<<<min(ceil_div(n, 256), 65535), 256, 0, s>>>(f, n, x, feat, idx);
   return cudaGetLastError();
 }
 
