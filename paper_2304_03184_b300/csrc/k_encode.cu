@@ -8,16 +8,18 @@
 // coherent).  Backward: one thread per (sample, level); a block takes one level of a chunk,
 // and the blocks of a chunk's levels run together (its positions are read from DRAM once,
 // then from L2).  Tables are level-major [L][T][2] FP32: each corner is one 8-byte load, and
-// the +x corner pair shares a 32-byte sector.  Features are written feature-major [L*2][S] (coalesced) for FP32 fields, and as
-// the 16-bit MMA operand tiles of the tensor-core MLPs for FP16/BF16 fields.
+// the +x corner pair shares a 32-byte sector.  Features are written feature-major [L*2][S]
+// (coalesced) for FP32 fields, and as the 16-bit MMA operand tiles of the tensor-core MLPs
+// for FP16/BF16 fields.
 //
 // Backward: the same corners receive w_corner * dL/dfeat through atomics into the gradient
 // table (same layout).  Corners are held by vertex parity, so consecutive lanes whose cells
 // share a vertex hold it in the same slot; on coarse levels each slot's runs are summed
 // first (segmented warp scan) and one atomic carries a run's sum.
 //
-// Bound: L2 (tables up to 64 MiB per field stay L2-resident) -- 8 x 8 B gathers per
-// sample-level forward, 8 x 8 B atomics backward.
+// Bound: the tables (up to 64 MiB per field) stay L2-resident; the forward is bound by the
+// L1 wavefronts of its 8 x 8 B gathers per sample-level, the backward by instruction issue
+// together with the L2's atomic rate (8 x 8 B of corner updates per sample-level).
 #include "hash_grid.cuh"
 #include "tc_ptx.cuh"
 
