@@ -467,6 +467,27 @@ def test_train_gradients_identity_motion(env):
     _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL)
 
 
+def test_train_gradients_16_features(env):
+    """The FP32 path with 16 encoding features (L = 8, the plain-forward field): its first
+    layer's adjoint writes dL/dfeat through the 16-row output mapping, and the 64 x 16 weight
+    gradient takes its narrow form.  Identity motion, so the adjoint chain is compared alone."""
+    invr, ctx, oracle = env
+    tw = synth.train_step_workload(seed=11, n_rays=1536, field_desc=synth.CFG1_FIELD, n_nodes=64)
+    g = tw.batches[0].view.graph
+    g.dq[:] = np.array([1, 0, 0, 0, 0, 0, 0, 0], np.float32)[:, None]
+    g.x_live[:] = g.x_canon
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
+    fp = tw.fields[0]
+    gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+    ogt, ogw = ograds[id(ofields[id(fp)])]
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL)
+
+
 # Mixed-precision gradients per tensor vs the FP64 oracle.  The MLP runs in 16 bit, so a
 # fraction of ReLU decisions (pre-activations within ~1 unit of roundoff of zero) differ
 # from the FP64 network's: ~0.2 per sample in FP16, ~4x more in BF16.  MLP-weight gradients
