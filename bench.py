@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-deform", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the batched key-frame step (no single-batch, FP32, render, LUT sections)")
+    ap.add_argument("--render-only", action="store_true",
+                    help="time only the two-field 512x512 render (all three precisions; for launch lists)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -390,6 +392,14 @@ def run_ours(args, rank, world, local):
 
     # the requested precision, then the other two for the mixed-vs-FP32 comparison
     order = [args.prec] + [p for p in ("fp32", "fp16", "bf16") if p != args.prec]
+    if args.render_only:          # the two-field render alone (clean launch lists)
+        render = {p: bench_render(invr, ctx, PRECS[p], args, flush) for p in order}
+        out = {"metric": "render Mrays/s (two-field 512x512)", "value": render[args.prec]["value"],
+               "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": render[args.prec]["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else f"{args.prec}-mlp/f32",
+               "data": "synthetic", "render": render, "clocks": clocks.stop()}
+        return out, tw
     variants, main = {}, None
     for p in order:
         tb, fields, keep = build_train(invr, ctx, tw, PRECS[p])

@@ -102,7 +102,7 @@ struct Workspace {
   int32_t* block_sums;      // [n_scan_blocks]
   int32_t* view_base;       // [kMaxViews + 1] padded sample base per view; [n_views] = total
   int32_t* view_count;      // [kMaxViews] occupied samples per view (before padding)
-  int32_t* occ_box;         // [kMaxViews][6] bounds of the occupied cells per view (lo xyz, hi xyz)
+  int32_t* occ_box;         // [kMaxViews][6] bounds of the occupied cells per view (lo xyz, -hi xyz)
   int32_t* s_ray;           // [S] global ray id of each sample, -1 = padding
   float* s_t;               // [S] sample depth t_j
   float* s_pos;             // [3][S] live position

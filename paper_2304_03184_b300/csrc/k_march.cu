@@ -25,59 +25,67 @@ __device__ __forceinline__ void load_ray(const ViewDev& V, int64_t r, float3& o,
   d = make_float3(__ldg(V.d + r), __ldg(V.d + n + r), __ldg(V.d + 2 * n + r));
 }
 
-// One block per view: the index bounds of the view's occupied cells (lo > hi: none; a view
-// without occupancy gets the whole grid).  Bit c of the field is cell (c % 128, c / 128 % 128,
-// c / 128^2), so a 32-bit word covers 32 consecutive x cells of one (y, z) row.
+// Index bounds of each view's occupied cells, as six minima per view: lo x, y, z and -hi x,
+// y, z (the workspace is preset to a large value; lo > hi: no occupied cell; a view without
+// occupancy gets the whole grid).  Grid (64, n_views): each block reduces 1,024 words of the
+// view's bitfield and folds its bounds in with atomicMin.  Bit c of the field is cell (c % 128,
+// c / 128 % 128, c / 128^2), so a 32-bit word covers 32 consecutive x cells of one (y, z) row.
+constexpr int kOccBoxBlocks = 64;
+
 __global__ void __launch_bounds__(256) k_occ_box(const __grid_constant__ Plan P) {
   __shared__ int part[8][6];
-  const int v = blockIdx.x;
+  const int v = blockIdx.y;
   const uint32_t* occ = P.v[v].occ;
-  int b[6] = {kOccRes, kOccRes, kOccRes, -1, -1, -1};
+  int b[6] = {kOccRes, kOccRes, kOccRes, 1, 1, 1};
   if (!occ) {
-    b[0] = b[1] = b[2] = 0;
-    b[3] = b[4] = b[5] = kOccRes - 1;
+    if (blockIdx.x == 0) {
+      b[0] = b[1] = b[2] = 0;
+      b[3] = b[4] = b[5] = -(kOccRes - 1);
+    }
   } else {
     constexpr int kWords = kOccRes * kOccRes * kOccRes / 32;
-    for (int w = threadIdx.x; w < kWords; w += blockDim.x) {
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < kWords; w += gridDim.x * blockDim.x) {
       const uint32_t m = __ldg(occ + w);
       if (!m) continue;
       const int x0 = 32 * (w % (kOccRes / 32)), y = (w / (kOccRes / 32)) % kOccRes, z = w / (kOccRes * kOccRes / 32);
       b[0] = min(b[0], x0 + __ffs(m) - 1);
-      b[3] = max(b[3], x0 + 31 - __clz(m));
+      b[3] = min(b[3], -(x0 + 31 - __clz(m)));
       b[1] = min(b[1], y);
-      b[4] = max(b[4], y);
+      b[4] = min(b[4], -y);
       b[2] = min(b[2], z);
-      b[5] = max(b[5], z);
+      b[5] = min(b[5], -z);
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    const int r = a < 3 ? __reduce_min_sync(0xffffffffu, b[a]) : __reduce_max_sync(0xffffffffu, b[a]);
+    const int r = __reduce_min_sync(0xffffffffu, b[a]);
     if (lane == 0) part[wid][a] = r;
   }
   __syncthreads();
   if (threadIdx.x < 6) {
     const int a = threadIdx.x;
     int r = part[0][a];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = a < 3 ? min(r, part[w][a]) : max(r, part[w][a]);
-    P.ws.occ_box[6 * v + a] = r;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = min(r, part[w][a]);
+    atomicMin(P.ws.occ_box + 6 * v + a, r);
   }
 }
 
-// The samples j0 .. j1 of a ray (tn, dt) that can lie in the box of occupied cells `b`: the
-// ray's interval inside the box widened by 1e-4 (covering every FP32 rounding of a sample
-// position and its cell) plus one sample on each side.  Outside it no sample is occupied,
-// so skipping those samples changes no result.  Returns false when the ray misses the box.
+// The samples j0 .. j1 of a ray (tn, dt) that can lie in the box of occupied cells `b` (lo
+// x, y, z, -hi x, y, z): the ray's interval inside the box widened by 1e-4 (covering every
+// FP32 rounding of a sample position and its cell) plus one sample on each side.  Outside
+// it no sample is occupied, so skipping those samples changes no result.  Returns false
+// when the ray misses the box.
 __device__ __forceinline__ bool occupied_range(const int32_t* b, float3 o, float3 d, float tn, float dt,
                                                int n_samples, int& j0, int& j1) {
-  if (b[0] > b[3]) return false;
+  const int lo_i[3] = {b[0], b[1], b[2]}, hi_i[3] = {-b[3], -b[4], -b[5]};
+  if (lo_i[0] > hi_i[0]) return false;
   constexpr float kCell = 2.0f / kOccRes, kMargin = 1e-4f;
   const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
   float t0 = -INFINITY, t1 = INFINITY;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float lo = -1.0f + kCell * (float)b[a] - kMargin, hi = -1.0f + kCell * (float)(b[a + 3] + 1) + kMargin;
+    const float lo = -1.0f + kCell * (float)lo_i[a] - kMargin, hi = -1.0f + kCell * (float)(hi_i[a] + 1) + kMargin;
     if (dd[a] == 0.0f) {
       if (oo[a] < lo || oo[a] > hi) return false;
       continue;
@@ -302,7 +310,9 @@ __global__ void __launch_bounds__(256) k_march_emit(const __grid_constant__ Plan
 }
 
 cudaError_t launch_march_count(const Plan& P, cudaStream_t s) {
-  k_occ_box<<<P.n_views, 256, 0, s>>>(P);
+  cudaError_t e = cudaMemsetAsync(P.ws.occ_box, 0x7F, 6 * sizeof(int32_t) * P.n_views, s);  // 0x7F7F7F7F
+  if (e != cudaSuccess) return e;
+  k_occ_box<<<dim3(kOccBoxBlocks, P.n_views), 256, 0, s>>>(P);
   k_march_count<<<ceil_div(P.total_rays, 256), 256, 0, s>>>(P);
   return cudaGetLastError();
 }
