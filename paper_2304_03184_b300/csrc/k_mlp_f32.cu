@@ -449,8 +449,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_mlp_fwd_f32(const __grid_consta
   }
 }
 
-// One block: the padded, transposed weights of a field into its global copy Wt.
-__global__ void k_prep_wt(const float* __restrict__ W, int in, float* Wt) { load_weights(W, in, Wt, nullptr); }
+// The padded, transposed weights of a field into its global copy Wt: one thread per element
+// of the [k][o] layout (layer 1 with in = 16 leaves its rows 16..31 unused).
+__global__ void __launch_bounds__(256) k_prep_wt(const float* __restrict__ W, int in, float* Wt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kWSize) return;
+  const WeightOffsets off(in);
+  const int base[5] = {kW1, kW2, kW3, kW4, kW5}, outs[5] = {64, 64, 16, 64, 16}, ins[5] = {in, 64, 64, 16, 64};
+  int layer = 4;
+  while (layer > 0 && e < base[layer]) --layer;
+  const int i = e - base[layer], k = i / outs[layer], o = i % outs[layer];
+  if (k < ins[layer]) Wt[e] = padded_w(W, off, in, layer + 1, o, k);
+}
 
 // X, Dp (dL/d(outputs)) and Rp (padding markers) staged and visible on entry.
 template <int IN>
@@ -600,7 +610,7 @@ cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s) {
     const FieldDev& F = P.v[v].field;
     bool seen = false;
     for (int u = 0; u < v; ++u) seen = seen || P.v[u].field.weights == F.weights;
-    if (F.mlp_kind == kMlpF32 && !seen) k_prep_wt<<<1, kThreads, 0, s>>>(F.weights, F.mlp_in, F.wt_f32);
+    if (F.mlp_kind == kMlpF32 && !seen) k_prep_wt<<<ceil_div(kWSize, 256), 256, 0, s>>>(F.weights, F.mlp_in, F.wt_f32);
   }
   cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
   k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(plan_args(P));
@@ -625,7 +635,7 @@ cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* fea
   A.f[0] = f;
   cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
   if (n > 0) {
-    k_prep_wt<<<1, kThreads, 0, s>>>(f.weights, f.mlp_in, f.wt_f32);
+    k_prep_wt<<<ceil_div(kWSize, 256), 256, 0, s>>>(f.weights, f.mlp_in, f.wt_f32);
     k_mlp_fwd_f32<<<num_sms * 2, kThreads, kFwdSmem, s>>>(A);
   }
   return cudaGetLastError();
