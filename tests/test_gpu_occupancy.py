@@ -67,6 +67,23 @@ def test_joint_render_matches_oracle(env, prec):
     assert np.abs(host(img) - host(rgba)).max() > 1e-3
 
 
+def test_joint_render_full_size_sampled(env):
+    """Joint compositing at the render configuration's full size (512 x 512 rays in one call,
+    FP32): sampled rays against the oracle."""
+    invr, ctx, oracle = env
+    w = synth.two_field_render()
+    (hv, kh), (ov, ko) = (gpu_view(invr, ctx, sv, invr.INVR_FP32) for sv in w.views)
+    rgba, depth = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [hv, ov], joint=True)
+    ctx.sync()
+    sel = np.sort(np.random.default_rng(37).choice(w.rays.n, 1500, replace=False))
+    rays = synth.subset_rays(w.rays, sel)
+    o_h, o_o = (oracle.View.from_synth(sv) for sv in w.views)
+    ref, ref_d, n_used = oracle.render_joint(rays.o, rays.d, w.n_samples, w.t_eps, o_h, o_o)
+    assert (ref[3] > 0.1).mean() > 0.05
+    np.testing.assert_allclose(host(rgba)[:, sel], ref, rtol=0, atol=COLOUR_TOL)
+    np.testing.assert_allclose(host(depth)[sel], ref_d, rtol=0, atol=4 * COLOUR_TOL)
+
+
 def test_joint_render_needs_two_views(env):
     invr, ctx, oracle = env
     w = synth.two_field_render(width=8, height=8, n_samples=16, n_nodes=64)
