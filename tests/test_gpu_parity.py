@@ -252,14 +252,21 @@ def test_render_two_fields_fp32_small(env):
     np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
 
 
-def test_render_two_fields_full_size_sampled(env):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_render_two_fields_full_size_sampled(env, prec):
+    invr = env[0]
     w = synth.two_field_render()                          # 512 x 512, 128 samples
     rng = np.random.default_rng(34)
     sel = np.sort(rng.choice(w.rays.n, 1500, replace=False))
-    rgba, depth, ref = _render_both(env, w, w.views, sel=sel)
-    ok = ~_near_tie(ref)
-    np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=COLOUR_TOL)
-    np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
+    code = invr.INVR_FP32 if prec == "fp32" else invr.INVR_MLP_BF16
+    rgba, depth, ref = _render_both(env, w, w.views, prec=code, sel=sel)
+    if prec == "fp32":
+        ok = ~_near_tie(ref)
+        np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=COLOUR_TOL)
+        np.testing.assert_allclose(depth[ok], ref.depth[ok], rtol=COLOUR_TOL, atol=COLOUR_TOL)
+    else:
+        ok = ~_near_tie(ref, 1e-2)
+        np.testing.assert_allclose(rgba[:, ok], ref.rgba[:, ok], rtol=0, atol=MIXED_RGB_TOL)
 
 
 def test_render_novel_view_full_size_sampled(env):
