@@ -29,3 +29,27 @@ def test_replica_aggregation_single_rank():
     import bench
     value, ms = bench.aggregate_replicas(2.0, 1000.0, 1)
     assert ms == 2.0 and abs(value - 1000.0 / 2e-3) < 1e-6
+
+
+def test_kernel_rooflines_arithmetic():
+    """The per-kernel roofline fractions: bytes (or FLOPs) of the stated algorithmic work over
+    the CUDA-event duration of one record, against the measured peak the bound names; the
+    gather and the scatter against the L2 probe ceilings when those were measured."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2304_03184_b300 import synth
+    tw = synth.keyframe_batch_workload(n_frames=1, log2_rays=(9.0, 9.5))
+    S, L = 1_000_000, tw.fields[0].desc.L
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1000.0}
+    kt = {"adam": (0.2, 2), "mlp_fwd_tc": (1.0, 1), "encode": (2.0, 1), "encode_bwd": (4.0, 1)}
+    r = bench.kernel_rooflines(kt, tw, 1000, S, peaks)
+    n_params = tw.fields[0].desc.n_table_params() + tw.fields[0].desc.n_weight_params()
+    assert abs(r["adam"]["achieved"] - n_params * 32 / 1e-4 / 1e9) < 0.1       # one launch: 0.1 ms
+    assert abs(r["mlp_fwd_tc"]["achieved"] - S * 2 * tw.fields[0].desc.n_weight_params() / 1e-3 / 1e12) < 0.1
+    assert r["encode"]["bound"] == "hbm" and abs(r["encode"]["frac"] - r["encode"]["achieved"] / 6000.0) < 1e-3
+    l2 = {"gather_v4_gbs": 4000.0, "atomic_v4_gbs": 3000.0}
+    r2 = bench.kernel_rooflines(kt, tw, 1000, S, peaks, l2)
+    payload = S * L * 64                                                       # 8 corners x 2 floats per level
+    assert r2["encode"]["bound"] == "l2" and abs(r2["encode"]["achieved"] - payload / 2e-3 / 1e9) < 0.1
+    assert abs(r2["encode_bwd"]["achieved"] - payload / 4e-3 / 1e9) < 0.1
+    assert abs(r2["encode_bwd"]["frac"] - r2["encode_bwd"]["achieved"] / 3000.0) < 1e-3
