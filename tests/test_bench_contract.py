@@ -53,3 +53,23 @@ def test_kernel_rooflines_arithmetic():
     assert r2["encode"]["bound"] == "l2" and abs(r2["encode"]["achieved"] - payload / 2e-3 / 1e9) < 0.1
     assert abs(r2["encode_bwd"]["achieved"] - payload / 4e-3 / 1e9) < 0.1
     assert abs(r2["encode_bwd"]["frac"] - r2["encode_bwd"]["achieved"] / 3000.0) < 1e-3
+
+
+def test_headline_roofline_object():
+    """The bench line's roofline: the kernel with the most time, its algorithmic bytes per
+    record (canonical position, dL/dfeat and the 8 corner updates per level for the scatter)
+    over the record's duration against the measured HBM copy bandwidth; the DRAM traffic
+    of the committed ncu capture only for the workload it was taken on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2304_03184_b300 import synth
+    tw = synth.keyframe_batch_workload(n_frames=1, log2_rays=(9.0, 9.5))
+    S, L = 2_000_000, tw.fields[0].desc.L
+    kt = {"encode_bwd": (10.0, 2), "encode": (4.0, 2), "adam": (0.2, 2)}
+    r = bench.roofline(kt, tw, 1000, S, {"hbm_gbs": 6000.0},
+                       {"gather_v4_gbs": 4000.0, "atomic_v4_gbs": 3000.0})
+    assert r["kernel"] == "encode_bwd" and r["bound"] == "hbm" and r["peak"] == 6000.0
+    want = S * (12 + L * (8 + 64)) / 5e-3 / 1e9                               # 5 ms per record
+    assert abs(r["achieved"] - want) < 0.1 and abs(r["frac"] - want / 6000.0) < 1e-4
+    assert r["traffic"] is None                                                # another workload
+    assert abs(r["l2"]["achieved"] - S * L * 64 / 5e-3 / 1e9) < 0.1
