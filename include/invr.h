@@ -73,7 +73,13 @@ invr_status invr_ctx_reserve(invr_ctx ctx, int64_t max_rays, int max_samples);
 /* Wait for `stream`, then read and clear the device status word, reporting the first of:
  * INVR_E_TIMEOUT if a bounded device wait gave up, INVR_E_STATE if a call's occupied samples
  * overflowed a reserved workspace, INVR_E_NONFINITE if a kernel flagged a non-finite output
- * since the last sync; else INVR_OK. */
+ * since the last sync; else INVR_OK.
+ * After a timeout the kernel waits (bounded again) for its own MMAs and copies in flight
+ * before it frees its tensor memory.  If that drain finished, the context stays usable: the
+ * outputs of the calls since the last sync are undefined, later calls are correct.  If the
+ * drain gave up too, the detail text (invr_last_error_detail) says so ("drain"): tensor-core
+ * work may then have written tensor or shared memory after the CTA released it, so results
+ * of any kernel that shared those SMs are undefined and the context should be destroyed. */
 invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around every kernel
@@ -338,8 +344,9 @@ invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4);
 invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in4);
 /* Polls of each bounded device-side wait (the tensor-core kernels' mbarrier waits) before
  * the kernel gives up, records INVR_E_TIMEOUT in the status word, lets its in-flight work
- * finish, frees its tensor memory and returns.  Default 2^22 (a few seconds).  0 makes every
- * such wait give up at once, which exercises the failure path without a fault. */
+ * finish (its own drain wait, bounded by 2^22 polls whatever this setting), frees its tensor
+ * memory and returns.  Default 2^22 (a few seconds).  0 makes every such wait give up at
+ * once, which exercises the failure path without a fault. */
 invr_status invr_ctx_set_wait_limit(invr_ctx ctx, uint32_t polls);
 
 /* ------------------------------------------------------------------ single steps */
@@ -373,11 +380,13 @@ invr_status invr_query_points(invr_ctx ctx, const invr_field_view* view, int64_t
  * allowed.  Inputs, outputs and results are those of invr_query_points.  Its scratch
  * (canonical positions and encoding features, (3 + mlp_in) floats per point) lives in one
  * fixed device array of 35 x INVR_NOALLOC_MAX_POINTS floats (9.2 MB) compiled into the
- * library; every device that loads the library holds it until the process exits.  The call
- * allocates nothing.  The first call on a device looks up the array's device address; make
- * that first call before any stream capture.  All calls share the one array and each call
- * overwrites it: calls that overlap on the GPU (other streams, other host threads) race, so
- * the caller must serialise them.  n > INVR_NOALLOC_MAX_POINTS returns INVR_E_ARG. */
+ * library.  invr_ctx_create, which allocates anyway, sets the query up on its device: it
+ * looks up the array's device address and loads the code of the kernels the query launches
+ * (with lazy module loading both would otherwise happen at the first query).  From then on
+ * the device holds the array until the process exits, and the query itself allocates
+ * nothing, on its first call too.  All calls share the one array and each call overwrites
+ * it: calls that overlap on the GPU (other streams, other host threads) race, so the caller
+ * must serialise them.  n > INVR_NOALLOC_MAX_POINTS returns INVR_E_ARG. */
 #define INVR_NOALLOC_MAX_POINTS 65536
 invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_view* view, int64_t n, const float* p_dev,
                                       float* out_dev, invr_stream stream);

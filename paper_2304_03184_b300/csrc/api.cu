@@ -177,7 +177,7 @@ bool capturing(cudaStream_t s) {
 
 void free_workspace(Workspace& w) {
   void* ptrs[] = {w.ray_count, w.ray_bits, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray,
-                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.loss_part,
+                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.mlp_mask, w.loss_part,
                   w.s_vt, w.feat_d, w.dvc, w.dfeat_d, w.def_x, w.def_h, w.def_g, w.def_gout};
   for (void* p : ptrs) dfree(p);
   w = Workspace{};
@@ -226,6 +226,7 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
   if (train) {
     INVR_CUDA(ctx, dmalloc(&w.dout, 4 * S));
     INVR_CUDA(ctx, dmalloc(&w.dfeat, (size_t)kMaxIn * S));
+    INVR_CUDA(ctx, dmalloc(&w.mlp_mask, (size_t)6 * S));
   }
   w.S_cap = S;
   w.R_cap = R;
@@ -475,7 +476,8 @@ cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
   if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
     return e;
   if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
-    e = TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_tc(P, ctx->num_sms, s));
+    e = P.feat_split ? TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_split_tc(P, ctx->num_sms, s))
+                     : TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_tc(P, ctx->num_sms, s));
   return e;
 }
 
@@ -571,6 +573,7 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
     if ((st = ensure_deform_tc_workspace(ctx, s)) != INVR_OK) return st;
     P.deform_store = 1;
   }
+  P.feat_split = 1;  // 16-bit fields train on split products (values plus rounding remainders)
   P.ws = ctx->ws;
   INVR_CUDA(ctx, run_forward(ctx, P, s));
   INVR_CUDA(ctx, TIMED(ctx, "composite_train", s, launch_composite_train(P, a->loss_dev, s)));
@@ -657,6 +660,13 @@ invr_status invr_ctx_create(invr_ctx* out, int device) {
     dfree(ctx->status);
     delete ctx;
     return INVR_E_OOM;
+  }
+  // the no-allocation query's scratch array and kernels are loaded here, where allocating is allowed
+  if (noalloc_prepare(device) != cudaSuccess) {
+    dfree(ctx->status);
+    dfree(ctx->pose_bias);
+    delete ctx;
+    return INVR_E_CUDA;
   }
   *out = ctx;
   return INVR_OK;
@@ -789,6 +799,11 @@ invr_status invr_ctx_sync(invr_ctx ctx, invr_stream stream) {
   INVR_CUDA(ctx, cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
   INVR_CUDA(ctx, cudaMemset(ctx->status, 0, sizeof(unsigned)));
   // root causes first: a timed-out or skipped stage leaves later stages reading stale values
+  if (st & kStatusDrainTimeout)
+    return fail(ctx, INVR_E_TIMEOUT,
+                "a bounded device wait gave up, and so did the drain of the kernel's own tensor-core work: "
+                "results since the last sync are undefined and tensor memory may have been written after release; "
+                "destroy this context");
   if (st & kStatusTimeout) return fail(ctx, INVR_E_TIMEOUT, "a bounded device wait gave up");
   if (st & kStatusOverflow) return fail(ctx, INVR_E_STATE, "sample workspace overflow");
   if (st & kStatusNonFinite) return fail(ctx, INVR_E_NONFINITE, "a kernel produced a non-finite output");

@@ -31,6 +31,10 @@ constexpr int kLossPaper = 1;
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusOverflow = 4u;
+// A kernel whose bounded wait gave up then waits (bounded again) for its own MMAs and copies
+// in flight before it frees its tensor memory; this bit says that second wait gave up too,
+// so that work may still have been writing the CTA's tensor and shared memory as it exited.
+constexpr unsigned kStatusDrainTimeout = 8u;
 
 enum MlpKind : int { kMlpF32 = 0, kMlpF16 = 1, kMlpBF16 = 2 };
 
@@ -111,6 +115,7 @@ struct Workspace {
   float* out;               // [4][S] sigma, r, g, b
   float* dout;              // [4][S] dL/d o_0, dL/d z_rgb
   float* dfeat;             // [mlp_in][S]
+  uint32_t* mlp_mask;       // [6][S] training: ReLU decisions of H1, H2, H4 (tensor-core fields)
   float* loss_part;         // [n loss blocks]
   // deformation net (allocated when a call has one)
   float* s_vt;              // [3][S] v_t, the warp before the net
@@ -150,6 +155,7 @@ struct Plan {
   int view_lo, view_hi;     // views processed by the per-field launches ([0, n_views) by default)
   int has_deform;           // some view has a deformation net
   int deform_store;         // training: the tensor-core forward keeps its operand tiles
+  int feat_split;           // training: 16-bit fields' features also as remainder tiles
   uint32_t wait_limit;      // polls per bounded device wait
   Tune tune;                // launch shapes (autotuned per context)
   Workspace ws;
@@ -295,6 +301,11 @@ __host__ __device__ constexpr size_t feat16_group_offset(int64_t S_cap, int64_t 
 // false if the driver's encoder is unavailable or rejects the map.
 bool encode_feat16_map(void* map, const void* feat, int64_t S_cap, int in);
 
+// Byte offset of the remainder tiles (training of a 16-bit field: each feature's 16-bit
+// value plus the 16-bit remainder of its rounding, tc::split2): the same layout 16 FP32
+// feature rows further, inside the tile's own columns again.
+__host__ __device__ constexpr size_t feat16_lo_offset(int64_t S_cap) { return (size_t)64 * (size_t)S_cap; }
+
 // Byte offset of feature k of sample s (k even: the pair k, k+1 is one 32-bit word).
 __host__ __device__ constexpr size_t feat16_offset(int64_t S_cap, int64_t s, int k) {
   return feat16_group_offset(S_cap, s >> 7, (int)((s & 127) >> 3)) + (size_t)((k >> 3) * 128) +
@@ -317,6 +328,8 @@ cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 bool plan_has_kind(const Plan& P, int kind);
 cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s);
+// training forward of the 16-bit fields: split products, ReLU decisions to ws.mlp_mask
+cudaError_t launch_mlp_fwd_split_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
                                  uint32_t wait_limit, int num_sms, cudaStream_t s);
@@ -346,6 +359,16 @@ cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, f
                                  cudaStream_t s);
 cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* feat, float* out, int num_sms,
                                   cudaStream_t s);
+
+// Load the code of the point-query kernels (warp, encoding, both MLP paths) now: with lazy
+// module loading their first launch would otherwise load it, allocating device memory.
+cudaError_t preload_warp_points();
+cudaError_t preload_encode_points();
+cudaError_t preload_mlp_points_f32();
+cudaError_t preload_mlp_points_tc();
+// Set up the no-allocation point query on the current device `dev`: look up its scratch
+// array's device address and load the kernels it launches (called by invr_ctx_create).
+cudaError_t noalloc_prepare(int dev);
 
 // deformation net
 cudaError_t launch_deform_forward(const Plan& P, int num_sms, cudaStream_t s);

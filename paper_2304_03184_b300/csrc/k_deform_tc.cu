@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
     if (t == 0) atomicOr(P.status, kStatusTimeout);
     // let this CTA's outstanding MMAs finish (bounded) before their tensor memory is freed
     for (int j = 0; j < 2; ++j)
-      if (pending[j]) tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit);
+      if (pending[j] && !tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
   if (!ok) {
     if (t == 0) atomicOr(P.status, kStatusTimeout);
     for (int j = 0; j < 2; ++j)
-      if (pending[j]) tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit);
+      if (pending[j] && !tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -699,8 +699,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
     // let this CTA's MMAs and copies in flight finish (bounded) before its tensor memory and
     // shared memory are released
     for (int b = 0; b < 2; ++b) {
-      if (pending[b]) tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit);
-      if (loading[b]) tc::mbar_wait(lbar0 + 8 * b, lphase[b], kDrainLimit);
+      if (pending[b] && !tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
+      if (loading[b] && !tc::mbar_wait(lbar0 + 8 * b, lphase[b], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
     }
   }
   tc::fence_before_sync();

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) 
                           : make_float3(0.0f, 0.0f, 0.0f);
     // F.L is a multiple of 4 (mlp_in = 2 L is 16 or 32; the deformation net's 2 L a multiple of 8)
     for (int l0 = 0; l0 < F.L; l0 += 4) {
-      uint32_t packed[4];
+      uint32_t packed[4], rest[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int l = l0 + j;
@@ -66,12 +66,19 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) 
           feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
         } else {
           // tensor-core field: the pair as 16-bit operand row s of its tile (rounded to nearest)
-          packed[j] = F.mlp_kind == kMlpBF16 ? tc::pack2<true>(f.x, f.y) : tc::pack2<false>(f.x, f.y);
+          // and, for training, the remainder of that rounding
+          if (F.mlp_kind == kMlpBF16)
+            tc::split2<true>(f.x, f.y, packed[j], rest[j]);
+          else
+            tc::split2<false>(f.x, f.y, packed[j], rest[j]);
         }
       }
-      if (F.mlp_kind != kMlpF32)
-        *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l0)) =
-            make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      if (F.mlp_kind != kMlpF32) {
+        uint8_t* dst = reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l0);
+        *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        if (P.feat_split)
+          *reinterpret_cast<uint4*>(dst + feat16_lo_offset(S_cap)) = make_uint4(rest[0], rest[1], rest[2], rest[3]);
+      }
     }
   }
 }
@@ -199,6 +206,11 @@ cudaError_t launch_encode_points(const FieldDev& f, int64_t n, const float* x, f
                                  cudaStream_t s) {
   if (n > 0) k_encode_points<<<min(ceil_div(n, 256), 65535), 256, 0, s>>>(f, n, x, feat, idx);
   return cudaGetLastError();
+}
+
+cudaError_t preload_encode_points() {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, k_encode_points);
 }
 
 }  // namespace invr

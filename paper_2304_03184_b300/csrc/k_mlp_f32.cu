@@ -641,4 +641,10 @@ cudaError_t launch_mlp_points_f32(const FieldDev& f, int64_t n, const float* fea
   return cudaGetLastError();
 }
 
+cudaError_t preload_mlp_points_f32() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  return e != cudaSuccess ? e : cudaFuncGetAttributes(&a, k_prep_wt);
+}
+
 }  // namespace invr

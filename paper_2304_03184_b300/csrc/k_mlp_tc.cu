@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
     // a wait gave up: record it, then let this CTA's MMAs and copies in flight finish
     // (bounded) before the tensor memory and shared memory they write are released
     if (t == 0) atomicOr(A.status, kStatusTimeout);
-    if (mma_pending) tc::mbar_wait(mbar, phase, kWaitLimit);
-    if (x_pending) tc::mbar_wait(xbar, xphase, kWaitLimit);
+    if (mma_pending && !tc::mbar_wait(mbar, phase, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
+    if (x_pending && !tc::mbar_wait(xbar, xphase, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -356,6 +356,322 @@ cudaError_t launch_tc(const TcArgs& A, int num_sms, cudaStream_t s) {
   cudaFuncSetAttribute(k_mlp_fwd_tc<BF16, TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
   k_mlp_fwd_tc<BF16, TILES><<<num_sms * kCtasPerSm, kThreadsTC, kSmemTC, s>>>(A);
   return cudaGetLastError();
+}
+
+
+// ====================================================================== training forward
+// The training forward of a 16-bit field with split operands: every layer's product is
+// formed as hi*hi + lo*hi + hi*lo from a 16-bit value and the 16-bit remainder of its
+// rounding (tc::split2), three MMAs into one FP32 accumulator.  The ReLU decisions of the
+// network are then taken at about twice the 16-bit precision: a pre-activation that rounds
+// across zero in plain 16-bit arithmetic flips its unit's gradient path in the backward,
+// and these flips, not the 16-bit rounding of values, are what carries the gradient error
+// of the plain 16-bit chain.  The kernel writes sigma, rgb and the ReLU decisions (one bit
+// per hidden unit of H1, H2, H4; [6][ld] words) that the backward applies.
+//
+// Hidden activations never touch shared memory: each epilogue writes its row's hi and lo
+// halves into tensor memory, from which the next layer's MMAs read their A operand.  Per CTA
+// 128 tensor-memory columns (accumulator [0,64), activations hi [64,96), lo [96,128)) and 53 KB
+// of shared memory (weights hi and lo, one tile of X hi and lo): four CTAs per SM.  X hi/lo
+// arrive by two TMA boxes; the next tile's are issued once layer 1 has read this tile's.
+constexpr int kCtasSplit = 4;
+constexpr uint32_t kTmemSplit = 128;
+constexpr uint32_t T_ACC = 0, T_HI = 64, T_LO = 96;
+constexpr uint32_t S_WHI = 0;                    // W1..W5 at the OFF_W* offsets
+constexpr uint32_t S_WLO = OFF_P;                // 18,432: the same layout, remainders
+constexpr uint32_t S_XHI = 2 * OFF_P;            // [128 x in]
+constexpr uint32_t S_XLO = S_XHI + kTM * 32 * 2;
+constexpr uint32_t S_MISC = S_XLO + kTM * 32 * 2;
+constexpr uint32_t kSmemSplit = S_MISC + 64;
+static_assert(kCtasSplit * (kSmemSplit + 1024) <= 228 * 1024, "four CTAs per SM");
+static_assert(kCtasSplit * kTmemSplit <= 512, "tensor memory of four CTAs");
+
+struct SplitArgs {
+  CUtensorMap xmap[2][2];   // [in == 32][hi, lo]: TMA maps of the feature tiles and their remainders
+  float* out;               // [4][ld]
+  uint32_t* mask;           // [6][ld]: ReLU decisions of H1 (words 0, 1), H2 (2, 3), H4 (4, 5)
+  const int32_t* view_base;
+  int64_t ld;
+  int n_views;
+  uint32_t wait_limit;
+  unsigned* status;
+  FieldDev f[kMaxViews];
+};
+
+// Stage one (padded) weight matrix [N][K] as K-major 16-bit values and remainders.
+template <bool BF16, int N, int K>
+__device__ __forceinline__ void stage_weight_split(uint8_t* hi, uint8_t* lo, const float* __restrict__ W,
+                                                   int layer, int in, const WOff& off) {
+  for (int e = threadIdx.x; e < N * K / 2; e += blockDim.x) {
+    const int o = (2 * e) / K, k = (2 * e) % K;
+    float a = 0.0f, b = 0.0f;
+    switch (layer) {
+      case 1: a = W[off.w1 + o * in + k]; b = W[off.w1 + o * in + k + 1]; break;
+      case 2: a = W[off.w2 + o * kHidden + k]; b = W[off.w2 + o * kHidden + k + 1]; break;
+      case 3: a = W[off.w3 + o * kHidden + k]; b = W[off.w3 + o * kHidden + k + 1]; break;
+      case 4:
+        a = k == 0 ? 0.0f : W[off.w4 + o * (kGeoOut - 1) + k - 1];
+        b = W[off.w4 + o * (kGeoOut - 1) + k];
+        break;
+      default:
+        a = o < 3 ? W[off.w5 + o * kColHidden + k] : 0.0f;
+        b = o < 3 ? W[off.w5 + o * kColHidden + k + 1] : 0.0f;
+        break;
+    }
+    uint32_t h, l;
+    tc::split2<BF16>(a, b, h, l);
+    *reinterpret_cast<uint32_t*>(hi + tc::kmajor_offset(o, k, K)) = h;
+    *reinterpret_cast<uint32_t*>(lo + tc::kmajor_offset(o, k, K)) = l;
+  }
+}
+
+template <bool BF16>
+__device__ void stage_weights_split(uint8_t* sm, const FieldDev& F) {
+  const WOff off(F.mlp_in);
+  uint8_t* hi = sm + S_WHI;
+  uint8_t* lo = sm + S_WLO;
+  if (F.mlp_in == 16)
+    stage_weight_split<BF16, 64, 16>(hi + OFF_W1, lo + OFF_W1, F.weights, 1, 16, off);
+  else
+    stage_weight_split<BF16, 64, 32>(hi + OFF_W1, lo + OFF_W1, F.weights, 1, 32, off);
+  stage_weight_split<BF16, 64, 64>(hi + OFF_W2, lo + OFF_W2, F.weights, 2, F.mlp_in, off);
+  stage_weight_split<BF16, 16, 64>(hi + OFF_W3, lo + OFF_W3, F.weights, 3, F.mlp_in, off);
+  stage_weight_split<BF16, 64, 16>(hi + OFF_W4, lo + OFF_W4, F.weights, 4, F.mlp_in, off);
+  stage_weight_split<BF16, 16, 64>(hi + OFF_W5, lo + OFF_W5, F.weights, 5, F.mlp_in, off);
+}
+
+// One thread: D = A B^T over K as split products, A in shared memory (the X tile).
+__device__ __forceinline__ void issue_split_ss(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                               uint32_t b_lo, int K, int N, bool bf16) {
+  const uint32_t idesc = tc::idesc_f16(kTM, N, bf16);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t ah = tc::smem_desc(a_hi + kk * 256, 128, K * 16);
+    const uint64_t al = tc::smem_desc(a_lo + kk * 256, 128, K * 16);
+    const uint64_t bh = tc::smem_desc(b_hi + kk * 256, 128, K * 16);
+    const uint64_t bl = tc::smem_desc(b_lo + kk * 256, 128, K * 16);
+    tc::mma_f16(d, ah, bh, idesc, kk > 0 ? 1u : 0u);
+    tc::mma_f16(d, al, bh, idesc, 1u);
+    tc::mma_f16(d, ah, bl, idesc, 1u);
+  }
+}
+
+// One thread: the same with A in tensor memory (8 columns per K step of 16).
+__device__ __forceinline__ void issue_split_ts(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                               uint32_t b_lo, int K, int N, bool bf16) {
+  const uint32_t idesc = tc::idesc_f16(kTM, N, bf16);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t bh = tc::smem_desc(b_hi + kk * 256, 128, K * 16);
+    const uint64_t bl = tc::smem_desc(b_lo + kk * 256, 128, K * 16);
+    tc::mma_f16_ts(d, a_hi + kk * 8, bh, idesc, kk > 0 ? 1u : 0u);
+    tc::mma_f16_ts(d, a_lo + kk * 8, bh, idesc, 1u);
+    tc::mma_f16_ts(d, a_hi + kk * 8, bl, idesc, 1u);
+  }
+}
+
+// Epilogue of a 64-unit ReLU layer: read this thread's 64 accumulator columns, write ReLU(z)
+// as hi and lo halves into its tensor-memory lane (32 columns each) and return the decisions
+// z > 0 as two 32-bit masks (bit j of m[w] = unit 32 w + j).
+template <bool BF16>
+__device__ __forceinline__ void relu_split64(uint32_t row, uint32_t (&m)[2]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float v[32];
+    tc::tmem_ld32(row + T_ACC + 32 * h, v);
+    uint32_t hi[16], lo[16], bits = 0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      bits |= (v[2 * c] > 0.0f ? 1u : 0u) << (2 * c);
+      bits |= (v[2 * c + 1] > 0.0f ? 1u : 0u) << (2 * c + 1);
+      tc::split2<BF16>(fmaxf(v[2 * c], 0.0f), fmaxf(v[2 * c + 1], 0.0f), hi[c], lo[c]);
+    }
+    m[h] = bits;
+    tc::tmem_st16(row + T_HI + 16 * h, hi);
+    tc::tmem_st16(row + T_LO + 16 * h, lo);
+  }
+}
+
+// Tensor-memory writes and reads of every thread done -> the tensor core may go on.
+__device__ __forceinline__ void tmem_ready() {
+  tc::fence_before_sync();
+  __syncthreads();
+}
+
+__device__ __forceinline__ int64_t next_tile_split(const SplitArgs& A, const int32_t* vb, int64_t tile,
+                                                   int64_t n_tiles, int kind, int& v) {
+  for (; tile < n_tiles; tile += gridDim.x) {
+    v = advance_view(vb, A.n_views, tile * kTM, v);
+    if (A.f[v].mlp_kind == kind) return tile;
+  }
+  return n_tiles;
+}
+
+// One warp (lane 0 works): X hi and lo of tile `tile` as two TMA boxes.
+__device__ __forceinline__ void load_x_split(const SplitArgs& A, int64_t tile, int in, uint32_t sbase, uint32_t bar) {
+  if ((threadIdx.x & 31) == 0) {
+    const int w = in == 32 ? 1 : 0;
+    tc::mbar_expect_tx(bar, 2u * 16u * 16u * (uint32_t)in);
+    tc::tma_load_3d(sbase + S_XHI, &A.xmap[w][0], 0, (int)tile, 0, bar);
+    tc::tma_load_3d(sbase + S_XLO, &A.xmap[w][1], 0, (int)tile, 0, bar);
+  }
+  __syncwarp();
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(const __grid_constant__ SplitArgs A) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ int32_t vb[kMaxViews + 1];
+  if ((int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t <= A.n_views) vb[t] = A.view_base[t];
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S_MISC + 16);
+  const uint32_t mbar = tc::smem_u32(sm + S_MISC);
+  const uint32_t xbar = tc::smem_u32(sm + S_MISC + 8);
+  const uint32_t sbase = tc::smem_u32(sm);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemSplit);
+  if (t == 0) {
+    tc::mbar_init(mbar, 1);
+    tc::mbar_init(xbar, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+  const int kind = BF16 ? kMlpBF16 : kMlpF16;
+  const int64_t S = (int64_t)A.view_base[A.n_views];
+  const int64_t n_tiles = (S + kTM - 1) / kTM;
+  const float* loaded = nullptr;
+  uint32_t phase = 0, xphase = 0;
+  bool ok = true, mma_pending = false, x_pending = false;
+
+  int vn = 0;
+  int64_t tile = next_tile_split(A, vb, blockIdx.x, n_tiles, kind, vn);
+  if (warp == 0 && tile < n_tiles) load_x_split(A, tile, A.f[vn].mlp_in, sbase, xbar);
+  x_pending = tile < n_tiles;
+
+#define INVR_SPLIT_WAIT()                                     \
+  mma_pending = true;                                         \
+  ok = tc::mbar_wait(mbar, phase, A.wait_limit);              \
+  if (!__syncthreads_and(ok)) { ok = false; break; }          \
+  phase ^= 1u;                                                \
+  mma_pending = false;                                        \
+  tc::fence_after_sync();
+
+  while (tile < n_tiles) {
+    const int64_t s0 = tile * kTM;
+    const FieldDev& F = A.f[vn];
+    const int64_t nxt = next_tile_split(A, vb, tile + gridDim.x, n_tiles, kind, vn);
+    if (F.weights != loaded) {
+      __syncthreads();
+      stage_weights_split<BF16>(sm, F);
+      loaded = F.weights;
+      tc::fence_smem_to_async();
+    }
+    const int in = F.mlp_in;
+    const int valid = (int)(S - s0 < kTM ? S - s0 : kTM);
+    tmem_ready();
+    ok = tc::mbar_wait(xbar, xphase, A.wait_limit);
+    if (!__syncthreads_and(ok)) { ok = false; break; }
+    xphase ^= 1u;
+    x_pending = false;
+    uint32_t m1[2], m2[2], m4[2];
+    // ---- layer 1: X (shared memory) -> H1
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_split_ss(tmem + T_ACC, sbase + S_XHI, sbase + S_XLO, sbase + S_WHI + OFF_W1, sbase + S_WLO + OFF_W1,
+                     in, 64, BF16);
+      tc::commit_to(mbar);
+    }
+    INVR_SPLIT_WAIT();
+    // X has been read: the next tile's lands while layers 2..5 run
+    if (nxt < n_tiles) {
+      if (warp == 0) load_x_split(A, nxt, A.f[vn].mlp_in, sbase, xbar);
+      x_pending = true;
+    }
+    relu_split64<BF16>(row, m1);
+    tmem_ready();
+    // ---- layer 2: H1 (tensor memory) -> H2
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_split_ts(tmem + T_ACC, tmem + T_HI, tmem + T_LO, sbase + S_WHI + OFF_W2, sbase + S_WLO + OFF_W2, 64,
+                     64, BF16);
+      tc::commit_to(mbar);
+    }
+    INVR_SPLIT_WAIT();
+    relu_split64<BF16>(row, m2);
+    tmem_ready();
+    // ---- layer 3: H2 -> o (16)
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_split_ts(tmem + T_ACC, tmem + T_HI, tmem + T_LO, sbase + S_WHI + OFF_W3, sbase + S_WLO + OFF_W3, 64,
+                     16, BF16);
+      tc::commit_to(mbar);
+    }
+    INVR_SPLIT_WAIT();
+    float sigma;
+    {
+      float o[16];
+      tc::tmem_ld16(row + T_ACC, o);
+      sigma = expf(o[0]);
+      o[0] = 0.0f;  // o_0 does not feed the colour MLP (W4p has a zero column for it)
+      uint32_t hi[8], lo[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) tc::split2<BF16>(o[2 * c], o[2 * c + 1], hi[c], lo[c]);
+      tc::tmem_st8(row + T_HI, hi);
+      tc::tmem_st8(row + T_LO, lo);
+    }
+    tmem_ready();
+    // ---- layer 4: O -> H4
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_split_ts(tmem + T_ACC, tmem + T_HI, tmem + T_LO, sbase + S_WHI + OFF_W4, sbase + S_WLO + OFF_W4, 16,
+                     64, BF16);
+      tc::commit_to(mbar);
+    }
+    INVR_SPLIT_WAIT();
+    relu_split64<BF16>(row, m4);
+    tmem_ready();
+    // ---- layer 5: H4 -> rgb
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue_split_ts(tmem + T_ACC, tmem + T_HI, tmem + T_LO, sbase + S_WHI + OFF_W5, sbase + S_WLO + OFF_W5, 64,
+                     16, BF16);
+      tc::commit_to(mbar);
+    }
+    INVR_SPLIT_WAIT();
+    {
+      float z[16];
+      tc::tmem_ld16(row + T_ACC, z);
+      if (t < valid) {
+        const int64_t gs = s0 + t;
+        A.out[gs] = sigma;
+        A.out[A.ld + gs] = 1.0f / (1.0f + expf(-z[0]));
+        A.out[2 * A.ld + gs] = 1.0f / (1.0f + expf(-z[1]));
+        A.out[3 * A.ld + gs] = 1.0f / (1.0f + expf(-z[2]));
+        A.mask[gs] = m1[0];
+        A.mask[A.ld + gs] = m1[1];
+        A.mask[2 * A.ld + gs] = m2[0];
+        A.mask[3 * A.ld + gs] = m2[1];
+        A.mask[4 * A.ld + gs] = m4[0];
+        A.mask[5 * A.ld + gs] = m4[1];
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // every thread is done with this tile's accumulator
+    tile = nxt;
+  }
+#undef INVR_SPLIT_WAIT
+  if (!ok) {
+    if (t == 0) atomicOr(A.status, kStatusTimeout);
+    if (mma_pending && !tc::mbar_wait(mbar, phase, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
+    if (x_pending && !tc::mbar_wait(xbar, xphase, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemSplit);
+  }
 }
 
 }  // namespace
@@ -406,6 +722,45 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (plan_has_kind(P, kMlpBF16)) e = launch_tc<true, true>(A, num_sms, s);
   if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) e = launch_tc<false, true>(A, num_sms, s);
+  return e;
+}
+
+cudaError_t preload_mlp_points_tc() {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_mlp_fwd_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
+  return e != cudaSuccess
+             ? e
+             : cudaFuncSetAttribute(k_mlp_fwd_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemTC);
+}
+
+cudaError_t launch_mlp_fwd_split_tc(const Plan& P, int num_sms, cudaStream_t s) {
+  SplitArgs A{};
+  A.out = P.ws.out;
+  A.mask = P.ws.mlp_mask;
+  A.view_base = P.ws.view_base;
+  A.ld = P.ws.S_cap;
+  A.n_views = P.n_views;
+  A.wait_limit = P.wait_limit;
+  A.status = P.status;
+  for (int v = 0; v < P.n_views; ++v) A.f[v] = P.v[v].field;
+  uint8_t* feat = static_cast<uint8_t*>(P.ws.feat);
+  for (int w = 0; w < 2; ++w)
+    for (int h = 0; h < 2; ++h)
+      if (!encode_feat16_map(&A.xmap[w][h], feat + (h ? feat16_lo_offset(P.ws.S_cap) : 0), P.ws.S_cap,
+                             w ? 32 : 16))
+        return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  if (plan_has_kind(P, kMlpBF16)) {
+    cudaFuncSetAttribute(k_mlp_fwd_split_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSplit);
+    k_mlp_fwd_split_tc<true><<<num_sms * kCtasSplit, kThreadsTC, kSmemSplit, s>>>(A);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) {
+    cudaFuncSetAttribute(k_mlp_fwd_split_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSplit);
+    k_mlp_fwd_split_tc<false><<<num_sms * kCtasSplit, kThreadsTC, kSmemSplit, s>>>(A);
+    e = cudaGetLastError();
+  }
   return e;
 }
 

@@ -7,7 +7,8 @@
 // Per 128-sample tile (epilogue thread t = sample t, row t of every M = 128 MMA):
 //   recompute  X -> H1 -> H2 -> O -> H4          (4 chained MMAs, ReLU epilogues)
 //   adjoint    dZ -> dH4 -> dO -> dH2 -> dH1 -> dX (5 chained MMAs; each reads the forward
-//              weight as an MN-major operand; ReLU masks read back from the stored activations)
+//              weight as an MN-major operand; the ReLU decisions are the training forward's,
+//              taken on split products, one bit per unit and sample)
 //   weights    dW5^T += H4^T dZ, dW4 += dH4^T O, dW3^T += H2^T dO, dW2 += dH2^T H1,
 //              dW1 += dH1^T X: M = 64 MMAs with K = the 128 samples, accumulated in tensor
 //              memory over every tile the CTA visits.
@@ -81,6 +82,7 @@ struct TcBwdArgs {
   const float* dout;        // [4][ld]: dL/do_0, dL/dz_rgb
   float* dfeat;             // [in][ld]
   const int32_t* s_ray;     // padding marker (< 0) or null
+  const uint32_t* mask;     // [6][ld] ReLU decisions of H1, H2, H4 from the training forward
   const int32_t* view_base;
   int64_t ld;
   int n_views;
@@ -188,14 +190,17 @@ __device__ __forceinline__ void load_x(const TcBwdArgs& A, int64_t tile, int in,
   __syncwarp();
 }
 
-// This thread's raw dL/do_0, dL/dz_rgb and padding marker of tile `tile` (slot < S: view
-// ranges are whole tiles).  No load depends on another, so all stay in flight under the
-// chain; padding slots (marker < 0) are zeroed where the values are used.
-__device__ __forceinline__ void load_dout(const TcBwdArgs& A, int64_t tile, int t, float (&d)[4], int& ray) {
+// This thread's raw dL/do_0, dL/dz_rgb, ReLU decisions and padding marker of tile `tile`
+// (slot < S: view ranges are whole tiles).  No load depends on another, so all stay in
+// flight under the chain; padding slots (marker < 0) are zeroed where the values are used.
+__device__ __forceinline__ void load_dout(const TcBwdArgs& A, int64_t tile, int t, float (&d)[4], uint32_t (&m)[6],
+                                          int& ray) {
   const int64_t s = tile * kTM + t;
   ray = A.s_ray ? A.s_ray[s] : 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) d[i] = A.dout[(int64_t)i * A.ld + s];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) m[i] = A.mask[(int64_t)i * A.ld + s];
 }
 
 // Epilogue thread: this thread's writes to MMA operands (shared memory) and reads of the
@@ -334,8 +339,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     if (!ok && lane == 0) atomicOr(A.status, kStatusTimeout);
     // retire every MMA and copy of this CTA (bounded) before the tensor memory is freed
     if (lane == 0) tc::commit_to(drain_bar);
-    tc::mbar_wait(drain_bar, 0, kWaitLimit);
-    if (x_pending) tc::mbar_wait(x_bar, x_ph, kWaitLimit);
+    if (!tc::mbar_wait(drain_bar, 0, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
+    if (x_pending && !tc::mbar_wait(x_bar, x_ph, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
   } else {
     // ================================================================ epilogue warps
     const uint32_t row_t = tmem + ((uint32_t)(warp * 32) << 16);
@@ -345,8 +350,9 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     int64_t tile = first;
     int vn = v_first;  // view of the next tile to process
     float dnext[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    uint32_t mnext[6] = {0u, 0u, 0u, 0u, 0u, 0u}, m[6];
     int ray_next = -1;
-    if (tile < n_tiles) load_dout(A, tile, t, dnext, ray_next);
+    if (tile < n_tiles) load_dout(A, tile, t, dnext, mnext, ray_next);
 #define INVR_ACC_WAIT()                                   \
   if (!(ok = tc::mbar_wait(acc_bar, acc_ph, A.wait_limit))) break; \
   acc_ph ^= 1u;                                           \
@@ -372,6 +378,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       // ---- dZ row (dL/dz for rgb; zero for the padded outputs) and dL/do_0 of this tile
       const bool live = t < valid && ray_next >= 0;
       const float do0 = live ? dnext[0] * A.in_scale : 0.0f;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) m[i] = mnext[i];
       {
         float dz[16];
 #pragma unroll
@@ -381,12 +389,12 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       epi_arrive(opr_bar);
       // ---- S1: H1
       INVR_ACC_WAIT();
-      if (nxt < n_tiles) load_dout(A, nxt, t, dnext, ray_next);
-      row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H1, nullptr, t);
+      if (nxt < n_tiles) load_dout(A, nxt, t, dnext, mnext, ray_next);
+      row64_relu<BF16>(row_t + C_CHAIN, sm + B_H1, t);
       epi_arrive(opr_bar);
       // ---- S2: H2
       INVR_ACC_WAIT();
-      row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H2, nullptr, t);
+      row64_relu<BF16>(row_t + C_CHAIN, sm + B_H2, t);
       epi_arrive(opr_bar);
       // ---- S3: O = (0, o_1..o_15)
       INVR_ACC_WAIT();
@@ -399,11 +407,11 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       epi_arrive(opr_bar);
       // ---- S4: H4
       INVR_ACC_WAIT();
-      row64_out<BF16, false>(row_t + C_CHAIN, sm + B_H4, nullptr, t);
+      row64_relu<BF16>(row_t + C_CHAIN, sm + B_H4, t);
       epi_arrive(opr_bar);
       // ---- S5: dH4
       INVR_ACC_WAIT();
-      row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH4, sm + B_H4, t);
+      row64_masked<BF16>(row_t + C_CHAIN, sm + B_DH4, m[4], m[5], t);
       epi_arrive(opr_bar);
       // ---- S6: dO (o_0 slot carries dL/do_0), over dZ
       INVR_ACC_WAIT();
@@ -416,11 +424,11 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       epi_arrive(opr_bar);
       // ---- S7: dH2, over H4
       INVR_ACC_WAIT();
-      row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH2, sm + B_H2, t);
+      row64_masked<BF16>(row_t + C_CHAIN, sm + B_DH2, m[2], m[3], t);
       epi_arrive(opr_bar);
       // ---- S8: dH1, over H2
       INVR_ACC_WAIT();
-      row64_out<BF16, true>(row_t + C_CHAIN, sm + B_DH1, sm + B_H1, t);
+      row64_masked<BF16>(row_t + C_CHAIN, sm + B_DH1, m[0], m[1], t);
       epi_arrive(opr_bar);
       // ---- S9: dX -> dL/dfeat (its TMEM read is covered by the next tile's first arrival)
       INVR_ACC_WAIT();
@@ -464,6 +472,7 @@ cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   A.dout = P.ws.dout;
   A.dfeat = P.ws.dfeat;
   A.s_ray = P.ws.s_ray;
+  A.mask = P.ws.mlp_mask;
   A.view_base = P.ws.view_base;
   A.ld = P.ws.S_cap;
   A.n_views = P.n_views;

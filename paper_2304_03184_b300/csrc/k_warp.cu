@@ -206,6 +206,11 @@ cudaError_t launch_warp_points(const WarpDev& w, int64_t n, const float* p, floa
   return cudaGetLastError();
 }
 
+cudaError_t preload_warp_points() {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, k_warp_points);
+}
+
 // ------------------------------------------------------------------ per-frame setup
 __global__ void k_graph_pack(const float* __restrict__ dq, const float* __restrict__ x, int n, float4* dq_out,
                              float4* x_out) {

@@ -63,46 +63,42 @@ __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint32_t a_saddr, u
   }
 }
 
-// Per 16-bit half of a stored ReLU output w (each half +0, -0 or positive): 0xFFFF where the
-// half is positive, else 0 (one packed half-precision compare).
+// Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0) as row t
+// of a K = 64 16-bit operand.
 template <bool BF16>
-__device__ __forceinline__ uint32_t positive_halves(uint32_t w) {
-  if constexpr (BF16) {
-    return __hgt2_mask(*reinterpret_cast<const __nv_bfloat162*>(&w), __nv_bfloat162(__float2bfloat16(0.0f), __float2bfloat16(0.0f)));
-  } else {
-    return __hgt2_mask(*reinterpret_cast<const __half2*>(&w), __half2(__float2half(0.0f), __float2half(0.0f)));
-  }
-}
-
-// Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0) (or v
-// where the mask row is positive, if MASK) as row t of a K = 64 16-bit operand.  A masked
-// value is rounded first and its 16 bits cleared where the mask is not positive (the same
-// bits as rounding 0).  The whole mask row is read before any chunk of dst is written, so
-// dst may also be the mask buffer itself.
-template <bool BF16, bool MASK>
-__device__ __forceinline__ void row64_out(uint32_t taddr, uint8_t* dst, const uint8_t* mask, int t) {
-  uint4 m[8];
-  if constexpr (MASK) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) m[c] = *reinterpret_cast<const uint4*>(mask + tc::kmajor_offset(t, 8 * c, 64));
-  }
+__device__ __forceinline__ void row64_relu(uint32_t taddr, uint8_t* dst, int t) {
   float v[64];
   tc::tmem_ld64(taddr, v);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float* x = v + 8 * c;
     uint4 q;
-    if constexpr (MASK) {
-      q.x = tc::pack2<BF16>(x[0], x[1]) & positive_halves<BF16>(m[c].x);
-      q.y = tc::pack2<BF16>(x[2], x[3]) & positive_halves<BF16>(m[c].y);
-      q.z = tc::pack2<BF16>(x[4], x[5]) & positive_halves<BF16>(m[c].z);
-      q.w = tc::pack2<BF16>(x[6], x[7]) & positive_halves<BF16>(m[c].w);
-    } else {
-      q.x = tc::pack2<BF16>(fmaxf(x[0], 0.0f), fmaxf(x[1], 0.0f));
-      q.y = tc::pack2<BF16>(fmaxf(x[2], 0.0f), fmaxf(x[3], 0.0f));
-      q.z = tc::pack2<BF16>(fmaxf(x[4], 0.0f), fmaxf(x[5], 0.0f));
-      q.w = tc::pack2<BF16>(fmaxf(x[6], 0.0f), fmaxf(x[7], 0.0f));
-    }
+    q.x = tc::pack2<BF16>(fmaxf(x[0], 0.0f), fmaxf(x[1], 0.0f));
+    q.y = tc::pack2<BF16>(fmaxf(x[2], 0.0f), fmaxf(x[3], 0.0f));
+    q.z = tc::pack2<BF16>(fmaxf(x[4], 0.0f), fmaxf(x[5], 0.0f));
+    q.w = tc::pack2<BF16>(fmaxf(x[6], 0.0f), fmaxf(x[7], 0.0f));
+    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
+  }
+}
+
+// Read 64 accumulator columns of this thread's row; write each value where its unit's ReLU
+// decision (bit j of m[j / 32], from the training forward) is positive, else 0, as row t of
+// a K = 64 16-bit operand.
+template <bool BF16>
+__device__ __forceinline__ void row64_masked(uint32_t taddr, uint8_t* dst, uint32_t m0, uint32_t m1, int t) {
+  float v[64];
+  tc::tmem_ld64(taddr, v);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t b = (c < 4 ? m0 : m1) >> (8 * (c & 3));
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = ((b >> i) & 1u) ? v[8 * c + i] : 0.0f;
+    uint4 q;
+    q.x = tc::pack2<BF16>(x[0], x[1]);
+    q.y = tc::pack2<BF16>(x[2], x[3]);
+    q.z = tc::pack2<BF16>(x[4], x[5]);
+    q.w = tc::pack2<BF16>(x[6], x[7]);
     *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
   }
 }

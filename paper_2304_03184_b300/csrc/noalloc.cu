@@ -25,24 +25,39 @@ constexpr int64_t kScratchFloats = (3 + kMaxIn) * kMaxPoints;  // 35 x 65536 flo
 static __device__ __align__(256) float g_query_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
-float* g_scratch_addr[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
+float* g_scratch_addr[kMaxDevices];  // null until a lookup on that device succeeded
+std::mutex g_scratch_mu;
 
-// Device address of the scratch array on `dev` (which the caller has made current); looked
-// up once per device.
+// Device address of the scratch array on `dev` (which the caller has made current).  Only a
+// successful lookup is kept, so a failed one (for example during a stream capture, or with
+// an error pending) is retried by the next call.
 cudaError_t scratch_on(int dev, float** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_scratch_once[dev], [dev] {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
     void* p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_query_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_query_scratch);
+    if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = static_cast<float*>(p);
-  });
+  }
   *out = g_scratch_addr[dev];
-  return g_scratch_err[dev];
+  return cudaSuccess;
 }
 
 }  // namespace
+
+// Called by invr_ctx_create with `dev` current.  The address lookup loads this file's module
+// (and with it the scratch array), and the preloads load the kernels the query launches; with
+// lazy module loading both would otherwise happen inside the first query, as allocations.
+cudaError_t invr::noalloc_prepare(int dev) {
+  float* p = nullptr;
+  cudaError_t e = scratch_on(dev, &p);
+  if (e == cudaSuccess) e = preload_warp_points();
+  if (e == cudaSuccess) e = preload_encode_points();
+  if (e == cudaSuccess) e = preload_mlp_points_f32();
+  if (e == cudaSuccess) e = preload_mlp_points_tc();
+  return e;
+}
 
 extern "C" invr_status invr_query_points_noalloc(invr_ctx ctx, const invr_field_view* view, int64_t n,
                                                  const float* p, float* out, invr_stream stream) {

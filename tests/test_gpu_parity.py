@@ -403,22 +403,32 @@ def _train_both(env, tw: synth.TrainWorkload, prec=0, loss="huber", depth_weight
     return tb, gfields, ofields, obatches, keep
 
 
-def _assert_grads_close(g, want, what, rtol=GRAD_RTOL):
-    """Relative L2 error of one gradient tensor (a hash level or a weight matrix)."""
+def _assert_grads_close(g, want, what, rtol=GRAD_RTOL, entry=False):
+    """One gradient tensor (a hash level or a weight matrix): relative L2 error <= rtol and,
+    if `entry`, every entry within rtol of itself plus rtol of the tensor's RMS over the
+    entries the oracle touches (an entry summing many cancelling per-sample terms carries
+    the absolute rounding of those terms).  The per-entry form catches a few wrong entries
+    that the norm of a 2^20-entry level would hide (a wrong slot on a rare hash path)."""
     n = np.linalg.norm(want)
     assert n > 0, what
     rel = np.linalg.norm(g - want) / n
     assert rel <= rtol, (what, rel, rtol)
+    if entry:
+        touched = want != 0
+        rms = np.sqrt(np.mean(want[touched] ** 2))
+        err = np.abs(g - want)
+        bad = err > rtol * np.abs(want) + rtol * rms
+        assert not bad.any(), (what, int(bad.sum()), float(err.max()), float(rms))
 
 
-def _assert_field_grads(gt, gw, ogt, ogw, desc, rtol):
+def _assert_field_grads(gt, gw, ogt, ogw, desc, rtol, entry=False):
     per_level = desc.T * desc.F
     for l in range(desc.L):
         sl = slice(l * per_level, (l + 1) * per_level)
-        _assert_grads_close(gt[sl], ogt[sl], f"table level {l}", rtol)
+        _assert_grads_close(gt[sl], ogt[sl], f"table level {l}", rtol, entry)
     off = 0
     for i, (r, c) in enumerate(desc.weight_shapes()):
-        _assert_grads_close(gw[off:off + r * c], ogw[off:off + r * c], f"W{i + 1}", rtol)
+        _assert_grads_close(gw[off:off + r * c], ogw[off:off + r * c], f"W{i + 1}", rtol, entry)
         off += r * c
 
 
@@ -471,7 +481,7 @@ def test_train_gradients_identity_motion(env):
     fp = tw.fields[0]
     gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
     ogt, ogw = ograds[id(ofields[id(fp)])]
-    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL)
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL, entry=True)
 
 
 def test_train_gradients_16_features(env):
@@ -492,16 +502,16 @@ def test_train_gradients_16_features(env):
     fp = tw.fields[0]
     gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
     ogt, ogw = ograds[id(ofields[id(fp)])]
-    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL)
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL, entry=True)
 
 
-# Mixed-precision gradients per tensor vs the FP64 oracle.  The MLP runs in 16 bit, so a
-# fraction of ReLU decisions (pre-activations within ~1 unit of roundoff of zero) differ
-# from the FP64 network's: ~0.2 per sample in FP16, ~4x more in BF16.  MLP-weight gradients
-# average over every sample and stay within the 1e-2 target; a fine hash level's entries
-# have one or two samples each and carry the per-sample error.
+# Mixed-precision gradients per tensor vs the FP64 oracle: the benchmark spec's bound of 1e-2
+# relative for every hash level and weight matrix, through the FP32 warp.  The training
+# forward takes its ReLU decisions on split 16-bit products (values plus rounding
+# remainders), so they agree with the FP64 network's as in FP32; what is left is the 16-bit
+# rounding of the adjoint chain's deltas and weights.
 MIXED_W_RTOL = 1e-2
-MIXED_TABLE_RTOL = {"fp16": 5e-2, "bf16": 1.5e-1}
+MIXED_TABLE_RTOL = {"fp16": 1e-2, "bf16": 1e-2}
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
@@ -514,7 +524,7 @@ def test_train_gradients_mixed_precision(env, prec):
     invr.backward(ctx, tb)
     ctx.sync()
     oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
-    assert abs(float(host(loss)[0]) - oloss) <= 1e-3 * oloss
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss  # the split forward's loss is as exact as FP32's
     fp = tw.fields[0]
     gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
     ogt, ogw = ograds[id(ofields[id(fp)])]
@@ -527,6 +537,29 @@ def test_train_gradients_mixed_precision(env, prec):
     for i, (r, c) in enumerate(d.weight_shapes()):
         _assert_grads_close(gw[off:off + r * c], ogw[off:off + r * c], f"W{i + 1}", MIXED_W_RTOL)
         off += r * c
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp16", 2e-3), ("bf16", 1e-2)])
+def test_train_gradients_mixed_identity_motion(env, prec, rtol):
+    """Mixed precision with identity motion (no warp rounding), so the 16-bit MLP chain is
+    measured alone: FP16 within 2e-3 per hash level and weight matrix (measured <= 7.7e-4),
+    BF16 within 1e-2 (<= 5.2e-3); the loss within 1e-5 relative."""
+    invr, ctx, oracle = env
+    code = invr.INVR_MLP_BF16 if prec == "bf16" else invr.INVR_MLP_FP16
+    tw = synth.train_step_workload(seed=7, n_rays=1536)
+    g = tw.batches[0].view.graph
+    g.dq[:] = np.array([1, 0, 0, 0, 0, 0, 0, 0], np.float32)[:, None]
+    g.x_live[:] = g.x_canon
+    tb, gfields, ofields, obatches, _ = _train_both(env, tw, code)
+    loss = invr.forward_train(ctx, tb)
+    invr.backward(ctx, tb)
+    ctx.sync()
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
+    fp = tw.fields[0]
+    gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
+    ogt, ogw = ograds[id(ofields[id(fp)])]
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, rtol)
 
 
 # ------------------------------------------------ the paper's losses (Sec. 4.4)
@@ -564,7 +597,7 @@ def test_paper_loss_gradients_identity_motion(env):
     fp = tw.fields[0]
     gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
     ogt, ogw = ograds[id(ofields[id(fp)])]
-    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL)
+    _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL, entry=True)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -579,7 +612,7 @@ def test_paper_loss_keyframe_two_fields(env, prec):
     invr.backward(ctx, tb)
     ctx.sync()
     oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta, loss="paper")
-    assert abs(float(host(loss)[0]) - oloss) <= (1e-5 if prec == "fp32" else 2e-3) * oloss
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
     w_rtol = GRAD_RTOL_WARP if prec == "fp32" else MIXED_W_RTOL
     for fp in tw.fields:
         gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
@@ -623,7 +656,7 @@ def test_fields_of_both_precisions_in_one_call(env):
     invr.backward(ctx, tb)
     ctx.sync()
     oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
-    assert abs(float(host(loss)[0]) - oloss) <= 2e-3 * oloss
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
     for fp, w_rtol, t_rtol in ((human, GRAD_RTOL_WARP, GRAD_RTOL_WARP), (obj, MIXED_W_RTOL, MIXED_TABLE_RTOL["bf16"])):
         gt, gw = (host(x) for x in gfields[id(fp)].get_grads())
         ogt, ogw = ograds[id(ofields[id(fp)])]

@@ -77,3 +77,48 @@ def test_noalloc_query_rejects_oversize(ctx_env):
     p = _cu(np.zeros((3, invr.NOALLOC_MAX_POINTS + 1), np.float32))
     with pytest.raises(invr.InvrError, match="INVR_NOALLOC_MAX_POINTS"):
         invr.query_points_noalloc(ctx, hv, p)
+
+
+def _pool_attr(rt, pool, attr):
+    err, v = rt.cudaMemPoolGetAttribute(pool, attr)
+    assert err == rt.cudaError_t.cudaSuccess
+    return int(v)
+
+
+def test_noalloc_query_allocates_nothing(ctx_env):
+    """What the entry point is for: a call, including the first one on a new context, leaves
+    the device's memory use unchanged.  Checked around two calls per MLP path (FP32 and BF16
+    tensor cores) with the output pre-allocated by the caller: the device's free memory
+    (a cudaMalloc or a lazily loaded module would lower it), the high-water mark of the
+    device's default stream-ordered pool (cudaMallocAsync) and torch's allocator peak."""
+    invr, _ = ctx_env
+    import torch
+    from cuda.bindings import driver as drv, runtime as rt
+    ctx = invr.Context(0)                    # sets the query up (address lookup, kernel loads)
+    rng = np.random.default_rng(43)
+    (fh, graph, hv), (fo, ov), g = _views(invr, ctx, rng)
+    fb = invr.Field.from_synth(ctx, synth.make_field(rng, synth.CFG1_FIELD), invr.INVR_MLP_BF16)
+    dq, _, _ = synth.make_object_pose(rng)
+    bv = invr.View(fb, rigid_dq=dq)
+    p = _cu(rng.uniform(-1, 1, size=(3, 5000)).astype(np.float32))
+    out = torch.empty((4, 5000), device="cuda")
+    torch.cuda.synchronize()
+    err, pool = rt.cudaDeviceGetDefaultMemPool(0)
+    assert err == rt.cudaError_t.cudaSuccess
+    high = rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh
+    used = rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent
+    err, = rt.cudaMemPoolSetAttribute(pool, high, drv.cuuint64_t(0))   # high mark := current use
+    assert err == rt.cudaError_t.cudaSuccess
+    used0 = _pool_attr(rt, pool, used)
+    torch.cuda.reset_peak_memory_stats()
+    peak0 = torch.cuda.max_memory_allocated()
+    free0 = torch.cuda.mem_get_info()[0]
+    for view in (hv, bv, hv, bv):
+        invr.query_points_noalloc(ctx, view, p, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert _pool_attr(rt, pool, high) == used0
+    assert torch.cuda.max_memory_allocated() == peak0
+    want = invr.query_points(ctx, bv, p)
+    ctx.sync()
+    np.testing.assert_allclose(out.cpu().numpy(), want.cpu().numpy(), rtol=0, atol=COLOUR_TOL)
