@@ -360,26 +360,30 @@ cudaError_t launch_tc(const TcArgs& A, int num_sms, cudaStream_t s) {
 
 
 // ====================================================================== training forward
-// The training forward of a 16-bit field with split operands: every layer's product is
-// formed as hi*hi + lo*hi + hi*lo from a 16-bit value and the 16-bit remainder of its
-// rounding (tc::split2), three MMAs into one FP32 accumulator.  The ReLU decisions of the
-// network are then taken at about twice the 16-bit precision: a pre-activation that rounds
-// across zero in plain 16-bit arithmetic flips its unit's gradient path in the backward,
-// and these flips, not the 16-bit rounding of values, are what carries the gradient error
-// of the plain 16-bit chain.  The kernel writes sigma, rgb and the ReLU decisions (one bit
-// per hidden unit of H1, H2, H4; [6][ld] words) that the backward applies.
+// The training forward of a 16-bit field with split operands: every tensor-core product is
+// formed as hi*hi + lo*hi + hi*lo of a 16-bit value and the 16-bit remainder of its rounding
+// (tc::split2), three MMAs into one FP32 accumulator.  The ReLU decisions of the network are
+// then taken at about twice the 16-bit precision: a pre-activation that rounds across zero in
+// plain 16-bit arithmetic flips its unit's gradient path in the backward, and these flips,
+// not the 16-bit rounding of values, are what carries the gradient error of the plain 16-bit
+// chain.  The kernel writes sigma, rgb and the ReLU decisions (one bit per hidden unit of H1,
+// H2, H4; [6][ld] words) that the backward applies.
 //
-// Hidden activations never touch shared memory: each epilogue writes its row's hi and lo
-// halves into tensor memory, from which the next layer's MMAs read their A operand.  Per CTA
-// 128 tensor-memory columns (accumulator [0,64), activations hi [64,96), lo [96,128)) and 53 KB
-// of shared memory (weights hi and lo, one tile of X hi and lo): four CTAs per SM.  X hi/lo
-// arrive by two TMA boxes; the next tile's are issued once layer 1 has read this tile's.
+// Layers 1 (X -> H1), 2 (H1 -> H2), 3 (H2 -> o) and 4 (O -> H4) run on the tensor cores; the
+// colour output z = W5 H4 (3 x 64) is formed by each thread in FP32 from its FP32 ReLU values
+// (192 FMAs per sample instead of a fifth MMA stage).  Hidden activations never touch shared
+// memory: each epilogue writes its row's hi and lo halves into tensor memory, from which the
+// next layer's MMAs read their A operand.  Per CTA 128 tensor-memory columns (accumulator
+// [0,64), activations hi [64,96), lo [96,128)) and 49 KB of shared memory (W1..W4 hi and lo,
+// W5 in FP32, one tile of X hi and lo): four CTAs per SM.  X hi/lo arrive by two TMA boxes;
+// the next tile's are issued once layer 1 has read this tile's.
 constexpr int kCtasSplit = 4;
 constexpr uint32_t kTmemSplit = 128;
 constexpr uint32_t T_ACC = 0, T_HI = 64, T_LO = 96;
-constexpr uint32_t S_WHI = 0;                    // W1..W5 at the OFF_W* offsets
-constexpr uint32_t S_WLO = OFF_P;                // 18,432: the same layout, remainders
-constexpr uint32_t S_XHI = 2 * OFF_P;            // [128 x in]
+constexpr uint32_t S_WHI = 0;                    // W1..W4 at the OFF_W* offsets
+constexpr uint32_t S_WLO = OFF_W5;               // 16,384: the same layout, remainders
+constexpr uint32_t S_W5 = 2 * OFF_W5;            // W5 FP32 [3][64]
+constexpr uint32_t S_XHI = S_W5 + 1024;          // [128 x in]
 constexpr uint32_t S_XLO = S_XHI + kTM * 32 * 2;
 constexpr uint32_t S_MISC = S_XLO + kTM * 32 * 2;
 constexpr uint32_t kSmemSplit = S_MISC + 64;
@@ -409,13 +413,9 @@ __device__ __forceinline__ void stage_weight_split(uint8_t* hi, uint8_t* lo, con
       case 1: a = W[off.w1 + o * in + k]; b = W[off.w1 + o * in + k + 1]; break;
       case 2: a = W[off.w2 + o * kHidden + k]; b = W[off.w2 + o * kHidden + k + 1]; break;
       case 3: a = W[off.w3 + o * kHidden + k]; b = W[off.w3 + o * kHidden + k + 1]; break;
-      case 4:
+      default:  // column 0 of W4p is zero: o_0 does not feed the colour MLP
         a = k == 0 ? 0.0f : W[off.w4 + o * (kGeoOut - 1) + k - 1];
         b = W[off.w4 + o * (kGeoOut - 1) + k];
-        break;
-      default:
-        a = o < 3 ? W[off.w5 + o * kColHidden + k] : 0.0f;
-        b = o < 3 ? W[off.w5 + o * kColHidden + k + 1] : 0.0f;
         break;
     }
     uint32_t h, l;
@@ -437,7 +437,8 @@ __device__ void stage_weights_split(uint8_t* sm, const FieldDev& F) {
   stage_weight_split<BF16, 64, 64>(hi + OFF_W2, lo + OFF_W2, F.weights, 2, F.mlp_in, off);
   stage_weight_split<BF16, 16, 64>(hi + OFF_W3, lo + OFF_W3, F.weights, 3, F.mlp_in, off);
   stage_weight_split<BF16, 64, 16>(hi + OFF_W4, lo + OFF_W4, F.weights, 4, F.mlp_in, off);
-  stage_weight_split<BF16, 16, 64>(hi + OFF_W5, lo + OFF_W5, F.weights, 5, F.mlp_in, off);
+  float* w5 = reinterpret_cast<float*>(sm + S_W5);
+  for (int e = threadIdx.x; e < 3 * kColHidden; e += blockDim.x) w5[e] = F.weights[off.w5 + e];
 }
 
 // One thread: D = A B^T over K as split products, A in shared memory (the X tile).
@@ -468,25 +469,67 @@ __device__ __forceinline__ void issue_split_ts(uint32_t d, uint32_t a_hi, uint32
   }
 }
 
-// Epilogue of a 64-unit ReLU layer: read this thread's 64 accumulator columns, write ReLU(z)
-// as hi and lo halves into its tensor-memory lane (32 columns each) and return the decisions
-// z > 0 as two 32-bit masks (bit j of m[w] = unit 32 w + j).
-template <bool BF16>
-__device__ __forceinline__ void relu_split64(uint32_t row, uint32_t (&m)[2]) {
+// This thread's 64 accumulator columns (two loads, one wait).
+__device__ __forceinline__ void tmem_ld64_pair(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
+        "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]),
+        "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr + 32)
+      : "memory");
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float v[32];
-    tc::tmem_ld32(row + T_ACC + 32 * h, v);
-    uint32_t hi[16], lo[16], bits = 0;
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue of a 64-unit ReLU layer: ReLU of this thread's 64 accumulator columns into `h`
+// (FP32), written as hi and lo halves into its tensor-memory lane (32 columns each, waited
+// for once), and the decisions z > 0 as two 32-bit masks (bit j of m[w] = unit 32 w + j).
+template <bool BF16, bool STORE>
+__device__ __forceinline__ void relu_split64(uint32_t row, float (&h)[64], uint32_t (&m)[2]) {
+  tmem_ld64_pair(row + T_ACC, h);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      bits |= (v[2 * c] > 0.0f ? 1u : 0u) << (2 * c);
-      bits |= (v[2 * c + 1] > 0.0f ? 1u : 0u) << (2 * c + 1);
-      tc::split2<BF16>(fmaxf(v[2 * c], 0.0f), fmaxf(v[2 * c + 1], 0.0f), hi[c], lo[c]);
+  for (int w = 0; w < 2; ++w) {
+    uint32_t bits = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) bits |= (h[32 * w + j] > 0.0f ? 1u : 0u) << j;
+    m[w] = bits;
+  }
+#pragma unroll
+  for (int i = 0; i < 64; ++i) h[i] = fmaxf(h[i], 0.0f);
+  if constexpr (STORE) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) tc::split2<BF16>(h[32 * q + 2 * c], h[32 * q + 2 * c + 1], hi[c], lo[c]);
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+              row + T_HI + 16 * q),
+          "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]), "r"(hi[8]),
+          "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]), "r"(hi[15])
+          : "memory");
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+              row + T_LO + 16 * q),
+          "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]), "r"(lo[8]),
+          "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]), "r"(lo[15])
+          : "memory");
     }
-    m[h] = bits;
-    tc::tmem_st16(row + T_HI + 16 * h, hi);
-    tc::tmem_st16(row + T_LO + 16 * h, lo);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
 }
 
@@ -527,6 +570,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
   const uint32_t mbar = tc::smem_u32(sm + S_MISC);
   const uint32_t xbar = tc::smem_u32(sm + S_MISC + 8);
   const uint32_t sbase = tc::smem_u32(sm);
+  const float* w5 = reinterpret_cast<const float*>(sm + S_W5);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemSplit);
   if (t == 0) {
     tc::mbar_init(mbar, 1);
@@ -575,6 +619,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
     xphase ^= 1u;
     x_pending = false;
     uint32_t m1[2], m2[2], m4[2];
+    float h[64];
     // ---- layer 1: X (shared memory) -> H1
     if (t == 0) {
       tc::fence_after_sync();
@@ -583,12 +628,12 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
       tc::commit_to(mbar);
     }
     INVR_SPLIT_WAIT();
-    // X has been read: the next tile's lands while layers 2..5 run
+    // X has been read: the next tile's lands while layers 2..4 run
     if (nxt < n_tiles) {
       if (warp == 0) load_x_split(A, nxt, A.f[vn].mlp_in, sbase, xbar);
       x_pending = true;
     }
-    relu_split64<BF16>(row, m1);
+    relu_split64<BF16, true>(row, h, m1);
     tmem_ready();
     // ---- layer 2: H1 (tensor memory) -> H2
     if (t == 0) {
@@ -598,7 +643,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
       tc::commit_to(mbar);
     }
     INVR_SPLIT_WAIT();
-    relu_split64<BF16>(row, m2);
+    relu_split64<BF16, true>(row, h, m2);
     tmem_ready();
     // ---- layer 3: H2 -> o (16)
     if (t == 0) {
@@ -617,11 +662,16 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
       uint32_t hi[8], lo[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) tc::split2<BF16>(o[2 * c], o[2 * c + 1], hi[c], lo[c]);
-      tc::tmem_st8(row + T_HI, hi);
-      tc::tmem_st8(row + T_LO, lo);
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(row + T_HI),
+                   "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7])
+                   : "memory");
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(row + T_LO),
+                   "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7])
+                   : "memory");
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     tmem_ready();
-    // ---- layer 4: O -> H4
+    // ---- layer 4: O -> H4; colour z = W5 H4 in FP32 by each thread
     if (t == 0) {
       tc::fence_after_sync();
       issue_split_ts(tmem + T_ACC, tmem + T_HI, tmem + T_LO, sbase + S_WHI + OFF_W4, sbase + S_WLO + OFF_W4, 16,
@@ -629,35 +679,25 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
       tc::commit_to(mbar);
     }
     INVR_SPLIT_WAIT();
-    relu_split64<BF16>(row, m4);
-    tmem_ready();
-    // ---- layer 5: H4 -> rgb
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue_split_ts(tmem + T_ACC, tmem + T_HI, tmem + T_LO, sbase + S_WHI + OFF_W5, sbase + S_WLO + OFF_W5, 64,
-                     16, BF16);
-      tc::commit_to(mbar);
+    relu_split64<BF16, false>(row, h, m4);
+    float z[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int j = 0; j < kColHidden; ++j) z[c] = fmaf(w5[c * kColHidden + j], h[j], z[c]);
+    if (t < valid) {
+      const int64_t gs = s0 + t;
+      A.out[gs] = sigma;
+      A.out[A.ld + gs] = 1.0f / (1.0f + expf(-z[0]));
+      A.out[2 * A.ld + gs] = 1.0f / (1.0f + expf(-z[1]));
+      A.out[3 * A.ld + gs] = 1.0f / (1.0f + expf(-z[2]));
+      A.mask[gs] = m1[0];
+      A.mask[A.ld + gs] = m1[1];
+      A.mask[2 * A.ld + gs] = m2[0];
+      A.mask[3 * A.ld + gs] = m2[1];
+      A.mask[4 * A.ld + gs] = m4[0];
+      A.mask[5 * A.ld + gs] = m4[1];
     }
-    INVR_SPLIT_WAIT();
-    {
-      float z[16];
-      tc::tmem_ld16(row + T_ACC, z);
-      if (t < valid) {
-        const int64_t gs = s0 + t;
-        A.out[gs] = sigma;
-        A.out[A.ld + gs] = 1.0f / (1.0f + expf(-z[0]));
-        A.out[2 * A.ld + gs] = 1.0f / (1.0f + expf(-z[1]));
-        A.out[3 * A.ld + gs] = 1.0f / (1.0f + expf(-z[2]));
-        A.mask[gs] = m1[0];
-        A.mask[A.ld + gs] = m1[1];
-        A.mask[2 * A.ld + gs] = m2[0];
-        A.mask[3 * A.ld + gs] = m2[1];
-        A.mask[4 * A.ld + gs] = m4[0];
-        A.mask[5 * A.ld + gs] = m4[1];
-      }
-    }
-    tc::fence_before_sync();
-    __syncthreads();  // every thread is done with this tile's accumulator
     tile = nxt;
   }
 #undef INVR_SPLIT_WAIT
