@@ -9,6 +9,9 @@
 //   adjoint    dZ -> dH4 -> dO -> dH2 -> dH1 -> dX (5 chained MMAs; each reads the forward
 //              weight as an MN-major operand; the ReLU decisions are the training forward's,
 //              taken on split products, one bit per unit and sample)
+// Every chain MMA after the first reads its A operand from tensor memory: each epilogue
+// writes its 16-bit row twice, into shared memory for the weight-gradient MMAs and into its
+// tensor-memory lane for the next chain MMA, which then streams only B from shared memory.
 //   weights    dW5^T += H4^T dZ, dW4 += dH4^T O, dW3^T += H2^T dO, dW2 += dH2^T H1,
 //              dW1 += dH1^T X: M = 64 MMAs with K = the 128 samples, accumulated in tensor
 //              memory over every tile the CTA visits.
@@ -54,6 +57,7 @@ constexpr uint32_t C_DW1 = 128;     // 32
 constexpr uint32_t C_DW4 = 160;     // 16
 constexpr uint32_t C_DW3T = 176;    // 16
 constexpr uint32_t C_DW5T = 192;    // 16
+constexpr uint32_t C_AOP = 208;     // 32: the chain MMA's A operand (16-bit, packed in pairs)
 
 // shared-memory plan (bytes); [n][k] = K-major operand with n rows and k columns.  The
 // transposed products of the adjoint chain read the forward weights as MN-major operands.
@@ -121,16 +125,15 @@ __device__ void stage_bwd_weights(uint8_t* sm, const FieldDev& F, int t) {
   stage<BF16, false, 16, 64>(sm + B_W5, F.weights, off, in, 5, t, kEpi);
 }
 
-// One thread: adjoint-chain MMA D (128 x N) = dY (smem, 128 x K, K-major) * W, with W the
-// forward weight [K rows][N columns] (K-major in its own layout) read as an MN-major
-// operand: column groups 128 B apart, row groups N*16 B apart.
-__device__ __forceinline__ void issue_adjoint(uint32_t d_tmem, uint32_t a_saddr, uint32_t w_saddr, int K, int N,
-                                              bool bf16) {
+// One thread: adjoint-chain MMA D (128 x N) = dY * W, with W the forward weight [K rows][N
+// columns] (K-major in its own layout) read as an MN-major operand (column groups 128 B
+// apart, row groups N*16 B apart) and dY in tensor memory: 8 columns per K step of 16.
+__device__ __forceinline__ void issue_adjoint_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t w_saddr, int K, int N,
+                                                 bool bf16) {
   const uint32_t idesc = tc::idesc_f16(kTM, N, bf16) | (1u << 16);
   for (int kk = 0; kk < K / 16; ++kk) {
-    const uint64_t ad = tc::smem_desc(a_saddr + kk * 256, 128, K * 16);
     const uint64_t bd = tc::smem_desc(w_saddr + kk * 32 * N, N * 16, 128);
-    tc::mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    tc::mma_f16_ts(d_tmem, a_tmem + kk * 8, bd, idesc, kk > 0 ? 1u : 0u);
   }
 }
 
@@ -291,36 +294,36 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       }
       // ---- S2 H2, S3 O, S4 H4
       INVR_OPR_WAIT();
-      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + B_H1, sb + B_W2, 64, 64, BF16);
+      if (lane == 0) issue_chain_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W2, 64, 64, BF16);
       INVR_ACC_COMMIT();
       INVR_OPR_WAIT();
-      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + B_H2, sb + B_W3, 64, 16, BF16);
+      if (lane == 0) issue_chain_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W3, 64, 16, BF16);
       INVR_ACC_COMMIT();
       INVR_OPR_WAIT();
-      if (lane == 0) issue_chain(tmem + C_CHAIN, sb + B_O, sb + B_W4, 16, 64, BF16);
+      if (lane == 0) issue_chain_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W4, 16, 64, BF16);
       INVR_ACC_COMMIT();
       // ---- S5 dH4 = (dZ W5p) [H4 > 0];  dW5p^T += H4^T dZ
       INVR_OPR_WAIT();
-      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DZ, sb + B_W5, 16, 64, BF16);
+      if (lane == 0) issue_adjoint_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W5, 16, 64, BF16);
       INVR_ACC_COMMIT();
       if (lane == 0) issue_dw(tmem + C_DW5T, sb + B_H4, 64, sb + B_DZ, 16, 16, dw_live, BF16);
       // ---- S6 dO = dH4 W4p  (dW4p += dH4^T O is issued after S9)
       INVR_OPR_WAIT();
-      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH4, sb + B_W4, 64, 16, BF16);
+      if (lane == 0) issue_adjoint_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W4, 64, 16, BF16);
       INVR_ACC_COMMIT();
       // ---- S7 dH2 = (dO W3) [H2 > 0];  dW3^T += H2^T dO
       INVR_OPR_WAIT();
-      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DO, sb + B_W3, 16, 64, BF16);
+      if (lane == 0) issue_adjoint_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W3, 16, 64, BF16);
       INVR_ACC_COMMIT();
       if (lane == 0) issue_dw(tmem + C_DW3T, sb + B_H2, 64, sb + B_DO, 16, 16, dw_live, BF16);
       // ---- S8 dH1 = (dH2 W2) [H1 > 0];  dW2 += dH2^T H1
       INVR_OPR_WAIT();
-      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH2, sb + B_W2, 64, 64, BF16);
+      if (lane == 0) issue_adjoint_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W2, 64, 64, BF16);
       INVR_ACC_COMMIT();
       if (lane == 0) issue_dw(tmem + C_DW2, sb + B_DH2, 64, sb + B_H1, 64, 64, dw_live, BF16);
       // ---- S9 dX = dH1 W1;  dW1 += dH1^T X
       INVR_OPR_WAIT();
-      if (lane == 0) issue_adjoint(tmem + C_CHAIN, sb + B_DH1, sb + B_W1, 64, in, BF16);
+      if (lane == 0) issue_adjoint_ts(tmem + C_CHAIN, tmem + C_AOP, sb + B_W1, 64, in, BF16);
       INVR_ACC_COMMIT();
       if (lane == 0) {
         issue_dw(tmem + C_DW1, sb + B_DH1, 64, sb + bx, in, in, dw_live, BF16);
@@ -380,21 +383,19 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       const float do0 = live ? dnext[0] * A.in_scale : 0.0f;
 #pragma unroll
       for (int i = 0; i < 6; ++i) m[i] = mnext[i];
-      {
-        float dz[16];
+      float dz[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dz[i] = (i < 3 && live) ? dnext[1 + i] * A.in_scale : 0.0f;
-        row16_out<BF16>(dz, sm + B_DZ, t);
-      }
+      for (int i = 0; i < 16; ++i) dz[i] = (i < 3 && live) ? dnext[1 + i] * A.in_scale : 0.0f;
+      row16_out<BF16, false>(dz, sm + B_DZ, t, 0u);
       epi_arrive(opr_bar);
       // ---- S1: H1
       INVR_ACC_WAIT();
       if (nxt < n_tiles) load_dout(A, nxt, t, dnext, mnext, ray_next);
-      row64_relu<BF16>(row_t + C_CHAIN, sm + B_H1, t);
+      row64_relu<BF16, true>(row_t + C_CHAIN, sm + B_H1, t, row_t + C_AOP);
       epi_arrive(opr_bar);
       // ---- S2: H2
       INVR_ACC_WAIT();
-      row64_relu<BF16>(row_t + C_CHAIN, sm + B_H2, t);
+      row64_relu<BF16, true>(row_t + C_CHAIN, sm + B_H2, t, row_t + C_AOP);
       epi_arrive(opr_bar);
       // ---- S3: O = (0, o_1..o_15)
       INVR_ACC_WAIT();
@@ -402,16 +403,23 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
         float o[16];
         tc::tmem_ld16(row_t + C_CHAIN, o);
         o[0] = 0.0f;
-        row16_out<BF16>(o, sm + B_O, t);
+        row16_out<BF16, true>(o, sm + B_O, t, row_t + C_AOP);
       }
       epi_arrive(opr_bar);
       // ---- S4: H4
       INVR_ACC_WAIT();
-      row64_relu<BF16>(row_t + C_CHAIN, sm + B_H4, t);
+      row64_relu<BF16, false>(row_t + C_CHAIN, sm + B_H4, t, 0u);
+      {
+        // the adjoint chain starts from dZ: S5's A operand
+        uint32_t w[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) w[c] = tc::pack2<BF16>(dz[2 * c], dz[2 * c + 1]);
+        tc::tmem_st8(row_t + C_AOP, w);
+      }
       epi_arrive(opr_bar);
       // ---- S5: dH4
       INVR_ACC_WAIT();
-      row64_masked<BF16>(row_t + C_CHAIN, sm + B_DH4, m[4], m[5], t);
+      row64_masked<BF16, true>(row_t + C_CHAIN, sm + B_DH4, m[4], m[5], t, row_t + C_AOP);
       epi_arrive(opr_bar);
       // ---- S6: dO (o_0 slot carries dL/do_0), over dZ
       INVR_ACC_WAIT();
@@ -419,16 +427,16 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
         float d[16];
         tc::tmem_ld16(row_t + C_CHAIN, d);
         d[0] = do0;
-        row16_out<BF16>(d, sm + B_DO, t);
+        row16_out<BF16, true>(d, sm + B_DO, t, row_t + C_AOP);
       }
       epi_arrive(opr_bar);
       // ---- S7: dH2, over H4
       INVR_ACC_WAIT();
-      row64_masked<BF16>(row_t + C_CHAIN, sm + B_DH2, m[2], m[3], t);
+      row64_masked<BF16, true>(row_t + C_CHAIN, sm + B_DH2, m[2], m[3], t, row_t + C_AOP);
       epi_arrive(opr_bar);
       // ---- S8: dH1, over H2
       INVR_ACC_WAIT();
-      row64_masked<BF16>(row_t + C_CHAIN, sm + B_DH1, m[0], m[1], t);
+      row64_masked<BF16, true>(row_t + C_CHAIN, sm + B_DH1, m[0], m[1], t, row_t + C_AOP);
       epi_arrive(opr_bar);
       // ---- S9: dX -> dL/dfeat (its TMEM read is covered by the next tile's first arrival)
       INVR_ACC_WAIT();

@@ -52,6 +52,16 @@ __device__ __forceinline__ void stage(uint8_t* dst, const float* __restrict__ W,
   }
 }
 
+// One thread: D(tmem) = A(tmem, 128 x K: 8 columns per K step of 16) * B(smem, N x K, K-major)^T.
+__device__ __forceinline__ void issue_chain_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_saddr, int K, int N,
+                                               bool bf16) {
+  const uint32_t idesc = tc::idesc_f16(kTM, N, bf16);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t bd = tc::smem_desc(b_saddr + kk * 256, 128, K * 16);
+    tc::mma_f16_ts(d_tmem, a_tmem + kk * 8, bd, idesc, kk > 0 ? 1u : 0u);
+  }
+}
+
 // One thread: D(tmem) (+)= A(smem, 128 x K, K-major) * B(smem, N x K, K-major)^T.
 __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, int N,
                                             bool bf16) {
@@ -63,60 +73,57 @@ __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint32_t a_saddr, u
   }
 }
 
-// Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0) as row t
-// of a K = 64 16-bit operand.
-template <bool BF16>
-__device__ __forceinline__ void row64_relu(uint32_t taddr, uint8_t* dst, int t) {
+// The epilogues below write the next MMA's 16-bit A operand row t twice when TS: into shared
+// memory (K-major layout, for the weight-gradient MMAs) and into this thread's tensor-memory
+// lane at column `aop` (packed pairs, for the chain MMA, which then reads A from tensor
+// memory and leaves the shared-memory bandwidth to B).
+
+// Store 32 packed words as row t of a K = 64 operand (and in tensor memory if TS).
+template <bool TS>
+__device__ __forceinline__ void put_row64(const uint32_t (&w)[32], uint8_t* dst, int t, uint32_t aop) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) =
+        make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+  if constexpr (TS) tc::tmem_st32(aop, w);
+}
+
+// Read 64 accumulator columns of this thread's row (one tcgen05.ld); write max(v, 0).
+template <bool BF16, bool TS>
+__device__ __forceinline__ void row64_relu(uint32_t taddr, uint8_t* dst, int t, uint32_t aop) {
   float v[64];
   tc::tmem_ld64(taddr, v);
+  uint32_t w[32];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float* x = v + 8 * c;
-    uint4 q;
-    q.x = tc::pack2<BF16>(fmaxf(x[0], 0.0f), fmaxf(x[1], 0.0f));
-    q.y = tc::pack2<BF16>(fmaxf(x[2], 0.0f), fmaxf(x[3], 0.0f));
-    q.z = tc::pack2<BF16>(fmaxf(x[4], 0.0f), fmaxf(x[5], 0.0f));
-    q.w = tc::pack2<BF16>(fmaxf(x[6], 0.0f), fmaxf(x[7], 0.0f));
-    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
-  }
+  for (int c = 0; c < 32; ++c) w[c] = tc::pack2<BF16>(fmaxf(v[2 * c], 0.0f), fmaxf(v[2 * c + 1], 0.0f));
+  put_row64<TS>(w, dst, t, aop);
 }
 
 // Read 64 accumulator columns of this thread's row; write each value where its unit's ReLU
-// decision (bit j of m[j / 32], from the training forward) is positive, else 0, as row t of
-// a K = 64 16-bit operand.
-template <bool BF16>
-__device__ __forceinline__ void row64_masked(uint32_t taddr, uint8_t* dst, uint32_t m0, uint32_t m1, int t) {
+// decision (bit j of m[j / 32], from the training forward) is positive, else 0.
+template <bool BF16, bool TS>
+__device__ __forceinline__ void row64_masked(uint32_t taddr, uint8_t* dst, uint32_t m0, uint32_t m1, int t,
+                                             uint32_t aop) {
   float v[64];
   tc::tmem_ld64(taddr, v);
+  uint32_t w[32];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const uint32_t b = (c < 4 ? m0 : m1) >> (8 * (c & 3));
-    float x[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = ((b >> i) & 1u) ? v[8 * c + i] : 0.0f;
-    uint4 q;
-    q.x = tc::pack2<BF16>(x[0], x[1]);
-    q.y = tc::pack2<BF16>(x[2], x[3]);
-    q.z = tc::pack2<BF16>(x[4], x[5]);
-    q.w = tc::pack2<BF16>(x[6], x[7]);
-    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8 * c, 64)) = q;
+  for (int c = 0; c < 32; ++c) {
+    const uint32_t b = (c < 16 ? m0 : m1) >> (2 * (c & 15));
+    w[c] = tc::pack2<BF16>((b & 1u) ? v[2 * c] : 0.0f, (b & 2u) ? v[2 * c + 1] : 0.0f);
   }
+  put_row64<TS>(w, dst, t, aop);
 }
 
-// Write a row of 16 values as row t of a K = 16 16-bit operand.
-template <bool BF16>
-__device__ __forceinline__ void row16_out(const float (&v)[16], uint8_t* dst, int t) {
-  uint4 lo, hi;
-  lo.x = tc::pack2<BF16>(v[0], v[1]);
-  lo.y = tc::pack2<BF16>(v[2], v[3]);
-  lo.z = tc::pack2<BF16>(v[4], v[5]);
-  lo.w = tc::pack2<BF16>(v[6], v[7]);
-  hi.x = tc::pack2<BF16>(v[8], v[9]);
-  hi.y = tc::pack2<BF16>(v[10], v[11]);
-  hi.z = tc::pack2<BF16>(v[12], v[13]);
-  hi.w = tc::pack2<BF16>(v[14], v[15]);
-  *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 0, 16)) = lo;
-  *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8, 16)) = hi;
+// Write a row of 16 values as row t of a K = 16 16-bit operand (and in tensor memory if TS).
+template <bool BF16, bool TS>
+__device__ __forceinline__ void row16_out(const float (&v)[16], uint8_t* dst, int t, uint32_t aop) {
+  uint32_t w[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) w[c] = tc::pack2<BF16>(v[2 * c], v[2 * c + 1]);
+  *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(t, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+  if constexpr (TS) tc::tmem_st8(aop, w);
 }
 
 // Operand writes done by every thread -> visible to the tensor core; TMEM reads ordered.
