@@ -177,7 +177,7 @@ bool capturing(cudaStream_t s) {
 
 void free_workspace(Workspace& w) {
   void* ptrs[] = {w.ray_count, w.ray_bits, w.ray_first, w.ray_used, w.ray_out, w.block_sums, w.view_base, w.s_ray,
-                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.mlp_mask, w.loss_part,
+                  w.s_t, w.s_pos, w.s_vc, w.feat, w.out, w.dout, w.dfeat, w.mlp_mask, w.loss_part, w.tickets,
                   w.s_vt, w.feat_d, w.dvc, w.dfeat_d, w.def_x, w.def_h, w.def_g, w.def_gout};
   for (void* p : ptrs) dfree(p);
   w = Workspace{};
@@ -223,6 +223,7 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
   w.feat = feat;
   INVR_CUDA(ctx, dmalloc(&w.out, 4 * S));
   INVR_CUDA(ctx, dmalloc(&w.loss_part, R / 256 + 1));
+  INVR_CUDA(ctx, dmalloc(&w.tickets, kTicketSlots));
   if (train) {
     INVR_CUDA(ctx, dmalloc(&w.dout, 4 * S));
     INVR_CUDA(ctx, dmalloc(&w.dfeat, (size_t)kMaxIn * S));

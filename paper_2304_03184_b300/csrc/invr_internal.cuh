@@ -24,6 +24,8 @@ constexpr int kKnnG = 128;      // nearest-node candidate grid resolution over [
 constexpr uint16_t kKnnOverflow = 0xFFFF;
 constexpr int kRayBitWords = 32;   // 1024 samples per ray at most
 constexpr uint32_t kLutEmpty = 0xFFFFFFFFu;
+constexpr int kTicketSlots = 16;   // work counters: one per persistent launch kind
+constexpr int kTicketSplitFwd = 0;   // + 1 for the FP16 instantiation
 constexpr int kLossHuber = 0;      // values of invr_loss
 constexpr int kLossPaper = 1;
 
@@ -117,6 +119,7 @@ struct Workspace {
   float* dfeat;             // [mlp_in][S]
   uint32_t* mlp_mask;       // [6][S] training: ReLU decisions of H1, H2, H4 (tensor-core fields)
   float* loss_part;         // [n loss blocks]
+  uint32_t* tickets;        // [kTicketSlots] work counters of the persistent kernels (zeroed before each launch)
   // deformation net (allocated when a call has one)
   float* s_vt;              // [3][S] v_t, the warp before the net
   float* feat_d;            // [n_feat][S] the net's hash features

@@ -394,6 +394,7 @@ struct SplitArgs {
   CUtensorMap xmap[2][2];   // [in == 32][hi, lo]: TMA maps of the feature tiles and their remainders
   float* out;               // [4][ld]
   uint32_t* mask;           // [6][ld]: ReLU decisions of H1 (words 0, 1), H2 (2, 3), H4 (4, 5)
+  uint32_t* ticket;         // work counter of this launch (zero at launch)
   const int32_t* view_base;
   int64_t ld;
   int n_views;
@@ -501,6 +502,8 @@ __device__ __forceinline__ void tmem_ld64_pair(uint32_t taddr, float (&v)[64]) {
 template <bool BF16, bool STORE>
 __device__ __forceinline__ void relu_split64(uint32_t row, float (&h)[64], uint32_t (&m)[2]) {
   tmem_ld64_pair(row + T_ACC, h);
+  // one compare per unit gives an all-ones / all-zeros word: it sets the unit's mask bit and
+  // zeroes the value where z <= 0 (two logic operations, no selects or shifts)
 #pragma unroll
   for (int w = 0; w < 2; ++w) {
     uint32_t bits = 0;
@@ -539,30 +542,31 @@ __device__ __forceinline__ void tmem_ready() {
   __syncthreads();
 }
 
-__device__ __forceinline__ int64_t next_tile_split(const SplitArgs& A, const int32_t* vb, int64_t tile,
-                                                   int64_t n_tiles, int kind, int& v) {
-  for (; tile < n_tiles; tile += gridDim.x) {
-    v = advance_view(vb, A.n_views, tile * kTM, v);
-    if (A.f[v].mlp_kind == kind) return tile;
+// One thread: the next tile of this kernel's MLP kind by the launch's work counter (tiles are
+// handed out in increasing order, so a CTA's tiles increase too), or n_tiles.  Dynamic: CTAs
+// that run faster take more tiles (with a fixed stride, CTAs with equal tile counts finished
+// up to 50% apart).
+__device__ __forceinline__ int64_t grab_tile(const SplitArgs& A, const int32_t* vb, int64_t n_tiles, int kind) {
+  for (;;) {
+    const int64_t tile = (int64_t)atomicAdd(A.ticket, 1u);
+    if (tile >= n_tiles) return n_tiles;
+    if (A.f[view_of_slot(vb, A.n_views, tile * kTM)].mlp_kind == kind) return tile;
   }
-  return n_tiles;
 }
 
-// One warp (lane 0 works): X hi and lo of tile `tile` as two TMA boxes.
+// One thread: X hi and lo of tile `tile` as two TMA boxes.
 __device__ __forceinline__ void load_x_split(const SplitArgs& A, int64_t tile, int in, uint32_t sbase, uint32_t bar) {
-  if ((threadIdx.x & 31) == 0) {
-    const int w = in == 32 ? 1 : 0;
-    tc::mbar_expect_tx(bar, 2u * 16u * 16u * (uint32_t)in);
-    tc::tma_load_3d(sbase + S_XHI, &A.xmap[w][0], 0, (int)tile, 0, bar);
-    tc::tma_load_3d(sbase + S_XLO, &A.xmap[w][1], 0, (int)tile, 0, bar);
-  }
-  __syncwarp();
+  const int w = in == 32 ? 1 : 0;
+  tc::mbar_expect_tx(bar, 2u * 16u * 16u * (uint32_t)in);
+  tc::tma_load_3d(sbase + S_XHI, &A.xmap[w][0], 0, (int)tile, 0, bar);
+  tc::tma_load_3d(sbase + S_XLO, &A.xmap[w][1], 0, (int)tile, 0, bar);
 }
 
 template <bool BF16>
 __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(const __grid_constant__ SplitArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ int32_t vb[kMaxViews + 1];
+  __shared__ int64_t s_next;  // thread 0's next tile, read by all after the next barrier
   if ((int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5;
   if (t <= A.n_views) vb[t] = A.view_base[t];
@@ -588,10 +592,18 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
   uint32_t phase = 0, xphase = 0;
   bool ok = true, mma_pending = false, x_pending = false;
 
-  int vn = 0;
-  int64_t tile = next_tile_split(A, vb, blockIdx.x, n_tiles, kind, vn);
-  if (warp == 0 && tile < n_tiles) load_x_split(A, tile, A.f[vn].mlp_in, sbase, xbar);
-  x_pending = tile < n_tiles;
+  __syncthreads();  // vb
+  if (t == 0) {
+    const int64_t first = grab_tile(A, vb, n_tiles, kind);
+    if (first < n_tiles) {
+      load_x_split(A, first, A.f[view_of_slot(vb, A.n_views, first * kTM)].mlp_in, sbase, xbar);
+      x_pending = true;
+    }
+    s_next = first;
+  }
+  __syncthreads();
+  int64_t tile = s_next;
+  int vn = tile < n_tiles ? view_of_slot(vb, A.n_views, tile * kTM) : 0;
 
 #define INVR_SPLIT_WAIT()                                     \
   mma_pending = true;                                         \
@@ -604,7 +616,6 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
   while (tile < n_tiles) {
     const int64_t s0 = tile * kTM;
     const FieldDev& F = A.f[vn];
-    const int64_t nxt = next_tile_split(A, vb, tile + gridDim.x, n_tiles, kind, vn);
     if (F.weights != loaded) {
       __syncthreads();
       stage_weights_split<BF16>(sm, F);
@@ -628,10 +639,14 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
       tc::commit_to(mbar);
     }
     INVR_SPLIT_WAIT();
-    // X has been read: the next tile's lands while layers 2..4 run
-    if (nxt < n_tiles) {
-      if (warp == 0) load_x_split(A, nxt, A.f[vn].mlp_in, sbase, xbar);
-      x_pending = true;
+    // X has been read: thread 0 takes the CTA's next tile, whose X lands while layers 2..4 run
+    if (t == 0) {
+      const int64_t nt = grab_tile(A, vb, n_tiles, kind);
+      if (nt < n_tiles) {
+        load_x_split(A, nt, A.f[view_of_slot(vb, A.n_views, nt * kTM)].mlp_in, sbase, xbar);
+        x_pending = true;
+      }
+      s_next = nt;
     }
     relu_split64<BF16, true>(row, h, m1);
     tmem_ready();
@@ -684,7 +699,13 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int j = 0; j < kColHidden; ++j) z[c] = fmaf(w5[c * kColHidden + j], h[j], z[c]);
+      for (int j = 0; j < kColHidden; j += 4) {
+        const float4 w = *reinterpret_cast<const float4*>(w5 + c * kColHidden + j);  // one 16-byte broadcast load
+        z[c] = fmaf(w.x, h[j], z[c]);
+        z[c] = fmaf(w.y, h[j + 1], z[c]);
+        z[c] = fmaf(w.z, h[j + 2], z[c]);
+        z[c] = fmaf(w.w, h[j + 3], z[c]);
+      }
     if (t < valid) {
       const int64_t gs = s0 + t;
       A.out[gs] = sigma;
@@ -698,7 +719,8 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
       A.mask[4 * A.ld + gs] = m4[0];
       A.mask[5 * A.ld + gs] = m4[1];
     }
-    tile = nxt;
+    tile = s_next;  // written by thread 0 before this tile's layer-2 barrier
+    if (tile < n_tiles) vn = advance_view(vb, A.n_views, tile * kTM, vn);
   }
 #undef INVR_SPLIT_WAIT
   if (!ok) {
@@ -792,14 +814,18 @@ cudaError_t launch_mlp_fwd_split_tc(const Plan& P, int num_sms, cudaStream_t s) 
         return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (plan_has_kind(P, kMlpBF16)) {
+    A.ticket = P.ws.tickets + kTicketSplitFwd;
+    e = cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), s);
     cudaFuncSetAttribute(k_mlp_fwd_split_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSplit);
-    k_mlp_fwd_split_tc<true><<<num_sms * kCtasSplit, kThreadsTC, kSmemSplit, s>>>(A);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) k_mlp_fwd_split_tc<true><<<num_sms * kCtasSplit, kThreadsTC, kSmemSplit, s>>>(A);
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
   if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) {
+    A.ticket = P.ws.tickets + kTicketSplitFwd + 1;
+    e = cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), s);
     cudaFuncSetAttribute(k_mlp_fwd_split_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSplit);
-    k_mlp_fwd_split_tc<false><<<num_sms * kCtasSplit, kThreadsTC, kSmemSplit, s>>>(A);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) k_mlp_fwd_split_tc<false><<<num_sms * kCtasSplit, kThreadsTC, kSmemSplit, s>>>(A);
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
   return e;
 }
