@@ -329,19 +329,24 @@ invr_status invr_field_backward(invr_ctx ctx, const invr_train_args* args, float
 invr_status invr_field_adam(invr_field field, float lr, float beta1, float beta2, float eps, invr_stream stream);
 
 /* Autotuner of the launch shapes (CTAs per SM of the warp, encoding and gradient-scatter
- * kernels, and the level resolution up to which gradient runs are summed per warp before
- * the atomics): coordinate descent, each candidate timed with CUDA events on `stream` over
- * forward_train + backward of `args` (best of 2 after a warm-up run).  Parameters are not
- * changed (no Adam step); the gradients it accumulates are cleared.  The chosen shapes are
- * kept in the context for all later calls.  Synchronises `stream`; not during capture. */
+ * kernels, the level resolution up to which gradient runs are summed per warp before the
+ * atomics, whether the forward warps and encodes in one fused kernel per field or in two
+ * staged kernels, and the fused kernel's work-item size): coordinate descent, each candidate
+ * timed with CUDA events on `stream` over forward_train + backward of `args` (best of 2
+ * after a warm-up run).  Parameters are not changed (no Adam step); the gradients it
+ * accumulates are cleared.  The chosen shapes are kept in the context for all later calls.
+ * Synchronises `stream`; not during capture. */
 invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* args, invr_stream stream);
-/* The context's launch shapes: out4 = {warp CTAs/SM, encode CTAs/SM, scatter CTAs/SM,
- * aggregation resolution}. */
-invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4);
-/* Set the launch shapes directly (e.g. ones an earlier autotune returned): in4 as for
- * invr_ctx_get_tune.  CTAs per SM in [1, 32], aggregation resolution in [0, 2^20] (0: no
- * level sums runs).  INVR_E_ARG on a value out of range; the context is then unchanged. */
-invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in4);
+#define INVR_TUNE_N 6
+/* The context's launch shapes: out[INVR_TUNE_N] = {warp CTAs/SM, encode CTAs/SM, scatter
+ * CTAs/SM, aggregation resolution, fused warp + encoding (1) or staged (0), samples per work
+ * item of the fused kernel (128 or 256)}. */
+invr_status invr_ctx_get_tune(invr_ctx ctx, int* out);
+/* Set the launch shapes directly (e.g. ones an earlier autotune returned): in[INVR_TUNE_N]
+ * as for invr_ctx_get_tune.  CTAs per SM in [1, 32], aggregation resolution in [0, 2^20]
+ * (0: no level sums runs), fused 0 or 1, work item 128 or 256.  INVR_E_ARG on a value out
+ * of range; the context is then unchanged.  Views with a deformation net always run staged. */
+invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in);
 /* Polls of each bounded device-side wait (the tensor-core kernels' mbarrier waits) before
  * the kernel gives up, records INVR_E_TIMEOUT in the status word, lets its in-flight work
  * finish (its own drain wait, bounded by 2^22 polls whatever this setting), frees its tensor

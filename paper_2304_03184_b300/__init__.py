@@ -189,16 +189,16 @@ class Context:
         """Polls per bounded device wait (0: every wait gives up at once; default 2^22)."""
         _check(lib().invr_ctx_set_wait_limit(self.h, polls), self.h)
 
+    TUNE_KEYS = ("warp_ctas_per_sm", "encode_ctas_per_sm", "encode_bwd_ctas_per_sm", "agg_res", "fused", "chunk")
+
     def tune(self):
-        out = (C.c_int * 4)()
+        out = (C.c_int * len(self.TUNE_KEYS))()
         _check(lib().invr_ctx_get_tune(self.h, out), self.h)
-        return {"warp_ctas_per_sm": out[0], "encode_ctas_per_sm": out[1], "encode_bwd_ctas_per_sm": out[2],
-                "agg_res": out[3]}
+        return dict(zip(self.TUNE_KEYS, list(out)))
 
     def set_tune(self, tune: dict):
         """Set the launch shapes (a dict as returned by tune() / autotune())."""
-        keys = ("warp_ctas_per_sm", "encode_ctas_per_sm", "encode_bwd_ctas_per_sm", "agg_res")
-        arr = (C.c_int * 4)(*[int(tune[k]) for k in keys])
+        arr = (C.c_int * len(self.TUNE_KEYS))(*[int(tune[k]) for k in self.TUNE_KEYS])
         _check(lib().invr_ctx_set_tune(self.h, arr), self.h)
 
     def enable_timing(self, on: bool = True):

@@ -456,12 +456,31 @@ cudaError_t deform_runs(const Plan& P, bool backward, Launch launch) {
   return cudaSuccess;
 }
 
+cudaError_t run_deform_and_encode(invr_ctx ctx, const Plan& P, cudaStream_t s);
+
 cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
   cudaError_t e;
   if ((e = TIMED(ctx, "march_count", s, launch_march_count(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "scan", s, launch_scan(P, s))) != cudaSuccess) return e;
   if ((e = TIMED(ctx, "march_emit", s, launch_march_emit(P, s))) != cudaSuccess) return e;
-  if ((e = TIMED(ctx, "warp", s, launch_warp(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  if (P.tune.fused && !P.has_deform) {
+    if ((e = TIMED(ctx, "warp_encode", s, launch_warp_encode_by_field(P, ctx->num_sms, s))) != cudaSuccess) return e;
+  } else {
+    if ((e = TIMED(ctx, "warp", s, launch_warp(P, ctx->num_sms, s))) != cudaSuccess) return e;
+    if ((e = run_deform_and_encode(ctx, P, s)) != cudaSuccess) return e;
+  }
+  if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
+    return e;
+  if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
+    e = P.feat_split ? TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_split_tc(P, ctx->num_sms, s))
+                     : TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_tc(P, ctx->num_sms, s));
+  return e;
+}
+
+// The staged forward after the warp: the deformation net (if any view has one), then the
+// field's encoding.
+cudaError_t run_deform_and_encode(invr_ctx ctx, const Plan& P, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   if (P.has_deform) {
     // v_t = the warp; the net's features of v_t; v_c = v_t + delta v (written over s_vc)
     if ((e = cudaMemcpyAsync(P.ws.s_vt, P.ws.s_vc, 3 * P.ws.S_cap * sizeof(float), cudaMemcpyDeviceToDevice, s)) !=
@@ -473,13 +492,7 @@ cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
       return e;
     if ((e = TIMED(ctx, "deform_fwd", s, launch_deform_forward(P, ctx->num_sms, s))) != cudaSuccess) return e;
   }
-  if ((e = TIMED(ctx, "encode", s, launch_encode_by_field(P, ctx->num_sms, s))) != cudaSuccess) return e;
-  if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
-    return e;
-  if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
-    e = P.feat_split ? TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_split_tc(P, ctx->num_sms, s))
-                     : TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_tc(P, ctx->num_sms, s));
-  return e;
+  return TIMED(ctx, "encode", s, launch_encode_by_field(P, ctx->num_sms, s));
 }
 
 invr_status check_desc(invr_ctx ctx, const invr_field_desc* d) {
@@ -728,16 +741,35 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
   Tune best = ctx->tune;
   float best_ms = 0.0f;
   invr_status st = measure(best_ms);
-  // coordinate descent over the launch shapes
-  const int warp_c[] = {4, 8, 16}, enc_c[] = {4, 8, 16, 32}, bwd_c[] = {1, 2, 4, 8},
+  // coordinate descent over the launch shapes: the forward's structure first
+  // (staged; fused with 256- or 128-sample work items: fused + 2 * (chunk == 128)),
+  // then the grid sizes and the aggregation threshold
+  const int form_c[] = {0, 1, 3}, warp_c[] = {4, 8, 16}, enc_c[] = {4, 8, 16, 32}, bwd_c[] = {1, 2, 4, 8},
             agg_c[] = {0, 64, 128, 256, 512, 1024};
-  for (int dim = 0; dim < 4 && st == INVR_OK; ++dim) {
-    const int* cands = dim == 0 ? warp_c : dim == 1 ? enc_c : dim == 2 ? bwd_c : agg_c;
-    const int n = dim == 0 ? 3 : (dim == 3 ? 6 : 4);
+  const int* dims[] = {form_c, warp_c, enc_c, bwd_c, agg_c};
+  const int dim_n[] = {3, 3, 4, 4, 6};
+  for (int dim = 0; dim < 5 && st == INVR_OK; ++dim) {
+    const int* cands = dims[dim];
+    const int n = dim_n[dim];
+    if (dim == 1 && best.fused) continue;  // the staged warp's grid only matters to the staged path
     for (int i = 0; i < n && st == INVR_OK; ++i) {
       Tune t = best;
-      int* slot = dim == 0 ? &t.warp_ctas_per_sm
-                           : dim == 1 ? &t.encode_ctas_per_sm : dim == 2 ? &t.encode_bwd_ctas_per_sm : &t.agg_res;
+      if (dim == 0) {
+        const int form = cands[i];
+        if (t.fused == (form & 1) && (!t.fused || t.chunk == ((form & 2) ? 128 : 256))) continue;
+        t.fused = form & 1;
+        t.chunk = (form & 2) ? 128 : 256;
+        ctx->tune = t;
+        float ms = 0.0f;
+        st = measure(ms);
+        if (st == INVR_OK && ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+        continue;
+      }
+      int* slot = dim == 1 ? &t.warp_ctas_per_sm
+                : dim == 2 ? &t.encode_ctas_per_sm : dim == 3 ? &t.encode_bwd_ctas_per_sm : &t.agg_res;
       if (*slot == cands[i]) continue;
       *slot = cands[i];
       ctx->tune = t;
@@ -762,16 +794,20 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
   return INVR_OK;
 }
 
-invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in4) {
+invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in) {
   if (!ctx) return INVR_E_ARG;
-  if (!in4) return fail(ctx, INVR_E_ARG, "null tune array");
+  if (!in) return fail(ctx, INVR_E_ARG, "null tune array");
   for (int i = 0; i < 3; ++i)
-    if (in4[i] < 1 || in4[i] > 32) return fail(ctx, INVR_E_ARG, "CTAs per SM must be in [1, 32]");
-  if (in4[3] < 0 || in4[3] > (1 << 20)) return fail(ctx, INVR_E_ARG, "aggregation resolution must be in [0, 2^20]");
-  ctx->tune.warp_ctas_per_sm = in4[0];
-  ctx->tune.encode_ctas_per_sm = in4[1];
-  ctx->tune.encode_bwd_ctas_per_sm = in4[2];
-  ctx->tune.agg_res = in4[3];
+    if (in[i] < 1 || in[i] > 32) return fail(ctx, INVR_E_ARG, "CTAs per SM must be in [1, 32]");
+  if (in[3] < 0 || in[3] > (1 << 20)) return fail(ctx, INVR_E_ARG, "aggregation resolution must be in [0, 2^20]");
+  if (in[4] != 0 && in[4] != 1) return fail(ctx, INVR_E_ARG, "fused must be 0 or 1");
+  if (in[5] != 128 && in[5] != 256) return fail(ctx, INVR_E_ARG, "the fused work item must be 128 or 256 samples");
+  ctx->tune.warp_ctas_per_sm = in[0];
+  ctx->tune.encode_ctas_per_sm = in[1];
+  ctx->tune.encode_bwd_ctas_per_sm = in[2];
+  ctx->tune.agg_res = in[3];
+  ctx->tune.fused = in[4];
+  ctx->tune.chunk = in[5];
   ctx->fwd_valid = false;
   return INVR_OK;
 }
@@ -782,12 +818,14 @@ invr_status invr_ctx_set_wait_limit(invr_ctx ctx, uint32_t polls) {
   return INVR_OK;
 }
 
-invr_status invr_ctx_get_tune(invr_ctx ctx, int* out4) {
-  if (!ctx || !out4) return INVR_E_ARG;
-  out4[0] = ctx->tune.warp_ctas_per_sm;
-  out4[1] = ctx->tune.encode_ctas_per_sm;
-  out4[2] = ctx->tune.encode_bwd_ctas_per_sm;
-  out4[3] = ctx->tune.agg_res;
+invr_status invr_ctx_get_tune(invr_ctx ctx, int* out) {
+  if (!ctx || !out) return INVR_E_ARG;
+  out[0] = ctx->tune.warp_ctas_per_sm;
+  out[1] = ctx->tune.encode_ctas_per_sm;
+  out[2] = ctx->tune.encode_bwd_ctas_per_sm;
+  out[3] = ctx->tune.agg_res;
+  out[4] = ctx->tune.fused;
+  out[5] = ctx->tune.chunk;
   return INVR_OK;
 }
 

@@ -141,6 +141,8 @@ struct Tune {
   int encode_ctas_per_sm = 32;
   int encode_bwd_ctas_per_sm = 8;
   int agg_res = 128;
+  int fused = 0;            // warp + encoding in one kernel per field (k_warp_encode), else staged
+  int chunk = 256;          // samples per work item of the fused kernel (128 or 256)
 };
 
 struct Plan {
@@ -327,6 +329,7 @@ cudaError_t launch_encode(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_by_field(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_bwd_by_field(const Plan& P, int num_sms, cudaStream_t s);
+cudaError_t launch_warp_encode_by_field(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_fwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_f32(const Plan& P, int num_sms, cudaStream_t s);
 bool plan_has_kind(const Plan& P, int kind);

@@ -22,8 +22,48 @@
 // together with the L2's atomic rate (8 x 8 B of corner updates per sample-level).
 #include "hash_grid.cuh"
 #include "tc_ptx.cuh"
+#include "warp.cuh"
 
 namespace invr {
+
+// The features of sample slot s at canonical position x (zero where !live), written as the
+// field's layout: FP32 feature-major, or the 16-bit operand tiles (and, for training, the
+// remainder tiles).
+__device__ __forceinline__ void encode_sample(const Plan& P, const FieldDev& F, int64_t s, float3 x, bool live) {
+  const int64_t S_cap = P.ws.S_cap;
+  float* feat = static_cast<float*>(P.ws.feat);
+  // F.L is a multiple of 4 (mlp_in = 2 L is 16 or 32; the deformation net's 2 L a multiple of 8)
+  for (int l0 = 0; l0 < F.L; l0 += 4) {
+    uint32_t packed[4], rest[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + j;
+      float2 f = make_float2(0.0f, 0.0f);
+      if (live) {
+        Corners c;
+        level_corners(F, l, x, c);
+        f = level_feature(F, l, c);
+      }
+      if (F.mlp_kind == kMlpF32) {
+        feat[(int64_t)(2 * l) * S_cap + s] = f.x;
+        feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
+      } else {
+        // tensor-core field: the pair as 16-bit operand row s of its tile (rounded to nearest)
+        // and, for training, the remainder of that rounding
+        if (F.mlp_kind == kMlpBF16)
+          tc::split2<true>(f.x, f.y, packed[j], rest[j]);
+        else
+          tc::split2<false>(f.x, f.y, packed[j], rest[j]);
+      }
+    }
+    if (F.mlp_kind != kMlpF32) {
+      uint8_t* dst = reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l0);
+      *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      if (P.feat_split)
+        *reinterpret_cast<uint4*>(dst + feat16_lo_offset(S_cap)) = make_uint4(rest[0], rest[1], rest[2], rest[3]);
+    }
+  }
+}
 
 // Work items: chunks of 256 consecutive samples.  A thread evaluates every level of its
 // sample, level by level in step with the other warps of its block, so the block's warps
@@ -38,48 +78,56 @@ __global__ void __launch_bounds__(256) k_encode(const __grid_constant__ Plan P) 
   if (threadIdx.x <= P.n_views) vb[threadIdx.x] = P.ws.view_base[threadIdx.x];
   __syncthreads();
   const int64_t S0 = vb[P.view_lo], S = vb[P.view_hi];
-  float* feat = static_cast<float*>(P.ws.feat);
   const int64_t n_chunks = (S - S0 + 255) / 256;
   int v = P.view_lo;  // cursor: this thread's samples only increase over its chunks
   for (int64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
     const int64_t s = S0 + chunk * 256 + threadIdx.x;
     if (s >= S) continue;
     v = advance_view(vb, P.view_hi, s, v);
-    const FieldDev& F = P.v[v].field;
     const bool live = P.ws.s_ray[s] >= 0;
     const float3 x = live ? make_float3(P.ws.s_vc[s], P.ws.s_vc[S_cap + s], P.ws.s_vc[2 * S_cap + s])
                           : make_float3(0.0f, 0.0f, 0.0f);
-    // F.L is a multiple of 4 (mlp_in = 2 L is 16 or 32; the deformation net's 2 L a multiple of 8)
-    for (int l0 = 0; l0 < F.L; l0 += 4) {
-      uint32_t packed[4], rest[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int l = l0 + j;
-        float2 f = make_float2(0.0f, 0.0f);
-        if (live) {
-          Corners c;
-          level_corners(F, l, x, c);
-          f = level_feature(F, l, c);
-        }
-        if (F.mlp_kind == kMlpF32) {
-          feat[(int64_t)(2 * l) * S_cap + s] = f.x;
-          feat[(int64_t)(2 * l + 1) * S_cap + s] = f.y;
-        } else {
-          // tensor-core field: the pair as 16-bit operand row s of its tile (rounded to nearest)
-          // and, for training, the remainder of that rounding
-          if (F.mlp_kind == kMlpBF16)
-            tc::split2<true>(f.x, f.y, packed[j], rest[j]);
-          else
-            tc::split2<false>(f.x, f.y, packed[j], rest[j]);
-        }
+    encode_sample(P, P.v[v].field, s, x, live);
+  }
+}
+
+// The forward chain's first two steps fused per work item of CHUNK consecutive samples: each
+// thread warps its sample (the K nearest nodes and the dual-quaternion blend, or the rigid
+// pose), writes v_c (the backward's scatter reads it), and -- after a block barrier, so that
+// the block's warps walk the levels together and share each level's table lines in L1 --
+// encodes it from registers.  One launch per field (the field's tables stay in L2); the
+// canonical positions never go through DRAM between the two steps, and the warp's latency
+// overlaps the other blocks' gathers.  CHUNK (128 or 256) is chosen by the autotuner.
+template <int KMAX, int CHUNK>
+__global__ void __launch_bounds__(CHUNK) k_warp_encode(const __grid_constant__ Plan P) {
+  __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
+  const int64_t S_cap = P.ws.S_cap;
+  if (P.ws.view_base[P.n_views] > S_cap) return;
+  if (threadIdx.x <= P.n_views) vb[threadIdx.x] = P.ws.view_base[threadIdx.x];
+  __syncthreads();
+  const int64_t S0 = vb[P.view_lo], S = vb[P.view_hi];
+  const int64_t n_chunks = (S - S0 + CHUNK - 1) / CHUNK;
+  int v = P.view_lo;  // cursor: this thread's samples only increase over its chunks
+  for (int64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+    const int64_t s = S0 + chunk * CHUNK + threadIdx.x;
+    bool live = false;
+    float3 x = make_float3(0.0f, 0.0f, 0.0f);
+    if (s < S) {
+      v = advance_view(vb, P.view_hi, s, v);
+      if (P.ws.s_ray[s] >= 0) {
+        live = true;
+        const WarpDev& W = P.v[v].warp;
+        const float3 p = make_float3(P.ws.s_pos[s], P.ws.s_pos[S_cap + s], P.ws.s_pos[2 * S_cap + s]);
+        int64_t cell = 0;
+        const uint32_t n = (W.mode == 0 || W.lut_live) ? 0u : knn_locate(W, p, cell);
+        x = warp_point_upto<KMAX>(W, p, cell, n);
       }
-      if (F.mlp_kind != kMlpF32) {
-        uint8_t* dst = reinterpret_cast<uint8_t*>(feat) + feat16_offset(S_cap, s, 2 * l0);
-        *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        if (P.feat_split)
-          *reinterpret_cast<uint4*>(dst + feat16_lo_offset(S_cap)) = make_uint4(rest[0], rest[1], rest[2], rest[3]);
-      }
+      P.ws.s_vc[s] = x.x;
+      P.ws.s_vc[S_cap + s] = x.y;
+      P.ws.s_vc[2 * S_cap + s] = x.z;
     }
+    __syncthreads();
+    if (s < S) encode_sample(P, P.v[v].field, s, x, live);
   }
 }
 
@@ -178,6 +226,25 @@ cudaError_t launch_encode_by_field(const Plan& P, int num_sms, cudaStream_t s) {
 
 cudaError_t launch_encode_bwd_by_field(const Plan& P, int num_sms, cudaStream_t s) {
   return per_field(P, [&](const Plan& Q) { return launch_encode_bwd(Q, num_sms, s); });
+}
+
+template <int KMAX>
+cudaError_t launch_warp_encode_k(const Plan& Q, int num_sms, cudaStream_t s) {
+  const int grid = num_sms * Q.tune.encode_ctas_per_sm;
+  if (Q.tune.chunk == 128)
+    k_warp_encode<KMAX, 128><<<grid, 128, 0, s>>>(Q);
+  else
+    k_warp_encode<KMAX, 256><<<grid, 256, 0, s>>>(Q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_warp_encode_by_field(const Plan& P, int num_sms, cudaStream_t s) {
+  int kmax = 0;
+  for (int v = 0; v < P.n_views; ++v)
+    if (P.v[v].warp.mode == 1 && P.v[v].warp.K > kmax) kmax = P.v[v].warp.K;
+  return per_field(P, [&](const Plan& Q) {
+    return kmax <= 4 ? launch_warp_encode_k<4>(Q, num_sms, s) : launch_warp_encode_k<8>(Q, num_sms, s);
+  });
 }
 
 // ------------------------------------------------------------------ single step

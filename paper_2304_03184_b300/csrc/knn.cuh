@@ -25,18 +25,25 @@ __device__ __forceinline__ void knn_insert(float key, int id, float (&keys)[K], 
   }
 }
 
+// The candidate-grid cell of p and its list length, or n = kKnnOverflow where every node
+// must be scanned (no grid, p outside the box, or the cell's list overflowed).
+__device__ __forceinline__ uint32_t knn_locate(const WarpDev& W, float3 p, int64_t& cell) {
+  cell = 0;
+  if (W.cand_n && fabsf(p.x) <= 1.001f && fabsf(p.y) <= 1.001f && fabsf(p.z) <= 1.001f) {
+    cell = grid_cell(p.x, kKnnG) + kKnnG * (grid_cell(p.y, kKnnG) + kKnnG * grid_cell(p.z, kKnnG));
+    return __ldg(W.cand_n + cell);
+  }
+  return kKnnOverflow;
+}
+
+// The K nearest nodes of p from the located cell's list (or all nodes).
 template <int K>
-__device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&keys)[K], int (&ids)[K]) {
+__device__ __forceinline__ void knn_scan(const WarpDev& W, float3 p, int64_t cell, uint32_t n, float (&keys)[K],
+                                         int (&ids)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     keys[k] = INFINITY;
     ids[k] = -1;
-  }
-  uint32_t n = kKnnOverflow;
-  int64_t cell = 0;
-  if (W.cand_n && fabsf(p.x) <= 1.001f && fabsf(p.y) <= 1.001f && fabsf(p.z) <= 1.001f) {
-    cell = grid_cell(p.x, kKnnG) + kKnnG * (grid_cell(p.y, kKnnG) + kKnnG * grid_cell(p.z, kKnnG));
-    n = __ldg(W.cand_n + cell);
   }
   if (n == kKnnOverflow) {
     for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
@@ -59,6 +66,13 @@ __device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&k
       knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
     }
   }
+}
+
+template <int K>
+__device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&keys)[K], int (&ids)[K]) {
+  int64_t cell;
+  const uint32_t n = knn_locate(W, p, cell);
+  knn_scan<K>(W, p, cell, n, keys, ids);
 }
 
 }  // namespace invr

@@ -65,6 +65,41 @@ def test_graph_replay_matches_eager_steps(env):
     assert eager[3] < eager[0]                              # training makes progress
 
 
+def test_graph_replay_matches_oracle(env):
+    """The captured batched step (key frames x both fields, BF16 MLPs, one graph launch)
+    against the FP64 oracle: the loss a replay reports, and the gradient it applied, recovered
+    from the Adam first moments before and after the replay (m1 = b1 m0 + (1 - b1) g), both
+    on the parameters the replay started from.  Mixed-precision tolerance: 1e-2 relative per
+    field's tables and weights; the loss within 1e-5."""
+    invr, oracle = env
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    total = sum(b.rays.n for b in tw.batches)
+    ctx = invr.Context(0)
+    tb, fields, keep = make_batches(invr, ctx, tw, invr.INVR_MLP_BF16)
+    ctx.reserve(total, tw.n_samples)
+    graph = invr.TrainGraph(ctx, tb, warmup=2)
+    before = {k: [x.cpu().numpy() if hasattr(x, "cpu") else x for x in f.get_params()] for k, f in fields.items()}
+    loss = float(graph.replay().item())
+    ctx.sync()
+    after = {k: [x.cpu().numpy() if hasattr(x, "cpu") else x for x in f.get_params()] for k, f in fields.items()}
+    ofields = {k: oracle.Field(fp.desc, before[id(fp)][0], before[id(fp)][1]) for fp in tw.fields
+               for k in [id(fp)]}
+    obatches = [oracle.TrainBatch(b.rays.o, b.rays.d, oracle.View.from_synth(b.view, field=ofields[id(b.view.field)]),
+                                  b.target) for b in tw.batches]
+    oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(loss - oloss) <= 1e-5 * oloss
+    for fp in tw.fields:
+        t0, w0, m0, v0, step0 = before[id(fp)]
+        _, _, m1, _, step1 = after[id(fp)]
+        assert step1 == step0 + 1
+        g = (m1.astype(np.float64) - tw.beta1 * m0.astype(np.float64)) / (1.0 - tw.beta1)
+        ogt, ogw = ograds[id(ofields[id(fp)])]
+        nt = ogt.size
+        for got, want, what in ((g[:nt], ogt, "tables"), (g[nt:], ogw, "weights")):
+            rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert rel <= 1e-2, (what, rel)
+
+
 def test_autotune_keeps_parameters(env):
     invr, _ = env
     import torch
@@ -75,6 +110,7 @@ def test_autotune_keeps_parameters(env):
     tune = ctx.autotune(tb)
     assert tune["warp_ctas_per_sm"] in (4, 8, 16) and tune["encode_ctas_per_sm"] in (4, 8, 16, 32)
     assert tune["encode_bwd_ctas_per_sm"] in (1, 2, 4, 8) and tune["agg_res"] in (0, 64, 128, 256, 512, 1024)
+    assert tune["fused"] in (0, 1) and tune["chunk"] in (128, 256)
     for f, (t0, w0) in zip(fields.values(), before):
         t1, w1, _, _, step = f.get_params()
         assert step == 0 and torch.equal(t0, t1) and torch.equal(w0, w1)
@@ -109,11 +145,36 @@ def test_gradient_scatter_independent_of_aggregation(env):
             np.testing.assert_allclose(gw1, gw0, rtol=1e-4, atol=1e-5 * np.abs(gw0).max())
 
 
+def test_fused_forward_matches_staged(env):
+    """The fused warp + encoding kernel and the staged pair (warp, then encoding) run the same
+    per-sample arithmetic: renders are bit-identical and so are the training losses, for
+    both work-item sizes of the fused kernel and both MLP paths."""
+    invr, _ = env
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    for prec in (invr.INVR_FP32, invr.INVR_MLP_BF16):
+        ctx = invr.Context(0)
+        tb, fields, keep = make_batches(invr, ctx, tw, prec)
+        base = ctx.tune()
+        o, d, view, _ = tb.batches[0]
+        out = []
+        for fused, chunk in ((0, 256), (1, 256), (1, 128)):
+            ctx.set_tune(dict(base, fused=fused, chunk=chunk))
+            rgba, depth = invr.render_rays(ctx, o, d, tw.n_samples, tw.t_eps, [view])
+            loss = invr.forward_train(ctx, tb)
+            ctx.sync()
+            out.append((rgba.cpu().numpy(), depth.cpu().numpy(), float(loss.item())))
+        for rgba, depth, loss in out[1:]:
+            np.testing.assert_array_equal(rgba, out[0][0])
+            np.testing.assert_array_equal(depth, out[0][1])
+            assert loss == out[0][2]
+
+
 def test_set_tune_validates(env):
     invr, _ = env
     ctx = invr.Context(0)
     t = ctx.tune()
-    for bad in (dict(t, warp_ctas_per_sm=0), dict(t, encode_ctas_per_sm=33), dict(t, agg_res=-1)):
+    for bad in (dict(t, warp_ctas_per_sm=0), dict(t, encode_ctas_per_sm=33), dict(t, agg_res=-1), dict(t, fused=2),
+                dict(t, chunk=64)):
         with pytest.raises(invr.InvrError):
             ctx.set_tune(bad)
     assert ctx.tune() == t
