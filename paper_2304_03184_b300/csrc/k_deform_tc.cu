@@ -73,6 +73,24 @@ __device__ __forceinline__ void issue(uint32_t d_tmem, uint32_t a_saddr, uint32_
   }
 }
 
+// Slot tensor memory: accumulator [0, 128) (the output layer's in [0, 16)), the current
+// layer's A operand as 16-bit values [128, 192) and rounding remainders [192, 256).
+constexpr uint32_t T_HI = 128, T_LO = 192;
+
+// One thread: D = A W^T with A in tensor memory as values and remainders (8 columns per K
+// step of 16): hi * W + lo * W, the activations to about twice the 16-bit precision (the
+// weights keep their single rounding).
+template <bool BF16>
+__device__ __forceinline__ void issue_split(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_saddr, int K,
+                                            int N) {
+  const uint32_t idesc = tc::idesc_f16(kTM, N, BF16);
+  for (int kk = 0; kk < K / 16; ++kk) {
+    const uint64_t bd = tc::smem_desc(b_saddr + kk * 256, 128, K * 16);
+    tc::mma_f16_ts(d_tmem, a_hi + kk * 8, bd, idesc, kk > 0 ? 1u : 0u);
+    tc::mma_f16_ts(d_tmem, a_lo + kk * 8, bd, idesc, 1u);
+  }
+}
+
 __device__ __forceinline__ void operands_ready() {
   tc::fence_smem_to_async();
   tc::fence_before_sync();
@@ -146,8 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       stage<BF16>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
       loaded = D.weights;
     }
-    // operands of both tiles: features (FP32 feature-major) -> BF16 rows, pose bias; every
-    // feature load of both tiles is issued before the first store
+    // operands of both tiles: features (FP32 feature-major) -> 16-bit values and rounding
+    // remainders in the slot's tensor memory (layer 1's A operand), pose bias; every feature
+    // load of both tiles is issued before the first store
     float xr[2][kKf];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -159,19 +178,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
     for (int j = 0; j < 2; ++j) {
       if (slot[j].s0 < 0) continue;
       const int64_t s0 = slot[j].s0;
-      uint8_t* X = sm + OFF_X + j * kTM * kKf * 2;
+      const uint32_t row = tmem + 256 * j + lane_off;
+      uint32_t hi[16], lo[16];
 #pragma unroll
-      for (int k = 0; k < kKf; k += 8) {
-        if (k >= Kf) break;
-        const float* x = xr[j] + k;
-        uint4 q;
-        q.x = tc::pack2<BF16>(x[0], x[1]);
-        q.y = tc::pack2<BF16>(x[2], x[3]);
-        q.z = tc::pack2<BF16>(x[4], x[5]);
-        q.w = tc::pack2<BF16>(x[6], x[7]);
-        *reinterpret_cast<uint4*>(X + tc::kmajor_offset(t, k, Kf)) = q;
-        if (P.deform_store)
-          *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(t, k, Kf)) = q;
+      for (int c = 0; c < 16; ++c) tc::split2<BF16>(xr[j][2 * c], xr[j][2 * c + 1], hi[c], lo[c]);
+      if (Kf == 32) {
+        tc::tmem_st16(row + T_HI, hi);
+        tc::tmem_st16(row + T_LO, lo);
+      } else {
+        uint32_t h8[8], l8[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          h8[c] = hi[c];
+          l8[c] = lo[c];
+        }
+        tc::tmem_st8(row + T_HI, h8);
+        tc::tmem_st8(row + T_LO, l8);
+      }
+      if (P.deform_store) {
+        for (int k = 0; k < Kf; k += 8)
+          *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(t, k, Kf)) =
+              make_uint4(hi[k / 2], hi[k / 2 + 1], hi[k / 2 + 2], hi[k / 2 + 3]);
       }
       float* bias = reinterpret_cast<float*>(sm + OFF_BIAS) + j * kH;
       for (int o = t; o < H; o += kThreads) bias[o] = P.v[slot[j].view].deform.pose_bias[o];
@@ -181,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       tc::fence_after_sync();
       for (int j = 0; j < 2; ++j) {
         if (slot[j].s0 < 0) continue;
-        issue<BF16>(tmem + 256 * j, sbase + OFF_X + j * kTM * kKf * 2, sbase + OFF_W1, Kf, H);
+        issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + OFF_W1, Kf, H);
         tc::commit_to(mbar0 + 8 * j);
       }
     }
@@ -199,7 +226,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
         pending[j] = false;
         tc::fence_after_sync();
         const uint32_t row = tmem + 256 * j + lane_off;
-        uint8_t* Hb = sm + OFF_HB + j * kTM * kH * 2;
         if (l < n) {
           const float* bias = reinterpret_cast<const float*>(sm + OFF_BIAS) + j * kH;
           uint8_t* g = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + slot[j].s0 / kTM) * kHTile;
@@ -210,31 +236,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
 #pragma unroll
               for (int i = 0; i < 32; ++i) v[i] += bias[c + i];
             }
+            uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int c8 = 0; c8 < 4; ++c8) {
-              const float* x = v + 8 * c8;
-              uint4 q;
-              q.x = tc::pack2<BF16>(fmaxf(x[0], 0.f), fmaxf(x[1], 0.f));
-              q.y = tc::pack2<BF16>(fmaxf(x[2], 0.f), fmaxf(x[3], 0.f));
-              q.z = tc::pack2<BF16>(fmaxf(x[4], 0.f), fmaxf(x[5], 0.f));
-              q.w = tc::pack2<BF16>(fmaxf(x[6], 0.f), fmaxf(x[7], 0.f));
-              *reinterpret_cast<uint4*>(Hb + tc::kmajor_offset(t, c + 8 * c8, H)) = q;
-              if (P.deform_store) *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c + 8 * c8, H)) = q;
+            for (int q = 0; q < 16; ++q) tc::split2<BF16>(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f), hi[q], lo[q]);
+            // h_l as the next layer's A operand (values and remainders) and, rounded, for the
+            // backward (its weight-gradient operand; its sign is the ReLU decision taken here)
+            tc::tmem_st16(row + T_HI + c / 2, hi);
+            tc::tmem_st16(row + T_LO + c / 2, lo);
+            if (P.deform_store) {
+#pragma unroll
+              for (int c8 = 0; c8 < 4; ++c8)
+                *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c + 8 * c8, H)) =
+                    make_uint4(hi[4 * c8], hi[4 * c8 + 1], hi[4 * c8 + 2], hi[4 * c8 + 3]);
             }
           }
-          operands_ready();
+          tc::fence_before_sync();
+          __syncthreads();
           if (t == 0) {
             tc::fence_after_sync();
             if (l + 1 < n)
-              issue<BF16>(tmem + 256 * j, sbase + OFF_HB + j * kTM * kH * 2, sbase + OFF_WH + l * kH * kH * 2, H, H);
+              issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO,
+                                sbase + OFF_WH + l * kH * kH * 2, H, H);
             else
-              issue<BF16>(tmem + 256 * j + 128, sbase + OFF_HB + j * kTM * kH * 2, sbase + OFF_WO, H, 16);
+              issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + OFF_WO, H, 16);
             tc::commit_to(mbar0 + 8 * j);
           }
           pending[j] = true;
         } else {
           float v[16];
-          tc::tmem_ld16(row + 128, v);
+          tc::tmem_ld16(row, v);
           const int64_t g = slot[j].s0 + t;
           if (P.ws.s_ray[g] >= 0) {
             P.ws.s_vc[g] = P.ws.s_vt[g] + v[0];
