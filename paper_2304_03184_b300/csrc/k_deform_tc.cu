@@ -38,6 +38,15 @@ constexpr uint32_t OFF_HB = OFF_X + 2 * kTM * kKf * 2;           // 2 x [128][H]
 constexpr uint32_t OFF_BIAS = OFF_HB + 2 * kTM * kH * 2;         // 2 x [H] floats
 constexpr uint32_t OFF_MISC = OFF_BIAS + 2 * kH * 4;             // 2 mbarriers + TMEM base
 constexpr uint32_t kSmem = OFF_MISC + 64 + 1024;
+// the forward's plan: every weight as 16-bit values directly followed by their rounding
+// remainders (the activations live in tensor memory)
+constexpr uint32_t F_W1 = 0;                                     // 2 x [H][Kf]
+constexpr uint32_t F_WH = F_W1 + 2 * kH * kKf * 2;               // 3 x 2 x [H][H]
+constexpr uint32_t F_WO = F_WH + 3 * 2 * kH * kH * 2;            // 2 x [16][H]
+constexpr uint32_t F_BIAS = F_WO + 2 * 16 * kH * 2;              // 2 x [H] floats
+constexpr uint32_t F_MISC = F_BIAS + 2 * kH * 4;                 // 2 mbarriers + TMEM base
+constexpr uint32_t kSmemF = F_MISC + 64 + 1024;
+static_assert(kSmemF <= 227 * 1024, "the forward's weights fit one CTA");
 
 __device__ __forceinline__ int view_of_slot(const Plan& P, int64_t s) {
   int v = 0;
@@ -63,6 +72,22 @@ __device__ void stage(uint8_t* dst, const float* __restrict__ W, int N, int K, i
   }
 }
 
+// The same as 16-bit values at dst and their rounding remainders at dst + N K 2 bytes.
+template <bool BF16>
+__device__ void stage_split(uint8_t* dst, const float* __restrict__ W, int N, int K, int ldw, int n_valid,
+                            int k_valid) {
+  uint8_t* lo = dst + N * K * 2;
+  for (int e = threadIdx.x; e < N * K / 2; e += kThreads) {
+    const int n = (2 * e) / K, k = (2 * e) % K;
+    const float a = (n < n_valid && k < k_valid) ? __ldg(W + (int64_t)n * ldw + k) : 0.0f;
+    const float b = (n < n_valid && k + 1 < k_valid) ? __ldg(W + (int64_t)n * ldw + k + 1) : 0.0f;
+    uint32_t h, l;
+    tc::split2<BF16>(a, b, h, l);
+    *reinterpret_cast<uint32_t*>(dst + tc::kmajor_offset(n, k, K)) = h;
+    *reinterpret_cast<uint32_t*>(lo + tc::kmajor_offset(n, k, K)) = l;
+  }
+}
+
 template <bool BF16>
 __device__ __forceinline__ void issue(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, int N) {
   const uint32_t idesc = tc::idesc_f16(kTM, N, BF16);
@@ -78,16 +103,18 @@ __device__ __forceinline__ void issue(uint32_t d_tmem, uint32_t a_saddr, uint32_
 constexpr uint32_t T_HI = 128, T_LO = 192;
 
 // One thread: D = A W^T with A in tensor memory as values and remainders (8 columns per K
-// step of 16): hi * W + lo * W, the activations to about twice the 16-bit precision (the
-// weights keep their single rounding).
+// step of 16) and W in shared memory as values and remainders (N K 2 bytes apart):
+// hi*hi + lo*hi + hi*lo, both operands to about twice the 16-bit precision.
 template <bool BF16>
 __device__ __forceinline__ void issue_split(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_saddr, int K,
                                             int N) {
   const uint32_t idesc = tc::idesc_f16(kTM, N, BF16);
   for (int kk = 0; kk < K / 16; ++kk) {
     const uint64_t bd = tc::smem_desc(b_saddr + kk * 256, 128, K * 16);
+    const uint64_t bl = tc::smem_desc(b_saddr + N * K * 2 + kk * 256, 128, K * 16);
     tc::mma_f16_ts(d_tmem, a_hi + kk * 8, bd, idesc, kk > 0 ? 1u : 0u);
     tc::mma_f16_ts(d_tmem, a_lo + kk * 8, bd, idesc, 1u);
+    tc::mma_f16_ts(d_tmem, a_hi + kk * 8, bl, idesc, 1u);
   }
 }
 
@@ -109,8 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
   const int64_t S = P.ws.view_base[P.n_views];
   if (S > S_cap) return;
   const int t = threadIdx.x, warp = t >> 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
-  const uint32_t mbar0 = tc::smem_u32(sm + OFF_MISC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + F_MISC + 16);
+  const uint32_t mbar0 = tc::smem_u32(sm + F_MISC);
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
   if (t == 0) {
@@ -159,9 +186,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
     if (D.weights != loaded) {
       __syncthreads();
       const int n_in = D.n_feat + D.pose_dim;
-      stage<BF16>(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
-      for (int l = 1; l < n; ++l) stage<BF16>(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
-      stage<BF16>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      stage_split<BF16>(sm + F_W1, D.weights, H, Kf, n_in, H, D.n_feat);
+      for (int l = 1; l < n; ++l)
+        stage_split<BF16>(sm + F_WH + (l - 1) * 2 * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
+      stage_split<BF16>(sm + F_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      tc::fence_smem_to_async();
       loaded = D.weights;
     }
     // operands of both tiles: features (FP32 feature-major) -> 16-bit values and rounding
@@ -200,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
           *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(t, k, Kf)) =
               make_uint4(hi[k / 2], hi[k / 2 + 1], hi[k / 2 + 2], hi[k / 2 + 3]);
       }
-      float* bias = reinterpret_cast<float*>(sm + OFF_BIAS) + j * kH;
+      float* bias = reinterpret_cast<float*>(sm + F_BIAS) + j * kH;
       for (int o = t; o < H; o += kThreads) bias[o] = P.v[slot[j].view].deform.pose_bias[o];
     }
     operands_ready();
@@ -208,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       tc::fence_after_sync();
       for (int j = 0; j < 2; ++j) {
         if (slot[j].s0 < 0) continue;
-        issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + OFF_W1, Kf, H);
+        issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + F_W1, Kf, H);
         tc::commit_to(mbar0 + 8 * j);
       }
     }
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
         tc::fence_after_sync();
         const uint32_t row = tmem + 256 * j + lane_off;
         if (l < n) {
-          const float* bias = reinterpret_cast<const float*>(sm + OFF_BIAS) + j * kH;
+          const float* bias = reinterpret_cast<const float*>(sm + F_BIAS) + j * kH;
           uint8_t* g = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + slot[j].s0 / kTM) * kHTile;
           for (int c = 0; c < H; c += 32) {
             float v[32];
@@ -256,9 +285,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
             tc::fence_after_sync();
             if (l + 1 < n)
               issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO,
-                                sbase + OFF_WH + l * kH * kH * 2, H, H);
+                                sbase + F_WH + l * 2 * kH * kH * 2, H, H);
             else
-              issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + OFF_WO, H, 16);
+              issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + F_WO, H, 16);
             tc::commit_to(mbar0 + 8 * j);
           }
           pending[j] = true;
@@ -757,9 +786,9 @@ static cudaError_t backward_tc(const Plan& P, int num_sms, cudaStream_t s) {
 
 template <bool BF16>
 static cudaError_t forward_tc(const Plan& P, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_deform_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_deform_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
   if (e != cudaSuccess) return e;
-  k_deform_fwd_tc<BF16><<<num_sms, kThreads, kSmem, s>>>(P);
+  k_deform_fwd_tc<BF16><<<num_sms, kThreads, kSmemF, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -77,8 +77,9 @@ def test_deform_render_matches_oracle(env):
 
 @pytest.mark.parametrize("field_prec,net_prec", [("fp32", "fp16"), ("bf16", "fp16"), ("bf16", "bf16")])
 def test_deform_tensor_core_forward_matches_oracle(env, field_prec, net_prec):
-    """The net's forward on the tensor cores (FP16 or BF16 operands, FP32 accumulation):
-    renders within the mixed-precision colour tolerance, with an FP32 or a BF16 field."""
+    """The net's forward on the tensor cores (FP16 or BF16 split operands, FP32 accumulation):
+    renders within 1e-5 with an FP32 field, within the mixed-precision colour tolerance with a
+    BF16 field."""
     invr, ctx, oracle = env
     rng = np.random.default_rng(107)
     w, dp, pose = _render_workload(rng)
@@ -88,15 +89,19 @@ def test_deform_tensor_core_forward_matches_oracle(env, field_prec, net_prec):
     rgba, _ = invr.render_rays(ctx, cu(w.rays.o), cu(w.rays.d), w.n_samples, w.t_eps, [hum.view])
     ctx.sync()
     ref = oracle.render(w.rays.o, w.rays.d, w.n_samples, w.t_eps, [hum.oview])
-    np.testing.assert_allclose(host(rgba), ref.rgba, rtol=0, atol=MIXED_COLOUR_TOL)
+    # with an FP32 field the split-product net is as exact as the FP32 one (measured 9e-7)
+    tol = COLOUR_TOL if field_prec == "fp32" else MIXED_COLOUR_TOL
+    np.testing.assert_allclose(host(rgba), ref.rgba, rtol=0, atol=tol)
 
 
-# The net on the tensor cores, trained: its 16-bit forward moves v_c by ~1e-4 (FP16) to
-# ~4e-4 (BF16), i.e. 10-40% of a finest-level cell (N_l ~ 2000), and dL/dv_c is the derivative
-# of the rough hash-grid field at that point, so the net's gradients follow the FP64 oracle's
-# to ~0.1 (FP16; measured 0.09-0.15 per layer) and ~0.4 (BF16; 0.28-0.54); the field's own
-# gradients keep the mixed-precision levels.  Deltas are scaled by 1 / loss_norm in 16 bits.
-NET_TC_RTOL = {"fp16": (0.25, 0.2, 0.06), "bf16": (0.7, 0.45, 0.15)}   # net weights, net tables, field tables
+# The net on the tensor cores, trained.  Its forward forms every product from 16-bit values
+# plus the 16-bit remainders of their rounding (activations in tensor memory, weights in shared
+# memory), so delta v -- and with it v_c, at which the rough hash-grid field is differentiated
+# -- is as exact as in FP32; the adjoint chain runs in 16 bit.  Measured: the net's gradients
+# within 0.005-0.010 of the oracle's per weight matrix and 0.007-0.010 over its tables, the
+# field's tables within 0.002-0.003, in both FP16 and BF16 (with single-rounded 16-bit
+# operands they were 0.09-0.15 and 0.28-0.54).
+NET_TC_RTOL = {"fp16": (3e-2, 3e-2, 1e-2), "bf16": (3e-2, 3e-2, 1e-2)}   # net weights, net tables, field tables
 
 
 @pytest.mark.parametrize("net_prec", ["fp16", "bf16"])
@@ -111,7 +116,7 @@ def test_deform_tensor_core_training(env, net_prec):
     invr.backward(ctx, tb)
     ctx.sync()
     oloss, ograds = oracle.train_loss_grad(obatches, tw.n_samples, tw.t_eps, tw.huber_delta)
-    assert abs(float(host(loss)[0]) - oloss) <= 1e-3 * oloss
+    assert abs(float(host(loss)[0]) - oloss) <= 1e-5 * oloss
     w_tol, t_tol, f_tol = NET_TC_RTOL[net_prec]
     gt, gw = (host(x) for x in net.get_grads())
     ogt, ogw = ograds[id(onet)]
