@@ -13,7 +13,8 @@
 //   dC/dc_j = T_j alpha_j,   dC/dsigma_j = dt (T_{j+1} c_j - (C - sum_{k<=j} T_k alpha_k c_k))
 // folded with sigma = exp(o_0) and c = sigmoid(z) into dL/do_0 and dL/dz per sample.
 //
-// One thread per ray; bound by the per-sample reads (16 B/sample), issued 4 samples at a time.
+// Rendering: one thread per ray, samples read 4 at a time.  Training: one warp per 32 rays
+// with segmented scans over their samples (k_composite_train).
 #include "invr_internal.cuh"
 
 namespace invr {
@@ -179,20 +180,110 @@ __device__ __forceinline__ float huber_grad(float x, float delta) {
   return fabsf(x) <= delta ? x : copysignf(delta, x);
 }
 
+// Training compositing, loss and adjoint: one warp per 32 consecutive rays.  The rays' occupied
+// samples are contiguous slots (in ray order; padding between views has ray id -1), so the warp
+// walks them 32 at a time, one sample per lane, and every per-ray sum is a segmented scan over
+// the lanes (segments = runs of equal ray id): the optical depth S_j = sum_{k<j} x_k with
+// x_k = sigma_k dt gives T_j = exp(-S_j) (the product of the exp(-x_k), in another rounding
+// order), and the prefixes of T_j alpha_j c_j and T_j alpha_j t_j give the adjoint.  A ray lane
+// keeps its ray's running sums between chunks.  Pass 1 accumulates C, A, D; the ray lanes then
+// take the loss; pass 2 recomputes the same scans and writes dL/do_0, dL/dz per sample.  Loads
+// and stores are coalesced and every lane of a chunk has a sample, where one thread per ray
+// left 7.8 of 32 lanes active (rays of a warp differ in length).
+__device__ __forceinline__ float seg_scan(float v, int lane, int start) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= start) v += y;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__ Plan P, float* loss_part) {
   __shared__ float red[8];
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ float seg[8][32][8];  // per warp, per ray of the group: this chunk's segment totals
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
   const int64_t S_cap = P.ws.S_cap;
+  const int64_t g0 = (int64_t)blockIdx.x * 256 + wid * 32;
+  const int64_t g = g0 + lane;  // this lane's ray
+  const bool ray_ok = P.ws.view_base[P.n_views] <= S_cap && g < P.total_rays;
   float loss = 0.0f;
-  if (g < P.total_rays && P.ws.view_base[P.n_views] <= S_cap) {
-    const ViewDev& V = P.v[view_of_ray(P, g)];
-    const int64_t r = g - V.ray_begin;
-    float dt = 0.0f;
-    float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    int used = 0;
-    if (ray_dt(V, r, P.n_samples, dt)) used = composite(P, g, dt, res);
-    P.ws.ray_used[g] = used;
-    float dC[3], dD = 0.0f;
+  // ---- ray lane set-up
+  int v = 0;
+  int64_t r = 0;
+  float dt = 0.0f;
+  int first = 0, cnt = 0;
+  if (ray_ok) {
+    v = view_of_ray(P, g);
+    r = g - P.v[v].ray_begin;
+    if (ray_dt(P.v[v], r, P.n_samples, dt)) {
+      first = P.ws.ray_first[g];
+      cnt = P.ws.ray_count[g];
+    }
+  }
+  seg[wid][lane][7] = 0.0f;  // no segment total pending
+  __syncwarp();
+  const int lo = __reduce_min_sync(FULL, cnt > 0 ? (unsigned)first : 0x7FFFFFFFu);
+  const int hi = (int)__reduce_max_sync(FULL, cnt > 0 ? (unsigned)(first + cnt) : 0u);
+  // one sample per lane of a chunk: its ray (local lane), the segment it belongs to
+  auto sample = [&](int base, int& lr, float& sg, float& c0, float& c1, float& c2, float& tt, int& start,
+                    unsigned& heads) {
+    const int s = base + lane;
+    const int key = s < hi ? P.ws.s_ray[s] : -1;
+    lr = key >= 0 ? (int)(key - g0) : -1;
+    sg = c0 = c1 = c2 = tt = 0.0f;
+    if (lr >= 0) {
+      sg = P.ws.out[s];
+      c0 = P.ws.out[S_cap + s];
+      c1 = P.ws.out[2 * S_cap + s];
+      c2 = P.ws.out[3 * S_cap + s];
+      tt = P.ws.s_t[s];
+    }
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    heads = __ballot_sync(FULL, lane == 0 || prev != key);
+    start = 31 - __clz(heads & (FULL >> (31 - lane)));
+  };
+  // ---- pass 1: C, A, D per ray
+  float xs = 0.0f, res[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, nused = 0.0f;
+  for (int base = lo; base < hi; base += 32) {
+    int lr, start;
+    unsigned heads;
+    float sg, c0, c1, c2, tt;
+    sample(base, lr, sg, c0, c1, c2, tt, start, heads);
+    const int src = lr >= 0 ? lr : 0;
+    const float dts = __shfl_sync(FULL, dt, src), carry = __shfl_sync(FULL, xs, src);
+    const float x = lr >= 0 ? sg * dts : 0.0f;
+    const float incl = seg_scan(x, lane, start);
+    const float up = __shfl_up_sync(FULL, incl, 1);
+    const float excl = lane > start ? up : 0.0f;
+    const float T = expf(-(carry + excl));
+    const bool used = lr >= 0 && T >= P.t_eps;
+    const float w = used ? T * -expm1f(-x) : 0.0f;
+    float q[6] = {w * c0, w * c1, w * c2, w, w * tt, used ? 1.0f : 0.0f};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = seg_scan(q[k], lane, start);
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && lr >= 0) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) seg[wid][lr][k] = q[k];
+      seg[wid][lr][6] = incl;
+      seg[wid][lr][7] = 1.0f;
+    }
+    __syncwarp();
+    if (seg[wid][lane][7] != 0.0f) {
+      for (int k = 0; k < 5; ++k) res[k] += seg[wid][lane][k];
+      nused += seg[wid][lane][5];
+      xs += seg[wid][lane][6];
+      seg[wid][lane][7] = 0.0f;
+    }
+    __syncwarp();
+  }
+  // ---- ray lane: loss and dL/dC, dL/dD
+  float dC[3] = {0.f, 0.f, 0.f}, dD = 0.0f;
+  if (ray_ok) {
+    const ViewDev& V = P.v[v];
+    P.ws.ray_used[g] = (int)nused;
     bool finite = true;
     float e[3];
     for (int c = 0; c < 3; ++c) {
@@ -220,70 +311,75 @@ __global__ void __launch_bounds__(256) k_composite_train(const __grid_constant__
       for (int c = 0; c < 4; ++c) V.rgba_out[c * V.n_rays + r] = res[c];
     }
     if (V.depth_out) V.depth_out[r] = res[4];
-    // adjoint walk
-    const int64_t first = P.ws.ray_first[g];
-    const int cnt = P.ws.ray_count[g];
-    float T = 1.0f, pre[3] = {0.f, 0.f, 0.f}, pre_d = 0.0f;
-    // chunks of 4 samples as in composite(): loads first, then the in-order arithmetic
-    for (int k0 = 0; k0 < cnt; k0 += 4) {
-      float sg[4], cl[4][3], tl[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t s = first + k0 + j;
-        const bool in = k0 + j < used;
-        sg[j] = in ? P.ws.out[s] : 0.0f;
-        cl[j][0] = in ? P.ws.out[S_cap + s] : 0.0f;
-        cl[j][1] = in ? P.ws.out[2 * S_cap + s] : 0.0f;
-        cl[j][2] = in ? P.ws.out[3 * S_cap + s] : 0.0f;
-        tl[j] = in && dD != 0.0f ? P.ws.s_t[s] : 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = k0 + j;
-        if (k >= cnt) break;
-        const int64_t s = first + k;
-        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
-        if (k < used) {
-          const float sigma = sg[j];
-          const float col[3] = {cl[j][0], cl[j][1], cl[j][2]};
-          const float x = sigma * dt;
-          const float alpha = -expm1f(-x);
-          const float w = T * alpha;
-          const float Tn = T * expf(-x);
-          float dsig = 0.0f;
-          float dz[3];
-          for (int c = 0; c < 3; ++c) {
-            pre[c] = fmaf(w, col[c], pre[c]);
-            dsig = fmaf(dC[c], Tn * col[c] - (res[c] - pre[c]), dsig);
-            dz[c] = dC[c] * w * col[c] * (1.0f - col[c]);
-          }
-          if (dD != 0.0f) {
-            // depth D = sum T_j alpha_j t_j: the colour adjoint with c_j -> t_j
-            const float tj = tl[j];
-            pre_d = fmaf(w, tj, pre_d);
-            dsig = fmaf(dD, Tn * tj - (res[4] - pre_d), dsig);
-          }
-          d0 = dsig * dt * sigma;
-          d1 = dz[0];
-          d2 = dz[1];
-          d3 = dz[2];
-          T = Tn;
-        }
-        P.ws.dout[s] = d0;
-        P.ws.dout[S_cap + s] = d1;
-        P.ws.dout[2 * S_cap + s] = d2;
-        P.ws.dout[3 * S_cap + s] = d3;
-      }
-    }
   }
-  // deterministic block sum of the per-ray Huber terms
+  // ---- pass 2: the adjoint, the same scans again
+  float xs2 = 0.0f, pre[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int base = lo; base < hi; base += 32) {
+    int lr, start;
+    unsigned heads;
+    float sg, c0, c1, c2, tt;
+    sample(base, lr, sg, c0, c1, c2, tt, start, heads);
+    const int src = lr >= 0 ? lr : 0;
+    const float dts = __shfl_sync(FULL, dt, src), carry = __shfl_sync(FULL, xs2, src);
+    const float x = lr >= 0 ? sg * dts : 0.0f;
+    const float incl = seg_scan(x, lane, start);
+    const float up = __shfl_up_sync(FULL, incl, 1);
+    const float excl = lane > start ? up : 0.0f;
+    const float T = expf(-(carry + excl));
+    const float Tn = expf(-(carry + incl));
+    const bool used = lr >= 0 && T >= P.t_eps;
+    const float w = used ? T * -expm1f(-x) : 0.0f;
+    float q[4] = {w * c0, w * c1, w * c2, w * tt};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = seg_scan(q[k], lane, start);
+    float rc[4], dc[4], pc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      rc[k] = __shfl_sync(FULL, k < 3 ? res[k] : res[4], src);
+      dc[k] = __shfl_sync(FULL, k < 3 ? dC[k] : dD, src);
+      pc[k] = __shfl_sync(FULL, pre[k], src);
+    }
+    if (lr >= 0) {
+      const int s = base + lane;
+      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+      if (used) {
+        const float col[4] = {c0, c1, c2, tt};
+        float dsig = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dsig = fmaf(dc[k], Tn * col[k] - (rc[k] - (pc[k] + q[k])), dsig);
+        d0 = dsig * dts * sg;
+        d1 = dc[0] * w * c0 * (1.0f - c0);
+        d2 = dc[1] * w * c1 * (1.0f - c1);
+        d3 = dc[2] * w * c2 * (1.0f - c2);
+      }
+      P.ws.dout[s] = d0;
+      P.ws.dout[S_cap + s] = d1;
+      P.ws.dout[2 * S_cap + s] = d2;
+      P.ws.dout[3 * S_cap + s] = d3;
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && lr >= 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) seg[wid][lr][k] = q[k];
+      seg[wid][lr][6] = incl;
+      seg[wid][lr][7] = 1.0f;
+    }
+    __syncwarp();
+    if (seg[wid][lane][7] != 0.0f) {
+      for (int k = 0; k < 4; ++k) pre[k] += seg[wid][lane][k];
+      xs2 += seg[wid][lane][6];
+      seg[wid][lane][7] = 0.0f;
+    }
+    __syncwarp();
+  }
+  // deterministic block sum of the per-ray loss terms
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loss;
+  if (lane == 0) red[wid] = loss;
   __syncthreads();
   if (threadIdx.x == 0) {
     float t = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int k = 0; k < 8; ++k) t += red[k];
     loss_part[blockIdx.x] = t;
   }
 }
