@@ -508,11 +508,12 @@ __device__ __forceinline__ void relu_split64(uint32_t row, float (&h)[64], uint3
   for (int w = 0; w < 2; ++w) {
     uint32_t bits = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) bits |= (h[32 * w + j] > 0.0f ? 1u : 0u) << j;
+    for (int j = 0; j < 32; ++j) {
+      if (h[32 * w + j] > 0.0f) bits |= 1u << j;
+      else h[32 * w + j] = 0.0f;
+    }
     m[w] = bits;
   }
-#pragma unroll
-  for (int i = 0; i < 64; ++i) h[i] = fmaxf(h[i], 0.0f);
   if constexpr (STORE) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
