@@ -73,7 +73,7 @@ struct invr_graph_s {
   struct Frame {
     float4* x_live = nullptr;
     float4* dq = nullptr;
-    uint16_t* cand = nullptr;
+    uint32_t* cand = nullptr;
     uint16_t* cand_n = nullptr;
     uint32_t* lut_live = nullptr;   // [G^3] live index field of this frame
     bool set = false;
@@ -86,7 +86,7 @@ struct invr_graph_s {
   int lut_res = 0;
   uint16_t* lut_canon = nullptr;   // [G^3][K] canonical KNN field
   float4* x_canon4 = nullptr;      // canonical nodes, packed
-  uint16_t* canon_cand = nullptr;  // candidate grid over the canonical nodes
+  uint32_t* canon_cand = nullptr;  // candidate grid over the canonical nodes
   uint16_t* canon_cand_n = nullptr;
 };
 
@@ -744,7 +744,7 @@ invr_status invr_ctx_autotune(invr_ctx ctx, const invr_train_args* a, invr_strea
   // coordinate descent over the launch shapes: the forward's structure first
   // (staged; fused with 256- or 128-sample work items: fused + 2 * (chunk == 128)),
   // then the grid sizes and the aggregation threshold
-  const int form_c[] = {0, 1, 3}, warp_c[] = {4, 8, 16}, enc_c[] = {4, 8, 16, 32}, bwd_c[] = {1, 2, 4, 8},
+  const int form_c[] = {0, 1, 3}, warp_c[] = {2, 3, 4}, enc_c[] = {4, 8, 16, 32}, bwd_c[] = {1, 2, 4, 8},
             agg_c[] = {0, 64, 128, 256, 512, 1024};
   const int* dims[] = {form_c, warp_c, enc_c, bwd_c, agg_c};
   const int dim_n[] = {3, 3, 4, 4, 6};

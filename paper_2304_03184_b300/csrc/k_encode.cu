@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(CHUNK) k_warp_encode(const __grid_constant__ P
         const float3 p = make_float3(P.ws.s_pos[s], P.ws.s_pos[S_cap + s], P.ws.s_pos[2 * S_cap + s]);
         int64_t cell = 0;
         const uint32_t n = (W.mode == 0 || W.lut_live) ? 0u : knn_locate(W, p, cell);
-        x = warp_point_upto<KMAX>(W, p, cell, n);
+        x = warp_point_upto<KMAX>(W, W.x_live, p, cell, n);
       }
       P.ws.s_vc[s] = x.x;
       P.ws.s_vc[S_cap + s] = x.y;

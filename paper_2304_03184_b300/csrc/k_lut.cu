@@ -159,7 +159,7 @@ static void live_k(const float4* x, const float4* dq, float inv_r2, int G, const
   k_lut_live<K><<<grid, 256, 0, s>>>(x, dq, inv_r2, G, canon, live);
 }
 
-cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint16_t* cand, const uint16_t* cand_n,
+cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint32_t* cand, const uint16_t* cand_n,
                              int cap, int G, uint16_t* canon, int num_sms, cudaStream_t s) {
   WarpDev W{};
   W.mode = 1;

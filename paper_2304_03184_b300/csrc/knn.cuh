@@ -1,14 +1,23 @@
 // Exact K-nearest-node selection shared by the warp and the look-up-table builder: the
 // FP32 key ((dx*dx)+(dy*dy))+(dz*dz), ties to the lower node index, candidates from the
 // per-frame 128^3 candidate grid (or all nodes where a cell overflowed).
+//
+// A cell's candidate list is sorted by the nodes' distance r_i from the cell centre c, each
+// entry holding the node id (low 16 bits) and a lower bound of r_i (high 16 bits, in units
+// of 2^-14).  For a point p of the cell, every node j at or after list position i is at
+// least r_i - |p - c| from p, so once that bound squared exceeds the current K-th key no
+// later candidate can enter the K nearest and the scan stops.
 #pragma once
 #include "invr_internal.cuh"
 
 namespace invr {
 
+constexpr float kKnnRUnit = 1.0f / 16384.0f;  // r bound units (r < 4 covers [-1,1]^3)
+
 // Insert (key, id) into the ascending list; equal keys keep the earlier (lower) id first.
 // From the first slot whose key is larger, every later entry shifts down by one (an
 // entry carried down is never compared again, so entries with equal keys keep their order).
+// For candidates arriving in index order.
 template <int K>
 __device__ __forceinline__ void knn_insert(float key, int id, float (&keys)[K], int (&ids)[K]) {
   if (!(key < keys[K - 1])) return;
@@ -25,6 +34,22 @@ __device__ __forceinline__ void knn_insert(float key, int id, float (&keys)[K], 
   }
 }
 
+// (key, id) ascending insertion with the tie rule written out, for candidates in any order.
+template <int K>
+__device__ __forceinline__ void knn_insert_any(float key, int id, float (&keys)[K], int (&ids)[K]) {
+  if (!(key < keys[K - 1] || (key == keys[K - 1] && id < ids[K - 1]))) return;
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const bool lt = key < keys[m] || (key == keys[m] && id < ids[m]);
+    const float tk = lt ? keys[m] : key;
+    const int ti = lt ? ids[m] : id;
+    keys[m] = lt ? key : keys[m];
+    ids[m] = lt ? id : ids[m];
+    key = tk;
+    id = ti;
+  }
+}
+
 // The candidate-grid cell of p and its list length, or n = kKnnOverflow where every node
 // must be scanned (no grid, p outside the box, or the cell's list overflowed).
 __device__ __forceinline__ uint32_t knn_locate(const WarpDev& W, float3 p, int64_t& cell) {
@@ -36,34 +61,55 @@ __device__ __forceinline__ uint32_t knn_locate(const WarpDev& W, float3 p, int64
   return kKnnOverflow;
 }
 
-// The K nearest nodes of p from the located cell's list (or all nodes).
-template <int K>
-__device__ __forceinline__ void knn_scan(const WarpDev& W, float3 p, int64_t cell, uint32_t n, float (&keys)[K],
-                                         int (&ids)[K]) {
+// Centre of candidate-grid cell `cell` (the builder's formula).
+__device__ __forceinline__ float3 knn_cell_centre(int64_t cell) {
+  constexpr float H = 2.0f / kKnnG;
+  const int ix = (int)(cell % kKnnG), iy = (int)((cell / kKnnG) % kKnnG), iz = (int)(cell / (kKnnG * kKnnG));
+  return make_float3(-1.0f + (ix + 0.5f) * H, -1.0f + (iy + 0.5f) * H, -1.0f + (iz + 0.5f) * H);
+}
+
+// Node i's live position, from global memory (read-only path) or from a copy in shared memory.
+template <bool SMEM>
+__device__ __forceinline__ float4 node_at(const float4* xs, int i) {
+  if constexpr (SMEM) return xs[i];
+  else return __ldg(xs + i);
+}
+
+// The K nearest nodes of p from the located cell's list (or all nodes); xs is W.x_live or
+// its copy in shared memory (SMEM).
+template <int K, bool SMEM = false>
+__device__ __forceinline__ void knn_scan(const WarpDev& W, const float4* xs, float3 p, int64_t cell, uint32_t n,
+                                         float (&keys)[K], int (&ids)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     keys[k] = INFINITY;
     ids[k] = -1;
   }
   if (n == kKnnOverflow) {
-    for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
-  } else {
-    // the list in chunks of 8 ids (one 16-byte load; cap is a multiple of 8), whose 8 node
-    // loads are issued together, then inserted in list order (= index order, as before)
-    const uint16_t* list = W.cand + cell * W.cap;
-    uint32_t c = 0;
-    for (; c + 8 <= n; c += 8) {
-      const uint4 q = __ldg(reinterpret_cast<const uint4*>(list + c));
-      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-      float4 x[8];
+    for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, node_at<SMEM>(xs, i)), i, keys, ids);
+    return;
+  }
+  // |p - c|, rounded up: the bound r_i - |p - c| must not exceed the true distance
+  const float3 c = knn_cell_centre(cell);
+  const float ex = p.x - c.x, ey = p.y - c.y, ez = p.z - c.z;
+  const float pc = sqrtf(ex * ex + ey * ey + ez * ez) * 1.00001f + 1e-7f;
+  // groups of 4 entries (one 16-byte load; cap is a multiple of 8) whose node loads are
+  // issued together; ids past the list's end are replaced by node 0 and never inserted
+  const uint32_t* list = W.cand + cell * W.cap;
+  for (uint32_t g = 0; g < n; g += 4) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(list + g));
+    const uint32_t e[4] = {q.x, q.y, q.z, q.w};
+    float4 x[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[j] = __ldg(W.x_live + ((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu));
+    for (int j = 0; j < 4; ++j) x[j] = node_at<SMEM>(xs, g + j < n ? (int)(e[j] & 0xFFFFu) : 0);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) knn_insert<K>(knn_key(p, x[j]), (int)((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu), keys, ids);
-    }
-    for (; c < n; ++c) {
-      const int i = __ldg(list + c);
-      knn_insert<K>(knn_key(p, __ldg(W.x_live + i)), i, keys, ids);
+    for (int j = 0; j < 4; ++j) {
+      if (g + j >= n) return;
+      // every later node is at least a = r_lo - |p - c| from p; its FP32 key is then at
+      // least a^2 (1 - 2^-20), so a^2 (1 - 1e-5) > the K-th key rules all of them out
+      const float a = (float)(e[j] >> 16) * kKnnRUnit - pc;
+      if (a > 0.0f && a * a * 0.99999f > keys[K - 1]) return;
+      knn_insert_any<K>(knn_key(p, x[j]), (int)(e[j] & 0xFFFFu), keys, ids);
     }
   }
 }
@@ -72,7 +118,7 @@ template <int K>
 __device__ __forceinline__ void knn_select(const WarpDev& W, float3 p, float (&keys)[K], int (&ids)[K]) {
   int64_t cell;
   const uint32_t n = knn_locate(W, p, cell);
-  knn_scan<K>(W, p, cell, n, keys, ids);
+  knn_scan<K>(W, W.x_live, p, cell, n, keys, ids);
 }
 
 }  // namespace invr

@@ -34,22 +34,6 @@ __device__ __forceinline__ float3 dq_inverse_apply(float4 br, float4 bd, float3 
   return make_float3(R00 * qx + R10 * qy + R20 * qz, R01 * qx + R11 * qy + R21 * qz, R02 * qx + R12 * qy + R22 * qz);
 }
 
-// (key, id) ascending insertion with the tie rule written out: the table's ids arrive in
-// canonical-key order, not in index order.
-template <int K>
-__device__ __forceinline__ void lut_insert(float key, int id, float (&keys)[K], int (&ids)[K]) {
-#pragma unroll
-  for (int m = 0; m < K; ++m) {
-    const bool lt = key < keys[m] || (key == keys[m] && id < ids[m]);
-    const float tk = lt ? keys[m] : key;
-    const int ti = lt ? ids[m] : id;
-    keys[m] = lt ? key : keys[m];
-    ids[m] = lt ? id : ids[m];
-    key = tk;
-    id = ti;
-  }
-}
-
 // Neighbour set from the tables (Sec. 4.2): the sample's live voxel (clamped into the
 // grid) -> the canonical voxel stored there -> its K nodes, ordered by the live key; a
 // hole (no canonical voxel landed there) falls back to the exact search.
@@ -71,20 +55,21 @@ __device__ __forceinline__ void lut_select(const WarpDev& W, float3 p, float (&k
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int id = __ldg(row + j);
-    lut_insert<K>(knn_key(p, __ldg(W.x_live + id)), id, keys, ids);
+    knn_insert_any<K>(knn_key(p, __ldg(W.x_live + id)), id, keys, ids);  // ids arrive in canonical-key order
   }
 }
 
-// The blend of the K nearest nodes; cell and n from knn_locate (ignored with look-up tables).
-template <int K>
-__device__ __forceinline__ float3 dqb_warp_at(const WarpDev& W, float3 p, int64_t cell, uint32_t n,
-                                              int32_t* ids_out, int64_t ids_ld, int64_t i) {
+// The blend of the K nearest nodes; cell and n from knn_locate (ignored with look-up tables);
+// xs: the node positions the search reads (W.x_live, or its copy in shared memory if SMEM).
+template <int K, bool SMEM = false>
+__device__ __forceinline__ float3 dqb_warp_at(const WarpDev& W, const float4* xs, float3 p, int64_t cell,
+                                              uint32_t n, int32_t* ids_out, int64_t ids_ld, int64_t i) {
   float keys[K];
   int ids[K];
-  if (W.lut_live) {
+  if (!SMEM && W.lut_live) {
     lut_select<K>(W, p, keys, ids);
   } else {
-    knn_scan<K>(W, p, cell, n, keys, ids);
+    knn_scan<K, SMEM>(W, xs, p, cell, n, keys, ids);
   }
   if (ids[0] < 0) return p;  // unreachable for finite p (every list holds >= K nodes)
   const float4 ref = __ldg(W.dq + 2 * ids[0]);
@@ -108,31 +93,33 @@ __device__ __forceinline__ float3 dqb_warp(const WarpDev& W, float3 p, int32_t* 
                                            int64_t i) {
   int64_t cell = 0;
   const uint32_t n = W.lut_live ? 0u : knn_locate(W, p, cell);
-  return dqb_warp_at<K>(W, p, cell, n, ids_out, ids_ld, i);
+  return dqb_warp_at<K>(W, W.x_live, p, cell, n, ids_out, ids_ld, i);
 }
 
 // Views whose K is at most KMAX (the plan's largest): the instantiations for larger K are not
 // compiled into the kernel, which keeps its registers (and so its occupancy) to what KMAX needs.
-template <int KMAX>
-__device__ __forceinline__ float3 warp_point_upto(const WarpDev& W, float3 p, int64_t cell, uint32_t n) {
+// SMEM: xs is a shared-memory copy of W.x_live (the caller has checked W.lut_live == null).
+template <int KMAX, bool SMEM = false>
+__device__ __forceinline__ float3 warp_point_upto(const WarpDev& W, const float4* xs, float3 p, int64_t cell,
+                                                  uint32_t n) {
   if (W.mode == 0) return rigid_inverse(W, p);
   if constexpr (KMAX <= 4) {
     switch (W.K) {
-      case 1: return dqb_warp_at<1>(W, p, cell, n, nullptr, 0, 0);
-      case 2: return dqb_warp_at<2>(W, p, cell, n, nullptr, 0, 0);
-      case 3: return dqb_warp_at<3>(W, p, cell, n, nullptr, 0, 0);
-      default: return dqb_warp_at<4>(W, p, cell, n, nullptr, 0, 0);
+      case 1: return dqb_warp_at<1, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 2: return dqb_warp_at<2, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 3: return dqb_warp_at<3, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      default: return dqb_warp_at<4, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
     }
   } else {
     switch (W.K) {
-      case 1: return dqb_warp_at<1>(W, p, cell, n, nullptr, 0, 0);
-      case 2: return dqb_warp_at<2>(W, p, cell, n, nullptr, 0, 0);
-      case 3: return dqb_warp_at<3>(W, p, cell, n, nullptr, 0, 0);
-      case 4: return dqb_warp_at<4>(W, p, cell, n, nullptr, 0, 0);
-      case 5: return dqb_warp_at<5>(W, p, cell, n, nullptr, 0, 0);
-      case 6: return dqb_warp_at<6>(W, p, cell, n, nullptr, 0, 0);
-      case 7: return dqb_warp_at<7>(W, p, cell, n, nullptr, 0, 0);
-      default: return dqb_warp_at<8>(W, p, cell, n, nullptr, 0, 0);
+      case 1: return dqb_warp_at<1, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 2: return dqb_warp_at<2, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 3: return dqb_warp_at<3, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 4: return dqb_warp_at<4, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 5: return dqb_warp_at<5, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 6: return dqb_warp_at<6, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      case 7: return dqb_warp_at<7, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
+      default: return dqb_warp_at<8, SMEM>(W, xs, p, cell, n, nullptr, 0, 0);
     }
   }
 }

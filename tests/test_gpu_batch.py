@@ -108,7 +108,7 @@ def test_autotune_keeps_parameters(env):
     tb, fields, keep = make_batches(invr, ctx, tw, invr.INVR_MLP_BF16)
     before = [f.get_params()[:2] for f in fields.values()]
     tune = ctx.autotune(tb)
-    assert tune["warp_ctas_per_sm"] in (4, 8, 16) and tune["encode_ctas_per_sm"] in (4, 8, 16, 32)
+    assert tune["warp_ctas_per_sm"] in (2, 3, 4) and tune["encode_ctas_per_sm"] in (4, 8, 16, 32)
     assert tune["encode_bwd_ctas_per_sm"] in (1, 2, 4, 8) and tune["agg_res"] in (0, 64, 128, 256, 512, 1024)
     assert tune["fused"] in (0, 1) and tune["chunk"] in (128, 256)
     for f, (t0, w0) in zip(fields.values(), before):
