@@ -19,6 +19,7 @@ no exchange step at one GPU per key-frame set); value = all ranks' samples / max
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -57,6 +58,13 @@ def parse():
     ap.add_argument("--render-only", action="store_true",
                     help="time only the two-field 512x512 render (all three precisions; for launch lists)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kf-frames", type=int, default=8,
+                    help="key frames of the batched workload (smaller cases for ncu captures)")
+    ap.add_argument("--kf-log2-rays", type=float, nargs=2, default=(14.0, 18.0),
+                    help="range of log2(rays) per frame and field of the batched workload")
+    ap.add_argument("--tune", type=str, default=None,
+                    help="fixed launch shapes of the batched step as JSON (keys of Context.TUNE_KEYS; the "
+                         "rest keep the context's defaults) instead of autotuning")
     return ap.parse_args()
 
 
@@ -276,6 +284,31 @@ L2_BOUND = {"encode": ("gather_v4_gbs", "random float4 loads from"),
             "encode_bwd": ("atomic_v4_gbs", "random float4 atomic adds into")}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step's scatter launches
+# (both fields) on the batched key-frame workload, from one ncu capture of that workload,
+# with a digest of the scatter's source files at the time of the capture: the bench line
+# carries the figure only while the kernel is unchanged (else traffic is null).
+SCATTER_SOURCES = ("paper_2304_03184_b300/csrc/k_encode.cu", "paper_2304_03184_b300/csrc/hash_grid.cuh")
+SCATTER_DRAM = {"sources_sha16": "e8433eea002116c7", "workload": "keyframe_batch_8frames_x2fields_s128",
+                "bytes": 2_212_779_520}
+
+
+def sources_sha16(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def scatter_traffic(workload):
+    """The captured DRAM bytes of the scatter per step, or None (no capture of this workload,
+    or the kernel's sources changed since)."""
+    if not SCATTER_DRAM or SCATTER_DRAM["workload"] != workload:
+        return None
+    return SCATTER_DRAM["bytes"] if sources_sha16(SCATTER_SOURCES) == SCATTER_DRAM["sources_sha16"] else None
+
+
 def roofline(ktime, tw, R, S_occ, peaks, l2=None):
     fp = tw.fields[0]
     n_params = fp.desc.n_table_params() + fp.desc.n_weight_params()
@@ -288,14 +321,17 @@ def roofline(ktime, tw, R, S_occ, peaks, l2=None):
         key, form = L2_BOUND[name]
         ach, peak = payload / dur / 1e9, l2[key]
         hbm_peak = peaks.get("hbm_gbs", 6400.0)
+        traffic = scatter_traffic(tw.name) if name == "encode_bwd" else None
         return {"kernel": name, "bound": "l2", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None,
+                "frac": round(ach / peak, 4), "traffic": traffic,
                 "peak_source": f"measured in this run by the library's L2 probe: {form} a 64 MiB resident table",
                 "algorithmic_bytes": payload, "ms": round(kms / kn, 4),
                 "hbm": {"bytes": work, "achieved": round(work / dur / 1e9, 1), "peak": hbm_peak,
                         "frac": round(work / dur / 1e9 / hbm_peak, 4),
                         "note": "the kernel's per-sample inputs and outputs; the table traffic stays in L2"},
-                "traffic_note": "DRAM bytes are measured by ncu only, not inside this run"}
+                "traffic_note": ("DRAM bytes of the stage from an ncu capture of this workload at the current "
+                                 "kernel sources (the table traffic stays in L2)" if traffic is not None else
+                                 "no ncu capture of this workload at the current kernel sources")}
     if bound == "alu":
         peak = fp32_alu_peak(peaks.get("sm_max_mhz", 2032.0))
         ach = work / dur / 1e12
@@ -384,6 +420,7 @@ def apply_batched(out, bt, invr, ctx, args, world, peaks):
     per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
     out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
                                     / nsteps * args.steps))
+    out["gpu_launches_per_step"] = round(out["gpu_launches"] / args.steps, 1)
     out["variants"] = {args.prec + "_graph": {"value": round(bvalue, 1), "ms_per_step": round(bt["ms"], 3)},
                        args.prec + "_eager": {"value": round(world * bt["S_nom"] / (bt["eager_ms"] * 1e-3), 1),
                                               "ms_per_step": round(bt["eager_ms"], 3)},
@@ -521,7 +558,7 @@ def bench_batched(invr, args, flush, world, prec_name, with_fp32=True):
     with_fp32 adds the plain comparison (the same frames as sequential FP32 calls)."""
     import torch
     from paper_2304_03184_b300 import synth
-    tw = synth.keyframe_batch_workload()
+    tw = synth.keyframe_batch_workload(n_frames=args.kf_frames, log2_rays=tuple(args.kf_log2_rays))
     R = sum(b.rays.n for b in tw.batches)
     S_nom = R * tw.n_samples
     stream = torch.cuda.current_stream()
@@ -530,7 +567,12 @@ def bench_batched(invr, args, flush, world, prec_name, with_fp32=True):
     tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
     S_occ = occupied_samples(invr, ctx, tb)
     ctx.reserve(R, max(32, 2 * (S_occ // R + 1)))       # fixed workspace: capture allocates nothing
-    tune = ctx.autotune(tb)
+    if args.tune:
+        tune = dict(ctx.tune(), **json.loads(args.tune))
+        ctx.set_tune(tune)
+        tune = ctx.tune()
+    else:
+        tune = ctx.autotune(tb)
     # eager timed steps: per-kernel breakdown (same kernels as the graph)
     eager_ms, ktime = time_train(invr, ctx, tb, max(5, args.steps // 4), args.warmup, flush, world)
     graph = invr.TrainGraph(ctx, tb, warmup=2)

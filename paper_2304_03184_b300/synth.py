@@ -488,5 +488,7 @@ def keyframe_batch_workload(seed: int = 4, n_frames: int = 8, n_samples: int = 1
             idx = rng.choice(all_rays.n, size=n, replace=False)
             rays = subset_rays(all_rays, idx)
             batches.append(TrainBatch(rays, v, target_colours(rng, rays), *sensor_depth_mask(rays, c, ax)))
-    return TrainWorkload(f"keyframe_batch_{n_frames}frames_x2fields_s{n_samples}", batches,
-                         [human, obj], n_samples)
+    name = f"keyframe_batch_{n_frames}frames_x2fields_s{n_samples}"
+    if tuple(log2_rays) != (14.0, 18.0):
+        name += f"_rays2^{log2_rays[0]:g}-2^{log2_rays[1]:g}"
+    return TrainWorkload(name, batches, [human, obj], n_samples)
