@@ -152,8 +152,9 @@ invr_status invr_graph_create(invr_ctx ctx, const invr_graph_desc* desc, const f
 /* Set frame `frame`'s motion (Sec. 4.2, Eq. 4): node dual quaternions dq_dev [8][N]
  * (canonical -> live) and deformed node positions x_live_dev [3][N] (x_i^t = dq_i^t x_i,
  * the tracker's output).  The library copies both and builds, on `stream`, its
- * per-frame nearest-node candidate grid over the live nodes (128^3 cells, ~260 MiB per
- * frame, through a 64^3 scratch grid owned by the graph: calls on one graph must be
+ * per-frame nearest-node candidate grid over the live nodes (128^3 cells: sorted lists of
+ * up to 64 entries (128 for K > 4) plus a 32-byte head per cell, ~576 MiB per frame at
+ * K <= 4, through a 64^3 scratch grid owned by the graph: calls on one graph must be
  * ordered, i.e. issued on one stream or synchronised). */
 invr_status invr_graph_set_pose(invr_graph graph, int frame, const float* dq_dev, const float* x_live_dev,
                                 invr_stream stream);

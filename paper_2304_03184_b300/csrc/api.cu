@@ -74,7 +74,7 @@ struct invr_graph_s {
     float4* x_live = nullptr;
     float4* dq = nullptr;
     uint32_t* cand = nullptr;
-    uint16_t* cand_n = nullptr;
+    uint32_t* cand_head = nullptr;  // [G^3][kKnnHead] the lists' heads
     uint32_t* lut_live = nullptr;   // [G^3] live index field of this frame
     bool set = false;
   };
@@ -87,7 +87,7 @@ struct invr_graph_s {
   uint16_t* lut_canon = nullptr;   // [G^3][K] canonical KNN field
   float4* x_canon4 = nullptr;      // canonical nodes, packed
   uint32_t* canon_cand = nullptr;  // candidate grid over the canonical nodes
-  uint16_t* canon_cand_n = nullptr;
+  uint32_t* canon_cand_head = nullptr;
 };
 
 namespace {
@@ -358,7 +358,7 @@ invr_status warp_dev(invr_ctx ctx, const invr_field_view& v, WarpDev& W) {
   W.x_live = fr.x_live;
   W.dq = fr.dq;
   W.cand = fr.cand;
-  W.cand_n = fr.cand_n;
+  W.cand_head = fr.cand_head;
   W.n_nodes = g->desc.n_nodes;
   W.K = g->desc.K;
   W.cap = g->cap;
@@ -1034,7 +1034,7 @@ invr_status invr_graph_set_pose(invr_graph g, int frame, const float* dq_dev, co
     if (g->cap > 0) {
       const size_t cells = (size_t)kKnnG * kKnnG * kKnnG;
       INVR_CUDA(ctx, dmalloc(&fr.cand, cells * g->cap));
-      INVR_CUDA(ctx, dmalloc(&fr.cand_n, cells));
+      INVR_CUDA(ctx, dmalloc(&fr.cand_head, cells * kKnnHead));
     }
   }
   INVR_CUDA(ctx, TIMED(ctx, "graph_pack", s, launch_graph_pack(dq_dev, x_live_dev, N, fr.dq, fr.x_live, s)));
@@ -1047,7 +1047,7 @@ invr_status invr_graph_set_pose(invr_graph g, int frame, const float* dq_dev, co
     }
     INVR_CUDA(ctx, TIMED(ctx, "knn_grid_build", s,
                          launch_knn_grid_build(fr.x_live, N, g->desc.K, g->cap, g->coarse, g->coarse_n, fr.cand,
-                                               fr.cand_n, ctx->num_sms, s)));
+                                               fr.cand_head, ctx->num_sms, s)));
   }
   if (g->lut_res > 0) {
     const size_t G3 = (size_t)g->lut_res * g->lut_res * g->lut_res;
@@ -1068,8 +1068,8 @@ static void free_lut(invr_graph g) {
     dfree(fr.lut_live);
     fr.lut_live = nullptr;
   }
-  dfree(g->lut_canon); dfree(g->x_canon4); dfree(g->canon_cand); dfree(g->canon_cand_n);
-  g->lut_canon = nullptr; g->x_canon4 = nullptr; g->canon_cand = nullptr; g->canon_cand_n = nullptr;
+  dfree(g->lut_canon); dfree(g->x_canon4); dfree(g->canon_cand); dfree(g->canon_cand_head);
+  g->lut_canon = nullptr; g->x_canon4 = nullptr; g->canon_cand = nullptr; g->canon_cand_head = nullptr;
   g->lut_res = 0;
 }
 
@@ -1093,7 +1093,7 @@ invr_status invr_graph_enable_lut(invr_graph g, int resolution, invr_stream stre
   }
   if (g->cap > 0) {
     const size_t cells = (size_t)kKnnG * kKnnG * kKnnG;
-    if (dmalloc(&g->canon_cand, cells * g->cap) != cudaSuccess || dmalloc(&g->canon_cand_n, cells) != cudaSuccess) {
+    if (dmalloc(&g->canon_cand, cells * g->cap) != cudaSuccess || dmalloc(&g->canon_cand_head, cells * kKnnHead) != cudaSuccess) {
       free_lut(g);
       return fail(ctx, INVR_E_OOM, "table allocation failed");
     }
@@ -1113,10 +1113,10 @@ invr_status invr_graph_enable_lut(invr_graph g, int resolution, invr_stream stre
       INVR_CUDA(ctx, dmalloc(&g->coarse_n, cc));
     }
     INVR_CUDA(ctx, launch_knn_grid_build(g->x_canon4, N, K, g->cap, g->coarse, g->coarse_n, g->canon_cand,
-                                         g->canon_cand_n, ctx->num_sms, s));
+                                         g->canon_cand_head, ctx->num_sms, s));
   }
   INVR_CUDA(ctx, TIMED(ctx, "lut_canon", s,
-                       launch_lut_canon(g->x_canon4, N, K, g->canon_cand, g->canon_cand_n, g->cap, resolution,
+                       launch_lut_canon(g->x_canon4, N, K, g->canon_cand, g->canon_cand_head, g->cap, resolution,
                                         g->lut_canon, ctx->num_sms, s)));
   for (auto& fr : g->frames) {
     if (!fr.set) continue;
@@ -1159,7 +1159,7 @@ invr_status invr_graph_destroy(invr_graph g) {
   cudaDeviceSynchronize();
   free_lut(g);
   for (auto& fr : g->frames) {
-    dfree(fr.x_live); dfree(fr.dq); dfree(fr.cand); dfree(fr.cand_n);
+    dfree(fr.x_live); dfree(fr.dq); dfree(fr.cand); dfree(fr.cand_head);
   }
   dfree(g->coarse); dfree(g->coarse_n);
   dfree(g->x_canon);

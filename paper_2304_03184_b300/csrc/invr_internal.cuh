@@ -22,6 +22,12 @@ constexpr int kOccRes = 128;    // occupancy grid resolution over [-1,1]^3
 constexpr int kTile = 128;      // sample tile: every view's sample range is padded to it
 constexpr int kKnnG = 128;      // nearest-node candidate grid resolution over [-1,1]^3
 constexpr uint16_t kKnnOverflow = 0xFFFF;
+// Candidate-list entries are (r bound << 16) | node id; ids are < 65535, so id 0xFFFF marks
+// the end of a list (kKnnEnd) and, in a cell's head with bound 0, a list that overflowed its
+// capacity (kKnnHeadOverflow: the cell's points scan every node).
+constexpr uint32_t kKnnEnd = 0xFFFFFFFFu;
+constexpr uint32_t kKnnHeadOverflow = 0x0000FFFFu;
+constexpr int kKnnHead = 8;     // entries of a cell's list kept in its 32-byte head
 constexpr int kKnnMaxCap = 128;  // largest candidate list capacity (a multiple of 32)
 constexpr int kRayBitWords = 32;   // 1024 samples per ray at most
 constexpr uint32_t kLutEmpty = 0xFFFFFFFFu;
@@ -60,8 +66,10 @@ struct WarpDev {
   float t[3];
   const float4* x_live;     // [N] (x, y, z, 0)
   const float4* dq;         // [N][2] (real, dual)
-  const uint32_t* cand;     // [G^3][cap] candidate entries per grid cell: (r bound << 16) | node id, ascending
-  const uint16_t* cand_n;   // [G^3] candidate count, kKnnOverflow = use all nodes
+  const uint32_t* cand;     // [G^3][cap] candidate entries per grid cell: (r bound << 16) | node id, ascending,
+                            // kKnnEnd after the last one (when shorter than cap)
+  const uint32_t* cand_head;  // [G^3][kKnnHead] the first entries of each cell's list (kKnnEnd past its
+                              // end; kKnnHeadOverflow: scan all nodes); null: no grid
   int n_nodes, K, cap;
   float inv_r2;             // 1 / radius^2
   // look-up-table neighbour search (Sec. 4.2); lut_live == null: exact search
@@ -356,7 +364,7 @@ cudaError_t launch_graph_pack(const float* dq_soa, const float* x_soa, int n, fl
 // (kKnnG/2)^3 x kKnnCoarseCapFactor * cap and (kKnnG/2)^3 entries)
 constexpr int kKnnCoarseCapFactor = 4;
 cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* coarse, uint16_t* coarse_n,
-                                  uint32_t* cand, uint16_t* cand_n, int num_sms, cudaStream_t s);
+                                  uint32_t* cand, uint32_t* cand_head, int num_sms, cudaStream_t s);
 
 // single-step entry points
 cudaError_t launch_ray_samples(int64_t n_rays, const float* o, const float* d, int n_samples, const uint32_t* occ,
@@ -398,7 +406,7 @@ cudaError_t launch_occ_update(const float* sigma, int64_t n, float decay, float 
 
 // look-up-table neighbour search (Sec. 4.2)
 cudaError_t launch_pack_points(const float* x_soa, int n, float4* out, cudaStream_t s);
-cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint32_t* cand, const uint16_t* cand_n,
+cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint32_t* cand, const uint32_t* cand_head,
                              int cap, int G, uint16_t* canon, int num_sms, cudaStream_t s);
 cudaError_t launch_lut_live(const float4* x_canon, const float4* dq, int n, int K, float inv_r2, int G,
                             const uint16_t* canon, uint32_t* live, int num_sms, cudaStream_t s);

@@ -159,13 +159,13 @@ static void live_k(const float4* x, const float4* dq, float inv_r2, int G, const
   k_lut_live<K><<<grid, 256, 0, s>>>(x, dq, inv_r2, G, canon, live);
 }
 
-cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint32_t* cand, const uint16_t* cand_n,
+cudaError_t launch_lut_canon(const float4* x_canon, int n, int K, const uint32_t* cand, const uint32_t* cand_head,
                              int cap, int G, uint16_t* canon, int num_sms, cudaStream_t s) {
   WarpDev W{};
   W.mode = 1;
   W.x_live = x_canon;  // the search runs over the canonical nodes
   W.cand = cand;
-  W.cand_n = cand_n;
+  W.cand_head = cand_head;
   W.cap = cap;
   W.n_nodes = n;
   W.K = K;

@@ -147,12 +147,15 @@ cudaError_t launch_graph_pack(const float* dq_soa, const float* x_soa, int n, fl
 // coarse lists (build scratch only: node ids in index order) hold 4x the fine capacity, so
 // few parents overflow; a child of an overflowed parent scans all nodes.  A fine list
 // (REFINE) is sorted by the entries (r_lo << 16) | id, r_lo a lower bound of the node's
-// distance from the cell centre in units of kKnnRUnit (the scan's early stop).
+// distance from the cell centre in units of kKnnRUnit (the scan's early stop), and ends with
+// kKnnEnd when shorter than cap; its first kKnnHead entries are copied into the cell's head
+// (kKnnEnd-padded), whose first entry is kKnnHeadOverflow when the list overflowed.  The
+// coarse level (!REFINE) writes ids in index order and a count per cell.
 template <int K, int G, bool REFINE>
 __global__ void __launch_bounds__(256) k_knn_grid_build(const float4* __restrict__ x, int n, int cap, int pcap,
                                                         const uint16_t* __restrict__ pcand,
                                                         const uint16_t* __restrict__ pcand_n, void* cand_out,
-                                                        uint16_t* cand_n) {
+                                                        uint16_t* cand_n, uint32_t* cand_head) {
   constexpr float H = 2.0f / G;
   constexpr float Rho = 0.8660254037844386f * H;
   __shared__ uint32_t srt[8][kKnnMaxCap];  // a fine cell's entries before sorting (one row per warp)
@@ -252,36 +255,45 @@ __global__ void __launch_bounds__(256) k_knn_grid_build(const float4* __restrict
         for (int t = 0; t < kKnnMaxCap / 32; ++t) rank[t] += o < e[t];
       }
       uint32_t* row = static_cast<uint32_t*>(cand_out) + cell * cap;
+      uint32_t* head = cand_head + cell * kKnnHead;
 #pragma unroll
       for (int t = 0; t < kKnnMaxCap / 32; ++t)
-        if (lane + 32 * t < count) row[rank[t]] = e[t];
+        if (lane + 32 * t < count) {
+          row[rank[t]] = e[t];
+          if (rank[t] < kKnnHead) head[rank[t]] = e[t];
+        }
+      if (lane < kKnnHead && lane >= count) head[lane] = kKnnEnd;
+      if (lane == 0 && count < cap) row[count] = kKnnEnd;
       __syncwarp();
+    } else if (REFINE && lane == 0) {
+      cand_head[cell * kKnnHead] = kKnnHeadOverflow;
     }
-    if (lane == 0) cand_n[cell] = count <= cap ? (uint16_t)count : kKnnOverflow;
+    if (!REFINE && lane == 0) cand_n[cell] = count <= cap ? (uint16_t)count : kKnnOverflow;
   }
 }
 
 template <int K>
 static void grid_build_k(const float4* x, int n, int cap, uint16_t* coarse, uint16_t* coarse_n, uint32_t* cand,
-                         uint16_t* cand_n, int grid, cudaStream_t s) {
+                         uint32_t* cand_head, int grid, cudaStream_t s) {
   const int pcap = kKnnCoarseCapFactor * cap;
-  k_knn_grid_build<K, kKnnG / 2, false><<<grid, 256, 0, s>>>(x, n, pcap, 0, nullptr, nullptr, coarse, coarse_n);
-  k_knn_grid_build<K, kKnnG, true><<<grid, 256, 0, s>>>(x, n, cap, pcap, coarse, coarse_n, cand, cand_n);
+  k_knn_grid_build<K, kKnnG / 2, false>
+      <<<grid, 256, 0, s>>>(x, n, pcap, 0, nullptr, nullptr, coarse, coarse_n, nullptr);
+  k_knn_grid_build<K, kKnnG, true><<<grid, 256, 0, s>>>(x, n, cap, pcap, coarse, coarse_n, cand, nullptr, cand_head);
 }
 
 cudaError_t launch_knn_grid_build(const float4* x_live, int n, int K, int cap, uint16_t* coarse, uint16_t* coarse_n,
-                                  uint32_t* cand, uint16_t* cand_n, int num_sms, cudaStream_t s) {
+                                  uint32_t* cand, uint32_t* cand_head, int num_sms, cudaStream_t s) {
   if (cap > kKnnMaxCap || cap % 8 != 0) return cudaErrorInvalidValue;
   const int grid = num_sms * 8;
   switch (K) {
-    case 1: grid_build_k<1>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    case 2: grid_build_k<2>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    case 3: grid_build_k<3>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    case 4: grid_build_k<4>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    case 5: grid_build_k<5>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    case 6: grid_build_k<6>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    case 7: grid_build_k<7>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
-    default: grid_build_k<8>(x_live, n, cap, coarse, coarse_n, cand, cand_n, grid, s); break;
+    case 1: grid_build_k<1>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    case 2: grid_build_k<2>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    case 3: grid_build_k<3>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    case 4: grid_build_k<4>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    case 5: grid_build_k<5>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    case 6: grid_build_k<6>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    case 7: grid_build_k<7>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
+    default: grid_build_k<8>(x_live, n, cap, coarse, coarse_n, cand, cand_head, grid, s); break;
   }
   return cudaGetLastError();
 }

@@ -6,7 +6,11 @@
 // entry holding the node id (low 16 bits) and a lower bound of r_i (high 16 bits, in units
 // of 2^-14).  For a point p of the cell, every node j at or after list position i is at
 // least r_i - |p - c| from p, so once that bound squared exceeds the current K-th key no
-// later candidate can enter the K nearest and the scan stops.
+// later candidate can enter the K nearest and the scan stops.  The first kKnnHead entries of
+// every list also sit in the cell's own 32-byte head (one sector, read without first reading
+// a count: lists end with an end marker), so a scan that stops within them -- most do --
+// touches one sector of a 64 MB array per frame (the occupied cells' heads stay in L2)
+// instead of a row of the cap-entry array.
 #pragma once
 #include "invr_internal.cuh"
 
@@ -50,13 +54,13 @@ __device__ __forceinline__ void knn_insert_any(float key, int id, float (&keys)[
   }
 }
 
-// The candidate-grid cell of p and its list length, or n = kKnnOverflow where every node
-// must be scanned (no grid, p outside the box, or the cell's list overflowed).
+// The candidate-grid cell of p (returns 0), or kKnnOverflow where every node must be scanned
+// (no grid, or p outside the box).  Reads no memory.
 __device__ __forceinline__ uint32_t knn_locate(const WarpDev& W, float3 p, int64_t& cell) {
   cell = 0;
-  if (W.cand_n && fabsf(p.x) <= 1.001f && fabsf(p.y) <= 1.001f && fabsf(p.z) <= 1.001f) {
+  if (W.cand_head && fabsf(p.x) <= 1.001f && fabsf(p.y) <= 1.001f && fabsf(p.z) <= 1.001f) {
     cell = grid_cell(p.x, kKnnG) + kKnnG * (grid_cell(p.y, kKnnG) + kKnnG * grid_cell(p.z, kKnnG));
-    return __ldg(W.cand_n + cell);
+    return 0u;
   }
   return kKnnOverflow;
 }
@@ -75,8 +79,33 @@ __device__ __forceinline__ float4 node_at(const float4* xs, int i) {
   else return __ldg(xs + i);
 }
 
+// Four entries of a cell's list (one 16-byte load), their node loads issued together: each
+// is inserted unless the list has ended or the distance bound rules it and every later entry
+// out.  Returns false once the scan must stop.
+template <int K, bool SMEM>
+__device__ __forceinline__ bool knn_group(const float4* xs, float3 p, float pc, uint4 q, float (&keys)[K],
+                                          int (&ids)[K]) {
+  const uint32_t e[4] = {q.x, q.y, q.z, q.w};
+  float4 x[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t id = e[j] & 0xFFFFu;
+    x[j] = node_at<SMEM>(xs, id == 0xFFFFu ? 0 : (int)id);  // end markers load node 0, never inserted
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if ((e[j] & 0xFFFFu) == 0xFFFFu) return false;
+    // every later node is at least a = r_lo - |p - c| from p; its FP32 key is then at
+    // least a^2 (1 - 2^-20), so a^2 (1 - 1e-5) > the K-th key rules all of them out
+    const float a = (float)(e[j] >> 16) * kKnnRUnit - pc;
+    if (a > 0.0f && a * a * 0.99999f > keys[K - 1]) return false;
+    knn_insert_any<K>(knn_key(p, x[j]), (int)(e[j] & 0xFFFFu), keys, ids);
+  }
+  return true;
+}
+
 // The K nearest nodes of p from the located cell's list (or all nodes); xs is W.x_live or
-// its copy in shared memory (SMEM).
+// its copy in shared memory (SMEM).  The list's head first, then the rest of its row.
 template <int K, bool SMEM = false>
 __device__ __forceinline__ void knn_scan(const WarpDev& W, const float4* xs, float3 p, int64_t cell, uint32_t n,
                                          float (&keys)[K], int (&ids)[K]) {
@@ -85,7 +114,13 @@ __device__ __forceinline__ void knn_scan(const WarpDev& W, const float4* xs, flo
     keys[k] = INFINITY;
     ids[k] = -1;
   }
-  if (n == kKnnOverflow) {
+  uint4 h0 = make_uint4(kKnnHeadOverflow, 0u, 0u, 0u), h1 = h0;
+  if (n != kKnnOverflow) {
+    const uint4* head = reinterpret_cast<const uint4*>(W.cand_head + cell * kKnnHead);
+    h0 = __ldg(head);
+    h1 = __ldg(head + 1);
+  }
+  if (h0.x == kKnnHeadOverflow) {
     for (int i = 0; i < W.n_nodes; ++i) knn_insert<K>(knn_key(p, node_at<SMEM>(xs, i)), i, keys, ids);
     return;
   }
@@ -93,25 +128,10 @@ __device__ __forceinline__ void knn_scan(const WarpDev& W, const float4* xs, flo
   const float3 c = knn_cell_centre(cell);
   const float ex = p.x - c.x, ey = p.y - c.y, ez = p.z - c.z;
   const float pc = sqrtf(ex * ex + ey * ey + ez * ez) * 1.00001f + 1e-7f;
-  // groups of 4 entries (one 16-byte load; cap is a multiple of 8) whose node loads are
-  // issued together; ids past the list's end are replaced by node 0 and never inserted
-  const uint32_t* list = W.cand + cell * W.cap;
-  for (uint32_t g = 0; g < n; g += 4) {
-    const uint4 q = __ldg(reinterpret_cast<const uint4*>(list + g));
-    const uint32_t e[4] = {q.x, q.y, q.z, q.w};
-    float4 x[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = node_at<SMEM>(xs, g + j < n ? (int)(e[j] & 0xFFFFu) : 0);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (g + j >= n) return;
-      // every later node is at least a = r_lo - |p - c| from p; its FP32 key is then at
-      // least a^2 (1 - 2^-20), so a^2 (1 - 1e-5) > the K-th key rules all of them out
-      const float a = (float)(e[j] >> 16) * kKnnRUnit - pc;
-      if (a > 0.0f && a * a * 0.99999f > keys[K - 1]) return;
-      knn_insert_any<K>(knn_key(p, x[j]), (int)(e[j] & 0xFFFFu), keys, ids);
-    }
-  }
+  if (!knn_group<K, SMEM>(xs, p, pc, h0, keys, ids) || !knn_group<K, SMEM>(xs, p, pc, h1, keys, ids)) return;
+  const uint32_t* list = W.cand + cell * W.cap;  // entries from kKnnHead on (cap is a multiple of 8)
+  for (int g = kKnnHead; g < W.cap; g += 4)
+    if (!knn_group<K, SMEM>(xs, p, pc, __ldg(reinterpret_cast<const uint4*>(list + g)), keys, ids)) return;
 }
 
 template <int K>
