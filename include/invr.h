@@ -346,7 +346,8 @@ invr_status invr_ctx_get_tune(invr_ctx ctx, int* out);
 /* Set the launch shapes directly (e.g. ones an earlier autotune returned): in[INVR_TUNE_N]
  * as for invr_ctx_get_tune.  CTAs per SM in [1, 32], aggregation resolution in [0, 2^20]
  * (0: no level sums runs), fused 0 or 1, work item 128 or 256.  INVR_E_ARG on a value out
- * of range; the context is then unchanged.  Views with a deformation net always run staged. */
+ * of range; the context is then unchanged.  Views with a deformation net always run staged.
+ * A new context starts at {4, 32, 8, 128, 1, 128}. */
 invr_status invr_ctx_set_tune(invr_ctx ctx, const int* in);
 /* Polls of each bounded device-side wait (the tensor-core kernels' mbarrier waits) before
  * the kernel gives up, records INVR_E_TIMEOUT in the status word, lets its in-flight work

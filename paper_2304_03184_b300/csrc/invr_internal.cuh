@@ -151,8 +151,8 @@ struct Tune {
   int encode_ctas_per_sm = 32;
   int encode_bwd_ctas_per_sm = 8;
   int agg_res = 128;
-  int fused = 0;            // warp + encoding in one kernel per field (k_warp_encode), else staged
-  int chunk = 256;          // samples per work item of the fused kernel (128 or 256)
+  int fused = 1;            // warp + encoding in one kernel per field (k_warp_encode), else staged
+  int chunk = 128;          // samples per work item of the fused kernel (128 or 256)
 };
 
 struct Plan {
