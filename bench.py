@@ -40,6 +40,12 @@ UNIT = "samples/s"
 KERNELS_PER_RECORD = {"scan": 3, "composite_train": 2, "march_count": 2}
 
 
+def launches_per_record(n_fields):
+    """Kernels per timed record for a step over n_fields fields: the encoding, fused forward
+    and scatter records launch once per field."""
+    return dict(KERNELS_PER_RECORD, encode=n_fields, warp_encode=n_fields, encode_bwd=n_fields)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,6 +175,8 @@ def kernel_work(name, R, S_occ, n_samples, L, n_params, n_w):
         return "hbm", n_params * 32       # read p,g,m,v; write p,g(=0),m,v
     if name == "encode":
         return "hbm", S_occ * (12 + L * (8 * 8 + 8))    # vc in, 8 corner gathers + 2 features out per level
+    if name == "warp_encode":
+        return "hbm", S_occ * (24 + L * (8 * 8 + 8))   # live position in, v_c out, the encoding's gathers and out
     if name == "encode_bwd":
         return "hbm", S_occ * (12 + L * (8 + 8 * 8))    # vc, dfeat in, 8 corner atomics per level
     if name == "march_count":
@@ -267,20 +275,22 @@ def l2_roofline(name, kms_per_launch, S_occ, L, l2):
     """The L2 view of a gather/scatter kernel: table payload per launch (8 corners x F=2
     floats per level and sample) over its duration, against the probe's ceiling for that
     access form."""
-    if l2 is None or name not in ("encode", "encode_bwd"):
+    if l2 is None or name not in ("encode", "warp_encode", "encode_bwd"):
         return None
     payload = S_occ * L * 8 * 2 * 4
     ach = payload / (kms_per_launch * 1e-3) / 1e9
-    peak = l2["gather_v4_gbs"] if name == "encode" else l2["atomic_v4_gbs"]
+    gather = name != "encode_bwd"
+    peak = l2["gather_v4_gbs"] if gather else l2["atomic_v4_gbs"]
     return {"achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
             "payload_bytes": payload,
-            "peak_source": "measured by probe: random float4 " + ("loads from" if name == "encode"
+            "peak_source": "measured by probe: random float4 " + ("loads from" if gather
                                                                   else "atomic adds into") + " a 64 MiB table"}
 
 
 # The encoding's gather and the gradient scatter keep the tables (64 MiB per field) in L2:
 # their bound is the L2, measured in the same run by the library's probe kernels.
 L2_BOUND = {"encode": ("gather_v4_gbs", "random float4 loads from"),
+            "warp_encode": ("gather_v4_gbs", "random float4 loads from"),
             "encode_bwd": ("atomic_v4_gbs", "random float4 atomic adds into")}
 
 
@@ -370,7 +380,7 @@ def kernel_rooflines(ktime, tw, R, S_occ, peaks, l2=None):
         bound, work = kernel_work(name, R, S_occ, tw.n_samples, fp.desc.L, n_params, fp.desc.n_weight_params())
         if bound is None:
             continue
-        if name in ("encode", "encode_bwd") and l2:
+        if name in ("encode", "warp_encode", "encode_bwd") and l2:
             r = l2_roofline(name, kms / kn, S_occ, fp.desc.L, l2)
             res[name] = {"bound": "l2", **{k: r[k] for k in ("achieved", "peak", "unit", "frac")},
                          "ms": round(kms / kn, 4)}
@@ -413,11 +423,11 @@ def apply_batched(out, bt, invr, ctx, args, world, peaks):
     out["l2_probe"] = l2
     out["roofline"] = roofline(bt["ktime"], btw, bR, bS, peaks, l2)
     out["l2_rooflines"] = {k: l2_roofline(k, bt["ktime"][k][0] / bt["ktime"][k][1], bS, btw.fields[0].desc.L, l2)
-                           for k in ("encode", "encode_bwd") if k in bt["ktime"]}
+                           for k in ("encode", "warp_encode", "encode_bwd") if k in bt["ktime"]}
     nsteps = max(5, args.steps // 4)
     out["kernels_ms_per_step"] = {k: round(v[0] / nsteps, 4) for k, v in sorted(bt["ktime"].items())}
     out["kernel_rooflines"] = kernel_rooflines(bt["ktime"], btw, bR, bS, peaks, l2)
-    per_rec = dict(KERNELS_PER_RECORD, encode=len(btw.fields), encode_bwd=len(btw.fields))
+    per_rec = launches_per_record(len(btw.fields))
     out["gpu_launches"] = int(round(sum(n * per_rec.get(k, 1) for k, (_, n) in bt["ktime"].items())
                                     / nsteps * args.steps))
     out["gpu_launches_per_step"] = round(out["gpu_launches"] / args.steps, 1)
@@ -483,7 +493,8 @@ def run_ours(args, rank, world, local):
     del tbp, fields_p, keep_p
     tb, fields, keep, ms, ktime = main
     value = world * S_nom / (ms * 1e-3)
-    launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktime.items())
+    per_rec = launches_per_record(len(tw.fields))
+    launches = sum(n * per_rec.get(k, 1) for k, (_, n) in ktime.items())
     roof = roofline(ktime, tw, R, S_occ, peaks)
 
     # end to end through the public API with host buffers: copy rays + targets in, loss out
@@ -702,13 +713,14 @@ def bench_lut(invr, args, flush, world, prec_name, G=512):
     base = synth.train_step_workload(n_rays=args.rays)
     b0 = base.batches[0]
     g_art = synth.articulated_pose(np.random.default_rng(9), b0.view.graph)
-    out = {"workload": base.name, "resolution": G, "prec": prec_name}
+    out = {"workload": base.name, "resolution": G, "prec": prec_name, "forward": "staged (warp timed alone)"}
     for motion, g in (("independent_nodes", b0.view.graph), ("articulated", g_art)):
         occ = b0.view.occupancy if g is b0.view.graph else synth.occupancy_near_nodes(g.x_live)
         view_s = synth.View(b0.view.field, graph=g, occupancy=occ)
         tw = synth.TrainWorkload(base.name, [synth.TrainBatch(b0.rays, view_s, b0.target)], base.fields,
                                  base.n_samples)
         ctx = invr.Context(torch.cuda.current_device())
+        ctx.set_tune(dict(ctx.tune(), fused=0))   # staged forward: the warp kernel timed on its own
         tb, fields, keep = build_train(invr, ctx, tw, PRECS[prec_name])
         graph, view = keep[0][0], keep[0][2]
         steps = max(5, args.steps // 4)

@@ -48,6 +48,7 @@ struct invr_field_s {
   float* v = nullptr;
   int64_t* step = nullptr;  // device step counter
   float* wt = nullptr;      // [kWtF32] the FP32 MLP's transposed weights (scratch of its forward)
+  uint8_t* w16 = nullptr;   // [kW16Bytes] the tensor-core MLPs' weight images (16-bit fields)
   int res[kMaxL] = {};
   uint32_t dense_mask = 0;
 };
@@ -285,6 +286,7 @@ DeformDev deform_dev(invr_ctx ctx, invr_deform d, const float* pose, int view) {
   D.enc.tables = d->params;
   D.enc.weights = nullptr;
   D.enc.wt_f32 = nullptr;
+  D.enc.w16 = nullptr;
   D.enc.grad_tables = d->grads;
   D.enc.grad_weights = nullptr;
   D.enc.L = q.L;
@@ -307,6 +309,7 @@ FieldDev field_dev(invr_field f) {
   F.tables = f->params;
   F.weights = f->params + f->n_tab;
   F.wt_f32 = f->wt;
+  F.w16 = f->w16;
   F.grad_tables = f->grads;
   F.grad_weights = f->grads + f->n_tab;
   F.L = f->desc.L;
@@ -471,9 +474,11 @@ cudaError_t run_forward(invr_ctx ctx, const Plan& P, cudaStream_t s) {
   }
   if (plan_has_kind(P, kMlpF32) && (e = TIMED(ctx, "mlp_fwd", s, launch_mlp_fwd_f32(P, ctx->num_sms, s))) != cudaSuccess)
     return e;
-  if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
+  if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16)) {
+    if ((e = TIMED(ctx, "prep_w16", s, launch_prep_w16_plan(P, s))) != cudaSuccess) return e;
     e = P.feat_split ? TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_split_tc(P, ctx->num_sms, s))
                      : TIMED(ctx, "mlp_fwd_tc", s, launch_mlp_fwd_tc(P, ctx->num_sms, s));
+  }
   return e;
 }
 
@@ -911,8 +916,8 @@ invr_status invr_field_create(invr_ctx ctx, const invr_field_desc* desc, invr_fi
   const int64_t n = f->n_tab + f->n_w;
   if (dmalloc(&f->params, n) != cudaSuccess || dmalloc(&f->grads, n) != cudaSuccess ||
       dmalloc(&f->m, n) != cudaSuccess || dmalloc(&f->v, n) != cudaSuccess || dmalloc(&f->step, 1) != cudaSuccess ||
-      dmalloc(&f->wt, kWtF32) != cudaSuccess) {
-    dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step); dfree(f->wt);
+      dmalloc(&f->wt, kWtF32) != cudaSuccess || dmalloc(&f->w16, kW16Bytes) != cudaSuccess) {
+    dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step); dfree(f->wt); dfree(f->w16);
     delete f;
     return fail(ctx, INVR_E_OOM, "field allocation failed");
   }
@@ -929,7 +934,7 @@ invr_status invr_field_destroy(invr_field f) {
   if (!f) return INVR_E_ARG;
   DeviceGuard guard(f->ctx->device);
   cudaDeviceSynchronize();
-  dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step); dfree(f->wt);
+  dfree(f->params); dfree(f->grads); dfree(f->m); dfree(f->v); dfree(f->step); dfree(f->wt); dfree(f->w16);
   delete f;
   return INVR_OK;
 }

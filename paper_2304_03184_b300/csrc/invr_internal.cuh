@@ -13,6 +13,9 @@ namespace invr {
 constexpr int kMaxViews = 16;   // batches per call (8 key frames x 2 fields)
 constexpr int kMaxL = 16;       // hash levels
 constexpr int kWtF32 = 9216;    // floats of the FP32 MLP's padded transposed weights
+// A 16-bit field's MLP weights as the render forward's and the backward's shared-memory image:
+// W1..W5 (padded) as 16-bit K-major operands.
+constexpr int kW16Bytes = 18432;
 constexpr int kF = 2;           // features per level
 constexpr int kMaxIn = kMaxL * kF;
 constexpr int kHidden = 64;
@@ -53,6 +56,8 @@ struct FieldDev {
   const float* weights;     // W1..W5 FP32, row-major [out][in]
   float* wt_f32;            // [9216]: the FP32 MLP's padded weights, transposed per layer (written
                             // by each FP32 forward launch from `weights`), or null
+  uint8_t* w16;             // [kW16Bytes]: a 16-bit field's weight image (written from `weights` before
+                            // each tensor-core forward), or null
   float* grad_tables;       // [L][T][F]
   float* grad_weights;      // W1..W5
   int L, log2T, mlp_in, mlp_kind;
@@ -347,6 +352,8 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s);
 // training forward of the 16-bit fields: split products, ReLU decisions to ws.mlp_mask
 cudaError_t launch_mlp_fwd_split_tc(const Plan& P, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s);
+// Rewrite the weight images (FieldDev::w16) of every 16-bit field of the plan.
+cudaError_t launch_prep_w16_plan(const Plan& P, cudaStream_t s);
 cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat, float* out, unsigned* status,
                                  uint32_t wait_limit, int num_sms, cudaStream_t s);
 constexpr uint32_t kDefaultWaitLimit = 1u << 22;  // polls of try_wait: a few seconds

@@ -16,8 +16,9 @@
 // operand row in the K-major layout.  The encoder writes the features as 16-bit operand
 // tiles, so a tile's X arrives by one TMA copy (a 3-D box of its 16 row groups); the copy of
 // the CTA's next tile is issued as soon as layer 3 has read P, and land while layers 4 and 5
-// run.  Weights (padded: W4p gets a zero column for o_0, W5p 13 zero rows) are converted
-// to 16 bit and staged in shared memory once per field.  50 KB of shared memory and 64
+// run.  Weights (padded: W4p gets a zero column for o_0, W5p 13 zero rows) arrive as the
+// field's 16-bit weight image (written from the FP32 weights by k_prep_w16 before each
+// launch) by one bulk copy per CTA and field.  50 KB of shared memory and 64
 // tensor-memory columns per CTA: four CTAs per SM overlap their chains.  Every mbarrier
 // wait is bounded; a timeout sets the status word, and the CTA waits (bounded) for its
 // own copies and MMAs in flight, frees its tensor memory and exits.
@@ -97,17 +98,31 @@ __device__ __forceinline__ void stage_weight(uint8_t* dst, const float* __restri
   }
 }
 
-template <bool BF16>
-__device__ void stage_weights(uint8_t* sm, const FieldDev& F) {
-  const WOff off(F.mlp_in);
-  if (F.mlp_in == 16)
-    stage_weight<BF16, 64, 16>(sm + OFF_W1, F.weights, 1, 16, off);
-  else
-    stage_weight<BF16, 64, 32>(sm + OFF_W1, F.weights, 1, 32, off);
-  stage_weight<BF16, 64, 64>(sm + OFF_W2, F.weights, 2, F.mlp_in, off);
-  stage_weight<BF16, 16, 64>(sm + OFF_W3, F.weights, 3, F.mlp_in, off);
-  stage_weight<BF16, 64, 16>(sm + OFF_W4, F.weights, 4, F.mlp_in, off);
-  stage_weight<BF16, 16, 64>(sm + OFF_W5, F.weights, 5, F.mlp_in, off);
+// All threads of the CTA: the field's weight image (`bytes` from global `src`) into shared
+// memory at `dst` by one bulk copy, its completion awaited on mbarrier `bar` (bounded);
+// every MMA that read the previous weights has completed.  The barrier's phase lives in
+// shared memory (`phase`, flipped by thread 0), not in a register of the tile loop.  On a
+// time-out the copy is drained (bounded) before returning false, so no write of it can land
+// after the CTA leaves.
+__device__ __forceinline__ bool load_weights(uint32_t dst, const uint8_t* src, int bytes, uint32_t bar,
+                                             uint32_t& phase, uint32_t wait_limit, unsigned* status) {
+  __syncthreads();
+  const uint32_t ph = phase;
+  if (threadIdx.x == 0) {
+    tc::mbar_expect_tx(bar, (uint32_t)bytes);
+    tc::bulk_g2s(dst, src, (uint32_t)bytes, bar);
+  }
+  const bool got = tc::mbar_wait(bar, ph, wait_limit);
+  if (!__syncthreads_and(got)) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, kStatusTimeout);
+      if (!tc::mbar_wait(bar, ph, kWaitLimit)) atomicOr(status, kStatusDrainTimeout);
+    }
+    __syncthreads();
+    return false;
+  }
+  if (threadIdx.x == 0) phase = ph ^ 1u;  // read by all threads at the next call, after its barrier
+  return true;
 }
 
 // One thread: issue D(tmem) = A(smem, 128 x K) * B(smem, N x K)^T as K/16 MMAs.
@@ -171,17 +186,21 @@ template <bool BF16, bool TILES>
 __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __grid_constant__ TcArgs A) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ int32_t vb[kMaxViews + 1];  // view sample bases
+  __shared__ uint32_t s_wphase;          // phase of the weight-image barrier
   if (A.view_base && (int64_t)A.view_base[A.n_views] > A.ld) return;  // overflow flagged by the scan
   const int t = threadIdx.x, warp = t >> 5;
   if (t <= A.n_views) vb[t] = A.view_base ? A.view_base[t] : 0;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
-  const uint32_t mbar = tc::smem_u32(sm + OFF_MISC);      // MMA completion
-  const uint32_t xbar = tc::smem_u32(sm + OFF_MISC + 8);  // X copies landed
+  const uint32_t mbar = tc::smem_u32(sm + OFF_MISC);       // MMA completion
+  const uint32_t xbar = tc::smem_u32(sm + OFF_MISC + 8);   // X copies landed
+  const uint32_t wbar = tc::smem_u32(sm + OFF_MISC + 24);  // weight image landed
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
   if (t == 0) {
     tc::mbar_init(mbar, 1);
     tc::mbar_init(xbar, 1);
+    tc::mbar_init(wbar, 1);
+    s_wphase = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -207,8 +226,12 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
     const FieldDev& F = A.f[vn];
     const int64_t nxt = next_tile(A, vb, tile + gridDim.x, n_tiles, kind, vn);
     if (F.weights != loaded) {
-      __syncthreads();
-      stage_weights<BF16>(sm, F);
+      // the field's weight image by one bulk copy (every MMA that read the previous field's
+      // weights has completed: the last tile waited for them)
+      if (!load_weights(sbase + OFF_W1, F.w16, kW16Bytes, wbar, s_wphase, A.wait_limit, A.status)) {
+        ok = false;
+        break;
+      }
       loaded = F.weights;
     }
     const int in = F.mlp_in;
@@ -228,7 +251,7 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasPerSm) k_mlp_fwd_tc(const __g
         *reinterpret_cast<uint4*>(sm + OFF_P + tc::kmajor_offset(t, 8 * j, in)) = q;
       }
     }
-    operands_ready();  // staged weights (and converted X) visible to the tensor core
+    operands_ready();  // converted X (points path) visible to the tensor core
     if constexpr (TILES) {
       ok = tc::mbar_wait(xbar, xphase, A.wait_limit);
       if (!__syncthreads_and(ok)) { ok = false; break; }
@@ -375,7 +398,8 @@ cudaError_t launch_tc(const TcArgs& A, int num_sms, cudaStream_t s) {
 // memory: each epilogue writes its row's hi and lo halves into tensor memory, from which the
 // next layer's MMAs read their A operand.  Per CTA 128 tensor-memory columns (accumulator
 // [0,64), activations hi [64,96), lo [96,128)) and 49 KB of shared memory (W1..W4 hi and lo,
-// W5 in FP32, one tile of X hi and lo): four CTAs per SM.  X hi/lo arrive by two TMA boxes;
+// W5 in FP32, one tile of X hi and lo): four CTAs per SM.  The CTA converts the weights itself
+// (a bulk copy of a prepared split image measured 5.6% slower).  X hi/lo arrive by two TMA boxes;
 // the next tile's are issued once layer 1 has read this tile's.
 constexpr int kCtasSplit = 4;
 constexpr uint32_t kTmemSplit = 128;
@@ -737,7 +761,70 @@ __global__ void __launch_bounds__(kThreadsTC, kCtasSplit) k_mlp_fwd_split_tc(con
   }
 }
 
+// ====================================================================== weight images
+// A 16-bit field's MLP weights as the shared-memory image the render forward above and the
+// backward copy in with one bulk copy per CTA: the padded W1..W5 as 16-bit K-major operands
+// (the layout of OFF_W1..OFF_W5 here and of the backward's weights).  Rewritten from the FP32
+// weights before each forward (the optimiser changes them every step; the backward reads the
+// image its training forward wrote, with the same weights): one launch for every 16-bit field
+// of the call, one block per matrix and field.
+static_assert(OFF_P == (uint32_t)kW16Bytes, "weight image = OFF_W1..OFF_W5");
+
+struct PrepArgs {
+  int n;
+  FieldDev f[kMaxViews];
+};
+
+template <bool BF16>
+__device__ __forceinline__ void prep_w16(const FieldDev& F) {
+  const WOff off(F.mlp_in);
+  uint8_t* plain = F.w16;
+  switch (blockIdx.x) {
+    case 0:
+      if (F.mlp_in == 16) stage_weight<BF16, 64, 16>(plain + OFF_W1, F.weights, 1, 16, off);
+      else stage_weight<BF16, 64, 32>(plain + OFF_W1, F.weights, 1, 32, off);
+      break;
+    case 1: stage_weight<BF16, 64, 64>(plain + OFF_W2, F.weights, 2, F.mlp_in, off); break;
+    case 2: stage_weight<BF16, 16, 64>(plain + OFF_W3, F.weights, 3, F.mlp_in, off); break;
+    case 3: stage_weight<BF16, 64, 16>(plain + OFF_W4, F.weights, 4, F.mlp_in, off); break;
+    default: stage_weight<BF16, 16, 64>(plain + OFF_W5, F.weights, 5, F.mlp_in, off); break;
+  }
+}
+
+constexpr int kPrepBlocks = 5;
+
+// blockIdx.x: the matrix, blockIdx.y: the field.
+__global__ void __launch_bounds__(256) k_prep_w16(const __grid_constant__ PrepArgs A) {
+  const FieldDev& F = A.f[blockIdx.y];
+  if (F.mlp_kind == kMlpBF16) prep_w16<true>(F);
+  else prep_w16<false>(F);
+}
+
+cudaError_t launch_prep_w16(const PrepArgs& A, cudaStream_t s) {
+  if (A.n > 0) k_prep_w16<<<dim3(kPrepBlocks, A.n), 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_w16(const FieldDev& f, cudaStream_t s) {
+  PrepArgs A{};
+  A.n = f.mlp_kind == kMlpF32 ? 0 : 1;
+  A.f[0] = f;
+  return launch_prep_w16(A, s);
+}
+
 }  // namespace
+
+// Every 16-bit field of the plan (once each), in one launch.
+cudaError_t launch_prep_w16_plan(const Plan& P, cudaStream_t s) {
+  PrepArgs A{};
+  for (int v = 0; v < P.n_views; ++v) {
+    const FieldDev& F = P.v[v].field;
+    bool seen = false;
+    for (int u = 0; u < v; ++u) seen = seen || P.v[u].field.weights == F.weights;
+    if (!seen && F.mlp_kind != kMlpF32) A.f[A.n++] = F;
+  }
+  return launch_prep_w16(A, s);
+}
 
 bool encode_feat16_map(void* map, const void* feat, int64_t S_cap, int in) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -782,7 +869,7 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   if (!encode_feat16_map(&A.xmap[0], P.ws.feat, P.ws.S_cap, 16) ||
       !encode_feat16_map(&A.xmap[1], P.ws.feat, P.ws.S_cap, 32))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaSuccess;  // the weight images: launch_prep_w16_plan, before this launch
   if (plan_has_kind(P, kMlpBF16)) e = launch_tc<true, true>(A, num_sms, s);
   if (e == cudaSuccess && plan_has_kind(P, kMlpF16)) e = launch_tc<false, true>(A, num_sms, s);
   return e;
@@ -791,10 +878,11 @@ cudaError_t launch_mlp_fwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
 cudaError_t preload_mlp_points_tc() {
   cudaError_t e =
       cudaFuncSetAttribute(k_mlp_fwd_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
-  return e != cudaSuccess
-             ? e
-             : cudaFuncSetAttribute(k_mlp_fwd_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kSmemTC);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_fwd_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC);
+  cudaFuncAttributes a;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_prep_w16);
+  return e;
 }
 
 cudaError_t launch_mlp_fwd_split_tc(const Plan& P, int num_sms, cudaStream_t s) {
@@ -813,7 +901,7 @@ cudaError_t launch_mlp_fwd_split_tc(const Plan& P, int num_sms, cudaStream_t s) 
       if (!encode_feat16_map(&A.xmap[w][h], feat + (h ? feat16_lo_offset(P.ws.S_cap) : 0), P.ws.S_cap,
                              w ? 32 : 16))
         return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaSuccess;  // the weight images: launch_prep_w16_plan, before this launch
   if (plan_has_kind(P, kMlpBF16)) {
     A.ticket = P.ws.tickets + kTicketSplitFwd;
     e = cudaMemsetAsync(A.ticket, 0, sizeof(uint32_t), s);
@@ -843,6 +931,8 @@ cudaError_t launch_mlp_points_tc(const FieldDev& f, int64_t n, const float* feat
   A.status = status;
   A.f[0] = f;
   if (n <= 0) return cudaSuccess;
+  const cudaError_t e = launch_prep_w16(f, s);
+  if (e != cudaSuccess) return e;
   return f.mlp_kind == kMlpBF16 ? launch_tc<true, false>(A, num_sms, s) : launch_tc<false, false>(A, num_sms, s);
 }
 

@@ -78,6 +78,7 @@ constexpr uint32_t B_DO = B_DZ;
 constexpr uint32_t B_DH2 = B_H4;
 constexpr uint32_t B_DH1 = B_H2;
 constexpr uint32_t kSmemB = B_MISC + 64;         // 106 KB: two CTAs per SM
+static_assert(B_X == (uint32_t)kW16Bytes, "W1..W5 = the field's weight image");
 static_assert(2 * (kSmemB + 1024) <= 228 * 1024, "two CTAs per SM");
 
 struct TcBwdArgs {
@@ -108,21 +109,6 @@ __device__ __forceinline__ void issue_dw(uint32_t d_tmem, uint32_t a_saddr, int 
     const uint64_t bd = tc::smem_desc(b_saddr + kk * 32 * b_units, b_units * 16, 128);
     tc::mma_f16(d_tmem, ad, bd, idesc, (accumulate || kk > 0) ? 1u : 0u);
   }
-}
-
-// Epilogue threads stage the five padded weight matrices (16-bit, K-major).
-template <bool BF16>
-__device__ void stage_bwd_weights(uint8_t* sm, const FieldDev& F, int t) {
-  const WOff off(F.mlp_in);
-  const int in = F.mlp_in;
-  if (in == 16)
-    stage<BF16, false, 64, 16>(sm + B_W1, F.weights, off, in, 1, t, kEpi);
-  else
-    stage<BF16, false, 64, 32>(sm + B_W1, F.weights, off, in, 1, t, kEpi);
-  stage<BF16, false, 64, 64>(sm + B_W2, F.weights, off, in, 2, t, kEpi);
-  stage<BF16, false, 16, 64>(sm + B_W3, F.weights, off, in, 3, t, kEpi);
-  stage<BF16, false, 64, 16>(sm + B_W4, F.weights, off, in, 4, t, kEpi);
-  stage<BF16, false, 16, 64>(sm + B_W5, F.weights, off, in, 5, t, kEpi);
 }
 
 // One thread: adjoint-chain MMA D (128 x N) = dY * W, with W the forward weight [K rows][N
@@ -227,6 +213,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
   const uint32_t x_bar = tc::smem_u32(sm + B_MISC + 16);     // X copies landed
   const uint32_t flush_bar = tc::smem_u32(sm + B_MISC + 24); // every MMA retired: dW may be read
   const uint32_t drain_bar = tc::smem_u32(sm + B_MISC + 32); // every MMA retired (exit)
+  const uint32_t w_bar = tc::smem_u32(sm + B_MISC + 48);     // weight image landed
   const uint32_t sb = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemColsB);
   if (t == 0) {
@@ -235,6 +222,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
     tc::mbar_init(x_bar, 1);
     tc::mbar_init(flush_bar, 1);
     tc::mbar_init(drain_bar, 1);
+    tc::mbar_init(w_bar, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -347,8 +335,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
   } else {
     // ================================================================ epilogue warps
     const uint32_t row_t = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t acc_ph = 0, fl_ph = 0;
-    bool dw_live = false;
+    uint32_t acc_ph = 0, fl_ph = 0, w_ph = 0;
+    bool dw_live = false, w_pending = false;
     int cur = -1;
     int64_t tile = first;
     int vn = v_first;  // view of the next tile to process
@@ -373,7 +361,15 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
           flush_dw(tmem, A.f[cur], A.out_scale);
           dw_live = false;
         }
-        stage_bwd_weights<BF16>(sm, F, t);  // every MMA has retired (or none was issued)
+        // the field's weight image by one bulk copy (every MMA has retired, or none was issued)
+        if (t == 0) {
+          tc::mbar_expect_tx(w_bar, (uint32_t)kW16Bytes);
+          tc::bulk_g2s(sb + B_W1, F.w16, (uint32_t)kW16Bytes, w_bar);
+        }
+        w_pending = true;
+        if (!(ok = tc::mbar_wait(w_bar, w_ph, A.wait_limit))) break;
+        w_ph ^= 1u;
+        w_pending = false;
         cur = v;
       }
       const int in = F.mlp_in;
@@ -463,6 +459,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
       if (ok) flush_dw(tmem, A.f[cur], A.out_scale);
     }
     if (!ok) atomicOr(A.status, kStatusTimeout);
+    // a weight copy still in flight must land before the shared memory is released
+    if (w_pending && !tc::mbar_wait(w_bar, w_ph, kWaitLimit)) atomicOr(A.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -493,7 +491,7 @@ cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   if (!encode_feat16_map(&A.xmap[0], P.ws.feat, P.ws.S_cap, 16) ||
       !encode_feat16_map(&A.xmap[1], P.ws.feat, P.ws.S_cap, 32))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaSuccess;  // the weight images its training forward wrote (same weights)
   if (plan_has_kind(P, kMlpBF16)) {
     cudaFuncSetAttribute(k_mlp_bwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB);
     k_mlp_bwd_tc<true><<<num_sms * 2, kThreadsB, kSmemB, s>>>(A);

@@ -22,6 +22,7 @@
 //
 // Bound: FP32 ALU and issue (about 10 operations per candidate key, the blend's ~150 per
 // sample) plus node reads from shared memory.
+#include "tc_ptx.cuh"
 #include "warp.cuh"
 
 namespace invr {
@@ -29,17 +30,24 @@ namespace invr {
 // Work items are chunks of kWarpChunk consecutive sample slots, taken from a per-launch counter
 // by the CTAs resident on the SMs.  Within a chunk, the samples of each view in turn; a human
 // view searched without look-up tables reads its nodes' live positions from a copy in shared
-// memory (staged when the CTA's view changes), when it has at most smem_nodes nodes.
+// memory (one bulk copy of the packed float4 records when the CTA's view changes), when it
+// has at most smem_nodes nodes.  The copy's wait is bounded: on a time-out the CTA flags the
+// status word, waits (bounded) for the copy to land and returns.
 constexpr int kWarpChunk = 4096;
+constexpr uint32_t kWarpDrainLimit = 1u << 22;
 
 template <int KMAX>
 __global__ void __launch_bounds__(256, KMAX <= 4 ? 4 : 1) k_warp(const __grid_constant__ Plan P, int smem_nodes) {
-  extern __shared__ float4 s_nodes[];
+  extern __shared__ __align__(16) float4 s_nodes[];
   __shared__ int32_t vb[kMaxViews + 1];
   __shared__ int64_t s_item;
+  __shared__ __align__(8) uint64_t s_nbar;  // node copy landed
   const int64_t S_cap = P.ws.S_cap;
   if (P.ws.view_base[P.n_views] > S_cap) return;
   if (threadIdx.x <= P.n_views) vb[threadIdx.x] = P.ws.view_base[threadIdx.x];
+  const uint32_t nbar = tc::smem_u32(&s_nbar);
+  if (threadIdx.x == 0) tc::mbar_init(nbar, 1);
+  uint32_t nphase = 0;
   const int64_t S = P.ws.view_base[P.n_views];
   const int64_t n_items = (S + kWarpChunk - 1) / kWarpChunk;
   int staged = -1;
@@ -56,9 +64,23 @@ __global__ void __launch_bounds__(256, KMAX <= 4 ? 4 : 1) k_warp(const __grid_co
       const WarpDev& W = P.v[v].warp;
       const bool in_smem = W.mode == 1 && !W.lut_live && W.n_nodes <= smem_nodes;
       if (in_smem && staged != v) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < W.n_nodes; i += blockDim.x) s_nodes[i] = __ldg(W.x_live + i);
-        __syncthreads();
+        __syncthreads();  // the block's reads of the previous copy are done
+        const uint32_t bytes = (uint32_t)W.n_nodes * (uint32_t)sizeof(float4);  // 16-byte records
+        if (threadIdx.x == 0) {
+          tc::fence_smem_to_async();
+          tc::mbar_expect_tx(nbar, bytes);
+          tc::bulk_g2s(tc::smem_u32(s_nodes), W.x_live, bytes, nbar);
+        }
+        const bool got = tc::mbar_wait(nbar, nphase, P.wait_limit);
+        if (!__syncthreads_and(got)) {
+          if (threadIdx.x == 0) {
+            flag_status(P.status, kStatusTimeout);
+            if (!tc::mbar_wait(nbar, nphase, kWarpDrainLimit)) flag_status(P.status, kStatusDrainTimeout);
+          }
+          __syncthreads();
+          return;
+        }
+        nphase ^= 1u;
         staged = v;
       }
       for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {

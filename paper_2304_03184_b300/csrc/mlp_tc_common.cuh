@@ -1,6 +1,5 @@
 // Pieces shared by the tensor-core MLP kernels (forward and backward): the weight layout
-// of W1..W5, staging of (padded, optionally transposed) weights as 16-bit K-major
-// operands, MMA chains over K, and the ReLU epilogue from tensor memory.
+// of W1..W5, MMA chains over K, and the ReLU epilogue from tensor memory.
 #pragma once
 
 #include "invr_internal.cuh"
@@ -23,34 +22,6 @@ struct WOff {
     w5 = w4 + kColHidden * (kGeoOut - 1);
   }
 };
-
-// Element [o][k] of padded layer `layer` (1..5): W4p has a zero column 0 (o_0 does not feed
-// the colour MLP), W5p has zero rows 3..15.
-__device__ __forceinline__ float padded_weight(const float* __restrict__ W, const WOff& off, int in, int layer,
-                                               int o, int k) {
-  switch (layer) {
-    case 1: return W[off.w1 + o * in + k];
-    case 2: return W[off.w2 + o * kHidden + k];
-    case 3: return W[off.w3 + o * kHidden + k];
-    case 4: return k == 0 ? 0.0f : W[off.w4 + o * (kGeoOut - 1) + k - 1];
-    default: return o < 3 ? W[off.w5 + o * kColHidden + k] : 0.0f;
-  }
-}
-
-// Stage padded layer `layer` ([OUT][IN]) as a 16-bit K-major operand with N rows and K
-// columns: the matrix itself (N = OUT, K = IN) or, if TRANS, its transpose (N = IN, K = OUT).
-// Threads tid = 0..nthr-1 share the work.
-template <bool BF16, bool TRANS, int N, int K>
-__device__ __forceinline__ void stage(uint8_t* dst, const float* __restrict__ W, const WOff& off, int in,
-                                      int layer, int tid, int nthr) {
-  for (int e = tid; e < N * K / 2; e += nthr) {
-    const int n = (2 * e) / K, k = (2 * e) % K;
-    const float a = TRANS ? padded_weight(W, off, in, layer, k, n) : padded_weight(W, off, in, layer, n, k);
-    const float b =
-        TRANS ? padded_weight(W, off, in, layer, k + 1, n) : padded_weight(W, off, in, layer, n, k + 1);
-    *reinterpret_cast<uint32_t*>(dst + tc::kmajor_offset(n, k, K)) = tc::pack2<BF16>(a, b);
-  }
-}
 
 // One thread: D(tmem) = A(tmem, 128 x K: 8 columns per K step of 16) * B(smem, N x K, K-major)^T.
 __device__ __forceinline__ void issue_chain_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_saddr, int K, int N,

@@ -217,11 +217,14 @@ def test_keyframe_batch_matches_oracle_loss(env):
     assert abs(loss - oloss) <= 1e-5 * oloss
 
 
-def test_device_wait_timeout_reported_and_recovered(env):
+@pytest.mark.parametrize("fused", [1, 0])
+def test_device_wait_timeout_reported_and_recovered(env, fused):
     """Bounded waits giving up (wait limit 0) are reported as INVR_E_TIMEOUT by the next
-    sync, with no fault; afterwards the same context renders and trains correctly."""
+    sync, with no fault; afterwards the same context renders and trains correctly.  With the
+    staged forward (fused = 0) the warp kernel's bulk copy of the node records waits too."""
     invr, oracle = env
     ctx = invr.Context(0)
+    ctx.set_tune(dict(ctx.tune(), fused=fused))
     w = synth.plain_forward(res=16, n_samples=32)
     sv = w.views[0]
     f = invr.Field.from_synth(ctx, sv.field, invr.INVR_MLP_BF16)

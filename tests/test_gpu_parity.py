@@ -143,6 +143,33 @@ def test_nearest_nodes_exact_ties(env):
     np.testing.assert_array_equal(host(ids), oids)
 
 
+def test_nearest_nodes_overflowing_and_long_lists(env):
+    """Candidate lists beyond their head and beyond their capacity.  300 nodes packed into a
+    ball of radius ~0.01: the lists of the cells around it would hold all 300 (more than the
+    64-entry capacity), so points there scan every node.  24 nodes on a circle of radius 0.03
+    about a point: equal distances from its centre, so a scan there cannot stop within the
+    first 8 entries and reads on into the cell's row.  Ids bit-exact against the oracle's scan
+    of all nodes."""
+    invr, ctx, oracle = env
+    rng = np.random.default_rng(34)
+    g = synth.make_graph(rng, 2048, K=4)
+    c0 = np.array([0.3, 0.1, -0.2])
+    g.x_live[:, :300] = (c0[:, None] + np.clip(rng.normal(scale=0.004, size=(3, 300)), -0.01, 0.01)).astype(np.float32)
+    c1 = np.array([-0.25, -0.4, 0.1])
+    a = 2.0 * np.pi * np.arange(24) / 24.0
+    ring = c1[:, None] + 0.03 * np.stack([np.cos(a), np.sin(a), np.zeros(24)])
+    g.x_live[:, 300:324] = ring.astype(np.float32)
+    sv = synth.View(synth.make_field(rng, synth.CFG1_FIELD), graph=g)
+    side = Side(invr, ctx, oracle, sv)
+    p = np.concatenate([c0[:, None] + rng.normal(scale=0.03, size=(3, 1500)),
+                        c1[:, None] + rng.normal(scale=0.01, size=(3, 1500)),
+                        c1[:, None] + np.array([[0.0, 1e-4, 0.0], [0.0, 0.0, 1e-4], [0.0, 0.0, 0.0]]),
+                        _probe_points(rng, g, 1000)], axis=1).astype(np.float32)
+    _, ids = invr.warp_points(ctx, side.view, cu(p), with_ids=True)
+    oids, _ = oracle.knn_points(side.oview.graph, p)
+    np.testing.assert_array_equal(host(ids), oids)
+
+
 def test_rigid_warp(env):
     invr, ctx, oracle = env
     rng = np.random.default_rng(32)
