@@ -32,6 +32,9 @@ struct invr_ctx_s {
     cudaEvent_t a, b;
   };
   std::vector<Rec> recs;
+  // side stream of the backward: one field's gradient scatter beside the other's MLP backward
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // state kept between invr_field_forward_train and invr_field_backward
   bool fwd_valid = false;
   Plan fwd_plan{};
@@ -593,6 +596,7 @@ invr_status train_forward(invr_ctx ctx, const invr_train_args* a, cudaStream_t s
     P.deform_store = 1;
   }
   P.feat_split = 1;  // 16-bit fields train on split products (values plus rounding remainders)
+  P.march_coop = 1;  // training batches draw their rays in random order
   P.ws = ctx->ws;
   INVR_CUDA(ctx, run_forward(ctx, P, s));
   INVR_CUDA(ctx, TIMED(ctx, "composite_train", s, launch_composite_train(P, a->loss_dev, s)));
@@ -607,6 +611,34 @@ invr_status train_backward(invr_ctx ctx, const invr_train_args* a, float scale, 
     return fail(ctx, INVR_E_STATE, "invr_field_backward needs the matching invr_field_forward_train first");
   Plan P = ctx->fwd_plan;
   P.grad_scale = scale;
+  // Two fields, both on the tensor cores, no deformation net, no per-kernel timing: the MLP
+  // backward of the field with fewer rays runs first, and that field's gradient scatter then
+  // runs on the context's side stream beside the other field's MLP backward (the scatter is
+  // bound by the L2's atomics, the MLP backward by its MMA chain; a scatter CTA fits beside
+  // two MLP CTAs on an SM); the side stream is joined before returning.
+  int split = 1;
+  while (split < P.n_views && P.v[split].field.tables == P.v[0].field.tables) ++split;
+  bool two = split < P.n_views;
+  for (int v = split + 1; v < P.n_views; ++v) two = two && P.v[v].field.tables == P.v[split].field.tables;
+  if (two && !ctx->timing && !P.has_deform && !plan_has_kind(P, kMlpF32)) {
+    int64_t r0 = 0, r1 = 0;
+    for (int v = 0; v < P.n_views; ++v) (v < split ? r0 : r1) += P.v[v].n_rays;
+    Plan A = P, B = P;  // A: the side field
+    A.view_lo = r0 <= r1 ? 0 : split;
+    A.view_hi = r0 <= r1 ? split : P.n_views;
+    B.view_lo = r0 <= r1 ? split : 0;
+    B.view_hi = r0 <= r1 ? P.n_views : split;
+    INVR_CUDA(ctx, launch_mlp_bwd_tc(A, ctx->num_sms, s));
+    INVR_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+    INVR_CUDA(ctx, launch_mlp_bwd_tc(B, ctx->num_sms, s));
+    A.grad_scale = B.grad_scale = 1.0f;  // dL/dfeat already carries the scale
+    INVR_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    INVR_CUDA(ctx, launch_encode_bwd(A, ctx->num_sms, ctx->side));
+    INVR_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    INVR_CUDA(ctx, launch_encode_bwd(B, ctx->num_sms, s));
+    INVR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    return INVR_OK;
+  }
   if (plan_has_kind(P, kMlpF32)) INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd", s, launch_mlp_bwd_f32(P, ctx->num_sms, s)));
   if (plan_has_kind(P, kMlpF16) || plan_has_kind(P, kMlpBF16))
     INVR_CUDA(ctx, TIMED(ctx, "mlp_bwd_tc", s, launch_mlp_bwd_tc(P, ctx->num_sms, s)));
@@ -681,7 +713,12 @@ invr_status invr_ctx_create(invr_ctx* out, int device) {
     return INVR_E_OOM;
   }
   // the no-allocation query's scratch array and kernels are loaded here, where allocating is allowed
-  if (noalloc_prepare(device) != cudaSuccess) {
+  if (noalloc_prepare(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     dfree(ctx->status);
     dfree(ctx->pose_bias);
     delete ctx;
@@ -697,6 +734,9 @@ invr_status invr_ctx_destroy(invr_ctx ctx) {
   cudaDeviceSynchronize();
   clear_timing(ctx);
   free_workspace(ctx->ws);
+  cudaEventDestroy(ctx->ev_fork);
+  cudaEventDestroy(ctx->ev_join);
+  cudaStreamDestroy(ctx->side);
   dfree(ctx->status);
   dfree(ctx->pose_bias);
   delete ctx;

@@ -176,6 +176,7 @@ struct Plan {
   int has_deform;           // some view has a deformation net
   int deform_store;         // training: the tensor-core forward keeps its operand tiles
   int feat_split;           // training: 16-bit fields' features also as remainder tiles
+  int march_coop;           // training: the march count tests a warp's rays in turn (rays in random order)
   uint32_t wait_limit;      // polls per bounded device wait
   Tune tune;                // launch shapes (autotuned per context)
   Workspace ws;

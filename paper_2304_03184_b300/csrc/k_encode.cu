@@ -207,10 +207,10 @@ cudaError_t launch_encode_bwd(const Plan& P, int num_sms, cudaStream_t s) {
 template <class Launch>
 cudaError_t per_field(const Plan& P, Launch launch) {
   Plan Q = P;
-  int lo = 0;
-  while (lo < P.n_views) {
+  int lo = P.view_lo;
+  while (lo < P.view_hi) {
     int hi = lo + 1;
-    while (hi < P.n_views && P.v[hi].field.tables == P.v[lo].field.tables) ++hi;
+    while (hi < P.view_hi && P.v[hi].field.tables == P.v[lo].field.tables) ++hi;
     Q.view_lo = lo;
     Q.view_hi = hi;
     const cudaError_t e = launch(Q);

@@ -89,6 +89,7 @@ struct TcBwdArgs {
   const int32_t* s_ray;     // padding marker (< 0) or null
   const uint32_t* mask;     // [6][ld] ReLU decisions of H1, H2, H4 from the training forward
   const int32_t* view_base;
+  int view_lo, view_hi;     // the views whose tiles this launch takes (ranges are whole tiles)
   int64_t ld;
   int n_views;
   float in_scale;           // applied to dL/d(outputs) before rounding to 16 bit
@@ -229,10 +230,11 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const int kind = BF16 ? kMlpBF16 : kMlpF16;
-  const int64_t S = (int64_t)A.view_base[A.n_views];
+  const int64_t S = (int64_t)vb[A.view_hi];
   const int64_t n_tiles = (S + kTM - 1) / kTM;
-  int v_first = 0;
-  const int64_t first = next_tile(A, vb, blockIdx.x, n_tiles, kind, v_first);
+  const int64_t t_lo = (int64_t)vb[A.view_lo] / kTM;  // view ranges start on a tile boundary
+  int v_first = A.view_lo;
+  const int64_t first = next_tile(A, vb, t_lo + blockIdx.x, n_tiles, kind, v_first);
   bool ok = true;
 
   if (warp == 4) {
@@ -472,8 +474,11 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_mlp_bwd_tc(const __grid_consta
 
 }  // namespace
 
+// The tiles of views [P.view_lo, P.view_hi).
 cudaError_t launch_mlp_bwd_tc(const Plan& P, int num_sms, cudaStream_t s) {
   TcBwdArgs A{};
+  A.view_lo = P.view_lo;
+  A.view_hi = P.view_hi;
   A.feat = P.ws.feat;
   A.dout = P.ws.dout;
   A.dfeat = P.ws.dfeat;
