@@ -330,3 +330,45 @@ def test_graph_replay_with_deformation_net_tables_and_paper_loss(env):
     # turns such jumps into steps of size lr (measured: 1e-5 after one step, ~1e-3 after two)
     np.testing.assert_allclose(replay[1], eager[3], rtol=1e-2)
     assert eager[3] < eager[0]
+
+
+@pytest.mark.parametrize("case", ["human_fewer_rays", "object_empty"])
+def test_two_field_backward_side_stream(env, case):
+    """In a two-field BF16 call the field with fewer rays has its MLP backward first and its
+    gradient scatter on the context's side stream, beside the other field's MLP backward.
+    Both orders of the fields are covered (the human field with fewer rays: the side field is
+    the plan's first), and a side field without a single occupied sample (its scatter and MLP
+    backward get no work).  Loss and both fields' gradients against the oracle."""
+    import dataclasses
+    invr, oracle = env
+    tw = synth.keyframe_batch_workload(n_frames=2, log2_rays=(9.0, 10.0))
+    batches = []
+    for b in tw.batches:
+        human = b.view.graph is not None
+        if case == "human_fewer_rays" and human:
+            keep = np.arange(min(b.rays.n, 200))
+            b = synth.TrainBatch(synth.subset_rays(b.rays, keep), b.view, np.ascontiguousarray(b.target[:, keep]))
+        if case == "object_empty" and not human:
+            keep = np.arange(min(b.rays.n, 100))
+            view = dataclasses.replace(b.view, occupancy=np.zeros_like(b.view.occupancy))
+            b = synth.TrainBatch(synth.subset_rays(b.rays, keep), view, np.ascontiguousarray(b.target[:, keep]))
+        batches.append(b)
+    tw = dataclasses.replace(tw, batches=batches)
+    ctx = invr.Context(0)
+    tb, fields, keep = make_batches(invr, ctx, tw, invr.INVR_MLP_BF16)
+    loss = float(invr.forward_train(ctx, tb).item())
+    invr.backward(ctx, tb)
+    ctx.sync()
+    ofields = {id(fp): oracle.Field.from_params(fp) for fp in tw.fields}
+    ob = [oracle.TrainBatch(b.rays.o, b.rays.d, oracle.View.from_synth(b.view, field=ofields[id(b.view.field)]),
+                            b.target) for b in tw.batches]
+    oloss, ograds = oracle.train_loss_grad(ob, tw.n_samples, tw.t_eps, tw.huber_delta)
+    assert abs(loss - oloss) <= 1e-5 * oloss
+    for fp in tw.fields:
+        gt, gw = (x.cpu().numpy() for x in fields[id(fp)].get_grads())
+        ogt, ogw = ograds[id(ofields[id(fp)])]
+        if not np.any(ogw):                      # the field saw no occupied sample
+            assert not np.any(gt) and not np.any(gw)
+            continue
+        for got, want in ((gt, ogt), (gw, ogw)):
+            assert np.linalg.norm(got - want) <= 1e-2 * np.linalg.norm(want)
