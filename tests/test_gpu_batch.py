@@ -372,3 +372,46 @@ def test_two_field_backward_side_stream(env, case):
             continue
         for got, want in ((gt, ogt), (gw, ogw)):
             assert np.linalg.norm(got - want) <= 1e-2 * np.linalg.norm(want)
+
+
+def test_full_size_keyframe_graph_replay_sampled_rays(env):
+    """The headline configuration itself: 8 key frames x both fields at their full ray counts
+    (1.77 M rays, 128 samples), BF16 MLPs, launch shapes autotuned, a reserved workspace and
+    the step replayed from a CUDA graph.  The replay's per-ray colour and opacity of 512
+    sampled rays per batch against the oracle's render of those rays with the parameters the
+    replay started from (mixed-precision tolerance 2e-3); every output finite."""
+    import torch
+    invr, oracle = env
+    tw = synth.keyframe_batch_workload()
+    total = sum(b.rays.n for b in tw.batches)
+    ctx = invr.Context(0)
+    fields = {id(fp): invr.Field.from_synth(ctx, fp, invr.INVR_MLP_BF16) for fp in tw.fields}
+    keep, batches = [], []
+    for b in tw.batches:
+        g = None
+        if b.view.graph is not None:
+            sg = b.view.graph
+            g = invr.Graph(ctx, sg.x_canon.shape[1], sg.K, sg.radius, 1, cu(sg.x_canon))
+            g.set_pose(0, cu(sg.dq), cu(sg.x_live))
+        occ = cu(b.view.occupancy)
+        keep.append((g, occ))
+        batches.append((cu(b.rays.o), cu(b.rays.d), invr.View(fields[id(b.view.field)], g, 0, b.view.rigid_dq, occ),
+                        cu(b.target)))
+    tb = invr.TrainBatches(batches, tw.n_samples, tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps,
+                           keep_outputs=True)
+    ctx.reserve(total, 32)
+    ctx.autotune(tb)
+    graph = invr.TrainGraph(ctx, tb, warmup=2)
+    before = {k: [x.cpu().numpy() for x in f.get_params()[:2]] for k, f in fields.items()}
+    graph.replay()
+    ctx.sync()
+    torch.cuda.synchronize()
+    ofields = {id(fp): oracle.Field(fp.desc, *before[id(fp)]) for fp in tw.fields}
+    rng = np.random.default_rng(77)
+    for b, (rgba, _) in zip(tw.batches, tb.outputs):
+        got = rgba.cpu().numpy()
+        assert np.isfinite(got).all()
+        idx = np.sort(rng.choice(b.rays.n, size=min(512, b.rays.n), replace=False))
+        ov = oracle.View.from_synth(b.view, field=ofields[id(b.view.field)])
+        ref = oracle.render(b.rays.o[:, idx], b.rays.d[:, idx], tw.n_samples, tw.t_eps, [ov])
+        np.testing.assert_allclose(got[:, idx], ref.rgba, rtol=0, atol=2e-3)
