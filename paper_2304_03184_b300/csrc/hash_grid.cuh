@@ -18,6 +18,12 @@ struct Corners {
 // parities px, py, pz.  Along each axis a cell's two vertices have opposite parity, so each
 // slot is filled once, and two cells that share a vertex hold it in the same slot.  Slots k
 // and k ^ 1 are the two x-adjacent vertices, the even-x one in the even slot.
+//
+// Per axis the even- and the odd-coordinate vertex (lower corner c, upper c + 1: the even one
+// is (c + 1) & ~1, the odd one c | 1) and their interpolation weights are formed once; each
+// slot then combines one term per axis: the dense row index x + y (N+1) + z (N+1)^2 or the hash
+// (x ^ y pi2 ^ z pi3) mod T from the two y and two z terms, and the weight (w_x w_y) w_z from
+// the four x-y products.  The same integers and the same FP32 products as slot-by-slot.
 __device__ __forceinline__ void level_corners(const FieldDev& F, int l, float3 x, Corners& c) {
   const int res = F.res[l];
   const bool dense = (F.dense_mask >> l) & 1u;
@@ -25,13 +31,36 @@ __device__ __forceinline__ void level_corners(const FieldDev& F, int l, float3 x
   float fx, fy, fz;
   const int cx = level_cell(x.x, res, fx), cy = level_cell(x.y, res, fy), cz = level_cell(x.z, res, fz);
   c.par = (uint32_t)((cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2));
+  // [0]: the even-coordinate vertex, [1]: the odd one; its weight is f where it is the upper
+  // corner (c + 1), 1 - f where it is the lower one
+  const uint32_t vx[2] = {(uint32_t)(cx + 1) & ~1u, (uint32_t)cx | 1u};
+  const uint32_t vy[2] = {(uint32_t)(cy + 1) & ~1u, (uint32_t)cy | 1u};
+  const uint32_t vz[2] = {(uint32_t)(cz + 1) & ~1u, (uint32_t)cz | 1u};
+  const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+  const float wx[2] = {(cx & 1) ? fx : gx, (cx & 1) ? gx : fx};
+  const float wy[2] = {(cy & 1) ? fy : gy, (cy & 1) ? gy : fy};
+  const float wz[2] = {(cz & 1) ? fz : gz, (cz & 1) ? gz : fz};
+  uint32_t hy[2], hz[2];
+  if (dense) {
+    const uint32_t n = (uint32_t)res + 1u;
+    hy[0] = vy[0] * n;
+    hy[1] = vy[1] * n;
+    hz[0] = vz[0] * n * n;
+    hz[1] = vz[1] * n * n;
+  } else {
+    hy[0] = vy[0] * 2654435761u;
+    hy[1] = vy[1] * 2654435761u;
+    hz[0] = vz[0] * 805459861u;
+    hz[1] = vz[1] * 805459861u;
+  }
+  float wxy[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) wxy[j] = wx[j & 1] * wy[j >> 1];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    // offset of slot k's vertex from the cell's lower corner, per axis
-    const int bx = (k & 1) ^ (cx & 1), by = ((k >> 1) & 1) ^ (cy & 1), bz = ((k >> 2) & 1) ^ (cz & 1);
-    c.idx[k] = vertex_index((uint32_t)(cx + bx), (uint32_t)(cy + by), (uint32_t)(cz + bz), res, dense, tmask);
-    const float wx = bx ? fx : 1.0f - fx, wy = by ? fy : 1.0f - fy, wz = bz ? fz : 1.0f - fz;
-    c.w[k] = (wx * wy) * wz;
+    const int px = k & 1, py = (k >> 1) & 1, pz = k >> 2;
+    c.idx[k] = dense ? vx[px] + hy[py] + hz[pz] : (vx[px] ^ hy[py] ^ hz[pz]) & tmask;
+    c.w[k] = wxy[k & 3] * wz[pz];
   }
 }
 
