@@ -226,7 +226,7 @@ invr_status ensure_workspace(invr_ctx ctx, int64_t R, int64_t S, bool train, cud
   INVR_CUDA(ctx, dmalloc(&feat, (size_t)kMaxIn * S));
   w.feat = feat;
   INVR_CUDA(ctx, dmalloc(&w.out, 4 * S));
-  INVR_CUDA(ctx, dmalloc(&w.loss_part, R / 256 + 1));
+  INVR_CUDA(ctx, dmalloc(&w.loss_part, R / 32 + 1));
   INVR_CUDA(ctx, dmalloc(&w.tickets, kTicketSlots));
   if (train) {
     INVR_CUDA(ctx, dmalloc(&w.dout, 4 * S));
