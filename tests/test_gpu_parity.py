@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
 inputs.  Discrete results (sample positions, occupancy, hash slots, nearest-node ids) must
 match bit for bit on identical FP32 inputs; FP32 colour and opacity within 1e-5 absolute;
-gradients within 1e-3 relative (spec tolerances of the FP32 path)."""
+gradients within 1e-3 relative (the stated tolerances of the FP32 path)."""
 import dataclasses
 import math
 
@@ -532,7 +532,7 @@ def test_train_gradients_16_features(env):
     _assert_field_grads(gt, gw, ogt, ogw, fp.desc, GRAD_RTOL, entry=True)
 
 
-# Mixed-precision gradients per tensor vs the FP64 oracle: the benchmark spec's bound of 1e-2
+# Mixed-precision gradients per tensor vs the FP64 oracle: the stated bound of 1e-2
 # relative for every hash level and weight matrix, through the FP32 warp.  The training
 # forward takes its ReLU decisions on split 16-bit products (values plus rounding
 # remainders), so they agree with the FP64 network's as in FP32; what is left is the 16-bit
