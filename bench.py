@@ -609,30 +609,31 @@ def bench_batched(invr, args, flush, world, prec_name, with_fp32=True):
     ctx.sync()
 
     # end to end: every step's rays and targets come from pinned host memory and its loss goes
-    # back to the host.  Pipelined as a caller streaming key frames would: step i+1's inputs
-    # are copied host -> device on a copy stream into one of two staging sets while step i
-    # runs; each step moves its staged inputs into the graph's buffers (device copies), replays
-    # the graph and reads the loss back.  The first step's copy is inside the timed region,
-    # and so is an L2 flush before every step.
+    # back to the host.  Pipelined as a caller streaming key frames would: two sets of the
+    # step's input buffers, each with its own captured graph; step i+1's inputs are copied
+    # host -> device on a copy stream into the other set while step i's graph runs, and each
+    # step replays its set's graph and reads the loss back.  The first step's copy is inside
+    # the timed region, and so is an L2 flush before every step.
     host_in = [(b[0].cpu().pin_memory(), b[1].cpu().pin_memory(), b[3].cpu().pin_memory()) for b in tb.batches]
     loss_h = torch.empty(1, pin_memory=True)
     h2d = sum(x.numel() * 4 for trip in host_in for x in trip)
-    stage = [[(torch.empty_like(b[0]), torch.empty_like(b[1])) for b in tb.batches] + [torch.empty_like(tb.targets)]
-             for _ in range(2)]
+    tb2 = invr.TrainBatches([(b[0].clone(), b[1].clone(), b[2], b[3].clone()) for b in tb.batches], tw.n_samples,
+                            tw.t_eps, tw.huber_delta, tw.lr, tw.beta1, tw.beta2, tw.adam_eps)
+    sets = [(tb, graph), (tb2, invr.TrainGraph(ctx, tb2, warmup=2))]
     cs = torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]     # host -> staging set done
-    consumed = [torch.cuda.Event() for _ in range(2)]   # staging set moved into the graph's buffers
+    copied = [torch.cuda.Event() for _ in range(2)]     # host -> input set done
+    consumed = [torch.cuda.Event() for _ in range(2)]   # the set's step has run
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def copy_in(i):
-        st = stage[i % 2]
+        t = sets[i % 2][0]
         with torch.cuda.stream(cs):
             cs.wait_event(consumed[i % 2] if i >= 2 else a)
             off = 0
             for j, (ho, hd, ht) in enumerate(host_in):
-                st[j][0].copy_(ho, non_blocking=True)
-                st[j][1].copy_(hd, non_blocking=True)
-                st[-1][off:off + ht.numel()].copy_(ht.reshape(-1), non_blocking=True)
+                t.batches[j][0].copy_(ho, non_blocking=True)
+                t.batches[j][1].copy_(hd, non_blocking=True)
+                t.targets[off:off + ht.numel()].copy_(ht.reshape(-1), non_blocking=True)
                 off += ht.numel()
             copied[i % 2].record(cs)
 
@@ -642,23 +643,19 @@ def bench_batched(invr, args, flush, world, prec_name, with_fp32=True):
     for i in range(args.steps):
         if i + 1 < args.steps:
             copy_in(i + 1)
-        st = stage[i % 2]
         stream.wait_event(copied[i % 2])
-        for j, (o, d, _v, _t, *_) in enumerate(tb.batches):
-            o.copy_(st[j][0], non_blocking=True)
-            d.copy_(st[j][1], non_blocking=True)
-        tb.targets.copy_(st[-1], non_blocking=True)
-        consumed[i % 2].record(stream)
         flush.fill_(1)                    # L2 flushed before every step, as in the device timing
-        loss_h.copy_(graph.replay(), non_blocking=True)
+        loss = sets[i % 2][1].replay()
+        consumed[i % 2].record(stream)
+        loss_h.copy_(loss, non_blocking=True)
     b.record(stream)
     torch.cuda.synchronize()
     e_ms = a.elapsed_time(b) / args.steps
     e2e = {"value": round(world * S_nom / (e_ms * 1e-3), 1), "unit": UNIT, "ms_per_step": round(e_ms, 3),
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
-           "copies": "pinned host -> device on a copy stream into two staging sets (next step's under "
-                     "this one), device copies into the graph's inputs, loss read back every step; "
-                     "L2 flushed before every step"}
+           "copies": "pinned host -> device on a copy stream into the inputs of one of two captured step "
+                     "graphs (next step's under this one), loss read back every step; L2 flushed before "
+                     "every step"}
     out = {"workload": tw.name, "rays": R, "samples_per_ray": tw.n_samples, "occupied_samples": S_occ,
            "batches": len(tw.batches), "S_nom": S_nom, "ms": ms, "eager_ms": eager_ms, "ktime": ktime,
            "tune": tune, "e2e": e2e, "tw": tw, "fp32_sequential": None}
