@@ -6,12 +6,13 @@
 //     -> D = H W_k^T (N = H) -> ReLU -> H        (k = 2..n_hidden)
 //     -> D = H W_out^T (N = 16, rows 3..15 zero) -> delta v; v_c = v_t + delta v.
 //
-// One CTA = 128 threads (one warpgroup) per SM; thread t owns sample t of a tile (row t of
-// every MMA, lane t of tensor memory).  Every layer's weights are staged once per net as
-// BF16 K-major operands (108 KB at 32 / 4 x 128).  Two tiles are in flight: while the
-// tensor core runs one tile's layer, the threads run the other tile's epilogue (tensor
-// memory -> bias, ReLU -> next operand row).  Waits are bounded; a timeout sets the status
-// word, drains this CTA's MMAs (bounded) and frees its tensor memory.
+// One CTA per SM; thread t of a warpgroup owns sample t of a tile (row t of every MMA, lane
+// t of tensor memory).  Every layer's weights are staged once per net as BF16 K-major
+// operands (108 KB at 32 / 4 x 128).  Two tiles are in flight: in the forward each belongs to
+// its own warpgroup, which runs its tile's epilogues while the tensor core runs the other
+// tile's layer; the backward's chain alternates one warpgroup between its two tiles.  Waits
+// are bounded; a timeout sets the status word, drains the outstanding MMAs (bounded) and
+// frees the tensor memory.
 #include "invr_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -72,12 +73,13 @@ __device__ void stage(uint8_t* dst, const float* __restrict__ W, int N, int K, i
   }
 }
 
-// The same as 16-bit values at dst and their rounding remainders at dst + N K 2 bytes.
-template <bool BF16>
+// The same as 16-bit values at dst and their rounding remainders at dst + N K 2 bytes (by
+// the NT threads of the block).
+template <bool BF16, int NT = kThreads>
 __device__ void stage_split(uint8_t* dst, const float* __restrict__ W, int N, int K, int ldw, int n_valid,
                             int k_valid) {
   uint8_t* lo = dst + N * K * 2;
-  for (int e = threadIdx.x; e < N * K / 2; e += kThreads) {
+  for (int e = threadIdx.x; e < N * K / 2; e += NT) {
     const int n = (2 * e) / K, k = (2 * e) % K;
     const float a = (n < n_valid && k < k_valid) ? __ldg(W + (int64_t)n * ldw + k) : 0.0f;
     const float b = (n < n_valid && k + 1 < k_valid) ? __ldg(W + (int64_t)n * ldw + k + 1) : 0.0f;
@@ -129,32 +131,52 @@ struct Slot {
   int view = 0;
 };
 
+// The forward's two tile slots belong to two warpgroups (256 threads): warpgroup g runs slot
+// g's whole layer chain -- its epilogues and, from its first thread, its MMAs -- with its own
+// named barrier (id 1 + g), so one slot's epilogue overlaps the other's MMAs on separate warps.
+constexpr int kThreadsF = 256;
+
+__device__ __forceinline__ void wg_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// Named-barrier AND over the 128 threads of a warpgroup.
+__device__ __forceinline__ bool wg_and(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
 template <bool BF16>
-__global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_constant__ Plan P) {
+__global__ void __launch_bounds__(kThreadsF, 1) k_deform_fwd_tc(const __grid_constant__ Plan P) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int64_t S_cap = P.ws.S_cap;
   const int64_t S = P.ws.view_base[P.n_views];
   if (S > S_cap) return;
   const int t = threadIdx.x, warp = t >> 5;
+  const int g = t >> 7, tl = t & 127;  // warpgroup = tile slot, thread within it
+  const int bar = 1 + g;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + F_MISC + 16);
-  const uint32_t mbar0 = tc::smem_u32(sm + F_MISC);
+  const uint32_t mbar = tc::smem_u32(sm + F_MISC) + 8 * g;
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
   if (t == 0) {
-    tc::mbar_init(mbar0, 1);
-    tc::mbar_init(mbar0 + 8, 1);
+    tc::mbar_init(tc::smem_u32(sm + F_MISC), 1);
+    tc::mbar_init(tc::smem_u32(sm + F_MISC) + 8, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t row = tmem + 256 * g + ((uint32_t)((warp & 3) * 32) << 16);  // this thread's lane of its slot
 
   // tiles of views with a net, in order; this CTA takes every gridDim.x-th one, two at a time
   const int64_t n_tiles = S / kTM;
   const float* loaded = nullptr;
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};  // an MMA commit of the slot not yet waited for
+  uint32_t phase = 0u;
+  bool pending = false;  // an MMA commit of this warpgroup's slot not yet waited for
   bool ok = true;
   int64_t next = blockIdx.x;
   auto next_tile = [&](Slot& sl) {
@@ -186,31 +208,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
     if (D.weights != loaded) {
       __syncthreads();
       const int n_in = D.n_feat + D.pose_dim;
-      stage_split<BF16>(sm + F_W1, D.weights, H, Kf, n_in, H, D.n_feat);
+      stage_split<BF16, kThreadsF>(sm + F_W1, D.weights, H, Kf, n_in, H, D.n_feat);
       for (int l = 1; l < n; ++l)
-        stage_split<BF16>(sm + F_WH + (l - 1) * 2 * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
-      stage_split<BF16>(sm + F_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+        stage_split<BF16, kThreadsF>(sm + F_WH + (l - 1) * 2 * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H,
+                                     H, H);
+      stage_split<BF16, kThreadsF>(sm + F_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
       tc::fence_smem_to_async();
+      __syncthreads();
       loaded = D.weights;
     }
-    // operands of both tiles: features (FP32 feature-major) -> 16-bit values and rounding
-    // remainders in the slot's tensor memory (layer 1's A operand), pose bias; every feature
-    // load of both tiles is issued before the first store
-    float xr[2][kKf];
+    const Slot sl = slot[g];
+    if (sl.s0 >= 0) {
+      const int64_t s0 = sl.s0;
+      // layer 1's operand: the features (FP32 feature-major) as 16-bit values and rounding
+      // remainders in the slot's tensor memory, and the pose bias
+      float xr[kKf];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-#pragma unroll
-      for (int k = 0; k < kKf; ++k)
-        xr[j][k] = slot[j].s0 >= 0 && k < D.n_feat ? P.ws.feat_d[(int64_t)k * S_cap + slot[j].s0 + t] : 0.0f;
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (slot[j].s0 < 0) continue;
-      const int64_t s0 = slot[j].s0;
-      const uint32_t row = tmem + 256 * j + lane_off;
+      for (int k = 0; k < kKf; ++k) xr[k] = k < D.n_feat ? P.ws.feat_d[(int64_t)k * S_cap + s0 + tl] : 0.0f;
       uint32_t hi[16], lo[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) tc::split2<BF16>(xr[j][2 * c], xr[j][2 * c + 1], hi[c], lo[c]);
+      for (int c = 0; c < 16; ++c) tc::split2<BF16>(xr[2 * c], xr[2 * c + 1], hi[c], lo[c]);
       if (Kf == 32) {
         tc::tmem_st16(row + T_HI, hi);
         tc::tmem_st16(row + T_LO, lo);
@@ -226,38 +243,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
       }
       if (P.deform_store) {
         for (int k = 0; k < Kf; k += 8)
-          *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(t, k, Kf)) =
+          *reinterpret_cast<uint4*>(P.ws.def_x + (s0 / kTM) * kXTile + tc::kmajor_offset(tl, k, Kf)) =
               make_uint4(hi[k / 2], hi[k / 2 + 1], hi[k / 2 + 2], hi[k / 2 + 3]);
       }
-      float* bias = reinterpret_cast<float*>(sm + F_BIAS) + j * kH;
-      for (int o = t; o < H; o += kThreads) bias[o] = P.v[slot[j].view].deform.pose_bias[o];
-    }
-    operands_ready();
-    if (t == 0) {
-      tc::fence_after_sync();
-      for (int j = 0; j < 2; ++j) {
-        if (slot[j].s0 < 0) continue;
-        issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + F_W1, Kf, H);
-        tc::commit_to(mbar0 + 8 * j);
-      }
-    }
-    for (int j = 0; j < 2; ++j) pending[j] = slot[j].s0 >= 0;
-    // layers 1..n: epilogue of layer l of tile j, then issue layer l+1 of tile j
-    for (int l = 0; l <= n && ok; ++l) {
-      for (int j = 0; j < 2; ++j) {
-        if (slot[j].s0 < 0) continue;
-        ok = tc::mbar_wait(mbar0 + 8 * j, phase[j], P.wait_limit);
-        if (!__syncthreads_and(ok)) {
-          ok = false;
-          break;
-        }
-        phase[j] ^= 1u;
-        pending[j] = false;
+      float* bias = reinterpret_cast<float*>(sm + F_BIAS) + g * kH;
+      for (int o = tl; o < H; o += 128) bias[o] = P.v[sl.view].deform.pose_bias[o];
+      tc::fence_smem_to_async();
+      tc::fence_before_sync();
+      wg_sync(bar);
+      if (tl == 0) {
         tc::fence_after_sync();
-        const uint32_t row = tmem + 256 * j + lane_off;
+        issue_split<BF16>(tmem + 256 * g, tmem + 256 * g + T_HI, tmem + 256 * g + T_LO, sbase + F_W1, Kf, H);
+        tc::commit_to(mbar);
+      }
+      pending = true;
+      // layers 1..n: epilogue of layer l, then issue layer l+1
+      for (int l = 0; l <= n; ++l) {
+        ok = wg_and(bar, tc::mbar_wait(mbar, phase, P.wait_limit));
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc::fence_after_sync();
         if (l < n) {
-          const float* bias = reinterpret_cast<const float*>(sm + F_BIAS) + j * kH;
-          uint8_t* g = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + slot[j].s0 / kTM) * kHTile;
+          const float* bias = reinterpret_cast<const float*>(sm + F_BIAS) + g * kH;
+          uint8_t* gh = P.ws.def_h + ((int64_t)l * (S_cap / kTM) + s0 / kTM) * kHTile;
           for (int c = 0; c < H; c += 32) {
             float v[32];
             tc::tmem_ld32(row + c, v);
@@ -265,52 +274,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_fwd_tc(const __grid_cons
 #pragma unroll
               for (int i = 0; i < 32; ++i) v[i] += bias[c + i];
             }
-            uint32_t hi[16], lo[16];
+            uint32_t hh[16], ll[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) tc::split2<BF16>(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f), hi[q], lo[q]);
+            for (int q = 0; q < 16; ++q)
+              tc::split2<BF16>(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f), hh[q], ll[q]);
             // h_l as the next layer's A operand (values and remainders) and, rounded, for the
             // backward (its weight-gradient operand; its sign is the ReLU decision taken here)
-            tc::tmem_st16(row + T_HI + c / 2, hi);
-            tc::tmem_st16(row + T_LO + c / 2, lo);
+            tc::tmem_st16(row + T_HI + c / 2, hh);
+            tc::tmem_st16(row + T_LO + c / 2, ll);
             if (P.deform_store) {
 #pragma unroll
               for (int c8 = 0; c8 < 4; ++c8)
-                *reinterpret_cast<uint4*>(g + tc::kmajor_offset(t, c + 8 * c8, H)) =
-                    make_uint4(hi[4 * c8], hi[4 * c8 + 1], hi[4 * c8 + 2], hi[4 * c8 + 3]);
+                *reinterpret_cast<uint4*>(gh + tc::kmajor_offset(tl, c + 8 * c8, H)) =
+                    make_uint4(hh[4 * c8], hh[4 * c8 + 1], hh[4 * c8 + 2], hh[4 * c8 + 3]);
             }
           }
           tc::fence_before_sync();
-          __syncthreads();
-          if (t == 0) {
+          wg_sync(bar);
+          if (tl == 0) {
             tc::fence_after_sync();
             if (l + 1 < n)
-              issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO,
+              issue_split<BF16>(tmem + 256 * g, tmem + 256 * g + T_HI, tmem + 256 * g + T_LO,
                                 sbase + F_WH + l * 2 * kH * kH * 2, H, H);
             else
-              issue_split<BF16>(tmem + 256 * j, tmem + 256 * j + T_HI, tmem + 256 * j + T_LO, sbase + F_WO, H, 16);
-            tc::commit_to(mbar0 + 8 * j);
+              issue_split<BF16>(tmem + 256 * g, tmem + 256 * g + T_HI, tmem + 256 * g + T_LO, sbase + F_WO, H, 16);
+            tc::commit_to(mbar);
           }
-          pending[j] = true;
+          pending = true;
         } else {
           float v[16];
           tc::tmem_ld16(row, v);
-          const int64_t g = slot[j].s0 + t;
-          if (P.ws.s_ray[g] >= 0) {
-            P.ws.s_vc[g] = P.ws.s_vt[g] + v[0];
-            P.ws.s_vc[S_cap + g] = P.ws.s_vt[S_cap + g] + v[1];
-            P.ws.s_vc[2 * S_cap + g] = P.ws.s_vt[2 * S_cap + g] + v[2];
+          const int64_t gs = s0 + tl;
+          if (P.ws.s_ray[gs] >= 0) {
+            P.ws.s_vc[gs] = P.ws.s_vt[gs] + v[0];
+            P.ws.s_vc[S_cap + gs] = P.ws.s_vt[S_cap + gs] + v[1];
+            P.ws.s_vc[2 * S_cap + gs] = P.ws.s_vt[2 * S_cap + gs] + v[2];
           }
           tc::fence_before_sync();
         }
       }
     }
-    __syncthreads();
+    ok = __syncthreads_and(ok);  // both slots' chains done (or one gave up)
   }
   if (!ok) {
     if (t == 0) atomicOr(P.status, kStatusTimeout);
-    // let this CTA's outstanding MMAs finish (bounded) before their tensor memory is freed
-    for (int j = 0; j < 2; ++j)
-      if (pending[j] && !tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
+    // let this warpgroup's outstanding MMAs finish (bounded) before their tensor memory is freed
+    if (tl == 0 && pending && !tc::mbar_wait(mbar, phase, kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -788,7 +797,7 @@ template <bool BF16>
 static cudaError_t forward_tc(const Plan& P, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_deform_fwd_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemF);
   if (e != cudaSuccess) return e;
-  k_deform_fwd_tc<BF16><<<num_sms, kThreads, kSmemF, s>>>(P);
+  k_deform_fwd_tc<BF16><<<num_sms, kThreadsF, kSmemF, s>>>(P);
   return cudaGetLastError();
 }
 
