@@ -63,9 +63,9 @@ __device__ __forceinline__ int64_t layer_offset(const DeformDev& D, int layer) {
 
 // dst = W (rows [0, N), columns [k0, k0 + K) of a row-major [.][ldw] matrix; zero rows
 // from n_valid on and zero columns from k_valid on) as a K-major BF16 operand.
-template <bool BF16>
+template <bool BF16, int NT = kThreads>
 __device__ void stage(uint8_t* dst, const float* __restrict__ W, int N, int K, int ldw, int n_valid, int k_valid) {
-  for (int e = threadIdx.x; e < N * K / 2; e += kThreads) {
+  for (int e = threadIdx.x; e < N * K / 2; e += NT) {
     const int n = (2 * e) / K, k = (2 * e) % K;
     const float a = (n < n_valid && k < k_valid) ? __ldg(W + (int64_t)n * ldw + k) : 0.0f;
     const float b = (n < n_valid && k + 1 < k_valid) ? __ldg(W + (int64_t)n * ldw + k + 1) : 0.0f;
@@ -118,12 +118,6 @@ __device__ __forceinline__ void issue_split(uint32_t d_tmem, uint32_t a_hi, uint
     tc::mma_f16_ts(d_tmem, a_lo + kk * 8, bd, idesc, 1u);
     tc::mma_f16_ts(d_tmem, a_hi + kk * 8, bl, idesc, 1u);
   }
-}
-
-__device__ __forceinline__ void operands_ready() {
-  tc::fence_smem_to_async();
-  tc::fence_before_sync();
-  __syncthreads();
 }
 
 struct Slot {
@@ -375,30 +369,32 @@ __device__ __forceinline__ uint32_t positive_halves(uint32_t w) {
 // padded g_out tile) is stored for the weight-gradient kernel; dL/df is written FP32
 // feature-major for the scatter into the net's tables.  Two tiles in flight, as the forward.
 template <bool BF16>
-__global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_constant__ Plan P) {
+__global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_constant__ Plan P) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int64_t S_cap = P.ws.S_cap;
   const int64_t S = P.ws.view_base[P.n_views];
   if (S > S_cap) return;
   const int t = threadIdx.x, warp = t >> 5;
+  const int g = t >> 7, tl = t & 127;  // warpgroup = tile slot, thread within it
+  const int bar = 1 + g;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC + 16);
-  const uint32_t mbar0 = tc::smem_u32(sm + OFF_MISC);
+  const uint32_t mbar = tc::smem_u32(sm + OFF_MISC) + 8 * g;
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
   if (t == 0) {
-    tc::mbar_init(mbar0, 1);
-    tc::mbar_init(mbar0 + 8, 1);
+    tc::mbar_init(tc::smem_u32(sm + OFF_MISC), 1);
+    tc::mbar_init(tc::smem_u32(sm + OFF_MISC) + 8, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t row = tmem + 256 * g + ((uint32_t)((warp & 3) * 32) << 16);  // this thread's lane of its slot
   const int64_t tiles_cap = S_cap / kTM;
   const int64_t n_tiles = S / kTM;
   const float* loaded = nullptr;
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
+  uint32_t phase = 0u;
+  bool pending = false;
   bool ok = true;
   int64_t next = blockIdx.x;
   auto next_tile = [&](Slot& sl) {
@@ -428,72 +424,66 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
     if (D.weights != loaded) {
       __syncthreads();
       const int n_in = D.n_feat + D.pose_dim;
-      stage<BF16>(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
-      for (int l = 1; l < n; ++l) stage<BF16>(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
-      stage<BF16>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      stage<BF16, kThreadsF>(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
+      for (int l = 1; l < n; ++l)
+        stage<BF16, kThreadsF>(sm + OFF_WH + (l - 1) * kH * kH * 2, D.weights + layer_offset(D, l), H, H, H, H, H);
+      stage<BF16, kThreadsF>(sm + OFF_WO, D.weights + layer_offset(D, n), 16, H, H, 3, H);
+      tc::fence_smem_to_async();
+      __syncthreads();
       loaded = D.weights;
     }
-    // g_out tiles: dL/dv_c (3 columns) padded to 16, in smem and stored
-    for (int j = 0; j < 2; ++j) {
-      if (slot[j].s0 < 0) continue;
-      const int64_t g = slot[j].s0 + t;
-      float v[16];
-      // scaled by 1 / loss_norm before rounding to 16 bits (the deltas of a mean loss are
-      // small enough to lose FP16 precision), unscaled in FP32 on the way out
-      const float in_scale = 1.0f / P.loss_norm;
+    const Slot sl = slot[g];
+    if (sl.s0 >= 0) {
+      const int64_t T = sl.s0 / kTM;
+      // g_out tile: dL/dv_c (3 columns) padded to 16, in smem and stored
+      {
+        const int64_t gs = sl.s0 + tl;
+        float v[16];
+        // scaled by 1 / loss_norm before rounding to 16 bits (the deltas of a mean loss are
+        // small enough to lose FP16 precision), unscaled in FP32 on the way out
+        const float in_scale = 1.0f / P.loss_norm;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = i < 3 ? P.ws.dvc[(int64_t)i * S_cap + g] * in_scale : 0.0f;
-      uint4 lo, hi;
-      lo.x = tc::pack2<BF16>(v[0], v[1]);
-      lo.y = tc::pack2<BF16>(v[2], v[3]);
-      lo.z = tc::pack2<BF16>(v[4], v[5]);
-      lo.w = tc::pack2<BF16>(v[6], v[7]);
-      hi.x = hi.y = hi.z = hi.w = 0u;
-      uint8_t* go = sm + OFF_X + j * kXTile;
-      *reinterpret_cast<uint4*>(go + tc::kmajor_offset(t, 0, 16)) = lo;
-      *reinterpret_cast<uint4*>(go + tc::kmajor_offset(t, 8, 16)) = hi;
-      uint8_t* gg = P.ws.def_gout + (slot[j].s0 / kTM) * kGoTile;
-      *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, 0, 16)) = lo;
-      *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, 8, 16)) = hi;
-    }
-    operands_ready();
-    if (t == 0) {
-      tc::fence_after_sync();
-      for (int j = 0; j < 2; ++j) {
-        if (slot[j].s0 < 0) continue;
-        issue_adjoint<BF16>(tmem + 256 * j, sbase + OFF_X + j * kXTile, sbase + OFF_WO, 16, H);
-        tc::commit_to(mbar0 + 8 * j);
+        for (int i = 0; i < 16; ++i) v[i] = i < 3 ? P.ws.dvc[(int64_t)i * S_cap + gs] * in_scale : 0.0f;
+        uint4 lo, hi;
+        lo.x = tc::pack2<BF16>(v[0], v[1]);
+        lo.y = tc::pack2<BF16>(v[2], v[3]);
+        lo.z = tc::pack2<BF16>(v[4], v[5]);
+        lo.w = tc::pack2<BF16>(v[6], v[7]);
+        hi.x = hi.y = hi.z = hi.w = 0u;
+        uint8_t* go = sm + OFF_X + g * kXTile;
+        *reinterpret_cast<uint4*>(go + tc::kmajor_offset(tl, 0, 16)) = lo;
+        *reinterpret_cast<uint4*>(go + tc::kmajor_offset(tl, 8, 16)) = hi;
+        uint8_t* gg = P.ws.def_gout + T * kGoTile;
+        *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(tl, 0, 16)) = lo;
+        *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(tl, 8, 16)) = hi;
       }
-    }
-    for (int j = 0; j < 2; ++j) pending[j] = slot[j].s0 >= 0;
-    // the ReLU mask rows (this thread's row of the stored h tile) of the next stage of each
-    // slot, loaded one stage ahead so that they arrive under the other slot's epilogue
-    uint4 mrow[2][16];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (slot[j].s0 < 0 || n < 1) continue;
-      const uint8_t* hg = P.ws.def_h + ((int64_t)(n - 1) * tiles_cap + slot[j].s0 / kTM) * kHTile;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) mrow[j][c] = __ldg(reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(t, 8 * c, H)));
-    }
-    // stage e = 0..n-1: mask with h_{n-1-e}, store g, issue the next adjoint; stage n: dL/df
-    for (int e = 0; e <= n && ok; ++e) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (slot[j].s0 < 0) continue;
-        ok = tc::mbar_wait(mbar0 + 8 * j, phase[j], P.wait_limit);
-        if (!__syncthreads_and(ok)) {
-          ok = false;
-          break;
-        }
-        phase[j] ^= 1u;
-        pending[j] = false;
+      tc::fence_smem_to_async();
+      tc::fence_before_sync();
+      wg_sync(bar);
+      if (tl == 0) {
         tc::fence_after_sync();
-        const uint32_t row = tmem + 256 * j + lane_off;
-        const int64_t T = slot[j].s0 / kTM;
+        issue_adjoint<BF16>(tmem + 256 * g, sbase + OFF_X + g * kXTile, sbase + OFF_WO, 16, H);
+        tc::commit_to(mbar);
+      }
+      pending = true;
+      // the ReLU mask rows (this thread's row of the stored h tile) of the next stage, loaded
+      // one stage ahead so that they arrive under the MMAs
+      uint4 mrow[16];
+      if (n >= 1) {
+        const uint8_t* hg = P.ws.def_h + ((int64_t)(n - 1) * tiles_cap + T) * kHTile;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) mrow[c] = __ldg(reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(tl, 8 * c, H)));
+      }
+      // stage e = 0..n-1: mask with h_{n-1-e}, store g, issue the next adjoint; stage n: dL/df
+      for (int e = 0; e <= n; ++e) {
+        ok = wg_and(bar, tc::mbar_wait(mbar, phase, P.wait_limit));
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc::fence_after_sync();
         if (e < n) {
           const int li = n - 1 - e;
-          uint8_t* gs = sm + OFF_HB + j * kHTile;
+          uint8_t* gsm = sm + OFF_HB + g * kHTile;
           uint8_t* gg = P.ws.def_g + ((int64_t)li * tiles_cap + T) * kHTile;
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
@@ -502,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
 #pragma unroll
             for (int c8 = 0; c8 < 4; ++c8) {
               // pack, then clear the halves whose stored activation is not positive
-              const uint4 m = mrow[j][4 * q4 + c8];
+              const uint4 m = mrow[4 * q4 + c8];
               const float* x = v + 8 * c8;
               uint4 q;
               q.x = tc::pack2<BF16>(x[0], x[1]) & positive_halves<BF16>(m.x);
@@ -510,45 +500,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_chain_tc(const __grid_co
               q.z = tc::pack2<BF16>(x[4], x[5]) & positive_halves<BF16>(m.z);
               q.w = tc::pack2<BF16>(x[6], x[7]) & positive_halves<BF16>(m.w);
               const int c = 32 * q4 + 8 * c8;
-              *reinterpret_cast<uint4*>(gs + tc::kmajor_offset(t, c, H)) = q;
-              *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(t, c, H)) = q;
+              *reinterpret_cast<uint4*>(gsm + tc::kmajor_offset(tl, c, H)) = q;
+              *reinterpret_cast<uint4*>(gg + tc::kmajor_offset(tl, c, H)) = q;
             }
           }
           if (li > 0) {
             const uint8_t* hn = P.ws.def_h + ((int64_t)(li - 1) * tiles_cap + T) * kHTile;
 #pragma unroll
             for (int c = 0; c < 16; ++c)
-              mrow[j][c] = __ldg(reinterpret_cast<const uint4*>(hn + tc::kmajor_offset(t, 8 * c, H)));
+              mrow[c] = __ldg(reinterpret_cast<const uint4*>(hn + tc::kmajor_offset(tl, 8 * c, H)));
           }
-          operands_ready();
-          if (t == 0) {
+          tc::fence_smem_to_async();
+          tc::fence_before_sync();
+          wg_sync(bar);
+          if (tl == 0) {
             tc::fence_after_sync();
             if (li > 0)
-              issue_adjoint<BF16>(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_WH + (li - 1) * kH * kH * 2, H, H);
+              issue_adjoint<BF16>(tmem + 256 * g, sbase + OFF_HB + g * kHTile, sbase + OFF_WH + (li - 1) * kH * kH * 2,
+                                  H, H);
             else
-              issue_adjoint<BF16>(tmem + 256 * j, sbase + OFF_HB + j * kHTile, sbase + OFF_W1, H, Kf);
-            tc::commit_to(mbar0 + 8 * j);
+              issue_adjoint<BF16>(tmem + 256 * g, sbase + OFF_HB + g * kHTile, sbase + OFF_W1, H, Kf);
+            tc::commit_to(mbar);
           }
-          pending[j] = true;
+          pending = true;
         } else {
-          const int64_t g = slot[j].s0 + t;
+          const int64_t gs = sl.s0 + tl;
           for (int c = 0; c < Kf; c += 16) {
             float v[16];
             tc::tmem_ld16(row + c, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-              if (c + i < D.n_feat) P.ws.dfeat_d[(int64_t)(c + i) * S_cap + g] = v[i] * P.loss_norm;
+              if (c + i < D.n_feat) P.ws.dfeat_d[(int64_t)(c + i) * S_cap + gs] = v[i] * P.loss_norm;
           }
           tc::fence_before_sync();
         }
       }
     }
-    __syncthreads();
+    ok = __syncthreads_and(ok);  // both slots' chains done (or one gave up)
   }
   if (!ok) {
     if (t == 0) atomicOr(P.status, kStatusTimeout);
-    for (int j = 0; j < 2; ++j)
-      if (pending[j] && !tc::mbar_wait(mbar0 + 8 * j, phase[j], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
+    if (tl == 0 && pending && !tc::mbar_wait(mbar, phase, kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -785,7 +777,7 @@ template <bool BF16>
 static cudaError_t backward_tc(const Plan& P, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_deform_chain_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e != cudaSuccess) return e;
-  k_deform_chain_tc<BF16><<<num_sms, kThreads, kSmem, s>>>(P);
+  k_deform_chain_tc<BF16><<<num_sms, kThreadsF, kSmem, s>>>(P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_deform_dw_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDw);
   if (e != cudaSuccess) return e;
