@@ -8,9 +8,9 @@
 //
 // One CTA per SM; thread t of a warpgroup owns sample t of a tile (row t of every MMA, lane
 // t of tensor memory).  Every layer's weights are staged once per net as BF16 K-major
-// operands (108 KB at 32 / 4 x 128).  Two tiles are in flight: in the forward each belongs to
-// its own warpgroup, which runs its tile's epilogues while the tensor core runs the other
-// tile's layer; the backward's chain alternates one warpgroup between its two tiles.  Waits
+// operands (108 KB at 32 / 4 x 128).  Two tiles are in flight, each owned by its own
+// warpgroup, which runs its tile's epilogues while the tensor core runs the other tile's
+// layer (in the forward and in the adjoint chain).  Waits
 // are bounded; a timeout sets the status word, drains the outstanding MMAs (bounded) and
 // frees the tensor memory.
 #include "invr_internal.cuh"
