@@ -300,7 +300,7 @@ L2_BOUND = {"encode": ("gather_v4_gbs", "random float4 loads from"),
 # carries the figure only while the kernel is unchanged (else traffic is null).
 SCATTER_SOURCES = ("paper_2304_03184_b300/csrc/k_encode.cu", "paper_2304_03184_b300/csrc/hash_grid.cuh")
 SCATTER_DRAM = {"sources_sha16": "16e6fbb41f7bfb4e", "workload": "keyframe_batch_8frames_x2fields_s128",
-                "bytes": 2_214_847_744}
+                "bytes": 2_214_847_744, "l2_bytes": 53_630_000_000}
 
 
 def sources_sha16(paths):
@@ -311,12 +311,12 @@ def sources_sha16(paths):
     return h.hexdigest()[:16]
 
 
-def scatter_traffic(workload):
-    """The captured DRAM bytes of the scatter per step, or None (no capture of this workload,
-    or the kernel's sources changed since)."""
+def scatter_traffic(workload, key="bytes"):
+    """The captured DRAM bytes (key "bytes") or L2 bytes ("l2_bytes") of the scatter per step, or
+    None (no capture of this workload, or the kernel's sources changed since)."""
     if not SCATTER_DRAM or SCATTER_DRAM["workload"] != workload:
         return None
-    return SCATTER_DRAM["bytes"] if sources_sha16(SCATTER_SOURCES) == SCATTER_DRAM["sources_sha16"] else None
+    return SCATTER_DRAM[key] if sources_sha16(SCATTER_SOURCES) == SCATTER_DRAM["sources_sha16"] else None
 
 
 def roofline(ktime, tw, R, S_occ, peaks, l2=None):
@@ -332,15 +332,19 @@ def roofline(ktime, tw, R, S_occ, peaks, l2=None):
         ach, peak = payload / dur / 1e9, l2[key]
         hbm_peak = peaks.get("hbm_gbs", 6400.0)
         traffic = scatter_traffic(tw.name) if name == "encode_bwd" else None
+        l2_bytes = scatter_traffic(tw.name, "l2_bytes") if name == "encode_bwd" else None
         return {"kernel": name, "bound": "l2", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
+                "l2_traffic": l2_bytes,
+                "l2_traffic_gbs": round(l2_bytes / dur / 1e9, 1) if l2_bytes else None,
                 "peak_source": f"measured in this run by the library's L2 probe: {form} a 64 MiB resident table",
                 "algorithmic_bytes": payload, "ms": round(kms / kn, 4),
                 "hbm": {"bytes": work, "achieved": round(work / dur / 1e9, 1), "peak": hbm_peak,
                         "frac": round(work / dur / 1e9 / hbm_peak, 4),
                         "note": "the kernel's per-sample inputs and outputs; the table traffic stays in L2"},
-                "traffic_note": ("DRAM bytes of the stage from an ncu capture of this workload at the current "
-                                 "kernel sources (the table traffic stays in L2)" if traffic is not None else
+                "traffic_note": ("DRAM bytes (traffic) and L2 bytes (lts__t_bytes, l2_traffic) of the stage from "
+                                 "ncu captures of this workload at the current kernel sources (the table traffic "
+                                 "stays in L2)" if traffic is not None else
                                  "no ncu capture of this workload at the current kernel sources")}
     if bound == "alu":
         peak = fp32_alu_peak(peaks.get("sm_max_mhz", 2032.0))
