@@ -249,8 +249,9 @@ cudaError_t launch_warp_encode_by_field(const Plan& P, int num_sms, cudaStream_t
 
 // ------------------------------------------------------------------ single step
 // One thread per point over all its levels, in step with its block (as k_encode); FP32
-// features [L*2][n].
-__global__ void __launch_bounds__(256) k_encode_points(const __grid_constant__ FieldDev F, int64_t n,
+// features [L*2][n].  Held to 48 registers (5 blocks per SM): with the per-axis corners it
+// took 56 (4 blocks), and the occupancy update's queries ran 5% slower.
+__global__ void __launch_bounds__(256, 5) k_encode_points(const __grid_constant__ FieldDev F, int64_t n,
                                                        const float* __restrict__ x, float* feat, uint32_t* idx) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float3 p = make_float3(x[i], x[n + i], x[2 * n + i]);

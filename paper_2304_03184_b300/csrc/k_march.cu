@@ -359,9 +359,11 @@ __global__ void __launch_bounds__(256) k_march_emit(const __grid_constant__ Plan
   }
 }
 
-// Blocks of two warps for the count and the emit: a warp's cost follows its rays' lengths,
-// and a block holds its slot until its slowest warp ends (count 0.203 -> 0.189 ms, emit 0.130
-// -> 0.124 ms per batched step against blocks of 8 warps).
+// Blocks of two warps for the count and, in training calls, the emit: a warp's cost follows
+// its rays' lengths, and a block holds its slot until its slowest warp ends (training rays in
+// random order: count 0.203 -> 0.189 ms, emit 0.130 -> 0.124 ms per batched step against
+// blocks of 8 warps).  A render's image-ordered rays are alike, and its emit keeps blocks of 8
+// warps (43 against 55 us per 512x512 frame in the ncu launch list).
 constexpr int kMarchB = 64;
 
 cudaError_t launch_march_count(const Plan& P, cudaStream_t s) {
@@ -381,7 +383,8 @@ cudaError_t launch_scan(const Plan& P, cudaStream_t s) {
 
 cudaError_t launch_march_emit(const Plan& P, cudaStream_t s) {
   const int64_t n = P.total_rays > (int64_t)P.n_views * kTile ? P.total_rays : (int64_t)P.n_views * kTile;
-  k_march_emit<<<ceil_div(n, kMarchB), kMarchB, 0, s>>>(P);
+  const int block = P.march_coop ? kMarchB : 256;
+  k_march_emit<<<ceil_div(n, block), block, 0, s>>>(P);
   return cudaGetLastError();
 }
 
