@@ -3,6 +3,7 @@ line carries the contract's keys, and the replica aggregation is the documented 
 import json
 import os
 import subprocess
+import dataclasses
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -72,9 +73,31 @@ def test_headline_roofline_object():
     assert r["kernel"] == "encode_bwd" and r["bound"] == "l2" and r["peak"] == 3000.0
     want = S * L * 64 / 5e-3 / 1e9                                             # 5 ms per record
     assert abs(r["achieved"] - want) < 0.1 and abs(r["frac"] - want / 3000.0) < 1e-4
-    assert r["traffic"] is None
+    assert r["traffic"] is None and r["l2_traffic"] is None and r["l2_traffic_gbs"] is None
     hbm = S * (12 + L * (8 + 64)) / 5e-3 / 1e9
     assert abs(r["hbm"]["achieved"] - hbm) < 0.1 and abs(r["hbm"]["frac"] - hbm / 6000.0) < 1e-4
     # without a probe measurement the scatter falls back to its HBM view
     r0 = bench.roofline(kt, tw, 1000, S, {"hbm_gbs": 6000.0})
     assert r0["bound"] == "hbm" and r0["traffic"] is None
+
+
+def test_scatter_traffic_only_for_the_captured_sources():
+    """The captured DRAM and L2 bytes of the scatter ride in the bench line only for the
+    workload they were captured on and while the kernel's sources match the capture's digest;
+    the roofline's L2 rate is those bytes over the record's duration."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2304_03184_b300 import synth
+    name = bench.SCATTER_DRAM["workload"]
+    assert bench.scatter_traffic("another_workload") is None
+    dram, l2 = bench.scatter_traffic(name), bench.scatter_traffic(name, "l2_bytes")
+    if bench.sources_sha16(bench.SCATTER_SOURCES) != bench.SCATTER_DRAM["sources_sha16"]:
+        assert dram is None and l2 is None
+        return
+    assert dram == bench.SCATTER_DRAM["bytes"] and l2 == bench.SCATTER_DRAM["l2_bytes"] and l2 > dram
+    tw = dataclasses.replace(synth.keyframe_batch_workload(n_frames=1, log2_rays=(9.0, 9.5)), name=name)
+    kt = {"encode_bwd": (10.0, 2)}
+    r = bench.roofline(kt, tw, 1000, 2_000_000, {"hbm_gbs": 6000.0}, {"gather_v4_gbs": 4000.0, "atomic_v4_gbs": 3000.0})
+    assert r["traffic"] == dram and r["l2_traffic"] == l2
+    assert abs(r["l2_traffic_gbs"] - l2 / 5e-3 / 1e9) < 0.1
+
