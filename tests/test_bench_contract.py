@@ -1,9 +1,9 @@
 """The bench's reference arm (the FP64 oracle on the host) runs without a GPU: its one JSON
 line carries the contract's keys, and the replica aggregation is the documented formula."""
+import dataclasses
 import json
 import os
 import subprocess
-import dataclasses
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
