@@ -604,6 +604,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   bool any = false;
   int theta_view = -1;
   const DeformDev* Dp = nullptr;
+  __shared__ int s_ok, s_any;          // warp 0's outcome, for the read-out by every warp
+  __shared__ const DeformDev* s_dp;
 
   // the sequence: tiles T = blockIdx.x, +gridDim.x, ... of views with this kind of net;
   // per tile n + 2 pairs
@@ -641,81 +643,106 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
     }
     loading[b] = true;
   };
-  // all threads: buffer b's MMAs have completed (bounded)
+  // warp 0: buffer b's MMAs have completed (bounded)
   auto drain = [&](int b) -> bool {
     if (!pending[b]) return true;
     const bool got = tc::mbar_wait(mbar0 + 8 * b, phase[b], P.wait_limit);
-    if (!__syncthreads_and(got)) return false;
+    if (!__all_sync(0xffffffffu, got)) return false;
     phase[b] ^= 1u;
     pending[b] = false;
     return true;
   };
 
-  int64_t T = first_tile(blockIdx.x);
-  int i = 0, v = T < n_tiles ? tile_view(T) : -1;
-  int p = 0;  // position in the sequence; buffer p & 1
-  if (T < n_tiles) load_pair(pair_of(T, 0, P.v[v].deform.n_hidden), 0);
-  while (T < n_tiles && ok) {
-    const DeformDev& D = P.v[v].deform;
-    const int n = D.n_hidden;
-    const int b = p & 1;
-    Dp = &D;
-    if (i == 0 && v != theta_view) {
-      // Theta rows = this view's pose, padded to 80 columns, once the MMAs that read the
-      // previous Theta have completed
-      if (!(ok = drain(0) && drain(1))) break;
-      for (int k = 0; k < kDeformTcMaxPose; k += 8) {
-        float x[8];
+  // the sequence runs in warp 0 alone (its waits are warp votes, not block barriers); the
+  // other warps join for the partial's read-out
+  if (warp == 0) {
+    int64_t T = first_tile(blockIdx.x);
+    int i = 0, v = T < n_tiles ? tile_view(T) : -1;
+    int p = 0;  // position in the sequence; buffer p & 1
+    if (T < n_tiles) load_pair(pair_of(T, 0, P.v[v].deform.n_hidden), 0);
+    while (T < n_tiles && ok) {
+      const DeformDev& D = P.v[v].deform;
+      const int n = D.n_hidden;
+      const int b = p & 1;
+      Dp = &D;
+      if (i == 0 && v != theta_view) {
+        // Theta rows = this view's pose, padded to 80 columns, once the MMAs that read the
+        // previous Theta have completed
+        if (!(ok = drain(0) && drain(1))) break;
+        for (int k = 0; k < kDeformTcMaxPose; k += 8) {
+          float x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = k + u < D.pose_dim ? D.pose[k + u] : 0.0f;
-        uint4 q;
-        q.x = tc::pack2<BF16>(x[0], x[1]);
-        q.y = tc::pack2<BF16>(x[2], x[3]);
-        q.z = tc::pack2<BF16>(x[4], x[5]);
-        q.w = tc::pack2<BF16>(x[6], x[7]);
-        *reinterpret_cast<uint4*>(sm + D_THETA + tc::kmajor_offset(t, k, kDeformTcMaxPose)) = q;
+          for (int u = 0; u < 8; ++u) x[u] = k + u < D.pose_dim ? D.pose[k + u] : 0.0f;
+          uint4 q;
+          q.x = tc::pack2<BF16>(x[0], x[1]);
+          q.y = tc::pack2<BF16>(x[2], x[3]);
+          q.z = tc::pack2<BF16>(x[4], x[5]);
+          q.w = tc::pack2<BF16>(x[6], x[7]);
+          for (int r = t; r < kTM; r += 32)  // four rows per lane
+            *reinterpret_cast<uint4*>(sm + D_THETA + tc::kmajor_offset(r, k, kDeformTcMaxPose)) = q;
+        }
+        tc::fence_smem_to_async();
+        __syncwarp();
+        theta_view = v;
       }
-      tc::fence_smem_to_async();
-      tc::fence_before_sync();
-      __syncthreads();
-      theta_view = v;
+      const DwPair cur = pair_of(T, i, n);
+      // the next pair of the sequence (possibly the next tile's first), loaded into the other
+      // buffer once pair p-1's MMAs have released it
+      int64_t T2 = T;
+      int i2 = i + 1, v2 = v;
+      if (i2 > n + 1) {
+        T2 = first_tile(T + gridDim.x);
+        i2 = 0;
+        v2 = T2 < n_tiles ? tile_view(T2) : -1;
+      }
+      if (T2 < n_tiles) {
+        if (!(ok = drain(b ^ 1))) break;
+        load_pair(pair_of(T2, i2, P.v[v2].deform.n_hidden), b ^ 1);
+      }
+      // this pair's tiles have landed: issue its MMAs
+      ok = tc::mbar_wait(lbar0 + 8 * b, lphase[b], P.wait_limit);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      lphase[b] ^= 1u;
+      loading[b] = false;
+      if (t == 0) {
+        tc::fence_after_sync();
+        issue_dw<BF16>(tmem + cur.dcol, sbase + D_BUF + (2 * b) * kHTile, cur.a_units,
+                       cur.b ? sbase + D_BUF + (2 * b + 1) * kHTile : sbase + D_THETA, cur.b_units, any);
+        tc::commit_to(mbar0 + 8 * b);
+      }
+      pending[b] = true;
+      ++p;
+      if (i == n + 1) any = true;  // every accumulator has been written once
+      T = T2;
+      i = i2;
+      v = v2;
     }
-    const DwPair cur = pair_of(T, i, n);
-    // the next pair of the sequence (possibly the next tile's first), loaded into the other
-    // buffer once pair p-1's MMAs have released it
-    int64_t T2 = T;
-    int i2 = i + 1, v2 = v;
-    if (i2 > n + 1) {
-      T2 = first_tile(T + gridDim.x);
-      i2 = 0;
-      v2 = T2 < n_tiles ? tile_view(T2) : -1;
+    for (int b = 0; b < 2 && ok; ++b) ok = drain(b);
+    if (!ok) {
+      if (t == 0) atomicOr(P.status, kStatusTimeout);
+      // let this CTA's MMAs and copies in flight finish (bounded) before its tensor memory and
+      // shared memory are released
+      for (int b = 0; b < 2; ++b) {
+        if (pending[b] && !tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit))
+          atomicOr(P.status, kStatusDrainTimeout);
+        if (loading[b] && !tc::mbar_wait(lbar0 + 8 * b, lphase[b], kDrainLimit))
+          atomicOr(P.status, kStatusDrainTimeout);
+      }
     }
-    if (T2 < n_tiles) {
-      if (!(ok = drain(b ^ 1))) break;
-      load_pair(pair_of(T2, i2, P.v[v2].deform.n_hidden), b ^ 1);
-    }
-    // this pair's tiles have landed: issue its MMAs
-    ok = tc::mbar_wait(lbar0 + 8 * b, lphase[b], P.wait_limit);
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    lphase[b] ^= 1u;
-    loading[b] = false;
     if (t == 0) {
-      tc::fence_after_sync();
-      issue_dw<BF16>(tmem + cur.dcol, sbase + D_BUF + (2 * b) * kHTile, cur.a_units,
-                     cur.b ? sbase + D_BUF + (2 * b + 1) * kHTile : sbase + D_THETA, cur.b_units, any);
-      tc::commit_to(mbar0 + 8 * b);
+      s_ok = ok;
+      s_any = any;
+      s_dp = Dp;
     }
-    pending[b] = true;
-    ++p;
-    if (i == n + 1) any = true;  // every accumulator has been written once
-    T = T2;
-    i = i2;
-    v = v2;
-  }
-  for (int b = 0; b < 2 && ok; ++b) ok = drain(b);
+  }  // warp 0
+  tc::fence_before_sync();
+  __syncthreads();
+  ok = s_ok;
+  any = s_any;
+  Dp = s_dp;
   if (ok && Dp) {
     // write this CTA's partial: lane t is row t of every accumulator
     tc::fence_after_sync();
@@ -752,15 +779,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
 #pragma unroll
       for (int u = 0; u < 16; ++u)
         if (c + u < D.pose_dim) part[(int64_t)t * n_in + D.n_feat + c + u] = any ? v16[u] * out_scale : 0.0f;
-    }
-  }
-  if (!ok) {
-    if (t == 0) atomicOr(P.status, kStatusTimeout);
-    // let this CTA's MMAs and copies in flight finish (bounded) before its tensor memory and
-    // shared memory are released
-    for (int b = 0; b < 2; ++b) {
-      if (pending[b] && !tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
-      if (loading[b] && !tc::mbar_wait(lbar0 + 8 * b, lphase[b], kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
     }
   }
   tc::fence_before_sync();
