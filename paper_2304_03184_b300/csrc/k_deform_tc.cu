@@ -559,8 +559,9 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
 // then written as this CTA's partial (summed over CTAs by k_deform_reduce).  The operand
 // pairs of the CTA's tiles form one sequence; pair p+1's stored tiles arrive by bulk copies
 // into the other of two buffers while pair p's MMAs run (as soon as pair p-1's MMAs have
-// released that buffer).  Theta is rewritten by the threads when the view changes, after
-// the MMAs in flight have drained.
+// released that buffer); a tile's last pair (g_1, x) also feeds dW_1p from the same g_1
+// tile, so each tile takes n + 1 pairs.  Theta is rewritten when the view changes, after the
+// MMAs in flight have drained.
 constexpr uint32_t C_DWO = 384, C_DW1F = 400, C_DW1P = 432;
 constexpr uint32_t D_BUF = 0;                              // 2 x 2 x [128 x 128] operand buffers
 constexpr uint32_t D_THETA = D_BUF + 4 * kHTile;           // [128 x 80]
@@ -570,7 +571,7 @@ constexpr uint32_t kSmemDw = D_MISC + 64 + 1024;
 // One operand pair of the weight-gradient sequence.
 struct DwPair {
   const uint8_t* a;   // [128 samples][a_units] stored tile
-  const uint8_t* b;   // [128 samples][b_units] stored tile, or null for Theta
+  const uint8_t* b;   // [128 samples][b_units] stored tile
   int a_units, b_units;
   uint32_t dcol;      // accumulator columns
 };
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   __shared__ const DeformDev* s_dp;
 
   // the sequence: tiles T = blockIdx.x, +gridDim.x, ... of views with this kind of net;
-  // per tile n + 2 pairs
+  // per tile n + 1 pairs
   auto tile_view = [&](int64_t T) -> int {
     for (; T < n_tiles; T += gridDim.x) {
       const int v = view_of_slot(P, T * kTM);
@@ -630,16 +631,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
     auto G_ = [&](int l) { return gb + ((int64_t)l * tiles_cap + T) * kHTile; };
     if (i == 0) return DwPair{H_(n - 1), P.ws.def_gout + T * kGoTile, kH, 16, C_DWO};
     if (i < n) return DwPair{G_(n - i), H_(n - i - 1), kH, kH, 128u * (uint32_t)(n - i - 1)};
-    if (i == n) return DwPair{G_(0), P.ws.def_x + T * kXTile, kH, kKf, C_DW1F};
-    return DwPair{G_(0), nullptr, kH, kDeformTcMaxPose, C_DW1P};
+    return DwPair{G_(0), P.ws.def_x + T * kXTile, kH, kKf, C_DW1F};
   };
   // one thread: bulk copies of a pair's stored tiles into buffer b
   auto load_pair = [&](const DwPair& q, int b) {
     if (t == 0) {
-      const uint32_t abytes = (uint32_t)(kTM * q.a_units * 2), bbytes = q.b ? (uint32_t)(kTM * q.b_units * 2) : 0u;
+      const uint32_t abytes = (uint32_t)(kTM * q.a_units * 2), bbytes = (uint32_t)(kTM * q.b_units * 2);
       tc::mbar_expect_tx(lbar0 + 8 * b, abytes + bbytes);
       tc::bulk_g2s(sbase + D_BUF + (2 * b) * kHTile, q.a, abytes, lbar0 + 8 * b);
-      if (q.b) tc::bulk_g2s(sbase + D_BUF + (2 * b + 1) * kHTile, q.b, bbytes, lbar0 + 8 * b);
+      tc::bulk_g2s(sbase + D_BUF + (2 * b + 1) * kHTile, q.b, bbytes, lbar0 + 8 * b);
     }
     loading[b] = true;
   };
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
       // buffer once pair p-1's MMAs have released it
       int64_t T2 = T;
       int i2 = i + 1, v2 = v;
-      if (i2 > n + 1) {
+      if (i2 > n) {
         T2 = first_tile(T + gridDim.x);
         i2 = 0;
         v2 = T2 < n_tiles ? tile_view(T2) : -1;
@@ -710,12 +710,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
       if (t == 0) {
         tc::fence_after_sync();
         issue_dw<BF16>(tmem + cur.dcol, sbase + D_BUF + (2 * b) * kHTile, cur.a_units,
-                       cur.b ? sbase + D_BUF + (2 * b + 1) * kHTile : sbase + D_THETA, cur.b_units, any);
+                       sbase + D_BUF + (2 * b + 1) * kHTile, cur.b_units, any);
+        if (i == n)  // the pose columns from the same g_1 tile
+          issue_dw<BF16>(tmem + C_DW1P, sbase + D_BUF + (2 * b) * kHTile, kH, sbase + D_THETA, kDeformTcMaxPose,
+                         any);
         tc::commit_to(mbar0 + 8 * b);
       }
       pending[b] = true;
       ++p;
-      if (i == n + 1) any = true;  // every accumulator has been written once
+      if (i == n) any = true;  // every accumulator has been written once
       T = T2;
       i = i2;
       v = v2;
