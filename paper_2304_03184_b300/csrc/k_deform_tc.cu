@@ -410,8 +410,11 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
       }
     }
   };
+  // The warpgroups meet at a block barrier only where a net's weights are staged: between
+  // stagings each runs its slots' chains at its own pace (a warpgroup that gave up walks on
+  // without work, so both reach every staging barrier and leave the loop together).
   Slot slot[2];
-  while (ok) {
+  while (true) {
     next_tile(slot[0]);
     next_tile(slot[1]);
     if (slot[0].s0 < 0) break;
@@ -422,7 +425,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
     }
     const int H = kH, n = D.n_hidden, Kf = kKf;
     if (D.weights != loaded) {
-      __syncthreads();
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
       const int n_in = D.n_feat + D.pose_dim;
       stage<BF16, kThreadsF>(sm + OFF_W1, D.weights, H, Kf, n_in, H, D.n_feat);
       for (int l = 1; l < n; ++l)
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
       loaded = D.weights;
     }
     const Slot sl = slot[g];
-    if (sl.s0 >= 0) {
+    if (ok && sl.s0 >= 0) {
       const int64_t T = sl.s0 / kTM;
       // g_out tile: dL/dv_c (3 columns) padded to 16, in smem and stored
       {
@@ -536,10 +540,9 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
         }
       }
     }
-    ok = __syncthreads_and(ok);  // both slots' chains done (or one gave up)
   }
   if (!ok) {
-    if (t == 0) atomicOr(P.status, kStatusTimeout);
+    if (tl == 0) atomicOr(P.status, kStatusTimeout);
     if (tl == 0 && pending && !tc::mbar_wait(mbar, phase, kDrainLimit)) atomicOr(P.status, kStatusDrainTimeout);
   }
   tc::fence_before_sync();
