@@ -560,15 +560,16 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
 //   dW_1p            += g_1^T Theta      (128 x 80, columns 432; Theta = the view's pose in
 //                                          every row, the pose columns of W_1)
 // then written as this CTA's partial (summed over CTAs by k_deform_reduce).  The operand
-// pairs of the CTA's tiles form one sequence; pair p+1's stored tiles arrive by bulk copies
-// into the other of two buffers while pair p's MMAs run (as soon as pair p-1's MMAs have
-// released that buffer); a tile's last pair (g_1, x) also feeds dW_1p from the same g_1
-// tile, so each tile takes n + 1 pairs.  Theta is rewritten when the view changes, after the
-// MMAs in flight have drained.
+// pairs of the CTA's tiles form one sequence; the stored tiles of pairs p+1 and p+2 arrive by
+// bulk copies into the other two of three buffers while pair p's MMAs run (pair p+2's as soon
+// as pair p-1's MMAs have released its buffer); a tile's last pair (g_1, x) also feeds dW_1p
+// from the same g_1 tile, so each tile takes n + 1 pairs.  Theta is rewritten when the view
+// changes, after the MMAs in flight have drained.
 constexpr uint32_t C_DWO = 384, C_DW1F = 400, C_DW1P = 432;
-constexpr uint32_t D_BUF = 0;                              // 2 x 2 x [128 x 128] operand buffers
-constexpr uint32_t D_THETA = D_BUF + 4 * kHTile;           // [128 x 80]
-constexpr uint32_t D_MISC = D_THETA + kTM * kDeformTcMaxPose * 2;   // 4 mbarriers + TMEM base
+constexpr int kDwBufs = 3;                                 // operand pair buffers
+constexpr uint32_t D_BUF = 0;                              // kDwBufs x 2 x [128 x 128] operand buffers
+constexpr uint32_t D_THETA = D_BUF + 2 * kDwBufs * kHTile;   // [128 x 80]
+constexpr uint32_t D_MISC = D_THETA + kTM * kDeformTcMaxPose * 2;   // 2 kDwBufs mbarriers + TMEM base
 constexpr uint32_t kSmemDw = D_MISC + 64 + 1024;
 
 // One operand pair of the weight-gradient sequence.
@@ -585,16 +586,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   const int64_t S_cap = P.ws.S_cap;
   const int64_t S = P.ws.view_base[P.n_views];
   const int t = threadIdx.x, warp = t >> 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + D_MISC + 32);
-  const uint32_t mbar0 = tc::smem_u32(sm + D_MISC);        // MMAs of buffer b done: mbar0 + 8 b
-  const uint32_t lbar0 = tc::smem_u32(sm + D_MISC + 16);   // copies into buffer b landed: lbar0 + 8 b
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + D_MISC + 16 * kDwBufs);
+  const uint32_t mbar0 = tc::smem_u32(sm + D_MISC);                 // MMAs of buffer b done: mbar0 + 8 b
+  const uint32_t lbar0 = tc::smem_u32(sm + D_MISC + 8 * kDwBufs);   // copies into buffer b landed: lbar0 + 8 b
   const uint32_t sbase = tc::smem_u32(sm);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), kTmemCols);
   if (t == 0) {
-    tc::mbar_init(mbar0, 1);
-    tc::mbar_init(mbar0 + 8, 1);
-    tc::mbar_init(lbar0, 1);
-    tc::mbar_init(lbar0 + 8, 1);
+    for (int b = 0; b < kDwBufs; ++b) {
+      tc::mbar_init(mbar0 + 8 * b, 1);
+      tc::mbar_init(lbar0 + 8 * b, 1);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -602,8 +603,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   const uint32_t tmem = *tmem_slot;
   const int64_t tiles_cap = S_cap / kTM;
   const int64_t n_tiles = S <= S_cap ? S / kTM : 0;
-  uint32_t phase[2] = {0u, 0u}, lphase[2] = {0u, 0u};
-  bool pending[2] = {false, false}, loading[2] = {false, false};
+  uint32_t phase[kDwBufs] = {}, lphase[kDwBufs] = {};
+  bool pending[kDwBufs] = {}, loading[kDwBufs] = {};
   bool ok = true;
   bool any = false;
   int theta_view = -1;
@@ -659,19 +660,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
   // the sequence runs in warp 0 alone (its waits are warp votes, not block barriers); the
   // other warps join for the partial's read-out
   if (warp == 0) {
-    int64_t T = first_tile(blockIdx.x);
-    int i = 0, v = T < n_tiles ? tile_view(T) : -1;
-    int p = 0;  // position in the sequence; buffer p & 1
-    if (T < n_tiles) load_pair(pair_of(T, 0, P.v[v].deform.n_hidden), 0);
-    while (T < n_tiles && ok) {
-      const DeformDev& D = P.v[v].deform;
-      const int n = D.n_hidden;
-      const int b = p & 1;
+    // a position in the sequence: tile T (view v), pair i
+    struct Pos {
+      int64_t T;
+      int i, v;
+    };
+    auto advance = [&](Pos q) -> Pos {
+      if (++q.i > P.v[q.v].deform.n_hidden) {
+        q.T = first_tile(q.T + gridDim.x);
+        q.i = 0;
+        q.v = q.T < n_tiles ? tile_view(q.T) : -1;
+      }
+      return q;
+    };
+    Pos cur{first_tile(blockIdx.x), 0, -1};
+    if (cur.T < n_tiles) cur.v = tile_view(cur.T);
+    Pos ahead = cur;  // the next pair to load
+    int p = 0, lp = 0;  // pairs issued, pairs loaded; pair p in buffer p % kDwBufs
+    for (; lp < kDwBufs - 1 && ahead.T < n_tiles; ++lp) {
+      load_pair(pair_of(ahead.T, ahead.i, P.v[ahead.v].deform.n_hidden), lp % kDwBufs);
+      ahead = advance(ahead);
+    }
+    while (cur.T < n_tiles && ok) {
+      const DeformDev& D = P.v[cur.v].deform;
+      const int n = D.n_hidden, i = cur.i;
+      const int b = p % kDwBufs;
       Dp = &D;
-      if (i == 0 && v != theta_view) {
+      if (i == 0 && cur.v != theta_view) {
         // Theta rows = this view's pose, padded to 80 columns, once the MMAs that read the
         // previous Theta have completed
-        if (!(ok = drain(0) && drain(1))) break;
+        for (int q = 0; q < kDwBufs && ok; ++q) ok = drain(q);
+        if (!ok) break;
         for (int k = 0; k < kDeformTcMaxPose; k += 8) {
           float x[8];
 #pragma unroll
@@ -686,23 +705,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
         }
         tc::fence_smem_to_async();
         __syncwarp();
-        theta_view = v;
+        theta_view = cur.v;
       }
-      const DwPair cur = pair_of(T, i, n);
-      // the next pair of the sequence (possibly the next tile's first), loaded into the other
-      // buffer once pair p-1's MMAs have released it
-      int64_t T2 = T;
-      int i2 = i + 1, v2 = v;
-      if (i2 > n) {
-        T2 = first_tile(T + gridDim.x);
-        i2 = 0;
-        v2 = T2 < n_tiles ? tile_view(T2) : -1;
-      }
-      if (T2 < n_tiles) {
-        if (!(ok = drain(b ^ 1))) break;
-        load_pair(pair_of(T2, i2, P.v[v2].deform.n_hidden), b ^ 1);
+      // keep kDwBufs - 1 pairs loading ahead (the sequence runs on into the next tiles): pair
+      // lp goes into the buffer that pair lp - kDwBufs = p - 1 releases when its MMAs complete
+      if (ahead.T < n_tiles) {
+        const int bl = lp % kDwBufs;
+        if (!(ok = drain(bl))) break;
+        load_pair(pair_of(ahead.T, ahead.i, P.v[ahead.v].deform.n_hidden), bl);
+        ahead = advance(ahead);
+        ++lp;
       }
       // this pair's tiles have landed: issue its MMAs
+      const DwPair q = pair_of(cur.T, i, n);
       ok = tc::mbar_wait(lbar0 + 8 * b, lphase[b], P.wait_limit);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
@@ -712,8 +727,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
       loading[b] = false;
       if (t == 0) {
         tc::fence_after_sync();
-        issue_dw<BF16>(tmem + cur.dcol, sbase + D_BUF + (2 * b) * kHTile, cur.a_units,
-                       sbase + D_BUF + (2 * b + 1) * kHTile, cur.b_units, any);
+        issue_dw<BF16>(tmem + q.dcol, sbase + D_BUF + (2 * b) * kHTile, q.a_units,
+                       sbase + D_BUF + (2 * b + 1) * kHTile, q.b_units, any);
         if (i == n)  // the pose columns from the same g_1 tile
           issue_dw<BF16>(tmem + C_DW1P, sbase + D_BUF + (2 * b) * kHTile, kH, sbase + D_THETA, kDeformTcMaxPose,
                          any);
@@ -722,16 +737,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_deform_dw_tc(const __grid_const
       pending[b] = true;
       ++p;
       if (i == n) any = true;  // every accumulator has been written once
-      T = T2;
-      i = i2;
-      v = v2;
+      cur = advance(cur);
     }
-    for (int b = 0; b < 2 && ok; ++b) ok = drain(b);
+    for (int b = 0; b < kDwBufs && ok; ++b) ok = drain(b);
     if (!ok) {
       if (t == 0) atomicOr(P.status, kStatusTimeout);
       // let this CTA's MMAs and copies in flight finish (bounded) before its tensor memory and
       // shared memory are released
-      for (int b = 0; b < 2; ++b) {
+      for (int b = 0; b < kDwBufs; ++b) {
         if (pending[b] && !tc::mbar_wait(mbar0 + 8 * b, phase[b], kDrainLimit))
           atomicOr(P.status, kStatusDrainTimeout);
         if (loading[b] && !tc::mbar_wait(lbar0 + 8 * b, lphase[b], kDrainLimit))
