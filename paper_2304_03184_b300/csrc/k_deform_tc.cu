@@ -577,6 +577,8 @@ constexpr uint32_t D_BUF = 0;                              // kDwBufs x 2 x [128
 constexpr uint32_t D_THETA = D_BUF + 2 * kDwBufs * kHTile;   // [128 x 80]
 constexpr uint32_t D_MISC = D_THETA + kTM * kDeformTcMaxPose * 2;   // 2 kDwBufs mbarriers + TMEM base
 constexpr uint32_t kSmemDw = D_MISC + 64 + 1024;
+static_assert(16 * kDwBufs + 4 <= 64, "the mbarriers and the tensor-memory base fit the misc block");
+static_assert(kSmemDw <= 227 * 1024, "the weight-gradient kernel's buffers fit one CTA");
 
 // One operand pair of the weight-gradient sequence.
 struct DwPair {
