@@ -445,6 +445,14 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
     const Slot sl = slot[g];
     if (ok && sl.s0 >= 0) {
       const int64_t T = sl.s0 / kTM;
+      // the ReLU mask rows (this thread's row of the stored h tile) of the next stage, loaded
+      // one stage ahead so that they arrive under the MMAs (the first stage's beside dL/dv_c)
+      uint4 mrow[16];
+      if (n >= 1) {
+        const uint8_t* hg = P.ws.def_h + ((int64_t)(n - 1) * tiles_cap + T) * kHTile;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) mrow[c] = __ldg(reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(tl, 8 * c, H)));
+      }
       // g_out tile: dL/dv_c (3 columns) padded to 16, in smem and stored
       {
         const int64_t gs = sl.s0 + tl;
@@ -476,14 +484,6 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_deform_chain_tc(const __grid_c
         tc::commit_to(mbar);
       }
       pending = true;
-      // the ReLU mask rows (this thread's row of the stored h tile) of the next stage, loaded
-      // one stage ahead so that they arrive under the MMAs
-      uint4 mrow[16];
-      if (n >= 1) {
-        const uint8_t* hg = P.ws.def_h + ((int64_t)(n - 1) * tiles_cap + T) * kHTile;
-#pragma unroll
-        for (int c = 0; c < 16; ++c) mrow[c] = __ldg(reinterpret_cast<const uint4*>(hg + tc::kmajor_offset(tl, 8 * c, H)));
-      }
       // stage e = 0..n-1: mask with h_{n-1-e}, store g, issue the next adjoint; stage n: dL/df
       for (int e = 0; e <= n; ++e) {
         ok = wg_and(bar, tc::mbar_wait(mbar, phase, P.wait_limit));
